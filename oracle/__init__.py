@@ -1,0 +1,395 @@
+"""Plain FP64 CPU oracle of the SPAI / SPAI-update / right-preconditioned block GMRES path.
+
+TEST INFRASTRUCTURE ONLY: the test-suite, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package; the product library never does.
+It shares no code with the CUDA path (separate C file, separate numpy code); both only
+consume the seeded inputs of the ``synth`` module.
+
+What it computes, with the passage of arXiv 1809.06574 it writes out:
+
+* ``coefficients`` / ``assemble`` -- A(p, s) = s^2 M + s D + K(p) with Rayleigh damping
+  D = 0.05 M + 0.01 K(p) and K(p) = K0 + p K1, written as the affine combination of
+  Sec. 1.1 (Eqs. (4)-(9)) on the union of the terms' patterns.
+* ``pattern`` / ``index_sets`` -- the fixed column patterns J_k (pattern of A or of A^2)
+  and row sets I_k of the column least-squares problems of Sec. 2.2.
+* ``spai_build`` -- min_P ||I - A P||_F, column by column (Sec. 2.2), by Householder QR.
+* ``spai_update`` -- min_Q ||A(1) - A(l) Q||_F (Table 1 first approach, Sec. 2.4),
+  P_l = Q_l P_1 kept factored; ``spai_update_chained`` is Table 1's second approach.
+* ``block_gmres`` -- the right-preconditioned (Sec. 2.2 footnote) block Krylov solve
+  of Sec. 2.1: block GMRES(m) over span{R0, AP R0, (AP)^2 R0, ...}.
+* ``lu_solve`` -- dense LU with partial pivoting for tiny reference solves.
+
+Pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py`` against closed forms
+(full pattern -> A^{-1}, diagonal A -> 1/a_ii, diagonal pattern -> a_kk/||A(:,k)||^2,
+unchanged parameter -> Q = I, scaled A -> Q = I/c, the Appendix I example), brute-force
+least squares on dense matrices, SciPy's GMRES for one right-hand side and a dense
+solve.  Parity is pinned for every function listed above.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        i32, i64, dbl = C.c_int32, C.c_int64, C.c_double
+        P = C.c_void_p
+        L.oracle_union_pattern.restype = i64
+        L.oracle_union_pattern.argtypes = [i32, i32, P, P, P, P, P]
+        L.oracle_assemble_values.restype = None
+        L.oracle_assemble_values.argtypes = [i32, i32, P, P, P, P, P, P, P, P]
+        L.oracle_csr_to_csc.restype = None
+        L.oracle_csr_to_csc.argtypes = [i32, P, P, P, P, P, P]
+        L.oracle_pattern_a2.restype = i64
+        L.oracle_pattern_a2.argtypes = [i32, P, P, P, P]
+        L.oracle_index_sets.restype = i64
+        L.oracle_index_sets.argtypes = [i32, P, P, P, P, P, P]
+        L.oracle_spai_columns.restype = i64
+        L.oracle_spai_columns.argtypes = [i32, P, P, P, P, P, P, P, i32, P, P, P, i32, i32, P, P]
+        L.oracle_spmm_csr.restype = None
+        L.oracle_spmm_csr.argtypes = [i32, P, P, P, i32, P, i64, P, i64]
+        L.oracle_spmm_csc.restype = None
+        L.oracle_spmm_csc.argtypes = [i32, P, P, P, i32, P, i64, P, i64]
+        L.oracle_dense_lu_solve.restype = i32
+        L.oracle_dense_lu_solve.argtypes = [i32, P, i64, i32, P, i64]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# --------------------------------------------------------------------------------------
+# assembly (Sec. 1.1)
+# --------------------------------------------------------------------------------------
+
+def coefficients(p: float, s: float):
+    """Coefficients of (M, K0, K1) in A(p, s) = s^2 M + s D(p) + K(p).
+
+    D(p) = 0.05 M + 0.01 K(p) (Rayleigh damping, the alpha M + beta K form of Sec. 3),
+    K(p) = K0 + p K1.  Collecting terms: (s^2 + 0.05 s) M + (1 + 0.01 s) K0
+    + (1 + 0.01 s) p K1.
+    """
+    return [s * s + 0.05 * s, 1.0 + 0.01 * s, (1.0 + 0.01 * s) * p]
+
+
+def _concat_terms(terms, n):
+    T = len(terms)
+    rp = np.concatenate([_i32(t[0]) for t in terms])
+    assert rp.size == T * (n + 1)
+    ci = np.concatenate([_i32(t[1]) for t in terms])
+    va = np.concatenate([_f64(t[2]) for t in terms])
+    off = np.zeros(T, dtype=np.int64)
+    acc = 0
+    for t in range(T):
+        off[t] = acc
+        acc += len(terms[t][1])
+    return T, rp, ci, va, off
+
+
+def union_pattern(terms, n):
+    T, rp, ci, _va, off = _concat_terms(terms, n)
+    L = lib()
+    nnz = L.oracle_union_pattern(n, T, _p(rp), _p(ci), _p(off), None, None)
+    rowptr = np.zeros(n + 1, np.int32)
+    colind = np.zeros(max(nnz, 1), np.int32)
+    L.oracle_union_pattern(n, T, _p(rp), _p(ci), _p(off), _p(rowptr), _p(colind))
+    return rowptr, colind[:nnz]
+
+
+def assemble(terms, coef, n):
+    """CSR of sum_t coef[t] * terms[t] on the union pattern (structural zeros kept)."""
+    T, rp, ci, va, off = _concat_terms(terms, n)
+    rowptr, colind = union_pattern(terms, n)
+    val = np.zeros(max(len(colind), 1))
+    cf = _f64(coef)
+    assert cf.size == T
+    lib().oracle_assemble_values(n, T, _p(rp), _p(ci), _p(va), _p(off), _p(cf), _p(rowptr),
+                                 _p(colind), _p(val))
+    return rowptr, colind, val[:len(colind)]
+
+
+# --------------------------------------------------------------------------------------
+# patterns and index sets (Sec. 2.2)
+# --------------------------------------------------------------------------------------
+
+def csr_to_csc(A, n):
+    rowptr, colind, val = _i32(A[0]), _i32(A[1]), _f64(A[2])
+    nnz = len(colind)
+    colptr = np.zeros(n + 1, np.int32)
+    rowind = np.zeros(max(nnz, 1), np.int32)
+    cval = np.zeros(max(nnz, 1))
+    lib().oracle_csr_to_csc(n, _p(rowptr), _p(colind), _p(val), _p(colptr), _p(rowind), _p(cval))
+    return colptr, rowind[:nnz], cval[:nnz]
+
+
+PATTERN_A = 0
+PATTERN_A2 = 1
+
+
+def pattern(A, n, kind=PATTERN_A):
+    """Column patterns J_k of P: pattern of A (columns of A) or structural pattern of A^2."""
+    colptr, rowind, _ = csr_to_csc(A, n)
+    if kind == PATTERN_A:
+        return colptr, rowind
+    L = lib()
+    tot = L.oracle_pattern_a2(n, _p(colptr), _p(rowind), None, None)
+    Jptr = np.zeros(n + 1, np.int32)
+    Jind = np.zeros(max(tot, 1), np.int32)
+    L.oracle_pattern_a2(n, _p(colptr), _p(rowind), _p(Jptr), _p(Jind))
+    return Jptr, Jind[:tot]
+
+
+def index_sets(A, n, Jptr, Jind):
+    colptr, rowind, _ = csr_to_csc(A, n)
+    Jptr, Jind = _i32(Jptr), _i32(Jind)
+    L = lib()
+    tot = L.oracle_index_sets(n, _p(colptr), _p(rowind), _p(Jptr), _p(Jind), None, None)
+    Iptr = np.zeros(n + 1, np.int32)
+    Ilist = np.zeros(max(tot, 1), np.int32)
+    L.oracle_index_sets(n, _p(colptr), _p(rowind), _p(Jptr), _p(Jind), _p(Iptr), _p(Ilist))
+    return Iptr, Ilist[:tot]
+
+
+# --------------------------------------------------------------------------------------
+# SPAI build and update (Sec. 2.2, Sec. 2.3 Table 1, Sec. 2.4)
+# --------------------------------------------------------------------------------------
+
+class Precond:
+    """Column-wise result on pattern J: column k has rows Jind[Jptr[k]:Jptr[k+1]], values val."""
+
+    def __init__(self, n, Jptr, Jind, Iptr, Ilist, val, status, base=None, A_csc=None):
+        self.n, self.Jptr, self.Jind, self.Iptr, self.Ilist = n, Jptr, Jind, Iptr, Ilist
+        self.val, self.status, self.base, self.A_csc = val, status, base, A_csc
+
+    def dense(self):
+        D = np.zeros((self.n, self.n))
+        for k in range(self.n):
+            sl = slice(self.Jptr[k], self.Jptr[k + 1])
+            D[self.Jind[sl], k] = self.val[sl]
+        return D
+
+    def apply_own(self, X):
+        """Y = (this factor) X, X of shape (n, s)."""
+        X = np.asfortranarray(X, dtype=np.float64)
+        n, s = X.shape
+        Y = np.zeros((n, s), order="F")
+        lib().oracle_spmm_csc(n, _p(self.Jptr), _p(self.Jind), _p(self.val), s, _p(X), n, _p(Y), n)
+        return Y
+
+    def apply(self, X):
+        """P_l X with P_l = Q_l P_base (factored apply, Sec. 2.4: P_l = Q_l P_1)."""
+        if self.base is None:
+            return self.apply_own(X)
+        return self.apply_own(self.base.apply(X))
+
+    def dense_product(self):
+        """Explicit P_l = Q_l P_base (test-only)."""
+        if self.base is None:
+            return self.dense()
+        return self.dense() @ self.base.dense_product()
+
+
+def _columns(A_csc, n, Jptr, Jind, Iptr, Ilist, mode, R_csc=None, k0=0, k1=None):
+    colptr, rowind, cval = A_csc
+    k1 = n if k1 is None else k1
+    val = np.zeros(max(len(Jind), 1))
+    status = np.zeros(max(k1 - k0, 1), np.int32)
+    if R_csc is None:
+        R_csc = (colptr, rowind, cval)
+    lib().oracle_spai_columns(n, _p(colptr), _p(rowind), _p(cval), _p(Jptr), _p(Jind), _p(Iptr),
+                              _p(Ilist), mode, _p(R_csc[0]), _p(R_csc[1]), _p(R_csc[2]), k0, k1,
+                              _p(val), _p(status))
+    return val[:len(Jind)], status[:k1 - k0]
+
+
+def spai_build(A, n, kind=PATTERN_A, k0=0, k1=None):
+    """SPAI of A (Sec. 2.2): column k = argmin over supp in J_k of ||e_k - A m||_2."""
+    A_csc = csr_to_csc(A, n)
+    Jptr, Jind = pattern(A, n, kind)
+    Iptr, Ilist = index_sets(A, n, Jptr, Jind)
+    val, status = _columns(A_csc, n, Jptr, Jind, Iptr, Ilist, 0, None, k0, k1)
+    return Precond(n, Jptr, Jind, Iptr, Ilist, val, status, None, A_csc)
+
+
+def spai_update(base: Precond, A_new, n, k0=0, k1=None):
+    """Update of the first approach (Table 1, Sec. 2.4).
+
+    Column k of Q_l = argmin over supp in J_k of ||a1_k - A(l) q||_2, where a1_k is column
+    k of the base matrix A(1); the preconditioner of A(l) is P_l = Q_l P_1, applied
+    factored.  Q_l takes P_1's pattern (the paper does not state one).
+    """
+    root = base
+    while root.base is not None:
+        root = root.base
+    A_csc = csr_to_csc(A_new, n)
+    val, status = _columns(A_csc, n, root.Jptr, root.Jind, root.Iptr, root.Ilist, 1, root.A_csc,
+                           k0, k1)
+    return Precond(n, root.Jptr, root.Jind, root.Iptr, root.Ilist, val, status, root, A_csc)
+
+
+def spai_update_chained(prev: Precond, A_new, n):
+    """Second approach of Table 1: min ||A(i-1) - A(i) Q_i||_F and P_i = Q_i P_{i-1}."""
+    A_csc = csr_to_csc(A_new, n)
+    val, status = _columns(A_csc, n, prev.Jptr, prev.Jind, prev.Iptr, prev.Ilist, 1, prev.A_csc)
+    return Precond(n, prev.Jptr, prev.Jind, prev.Iptr, prev.Ilist, val, status, prev, A_csc)
+
+
+def spmm(A, X, n):
+    """Y = A X for CSR A and dense X (n, s)."""
+    X = np.asfortranarray(X, dtype=np.float64)
+    s = X.shape[1]
+    Y = np.zeros((n, s), order="F")
+    lib().oracle_spmm_csr(n, _p(_i32(A[0])), _p(_i32(A[1])), _p(_f64(A[2])), s, _p(X), n, _p(Y), n)
+    return Y
+
+
+def lu_solve(D, B):
+    """Dense LU with partial pivoting: returns D^{-1} B (D and B are copied)."""
+    D = np.array(D, dtype=np.float64, order="F")
+    B = np.array(B, dtype=np.float64, order="F", ndmin=2)
+    if B.shape[0] != D.shape[0]:
+        B = B.T.copy(order="F")
+    n, nrhs = B.shape
+    rc = lib().oracle_dense_lu_solve(n, _p(D), n, nrhs, _p(B), n)
+    if rc != 0:
+        raise np.linalg.LinAlgError("singular matrix")
+    return B
+
+
+# --------------------------------------------------------------------------------------
+# right-preconditioned block GMRES(m) (Sec. 2.1; right preconditioning: Sec. 2.2 footnote)
+# --------------------------------------------------------------------------------------
+
+DEFLATE_REL = 1e-12
+
+
+def _block_qr(W, ref):
+    """Orthonormal basis of range(W): W = Q R with R upper triangular (Householder QR).
+
+    Columns are taken in order.  A column whose new direction is negligible -- its
+    diagonal |R_kk| in the QR of [kept columns before it, itself] is <= 1e-12 * ref_k
+    (ref = the column's norm before orthogonalisation) -- is deflated: it gets no basis
+    vector (Q[:, k] = 0, row k of R = 0) and is represented by its coefficients on the
+    kept vectors before it, so it adds nothing to the Krylov space.
+    """
+    n, s = W.shape
+    kept = []
+    for k in range(s):
+        _, Rt = np.linalg.qr(W[:, kept + [k]], mode="reduced")
+        if abs(Rt[-1, -1]) > DEFLATE_REL * ref[k]:
+            kept.append(k)
+    Q = np.zeros((n, s))
+    R = np.zeros((s, s))
+    if kept:
+        Qk, Rk = np.linalg.qr(W[:, kept], mode="reduced")
+        Q[:, kept] = Qk
+        for a, ka in enumerate(kept):
+            for b, kb in enumerate(kept):
+                R[ka, kb] = Rk[a, b]
+        for k in range(s):
+            if k in kept:
+                continue
+            for a, ka in enumerate(kept):
+                if ka < k:
+                    R[ka, k] = Qk[:, a] @ W[:, k]
+    return Q, R
+
+
+class GmresInfo(dict):
+    pass
+
+
+def block_gmres(apply_A, apply_P, B, restart, tol, max_cycles, X0=None, history=False):
+    """Solve A X = B by right-preconditioned block GMRES(restart): A P X~ = B, X = P X~.
+
+    Each cycle builds an orthonormal basis V_0..V_j of the block Krylov space
+    span{R0, (AP) R0, ..., (AP)^j R0} (R0 = B - A X0) by block Arnoldi with two passes of
+    block classical Gram-Schmidt, and takes the iterate minimising every column's
+    residual over that space: Y = argmin ||E_1 S_0 - Hbar_j Y|| (solved directly by
+    least squares), X = X0 + P [V_0..V_j] Y.  The cycle stops early once every column's
+    least-squares residual is <= tol * ||b_i||; after each cycle the true residual
+    B - A X is formed, and the solve stops when every column has ||b_i - A x_i|| <=
+    tol * ||b_i||.  ``apply_P`` may be None (no preconditioner).
+    """
+    B = np.asarray(B, dtype=np.float64)
+    n, s = B.shape
+    m = int(restart)
+    if apply_P is None:
+        def apply_P(X):
+            return X
+    X = np.zeros((n, s)) if X0 is None else np.array(X0, dtype=np.float64)
+    bnorm = np.linalg.norm(B, axis=0)
+    thresh = tol * bnorm
+    R = B - apply_A(X)
+    iters, cycles = 0, 0
+    est_hist = []
+    while True:
+        rn = np.linalg.norm(R, axis=0)
+        if np.all(rn <= thresh) or cycles >= max_cycles:
+            break
+        cycles += 1
+        V0, S0 = _block_qr(R, rn)
+        Vs = [V0]
+        H = np.zeros(((m + 1) * s, m * s))
+        G0 = np.zeros(((m + 1) * s, s))
+        G0[:s] = S0
+        Y = None
+        for j in range(m):
+            Z = apply_P(Vs[j])
+            W = apply_A(Z)
+            wn = np.linalg.norm(W, axis=0)
+            Vc = np.hstack(Vs)
+            H1 = Vc.T @ W
+            W = W - Vc @ H1
+            H2 = Vc.T @ W
+            W = W - Vc @ H2
+            H[:(j + 1) * s, j * s:(j + 1) * s] = H1 + H2
+            Vn, Rn = _block_qr(W, wn)
+            H[(j + 1) * s:(j + 2) * s, j * s:(j + 1) * s] = Rn
+            Vs.append(Vn)
+            Hb = H[:(j + 2) * s, :(j + 1) * s]
+            Gb = G0[:(j + 2) * s]
+            Y = np.linalg.lstsq(Hb, Gb, rcond=None)[0]
+            est = np.linalg.norm(Gb - Hb @ Y, axis=0)
+            est_hist.append(est)
+            iters += 1
+            if np.all(est <= thresh):
+                break
+        U = np.hstack(Vs[:Y.shape[0] // s]) @ Y
+        X = X + apply_P(U)
+        R = B - apply_A(X)
+    rn = np.linalg.norm(R, axis=0)
+    rel = np.where(bnorm > 0, rn / np.where(bnorm > 0, bnorm, 1.0), rn)
+    info = GmresInfo(iterations=iters, cycles=cycles, converged=bool(np.all(rn <= thresh)),
+                     rel_residual=rel)
+    if history:
+        info["estimates"] = est_hist
+    return X, info
+
+
+def csr_apply(A, n):
+    """Closure X -> A X for the oracle's solve (CSR sparse times dense)."""
+    def f(X):
+        return np.asarray(spmm(A, X, n))
+    return f
