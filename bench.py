@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Parameter-sweep benchmark of the SPAI / SPAI-update / block-GMRES hot path on one GPU.
+
+One step = one parameter sweep of the 3D 64^3 7-point workload (n = 262,144):
+20 parameters p ~ U[0.1, 1] (sorted) x shifts s in {0.5, 1, 2} = 60 systems
+A(p, s) = s^2 M + s D(p) + K(p), D = 0.05 M + 0.01 K(p), K(p) = K0 + p K1.  Per shift:
+assemble + SPAI build at the first p and block-GMRES(50) solve, then for the other 19 p:
+assemble + SPAI update (first approach of Table 1) + solve.  B = n x 8, N(0,1), tol 1e-8
+on every column's true residual, FP64 throughout.  value = solves/s over the timed steps.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun each rank runs its own sweep on its own GPU (independent systems, no
+collective; weak scaling) and rank 0 prints one JSON line.  ``--impl reference`` times the
+CPU oracle (test infrastructure) on a bounded sample of the same workload instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "param-sweep solves/s to residual 1e-8, served vs plain FP64; HBM %; p99 latency"
+UNIT = "solves/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--side", type=int, default=64)
+    ap.add_argument("--nparams", type=int, default=20)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(w, nnz):
+    return {
+        "workload": f"3d-{w.dims[0]}^3-7pt parameter sweep: {len(w.params)} p x {len(w.shifts)} s, "
+                    f"{w.B.shape[1]} RHS, SPAI(pattern A) build per shift + updates (Table 1 first "
+                    f"approach), block GMRES({w.restart}), tol {w.tol:g}, FP64",
+        "n": w.n, "nnz": int(nnz), "systems_per_step": len(w.params) * len(w.shifts),
+        "nrhs": int(w.B.shape[1]), "restart": w.restart,
+        "l2": "no flush: the per-solve working set (Krylov basis, 0.86 GB at n=262144) exceeds L2",
+    }
+
+
+# ------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------- oracle
+def oracle_sample(side, nparams, nsys, seed=0):
+    """Time the CPU oracle on the first `nsys` systems of the sweep (build, then updates)."""
+    import oracle
+    import synth
+    w = synth.grid3d_7pt(side=side, nparams=nparams, seed=seed)
+    n = w.n
+    s = w.shifts[0]
+    t0 = time.perf_counter()
+    base = None
+    iters = []
+    for i in range(nsys):
+        p = w.params[i]
+        A = oracle.assemble(w.terms, oracle.coefficients(p, s), n)
+        if i == 0:
+            base = oracle.spai_build(A, n)
+            P = base
+        else:
+            P = oracle.spai_update(base, A, n)
+        X, info = oracle.block_gmres(oracle.csr_apply(A, n), P.apply, w.B, w.restart, w.tol, 50)
+        assert info["converged"]
+        iters.append(info["iterations"])
+    dt = time.perf_counter() - t0
+    return nsys / dt, dt, iters
+
+
+def cpu_baseline(side, nparams, nsys):
+    """Run the oracle sample in a fresh interpreter (all host cores for BLAS)."""
+    cores = os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS=str(cores), OPENBLAS_NUM_THREADS=str(cores))
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "v, dt, it = bench.oracle_sample(%d, %d, %d); print(json.dumps([v, dt, it]))"
+            % (ROOT, side, nparams, nsys))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": f"failed: {r.stderr.strip()[-200:]}"}
+    v, dt, it = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {nsys} systems of the sweep (s=0.5: SPAI build + solve, then update + "
+                      f"solve), same n and RHS, {dt:.1f} s wall, {it} GMRES iterations; FP64 C "
+                      f"(SPAI, sparse products) + numpy/BLAS (block GMRES) with {cores} BLAS threads"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import synth
+    w = synth.grid3d_7pt(side=args.side, nparams=args.nparams)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle_sample(args.side, args.nparams, 1)
+    times = []
+    for _ in range(args.steps):
+        _, dt, it = oracle_sample(args.side, args.nparams, 1)
+        times.append(dt)
+    total = sum(times)
+    value = args.steps / total
+    nnz = 7 * w.n - 6 * w.dims[0] ** 2
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(w, nnz),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "each step: system 1 of the sweep (s=0.5, first p): assemble, "
+                                   "SPAI build, block GMRES(50) to 1e-8, on the host cores"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------- GPU sweep
+class Sweep:
+    def __init__(self, sg, torch, ctx, w, host_inputs=False):
+        self.sg, self.torch, self.ctx, self.w = sg, torch, ctx, w
+        n = w.n
+        self.n = n
+        self.s = w.B.shape[1]
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.dev = dev
+        self.host_inputs = host_inputs
+        if host_inputs:
+            # pinned host copies of the inputs; copied to the device inside every step
+            self.h_terms = []
+            for t in w.terms:
+                self.h_terms.append(tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                                          for a in t))
+            self.h_B = torch.from_numpy(np.ascontiguousarray(w.B.T)).pin_memory()
+            self.h_X = torch.zeros((self.s, n), dtype=torch.float64).pin_memory()
+            self.aff = None
+        else:
+            self.d_terms = [tuple(torch.as_tensor(np.ascontiguousarray(a), device=dev) for a in t)
+                            for t in w.terms]
+            self.aff = sg.spai_affine_create(ctx, [sg.csr(n, *t) for t in self.d_terms])
+            self.d_B = torch.as_tensor(np.ascontiguousarray(w.B.T), device=dev)
+            self.d_X = torch.zeros((self.s, n), dtype=torch.float64, device=dev)
+        self.solves = 0
+        self.iters = []
+
+    def h2d_bytes(self):
+        tb = sum(a.numel() * a.element_size() for t in self.h_terms for a in t)
+        nsys = len(self.w.params) * len(self.w.shifts)
+        per = self.n * self.s * 8
+        return tb + nsys * 2 * per  # terms once + B and the initial guess X0 per solve
+
+    def d2h_bytes(self):
+        return len(self.w.params) * len(self.w.shifts) * self.n * self.s * 8
+
+    def step(self):
+        sg, torch, ctx, w, n = self.sg, self.torch, self.ctx, self.w, self.n
+        aff = self.aff
+        if self.host_inputs:
+            aff = sg.spai_affine_create(ctx, [sg.csr(n, *t) for t in self.h_terms])
+        _, nnz, rp, ci = sg.spai_affine_pattern(aff)
+        vb = torch.empty(nnz, dtype=torch.float64, device=self.dev)
+        va = torch.empty(nnz, dtype=torch.float64, device=self.dev)
+        for s in w.shifts:
+            base = None
+            for i, p in enumerate(w.params):
+                buf = vb if i == 0 else va
+                sg.spai_assemble(ctx, aff, sg.affine_coefficients(p, s), buf)
+                A = sg.csr(n, rp, ci, buf, nnz)
+                if i == 0:
+                    base, _ = sg.spai_build(ctx, A, sg.PATTERN_A)
+                    pc = base
+                else:
+                    pc, _ = sg.spai_update(ctx, base, A, sg.UPDATE_FIRST)
+                if self.host_inputs:
+                    self.h_X.zero_()
+                    st, info, rel = sg.block_solve(ctx, A, pc, self.s, self.h_B, n, self.h_X, n,
+                                                   w.restart, w.tol, 50)
+                else:
+                    self.d_X.zero_()
+                    st, info, rel = sg.block_solve(ctx, A, pc, self.s, self.d_B, n, self.d_X, n,
+                                                   w.restart, w.tol, 50)
+                if not info["converged"]:
+                    raise RuntimeError(f"solve did not converge: p={p} s={s} {info}")
+                self.solves += 1
+                self.iters.append(info["iterations"])
+                if i > 0:
+                    sg.spai_pc_destroy(pc)
+            sg.spai_pc_destroy(base)
+        if self.host_inputs:
+            sg.spai_affine_destroy(aff)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import synth
+    w = synth.grid3d_7pt(side=args.side, nparams=args.nparams, seed=rank)
+    nnz_expected = 7 * w.n - 6 * w.dims[0] ** 2
+
+    # CPU baseline first, before any CUDA work in this process
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.side, args.nparams, 2)
+
+    import torch
+    import paper_1809_06574_gb300 as sg
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    ctx = sg.spai_ctx_create(stream.cuda_stream, 0)
+    fp64_tflops = sg.spai_measure_fp64_rate(ctx)
+
+    sweep = Sweep(sg, torch, ctx, w)
+    for _ in range(args.warmup):
+        sweep.step()
+    sweep.solves, sweep.iters = 0, []
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    sg.spai_ctx_profile(ctx, 1)
+    l0 = sg.spai_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sweep.step()
+    e1.record(stream)
+    barrier()
+    launches = sg.spai_launch_count() - l0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = [sg.spai_ctx_profile_entry(ctx, i) for i in range(sg.spai_ctx_profile_count(ctx))]
+    sg.spai_ctx_profile(ctx, 0)
+    solves = sweep.solves
+    iters = list(sweep.iters)
+    t_local = ms / 1e3
+    if dist is not None:
+        t = torch.tensor([t_local, float(solves)], device="cuda")
+        tm = t.clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ts = t.clone()
+        dist.all_reduce(ts, op=dist.ReduceOp.SUM)
+        t_max, total_solves = tm[0].item(), ts[1].item()
+    else:
+        t_max, total_solves = t_local, float(solves)
+    value = total_solves / t_max
+
+    # end-to-end through the C ABI with pinned host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        hs = Sweep(sg, torch, ctx, w, host_inputs=True)
+        hs.step()  # warm-up
+        hs.solves = 0
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hs.step()
+        barrier()
+        dt = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = t.item()
+        e2e = {"value": total_solves / dt, "unit": UNIT, "h2d_bytes_per_step": hs.h2d_bytes(),
+               "d2h_bytes_per_step": hs.d2h_bytes()}
+
+    if rank == 0:
+        total_ms = sum(f["ms"] for f in prof) or 1.0
+        dom = max(prof, key=lambda f: f["ms"])
+        avg_ms = dom["ms"] / max(dom["launches"], 1)
+        ach_tflops = dom["flops"] / (dom["ms"] * 1e-3) / 1e12 if dom["ms"] else 0.0
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        nominal_fp64 = 152 * 4 * 2070e6 / 1e12
+        roofline = {
+            "kernel": dom["name"], "bound": "alu", "achieved": ach_tflops,
+            "peak": fp64_tflops, "unit": "TFLOP/s", "frac": ach_tflops / fp64_tflops,
+            "traffic": None,
+            "peak_source": "FP64 FMA rate measured in this run (spai_measure_fp64_rate); nominal "
+                           f"152 SM x 4 flop/clk x 2.07 GHz = {nominal_fp64:.2f} TFLOP/s",
+            "avg_launch_ms": avg_ms, "launches": dom["launches"],
+            "algorithmic_bytes_per_launch": dom["bytes"] / max(dom["launches"], 1),
+            "achieved_gbs": dom["bytes"] / (dom["ms"] * 1e-3) / 1e9 if dom["ms"] else 0.0,
+            "hbm_peak_gbs": peaks.get("hbm_gbs"),
+        }
+        kernels = {f["name"]: {"launches": f["launches"], "ms": round(f["ms"], 3),
+                               "share": round(f["ms"] / total_ms, 4),
+                               "tflops": round(f["flops"] / (f["ms"] * 1e-3) / 1e12, 4) if f["ms"] else 0,
+                               "gbs": round(f["bytes"] / (f["ms"] * 1e-3) / 1e9, 1) if f["ms"] else 0}
+                   for f in sorted(prof, key=lambda f: -f["ms"])}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {**workload_config(w, nnz_expected),
+                                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk, "fp64_tflops_measured": fp64_tflops,
+            "gmres_iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)),
+                                 "max": int(max(iters))},
+            "kernels": kernels,
+        }
+        print(json.dumps(line), flush=True)
+    sg.spai_ctx_destroy(ctx)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

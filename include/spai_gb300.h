@@ -1,0 +1,232 @@
+/*
+ * spai_gb300 -- C ABI of the GB300 (sm_103a) library for SPAI preconditioning of
+ * parametric shifted second-order systems, its cheap parameter update, and the
+ * right-preconditioned block GMRES solve that applies it.
+ *
+ * Method: arXiv 1809.06574 (Singh & Ahuja, "Preconditioned Linear Solves for Parametric
+ * Model Order Reduction").  Each entry point below cites the passage that defines the
+ * operation it performs.
+ *
+ * General rules
+ *  - Plain C types only.  Indices are int32 (nnz < 2^31, checked).  Values are FP64.
+ *  - Matrices are CSR with strictly increasing column indices in every row (checked:
+ *    SPAI_EINVAL).  Only square matrices are accepted.
+ *  - Dense blocks (B, X, Y) are column-major n x s arrays with a leading dimension >= n.
+ *  - Unless stated otherwise, pointers are DEVICE pointers to memory the caller owns and
+ *    keeps alive for the duration of the call.  Entry points that also accept HOST
+ *    pointers say so; they detect the memory kind with cudaPointerGetAttributes.
+ *  - Handles (spai_ctx, spai_affine, spai_pc) are owned by the library and released
+ *    with their destroy call.  A handle must not outlive the context that made it.
+ *  - Work is enqueued on the context's CUDA stream.  Calls return after enqueueing
+ *    except where a call must read a result on the host (noted per call).
+ *  - No call aborts, traps or exits: every failure is a status code, with a message
+ *    readable through spai_last_error(ctx).  Device-side checks report through an error
+ *    word, never through a trap.
+ */
+#ifndef SPAI_GB300_H
+#define SPAI_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SPAI_API __attribute__((visibility("default")))
+#else
+#define SPAI_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPAI_OK = 0,
+    SPAI_EINVAL = 1,     /* malformed argument or matrix */
+    SPAI_ENOMEM = 2,     /* device allocation failed or the context's budget is exceeded */
+    SPAI_ECUDA = 3,      /* a CUDA runtime call failed */
+    SPAI_ESINGULAR = 4,  /* a column least-squares problem is rank deficient */
+    SPAI_ENOTCONV = 5,   /* block_solve reached max_cycles before every column converged */
+    SPAI_ETIMEOUT = 6    /* a bounded device-side wait gave up */
+} spai_status;
+
+/* Square CSR matrix: rowptr[n+1], colind[nnz] (ascending within each row), val[nnz]. */
+typedef struct {
+    int32_t n;
+    int32_t nnz;
+    const int32_t *rowptr;
+    const int32_t *colind;
+    const double *val;
+} spai_csr;
+
+typedef struct spai_ctx_s *spai_ctx;
+typedef struct spai_affine_s *spai_affine;
+typedef struct spai_pc_s *spai_pc;
+
+/* Column patterns of the preconditioner (the paper's MSPAI run grows the pattern
+ * adaptively, Sec. 3; here it is fixed). */
+#define SPAI_PATTERN_A 0   /* J_k = rows of column k of A */
+#define SPAI_PATTERN_A2 1  /* J_k = rows of column k of A^2 (structural) */
+
+/* Update approaches of Table 1 (Sec. 2.3). */
+#define SPAI_UPDATE_FIRST 1    /* min ||A(1) - A(l) Q||_F, P_l = Q_l P_1 (proposed, Sec. 2.4) */
+#define SPAI_UPDATE_CHAINED 2  /* min ||A(l-1) - A(l) Q||_F, P_l = Q_l P_{l-1} */
+
+/* ----------------------------------------------------------------------------------
+ * Context
+ * ---------------------------------------------------------------------------------- */
+
+/* Create a context bound to the current CUDA device and to `stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  `mem_budget` caps the device bytes the library
+ * holds at once (0 = no cap); exceeding it returns SPAI_ENOMEM.  The stream is not
+ * owned.  *out is NULL on failure. */
+SPAI_API spai_status spai_ctx_create(spai_ctx *out, void *stream, size_t mem_budget);
+
+/* Release the context's workspace.  Every spai_affine / spai_pc made with it must have
+ * been destroyed first. */
+SPAI_API spai_status spai_ctx_destroy(spai_ctx ctx);
+
+/* Message of the last failed call on this context (never NULL; "" if none). */
+SPAI_API const char *spai_last_error(spai_ctx ctx);
+
+/* Block the host until the context's stream has finished its work. */
+SPAI_API spai_status spai_ctx_sync(spai_ctx ctx);
+
+/* Device bytes currently held by the library for this context (handles + workspace). */
+SPAI_API size_t spai_ctx_mem_in_use(spai_ctx ctx);
+
+/* Number of kernels the library has launched in this process (all contexts). */
+SPAI_API int64_t spai_launch_count(void);
+
+/* Diagnostics: measured FP64 fused-multiply-add throughput of the current device in
+ * TFLOP/s (a short kernel of independent FMA chains on every SM; synchronises).  Most of
+ * this library's FP64 kernels are bound by this rate rather than by HBM bandwidth. */
+SPAI_API spai_status spai_measure_fp64_rate(spai_ctx ctx, double *tflops);
+
+/* Optional timing of the library's kernels by family ("spmm_A", "block_dot", ...): while
+ * enabled, each launch is bracketed by CUDA events recorded on the context's stream and
+ * credited with the algorithmic flops and bytes of that launch.  spai_ctx_profile
+ * enables / disables and clears the totals. */
+SPAI_API spai_status spai_ctx_profile(spai_ctx ctx, int32_t enable);
+/* Number of kernel families recorded so far (synchronises the stream). */
+SPAI_API int32_t spai_ctx_profile_count(spai_ctx ctx);
+/* Totals of family i: launches, summed event time (ms), algorithmic flops and bytes.
+ * *name stays valid until the next spai_ctx_profile call. */
+SPAI_API spai_status spai_ctx_profile_entry(spai_ctx ctx, int32_t i, const char **name,
+                                            int64_t *launches, double *ms, double *flops,
+                                            double *bytes);
+
+/* ----------------------------------------------------------------------------------
+ * Affine assembly, Sec. 1.1 Eqs. (4)-(9): A = A_0 + s~_1 A_1 + ... + s~_{w+1} A_{w+1},
+ * every A(l) being the same combination with other coefficients.  The terms are
+ * merged once onto the union of their patterns (structural zeros kept); afterwards
+ * every A(l) costs one value-only pass.
+ * ---------------------------------------------------------------------------------- */
+
+/* Copy `nterms` (1..16) CSR terms of equal size n into library memory and build the
+ * union pattern.  terms[t] pointers may be HOST or DEVICE memory.  Validates every term
+ * (SPAI_EINVAL).  Synchronises the stream once (it reads the union size). */
+SPAI_API spai_status spai_affine_create(spai_ctx ctx, int32_t nterms, const spai_csr *terms,
+                               spai_affine *out);
+
+/* Union pattern (device pointers owned by the handle, valid until it is destroyed). */
+SPAI_API spai_status spai_affine_pattern(spai_affine aff, int32_t *n, int32_t *nnz,
+                                const int32_t **rowptr, const int32_t **colind);
+
+/* val_out[q] = sum_t coef[t] * term_t(q) on the union pattern, t in order, each product
+ * and sum rounded separately.  coef: HOST array of nterms doubles.  val_out: device,
+ * nnz doubles.  Asynchronous. */
+SPAI_API spai_status spai_assemble(spai_ctx ctx, spai_affine aff, const double *coef, double *val_out);
+
+/* Copy the union pattern into caller memory (HOST or DEVICE): rowptr[n+1], colind[nnz].
+ * Synchronises the stream. */
+SPAI_API spai_status spai_affine_export(spai_ctx ctx, spai_affine aff, int32_t *rowptr,
+                                        int32_t *colind);
+
+SPAI_API spai_status spai_affine_destroy(spai_affine aff);
+
+/* ----------------------------------------------------------------------------------
+ * SPAI build, Sec. 2.2: min_P ||I - A P||_F^2 = sum_k min ||e_k - A p_k||_2^2, one
+ * small least-squares problem per column over the fixed pattern J_k, restricted to
+ * the rows I_k = union of rows(A(:,j)), j in J_k.  Solved on the device by Householder
+ * QR of A(I_k, J_k) and back substitution.
+ * ---------------------------------------------------------------------------------- */
+
+/* Build P for A (device CSR, values read during the call).  pattern_kind is
+ * SPAI_PATTERN_A or SPAI_PATTERN_A2.  The handle keeps the pattern analysis (I_k, J_k),
+ * A's values in column order (for later updates) and P in row order (for the apply).
+ * Synchronises once (reads index-set sizes and the column status).  Returns
+ * SPAI_ESINGULAR if some column problem is rank deficient (|I_k| < |J_k| or
+ * |R_cc| <= 1e-14 max|R_tt|): the handle is still returned, those columns are zero,
+ * and spai_pc_export reports them. */
+SPAI_API spai_status spai_build(spai_ctx ctx, const spai_csr *A, int32_t pattern_kind, spai_pc *out);
+
+/* Cheap update, Table 1 and Sec. 2.4: for A_new = A(l) on the SAME pattern as the base
+ * matrix, column k of Q_l = argmin_{supp q in J_k} ||a1_k - A(l) q||_2 with a1_k column
+ * k of A(1) (approach SPAI_UPDATE_FIRST: A(1) is the root build's matrix; approach
+ * SPAI_UPDATE_CHAINED: A(1) is `base`'s own matrix).  The preconditioner of A(l) is
+ * P_l = Q_l P_base, applied factored as Q_l (P_base X).  No pattern analysis is redone.
+ * `base` must stay alive while the result is used.  Synchronises once (column status).
+ * Returns SPAI_ESINGULAR like spai_build. */
+SPAI_API spai_status spai_update(spai_ctx ctx, spai_pc base, const spai_csr *A_new, int32_t approach,
+                        spai_pc *out);
+
+/* Sizes: n, nnz of this handle's own factor (P or Q_l), total length of the I_k lists,
+ * and depth (0 = built, 1 = updated from a build, ...).  Host outputs, any may be NULL. */
+SPAI_API spai_status spai_pc_info(spai_pc pc, int32_t *n, int32_t *nnz, int64_t *nI, int32_t *depth);
+
+/* Copy out this handle's own factor in column order on its pattern -- Jptr[n+1],
+ * Jind[nnz], val[nnz] -- the row sets Iptr[n+1], Ilist[nI], and col_status[n] (0 ok, 1
+ * singular).  DEVICE pointers; any may be NULL.  Asynchronous. */
+SPAI_API spai_status spai_pc_export(spai_ctx ctx, spai_pc pc, int32_t *Jptr, int32_t *Jind, double *val,
+                           int32_t *Iptr, int32_t *Ilist, int32_t *col_status);
+
+SPAI_API spai_status spai_pc_destroy(spai_pc pc);
+
+/* ----------------------------------------------------------------------------------
+ * Products of the right-preconditioned Krylov method (Sec. 2.2 footnote: A P X~ = B,
+ * X = P X~).  s in {1, 2, 4, 8, 16}.  Column-major device blocks.  Asynchronous.
+ * ---------------------------------------------------------------------------------- */
+
+/* Y = A X. */
+SPAI_API spai_status spai_spmm(spai_ctx ctx, const spai_csr *A, int32_t s, const double *X, int64_t ldx,
+                      double *Y, int64_t ldy);
+
+/* Y = P X for a handle (factored for updated handles: Q_l (P_base X)). */
+SPAI_API spai_status spai_pc_apply(spai_ctx ctx, spai_pc pc, int32_t s, const double *X, int64_t ldx,
+                          double *Y, int64_t ldy);
+
+/* ----------------------------------------------------------------------------------
+ * Block Krylov solve, Sec. 2.1 (block methods solve all right-hand sides at once in
+ * span{R0, A R0, A^2 R0, ...}) with right preconditioning (Sec. 2.2 footnote): block
+ * GMRES(m) on A P X~ = B, X = X0 + P X~.
+ * ---------------------------------------------------------------------------------- */
+
+typedef struct {
+    int32_t restart;     /* m: block Arnoldi steps per cycle, >= 1 */
+    int32_t max_cycles;  /* restart cycles before SPAI_ENOTCONV, >= 1 */
+    double tol;          /* stop when ||b_i - A x_i||_2 <= tol * ||b_i||_2 for every column */
+} spai_solve_opts;
+
+typedef struct {
+    int32_t iterations;        /* block Arnoldi steps over all cycles */
+    int32_t cycles;            /* restart cycles run */
+    int32_t converged;         /* 1 if every column met tol (true residual) */
+    int32_t worst_column;      /* column with the largest relative true residual */
+    double max_rel_residual;   /* that residual, ||b_i - A x_i|| / ||b_i|| (FP64) */
+} spai_solve_info;
+
+/* Solve A X = B for s right-hand sides at once.  P may be NULL (no preconditioner).
+ * B (n x s, ldb) and X (n x s, ldx) may be HOST or DEVICE memory; X holds the initial
+ * guess on entry and the solution on return.  rel_residual: HOST array of s doubles
+ * (or NULL) receiving every column's final relative true residual.  Synchronises: it
+ * returns after the final true-residual check.  Returns SPAI_ENOTCONV (X still holds
+ * the last iterate) if max_cycles ran out. */
+SPAI_API spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, int32_t s, const double *B,
+                        int64_t ldb, double *X, int64_t ldx, const spai_solve_opts *opts,
+                        spai_solve_info *info, double *rel_residual);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPAI_GB300_H */

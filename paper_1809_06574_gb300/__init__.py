@@ -1,0 +1,301 @@
+"""GB300-native SPAI preconditioning, cheap parameter update and block GMRES.
+
+Thin ctypes binding over ``libspai_gb300.so``, whose C ABI is declared in
+``include/spai_gb300.h``.  Every function here has the name of the C entry point it
+wraps and only marshals arguments: device memory comes from the caller (typically torch
+tensors, passed by ``data_ptr()``), every step of the computation runs in the library's
+CUDA kernels, and there is no CPU fallback -- if the library has not been built, the
+first call raises.
+
+Method: arXiv 1809.06574 -- SPAI (Sec. 2.2), its update (Sec. 2.3 Table 1, Sec. 2.4),
+and right-preconditioned block Krylov solves (Sec. 2.1, Sec. 2.2 footnote).
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+__all__ = [
+    "SpaiError", "spai_csr", "spai_solve_opts", "spai_solve_info", "csr", "lib",
+    "spai_ctx_create", "spai_ctx_destroy", "spai_last_error", "spai_ctx_sync",
+    "spai_ctx_mem_in_use", "spai_launch_count", "spai_ctx_profile", "spai_ctx_profile_count", "spai_measure_fp64_rate",
+    "spai_ctx_profile_entry", "spai_affine_create", "spai_affine_pattern",
+    "spai_assemble", "spai_affine_export", "spai_affine_destroy", "spai_build", "spai_update", "spai_pc_info",
+    "spai_pc_export", "spai_pc_destroy", "spai_spmm", "spai_pc_apply", "block_solve",
+    "affine_coefficients", "PATTERN_A", "PATTERN_A2", "UPDATE_FIRST", "UPDATE_CHAINED",
+    "LIB_PATH",
+]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libspai_gb300.so")
+
+SPAI_OK, SPAI_EINVAL, SPAI_ENOMEM, SPAI_ECUDA, SPAI_ESINGULAR, SPAI_ENOTCONV, SPAI_ETIMEOUT = range(7)
+STATUS_NAMES = {0: "SPAI_OK", 1: "SPAI_EINVAL", 2: "SPAI_ENOMEM", 3: "SPAI_ECUDA",
+                4: "SPAI_ESINGULAR", 5: "SPAI_ENOTCONV", 6: "SPAI_ETIMEOUT"}
+PATTERN_A, PATTERN_A2 = 0, 1
+UPDATE_FIRST, UPDATE_CHAINED = 1, 2
+
+
+class SpaiError(RuntimeError):
+    def __init__(self, status, message, result=None):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+        self.result = result
+
+
+class spai_csr(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int32), ("rowptr", C.c_void_p),
+                ("colind", C.c_void_p), ("val", C.c_void_p)]
+
+
+class spai_solve_opts(C.Structure):
+    _fields_ = [("restart", C.c_int32), ("max_cycles", C.c_int32), ("tol", C.c_double)]
+
+
+class spai_solve_info(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("cycles", C.c_int32), ("converged", C.c_int32),
+                ("worst_column", C.c_int32), ("max_rel_residual", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load the library (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, dbl, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_size_t
+    P = C.POINTER
+    sig = {
+        "spai_ctx_create": (i32, [P(vp), vp, sz]),
+        "spai_ctx_destroy": (i32, [vp]),
+        "spai_last_error": (C.c_char_p, [vp]),
+        "spai_ctx_sync": (i32, [vp]),
+        "spai_ctx_mem_in_use": (sz, [vp]),
+        "spai_launch_count": (i64, []),
+        "spai_measure_fp64_rate": (i32, [vp, P(dbl)]),
+        "spai_ctx_profile": (i32, [vp, i32]),
+        "spai_ctx_profile_count": (i32, [vp]),
+        "spai_ctx_profile_entry": (i32, [vp, i32, P(C.c_char_p), P(i64), P(dbl), P(dbl), P(dbl)]),
+        "spai_affine_create": (i32, [vp, i32, P(spai_csr), P(vp)]),
+        "spai_affine_pattern": (i32, [vp, P(i32), P(i32), P(vp), P(vp)]),
+        "spai_assemble": (i32, [vp, vp, P(dbl), vp]),
+        "spai_affine_export": (i32, [vp, vp, vp, vp]),
+        "spai_affine_destroy": (i32, [vp]),
+        "spai_build": (i32, [vp, P(spai_csr), i32, P(vp)]),
+        "spai_update": (i32, [vp, vp, P(spai_csr), i32, P(vp)]),
+        "spai_pc_info": (i32, [vp, P(i32), P(i32), P(i64), P(i32)]),
+        "spai_pc_export": (i32, [vp, vp, vp, vp, vp, vp, vp, vp]),
+        "spai_pc_destroy": (i32, [vp]),
+        "spai_spmm": (i32, [vp, P(spai_csr), i32, vp, i64, vp, i64]),
+        "spai_pc_apply": (i32, [vp, vp, i32, vp, i64, vp, i64]),
+        "block_solve": (i32, [vp, P(spai_csr), vp, i32, vp, i64, vp, i64, P(spai_solve_opts),
+                              P(spai_solve_info), P(dbl)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)!r}")
+
+
+def csr(n, rowptr, colind, val, nnz=None):
+    """spai_csr from arrays (torch tensors or numpy arrays) or raw integer pointers.
+
+    The returned struct keeps references to the arrays so they outlive the call.
+    """
+    if nnz is None:
+        nnz = int(colind.shape[0]) if hasattr(colind, "shape") else 0
+    s = spai_csr(int(n), int(nnz), _ptr(rowptr), _ptr(colind), _ptr(val))
+    s._keep = (rowptr, colind, val)
+    return s
+
+
+def _check(ctx, st, allow=()):
+    if st != SPAI_OK and st not in allow:
+        raise SpaiError(st, spai_last_error(ctx) if ctx else "")
+    return st
+
+
+# ------------------------------------------------------------------ context
+def spai_ctx_create(stream=None, mem_budget=0):
+    out = C.c_void_p()
+    st = lib().spai_ctx_create(C.byref(out), _ptr(stream) if stream is not None else None,
+                               int(mem_budget))
+    if st != SPAI_OK:
+        raise SpaiError(st, "spai_ctx_create failed")
+    return out
+
+
+def spai_ctx_destroy(ctx):
+    return _check(None, lib().spai_ctx_destroy(ctx))
+
+
+def spai_last_error(ctx):
+    r = lib().spai_last_error(ctx)
+    return r.decode() if r else ""
+
+
+def spai_ctx_sync(ctx):
+    return _check(ctx, lib().spai_ctx_sync(ctx))
+
+
+def spai_ctx_mem_in_use(ctx):
+    return int(lib().spai_ctx_mem_in_use(ctx))
+
+
+def spai_launch_count():
+    return int(lib().spai_launch_count())
+
+
+def spai_measure_fp64_rate(ctx):
+    r = C.c_double()
+    _check(ctx, lib().spai_measure_fp64_rate(ctx, C.byref(r)))
+    return r.value
+
+
+def spai_ctx_profile(ctx, enable):
+    return _check(ctx, lib().spai_ctx_profile(ctx, int(bool(enable))))
+
+
+def spai_ctx_profile_count(ctx):
+    return int(lib().spai_ctx_profile_count(ctx))
+
+
+def spai_ctx_profile_entry(ctx, i):
+    name = C.c_char_p()
+    launches = C.c_int64()
+    ms, fl, by = C.c_double(), C.c_double(), C.c_double()
+    _check(ctx, lib().spai_ctx_profile_entry(ctx, int(i), C.byref(name), C.byref(launches),
+                                             C.byref(ms), C.byref(fl), C.byref(by)))
+    return {"name": name.value.decode(), "launches": launches.value, "ms": ms.value,
+            "flops": fl.value, "bytes": by.value}
+
+
+# ------------------------------------------------------------------ affine assembly
+def affine_coefficients(p: float, s: float):
+    """Coefficients of (M, K0, K1) in A(p, s) = s^2 M + s D(p) + K(p).
+
+    With Rayleigh damping D = 0.05 M + 0.01 K(p) and K(p) = K0 + p K1:
+    A = (s^2 + 0.05 s) M + (1 + 0.01 s) K0 + (1 + 0.01 s) p K1.
+    """
+    c = 1.0 + 0.01 * s
+    return [s * s + 0.05 * s, c, c * p]
+
+
+def spai_affine_create(ctx, terms):
+    """terms: list of spai_csr (host or device arrays)."""
+    arr = (spai_csr * len(terms))(*terms)
+    out = C.c_void_p()
+    _check(ctx, lib().spai_affine_create(ctx, len(terms), arr, C.byref(out)))
+    return out
+
+
+def spai_affine_pattern(aff):
+    n, nnz = C.c_int32(), C.c_int32()
+    rp, ci = C.c_void_p(), C.c_void_p()
+    _check(None, lib().spai_affine_pattern(aff, C.byref(n), C.byref(nnz), C.byref(rp), C.byref(ci)))
+    return n.value, nnz.value, rp.value, ci.value
+
+
+def spai_assemble(ctx, aff, coef, val_out):
+    cf = (C.c_double * len(coef))(*[float(c) for c in coef])
+    return _check(ctx, lib().spai_assemble(ctx, aff, cf, _ptr(val_out)))
+
+
+def spai_affine_export(ctx, aff, rowptr, colind):
+    """Copy the union pattern into rowptr / colind (host numpy or device tensors)."""
+    return _check(ctx, lib().spai_affine_export(ctx, aff, _ptr(rowptr), _ptr(colind)))
+
+
+def spai_affine_destroy(aff):
+    return _check(None, lib().spai_affine_destroy(aff))
+
+
+# ------------------------------------------------------------------ preconditioner
+def spai_build(ctx, A, pattern_kind=PATTERN_A, allow_singular=False):
+    """Returns (pc, status).  SPAI_ESINGULAR raises unless allow_singular."""
+    out = C.c_void_p()
+    st = lib().spai_build(ctx, C.byref(A), int(pattern_kind), C.byref(out))
+    if st == SPAI_ESINGULAR and not allow_singular:
+        msg = spai_last_error(ctx)
+        if out:
+            lib().spai_pc_destroy(out)
+        raise SpaiError(st, msg)
+    _check(ctx, st, allow=(SPAI_ESINGULAR,))
+    return out, st
+
+
+def spai_update(ctx, base, A_new, approach=UPDATE_FIRST, allow_singular=False):
+    out = C.c_void_p()
+    st = lib().spai_update(ctx, base, C.byref(A_new), int(approach), C.byref(out))
+    if st == SPAI_ESINGULAR and not allow_singular:
+        msg = spai_last_error(ctx)
+        if out:
+            lib().spai_pc_destroy(out)
+        raise SpaiError(st, msg)
+    _check(ctx, st, allow=(SPAI_ESINGULAR,))
+    return out, st
+
+
+def spai_pc_info(pc):
+    n, nnz, depth = C.c_int32(), C.c_int32(), C.c_int32()
+    nI = C.c_int64()
+    _check(None, lib().spai_pc_info(pc, C.byref(n), C.byref(nnz), C.byref(nI), C.byref(depth)))
+    return {"n": n.value, "nnz": nnz.value, "nI": nI.value, "depth": depth.value}
+
+
+def spai_pc_export(ctx, pc, Jptr=None, Jind=None, val=None, Iptr=None, Ilist=None,
+                   col_status=None):
+    return _check(ctx, lib().spai_pc_export(ctx, pc, _ptr(Jptr), _ptr(Jind), _ptr(val), _ptr(Iptr),
+                                            _ptr(Ilist), _ptr(col_status)))
+
+
+def spai_pc_destroy(pc):
+    return _check(None, lib().spai_pc_destroy(pc))
+
+
+# ------------------------------------------------------------------ products and solve
+def spai_spmm(ctx, A, s, X, ldx, Y, ldy):
+    return _check(ctx, lib().spai_spmm(ctx, C.byref(A), int(s), _ptr(X), int(ldx), _ptr(Y), int(ldy)))
+
+
+def spai_pc_apply(ctx, pc, s, X, ldx, Y, ldy):
+    return _check(ctx, lib().spai_pc_apply(ctx, pc, int(s), _ptr(X), int(ldx), _ptr(Y), int(ldy)))
+
+
+def block_solve(ctx, A, P, s, B, ldb, X, ldx, restart, tol, max_cycles, allow_notconv=False):
+    """Solve A X = B (column-major n x s; host or device).  Returns (status, info, rel)."""
+    opts = spai_solve_opts(int(restart), int(max_cycles), float(tol))
+    info = spai_solve_info()
+    rel = (C.c_double * int(s))()
+    st = lib().block_solve(ctx, C.byref(A), P, int(s), _ptr(B), int(ldb), _ptr(X), int(ldx),
+                           C.byref(opts), C.byref(info), rel)
+    result = (st, info.as_dict(), list(rel))
+    if st == SPAI_ENOTCONV and not allow_notconv:
+        raise SpaiError(st, spai_last_error(ctx), result)
+    _check(ctx, st, allow=(SPAI_ENOTCONV,))
+    return result

@@ -1,0 +1,593 @@
+// Kernels of the right-preconditioned block GMRES(m) solve (Sec. 2.1: block Krylov
+// methods build span{R0, A R0, A^2 R0, ...} for all right-hand sides together; Sec. 2.2
+// footnote: right preconditioning A P X~ = B, X = P X~).  All FP64.
+//
+// Blocks are n x S row-major (S consecutive doubles per row).  The Krylov basis is
+// (m+1) such blocks back to back.  Reductions over n are split into a fixed number of
+// row chunks whose partial sums are added in chunk order, so results do not depend on
+// scheduling.
+#include <cmath>
+
+#include "spai_internal.cuh"
+
+namespace spai {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int check_launch(int kernels = 1)
+{
+    note_launches(kernels);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+inline int grid_for(int64_t work)
+{
+    int64_t g = (work + kThreads - 1) / kThreads;
+    if (g < 1) g = 1;
+    if (g > (1LL << 30)) g = 1 << 30;
+    return (int)g;
+}
+
+// rows [r0, r1) of chunk `c` out of `chunks`
+__device__ __forceinline__ void chunk_rows(int32_t n, int c, int chunks, int64_t &r0, int64_t &r1)
+{
+    r0 = (int64_t)n * c / chunks;
+    r1 = (int64_t)n * (c + 1) / chunks;
+}
+
+// ---------------------------------------------------------------------------------
+// column norms^2 of a block: partial[chunk][c]
+// ---------------------------------------------------------------------------------
+template <int S>
+__global__ void k_colnorm2(int32_t n, const double *__restrict__ W, double *__restrict__ partial)
+{
+    constexpr int RG = kThreads / S;
+    __shared__ double red[kThreads];
+    const int c = threadIdx.x % S, g = threadIdx.x / S;
+    int64_t r0, r1;
+    chunk_rows(n, blockIdx.x, gridDim.x, r0, r1);
+    double acc = 0.0;
+    for (int64_t r = r0 + g; r < r1; r += RG) {
+        double w = W[r * S + c];
+        acc = fma(w, w, acc);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = RG / 2; h > 0; h >>= 1) {
+        if (g < h) red[threadIdx.x] += red[threadIdx.x + h * S];
+        __syncthreads();
+    }
+    if (g == 0) partial[(int64_t)blockIdx.x * S + c] = red[c];
+}
+
+// out[p] = sum over chunks of partial[chunk][p], p < count, chunks added in order
+__global__ void k_reduce_chunks(int32_t count, int chunks, const double *__restrict__ partial,
+                                double *__restrict__ out)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= count) return;
+    double acc = 0.0;
+    for (int c = 0; c < chunks; ++c) acc += partial[(int64_t)c * count + p];
+    out[p] = acc;
+}
+
+// ---------------------------------------------------------------------------------
+// H_i = V_i^T W for i < nblk: partial[chunk][i][a][b]; grid (chunks, nblk)
+// ---------------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_block_dot(int32_t n, const double *__restrict__ V,
+                                                        const double *__restrict__ W,
+                                                        double *__restrict__ partial, int nblk)
+{
+    constexpr int P = S * S;
+    constexpr int RG = (kThreads / P) > 0 ? kThreads / P : 1;
+    __shared__ double red[kThreads];
+    const int i = blockIdx.y;
+    const int p = threadIdx.x % P, g = threadIdx.x / P;
+    const int a = p / S, b = p % S;
+    const double *Vi = V + (int64_t)i * n * S;
+    int64_t r0, r1;
+    chunk_rows(n, blockIdx.x, gridDim.x, r0, r1);
+    double acc = 0.0;
+    if (g < RG)
+        for (int64_t r = r0 + g; r < r1; r += RG)
+            acc = fma(__ldg(Vi + r * S + a), __ldg(W + r * S + b), acc);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = RG / 2; h > 0; h >>= 1) {
+        if (g < h) red[threadIdx.x] += red[threadIdx.x + h * P];
+        __syncthreads();
+    }
+    if (g == 0) partial[((int64_t)blockIdx.x * nblk + i) * P + p] = red[p];
+}
+
+// ---------------------------------------------------------------------------------
+// out = base + sign * sum_i V_i H_i  (H_i = S x S, [i][a][b]); thread per (row, b)
+// ---------------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_block_update(int32_t n, int nblk,
+                                                           const double *__restrict__ V,
+                                                           const double *__restrict__ H,
+                                                           const double *__restrict__ base,
+                                                           double *__restrict__ out, double sign)
+{
+    int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t r = gid / S;
+    int b = (int)(gid % S);
+    if (r >= n) return;
+    double acc = 0.0;
+    for (int i = 0; i < nblk; ++i) {
+        const double *vr = V + ((int64_t)i * n + r) * S;
+        const double *hi = H + (int64_t)i * S * S;
+#pragma unroll
+        for (int a = 0; a < S; ++a) acc = fma(__ldg(vr + a), __ldg(hi + a * S + b), acc);
+    }
+    double o = sign * acc;
+    if (base) o += base[r * S + b];
+    out[r * S + b] = o;
+}
+
+// ---------------------------------------------------------------------------------
+// Cholesky G = R^T R (S x S, one warp, lane j owns column j) with deflation:
+// a pivot d_k <= tau2 * ref2[k] (ref2 = squared column norms before orthogonalisation),
+// d_k <= 1e-15 * G_kk, or d_k <= 0 marks column k as deflated: row k of R = 0.
+// ---------------------------------------------------------------------------------
+template <int S>
+__global__ void k_chol_small(const double *__restrict__ G, const double *__restrict__ ref2,
+                             double tau2, double *__restrict__ R, int32_t *__restrict__ deflated)
+{
+    __shared__ double A[S][S];
+    __shared__ double Rs[S][S];
+    const int lane = threadIdx.x;
+    if (lane < S)
+        for (int i = 0; i < S; ++i) {
+            A[i][lane] = G[i * S + lane];
+            Rs[i][lane] = 0.0;
+        }
+    __syncwarp();
+    for (int k = 0; k < S; ++k) {
+        const double d = A[k][k];
+        const double gkk = G[k * S + k];
+        bool defl = !(d > 0.0) || d <= 1e-15 * gkk || (ref2 && d <= tau2 * ref2[k]);
+        if (!defl) {
+            const double rkk = sqrt(d);
+            if (lane >= k && lane < S) Rs[k][lane] = (lane == k) ? rkk : A[k][lane] / rkk;
+        }
+        __syncwarp();
+        if (!defl && lane > k && lane < S) {
+            const double rkj = Rs[k][lane];
+            for (int i = k + 1; i <= lane; ++i) A[i][lane] = fma(-Rs[k][i], rkj, A[i][lane]);
+        }
+        if (lane == 0) deflated[k] = defl ? 1 : 0;
+        __syncwarp();
+    }
+    if (lane < S)
+        for (int i = 0; i < S; ++i) R[i * S + lane] = Rs[i][lane];
+}
+
+// out[r] = W[r] R^{-1} (R upper triangular, deflated columns -> 0); thread per row
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_trsm_rows(int32_t n, const double *__restrict__ W,
+                                                        const double *__restrict__ R,
+                                                        const int32_t *__restrict__ deflated,
+                                                        double *__restrict__ out)
+{
+    __shared__ double Rs[S * S];
+    __shared__ int32_t df[S];
+    for (int e = threadIdx.x; e < S * S; e += blockDim.x) Rs[e] = R[e];
+    if (threadIdx.x < S) df[threadIdx.x] = deflated[threadIdx.x];
+    __syncthreads();
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double x[S];
+#pragma unroll
+    for (int b = 0; b < S; ++b) {
+        double acc = W[r * S + b];
+#pragma unroll
+        for (int a = 0; a < b; ++a) acc = fma(-x[a], Rs[a * S + b], acc);
+        x[b] = df[b] ? 0.0 : acc / Rs[b * S + b];
+    }
+#pragma unroll
+    for (int b = 0; b < S; ++b) out[r * S + b] = x[b];
+}
+
+template <int S>
+__global__ void k_triu_mul(const double *__restrict__ R2, const double *__restrict__ R1,
+                           double *__restrict__ out)
+{
+    const int a = threadIdx.x / S, b = threadIdx.x % S;
+    if (threadIdx.x >= S * S) return;
+    double acc = 0.0;
+    for (int c = a; c <= b; ++c) acc = fma(R2[a * S + c], R1[c * S + b], acc);
+    out[a * S + b] = acc;
+}
+
+__global__ void k_add_small(int32_t count, const double *a, const double *b, double *out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] = a[i] + b[i];
+}
+
+// Hcol (column-major, leading dim ldh): rows [0,(j+1)S) from Hup[i][a][b]
+// (row i*S + a, column b), rows [(j+1)S, (j+2)S) from Rsub[a][b]
+__global__ void k_copy_hcol(int32_t S, int32_t j, int32_t ldh, const double *__restrict__ Hup,
+                            const double *__restrict__ Rsub, double *__restrict__ Hcol)
+{
+    const int rows = (j + 2) * S;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rows * S; e += gridDim.x * blockDim.x) {
+        const int row = e / S, b = e % S;
+        double v = (row < (j + 1) * S) ? Hup[(int64_t)row * S + b] : Rsub[(row - (j + 1) * S) * S + b];
+        Hcol[(int64_t)b * ldh + row] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Projected least squares, updated one block column at a time (one CTA).
+//  Hcol: new block column (column-major, ld = (m+1)S), rows [0, (j+2)S).
+//  Qs:   for every earlier step j' the 2S x 2S orthogonal matrix M_j' (row-major) that
+//        triangularised block column j' on rows [j'S, j'S + 2S).
+//  Rtri: triangular factor, column-major, ld = (m+1)S; block column j is written here.
+//  G:    transformed right-hand side ((m+1)S x S, row-major).
+//  est:  per-column least-squares residual norm = || G[(j+1)S : (j+2)S, i] ||.
+// A zero column (deflated basis vector) gets an identity reflector and R_cc = 0.
+// ---------------------------------------------------------------------------------
+template <int S>
+__global__ void k_arnoldi_ls(int32_t j, int32_t m, double *__restrict__ Hcol,
+                             double *__restrict__ Qs, double *__restrict__ Rtri,
+                             double *__restrict__ G, const double *__restrict__ thresh,
+                             double *__restrict__ est, int32_t *__restrict__ flag)
+{
+    constexpr int S2 = 2 * S;
+    const int ld = (m + 1) * S;
+    __shared__ double X[S2][S];     // working rows of the new column block
+    __shared__ double Mq[S2][S2];   // orthogonal factor being formed
+    __shared__ double Vr[S][S2];    // reflectors of this step
+    __shared__ double beta[S];      // 2 / v^T v (0 = identity)
+    __shared__ double rdiag[S];     // R_cc
+    __shared__ double Gx[S2][S];
+    __shared__ double Gy[S2][S];
+    const int tid = threadIdx.x, nt = blockDim.x;
+
+    // (a) apply the earlier steps' orthogonal factors
+    for (int jp = 0; jp < j; ++jp) {
+        const double *M = Qs + (int64_t)jp * S2 * S2;
+        for (int e = tid; e < S2 * S; e += nt) {
+            const int r = e / S, t = e % S;
+            X[r][t] = Hcol[(int64_t)t * ld + jp * S + r];
+        }
+        __syncthreads();
+        for (int e = tid; e < S2 * S; e += nt) {
+            const int r = e / S, t = e % S;
+            double acc = 0.0;
+            for (int q = 0; q < S2; ++q) acc = fma(M[r * S2 + q], X[q][t], acc);
+            Hcol[(int64_t)t * ld + jp * S + r] = acc;
+        }
+        __syncthreads();
+    }
+    // (b) Householder QR of rows [jS, jS + 2S)
+    for (int e = tid; e < S2 * S; e += nt) {
+        const int r = e / S, t = e % S;
+        X[r][t] = Hcol[(int64_t)t * ld + j * S + r];
+    }
+    __syncthreads();
+    for (int c = 0; c < S; ++c) {
+        // warp 0 forms reflector c from X[c:, c]
+        if (tid < 32) {
+            const int r = tid;
+            double x = (r >= c && r < S2) ? X[r][c] : 0.0;
+            double ss = x * x;
+            for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            const double alpha = sqrt(ss);
+            const double xc = X[c][c];
+            const double sgn = (xc >= 0.0) ? 1.0 : -1.0;
+            double v = x;
+            if (r == c) v += sgn * alpha;
+            if (r < S2) Vr[c][r] = (alpha > 0.0) ? v : 0.0;
+            if (r == 0) {
+                beta[c] = (alpha > 0.0) ? 1.0 / (alpha * (alpha + fabs(xc))) : 0.0;
+                rdiag[c] = (alpha > 0.0) ? -sgn * alpha : 0.0;
+            }
+        }
+        __syncthreads();
+        // apply to columns t > c of X (thread per column t, serial over 2S rows)
+        if (beta[c] != 0.0) {
+            for (int t = c + 1 + tid; t < S; t += nt) {
+                double d = 0.0;
+                for (int r = c; r < S2; ++r) d = fma(Vr[c][r], X[r][t], d);
+                const double g = d * beta[c];
+                for (int r = c; r < S2; ++r) X[r][t] = fma(-g, Vr[c][r], X[r][t]);
+            }
+        }
+        __syncthreads();
+        // column c itself becomes (R_cc, 0, ..., 0)
+        if (tid == c) X[c][c] = rdiag[c];
+        if (tid < S2 && tid > c) X[tid][c] = 0.0;
+        __syncthreads();
+    }
+    // (c) M = H_{S-1} ... H_0 (so that M X_original = R)
+    for (int e = tid; e < S2 * S2; e += nt) Mq[e / S2][e % S2] = (e / S2 == e % S2) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int c = 0; c < S; ++c) {
+        if (beta[c] != 0.0) {
+            for (int col = tid; col < S2; col += nt) {
+                double d = 0.0;
+                for (int r = c; r < S2; ++r) d = fma(Vr[c][r], Mq[r][col], d);
+                const double g = d * beta[c];
+                for (int r = c; r < S2; ++r) Mq[r][col] = fma(-g, Vr[c][r], Mq[r][col]);
+            }
+        }
+        __syncthreads();
+    }
+    double *Mj = Qs + (int64_t)j * S2 * S2;
+    for (int e = tid; e < S2 * S2; e += nt) Mj[e] = Mq[e / S2][e % S2];
+    // (d) write the triangularised block column: rows [0, (j+1)S)
+    for (int e = tid; e < (j + 1) * S * S; e += nt) {
+        const int row = e / S, t = e % S;
+        double v;
+        if (row < j * S) v = Hcol[(int64_t)t * ld + row];
+        else v = (row - j * S <= t) ? X[row - j * S][t] : 0.0;
+        Rtri[(int64_t)(j * S + t) * ld + row] = v;
+    }
+    // (e) transform G rows [jS, jS + 2S)
+    for (int e = tid; e < S2 * S; e += nt) {
+        const int r = e / S, i = e % S;
+        Gx[r][i] = G[(int64_t)(j * S + r) * S + i];
+    }
+    __syncthreads();
+    for (int e = tid; e < S2 * S; e += nt) {
+        const int r = e / S, i = e % S;
+        double acc = 0.0;
+        for (int q = 0; q < S2; ++q) acc = fma(Mq[r][q], Gx[q][i], acc);
+        G[(int64_t)(j * S + r) * S + i] = acc;
+        Gy[r][i] = acc;
+    }
+    __syncthreads();
+    // (f) residual estimates
+    if (tid < S) {
+        double ss = 0.0;
+        for (int r = S; r < S2; ++r) ss += Gy[r][tid] * Gy[r][tid];
+        est[tid] = sqrt(ss);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int ok = 1;
+        for (int i = 0; i < S; ++i) ok &= (est[i] <= thresh[i]);
+        *flag = ok;
+    }
+}
+
+// G = 0; G[0:S] = S0 (S x S row-major)
+template <int S>
+__global__ void k_set_rhs(int32_t m, const double *__restrict__ S0, double *__restrict__ G)
+{
+    const int count = (m + 1) * S * S;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x)
+        G[e] = (e < S * S) ? S0[e] : 0.0;
+}
+
+// Solve R Y = G[0:JS] (R = Rtri, upper, column-major ld); zero diagonal -> y = 0.
+// One CTA; Y row-major (JS x S).
+template <int S>
+__global__ void k_backsolve(int32_t J, int32_t ldr, const double *__restrict__ Rtri,
+                            const double *__restrict__ G, double *__restrict__ Y)
+{
+    const int N = J * S;
+    __shared__ double yc[S];
+    for (int e = threadIdx.x; e < N * S; e += blockDim.x) Y[e] = G[e];
+    __syncthreads();
+    for (int c = N - 1; c >= 0; --c) {
+        const double rcc = Rtri[(int64_t)c * ldr + c];
+        if (threadIdx.x < S) {
+            const double v = (rcc != 0.0) ? Y[(int64_t)c * S + threadIdx.x] / rcc : 0.0;
+            yc[threadIdx.x] = v;
+            Y[(int64_t)c * S + threadIdx.x] = v;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < c * S; e += blockDim.x) {
+            const int r = e / S, i = e % S;
+            Y[e] = fma(-Rtri[(int64_t)c * ldr + r], yc[i], Y[e]);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_axpy(int64_t count, double alpha, const double *__restrict__ x,
+                       double *__restrict__ y)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = fma(alpha, x[i], y[i]);
+}
+
+__global__ void k_zero(int64_t count, double *dst)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = 0.0;
+}
+
+// R = B - A X (row-major blocks), S lanes per row
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_residual(int32_t n, const int32_t *__restrict__ rowptr,
+                                                       const int32_t *__restrict__ colind,
+                                                       const double *__restrict__ val,
+                                                       const double *__restrict__ X,
+                                                       const double *__restrict__ B,
+                                                       double *__restrict__ R)
+{
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t row = g / S;
+    int c = (int)(g % S);
+    if (row >= n) return;
+    double acc = 0.0;
+    for (int32_t q = __ldg(rowptr + row); q < __ldg(rowptr + row + 1); ++q)
+        acc = fma(__ldg(val + q), __ldg(X + (int64_t)__ldg(colind + q) * S + c), acc);
+    R[row * S + c] = B[row * S + c] - acc;
+}
+
+inline int cap_grid(int64_t want)
+{
+    return (int)(want < 1 ? 1 : (want > 65535 ? 65535 : want));
+}
+
+}  // namespace
+
+// ===================================================================================
+int krylov_chunks(int32_t n)
+{
+    int64_t c = ((int64_t)n + 2047) / 2048;
+    if (c < 1) c = 1;
+    if (c > 608) c = 608;
+    return (int)c;
+}
+
+#define SPAI_DISPATCH_S(s, CALL)          \
+    switch (s) {                          \
+    case 1: { constexpr int S = 1; CALL; } break;   \
+    case 2: { constexpr int S = 2; CALL; } break;   \
+    case 4: { constexpr int S = 4; CALL; } break;   \
+    case 8: { constexpr int S = 8; CALL; } break;   \
+    case 16: { constexpr int S = 16; CALL; } break; \
+    default: return -1;                   \
+    }
+
+int launch_colnorm2(cudaStream_t st, int32_t s, int32_t n, const double *W, double *partial,
+                    double *out, int chunks)
+{
+    SPAI_DISPATCH_S(s, (k_colnorm2<S><<<chunks, kThreads, 0, st>>>(n, W, partial)));
+    k_reduce_chunks<<<1, 32, 0, st>>>(s, chunks, partial, out);
+    return check_launch(2);
+}
+
+int launch_block_dot(cudaStream_t st, int32_t s, int32_t n, int32_t nblk, const double *V,
+                     const double *W, double *partial, double *out, int chunks)
+{
+    dim3 grid(chunks, nblk);
+    SPAI_DISPATCH_S(s, (k_block_dot<S><<<grid, kThreads, 0, st>>>(n, V, W, partial, nblk)));
+    const int count = nblk * s * s;
+    k_reduce_chunks<<<(count + 255) / 256, 256, 0, st>>>(count, chunks, partial, out);
+    return check_launch(2);
+}
+
+int launch_block_update(cudaStream_t st, int32_t s, int32_t n, int32_t nblk, const double *V,
+                        const double *H, const double *base, double *out, double sign)
+{
+    if (n <= 0) return 0;
+    int g = grid_for((int64_t)n * s);
+    SPAI_DISPATCH_S(s, (k_block_update<S><<<g, kThreads, 0, st>>>(n, nblk, V, H, base, out, sign)));
+    return check_launch();
+}
+
+int launch_chol_small(cudaStream_t st, int32_t s, const double *G, const double *ref2, double tau2,
+                      double *R, int32_t *deflated)
+{
+    SPAI_DISPATCH_S(s, (k_chol_small<S><<<1, 32, 0, st>>>(G, ref2, tau2, R, deflated)));
+    return check_launch();
+}
+
+int launch_trsm_rows(cudaStream_t st, int32_t s, int32_t n, const double *W, const double *R,
+                     const int32_t *deflated, double *out)
+{
+    if (n <= 0) return 0;
+    SPAI_DISPATCH_S(s, (k_trsm_rows<S><<<grid_for(n), kThreads, 0, st>>>(n, W, R, deflated, out)));
+    return check_launch();
+}
+
+int launch_triu_mul(cudaStream_t st, int32_t s, const double *R2, const double *R1, double *out)
+{
+    SPAI_DISPATCH_S(s, (k_triu_mul<S><<<1, S * S < 32 ? 32 : S * S, 0, st>>>(R2, R1, out)));
+    return check_launch();
+}
+
+int launch_add_small(cudaStream_t st, int32_t count, const double *a, const double *b, double *out)
+{
+    k_add_small<<<(count + 255) / 256, 256, 0, st>>>(count, a, b, out);
+    return check_launch();
+}
+
+int launch_copy_hcol(cudaStream_t st, int32_t s, int32_t j, int32_t ldh, const double *Hup,
+                     const double *Rsub, double *Hcol)
+{
+    const int count = (j + 2) * s * s;
+    k_copy_hcol<<<cap_grid((count + 255) / 256), 256, 0, st>>>(s, j, ldh, Hup, Rsub, Hcol);
+    return check_launch();
+}
+
+int launch_arnoldi_ls(cudaStream_t st, int32_t s, int32_t j, int32_t m, double *Hcol, double *Qs,
+                      double *Rtri, double *G, const double *thresh, double *est, int32_t *flag)
+{
+    SPAI_DISPATCH_S(s, (k_arnoldi_ls<S><<<1, 256, 0, st>>>(j, m, Hcol, Qs, Rtri, G, thresh, est,
+                                                          flag)));
+    return check_launch();
+}
+
+int launch_set_rhs(cudaStream_t st, int32_t s, int32_t m, const double *S0, double *G)
+{
+    const int count = (m + 1) * s * s;
+    SPAI_DISPATCH_S(s, (k_set_rhs<S><<<cap_grid((count + 255) / 256), 256, 0, st>>>(m, S0, G)));
+    return check_launch();
+}
+
+int launch_backsolve(cudaStream_t st, int32_t s, int32_t J, int32_t ldr, const double *Rtri,
+                     const double *G, double *Y)
+{
+    SPAI_DISPATCH_S(s, (k_backsolve<S><<<1, 512, 0, st>>>(J, ldr, Rtri, G, Y)));
+    return check_launch();
+}
+
+int launch_axpy(cudaStream_t st, int64_t count, double alpha, const double *x, double *y)
+{
+    if (count <= 0) return 0;
+    k_axpy<<<cap_grid((count + kThreads - 1) / kThreads), kThreads, 0, st>>>(count, alpha, x, y);
+    return check_launch();
+}
+
+int launch_zero(cudaStream_t st, int64_t count, double *dst)
+{
+    if (count <= 0) return 0;
+    k_zero<<<cap_grid((count + kThreads - 1) / kThreads), kThreads, 0, st>>>(count, dst);
+    return check_launch();
+}
+
+int launch_residual(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr,
+                    const int32_t *colind, const double *val, const double *X, const double *B,
+                    double *R)
+{
+    if (n <= 0) return 0;
+    int g = grid_for((int64_t)n * s);
+    SPAI_DISPATCH_S(s, (k_residual<S><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, B, R)));
+    return check_launch();
+}
+
+}  // namespace spai
+
+// ---------------------------------------------------------------------------------
+// FP64 FMA throughput probe: 8 independent dependency chains per thread.
+// ---------------------------------------------------------------------------------
+namespace spai {
+namespace {
+__global__ void k_fp64_fma_probe(int iters, double seed, double *sink)
+{
+    double a[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a[c] = seed + threadIdx.x * 1e-9 + c * 1e-7;
+    const double b = 0.999999999, d = 1e-12;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a[c] = fma(a[c], b, d);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += a[c];
+    if (s == 12345.678) sink[0] = s;  // never true; keeps the chains alive
+}
+}  // namespace
+
+int launch_fp64_probe(cudaStream_t st, int blocks, int threads, int iters, double *sink)
+{
+    k_fp64_fma_probe<<<blocks, threads, 0, st>>>(iters, 1.0, sink);
+    return check_launch();
+}
+}  // namespace spai

@@ -1,0 +1,597 @@
+// Sparse-structure and streaming kernels of the SPAI path:
+//  * CSR validation, union of the affine terms' patterns and value assembly
+//    (Sec. 1.1, Eqs. (4)-(9): every A(l) is one affine combination of fixed matrices);
+//  * CSR -> CSC transposition (column access for the column least-squares problems of
+//    Sec. 2.2) and the row sets I_k = union of rows(A(:,j)), j in J_k;
+//  * the CSR sparse-times-block product used for A P V in the block Krylov method
+//    (Sec. 2.1) and for the preconditioner apply (Sec. 2.2 footnote).
+#include <atomic>
+#include <climits>
+
+#include "spai_internal.cuh"
+
+namespace spai {
+
+static std::atomic<long long> g_launches{0};
+
+void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int grid_for(int64_t work, int threads = kThreads)
+{
+    int64_t g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > (1LL << 30)) g = 1 << 30;
+    return (int)g;
+}
+
+inline int check_launch(int kernels = 1)
+{
+    note_launches(kernels);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ---------------------------------------------------------------------------------
+// validation
+// ---------------------------------------------------------------------------------
+__global__ void k_validate_csr(int32_t n, int32_t nnz, const int32_t *__restrict__ rowptr,
+                               const int32_t *__restrict__ colind, int *err)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i == 0 && (rowptr[0] != 0 || rowptr[n] != nnz)) atomicOr(err, ERR_ROWPTR);
+    if (i >= n) return;
+    int32_t a = rowptr[i], b = rowptr[i + 1];
+    if (a < 0 || b < a || b > nnz) {
+        atomicOr(err, ERR_ROWPTR);
+        return;
+    }
+    int32_t prev = -1;
+    for (int32_t q = a; q < b; ++q) {
+        int32_t c = colind[q];
+        if (c < 0 || c >= n || c <= prev) {
+            atomicOr(err, ERR_COLIND);
+            return;
+        }
+        prev = c;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// union pattern of T terms (thread per row, T-way merge of sorted rows)
+// ---------------------------------------------------------------------------------
+template <bool FILL>
+__global__ void k_union(int32_t n, int32_t T, TermPtrs tp, int32_t *counts,
+                        const int32_t *__restrict__ u_rowptr, int32_t *__restrict__ u_colind,
+                        double *__restrict__ aligned, int64_t nnzU)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t pos[kMaxTerms], end[kMaxTerms];
+    for (int t = 0; t < T; ++t) {
+        pos[t] = tp.rowptr[t][i];
+        end[t] = tp.rowptr[t][i + 1];
+    }
+    int64_t out = FILL ? (int64_t)u_rowptr[i] : 0;
+    int32_t cnt = 0;
+    while (true) {
+        int32_t m = INT_MAX;
+        for (int t = 0; t < T; ++t)
+            if (pos[t] < end[t]) m = min(m, tp.colind[t][pos[t]]);
+        if (m == INT_MAX) break;
+        if (FILL) u_colind[out + cnt] = m;
+        for (int t = 0; t < T; ++t) {
+            double v = 0.0;
+            if (pos[t] < end[t] && tp.colind[t][pos[t]] == m) {
+                v = tp.val[t][pos[t]];
+                ++pos[t];
+            }
+            if (FILL) aligned[(int64_t)t * nnzU + out + cnt] = v;
+        }
+        ++cnt;
+    }
+    if (!FILL) counts[i] = cnt;
+}
+
+// val[q] = sum_t c_t * aligned_t[q], t in order, product and sum rounded separately
+__global__ void k_assemble(int64_t nnz, int32_t T, const double *__restrict__ aligned,
+                           TermPtrs tp, double *__restrict__ out)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int t = 0; t < T; ++t)
+            acc = __dadd_rn(acc, __dmul_rn(tp.coef[t], __ldg(aligned + (int64_t)t * nnz + q)));
+        out[q] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// exclusive scan of int32 counts into an int32 pointer array (3 phases, int64 carries)
+// ---------------------------------------------------------------------------------
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kThreads * kScanItems;
+
+__device__ long long block_exclusive_scan(long long v, long long *total)
+{
+    __shared__ long long warp_sums[kThreads / 32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_sums[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        long long w = (lane < kThreads / 32) ? warp_sums[lane] : 0;
+        long long wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < kThreads / 32) warp_sums[lane] = wi - w;
+        if (lane == kThreads / 32 - 1) *total = wi;
+    }
+    __syncthreads();
+    long long r = incl - v + warp_sums[wid];
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_tile_sums(const int32_t *__restrict__ counts, int64_t n,
+                                 long long *__restrict__ sums)
+{
+    __shared__ long long tot;
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    long long s = 0;
+    for (int u = 0; u < kScanItems; ++u)
+        if (base + u < n) s += counts[base + u];
+    block_exclusive_scan(s, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(long long *sums, int64_t ntiles, int32_t *ptr, int64_t n, int *err)
+{
+    __shared__ long long tot;
+    long long carry = 0;
+    for (int64_t base = 0; base < ntiles; base += kThreads) {
+        int64_t i = base + threadIdx.x;
+        long long v = (i < ntiles) ? sums[i] : 0;
+        long long ex = block_exclusive_scan(v, &tot);
+        if (i < ntiles) sums[i] = carry + ex;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (carry > INT_MAX) atomicOr(err, ERR_OVERFLOW);
+        ptr[n] = (int32_t)carry;
+    }
+}
+
+__global__ void k_scan_apply(const int32_t *__restrict__ counts, int64_t n,
+                             const long long *__restrict__ sums, int32_t *__restrict__ ptr)
+{
+    __shared__ long long tot;
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    long long v[kScanItems];
+    long long s = 0;
+    for (int u = 0; u < kScanItems; ++u) {
+        v[u] = (base + u < n) ? counts[base + u] : 0;
+        s += v[u];
+    }
+    long long ex = block_exclusive_scan(s, &tot) + sums[blockIdx.x];
+    for (int u = 0; u < kScanItems; ++u) {
+        if (base + u < n) ptr[base + u] = (int32_t)ex;
+        ex += v[u];
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// transposition
+// ---------------------------------------------------------------------------------
+__global__ void k_count_cols(int32_t nnz, const int32_t *__restrict__ colind, int32_t *cnt)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz;
+         q += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(cnt + colind[q], 1);
+}
+
+__global__ void k_fill_cols(int32_t n, const int32_t *__restrict__ rowptr,
+                            const int32_t *__restrict__ colind, int32_t *next,
+                            int32_t *__restrict__ rowind_tmp, int32_t *__restrict__ perm_tmp)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int32_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+        int32_t d = atomicAdd(next + colind[q], 1);
+        rowind_tmp[d] = (int32_t)i;
+        perm_tmp[d] = q;
+    }
+}
+
+// warp per column: place every entry at its rank (rows are distinct inside a column)
+__global__ void k_rank_sort_cols(int32_t n, const int32_t *__restrict__ colptr,
+                                 const int32_t *__restrict__ rowind_tmp,
+                                 const int32_t *__restrict__ perm_tmp,
+                                 int32_t *__restrict__ rowind, int32_t *__restrict__ perm)
+{
+    int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (w >= n) return;
+    int32_t a = colptr[w], L = colptr[w + 1] - a;
+    for (int32_t e = lane; e < L; e += 32) {
+        int32_t r = rowind_tmp[a + e];
+        int32_t rank = 0;
+        for (int32_t f = 0; f < L; ++f) rank += (rowind_tmp[a + f] < r);
+        rowind[a + rank] = r;
+        if (perm) perm[a + rank] = perm_tmp[a + e];
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// column unions (row sets): warp per output column, warp-wide minimum merge of the
+// sorted row lists of the columns in L_k (at most 4 lists per lane)
+// ---------------------------------------------------------------------------------
+constexpr int kListsPerLane = 4;
+
+template <bool FILL>
+__global__ void k_colunion(int32_t n, const int32_t *__restrict__ Lptr,
+                           const int32_t *__restrict__ Lind, const int32_t *__restrict__ colptr,
+                           const int32_t *__restrict__ rowind, const int32_t *__restrict__ out_ptr,
+                           int32_t *__restrict__ out, int *err)
+{
+    int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (k >= n) return;
+    int32_t a = Lptr[k], L = Lptr[k + 1] - a;
+    if (L > 32 * kListsPerLane) {
+        if (lane == 0 && err) atomicOr(err, ERR_TOO_WIDE);
+        return;
+    }
+    int32_t pos[kListsPerLane], end[kListsPerLane], head[kListsPerLane];
+#pragma unroll
+    for (int u = 0; u < kListsPerLane; ++u) {
+        int32_t c = lane + 32 * u;
+        pos[u] = end[u] = 0;
+        head[u] = INT_MAX;
+        if (c < L) {
+            int32_t j = Lind[a + c];
+            pos[u] = colptr[j];
+            end[u] = colptr[j + 1];
+            if (pos[u] < end[u]) head[u] = rowind[pos[u]];
+        }
+    }
+    int64_t ob = FILL ? (int64_t)out_ptr[k] : 0;
+    int32_t cnt = 0;
+    while (true) {
+        int32_t cand = head[0];
+#pragma unroll
+        for (int u = 1; u < kListsPerLane; ++u) cand = min(cand, head[u]);
+        int32_t m = __reduce_min_sync(0xffffffffu, cand);
+        if (m == INT_MAX) break;
+        if (FILL && lane == 0) out[ob + cnt] = m;
+#pragma unroll
+        for (int u = 0; u < kListsPerLane; ++u) {
+            if (head[u] == m) {
+                ++pos[u];
+                head[u] = (pos[u] < end[u]) ? rowind[pos[u]] : INT_MAX;
+            }
+        }
+        ++cnt;
+    }
+    if (!FILL && lane == 0) out[k] = cnt;
+}
+
+__global__ void k_gather_f64(int64_t count, const int32_t *__restrict__ idx,
+                             const double *__restrict__ src, double *__restrict__ dst)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[idx[i]];
+}
+
+__global__ void k_invert_perm(int64_t count, const int32_t *__restrict__ perm,
+                              int32_t *__restrict__ inv)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        inv[perm[i]] = (int32_t)i;
+}
+
+__global__ void k_max_diff(int32_t n, const int32_t *__restrict__ ptr, int32_t *out)
+{
+    int32_t m = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, ptr[i + 1] - ptr[i]);
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+__global__ void k_first_nonzero(int32_t n, const int32_t *__restrict__ a, int32_t *out)
+{
+    int32_t best = INT_MAX;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (a[i] != 0) { best = (int32_t)i; break; }
+    best = __reduce_min_sync(0xffffffffu, best);
+    if ((threadIdx.x & 31) == 0 && best != INT_MAX) atomicMin(out, best);
+}
+
+__global__ void k_compare_i32(int64_t count, const int32_t *__restrict__ a,
+                              const int32_t *__restrict__ b, int *err)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (a[i] != b[i]) { atomicOr(err, ERR_PATTERN); return; }
+}
+
+__global__ void k_fill_i32(int64_t count, int32_t v, int32_t *dst)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = v;
+}
+
+// ---------------------------------------------------------------------------------
+// CSR times row-major block: S consecutive lanes per row, lane c owns column c
+// ---------------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_spmm(int32_t n, const int32_t *__restrict__ rowptr,
+                                                   const int32_t *__restrict__ colind,
+                                                   const double *__restrict__ val,
+                                                   const double *__restrict__ X,
+                                                   double *__restrict__ Y)
+{
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t row = g / S;
+    int c = (int)(g % S);
+    if (row >= n) return;
+    int32_t a = __ldg(rowptr + row), b = __ldg(rowptr + row + 1);
+    double acc = 0.0;
+    for (int32_t q = a; q < b; ++q)
+        acc = fma(__ldg(val + q), __ldg(X + (int64_t)__ldg(colind + q) * S + c), acc);
+    Y[row * S + c] = acc;
+}
+
+template <int S>
+__global__ void k_pack(int32_t n, const double *__restrict__ src, int64_t ld,
+                       double *__restrict__ dst)
+{
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= (int64_t)n * S) return;
+    int64_t r = g % n;
+    int c = (int)(g / n);
+    dst[r * S + c] = src[(int64_t)c * ld + r];
+}
+
+template <int S>
+__global__ void k_unpack(int32_t n, const double *__restrict__ src, double *__restrict__ dst,
+                         int64_t ld)
+{
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= (int64_t)n * S) return;
+    int64_t r = g % n;
+    int c = (int)(g / n);
+    dst[(int64_t)c * ld + r] = src[r * S + c];
+}
+
+}  // namespace
+
+// ===================================================================================
+// launchers
+// ===================================================================================
+int launch_validate_csr(cudaStream_t st, int32_t n, int32_t nnz, const int32_t *rowptr,
+                        const int32_t *colind, int *d_err)
+{
+    k_validate_csr<<<grid_for((int64_t)n + 1), kThreads, 0, st>>>(n, nnz, rowptr, colind, d_err);
+    return check_launch();
+}
+
+int launch_union_count(cudaStream_t st, int32_t n, int32_t T, const TermPtrs &tp, int32_t *counts)
+{
+    k_union<false><<<grid_for(n), kThreads, 0, st>>>(n, T, tp, counts, nullptr, nullptr, nullptr, 0);
+    return check_launch();
+}
+
+int launch_union_fill(cudaStream_t st, int32_t n, int32_t T, const TermPtrs &tp,
+                      const int32_t *u_rowptr, int32_t *u_colind, double *aligned, int64_t nnzU)
+{
+    k_union<true><<<grid_for(n), kThreads, 0, st>>>(n, T, tp, nullptr, u_rowptr, u_colind,
+                                                     aligned, nnzU);
+    return check_launch();
+}
+
+int launch_assemble(cudaStream_t st, int64_t nnz, int32_t T, const double *aligned,
+                    const double *coef_host, double *out)
+{
+    TermPtrs tp{};
+    for (int t = 0; t < T; ++t) tp.coef[t] = coef_host[t];
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t want = (nnz + kThreads - 1) / kThreads;
+    int64_t cap = (int64_t)sms * 8;
+    int grid = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+    k_assemble<<<grid, kThreads, 0, st>>>(nnz, T, aligned, tp, out);
+    return check_launch();
+}
+
+size_t scan_temp_bytes(int64_t n)
+{
+    int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    return (size_t)(tiles + 1) * sizeof(long long);
+}
+
+int launch_exclusive_scan(cudaStream_t st, const int32_t *counts, int32_t *ptr, int64_t n,
+                          void *temp, int *d_err)
+{
+    int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles < 1) tiles = 1;
+    long long *sums = (long long *)temp;
+    k_scan_tile_sums<<<(unsigned)tiles, kThreads, 0, st>>>(counts, n, sums);
+    k_scan_sums<<<1, kThreads, 0, st>>>(sums, tiles, ptr, n, d_err);
+    k_scan_apply<<<(unsigned)tiles, kThreads, 0, st>>>(counts, n, sums, ptr);
+    return check_launch(3);
+}
+
+static size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+// must match the carving in launch_transpose: every piece is rounded up to 256 bytes
+size_t transpose_temp_bytes(int32_t n, int32_t nnz)
+{
+    return 2 * round256(((size_t)n + 1) * sizeof(int32_t)) +
+           2 * round256(((size_t)nnz + 1) * sizeof(int32_t)) + round256(scan_temp_bytes(n));
+}
+
+int launch_transpose(cudaStream_t st, int32_t n, int32_t nnz, const int32_t *rowptr,
+                     const int32_t *colind, int32_t *colptr, int32_t *rowind, int32_t *perm,
+                     void *temp, int *d_err)
+{
+    char *p = (char *)temp;
+    auto take = [&](size_t bytes) {
+        void *r = p;
+        p += (bytes + 255) / 256 * 256;
+        return r;
+    };
+    int32_t *cnt = (int32_t *)take(((size_t)n + 1) * sizeof(int32_t));
+    int32_t *next = (int32_t *)take(((size_t)n + 1) * sizeof(int32_t));
+    int32_t *rtmp = (int32_t *)take(((size_t)nnz + 1) * sizeof(int32_t));
+    int32_t *ptmp = (int32_t *)take(((size_t)nnz + 1) * sizeof(int32_t));
+    void *stemp = take(scan_temp_bytes(n));
+    if (cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(int32_t), st) != cudaSuccess) return -1;
+    k_count_cols<<<grid_for(nnz), kThreads, 0, st>>>(nnz, colind, cnt);
+    if (launch_exclusive_scan(st, cnt, colptr, n, stemp, d_err)) return -1;
+    if (cudaMemcpyAsync(next, colptr, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st) !=
+        cudaSuccess)
+        return -1;
+    k_fill_cols<<<grid_for(n), kThreads, 0, st>>>(n, rowptr, colind, next, rtmp, ptmp);
+    k_rank_sort_cols<<<grid_for((int64_t)n * 32), kThreads, 0, st>>>(n, colptr, rtmp, ptmp, rowind,
+                                                                      perm);
+    return check_launch(3);
+}
+
+int colunion_max_lists() { return 32 * kListsPerLane; }
+
+int launch_colunion_count(cudaStream_t st, int32_t n, const int32_t *Lptr, const int32_t *Lind,
+                          const int32_t *colptr, const int32_t *rowind, int32_t *counts,
+                          int *d_err)
+{
+    if (n <= 0) return 0;
+    k_colunion<false><<<grid_for((int64_t)n * 32), kThreads, 0, st>>>(n, Lptr, Lind, colptr, rowind,
+                                                                       nullptr, counts, d_err);
+    return check_launch();
+}
+
+int launch_colunion_fill(cudaStream_t st, int32_t n, const int32_t *Lptr, const int32_t *Lind,
+                         const int32_t *colptr, const int32_t *rowind, const int32_t *out_ptr,
+                         int32_t *out_list, int *d_err)
+{
+    if (n <= 0) return 0;
+    k_colunion<true><<<grid_for((int64_t)n * 32), kThreads, 0, st>>>(n, Lptr, Lind, colptr, rowind,
+                                                                      out_ptr, out_list, d_err);
+    return check_launch();
+}
+
+int launch_gather_f64(cudaStream_t st, int64_t count, const int32_t *idx, const double *src,
+                      double *dst)
+{
+    if (count <= 0) return 0;
+    k_gather_f64<<<grid_for(count), kThreads, 0, st>>>(count, idx, src, dst);
+    return check_launch();
+}
+
+int launch_invert_perm(cudaStream_t st, int64_t count, const int32_t *perm, int32_t *inv)
+{
+    if (count <= 0) return 0;
+    k_invert_perm<<<grid_for(count), kThreads, 0, st>>>(count, perm, inv);
+    return check_launch();
+}
+
+int launch_max_i32_diff(cudaStream_t st, int32_t n, const int32_t *ptr, int32_t *d_max)
+{
+    if (cudaMemsetAsync(d_max, 0, sizeof(int32_t), st) != cudaSuccess) return -1;
+    if (n <= 0) return 0;
+    int g = grid_for(n);
+    if (g > 4096) g = 4096;
+    k_max_diff<<<g, kThreads, 0, st>>>(n, ptr, d_max);
+    return check_launch();
+}
+
+int launch_fill_i32(cudaStream_t st, int64_t count, int32_t v, int32_t *dst)
+{
+    if (count <= 0) return 0;
+    k_fill_i32<<<grid_for(count), kThreads, 0, st>>>(count, v, dst);
+    return check_launch();
+}
+
+int launch_first_nonzero(cudaStream_t st, int32_t n, const int32_t *a, int32_t *d_out)
+{
+    k_fill_i32<<<1, 32, 0, st>>>(1, INT_MAX, d_out);
+    if (n <= 0) return check_launch();
+    int g = grid_for(n);
+    if (g > 4096) g = 4096;
+    k_first_nonzero<<<g, kThreads, 0, st>>>(n, a, d_out);
+    return check_launch(2);
+}
+
+int launch_compare_i32(cudaStream_t st, int64_t count, const int32_t *a, const int32_t *b, int *d_err)
+{
+    if (count <= 0) return 0;
+    int g = grid_for(count);
+    if (g > 8192) g = 8192;
+    k_compare_i32<<<g, kThreads, 0, st>>>(count, a, b, d_err);
+    return check_launch();
+}
+
+int launch_spmm(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr,
+                const int32_t *colind, const double *val, const double *X, double *Y)
+{
+    if (n <= 0) return 0;
+    int g = grid_for((int64_t)n * s);
+    switch (s) {
+    case 1: k_spmm<1><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, Y); break;
+    case 2: k_spmm<2><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, Y); break;
+    case 4: k_spmm<4><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, Y); break;
+    case 8: k_spmm<8><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, Y); break;
+    case 16: k_spmm<16><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, Y); break;
+    default: return -1;
+    }
+    return check_launch();
+}
+
+int launch_pack(cudaStream_t st, int32_t s, int32_t n, const double *src, int64_t ld, double *dst)
+{
+    if (n <= 0) return 0;
+    int g = grid_for((int64_t)n * s);
+    switch (s) {
+    case 1: k_pack<1><<<g, kThreads, 0, st>>>(n, src, ld, dst); break;
+    case 2: k_pack<2><<<g, kThreads, 0, st>>>(n, src, ld, dst); break;
+    case 4: k_pack<4><<<g, kThreads, 0, st>>>(n, src, ld, dst); break;
+    case 8: k_pack<8><<<g, kThreads, 0, st>>>(n, src, ld, dst); break;
+    case 16: k_pack<16><<<g, kThreads, 0, st>>>(n, src, ld, dst); break;
+    default: return -1;
+    }
+    return check_launch();
+}
+
+int launch_unpack(cudaStream_t st, int32_t s, int32_t n, const double *src, double *dst, int64_t ld)
+{
+    if (n <= 0) return 0;
+    int g = grid_for((int64_t)n * s);
+    switch (s) {
+    case 1: k_unpack<1><<<g, kThreads, 0, st>>>(n, src, dst, ld); break;
+    case 2: k_unpack<2><<<g, kThreads, 0, st>>>(n, src, dst, ld); break;
+    case 4: k_unpack<4><<<g, kThreads, 0, st>>>(n, src, dst, ld); break;
+    case 8: k_unpack<8><<<g, kThreads, 0, st>>>(n, src, dst, ld); break;
+    case 16: k_unpack<16><<<g, kThreads, 0, st>>>(n, src, dst, ld); break;
+    default: return -1;
+    }
+    return check_launch();
+}
+
+}  // namespace spai

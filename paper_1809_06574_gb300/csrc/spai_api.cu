@@ -1,0 +1,1104 @@
+// C ABI of libspai_gb300 (declared in include/spai_gb300.h): context and handle
+// management, the build / update pipelines of the SPAI preconditioner (Sec. 2.2,
+// Sec. 2.3 Table 1, Sec. 2.4) and the host loop of right-preconditioned block GMRES(m)
+// (Sec. 2.1, Sec. 2.2 footnote).  Every arithmetic step runs in the kernels of
+// k_sparse.cu, k_spai.cu and k_krylov.cu; this file only sequences them, owns device
+// memory and turns failures into status codes.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "spai_internal.cuh"
+
+using namespace spai;
+
+struct spai_ctx_s {
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    size_t budget = 0;
+    size_t in_use = 0;
+    std::unordered_map<void *, size_t> sizes;
+    std::string err;
+    int *d_err = nullptr;      // device error word
+    int32_t *d_scalar = nullptr;  // small device scratch for host read-backs
+    void *ws = nullptr;        // grow-only solve workspace
+    size_t ws_bytes = 0;
+    double *h_pinned = nullptr;  // pinned host scratch for per-iteration read-backs
+    // optional per-kernel-family timing with CUDA events on the context's stream
+    struct ProfRec {
+        int family;
+        cudaEvent_t a, b;
+        double flops, bytes;
+    };
+    struct ProfFamily {
+        std::string name;
+        int64_t launches = 0;
+        double ms = 0.0, flops = 0.0, bytes = 0.0;
+    };
+    bool prof_on = false;
+    std::vector<ProfRec> prof_recs;
+    std::vector<cudaEvent_t> prof_pool;
+    std::vector<ProfFamily> prof_fam;
+};
+
+namespace {
+
+struct Sym {
+    int refs = 1;
+    spai_ctx ctx = nullptr;
+    int32_t n = 0, nnzA = 0, kind = 0;
+    int32_t *a_rowptr = nullptr, *a_colind = nullptr;            // copy of A's CSR pattern
+    int32_t *a_colptr = nullptr, *a_rowind = nullptr, *a_perm = nullptr;  // CSC + csc->csr
+    int32_t *Jptr = nullptr, *Jind = nullptr;                     // pattern of P (columns)
+    int32_t nnzP = 0;
+    int32_t *p_rowptr = nullptr, *p_colind = nullptr;             // pattern of P (rows)
+    int32_t *p_map = nullptr;                                     // J position -> P CSR position
+    bool alias = true;                                            // P pattern == A pattern
+    int32_t nI = 0;
+    int32_t *Iptr = nullptr, *Ilist = nullptr;
+    int32_t maxI = 0, maxJ = 0;
+};
+
+}  // namespace
+
+struct spai_pc_s {
+    spai_ctx ctx = nullptr;
+    Sym *sym = nullptr;
+    spai_pc parent = nullptr;
+    spai_pc root = nullptr;
+    int depth = 0;
+    double *fval = nullptr;    // own factor, P's CSR order
+    double *a_cval = nullptr;  // this matrix's values in CSC order
+    int32_t *status = nullptr;
+};
+
+struct spai_affine_s {
+    spai_ctx ctx = nullptr;
+    int32_t n = 0, T = 0;
+    int64_t nnz = 0;
+    int32_t *rowptr = nullptr, *colind = nullptr;
+    double *aligned = nullptr;  // T x nnz
+};
+
+namespace {
+
+spai_status fail(spai_ctx ctx, spai_status st, const char *fmt, ...)
+{
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return st;
+}
+
+spai_status cuda_fail(spai_ctx ctx, cudaError_t e, const char *what)
+{
+    return fail(ctx, SPAI_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CU(call, what)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+#define KL(call, what)                                                     \
+    do {                                                                   \
+        if ((call) != 0) {                                                 \
+            cudaError_t e_ = cudaGetLastError();                           \
+            return fail(ctx, SPAI_ECUDA, "%s: kernel launch failed (%s)", what, \
+                        cudaGetErrorString(e_));                           \
+        }                                                                  \
+    } while (0)
+
+cudaEvent_t prof_event(spai_ctx ctx)
+{
+    if (!ctx->prof_pool.empty()) {
+        cudaEvent_t e = ctx->prof_pool.back();
+        ctx->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+int prof_family(spai_ctx ctx, const char *name)
+{
+    for (size_t i = 0; i < ctx->prof_fam.size(); ++i)
+        if (ctx->prof_fam[i].name == name) return (int)i;
+    ctx->prof_fam.push_back({name});
+    return (int)ctx->prof_fam.size() - 1;
+}
+
+// Resolve recorded event pairs into the per-family totals (synchronises the stream).
+void prof_flush(spai_ctx ctx)
+{
+    if (ctx->prof_recs.empty()) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &r : ctx->prof_recs) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        auto &f = ctx->prof_fam[r.family];
+        f.launches += 1;
+        f.ms += ms;
+        f.flops += r.flops;
+        f.bytes += r.bytes;
+        ctx->prof_pool.push_back(r.a);
+        ctx->prof_pool.push_back(r.b);
+    }
+    ctx->prof_recs.clear();
+}
+
+// RAII timing of the launches issued inside its scope (no-op unless profiling is on).
+struct ProfScope {
+    spai_ctx ctx;
+    int fam = -1;
+    cudaEvent_t a = nullptr;
+    double flops, bytes;
+    ProfScope(spai_ctx c, const char *name, double fl, double by) : ctx(c), flops(fl), bytes(by)
+    {
+        if (!ctx->prof_on) return;
+        fam = prof_family(ctx, name);
+        a = prof_event(ctx);
+        cudaEventRecord(a, ctx->stream);
+    }
+    ~ProfScope()
+    {
+        if (fam < 0) return;
+        cudaEvent_t b = prof_event(ctx);
+        cudaEventRecord(b, ctx->stream);
+        ctx->prof_recs.push_back({fam, a, b, flops, bytes});
+        if (ctx->prof_recs.size() > 4096) prof_flush(ctx);
+    }
+};
+
+#define PKL(name, fl, by, call, what)          \
+    do {                                       \
+        ProfScope ps_(ctx, name, (fl), (by));  \
+        KL(call, what);                        \
+    } while (0)
+
+spai_status dalloc(spai_ctx ctx, void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) / 256 * 256;
+    if (ctx->budget && ctx->in_use + bytes > ctx->budget)
+        return fail(ctx, SPAI_ENOMEM, "memory budget exceeded: %zu in use + %zu requested > %zu",
+                    ctx->in_use, bytes, ctx->budget);
+    cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(ctx, SPAI_ENOMEM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    ctx->in_use += bytes;
+    ctx->sizes[*p] = bytes;
+    return SPAI_OK;
+}
+
+template <class Tp>
+spai_status dalloc_n(spai_ctx ctx, Tp **p, int64_t count)
+{
+    void *q = nullptr;
+    spai_status st = dalloc(ctx, &q, (size_t)(count < 1 ? 1 : count) * sizeof(Tp));
+    *p = (Tp *)q;
+    return st;
+}
+
+void dfree(spai_ctx ctx, void *p)
+{
+    if (!p) return;
+    auto it = ctx->sizes.find(p);
+    if (it != ctx->sizes.end()) {
+        ctx->in_use -= it->second;
+        ctx->sizes.erase(it);
+    }
+    cudaFreeAsync(p, ctx->stream);
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+spai_status read_err(spai_ctx ctx, int *h)
+{
+    CU(cudaMemcpyAsync(h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "read error word");
+    CU(cudaStreamSynchronize(ctx->stream), "stream sync");
+    CU(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream), "clear error word");
+    return SPAI_OK;
+}
+
+spai_status read_i32(spai_ctx ctx, const int32_t *d, int32_t *h)
+{
+    CU(cudaMemcpyAsync(h, d, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream), "read back");
+    CU(cudaStreamSynchronize(ctx->stream), "stream sync");
+    return SPAI_OK;
+}
+
+spai_status check_csr_args(spai_ctx ctx, const spai_csr *A, const char *name)
+{
+    if (!A) return fail(ctx, SPAI_EINVAL, "%s is NULL", name);
+    if (A->n < 0 || A->nnz < 0) return fail(ctx, SPAI_EINVAL, "%s: negative size", name);
+    if (A->n > 0 && (!A->rowptr || (A->nnz > 0 && (!A->colind || !A->val))))
+        return fail(ctx, SPAI_EINVAL, "%s: NULL array", name);
+    return SPAI_OK;
+}
+
+spai_status validate_device_csr(spai_ctx ctx, const spai_csr *A, const char *name)
+{
+    spai_status st = check_csr_args(ctx, A, name);
+    if (st) return st;
+    if (A->n == 0) return SPAI_OK;
+    if (!is_device_ptr(A->rowptr) || (A->nnz > 0 && (!is_device_ptr(A->colind) || !is_device_ptr(A->val))))
+        return fail(ctx, SPAI_EINVAL, "%s: arrays must be device memory", name);
+    KL(launch_validate_csr(ctx->stream, A->n, A->nnz, A->rowptr, A->colind, ctx->d_err), "validate");
+    int h = 0;
+    st = read_err(ctx, &h);
+    if (st) return st;
+    if (h & ERR_ROWPTR) return fail(ctx, SPAI_EINVAL, "%s: row pointer array is not a valid CSR row pointer", name);
+    if (h & ERR_COLIND)
+        return fail(ctx, SPAI_EINVAL, "%s: column indices out of range or not strictly increasing in a row", name);
+    return SPAI_OK;
+}
+
+void sym_release(Sym *s)
+{
+    if (!s || --s->refs > 0) return;
+    spai_ctx ctx = s->ctx;
+    dfree(ctx, s->a_rowptr);
+    dfree(ctx, s->a_colind);
+    dfree(ctx, s->a_colptr);
+    dfree(ctx, s->a_rowind);
+    dfree(ctx, s->a_perm);
+    if (!s->alias) {
+        dfree(ctx, s->Jptr);
+        dfree(ctx, s->Jind);
+        dfree(ctx, s->p_rowptr);
+        dfree(ctx, s->p_colind);
+        dfree(ctx, s->p_map);
+    }
+    dfree(ctx, s->Iptr);
+    dfree(ctx, s->Ilist);
+    delete s;
+}
+
+// sorted unions over columns of A: out_k = U_{j in L_k} rows(A(:,j))
+spai_status column_union(spai_ctx ctx, Sym *s, const int32_t *Lptr, const int32_t *Lind,
+                         int32_t **out_ptr, int32_t **out_list, int32_t *total, int32_t *maxlen)
+{
+    const int32_t n = s->n;
+    int32_t maxL = 0;
+    KL(launch_max_i32_diff(ctx->stream, n, Lptr, ctx->d_scalar), "max list length");
+    spai_status st = read_i32(ctx, ctx->d_scalar, &maxL);
+    if (st) return st;
+    if (maxL > colunion_max_lists())
+        return fail(ctx, SPAI_EINVAL, "a column pattern has %d entries; at most %d are supported", maxL,
+                    colunion_max_lists());
+    int32_t *counts = nullptr;
+    void *stemp = nullptr;
+    if ((st = dalloc_n(ctx, &counts, (int64_t)n + 1))) return st;
+    if ((st = dalloc(ctx, &stemp, scan_temp_bytes(n)))) { dfree(ctx, counts); return st; }
+    if ((st = dalloc_n(ctx, out_ptr, (int64_t)n + 1))) { dfree(ctx, counts); dfree(ctx, stemp); return st; }
+    KL(launch_colunion_count(ctx->stream, n, Lptr, Lind, s->a_colptr, s->a_rowind, counts, ctx->d_err), "union count");
+    KL(launch_exclusive_scan(ctx->stream, counts, *out_ptr, n, stemp, ctx->d_err), "scan");
+    int h = 0;
+    if ((st = read_err(ctx, &h))) return st;
+    if (h & ERR_OVERFLOW) return fail(ctx, SPAI_EINVAL, "index sets exceed 2^31 entries");
+    if ((st = read_i32(ctx, *out_ptr + n, total))) return st;
+    if ((st = dalloc_n(ctx, out_list, *total))) return st;
+    KL(launch_colunion_fill(ctx->stream, n, Lptr, Lind, s->a_colptr, s->a_rowind, *out_ptr, *out_list,
+                            ctx->d_err), "union fill");
+    KL(launch_max_i32_diff(ctx->stream, n, *out_ptr, ctx->d_scalar), "max set size");
+    if ((st = read_i32(ctx, ctx->d_scalar, maxlen))) return st;
+    dfree(ctx, counts);
+    dfree(ctx, stemp);
+    return SPAI_OK;
+}
+
+spai_status sym_create(spai_ctx ctx, const spai_csr *A, int32_t kind, Sym **out)
+{
+    *out = nullptr;
+    Sym *s = new Sym();
+    s->ctx = ctx;
+    s->n = A->n;
+    s->nnzA = A->nnz;
+    s->kind = kind;
+    const int32_t n = A->n, nnz = A->nnz;
+    spai_status st;
+    void *temp = nullptr;
+#define TRY(x)                 \
+    do {                       \
+        st = (x);              \
+        if (st) {              \
+            dfree(ctx, temp);  \
+            sym_release(s);    \
+            return st;         \
+        }                      \
+    } while (0)
+    TRY(dalloc_n(ctx, &s->a_rowptr, (int64_t)n + 1));
+    TRY(dalloc_n(ctx, &s->a_colind, nnz));
+    TRY(dalloc_n(ctx, &s->a_colptr, (int64_t)n + 1));
+    TRY(dalloc_n(ctx, &s->a_rowind, nnz));
+    TRY(dalloc_n(ctx, &s->a_perm, nnz));
+    CU(cudaMemcpyAsync(s->a_rowptr, A->rowptr, ((size_t)n + 1) * 4, cudaMemcpyDeviceToDevice, ctx->stream), "copy");
+    if (nnz) CU(cudaMemcpyAsync(s->a_colind, A->colind, (size_t)nnz * 4, cudaMemcpyDeviceToDevice, ctx->stream), "copy");
+    TRY(dalloc(ctx, &temp, transpose_temp_bytes(n, nnz)));
+    KL(launch_transpose(ctx->stream, n, nnz, s->a_rowptr, s->a_colind, s->a_colptr, s->a_rowind, s->a_perm,
+                        temp, ctx->d_err), "transpose");
+    if (kind == SPAI_PATTERN_A) {
+        s->alias = true;
+        s->Jptr = s->a_colptr;
+        s->Jind = s->a_rowind;
+        s->nnzP = nnz;
+        s->p_rowptr = s->a_rowptr;
+        s->p_colind = s->a_colind;
+        s->p_map = s->a_perm;
+        KL(launch_max_i32_diff(ctx->stream, n, s->Jptr, ctx->d_scalar), "max |J|");
+        TRY(read_i32(ctx, ctx->d_scalar, &s->maxJ));
+    } else {
+        s->alias = false;
+        // J_k = union over j in rows(A(:,k)) of rows(A(:,j)): the structural pattern of A^2
+        TRY(column_union(ctx, s, s->a_colptr, s->a_rowind, &s->Jptr, &s->Jind, &s->nnzP, &s->maxJ));
+        // row-wise pattern of P and the map from column positions to row positions
+        int32_t *perm_rows = nullptr;
+        TRY(dalloc_n(ctx, &s->p_rowptr, (int64_t)n + 1));
+        TRY(dalloc_n(ctx, &s->p_colind, s->nnzP));
+        TRY(dalloc_n(ctx, &s->p_map, s->nnzP));
+        TRY(dalloc_n(ctx, &perm_rows, s->nnzP));
+        dfree(ctx, temp);
+        temp = nullptr;
+        TRY(dalloc(ctx, &temp, transpose_temp_bytes(n, s->nnzP)));
+        KL(launch_transpose(ctx->stream, n, s->nnzP, s->Jptr, s->Jind, s->p_rowptr, s->p_colind, perm_rows,
+                            temp, ctx->d_err), "transpose pattern");
+        KL(launch_invert_perm(ctx->stream, s->nnzP, perm_rows, s->p_map), "invert");
+        dfree(ctx, perm_rows);
+    }
+    TRY(column_union(ctx, s, s->Jptr, s->Jind, &s->Iptr, &s->Ilist, &s->nI, &s->maxI));
+    int h = 0;
+    TRY(read_err(ctx, &h));
+    if (h) {
+        st = fail(ctx, SPAI_EINVAL, "pattern analysis failed (device error 0x%x)", h);
+        dfree(ctx, temp);
+        sym_release(s);
+        return st;
+    }
+    if (s->maxJ > 32 || s->maxI > 128) {
+        st = fail(ctx, SPAI_EINVAL, "column problem of %d x %d exceeds the 128 x 32 warp tile", s->maxI, s->maxJ);
+        dfree(ctx, temp);
+        sym_release(s);
+        return st;
+    }
+    dfree(ctx, temp);
+#undef TRY
+    *out = s;
+    return SPAI_OK;
+}
+
+spai_status run_columns(spai_ctx ctx, spai_pc pc, int mode, const double *rhs_cval)
+{
+    Sym *s = pc->sym;
+    ColumnProblem cp{};
+    cp.n = s->n;
+    cp.colptr = s->a_colptr;
+    cp.rowind = s->a_rowind;
+    cp.cval = pc->a_cval;
+    cp.Jptr = s->Jptr;
+    cp.Jind = s->Jind;
+    cp.Iptr = s->Iptr;
+    cp.Ilist = s->Ilist;
+    cp.mode = mode;
+    cp.r_colptr = s->a_colptr;
+    cp.r_rowind = s->a_rowind;
+    cp.r_val = rhs_cval;
+    cp.out_map = s->p_map;
+    cp.out_val = pc->fval;
+    cp.col_status = pc->status;
+    cp.d_err = ctx->d_err;
+    if (s->n == 0) return SPAI_OK;
+    {
+        const double aI = (double)s->nI / s->n, aJ = (double)s->nnzP / s->n;
+        const double fl = (double)s->n * (2 * aJ * aJ * (aI - aJ / 3) + 4 * aI * aJ + aJ * aJ);
+        const double by = 12.0 * s->nnzA * (mode ? 2 : 1) + 8.0 * (s->n + 1) + 4.0 * s->nI + 16.0 * s->nnzP;
+        PKL("spai_columns", fl, by, launch_spai_columns(ctx->stream, cp, s->maxI, s->maxJ), "column least squares");
+    }
+    // first singular column (or INT_MAX)
+    KL(launch_first_nonzero(ctx->stream, s->n, pc->status, ctx->d_scalar), "status scan");
+    int32_t first = INT_MAX;
+    spai_status st = read_i32(ctx, ctx->d_scalar, &first);
+    if (st) return st;
+    int h = 0;
+    if ((st = read_err(ctx, &h))) return st;
+    if (h) return fail(ctx, SPAI_EINVAL, "column least squares failed (device error 0x%x)", h);
+    if (first != INT_MAX)
+        return fail(ctx, SPAI_ESINGULAR, "column %d: rank-deficient least-squares problem (column set to 0)", first);
+    return SPAI_OK;
+}
+
+spai_status pc_alloc(spai_ctx ctx, Sym *s, spai_pc *out)
+{
+    spai_pc pc = new spai_pc_s();
+    pc->ctx = ctx;
+    pc->sym = s;
+    spai_status st;
+    if ((st = dalloc_n(ctx, &pc->fval, s->nnzP)) || (st = dalloc_n(ctx, &pc->a_cval, s->nnzA)) ||
+        (st = dalloc_n(ctx, &pc->status, s->n))) {
+        dfree(ctx, pc->fval);
+        dfree(ctx, pc->a_cval);
+        dfree(ctx, pc->status);
+        delete pc;
+        return st;
+    }
+    if (s->nnzP) CU(cudaMemsetAsync(pc->fval, 0, (size_t)s->nnzP * 8, ctx->stream), "memset");
+    *out = pc;
+    return SPAI_OK;
+}
+
+// Y = (chain of factors) X on row-major blocks; t0/t1 are n*s scratch blocks
+spai_status apply_rm(spai_ctx ctx, spai_pc pc, int32_t s, const double *X, double *Y, double *t0, double *t1)
+{
+    std::vector<spai_pc> chain;
+    for (spai_pc p = pc; p; p = p->parent) chain.push_back(p);
+    const double *cur = X;
+    double *bufs[2] = {t0, t1};
+    for (size_t i = chain.size(); i-- > 0;) {
+        spai_pc h = chain[i];
+        double *dst = (i == 0) ? Y : bufs[(chain.size() - 1 - i) & 1];
+        const double nz = h->sym->nnzP, nn = h->sym->n;
+        PKL("spmm_P", 2.0 * nz * s, 12.0 * nz + 4.0 * (nn + 1) + 16.0 * nn * s,
+            launch_spmm(ctx->stream, s, h->sym->n, h->sym->p_rowptr, h->sym->p_colind, h->fval, cur, dst),
+            "preconditioner apply");
+        cur = dst;
+    }
+    return SPAI_OK;
+}
+
+bool valid_s(int32_t s) { return s == 1 || s == 2 || s == 4 || s == 8 || s == 16; }
+
+}  // namespace
+
+// ===================================================================================
+// context
+// ===================================================================================
+extern "C" spai_status spai_ctx_create(spai_ctx *out, void *stream, size_t mem_budget)
+{
+    if (!out) return SPAI_EINVAL;
+    *out = nullptr;
+    spai_ctx ctx = new spai_ctx_s();
+    ctx->stream = (cudaStream_t)stream;
+    ctx->budget = mem_budget;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, 256);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, 256);
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pinned, 4096);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->d_err) cudaFree(ctx->d_err);
+        delete ctx;
+        return SPAI_ECUDA;
+    }
+    ctx->d_scalar = (int32_t *)(ctx->d_err + 16);
+    *out = ctx;
+    return SPAI_OK;
+}
+
+extern "C" spai_status spai_ctx_destroy(spai_ctx ctx)
+{
+    if (!ctx) return SPAI_EINVAL;
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->ws) dfree(ctx, ctx->ws);
+    cudaStreamSynchronize(ctx->stream);
+    prof_flush(ctx);
+    for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
+    cudaFree(ctx->d_err);
+    cudaFreeHost(ctx->h_pinned);
+    delete ctx;
+    return SPAI_OK;
+}
+
+extern "C" const char *spai_last_error(spai_ctx ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+extern "C" spai_status spai_ctx_sync(spai_ctx ctx)
+{
+    if (!ctx) return SPAI_EINVAL;
+    CU(cudaStreamSynchronize(ctx->stream), "stream sync");
+    return SPAI_OK;
+}
+
+extern "C" size_t spai_ctx_mem_in_use(spai_ctx ctx) { return ctx ? ctx->in_use : 0; }
+
+extern "C" int64_t spai_launch_count(void) { return spai::launches_total(); }
+
+extern "C" spai_status spai_measure_fp64_rate(spai_ctx ctx, double *tflops)
+{
+    if (!ctx || !tflops) return fail(ctx, SPAI_EINVAL, "NULL argument");
+    int sms = 0;
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "attribute");
+    const int blocks = sms * 8, threads = 256, iters = 4096;
+    cudaEvent_t a = nullptr, b = nullptr;
+    CU(cudaEventCreate(&a), "event");
+    CU(cudaEventCreate(&b), "event");
+    double *sink = (double *)ctx->d_scalar + 8;
+    KL(launch_fp64_probe(ctx->stream, blocks, threads, 256, sink), "warm-up");
+    CU(cudaEventRecord(a, ctx->stream), "event");
+    KL(launch_fp64_probe(ctx->stream, blocks, threads, iters, sink), "probe");
+    CU(cudaEventRecord(b, ctx->stream), "event");
+    CU(cudaEventSynchronize(b), "event sync");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *tflops = 2.0 * 8.0 * (double)blocks * threads * iters / (ms * 1e-3) / 1e12;
+    return SPAI_OK;
+}
+
+extern "C" spai_status spai_ctx_profile(spai_ctx ctx, int32_t enable)
+{
+    if (!ctx) return SPAI_EINVAL;
+    prof_flush(ctx);
+    ctx->prof_fam.clear();
+    ctx->prof_on = enable != 0;
+    return SPAI_OK;
+}
+
+extern "C" int32_t spai_ctx_profile_count(spai_ctx ctx)
+{
+    if (!ctx) return 0;
+    prof_flush(ctx);
+    return (int32_t)ctx->prof_fam.size();
+}
+
+extern "C" spai_status spai_ctx_profile_entry(spai_ctx ctx, int32_t i, const char **name, int64_t *launches,
+                                              double *ms, double *flops, double *bytes)
+{
+    if (!ctx) return SPAI_EINVAL;
+    prof_flush(ctx);
+    if (i < 0 || i >= (int32_t)ctx->prof_fam.size()) return fail(ctx, SPAI_EINVAL, "profile index out of range");
+    const auto &f = ctx->prof_fam[i];
+    if (name) *name = f.name.c_str();
+    if (launches) *launches = f.launches;
+    if (ms) *ms = f.ms;
+    if (flops) *flops = f.flops;
+    if (bytes) *bytes = f.bytes;
+    return SPAI_OK;
+}
+
+// ===================================================================================
+// affine assembly
+// ===================================================================================
+extern "C" spai_status spai_affine_create(spai_ctx ctx, int32_t nterms, const spai_csr *terms, spai_affine *out)
+{
+    if (!ctx || !out || !terms) return fail(ctx, SPAI_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (nterms < 1 || nterms > kMaxTerms) return fail(ctx, SPAI_EINVAL, "nterms must be in 1..%d", kMaxTerms);
+    const int32_t n = terms[0].n;
+    for (int t = 0; t < nterms; ++t) {
+        spai_status st = check_csr_args(ctx, &terms[t], "term");
+        if (st) return st;
+        if (terms[t].n != n) return fail(ctx, SPAI_EINVAL, "term %d has n=%d, expected %d", t, terms[t].n, n);
+    }
+    // copy every term to library memory (host or device source)
+    std::vector<int32_t *> rp(nterms, nullptr), ci(nterms, nullptr);
+    std::vector<double *> va(nterms, nullptr);
+    auto cleanup = [&]() {
+        for (int t = 0; t < nterms; ++t) { dfree(ctx, rp[t]); dfree(ctx, ci[t]); dfree(ctx, va[t]); }
+    };
+    spai_status st = SPAI_OK;
+    for (int t = 0; t < nterms && !st; ++t) {
+        const spai_csr &A = terms[t];
+        if ((st = dalloc_n(ctx, &rp[t], (int64_t)n + 1)) || (st = dalloc_n(ctx, &ci[t], A.nnz)) ||
+            (st = dalloc_n(ctx, &va[t], A.nnz)))
+            break;
+        cudaError_t e = cudaMemcpyAsync(rp[t], A.rowptr, ((size_t)n + 1) * 4, cudaMemcpyDefault, ctx->stream);
+        if (e == cudaSuccess && A.nnz)
+            e = cudaMemcpyAsync(ci[t], A.colind, (size_t)A.nnz * 4, cudaMemcpyDefault, ctx->stream);
+        if (e == cudaSuccess && A.nnz)
+            e = cudaMemcpyAsync(va[t], A.val, (size_t)A.nnz * 8, cudaMemcpyDefault, ctx->stream);
+        if (e != cudaSuccess) st = cuda_fail(ctx, e, "copy term");
+        if (!st && n > 0) {
+            if (launch_validate_csr(ctx->stream, n, A.nnz, rp[t], ci[t], ctx->d_err)) st = fail(ctx, SPAI_ECUDA, "validate");
+        }
+    }
+    int h = 0;
+    if (!st) st = read_err(ctx, &h);
+    if (!st && h) st = fail(ctx, SPAI_EINVAL, "a term is not a valid CSR matrix (device error 0x%x)", h);
+    if (st) { cleanup(); return st; }
+    TermPtrs tp{};
+    for (int t = 0; t < nterms; ++t) { tp.rowptr[t] = rp[t]; tp.colind[t] = ci[t]; tp.val[t] = va[t]; }
+    spai_affine aff = new spai_affine_s();
+    aff->ctx = ctx;
+    aff->n = n;
+    aff->T = nterms;
+    int32_t *counts = nullptr;
+    void *stemp = nullptr;
+    st = dalloc_n(ctx, &aff->rowptr, (int64_t)n + 1);
+    if (!st) st = dalloc_n(ctx, &counts, (int64_t)n + 1);
+    if (!st) st = dalloc(ctx, &stemp, scan_temp_bytes(n));
+    if (!st && n > 0) {
+        if (launch_union_count(ctx->stream, n, nterms, tp, counts) ||
+            launch_exclusive_scan(ctx->stream, counts, aff->rowptr, n, stemp, ctx->d_err))
+            st = fail(ctx, SPAI_ECUDA, "union pattern");
+    } else if (!st) {
+        cudaMemsetAsync(aff->rowptr, 0, 4, ctx->stream);
+    }
+    int32_t nnzU = 0;
+    if (!st) st = read_i32(ctx, aff->rowptr + n, &nnzU);
+    if (!st) st = read_err(ctx, &h);
+    if (!st && h) st = fail(ctx, SPAI_EINVAL, "union pattern exceeds 2^31 entries");
+    if (!st) { aff->nnz = nnzU; st = dalloc_n(ctx, &aff->colind, nnzU); }
+    if (!st) st = dalloc_n(ctx, &aff->aligned, (int64_t)nterms * nnzU);
+    if (!st && n > 0 && launch_union_fill(ctx->stream, n, nterms, tp, aff->rowptr, aff->colind, aff->aligned, nnzU))
+        st = fail(ctx, SPAI_ECUDA, "union fill");
+    if (!st) { cudaError_t e = cudaStreamSynchronize(ctx->stream); if (e) st = cuda_fail(ctx, e, "sync"); }
+    dfree(ctx, counts);
+    dfree(ctx, stemp);
+    cleanup();
+    if (st) { spai_affine_destroy(aff); return st; }
+    *out = aff;
+    return SPAI_OK;
+}
+
+extern "C" spai_status spai_affine_pattern(spai_affine aff, int32_t *n, int32_t *nnz, const int32_t **rowptr,
+                                           const int32_t **colind)
+{
+    if (!aff) return SPAI_EINVAL;
+    if (n) *n = aff->n;
+    if (nnz) *nnz = (int32_t)aff->nnz;
+    if (rowptr) *rowptr = aff->rowptr;
+    if (colind) *colind = aff->colind;
+    return SPAI_OK;
+}
+
+extern "C" spai_status spai_assemble(spai_ctx ctx, spai_affine aff, const double *coef, double *val_out)
+{
+    if (!ctx || !aff || !coef || (!val_out && aff->nnz)) return fail(ctx, SPAI_EINVAL, "NULL argument");
+    if (aff->nnz == 0) return SPAI_OK;
+    if (!is_device_ptr(val_out)) return fail(ctx, SPAI_EINVAL, "val_out must be device memory");
+    PKL("assemble", 2.0 * aff->T * aff->nnz, 8.0 * (aff->T + 1) * aff->nnz,
+        launch_assemble(ctx->stream, aff->nnz, aff->T, aff->aligned, coef, val_out), "assemble");
+    return SPAI_OK;
+}
+
+extern "C" spai_status spai_affine_export(spai_ctx ctx, spai_affine aff, int32_t *rowptr, int32_t *colind)
+{
+    if (!ctx || !aff) return fail(ctx, SPAI_EINVAL, "NULL argument");
+    if (rowptr)
+        CU(cudaMemcpyAsync(rowptr, aff->rowptr, ((size_t)aff->n + 1) * 4, cudaMemcpyDefault, ctx->stream), "export");
+    if (colind && aff->nnz)
+        CU(cudaMemcpyAsync(colind, aff->colind, (size_t)aff->nnz * 4, cudaMemcpyDefault, ctx->stream), "export");
+    CU(cudaStreamSynchronize(ctx->stream), "sync");
+    return SPAI_OK;
+}
+
+extern "C" spai_status spai_affine_destroy(spai_affine aff)
+{
+    if (!aff) return SPAI_EINVAL;
+    spai_ctx ctx = aff->ctx;
+    dfree(ctx, aff->rowptr);
+    dfree(ctx, aff->colind);
+    dfree(ctx, aff->aligned);
+    delete aff;
+    return SPAI_OK;
+}
+
+// ===================================================================================
+// SPAI build / update
+// ===================================================================================
+extern "C" spai_status spai_build(spai_ctx ctx, const spai_csr *A, int32_t pattern_kind, spai_pc *out)
+{
+    if (!ctx || !out) return fail(ctx, SPAI_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (pattern_kind != SPAI_PATTERN_A && pattern_kind != SPAI_PATTERN_A2)
+        return fail(ctx, SPAI_EINVAL, "unknown pattern kind %d", pattern_kind);
+    spai_status st = validate_device_csr(ctx, A, "A");
+    if (st) return st;
+    Sym *s = nullptr;
+    if ((st = sym_create(ctx, A, pattern_kind, &s))) return st;
+    spai_pc pc = nullptr;
+    if ((st = pc_alloc(ctx, s, &pc))) { sym_release(s); return st; }
+    pc->root = pc;
+    if (s->nnzA)
+        PKL("gather_csc", 0.0, 20.0 * s->nnzA, launch_gather_f64(ctx->stream, s->nnzA, s->a_perm, A->val, pc->a_cval),
+            "gather values");
+    st = run_columns(ctx, pc, 0, nullptr);
+    if (st && st != SPAI_ESINGULAR) { spai_pc_destroy(pc); return st; }
+    *out = pc;
+    return st;
+}
+
+extern "C" spai_status spai_update(spai_ctx ctx, spai_pc base, const spai_csr *A_new, int32_t approach, spai_pc *out)
+{
+    if (!ctx || !out || !base) return fail(ctx, SPAI_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (approach != SPAI_UPDATE_FIRST && approach != SPAI_UPDATE_CHAINED)
+        return fail(ctx, SPAI_EINVAL, "unknown update approach %d", approach);
+    spai_status st = check_csr_args(ctx, A_new, "A_new");
+    if (st) return st;
+    Sym *s = base->sym;
+    if (A_new->n != s->n || A_new->nnz != s->nnzA)
+        return fail(ctx, SPAI_EINVAL, "A_new (n=%d, nnz=%d) does not have the base pattern (n=%d, nnz=%d)",
+                    A_new->n, A_new->nnz, s->n, s->nnzA);
+    if (s->n && (!is_device_ptr(A_new->rowptr) || (s->nnzA && (!is_device_ptr(A_new->colind) || !is_device_ptr(A_new->val)))))
+        return fail(ctx, SPAI_EINVAL, "A_new: arrays must be device memory");
+    if (s->n) {
+        KL(launch_compare_i32(ctx->stream, (int64_t)s->n + 1, A_new->rowptr, s->a_rowptr, ctx->d_err), "compare");
+        KL(launch_compare_i32(ctx->stream, s->nnzA, A_new->colind, s->a_colind, ctx->d_err), "compare");
+        int h = 0;
+        if ((st = read_err(ctx, &h))) return st;
+        if (h) return fail(ctx, SPAI_EINVAL, "A_new does not have the base matrix's sparsity pattern");
+    }
+    spai_pc pc = nullptr;
+    if ((st = pc_alloc(ctx, s, &pc))) return st;
+    s->refs++;
+    spai_pc from = (approach == SPAI_UPDATE_FIRST) ? base->root : base;
+    pc->parent = from;
+    pc->root = base->root;
+    pc->depth = from->depth + 1;
+    if (s->nnzA)
+        PKL("gather_csc", 0.0, 20.0 * s->nnzA,
+            launch_gather_f64(ctx->stream, s->nnzA, s->a_perm, A_new->val, pc->a_cval), "gather values");
+    st = run_columns(ctx, pc, 1, from->a_cval);
+    if (st && st != SPAI_ESINGULAR) { spai_pc_destroy(pc); return st; }
+    *out = pc;
+    return st;
+}
+
+extern "C" spai_status spai_pc_info(spai_pc pc, int32_t *n, int32_t *nnz, int64_t *nI, int32_t *depth)
+{
+    if (!pc) return SPAI_EINVAL;
+    if (n) *n = pc->sym->n;
+    if (nnz) *nnz = pc->sym->nnzP;
+    if (nI) *nI = pc->sym->nI;
+    if (depth) *depth = pc->depth;
+    return SPAI_OK;
+}
+
+extern "C" spai_status spai_pc_export(spai_ctx ctx, spai_pc pc, int32_t *Jptr, int32_t *Jind, double *val,
+                                      int32_t *Iptr, int32_t *Ilist, int32_t *col_status)
+{
+    if (!ctx || !pc) return fail(ctx, SPAI_EINVAL, "NULL argument");
+    Sym *s = pc->sym;
+    const int32_t n = s->n;
+    if (Jptr) CU(cudaMemcpyAsync(Jptr, s->Jptr, ((size_t)n + 1) * 4, cudaMemcpyDeviceToDevice, ctx->stream), "export");
+    if (Jind && s->nnzP) CU(cudaMemcpyAsync(Jind, s->Jind, (size_t)s->nnzP * 4, cudaMemcpyDeviceToDevice, ctx->stream), "export");
+    if (val && s->nnzP) KL(launch_gather_f64(ctx->stream, s->nnzP, s->p_map, pc->fval, val), "export values");
+    if (Iptr) CU(cudaMemcpyAsync(Iptr, s->Iptr, ((size_t)n + 1) * 4, cudaMemcpyDeviceToDevice, ctx->stream), "export");
+    if (Ilist && s->nI) CU(cudaMemcpyAsync(Ilist, s->Ilist, (size_t)s->nI * 4, cudaMemcpyDeviceToDevice, ctx->stream), "export");
+    if (col_status && n) CU(cudaMemcpyAsync(col_status, pc->status, (size_t)n * 4, cudaMemcpyDeviceToDevice, ctx->stream), "export");
+    return SPAI_OK;
+}
+
+extern "C" spai_status spai_pc_destroy(spai_pc pc)
+{
+    if (!pc) return SPAI_EINVAL;
+    spai_ctx ctx = pc->ctx;
+    dfree(ctx, pc->fval);
+    dfree(ctx, pc->a_cval);
+    dfree(ctx, pc->status);
+    sym_release(pc->sym);
+    delete pc;
+    return SPAI_OK;
+}
+
+// ===================================================================================
+// products
+// ===================================================================================
+namespace {
+
+struct Block {
+    double *p = nullptr;
+};
+
+spai_status temp_blocks(spai_ctx ctx, size_t bytes, void **p)
+{
+    if (ctx->ws_bytes >= bytes) { *p = ctx->ws; return SPAI_OK; }
+    if (ctx->ws) { dfree(ctx, ctx->ws); ctx->ws = nullptr; ctx->ws_bytes = 0; }
+    spai_status st = dalloc(ctx, &ctx->ws, bytes);
+    if (st) return st;
+    ctx->ws_bytes = bytes;
+    *p = ctx->ws;
+    return SPAI_OK;
+}
+
+}  // namespace
+
+extern "C" spai_status spai_spmm(spai_ctx ctx, const spai_csr *A, int32_t s, const double *X, int64_t ldx,
+                                 double *Y, int64_t ldy)
+{
+    if (!ctx) return SPAI_EINVAL;
+    spai_status st = check_csr_args(ctx, A, "A");
+    if (st) return st;
+    if (!valid_s(s)) return fail(ctx, SPAI_EINVAL, "s must be 1, 2, 4, 8 or 16");
+    const int32_t n = A->n;
+    if (n == 0) return SPAI_OK;
+    if (ldx < n || ldy < n || !X || !Y) return fail(ctx, SPAI_EINVAL, "bad block arguments");
+    void *w = nullptr;
+    const size_t blk = (size_t)n * s * 8;
+    if ((st = temp_blocks(ctx, 2 * blk, &w))) return st;
+    double *xr = (double *)w, *yr = (double *)((char *)w + blk);
+    KL(launch_pack(ctx->stream, s, n, X, ldx, xr), "pack");
+    KL(launch_spmm(ctx->stream, s, n, A->rowptr, A->colind, A->val, xr, yr), "spmm");
+    KL(launch_unpack(ctx->stream, s, n, yr, Y, ldy), "unpack");
+    return SPAI_OK;
+}
+
+extern "C" spai_status spai_pc_apply(spai_ctx ctx, spai_pc pc, int32_t s, const double *X, int64_t ldx, double *Y,
+                                     int64_t ldy)
+{
+    if (!ctx || !pc) return fail(ctx, SPAI_EINVAL, "NULL argument");
+    if (!valid_s(s)) return fail(ctx, SPAI_EINVAL, "s must be 1, 2, 4, 8 or 16");
+    const int32_t n = pc->sym->n;
+    if (n == 0) return SPAI_OK;
+    if (ldx < n || ldy < n || !X || !Y) return fail(ctx, SPAI_EINVAL, "bad block arguments");
+    void *w = nullptr;
+    const size_t blk = (size_t)n * s * 8;
+    spai_status st = temp_blocks(ctx, 4 * blk, &w);
+    if (st) return st;
+    double *xr = (double *)w, *yr = xr + (size_t)n * s, *t0 = yr + (size_t)n * s, *t1 = t0 + (size_t)n * s;
+    KL(launch_pack(ctx->stream, s, n, X, ldx, xr), "pack");
+    if ((st = apply_rm(ctx, pc, s, xr, yr, t0, t1))) return st;
+    KL(launch_unpack(ctx->stream, s, n, yr, Y, ldy), "unpack");
+    return SPAI_OK;
+}
+
+// ===================================================================================
+// block GMRES(m)
+// ===================================================================================
+namespace {
+
+struct SolveWs {
+    double *Bw, *Xw, *W, *Z, *T0, *T1, *V;
+    double *partial, *H1, *H2, *Hup, *G1, *R1, *R2, *Rn, *ref2, *nrm2, *thresh, *Hcol, *Qs, *Rtri, *G, *Y, *est;
+    int32_t *defl1, *defl2, *flag;
+};
+
+size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks)
+{
+    char *p = (char *)base;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void * {
+        void *r = base ? (void *)(p + off) : nullptr;
+        off += (bytes + 255) / 256 * 256;
+        return r;
+    };
+    const size_t blk = (size_t)n * s * 8;
+    const size_t ss = (size_t)s * s * 8;
+    w.Bw = (double *)take(blk);
+    w.Xw = (double *)take(blk);
+    w.W = (double *)take(blk);
+    w.Z = (double *)take(blk);
+    w.T0 = (double *)take(blk);
+    w.T1 = (double *)take(blk);
+    w.V = (double *)take(blk * (m + 1));
+    w.partial = (double *)take((size_t)chunks * (m + 1) * ss);
+    w.H1 = (double *)take((m + 1) * ss);
+    w.H2 = (double *)take((m + 1) * ss);
+    w.Hup = (double *)take((m + 1) * ss);
+    w.G1 = (double *)take(ss);
+    w.R1 = (double *)take(ss);
+    w.R2 = (double *)take(ss);
+    w.Rn = (double *)take(ss);
+    w.ref2 = (double *)take(s * 8);
+    w.nrm2 = (double *)take(s * 8);
+    w.thresh = (double *)take(s * 8);
+    w.Hcol = (double *)take((size_t)(m + 1) * s * s * 8);
+    w.Qs = (double *)take((size_t)m * 4 * ss);
+    w.Rtri = (double *)take((size_t)(m + 1) * s * m * s * 8);
+    w.G = (double *)take((m + 1) * ss);
+    w.Y = (double *)take(m * ss);
+    w.est = (double *)take(s * 8);
+    w.defl1 = (int32_t *)take(s * 4);
+    w.defl2 = (int32_t *)take(s * 4);
+    w.flag = (int32_t *)take(64);
+    return off;
+}
+
+// W = Q R with Q orthonormal (deflated columns zero), two passes of Cholesky QR
+spai_status cholqr2(spai_ctx ctx, SolveWs &w, int32_t n, int32_t s, int chunks, const double *Win, double *Qout,
+                    double *Rout, const double *ref2)
+{
+    cudaStream_t st = ctx->stream;
+    const double nsd = (double)n * s;
+    PKL("block_dot", 2.0 * nsd * s, 8.0 * nsd, launch_block_dot(st, s, n, 1, Win, Win, w.partial, w.G1, chunks), "gram");
+    PKL("small_dense", 0.0, 0.0, launch_chol_small(st, s, w.G1, ref2, 1e-24, w.R1, w.defl1), "chol");
+    PKL("trsm_rows", nsd * s, 16.0 * nsd, launch_trsm_rows(st, s, n, Win, w.R1, w.defl1, Qout), "trsm");
+    PKL("block_dot", 2.0 * nsd * s, 8.0 * nsd, launch_block_dot(st, s, n, 1, Qout, Qout, w.partial, w.G1, chunks), "gram");
+    PKL("small_dense", 0.0, 0.0, launch_chol_small(st, s, w.G1, nullptr, 0.0, w.R2, w.defl2), "chol");
+    PKL("trsm_rows", nsd * s, 16.0 * nsd, launch_trsm_rows(st, s, n, Qout, w.R2, w.defl2, Qout), "trsm");
+    PKL("small_dense", 0.0, 0.0, launch_triu_mul(st, s, w.R2, w.R1, Rout), "triu");
+    return SPAI_OK;
+}
+
+}  // namespace
+
+extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, int32_t s, const double *B,
+                                   int64_t ldb, double *X, int64_t ldx, const spai_solve_opts *opts,
+                                   spai_solve_info *info, double *rel_residual)
+{
+    if (!ctx) return SPAI_EINVAL;
+    spai_status st = check_csr_args(ctx, A, "A");
+    if (st) return st;
+    if (!opts || !B || !X) return fail(ctx, SPAI_EINVAL, "NULL argument");
+    if (!valid_s(s)) return fail(ctx, SPAI_EINVAL, "s must be 1, 2, 4, 8 or 16");
+    const int32_t n = A->n, m = opts->restart;
+    if (m < 1 || opts->max_cycles < 1 || !(opts->tol >= 0.0))
+        return fail(ctx, SPAI_EINVAL, "restart and max_cycles must be >= 1 and tol >= 0");
+    if (ldb < n || ldx < n) return fail(ctx, SPAI_EINVAL, "leading dimension smaller than n");
+    if (P && P->sym->n != n) return fail(ctx, SPAI_EINVAL, "preconditioner size %d != n %d", P->sym->n, n);
+    if (n > 0 && (!is_device_ptr(A->rowptr) || !is_device_ptr(A->colind) || !is_device_ptr(A->val)))
+        return fail(ctx, SPAI_EINVAL, "A: arrays must be device memory");
+    if (info) memset(info, 0, sizeof *info);
+    if (n == 0) {
+        if (info) info->converged = 1;
+        return SPAI_OK;
+    }
+    const int chunks = krylov_chunks(n);
+    SolveWs w{};
+    const size_t need = carve(w, nullptr, n, s, m, chunks);
+    void *base = nullptr;
+    if ((st = temp_blocks(ctx, need, &base))) return st;
+    carve(w, base, n, s, m, chunks);
+    cudaStream_t cs = ctx->stream;
+    const bool b_dev = is_device_ptr(B), x_dev = is_device_ptr(X);
+
+    // inputs -> row-major device blocks (T0 stages host data column-major)
+    if (b_dev) {
+        KL(launch_pack(cs, s, n, B, ldb, w.Bw), "pack B");
+    } else {
+        CU(cudaMemcpy2DAsync(w.T0, (size_t)n * 8, B, (size_t)ldb * 8, (size_t)n * 8, s, cudaMemcpyHostToDevice, cs), "copy B");
+        KL(launch_pack(cs, s, n, w.T0, n, w.Bw), "pack B");
+    }
+    if (x_dev) {
+        KL(launch_pack(cs, s, n, X, ldx, w.Xw), "pack X");
+    } else {
+        CU(cudaMemcpy2DAsync(w.T0, (size_t)n * 8, X, (size_t)ldx * 8, (size_t)n * 8, s, cudaMemcpyHostToDevice, cs), "copy X");
+        KL(launch_pack(cs, s, n, w.T0, n, w.Xw), "pack X");
+    }
+    const size_t blk_elems = (size_t)n * s;
+    const double nsd = (double)n * s;
+    double *h = ctx->h_pinned;  // [0,16) bnorm2, [16,32) rn2, [32,48) est, [48] flag
+    KL(launch_colnorm2(cs, s, n, w.Bw, w.partial, w.nrm2, chunks), "norm B");
+    CU(cudaMemcpyAsync(h, w.nrm2, s * 8, cudaMemcpyDeviceToHost, cs), "read norms");
+    CU(cudaStreamSynchronize(cs), "sync");
+    double thresh[16], bnorm[16];
+    for (int i = 0; i < s; ++i) {
+        bnorm[i] = sqrt(h[i]);
+        thresh[i] = opts->tol * bnorm[i];
+    }
+    CU(cudaMemcpyAsync(w.thresh, thresh, s * 8, cudaMemcpyHostToDevice, cs), "write thresholds");
+
+    auto residual = [&]() -> spai_status {
+        PKL("residual", 2.0 * A->nnz * s + nsd, 12.0 * A->nnz + 4.0 * (n + 1) + 24.0 * nsd,
+            launch_residual(cs, s, n, A->rowptr, A->colind, A->val, w.Xw, w.Bw, w.W), "residual");
+        PKL("colnorm2", 2.0 * nsd, 8.0 * nsd, launch_colnorm2(cs, s, n, w.W, w.partial, w.ref2, chunks), "residual norms");
+        CU(cudaMemcpyAsync(h + 16, w.ref2, s * 8, cudaMemcpyDeviceToHost, cs), "read norms");
+        CU(cudaStreamSynchronize(cs), "sync");
+        return SPAI_OK;
+    };
+    auto converged = [&]() {
+        for (int i = 0; i < s; ++i)
+            if (!(sqrt(h[16 + i]) <= thresh[i])) return false;
+        return true;
+    };
+    if ((st = residual())) return st;
+    int cycles = 0, iters = 0;
+    while (!converged() && cycles < opts->max_cycles) {
+        ++cycles;
+        // V_0 S_0 = R (ref2 holds the residual norms^2)
+        if ((st = cholqr2(ctx, w, n, s, chunks, w.W, w.V, w.Rn, w.ref2))) return st;
+        PKL("small_dense", 0.0, 0.0, launch_set_rhs(cs, s, m, w.Rn, w.G), "rhs");
+        int J = 0;
+        for (int j = 0; j < m; ++j) {
+            const double *Vj = w.V + (size_t)j * blk_elems;
+            const double *Zj = Vj;
+            if (P) {
+                if ((st = apply_rm(ctx, P, s, Vj, w.Z, w.T0, w.T1))) return st;
+                Zj = w.Z;
+            }
+            PKL("spmm_A", 2.0 * A->nnz * s, 12.0 * A->nnz + 4.0 * (n + 1) + 16.0 * nsd,
+                launch_spmm(cs, s, n, A->rowptr, A->colind, A->val, Zj, w.W), "A Z");
+            PKL("colnorm2", 2.0 * nsd, 8.0 * nsd, launch_colnorm2(cs, s, n, w.W, w.partial, w.ref2, chunks), "norms");
+            // two passes of block classical Gram-Schmidt against V_0..V_j
+            const double nb = j + 1;
+            PKL("block_dot", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
+                launch_block_dot(cs, s, n, j + 1, w.V, w.W, w.partial, w.H1, chunks), "H1");
+            PKL("block_update", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 2),
+                launch_block_update(cs, s, n, j + 1, w.V, w.H1, w.W, w.W, -1.0), "W -= V H1");
+            PKL("block_dot", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
+                launch_block_dot(cs, s, n, j + 1, w.V, w.W, w.partial, w.H2, chunks), "H2");
+            PKL("block_update", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 2),
+                launch_block_update(cs, s, n, j + 1, w.V, w.H2, w.W, w.W, -1.0), "W -= V H2");
+            PKL("small_dense", 0.0, 0.0, launch_add_small(cs, (j + 1) * s * s, w.H1, w.H2, w.Hup), "H1 + H2");
+            double *Vn = w.V + (size_t)(j + 1) * blk_elems;
+            if ((st = cholqr2(ctx, w, n, s, chunks, w.W, Vn, w.Rn, w.ref2))) return st;
+            PKL("small_dense", 0.0, 0.0, launch_copy_hcol(cs, s, j, (m + 1) * s, w.Hup, w.Rn, w.Hcol), "H column");
+            PKL("arnoldi_ls", 16.0 * s * s * s * (j + 1), 0.0,
+                launch_arnoldi_ls(cs, s, j, m, w.Hcol, w.Qs, w.Rtri, w.G, w.thresh, w.est, w.flag), "least squares");
+            CU(cudaMemcpyAsync(h + 32, w.est, s * 8, cudaMemcpyDeviceToHost, cs), "read estimates");
+            CU(cudaMemcpyAsync(h + 48, w.flag, 4, cudaMemcpyDeviceToHost, cs), "read flag");
+            CU(cudaStreamSynchronize(cs), "sync");
+            ++iters;
+            J = j + 1;
+            if (*(int32_t *)(h + 48)) break;
+        }
+        // X += P (V Y)
+        PKL("backsolve", (double)J * s * J * s * s, 0.0, launch_backsolve(cs, s, J, (m + 1) * s, w.Rtri, w.G, w.Y),
+            "back substitution");
+        PKL("block_update", 2.0 * nsd * s * J, 8.0 * nsd * (J + 1), launch_block_update(cs, s, n, J, w.V, w.Y, nullptr, w.W, 1.0),
+            "V Y");
+        const double *U = w.W;
+        if (P) {
+            if ((st = apply_rm(ctx, P, s, w.W, w.Z, w.T0, w.T1))) return st;
+            U = w.Z;
+        }
+        PKL("axpy", 2.0 * nsd, 24.0 * nsd, launch_axpy(cs, (int64_t)blk_elems, 1.0, U, w.Xw), "X update");
+        if ((st = residual())) return st;
+    }
+    // solution out
+    if (x_dev) {
+        KL(launch_unpack(cs, s, n, w.Xw, X, ldx), "unpack X");
+    } else {
+        KL(launch_unpack(cs, s, n, w.Xw, w.T0, n), "unpack X");
+        CU(cudaMemcpy2DAsync(X, (size_t)ldx * 8, w.T0, (size_t)n * 8, (size_t)n * 8, s, cudaMemcpyDeviceToHost, cs), "copy X");
+    }
+    CU(cudaStreamSynchronize(cs), "sync");
+    int worst = 0;
+    double worst_rel = -1.0;
+    bool conv = true;
+    for (int i = 0; i < s; ++i) {
+        const double rn = sqrt(h[16 + i]);
+        const double rel = bnorm[i] > 0 ? rn / bnorm[i] : rn;
+        if (rel > worst_rel) { worst_rel = rel; worst = i; }
+        if (!(rn <= thresh[i])) conv = false;
+        if (rel_residual) rel_residual[i] = rel;
+    }
+    if (info) {
+        info->iterations = iters;
+        info->cycles = cycles;
+        info->converged = conv ? 1 : 0;
+        info->worst_column = worst;
+        info->max_rel_residual = worst_rel;
+    }
+    if (!conv) return fail(ctx, SPAI_ENOTCONV, "not converged after %d cycles: column %d relative residual %.3e",
+                           cycles, worst, worst_rel);
+    return SPAI_OK;
+}

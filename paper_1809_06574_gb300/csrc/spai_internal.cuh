@@ -1,0 +1,130 @@
+// Internal declarations shared by the CUDA translation units of libspai_gb300.
+// Kernels live in k_sparse.cu (assembly, transposition, index sets, SpMM), k_spai.cu
+// (per-column gather + Householder least squares) and k_krylov.cu (block GMRES pieces);
+// spai_api.cu implements the C ABI declared in include/spai_gb300.h on top of them.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "spai_gb300.h"
+
+namespace spai {
+
+constexpr int kMaxTerms = 16;
+
+// Device-side error word bits (written with atomicOr, read by the host after a sync).
+enum : int {
+    ERR_ROWPTR = 1 << 0,      // rowptr not monotone / wrong ends
+    ERR_COLIND = 1 << 1,      // column index out of range or not strictly increasing
+    ERR_OVERFLOW = 1 << 2,    // a prefix sum exceeds int32
+    ERR_TOO_WIDE = 1 << 3,    // a column problem exceeds the kernel's tile
+    ERR_PATTERN = 1 << 4,     // values do not fit the expected pattern
+};
+
+struct TermPtrs {
+    const int32_t *rowptr[kMaxTerms];
+    const int32_t *colind[kMaxTerms];
+    const double *val[kMaxTerms];
+    double coef[kMaxTerms];
+};
+
+// process-wide count of kernels launched by the library
+void note_launches(int k);
+long long launches_total();
+
+// ---------------------------------------------------------------------- k_sparse.cu
+int launch_validate_csr(cudaStream_t st, int32_t n, int32_t nnz, const int32_t *rowptr,
+                        const int32_t *colind, int *d_err);
+int launch_union_count(cudaStream_t st, int32_t n, int32_t T, const TermPtrs &tp, int32_t *counts);
+int launch_union_fill(cudaStream_t st, int32_t n, int32_t T, const TermPtrs &tp,
+                      const int32_t *u_rowptr, int32_t *u_colind, double *aligned,
+                      int64_t nnzU);
+int launch_assemble(cudaStream_t st, int64_t nnz, int32_t T, const double *aligned,
+                    const double *coef_host, double *out);
+// ptr[0] = 0, ptr[i+1] = ptr[i] + counts[i]; temp must hold scan_temp_bytes(n)
+size_t scan_temp_bytes(int64_t n);
+int launch_exclusive_scan(cudaStream_t st, const int32_t *counts, int32_t *ptr, int64_t n,
+                          void *temp, int *d_err);
+// CSR (n x n) -> CSC pattern: colptr[n+1], rowind[nnz] ascending per column, perm[csc] = csr
+size_t transpose_temp_bytes(int32_t n, int32_t nnz);
+int launch_transpose(cudaStream_t st, int32_t n, int32_t nnz, const int32_t *rowptr,
+                     const int32_t *colind, int32_t *colptr, int32_t *rowind, int32_t *perm,
+                     void *temp, int *d_err);
+// out_k = sorted union over j in L_k of rows(colptr/rowind column j); two passes
+// (at most colunion_max_lists() columns in any L_k, else ERR_TOO_WIDE)
+int colunion_max_lists();
+int launch_colunion_count(cudaStream_t st, int32_t n, const int32_t *Lptr, const int32_t *Lind,
+                          const int32_t *colptr, const int32_t *rowind, int32_t *counts,
+                          int *d_err);
+int launch_colunion_fill(cudaStream_t st, int32_t n, const int32_t *Lptr, const int32_t *Lind,
+                         const int32_t *colptr, const int32_t *rowind, const int32_t *out_ptr,
+                         int32_t *out_list, int *d_err);
+int launch_gather_f64(cudaStream_t st, int64_t count, const int32_t *idx, const double *src,
+                      double *dst);
+int launch_invert_perm(cudaStream_t st, int64_t count, const int32_t *perm, int32_t *inv);
+int launch_max_i32_diff(cudaStream_t st, int32_t n, const int32_t *ptr, int32_t *d_max);
+int launch_fill_i32(cudaStream_t st, int64_t count, int32_t v, int32_t *dst);
+// *d_out = smallest i with a[i] != 0, or INT_MAX
+int launch_first_nonzero(cudaStream_t st, int32_t n, const int32_t *a, int32_t *d_out);
+// sets ERR_PATTERN in *d_err if a[i] != b[i] for some i < count
+int launch_compare_i32(cudaStream_t st, int64_t count, const int32_t *a, const int32_t *b, int *d_err);
+// row-major blocks: X[r * s + c]
+int launch_spmm(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr,
+                const int32_t *colind, const double *val, const double *X, double *Y);
+int launch_pack(cudaStream_t st, int32_t s, int32_t n, const double *src, int64_t ld, double *dst);
+int launch_unpack(cudaStream_t st, int32_t s, int32_t n, const double *src, double *dst,
+                  int64_t ld);
+
+// ---------------------------------------------------------------------- k_spai.cu
+struct ColumnProblem {
+    int32_t n;
+    const int32_t *colptr, *rowind;  // CSC pattern of A (matrix of the least squares)
+    const double *cval;              // A values in CSC order
+    const int32_t *Jptr, *Jind;      // column pattern of the result
+    const int32_t *Iptr, *Ilist;     // row sets
+    int32_t mode;                    // 0 build (rhs e_k), 1 update (rhs column k of R)
+    const int32_t *r_colptr, *r_rowind;
+    const double *r_val;             // rhs matrix (CSC values) in update mode
+    const int32_t *out_map;          // J position -> position in the output array
+    double *out_val;
+    int32_t *col_status;             // 0 ok, 1 singular
+    int *d_err;
+};
+// Picks the tile by the largest |I_k|, |J_k|; returns 0 or -1 if no tile fits.
+int launch_spai_columns(cudaStream_t st, const ColumnProblem &cp, int32_t maxI, int32_t maxJ);
+
+// ---------------------------------------------------------------------- k_krylov.cu
+struct KrylovWs;
+int krylov_chunks(int32_t n);
+int launch_colnorm2(cudaStream_t st, int32_t s, int32_t n, const double *W, double *partial,
+                    double *out, int chunks);
+int launch_block_dot(cudaStream_t st, int32_t s, int32_t n, int32_t nblk, const double *V,
+                     const double *W, double *partial, double *out, int chunks);
+int launch_block_update(cudaStream_t st, int32_t s, int32_t n, int32_t nblk, const double *V,
+                        const double *H, const double *base, double *out, double sign);
+int launch_chol_small(cudaStream_t st, int32_t s, const double *G, const double *ref2,
+                      double tau2, double *R, int32_t *deflated);
+int launch_trsm_rows(cudaStream_t st, int32_t s, int32_t n, const double *W, const double *R,
+                     const int32_t *deflated, double *out);
+int launch_triu_mul(cudaStream_t st, int32_t s, const double *R2, const double *R1, double *out);
+int launch_add_small(cudaStream_t st, int32_t count, const double *a, const double *b, double *out);
+int launch_copy_hcol(cudaStream_t st, int32_t s, int32_t j, int32_t ldh, const double *Hup,
+                     const double *Rsub, double *Hcol);
+int launch_arnoldi_ls(cudaStream_t st, int32_t s, int32_t j, int32_t m, double *Hcol,
+                      double *Qs, double *Rtri, double *G, const double *thresh, double *est,
+                      int32_t *flag);
+int launch_set_rhs(cudaStream_t st, int32_t s, int32_t m, const double *S0, double *G);
+int launch_backsolve(cudaStream_t st, int32_t s, int32_t J, int32_t ldr, const double *Rtri,
+                     const double *G, double *Y);
+int launch_axpy(cudaStream_t st, int64_t count, double alpha, const double *x, double *y);
+int launch_residual(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr,
+                    const int32_t *colind, const double *val, const double *X, const double *B,
+                    double *R);
+int launch_zero(cudaStream_t st, int64_t count, double *dst);
+// FP64 FMA throughput probe: blocks x threads x 8 chains x iters FMAs
+int launch_fp64_probe(cudaStream_t st, int blocks, int threads, int iters, double *sink);
+
+}  // namespace spai

@@ -1,0 +1,75 @@
+"""Host-side checks of the C ABI (no GPU needed): the shared library loads and exports
+every function declared in include/spai_gb300.h, and the Python binding wraps exactly
+those names.  Also checks that the product package never imports the oracle."""
+
+import ast
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "spai_gb300.h")
+PKG = os.path.join(ROOT, "paper_1809_06574_gb300")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    names = re.findall(r"^SPAI_API\s+[\w\s\*]+?\b(\w+)\s*\(", text, flags=re.M)
+    assert names, "no declarations found"
+    return names
+
+
+@pytest.fixture(scope="module")
+def library():
+    import ctypes
+
+    from paper_1809_06574_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = set(declared_functions())
+    for required in ("spai_build", "spai_update", "block_solve", "spai_ctx_create",
+                     "spai_assemble", "spai_pc_export", "spai_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(library):
+    missing = [n for n in declared_functions() if not hasattr(library, n)]
+    assert not missing, missing
+
+
+def test_binding_wraps_every_declared_symbol():
+    import paper_1809_06574_gb300 as sg
+    for n in declared_functions():
+        assert callable(getattr(sg, n, None)), n
+
+
+def test_product_never_imports_oracle():
+    for dirpath, _, files in os.walk(PKG):
+        for f in files:
+            if not f.endswith(".py"):
+                continue
+            tree = ast.parse(open(os.path.join(dirpath, f)).read())
+            for node in ast.walk(tree):
+                if isinstance(node, ast.Import):
+                    assert all(not a.name.startswith("oracle") for a in node.names), f
+                elif isinstance(node, ast.ImportFrom):
+                    assert not (node.module or "").startswith("oracle"), f
+
+
+def test_binding_fails_loudly_without_library(monkeypatch):
+    import paper_1809_06574_gb300 as sg
+    monkeypatch.setattr(sg, "_lib", None)
+    monkeypatch.setattr(sg, "LIB_PATH", "/nonexistent/libspai_gb300.so")
+    with pytest.raises(RuntimeError):
+        sg.lib()
+
+
+def test_affine_coefficients_match_oracle():
+    import oracle
+    import paper_1809_06574_gb300 as sg
+    for p, s in ((0.1, 1.0), (0.7, 0.5), (1.0, 2.0)):
+        assert sg.affine_coefficients(p, s) == pytest.approx(oracle.coefficients(p, s), rel=1e-15)

@@ -1,0 +1,59 @@
+"""Parity at the benchmark's full size (3D 64^3 7-point grid, n = 262,144, 8 RHS), through
+the same C ABI calls and launch configuration that bench.py times.
+
+The oracle is fast enough here to compare every index set and every SPAI / update
+entry, and to run one full block-GMRES(50) solve.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import column_rel_err_vec, context, export
+
+pytestmark = pytest.mark.gpu
+
+
+def test_fullsize_sweep_pieces():
+    import torch
+    import paper_1809_06574_gb300 as sg
+    w = synth.grid3d_7pt(side=64, nparams=20)
+    n = w.n
+    s_shift = 0.5
+    p1, p2 = w.params[0], w.params[7]
+    with context() as ctx:
+        d_terms = [tuple(torch.as_tensor(np.ascontiguousarray(a), device="cuda:0") for a in t)
+                   for t in w.terms]
+        aff = sg.spai_affine_create(ctx, [sg.csr(n, *t) for t in d_terms])
+        _, nnz, rp, ci = sg.spai_affine_pattern(aff)
+        assert nnz == 1810432
+        v1 = torch.empty(nnz, dtype=torch.float64, device="cuda:0")
+        v2 = torch.empty(nnz, dtype=torch.float64, device="cuda:0")
+        sg.spai_assemble(ctx, aff, sg.affine_coefficients(p1, s_shift), v1)
+        sg.spai_assemble(ctx, aff, sg.affine_coefficients(p2, s_shift), v2)
+        A1d, A2d = sg.csr(n, rp, ci, v1, nnz), sg.csr(n, rp, ci, v2, nnz)
+        pc1, _ = sg.spai_build(ctx, A1d, sg.PATTERN_A)
+        pc2, _ = sg.spai_update(ctx, pc1, A2d, sg.UPDATE_FIRST)
+        g1, g2 = export(ctx, pc1), export(ctx, pc2)
+        X = np.zeros((n, 8), order="F")
+        st, info, rel = sg.block_solve(ctx, A2d, pc2, 8, np.asfortranarray(w.B), n, X, n, 50, 1e-8, 50)
+        v2h = v2.cpu().numpy()
+        sg.spai_pc_destroy(pc2)
+        sg.spai_pc_destroy(pc1)
+        sg.spai_affine_destroy(aff)
+    A1 = oracle.assemble(w.terms, oracle.coefficients(p1, s_shift), n)
+    A2 = oracle.assemble(w.terms, oracle.coefficients(p2, s_shift), n)
+    assert np.array_equal(v2h, A2[2])
+    P1 = oracle.spai_build(A1, n)
+    Q2 = oracle.spai_update(P1, A2, n)
+    for g, ref in ((g1, P1), (g2, Q2)):
+        assert np.array_equal(g["Jptr"], ref.Jptr) and np.array_equal(g["Jind"], ref.Jind)
+        assert np.array_equal(g["Iptr"], ref.Iptr) and np.array_equal(g["Ilist"], ref.Ilist)
+        assert not g["status"].any()
+        assert column_rel_err_vec(ref.Jptr, g["val"], ref.val) <= 1e-10
+    assert info["converged"]
+    true_rel = np.linalg.norm(w.B - oracle.spmm(A2, X, n), axis=0) / np.linalg.norm(w.B, axis=0)
+    assert np.all(true_rel <= 1e-8)
+    Xo, io = oracle.block_gmres(oracle.csr_apply(A2, n), Q2.apply, w.B, 50, 1e-8, 50)
+    assert np.linalg.norm(X - Xo) <= 1e-6 * np.linalg.norm(Xo)
