@@ -62,15 +62,19 @@ __global__ void k_colnorm2(int32_t n, const double *__restrict__ W, double *__re
     if (g == 0) partial[(int64_t)blockIdx.x * S + c] = red[c];
 }
 
-// out[p] = sum over chunks of partial[chunk][p], p < count, chunks added in order
+// out[p] = sum over chunks of partial[chunk][p], p < count: one warp per p, lane l adds
+// chunks l, l+32, ... in order, then a fixed butterfly (deterministic)
 __global__ void k_reduce_chunks(int32_t count, int chunks, const double *__restrict__ partial,
                                 double *__restrict__ out)
 {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (p >= count) return;
     double acc = 0.0;
-    for (int c = 0; c < chunks; ++c) acc += partial[(int64_t)c * count + p];
-    out[p] = acc;
+    for (int c = lane; c < chunks; c += 32) acc += partial[(int64_t)c * count + p];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[p] = acc;
 }
 
 // ---------------------------------------------------------------------------------
@@ -175,9 +179,10 @@ __global__ void __launch_bounds__(kThreads) k_trsm_rows(int32_t n, const double 
                                                         double *__restrict__ out)
 {
     __shared__ double Rs[S * S];
-    __shared__ int32_t df[S];
+    __shared__ double rinv[S];  // 1 / R_bb, 0 for deflated columns
     for (int e = threadIdx.x; e < S * S; e += blockDim.x) Rs[e] = R[e];
-    if (threadIdx.x < S) df[threadIdx.x] = deflated[threadIdx.x];
+    if (threadIdx.x < S)
+        rinv[threadIdx.x] = deflated[threadIdx.x] ? 0.0 : 1.0 / R[threadIdx.x * S + threadIdx.x];
     __syncthreads();
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n) return;
@@ -187,7 +192,7 @@ __global__ void __launch_bounds__(kThreads) k_trsm_rows(int32_t n, const double 
         double acc = W[r * S + b];
 #pragma unroll
         for (int a = 0; a < b; ++a) acc = fma(-x[a], Rs[a * S + b], acc);
-        x[b] = df[b] ? 0.0 : acc / Rs[b * S + b];
+        x[b] = acc * rinv[b];
     }
 #pragma unroll
     for (int b = 0; b < S; ++b) out[r * S + b] = x[b];
@@ -457,17 +462,37 @@ int launch_colnorm2(cudaStream_t st, int32_t s, int32_t n, const double *W, doub
                     double *out, int chunks)
 {
     SPAI_DISPATCH_S(s, (k_colnorm2<S><<<chunks, kThreads, 0, st>>>(n, W, partial)));
-    k_reduce_chunks<<<1, 32, 0, st>>>(s, chunks, partial, out);
+    k_reduce_chunks<<<(s * 32 + 255) / 256, 256, 0, st>>>(s, chunks, partial, out);
     return check_launch(2);
 }
 
-int launch_block_dot(cudaStream_t st, int32_t s, int32_t n, int32_t nblk, const double *V,
-                     const double *W, double *partial, double *out, int chunks)
+// row chunks of the block Gram product: ~kDotBlocks CTAs in total whatever nblk is (the
+// grid is chunks x nblk), at least 512 rows per chunk
+constexpr int kDotBlocks = 2432;  // 16 per SM on 152 SMs
+
+int dot_chunks(int32_t n, int32_t nblk)
 {
+    int64_t c = (kDotBlocks + nblk - 1) / nblk;
+    int64_t cap = n / 512;
+    if (cap < 1) cap = 1;
+    if (c > cap) c = cap;
+    if (c < 1) c = 1;
+    return (int)c;
+}
+
+size_t dot_partial_elems(int32_t s, int32_t nblk_max)
+{
+    return (size_t)(kDotBlocks + nblk_max + 1) * s * s;
+}
+
+int launch_block_dot(cudaStream_t st, int32_t s, int32_t n, int32_t nblk, const double *V,
+                     const double *W, double *partial, double *out, int /*unused*/)
+{
+    const int chunks = dot_chunks(n, nblk);
     dim3 grid(chunks, nblk);
     SPAI_DISPATCH_S(s, (k_block_dot<S><<<grid, kThreads, 0, st>>>(n, V, W, partial, nblk)));
     const int count = nblk * s * s;
-    k_reduce_chunks<<<(count + 255) / 256, 256, 0, st>>>(count, chunks, partial, out);
+    k_reduce_chunks<<<(unsigned)(((int64_t)count * 32 + 255) / 256), 256, 0, st>>>(count, chunks, partial, out);
     return check_launch(2);
 }
 

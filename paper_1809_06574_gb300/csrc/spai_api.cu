@@ -402,8 +402,8 @@ spai_status sym_create(spai_ctx ctx, const spai_csr *A, int32_t kind, Sym **out)
         sym_release(s);
         return st;
     }
-    if (s->maxJ > 32 || s->maxI > 128) {
-        st = fail(ctx, SPAI_EINVAL, "column problem of %d x %d exceeds the 128 x 32 warp tile", s->maxI, s->maxJ);
+    if (!spai_columns_fit(s->maxI, s->maxJ)) {
+        st = fail(ctx, SPAI_EINVAL, "column problem of %d x %d exceeds the shared-memory tile", s->maxI, s->maxJ);
         dfree(ctx, temp);
         sym_release(s);
         return st;
@@ -909,7 +909,10 @@ size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks
     w.T0 = (double *)take(blk);
     w.T1 = (double *)take(blk);
     w.V = (double *)take(blk * (m + 1));
-    w.partial = (double *)take((size_t)chunks * (m + 1) * ss);
+    {
+        const size_t a = (size_t)chunks * s * 8, b = dot_partial_elems(s, m + 1) * 8;
+        w.partial = (double *)take(a > b ? a : b);
+    }
     w.H1 = (double *)take((m + 1) * ss);
     w.H2 = (double *)take((m + 1) * ss);
     w.Hup = (double *)take((m + 1) * ss);

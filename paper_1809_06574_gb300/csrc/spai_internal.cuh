@@ -93,12 +93,16 @@ struct ColumnProblem {
     int32_t *col_status;             // 0 ok, 1 singular
     int *d_err;
 };
-// Picks the tile by the largest |I_k|, |J_k|; returns 0 or -1 if no tile fits.
+// true if one column problem of maxI x maxJ fits the kernel's shared-memory tile
+bool spai_columns_fit(int32_t maxI, int32_t maxJ);
+// Picks the team size by the largest |I_k|, |J_k|; returns 0 or -1 if no tile fits.
 int launch_spai_columns(cudaStream_t st, const ColumnProblem &cp, int32_t maxI, int32_t maxJ);
 
 // ---------------------------------------------------------------------- k_krylov.cu
 struct KrylovWs;
 int krylov_chunks(int32_t n);
+// doubles needed for the partial sums of launch_block_dot with up to nblk_max blocks
+size_t dot_partial_elems(int32_t s, int32_t nblk_max);
 int launch_colnorm2(cudaStream_t st, int32_t s, int32_t n, const double *W, double *partial,
                     double *out, int chunks);
 int launch_block_dot(cudaStream_t st, int32_t s, int32_t n, int32_t nblk, const double *V,
