@@ -195,6 +195,21 @@ SPAI_API spai_status spai_spmm(spai_ctx ctx, const spai_csr *A, int32_t s, const
 SPAI_API spai_status spai_pc_apply(spai_ctx ctx, spai_pc pc, int32_t s, const double *X, int64_t ldx,
                           double *Y, int64_t ldy);
 
+/* Y = P X like spai_pc_apply, but without allocating any device memory.  The paper has
+ * no counterpart: this entry point serves callers that cannot allocate at the point of
+ * the apply -- an outside Krylov solver whose inner loop must not stall the device (a
+ * cudaMalloc or cudaFree can synchronise it), or a process whose device memory is
+ * already reserved by another allocator so that a new allocation would fail.
+ * The staging blocks live in one fixed device array of 64 MiB built into the library,
+ * which every device that loads the library holds until the process exits; n * s must
+ * be <= 2,097,152, else SPAI_EINVAL.  X and Y must be DEVICE memory on the context's
+ * device (current device).  The first call on each device looks up the array's address
+ * and caches it, so make that call before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU (other streams, other host threads) race.
+ * Asynchronous on the context's stream. */
+SPAI_API spai_status spai_pc_apply_noalloc(spai_ctx ctx, spai_pc pc, int32_t s, const double *X,
+                                           int64_t ldx, double *Y, int64_t ldy);
+
 /* ----------------------------------------------------------------------------------
  * Block Krylov solve, Sec. 2.1 (block methods solve all right-hand sides at once in
  * span{R0, A R0, A^2 R0, ...}) with right preconditioning (Sec. 2.2 footnote): block

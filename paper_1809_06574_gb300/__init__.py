@@ -99,6 +99,7 @@ def lib():
         "spai_pc_destroy": (i32, [vp]),
         "spai_spmm": (i32, [vp, P(spai_csr), i32, vp, i64, vp, i64]),
         "spai_pc_apply": (i32, [vp, vp, i32, vp, i64, vp, i64]),
+        "spai_pc_apply_noalloc": (i32, [vp, vp, i32, vp, i64, vp, i64]),
         "block_solve": (i32, [vp, P(spai_csr), vp, i32, vp, i64, vp, i64, P(spai_solve_opts),
                               P(spai_solve_info), P(dbl)]),
     }
@@ -285,6 +286,19 @@ def spai_spmm(ctx, A, s, X, ldx, Y, ldy):
 
 def spai_pc_apply(ctx, pc, s, X, ldx, Y, ldy):
     return _check(ctx, lib().spai_pc_apply(ctx, pc, int(s), _ptr(X), int(ldx), _ptr(Y), int(ldy)))
+
+
+def spai_pc_apply_noalloc(ctx, pc, s, X, ldx, Y, ldy):
+    """Y = P X without allocating device memory (fixed 64 MiB staging array in the library).
+
+    For callers that must not allocate where they apply the preconditioner, e.g. an outside
+    solver loop that must not stall the device, or a process whose device memory is held
+    by another allocator.  n * s <= 2,097,152; X and Y on the device.  The first call on a
+    device caches the array's address (do it before any stream capture); overlapping
+    calls share the array and race.
+    """
+    return _check(ctx, lib().spai_pc_apply_noalloc(ctx, pc, int(s), _ptr(X), int(ldx), _ptr(Y),
+                                                   int(ldy)))
 
 
 def block_solve(ctx, A, P, s, B, ldb, X, ldx, restart, tol, max_cycles, allow_notconv=False):

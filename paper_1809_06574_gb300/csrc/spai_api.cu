@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -1103,5 +1104,80 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
     }
     if (!conv) return fail(ctx, SPAI_ENOTCONV, "not converged after %d cycles: column %d relative residual %.3e",
                            cycles, worst, worst_rel);
+    return SPAI_OK;
+}
+
+// ===================================================================================
+// Preconditioner apply that allocates nothing.
+//
+// For callers that cannot allocate device memory at the point where they apply the
+// preconditioner: an outside Krylov solver whose inner loop must not stall the device
+// (cudaMalloc / cudaFree may synchronise), or a process whose device memory is already
+// reserved by another allocator, so that a new allocation would fail.  The row-major
+// staging blocks live in one file-scope device array of fixed size, allocated when the
+// library's module is loaded on a device and held by every device that loads it until
+// the process exits.  The first call on each device looks the array's address up (with
+// that device current) and caches it; make that first call before any stream capture.
+// Every call shares the array, so calls that overlap on the GPU (two streams, two host
+// threads) race; the staging blocks are fully overwritten by each call, nothing in them
+// needs to start at zero.
+// ===================================================================================
+namespace {
+
+constexpr size_t kNoAllocDoubles = (size_t)1 << 23;  // 64 MiB: four n x s blocks, n * s <= 2^21
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+double *g_noalloc_addr[kNoAllocMaxDevices] = {};
+std::mutex g_noalloc_mutex;
+
+}  // namespace
+
+extern "C" spai_status spai_pc_apply_noalloc(spai_ctx ctx, spai_pc pc, int32_t s, const double *X, int64_t ldx,
+                                             double *Y, int64_t ldy)
+{
+    if (!ctx || !pc) return fail(ctx, SPAI_EINVAL, "NULL argument");
+    if (!valid_s(s)) return fail(ctx, SPAI_EINVAL, "s must be 1, 2, 4, 8 or 16");
+    const int32_t n = pc->sym->n;
+    if (n == 0) return SPAI_OK;
+    if (ldx < n || ldy < n || !X || !Y) return fail(ctx, SPAI_EINVAL, "bad block arguments");
+    if (!is_device_ptr(X) || !is_device_ptr(Y)) return fail(ctx, SPAI_EINVAL, "X and Y must be device memory");
+    const size_t blk = (size_t)n * s;
+    if (4 * blk > kNoAllocDoubles)
+        return fail(ctx, SPAI_EINVAL, "n * s = %zu exceeds the no-allocation apply limit of %zu", blk,
+                    kNoAllocDoubles / 4);
+    int dev = -1;
+    CU(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != ctx->device || dev < 0 || dev >= kNoAllocMaxDevices)
+        return fail(ctx, SPAI_EINVAL, "current device %d is not the context's device %d", dev, ctx->device);
+    double *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_addr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) return cuda_fail(ctx, e, "cudaGetSymbolAddress(no-allocation scratch)");
+            g_noalloc_addr[dev] = (double *)p;
+        }
+        base = g_noalloc_addr[dev];
+    }
+    double *xr = base, *yr = base + blk, *t0 = yr + blk, *t1 = t0 + blk;
+    KL(launch_pack(ctx->stream, s, n, X, ldx, xr), "pack");
+    // factors from the root build to pc, as in the allocating apply, on the fixed staging
+    // blocks; the chain is walked through parent pointers (no container)
+    int len = 0;
+    for (spai_pc p = pc; p; p = p->parent) ++len;
+    const double *cur = xr;
+    double *bufs[2] = {t0, t1};
+    for (int i = len - 1; i >= 0; --i) {
+        spai_pc h = pc;
+        for (int hop = 0; hop < i; ++hop) h = h->parent;
+        double *dst = (i == 0) ? yr : bufs[(len - 1 - i) & 1];
+        KL(launch_spmm(ctx->stream, s, n, h->sym->p_rowptr, h->sym->p_colind, h->fval, cur, dst),
+           "preconditioner apply");
+        cur = dst;
+    }
+    KL(launch_unpack(ctx->stream, s, n, yr, Y, ldy), "unpack");
     return SPAI_OK;
 }
