@@ -216,11 +216,30 @@ SPAI_API spai_status spai_pc_apply_noalloc(spai_ctx ctx, spai_pc pc, int32_t s, 
  * GMRES(m) on A P X~ = B, X = X0 + P X~.
  * ---------------------------------------------------------------------------------- */
 
+/* How the block Gram products V^T W of the orthogonalisation are computed. */
+#define SPAI_ORTH_AUTO 0    /* tensor-core digits when s == 8 and j + 1 >= 4 blocks, else FP64 */
+#define SPAI_ORTH_FP64 1    /* FP64 fused multiply-adds on the CUDA cores */
+#define SPAI_ORTH_TENSOR 2  /* tensor-core digits whenever s == 8 */
+
 typedef struct {
     int32_t restart;     /* m: block Arnoldi steps per cycle, >= 1 */
     int32_t max_cycles;  /* restart cycles before SPAI_ENOTCONV, >= 1 */
     double tol;          /* stop when ||b_i - A x_i||_2 <= tol * ||b_i||_2 for every column */
+    int32_t orth;        /* SPAI_ORTH_* */
+    int32_t reserved;
 } spai_solve_opts;
+
+/* Block Gram product H_i = V_i^T W, i < nblk, of the block orthogonalisation (Sec. 2.1).
+ * V: nblk blocks of n x s, each row-major (s consecutive doubles per row) and back to
+ * back; W: n x s row-major; H: nblk x s x s, H[i][a][b] = sum_r V_i[r][a] W[r][b].  All
+ * DEVICE memory.  method SPAI_ORTH_FP64: FP64 on the CUDA cores; SPAI_ORTH_TENSOR (s == 8
+ * only): every value is cut into nine 6-bit fixed-point digits (V's entries must satisfy
+ * |v| < 2; W's columns are scaled by powers of two), digit products are summed exactly in
+ * FP32 on the tensor cores and combined in FP64 -- as accurate as FP64 arithmetic.
+ * Returns SPAI_EINVAL if a V entry is out of range, SPAI_ETIMEOUT if a bounded device
+ * wait gave up.  Synchronises. */
+SPAI_API spai_status spai_block_gram(spai_ctx ctx, int32_t s, int32_t n, int32_t nblk, const double *V,
+                                     const double *W, double *H, int32_t method);
 
 typedef struct {
     int32_t iterations;        /* block Arnoldi steps over all cycles */

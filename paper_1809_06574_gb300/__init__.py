@@ -51,7 +51,11 @@ class spai_csr(C.Structure):
 
 
 class spai_solve_opts(C.Structure):
-    _fields_ = [("restart", C.c_int32), ("max_cycles", C.c_int32), ("tol", C.c_double)]
+    _fields_ = [("restart", C.c_int32), ("max_cycles", C.c_int32), ("tol", C.c_double),
+                ("orth", C.c_int32), ("reserved", C.c_int32)]
+
+
+ORTH_AUTO, ORTH_FP64, ORTH_TENSOR = 0, 1, 2
 
 
 class spai_solve_info(C.Structure):
@@ -100,6 +104,7 @@ def lib():
         "spai_spmm": (i32, [vp, P(spai_csr), i32, vp, i64, vp, i64]),
         "spai_pc_apply": (i32, [vp, vp, i32, vp, i64, vp, i64]),
         "spai_pc_apply_noalloc": (i32, [vp, vp, i32, vp, i64, vp, i64]),
+        "spai_block_gram": (i32, [vp, i32, i32, i32, vp, vp, vp, i32]),
         "block_solve": (i32, [vp, P(spai_csr), vp, i32, vp, i64, vp, i64, P(spai_solve_opts),
                               P(spai_solve_info), P(dbl)]),
     }
@@ -301,9 +306,16 @@ def spai_pc_apply_noalloc(ctx, pc, s, X, ldx, Y, ldy):
                                                    int(ldy)))
 
 
-def block_solve(ctx, A, P, s, B, ldb, X, ldx, restart, tol, max_cycles, allow_notconv=False):
+def spai_block_gram(ctx, s, n, nblk, V, W, H, method=ORTH_FP64):
+    """H_i = V_i^T W for nblk row-major n x s blocks (device); method ORTH_FP64 / ORTH_TENSOR."""
+    return _check(ctx, lib().spai_block_gram(ctx, int(s), int(n), int(nblk), _ptr(V), _ptr(W),
+                                             _ptr(H), int(method)))
+
+
+def block_solve(ctx, A, P, s, B, ldb, X, ldx, restart, tol, max_cycles, allow_notconv=False,
+                orth=ORTH_AUTO):
     """Solve A X = B (column-major n x s; host or device).  Returns (status, info, rel)."""
-    opts = spai_solve_opts(int(restart), int(max_cycles), float(tol))
+    opts = spai_solve_opts(int(restart), int(max_cycles), float(tol), int(orth), 0)
     info = spai_solve_info()
     rel = (C.c_double * int(s))()
     st = lib().block_solve(ctx, C.byref(A), P, int(s), _ptr(B), int(ldb), _ptr(X), int(ldx),

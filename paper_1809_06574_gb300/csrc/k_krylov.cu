@@ -85,26 +85,52 @@ __global__ void __launch_bounds__(kThreads) k_block_dot(int32_t n, const double 
                                                         const double *__restrict__ W,
                                                         double *__restrict__ partial, int nblk)
 {
+    // thread = (row group g, row a of H_i, BQ consecutive columns b of H_i): BQ independent
+    // accumulators, rows unrolled by two for more loads in flight
     constexpr int P = S * S;
-    constexpr int RG = (kThreads / P) > 0 ? kThreads / P : 1;
-    __shared__ double red[kThreads];
+    constexpr int BQ = S < 4 ? S : 4;
+    constexpr int PQ = S * (S / BQ);
+    constexpr int RG = kThreads / PQ;
+    __shared__ double red[kThreads * BQ];
     const int i = blockIdx.y;
-    const int p = threadIdx.x % P, g = threadIdx.x / P;
-    const int a = p / S, b = p % S;
+    const int pq = threadIdx.x % PQ, g = threadIdx.x / PQ;
+    const int a = pq / (S / BQ), b0 = (pq % (S / BQ)) * BQ;
     const double *Vi = V + (int64_t)i * n * S;
     int64_t r0, r1;
     chunk_rows(n, blockIdx.x, gridDim.x, r0, r1);
-    double acc = 0.0;
-    if (g < RG)
-        for (int64_t r = r0 + g; r < r1; r += RG)
-            acc = fma(__ldg(Vi + r * S + a), __ldg(W + r * S + b), acc);
-    red[threadIdx.x] = acc;
+    double acc[BQ];
+#pragma unroll
+    for (int u = 0; u < BQ; ++u) acc[u] = 0.0;
+    int64_t r = r0 + g;
+    for (; r + RG < r1; r += 2 * RG) {
+        const double va0 = __ldg(Vi + r * S + a), va1 = __ldg(Vi + (r + RG) * S + a);
+        double w0[BQ], w1[BQ];
+#pragma unroll
+        for (int u = 0; u < BQ; ++u) {
+            w0[u] = __ldg(W + r * S + b0 + u);
+            w1[u] = __ldg(W + (r + RG) * S + b0 + u);
+        }
+#pragma unroll
+        for (int u = 0; u < BQ; ++u) acc[u] = fma(va1, w1[u], fma(va0, w0[u], acc[u]));
+    }
+    if (r < r1) {
+        const double va0 = __ldg(Vi + r * S + a);
+#pragma unroll
+        for (int u = 0; u < BQ; ++u) acc[u] = fma(va0, __ldg(W + r * S + b0 + u), acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < BQ; ++u) red[threadIdx.x * BQ + u] = acc[u];
     __syncthreads();
     for (int h = RG / 2; h > 0; h >>= 1) {
-        if (g < h) red[threadIdx.x] += red[threadIdx.x + h * P];
+        if (g < h)
+#pragma unroll
+            for (int u = 0; u < BQ; ++u) red[threadIdx.x * BQ + u] += red[(threadIdx.x + h * PQ) * BQ + u];
         __syncthreads();
     }
-    if (g == 0) partial[((int64_t)blockIdx.x * nblk + i) * P + p] = red[p];
+    if (g == 0)
+#pragma unroll
+        for (int u = 0; u < BQ; ++u)
+            partial[((int64_t)blockIdx.x * nblk + i) * P + a * S + b0 + u] = red[threadIdx.x * BQ + u];
 }
 
 // ---------------------------------------------------------------------------------
@@ -468,12 +494,12 @@ int launch_colnorm2(cudaStream_t st, int32_t s, int32_t n, const double *W, doub
 
 // row chunks of the block Gram product: ~kDotBlocks CTAs in total whatever nblk is (the
 // grid is chunks x nblk), at least 512 rows per chunk
-constexpr int kDotBlocks = 2432;  // 16 per SM on 152 SMs
+constexpr int kDotBlocks = 4864;  // 32 per SM on 152 SMs
 
 int dot_chunks(int32_t n, int32_t nblk)
 {
     int64_t c = (kDotBlocks + nblk - 1) / nblk;
-    int64_t cap = n / 512;
+    int64_t cap = n / 256;
     if (cap < 1) cap = 1;
     if (c > cap) c = cap;
     if (c < 1) c = 1;
@@ -483,6 +509,12 @@ int dot_chunks(int32_t n, int32_t nblk)
 size_t dot_partial_elems(int32_t s, int32_t nblk_max)
 {
     return (size_t)(kDotBlocks + nblk_max + 1) * s * s;
+}
+
+int launch_reduce_chunks(cudaStream_t st, int32_t count, int chunks, const double *partial, double *out)
+{
+    k_reduce_chunks<<<(unsigned)(((int64_t)count * 32 + 255) / 256), 256, 0, st>>>(count, chunks, partial, out);
+    return check_launch();
 }
 
 int launch_block_dot(cudaStream_t st, int32_t s, int32_t n, int32_t nblk, const double *V,

@@ -1,0 +1,469 @@
+// FP64-accurate block Gram product H = V_{0..j}^T W on the tensor cores (tcgen05).
+//
+// The block orthogonalisation of the Krylov basis (block classical Gram-Schmidt inside
+// block GMRES, Sec. 2.1) is the one dense contraction of the path: K = n rows, M = (j+1) s
+// basis columns, N = s right-hand sides.  GB300's FP64 pipe gives ~1.2 TFLOP/s, so it is
+// done here with integer digits on the BF16 tensor cores and FP64 only for the final sum:
+//
+//  * every value is written in fixed point with 54 bits below 2^1 (V's columns are unit
+//    vectors, so |v| <= 1; W's columns are scaled by a power of two 2^-e_b so that
+//    |w| < 1) and rounded to nearest: x = sign * sum_p d_p 2^(6(8-p)-53), d_p in [0, 63];
+//  * each digit is exact in BF16; a digit product is < 2^12 and a sum of at most 4096 of
+//    them is < 2^24, so FP32 accumulation in tensor memory stays exact over a CTA's rows;
+//  * digit pairs with p + q <= 9 are kept (53 products); the dropped pairs weigh < 2^-58
+//    relative, below FP64 rounding of the same dot products;
+//  * the exact FP32 sums are combined in FP64 with their powers of two.
+//
+// Digits are made once per basis block (when the block is created; it is reused by every
+// later Gram product) and once per W, by k_to_digits, and stored in global memory already
+// in the MMA's shared-memory layout: for 16-row sub-tile t, digit plane p and block i, one
+// 256-byte piece holding the block's 8 columns as 8 rows of two K-major core matrices
+// (8 rows x 16 bytes each).  In the Gram kernel one thread streams the pieces of up to 16
+// blocks into shared memory with cp.async.bulk (completion counted on an mbarrier), five
+// stages deep, while another thread issues, for every V digit plane p, one K=16 MMA
+// against all W digit planes q at once (N = 8 * #q, padded to 16) into tensor memory;
+// tcgen05.commit frees a stage for the next copy.  Every wait is bounded: on time-out the
+// kernel raises an error bit, waits (bounded) for its copies in flight, frees its tensor
+// memory and returns.
+#include <cstdint>
+
+#include "spai_internal.cuh"
+
+namespace spai {
+
+namespace {
+
+constexpr int kS = 8;              // right-hand-side block width handled here
+constexpr int kBlocksPerTile = 16; // basis blocks per CTA: MMA M = 128 columns
+constexpr int kM = kS * kBlocksPerTile;
+constexpr int kKT = 16;            // rows per sub-tile / digit piece (= MMA K)
+constexpr int kDig = 9;            // 6-bit digits per value
+constexpr int kPiece = kS * kKT * 2;             // 256 bytes: 8 columns x 16 rows of BF16
+constexpr int kLBO = 128;                        // next core matrix along K
+constexpr int kSBO = kPiece;                     // next 8-row group (next block / digit)
+constexpr int kThreads = 128;
+constexpr int kAPlane = kBlocksPerTile * kPiece;            // 4 KB
+constexpr int kABytes = kDig * kAPlane;                      // 36 KB
+constexpr int kBBytes = (kDig + 1) * kPiece;                 // 9 W digits + a zero row group
+constexpr int kStage = kABytes + kBBytes;                    // 39424
+constexpr int kStages = 5;
+constexpr int kSmemBar = kStages * kStage;                   // full[5], empty[5]
+constexpr int kSmemFlag = kSmemBar + 2 * kStages * 8;
+constexpr int kSmemTmem = kSmemFlag + 8;
+constexpr int kSmemTotal = kSmemTmem + 16;
+constexpr int kTmemCols = 512;
+constexpr unsigned kWaitLimit = 1u << 22;
+constexpr int kMaxRows = 4096;     // exactness bound of the FP32 sums
+static_assert(kSmemTotal <= 227 * 1024, "shared memory");
+
+// number of W digits q used with V digit p (q <= min(8, 9 - p)), MMA N (padded to 16)
+__host__ __device__ constexpr int nq(int p) { return (9 - p < 8 ? 9 - p : 8) + 1; }
+__host__ __device__ constexpr int nmma(int p) { return ((8 * nq(p) + 15) / 16) * 16; }
+__host__ __device__ constexpr int tcol(int p)
+{
+    int c = 0;
+    for (int i = 0; i < p; ++i) c += nmma(i);
+    return c;
+}
+static_assert(tcol(8) + nmma(8) <= kTmemCols, "tensor memory columns");
+static_assert(nmma(0) <= 8 * (kDig + 1), "B row groups");
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((kLBO >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((kSBO >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+    return d;                // base offset 0, no swizzle
+}
+
+// kind::f16, BF16 x BF16 -> FP32, both operands K-major
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P1;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P1;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+{
+    unsigned it = 0;
+    while (!mbar_try_wait(bar, parity))
+        if (++it >= kWaitLimit) return false;
+    return true;
+}
+
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// fixed-point magnitude round(|x| * 2^(53 - e)) from the IEEE bits (integer ops only);
+// returns false if |x| * 2^-e >= 2
+__device__ __forceinline__ bool fixed_mag(double x, int e, uint64_t &mag, uint32_t &neg)
+{
+    const uint64_t bits = (uint64_t)__double_as_longlong(x);
+    neg = (uint32_t)(bits >> 63);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    if (ex == 0) {  // zero or subnormal: below the fixed-point resolution
+        mag = 0;
+        return true;
+    }
+    const uint64_t mant = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+    const int shift = ex - 1022 - e;  // mag = mant * 2^shift
+    if (shift > 1) {
+        mag = 0;
+        return false;
+    }
+    if (shift >= 0) {
+        mag = mant << shift;
+    } else if (shift > -64) {
+        const int rs = -shift;
+        mag = (mant >> rs) + ((mant >> (rs - 1)) & 1ull);
+    } else {
+        mag = 0;
+    }
+    return true;
+}
+
+// BF16 bits of the signed digit (sign, d in [0, 63])
+__device__ __forceinline__ uint32_t digit_bf16(uint32_t d, uint32_t neg)
+{
+    const float f = __uint_as_float(0x4B000000u | d) - 8388608.0f;  // exact
+    return (__float_as_uint(f) >> 16) | (neg << 15);
+}
+
+// Digit pieces of one n x 8 row-major block X (scaled by 2^-exps[a] if exps != null):
+// piece (t, p) at dig + ((t * 9 + p) * ipad + iblk) * 256 bytes; rows >= n are zero.
+// Thread = (sub-tile t, column a, 8-row group ko).
+__global__ void k_to_digits(int32_t n, const double *__restrict__ X, const int32_t *__restrict__ exps,
+                            char *__restrict__ dig, int32_t ipad, int32_t iblk, int *err)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nt = ((int64_t)n + kKT - 1) / kKT;
+    if (g >= nt * kS * (kKT / 8)) return;
+    const int a = (int)(g % kS), ko = (int)((g / kS) % (kKT / 8));
+    const int64_t t = g / (kS * (kKT / 8));
+    const int e = exps ? exps[a] : 0;
+    uint64_t mag[8];
+    uint32_t neg[8];
+    bool bad = false;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int64_t r = t * kKT + ko * 8 + u;
+        const double x = (r < n) ? X[r * kS + a] : 0.0;
+        if (!fixed_mag(x, e, mag[u], neg[u])) bad = true;
+    }
+    if (bad) atomicOr(err, ERR_RANGE);
+#pragma unroll
+    for (int p = 0; p < kDig; ++p) {
+        const int sh = 6 * (8 - p);
+        uint32_t w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t lo = digit_bf16((uint32_t)(mag[2 * u] >> sh) & 63u, neg[2 * u]);
+            const uint32_t hi = digit_bf16((uint32_t)(mag[2 * u + 1] >> sh) & 63u, neg[2 * u + 1]);
+            w[u] = lo | (hi << 16);
+        }
+        char *dst = dig + ((t * kDig + p) * (int64_t)ipad + iblk) * kPiece + ko * kLBO + a * 16;
+        *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// Gram product from digit pieces.  grid = (row chunks, M tiles of 16 blocks); a chunk is
+// a whole number of 16-row sub-tiles, at most 4096 rows.  Thread 0 copies, thread 32
+// issues MMAs, warps 0..3 drain tensor memory.
+__global__ void __launch_bounds__(kThreads, 1)
+    k_block_dot_tc(int32_t n, int32_t nblk, int32_t subs_per_chunk, const char *__restrict__ vdig, int32_t ipad,
+                   const char *__restrict__ wdig, const int32_t *__restrict__ wexp, double *__restrict__ partial,
+                   int *err)
+{
+    extern __shared__ __align__(128) char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int chunk = blockIdx.x, mt = blockIdx.y;
+    const int64_t nt = ((int64_t)n + kKT - 1) / kKT;
+    const int64_t t0 = (int64_t)chunk * subs_per_chunk;
+    const int nsub = (int)min((int64_t)subs_per_chunk, nt - t0);
+    const int blk0 = mt * kBlocksPerTile;
+    const int nvb = min(kBlocksPerTile, nblk - blk0);  // valid blocks in this tile
+    const uint32_t full0 = smem_u32(smem + kSmemBar), empty0 = full0 + kStages * 8;
+    volatile int *flag = reinterpret_cast<volatile int *>(smem + kSmemFlag);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kSmemTmem);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8 * s));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty0 + 8 * s));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        *flag = 0;
+    }
+    // zero row group 9 of every B stage (MMAs with N = 80 read it; copies never write it)
+    for (int e = tid; e < kStages * (kPiece / 16); e += kThreads) {
+        const int s = e / (kPiece / 16), o = e % (kPiece / 16);
+        *reinterpret_cast<uint4 *>(smem + s * kStage + kABytes + kDig * kPiece + o * 16) = make_uint4(0, 0, 0, 0);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+    const bool work = nvb > 0 && nsub > 0;
+
+    if (tid == 0 && work) {  // ---- producer: bulk copies of sub-tile u into stage u % kStages
+        const uint32_t abytes = (uint32_t)nvb * kPiece;
+        const uint32_t stage_bytes = kDig * abytes + kDig * kPiece;
+        int issued = 0;
+        for (int u = 0; u < nsub; ++u) {
+            const int s = u % kStages;
+            if (u >= kStages && !mbar_wait_bounded(empty0 + 8 * s, (uint32_t)(((u - kStages) / kStages) & 1))) {
+                *flag = 1;
+                break;
+            }
+            if (*flag) break;
+            const uint32_t fb = full0 + 8 * s;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(stage_bytes)
+                         : "memory");
+            const int64_t t = t0 + u;
+            char *st = smem + s * kStage;
+#pragma unroll 1
+            for (int p = 0; p < kDig; ++p)
+                bulk_copy(smem_u32(st + p * kAPlane), vdig + ((t * kDig + p) * (int64_t)ipad + blk0) * kPiece,
+                          abytes, fb);
+            bulk_copy(smem_u32(st + kABytes), wdig + t * kDig * kPiece, kDig * kPiece, fb);
+            issued = u + 1;
+        }
+        // every copy issued must have landed before shared memory is released
+        for (int u = issued - kStages < 0 ? 0 : issued - kStages; u < issued; ++u)
+            if (!mbar_wait_bounded(full0 + 8 * (u % kStages), (uint32_t)((u / kStages) & 1))) *flag = 1;
+    } else if (tid == 32 && work) {  // ---- MMA issuer
+        int done = 0;
+        for (int u = 0; u < nsub; ++u) {
+            const int s = u % kStages;
+            if (!mbar_wait_bounded(full0 + 8 * s, (uint32_t)((u / kStages) & 1))) {
+                *flag = 1;
+                break;
+            }
+            if (*flag) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const char *st = smem + s * kStage;
+#pragma unroll
+            for (int p = 0; p < kDig; ++p) {
+                const uint64_t da = make_desc(smem_u32(st + p * kAPlane));
+                const uint64_t db = make_desc(smem_u32(st + kABytes));
+                mma_bf16(tmem + tcol(p), da, db, make_idesc(kM, nmma(p)), u > 0 ? 1u : 0u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             empty0 + 8 * s)
+                         : "memory");
+            done = u + 1;
+        }
+        // the last commit: all MMAs done before tensor memory is read
+        if (done > 0) {
+            const int u = done - 1;
+            if (!mbar_wait_bounded(empty0 + 8 * (u % kStages), (uint32_t)((u / kStages) & 1))) *flag = 1;
+        }
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const bool failed = *flag != 0;
+    if (failed && tid == 0) atomicOr(err, ERR_TIMEOUT);
+
+    // ---- drain: warp w owns tensor-memory lanes 32w..32w+31 = basis columns
+    if (!failed && work) {
+        const int m = warp * 32 + lane;
+        double h[kS];
+#pragma unroll
+        for (int b = 0; b < kS; ++b) h[b] = 0.0;
+#pragma unroll
+        for (int p = kDig - 1; p >= 0; --p) {
+#pragma unroll
+            for (int c0 = 0; c0 < nmma(p); c0 += 16) {
+                uint32_t v[16];
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(tcol(p) + c0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const int q = (c0 + c) >> 3, b = (c0 + c) & 7;
+                    if (q < nq(p)) {
+                        // weight 2^(-10 - 6(p+q)), an exact power of two
+                        const double wgt = __longlong_as_double((long long)(1023 - 10 - 6 * (p + q)) << 52);
+                        h[b] = fma((double)__uint_as_float(v[c]), wgt, h[b]);
+                    }
+                }
+            }
+        }
+        if (m < nvb * kS) {
+            const int gm = blk0 * kS + m;
+            double *dst = partial + ((int64_t)chunk * nblk + (gm >> 3)) * (kS * kS) + (gm & 7) * kS;
+#pragma unroll
+            for (int b = 0; b < kS; ++b) dst[b] = h[b] * __longlong_as_double((long long)(1023 + wexp[b]) << 52);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    }
+}
+
+// per-column max |W| (bit patterns of non-negative doubles order like the values):
+// warp and block reductions, then one atomicMax per column per block
+__global__ void k_col_maxabs(int32_t n, const double *__restrict__ W, unsigned long long *scratch)
+{
+    __shared__ unsigned long long red[kS][32];
+    unsigned long long m[kS];
+#pragma unroll
+    for (int b = 0; b < kS; ++b) m[b] = 0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const double2 *row = reinterpret_cast<const double2 *>(W + r * kS);
+#pragma unroll
+        for (int h = 0; h < kS / 2; ++h) {
+            const double2 x = row[h];
+            const unsigned long long b0 = (unsigned long long)__double_as_longlong(fabs(x.x));
+            const unsigned long long b1 = (unsigned long long)__double_as_longlong(fabs(x.y));
+            m[2 * h] = b0 > m[2 * h] ? b0 : m[2 * h];
+            m[2 * h + 1] = b1 > m[2 * h + 1] ? b1 : m[2 * h + 1];
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int b = 0; b < kS; ++b) {
+        unsigned long long v = m[b];
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, v, o);
+            v = y > v ? y : v;
+        }
+        if (lane == 0) red[b][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kS) {
+        unsigned long long v = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = red[threadIdx.x][w] > v ? red[threadIdx.x][w] : v;
+        if (v) atomicMax(scratch + threadIdx.x, v);
+    }
+}
+
+__global__ void k_maxexp_finish(unsigned long long *scratch, int32_t *exps)
+{
+    const int b = threadIdx.x;
+    if (b >= kS) return;
+    const unsigned long long bits = scratch[b];
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    exps[b] = ex == 0 ? 0 : ex - 1022;  // |w| < 2^(ex - 1022) for a normal number
+    scratch[b] = 0;                      // ready for the next use
+}
+
+}  // namespace
+
+bool block_dot_tc_supported(int32_t s) { return s == kS; }
+
+size_t tc_digit_bytes(int32_t n, int32_t nblocks)
+{
+    const int64_t nt = ((int64_t)n + kKT - 1) / kKT;
+    return (size_t)nt * kDig * (size_t)nblocks * kPiece;
+}
+
+size_t tc_scratch_bytes() { return 256; }
+
+int launch_to_digits(cudaStream_t st, int32_t n, const double *X, const int32_t *exps, void *dig, int32_t ipad,
+                     int32_t iblk, int *d_err)
+{
+    const int64_t nt = ((int64_t)n + kKT - 1) / kKT;
+    const int64_t work = nt * kS * (kKT / 8);
+    k_to_digits<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(n, X, exps, (char *)dig, ipad, iblk, d_err);
+    note_launches(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_w_digits(cudaStream_t st, int32_t n, const double *W, void *wdig, void *scratch, int *d_err)
+{
+    unsigned long long *mx = reinterpret_cast<unsigned long long *>(scratch);
+    int32_t *exps = reinterpret_cast<int32_t *>(mx + kS);
+    int g = (int)(((int64_t)n + 255) / 256);
+    if (g > 2 * 152) g = 2 * 152;
+    k_col_maxabs<<<g, 256, 0, st>>>(n, W, mx);
+    k_maxexp_finish<<<1, 32, 0, st>>>(mx, exps);
+    note_launches(2);
+    if (cudaGetLastError() != cudaSuccess) return -1;
+    return launch_to_digits(st, n, W, exps, wdig, 1, 0, d_err);
+}
+
+int tc_subs_per_chunk(int32_t n, int32_t nblk)
+{
+    const int mtiles = (nblk + kBlocksPerTile - 1) / kBlocksPerTile;
+    const int64_t nt = ((int64_t)n + kKT - 1) / kKT;
+    int64_t want = (nt * mtiles + 152 - 1) / 152;  // ~1 CTA per SM in total
+    if (want < 8) want = 8;
+    if (want > kMaxRows / kKT) want = kMaxRows / kKT;
+    return (int)want;
+}
+
+size_t tc_partial_elems(int32_t n, int32_t nblk)
+{
+    const int64_t nt = ((int64_t)n + kKT - 1) / kKT;
+    return (size_t)((nt + 7) / 8) * nblk * kS * kS;  // chunks hold at least 8 sub-tiles
+}
+
+int launch_block_dot_tc(cudaStream_t st, int32_t n, int32_t nblk, const void *vdig, int32_t ipad, const void *wdig,
+                        const void *scratch, double *partial, double *out, int *d_err)
+{
+    if (n <= 0 || nblk <= 0) return -1;
+    if (cudaFuncSetAttribute(k_block_dot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal) != cudaSuccess)
+        return -1;
+    const int32_t *exps = reinterpret_cast<const int32_t *>(reinterpret_cast<const unsigned long long *>(scratch) + kS);
+    const int spc = tc_subs_per_chunk(n, nblk);
+    const int64_t nt = ((int64_t)n + kKT - 1) / kKT;
+    const int chunks = (int)((nt + spc - 1) / spc);
+    const int mtiles = (nblk + kBlocksPerTile - 1) / kBlocksPerTile;
+    dim3 grid(chunks, mtiles);
+    k_block_dot_tc<<<grid, kThreads, kSmemTotal, st>>>(n, nblk, spc, (const char *)vdig, ipad, (const char *)wdig,
+                                                         exps, partial, d_err);
+    note_launches(1);
+    if (cudaGetLastError() != cudaSuccess) return -1;
+    return launch_reduce_chunks(st, nblk * kS * kS, chunks, partial, out);
+}
+
+}  // namespace spai

@@ -890,6 +890,8 @@ struct SolveWs {
     double *Bw, *Xw, *W, *Z, *T0, *T1, *V;
     double *partial, *H1, *H2, *Hup, *G1, *R1, *R2, *Rn, *ref2, *nrm2, *thresh, *Hcol, *Qs, *Rtri, *G, *Y, *est;
     int32_t *defl1, *defl2, *flag;
+    void *tc_scratch;  // column exponents of the tensor-core Gram product (zeroed per solve)
+    void *vdig, *wdig; // digit pieces of the basis blocks and of W (tensor-core Gram product)
 };
 
 size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks)
@@ -912,7 +914,9 @@ size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks
     w.V = (double *)take(blk * (m + 1));
     {
         const size_t a = (size_t)chunks * s * 8, b = dot_partial_elems(s, m + 1) * 8;
-        w.partial = (double *)take(a > b ? a : b);
+        const size_t c = tc_partial_elems(n, m + 1) * 8;  // tensor-core row chunks
+        size_t mx = a > b ? a : b;
+        w.partial = (double *)take(mx > c ? mx : c);
     }
     w.H1 = (double *)take((m + 1) * ss);
     w.H2 = (double *)take((m + 1) * ss);
@@ -933,6 +937,10 @@ size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks
     w.defl1 = (int32_t *)take(s * 4);
     w.defl2 = (int32_t *)take(s * 4);
     w.flag = (int32_t *)take(64);
+    w.tc_scratch = take(tc_scratch_bytes());
+    const bool digits = block_dot_tc_supported(s);
+    w.vdig = take(digits ? tc_digit_bytes(n, m + 1) : 16);
+    w.wdig = take(digits ? tc_digit_bytes(n, 1) : 16);
     return off;
 }
 
@@ -983,6 +991,17 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
     carve(w, base, n, s, m, chunks);
     cudaStream_t cs = ctx->stream;
     const bool b_dev = is_device_ptr(B), x_dev = is_device_ptr(X);
+    if (opts->orth < SPAI_ORTH_AUTO || opts->orth > SPAI_ORTH_TENSOR)
+        return fail(ctx, SPAI_EINVAL, "unknown orthogonalisation method %d", opts->orth);
+    CU(cudaMemsetAsync(w.tc_scratch, 0, tc_scratch_bytes(), cs), "clear scratch");
+    // tensor-core Gram products need every basis block as digit pieces
+    const bool use_digits = block_dot_tc_supported(s) && opts->orth != SPAI_ORTH_FP64;
+    auto make_digits = [&](int blk) -> spai_status {
+        if (!use_digits) return SPAI_OK;
+        PKL("to_digits", 0.0, 26.0 * n * s,
+            launch_to_digits(cs, n, w.V + (size_t)blk * n * s, nullptr, w.vdig, m + 1, blk, ctx->d_err), "digits");
+        return SPAI_OK;
+    };
 
     // inputs -> row-major device blocks (T0 stages host data column-major)
     if (b_dev) {
@@ -1029,6 +1048,7 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
         ++cycles;
         // V_0 S_0 = R (ref2 holds the residual norms^2)
         if ((st = cholqr2(ctx, w, n, s, chunks, w.W, w.V, w.Rn, w.ref2))) return st;
+        if ((st = make_digits(0))) return st;
         PKL("small_dense", 0.0, 0.0, launch_set_rhs(cs, s, m, w.Rn, w.G), "rhs");
         int J = 0;
         for (int j = 0; j < m; ++j) {
@@ -1043,17 +1063,37 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
             PKL("colnorm2", 2.0 * nsd, 8.0 * nsd, launch_colnorm2(cs, s, n, w.W, w.partial, w.ref2, chunks), "norms");
             // two passes of block classical Gram-Schmidt against V_0..V_j
             const double nb = j + 1;
-            PKL("block_dot", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
-                launch_block_dot(cs, s, n, j + 1, w.V, w.W, w.partial, w.H1, chunks), "H1");
+            const bool tc = use_digits && (opts->orth == SPAI_ORTH_TENSOR || j + 1 >= 2);
+            if (tc) {
+                PKL("w_digits", 0.0, 16.0 * nsd + 18.0 * nsd,
+                    launch_w_digits(cs, n, w.W, w.wdig, w.tc_scratch, ctx->d_err), "W digits");
+                PKL("block_dot_tc", 2.0 * nsd * s * nb, 18.0 * nsd * (nb + 1),
+                    launch_block_dot_tc(cs, n, j + 1, w.vdig, m + 1, w.wdig, w.tc_scratch, w.partial, w.H1,
+                                        ctx->d_err),
+                    "H1");
+            } else {
+                PKL("block_dot", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
+                    launch_block_dot(cs, s, n, j + 1, w.V, w.W, w.partial, w.H1, chunks), "H1");
+            }
             PKL("block_update", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 2),
                 launch_block_update(cs, s, n, j + 1, w.V, w.H1, w.W, w.W, -1.0), "W -= V H1");
-            PKL("block_dot", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
-                launch_block_dot(cs, s, n, j + 1, w.V, w.W, w.partial, w.H2, chunks), "H2");
+            if (tc) {
+                PKL("w_digits", 0.0, 16.0 * nsd + 18.0 * nsd,
+                    launch_w_digits(cs, n, w.W, w.wdig, w.tc_scratch, ctx->d_err), "W digits");
+                PKL("block_dot_tc", 2.0 * nsd * s * nb, 18.0 * nsd * (nb + 1),
+                    launch_block_dot_tc(cs, n, j + 1, w.vdig, m + 1, w.wdig, w.tc_scratch, w.partial, w.H2,
+                                        ctx->d_err),
+                    "H2");
+            } else {
+                PKL("block_dot", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
+                    launch_block_dot(cs, s, n, j + 1, w.V, w.W, w.partial, w.H2, chunks), "H2");
+            }
             PKL("block_update", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 2),
                 launch_block_update(cs, s, n, j + 1, w.V, w.H2, w.W, w.W, -1.0), "W -= V H2");
             PKL("small_dense", 0.0, 0.0, launch_add_small(cs, (j + 1) * s * s, w.H1, w.H2, w.Hup), "H1 + H2");
             double *Vn = w.V + (size_t)(j + 1) * blk_elems;
             if ((st = cholqr2(ctx, w, n, s, chunks, w.W, Vn, w.Rn, w.ref2))) return st;
+            if (j + 1 < m && (st = make_digits(j + 1))) return st;
             PKL("small_dense", 0.0, 0.0, launch_copy_hcol(cs, s, j, (m + 1) * s, w.Hup, w.Rn, w.Hcol), "H column");
             PKL("arnoldi_ls", 16.0 * s * s * s * (j + 1), 0.0,
                 launch_arnoldi_ls(cs, s, j, m, w.Hcol, w.Qs, w.Rtri, w.G, w.thresh, w.est, w.flag), "least squares");
@@ -1085,6 +1125,12 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
         CU(cudaMemcpy2DAsync(X, (size_t)ldx * 8, w.T0, (size_t)n * 8, (size_t)n * 8, s, cudaMemcpyDeviceToHost, cs), "copy X");
     }
     CU(cudaStreamSynchronize(cs), "sync");
+    {
+        int h_err = 0;
+        if ((st = read_err(ctx, &h_err))) return st;
+        if (h_err & ERR_TIMEOUT) return fail(ctx, SPAI_ETIMEOUT, "a bounded wait in the tensor-core Gram product gave up");
+        if (h_err & ERR_RANGE) return fail(ctx, SPAI_EINVAL, "basis entry out of the digit range (|v| >= 2)");
+    }
     int worst = 0;
     double worst_rel = -1.0;
     bool conv = true;
@@ -1104,6 +1150,48 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
     }
     if (!conv) return fail(ctx, SPAI_ENOTCONV, "not converged after %d cycles: column %d relative residual %.3e",
                            cycles, worst, worst_rel);
+    return SPAI_OK;
+}
+
+extern "C" spai_status spai_block_gram(spai_ctx ctx, int32_t s, int32_t n, int32_t nblk, const double *V,
+                                       const double *W, double *H, int32_t method)
+{
+    if (!ctx) return SPAI_EINVAL;
+    if (!valid_s(s) || n < 1 || nblk < 1 || !V || !W || !H) return fail(ctx, SPAI_EINVAL, "bad arguments");
+    if (!is_device_ptr(V) || !is_device_ptr(W) || !is_device_ptr(H))
+        return fail(ctx, SPAI_EINVAL, "V, W and H must be device memory");
+    if (method != SPAI_ORTH_FP64 && method != SPAI_ORTH_TENSOR) return fail(ctx, SPAI_EINVAL, "unknown method");
+    if (method == SPAI_ORTH_TENSOR && !block_dot_tc_supported(s))
+        return fail(ctx, SPAI_EINVAL, "the tensor-core Gram product needs s == 8");
+    if (((uintptr_t)V | (uintptr_t)W | (uintptr_t)H) & 15)
+        return fail(ctx, SPAI_EINVAL, "V, W and H must be 16-byte aligned");
+    auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t a = dot_partial_elems(s, nblk) * 8;
+    const bool tcm = method == SPAI_ORTH_TENSOR;
+    const size_t c = tcm ? tc_partial_elems(n, nblk) * 8 : 0;
+    const size_t scratch = r256(tc_scratch_bytes());
+    const size_t pbytes = r256(a > c ? a : c);
+    const size_t vd = tcm ? r256(tc_digit_bytes(n, nblk)) : 0, wd = tcm ? r256(tc_digit_bytes(n, 1)) : 0;
+    void *ws = nullptr;
+    spai_status st = temp_blocks(ctx, scratch + pbytes + vd + wd, &ws);
+    if (st) return st;
+    char *base = (char *)ws;
+    double *partial = (double *)(base + scratch);
+    void *vdig = base + scratch + pbytes, *wdig = base + scratch + pbytes + vd;
+    const int chunks = krylov_chunks(n);
+    if (!tcm) {
+        KL(launch_block_dot(ctx->stream, s, n, nblk, V, W, partial, H, chunks), "gram");
+    } else {
+        CU(cudaMemsetAsync(ws, 0, scratch, ctx->stream), "clear scratch");
+        for (int i = 0; i < nblk; ++i)
+            KL(launch_to_digits(ctx->stream, n, V + (size_t)i * n * s, nullptr, vdig, nblk, i, ctx->d_err), "digits");
+        KL(launch_w_digits(ctx->stream, n, W, wdig, ws, ctx->d_err), "W digits");
+        KL(launch_block_dot_tc(ctx->stream, n, nblk, vdig, nblk, wdig, ws, partial, H, ctx->d_err), "tensor gram");
+    }
+    int h = 0;
+    if ((st = read_err(ctx, &h))) return st;
+    if (h & ERR_TIMEOUT) return fail(ctx, SPAI_ETIMEOUT, "a bounded wait in the tensor-core Gram product gave up");
+    if (h & ERR_RANGE) return fail(ctx, SPAI_EINVAL, "a V entry is out of the digit range (|v| >= 2)");
     return SPAI_OK;
 }
 

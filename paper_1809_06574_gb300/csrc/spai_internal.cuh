@@ -22,6 +22,8 @@ enum : int {
     ERR_OVERFLOW = 1 << 2,    // a prefix sum exceeds int32
     ERR_TOO_WIDE = 1 << 3,    // a column problem exceeds the kernel's tile
     ERR_PATTERN = 1 << 4,     // values do not fit the expected pattern
+    ERR_TIMEOUT = 1 << 5,     // a bounded device-side wait gave up
+    ERR_RANGE = 1 << 6,       // a value outside the fixed-point range of the digit Gram product
 };
 
 struct TermPtrs {
@@ -128,6 +130,24 @@ int launch_residual(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr
                     const int32_t *colind, const double *val, const double *X, const double *B,
                     double *R);
 int launch_zero(cudaStream_t st, int64_t count, double *dst);
+// out[p] = sum over chunks of partial[chunk * count + p] (deterministic)
+int launch_reduce_chunks(cudaStream_t st, int32_t count, int chunks, const double *partial, double *out);
+
+// ---------------------------------------------------------------------- k_ozaki.cu
+// H = V_{0..nblk-1}^T W on the tensor cores with FP64-accurate digit products (s == 8).
+// Basis blocks are turned into digit pieces once (launch_to_digits, block iblk of an
+// array of ipad blocks, tc_digit_bytes(n, ipad) bytes); W per product (launch_w_digits,
+// tc_digit_bytes(n, 1) bytes, column exponents in scratch: tc_scratch_bytes(), zeroed
+// once before first use).  partial needs tc_partial_elems(n, nblk) doubles.
+bool block_dot_tc_supported(int32_t s);
+size_t tc_digit_bytes(int32_t n, int32_t nblocks);
+size_t tc_scratch_bytes();
+size_t tc_partial_elems(int32_t n, int32_t nblk);
+int launch_to_digits(cudaStream_t st, int32_t n, const double *X, const int32_t *exps, void *dig, int32_t ipad,
+                     int32_t iblk, int *d_err);
+int launch_w_digits(cudaStream_t st, int32_t n, const double *W, void *wdig, void *scratch, int *d_err);
+int launch_block_dot_tc(cudaStream_t st, int32_t n, int32_t nblk, const void *vdig, int32_t ipad, const void *wdig,
+                        const void *scratch, double *partial, double *out, int *d_err);
 // FP64 FMA throughput probe: blocks x threads x 8 chains x iters FMAs
 int launch_fp64_probe(cudaStream_t st, int blocks, int threads, int iters, double *sink);
 

@@ -1,0 +1,105 @@
+"""Block Gram product H = V^T W of the orthogonalisation: tensor-core digit method vs FP64.
+
+The digit method (nine 6-bit fixed-point digits, exact FP32 sums on the tensor cores, FP64
+recombination) must be as accurate as FP64 arithmetic: both are compared with a sum in
+extended precision on the host, per column relative to ||w_b|| ||v_a|| (= ||w_b||).
+Solves with either method must give the same iterates up to rounding.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import context, dev_csr
+
+pytestmark = pytest.mark.gpu
+
+
+def _blocks(n, nblk, seed):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, nblk * 8)))   # orthonormal basis columns
+    W = rng.standard_normal((n, 8)) * np.array([1e3, 1.0, 1e-5, 3.0, 1e8, 0.5, 2.0, 0.0])
+    W[: n // 3, 6] *= 1e-9                                      # mixed magnitudes in one column
+    return Q, W
+
+
+def _to_dev_blocks(Q, n, nblk):
+    import torch
+    # block i = rows x 8 row-major: element (r, a) of block i at (i * n + r) * 8 + a
+    Vb = np.ascontiguousarray(Q.reshape(n, nblk, 8).transpose(1, 0, 2))
+    return torch.as_tensor(Vb, device="cuda:0")
+
+
+def _ref(Q, W):
+    return (Q.astype(np.longdouble).T @ W.astype(np.longdouble)).astype(np.float64)
+
+
+@pytest.mark.parametrize("n,nblk", [(1000, 1), (4999, 4), (20000, 17), (70001, 51)])
+def test_tensor_gram_as_accurate_as_fp64(n, nblk):
+    import torch
+    import paper_1809_06574_gb300 as sg
+    Q, W = _blocks(n, nblk, seed=n + nblk)
+    # extended-precision reference on a subset of basis columns (first and last block)
+    cols = np.r_[0:8, nblk * 8 - 8:nblk * 8]
+    ref = _ref(Q[:, cols], W)
+    wn = np.linalg.norm(W, axis=0)
+    scale = np.where(wn > 0, wn, 1.0)
+    with context() as ctx:
+        Vd = _to_dev_blocks(Q, n, nblk)
+        Wd = torch.as_tensor(np.ascontiguousarray(W), device="cuda:0")
+        outs = {}
+        for method in (sg.ORTH_FP64, sg.ORTH_TENSOR):
+            Hd = torch.full((nblk, 8, 8), np.nan, dtype=torch.float64, device="cuda:0")
+            sg.spai_block_gram(ctx, 8, n, nblk, Vd, Wd, Hd, method)
+            outs[method] = Hd.cpu().numpy().reshape(nblk * 8, 8)
+    e64 = np.max(np.abs(outs[sg.ORTH_FP64][cols] - ref) / scale)
+    etc = np.max(np.abs(outs[sg.ORTH_TENSOR][cols] - ref) / scale)
+    assert np.all(outs[sg.ORTH_TENSOR][:, 7] == 0.0)              # zero column stays exact
+    assert e64 <= 1e-14 and etc <= 1e-14, (e64, etc)
+    assert etc <= 4 * max(e64, 1e-16), (e64, etc)
+    # and the two methods agree on every entry
+    assert np.max(np.abs(outs[sg.ORTH_TENSOR] - outs[sg.ORTH_FP64]) / scale) <= 2e-14
+
+
+def test_tensor_gram_rejects_out_of_range_basis():
+    import torch
+    import paper_1809_06574_gb300 as sg
+    n = 2048
+    Q, W = _blocks(n, 4, seed=1)
+    Q[5, 3] = 3.0                                               # |v| >= 2 is outside the digits
+    with context() as ctx:
+        Vd = _to_dev_blocks(Q, n, 4)
+        Wd = torch.as_tensor(np.ascontiguousarray(W), device="cuda:0")
+        Hd = torch.zeros((4, 8, 8), dtype=torch.float64, device="cuda:0")
+        with pytest.raises(sg.SpaiError) as ei:
+            sg.spai_block_gram(ctx, 8, n, 4, Vd, Wd, Hd, sg.ORTH_TENSOR)
+        assert ei.value.status == sg.SPAI_EINVAL
+
+
+def test_solve_with_tensor_orthogonalisation_matches_fp64():
+    import paper_1809_06574_gb300 as sg
+    w = synth.grid3d_7pt(side=24, nparams=2, nrhs=8)
+    n = w.n
+    A = oracle.assemble(w.terms, oracle.coefficients(w.params[0], 0.5), n)
+    P = oracle.spai_build(A, n)
+    Xo, io = oracle.block_gmres(oracle.csr_apply(A, n), P.apply, w.B, 50, 1e-8, 20)
+    res = {}
+    with context() as ctx:
+        Ad = dev_csr(A, n)
+        pc, _ = sg.spai_build(ctx, Ad)
+        for orth in (sg.ORTH_FP64, sg.ORTH_TENSOR, sg.ORTH_AUTO):
+            X = np.zeros((n, 8), order="F")
+            st, info, rel = sg.block_solve(ctx, Ad, pc, 8, np.asfortranarray(w.B), n, X, n, 50, 1e-8, 20,
+                                           orth=orth)
+            res[orth] = (X, info)
+        sg.spai_pc_destroy(pc)
+    for orth, (X, info) in res.items():
+        assert info["converged"]
+        true_rel = np.linalg.norm(w.B - oracle.spmm(A, X, n), axis=0) / np.linalg.norm(w.B, axis=0)
+        assert np.all(true_rel <= 1e-8)
+        assert np.linalg.norm(X - Xo) <= 1e-6 * np.linalg.norm(Xo)
+    X64, i64 = res[sg.ORTH_FP64]
+    Xtc, itc = res[sg.ORTH_TENSOR]
+    assert itc["iterations"] == i64["iterations"]
+    assert np.linalg.norm(Xtc - X64) <= 1e-10 * np.linalg.norm(X64)
