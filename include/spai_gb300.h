@@ -241,6 +241,13 @@ typedef struct {
 SPAI_API spai_status spai_block_gram(spai_ctx ctx, int32_t s, int32_t n, int32_t nblk, const double *V,
                                      const double *W, double *H, int32_t method);
 
+/* Block update of the orthogonalisation (Sec. 2.1): W := W + sign * sum_i V_i H_i, with V
+ * and W laid out as for spai_block_gram and H as its output (nblk x s x s).  DEVICE
+ * memory, in place.  method SPAI_ORTH_TENSOR (s == 8) uses the same digit scheme with the
+ * basis rows as the MMA's M dimension.  Synchronises. */
+SPAI_API spai_status spai_block_update(spai_ctx ctx, int32_t s, int32_t n, int32_t nblk, const double *V,
+                                       const double *H, double *W, double sign, int32_t method);
+
 typedef struct {
     int32_t iterations;        /* block Arnoldi steps over all cycles */
     int32_t cycles;            /* restart cycles run */

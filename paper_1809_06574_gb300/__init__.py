@@ -105,6 +105,7 @@ def lib():
         "spai_pc_apply": (i32, [vp, vp, i32, vp, i64, vp, i64]),
         "spai_pc_apply_noalloc": (i32, [vp, vp, i32, vp, i64, vp, i64]),
         "spai_block_gram": (i32, [vp, i32, i32, i32, vp, vp, vp, i32]),
+        "spai_block_update": (i32, [vp, i32, i32, i32, vp, vp, vp, dbl, i32]),
         "block_solve": (i32, [vp, P(spai_csr), vp, i32, vp, i64, vp, i64, P(spai_solve_opts),
                               P(spai_solve_info), P(dbl)]),
     }
@@ -310,6 +311,12 @@ def spai_block_gram(ctx, s, n, nblk, V, W, H, method=ORTH_FP64):
     """H_i = V_i^T W for nblk row-major n x s blocks (device); method ORTH_FP64 / ORTH_TENSOR."""
     return _check(ctx, lib().spai_block_gram(ctx, int(s), int(n), int(nblk), _ptr(V), _ptr(W),
                                              _ptr(H), int(method)))
+
+
+def spai_block_update(ctx, s, n, nblk, V, H, W, sign=-1.0, method=ORTH_FP64):
+    """W := W + sign * sum_i V_i H_i in place (device, row-major blocks)."""
+    return _check(ctx, lib().spai_block_update(ctx, int(s), int(n), int(nblk), _ptr(V), _ptr(H), _ptr(W),
+                                               float(sign), int(method)))
 
 
 def block_solve(ctx, A, P, s, B, ldb, X, ldx, restart, tol, max_cycles, allow_notconv=False,

@@ -166,8 +166,11 @@ __device__ __forceinline__ uint32_t digit_bf16(uint32_t d, uint32_t neg)
 // Digit pieces of one n x 8 row-major block X (scaled by 2^-exps[a] if exps != null):
 // piece (t, p) at dig + ((t * 9 + p) * ipad + iblk) * 256 bytes; rows >= n are zero.
 // Thread = (sub-tile t, column a, 8-row group ko).
+// If udig != null the same pieces are also written row-tile-major for the update kernel:
+// piece (t, p) at udig + ((p * nt8 + t / 8) * ipad + iblk) * 2048 + (t % 8) * 256.
 __global__ void k_to_digits(int32_t n, const double *__restrict__ X, const int32_t *__restrict__ exps,
-                            char *__restrict__ dig, int32_t ipad, int32_t iblk, int *err)
+                            char *__restrict__ dig, int32_t ipad, int32_t iblk, int *err,
+                            char *__restrict__ udig, int64_t nt8)
 {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nt = ((int64_t)n + kKT - 1) / kKT;
@@ -195,8 +198,14 @@ __global__ void k_to_digits(int32_t n, const double *__restrict__ X, const int32
             const uint32_t hi = digit_bf16((uint32_t)(mag[2 * u + 1] >> sh) & 63u, neg[2 * u + 1]);
             w[u] = lo | (hi << 16);
         }
+        const uint4 val = make_uint4(w[0], w[1], w[2], w[3]);
         char *dst = dig + ((t * kDig + p) * (int64_t)ipad + iblk) * kPiece + ko * kLBO + a * 16;
-        *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4 *>(dst) = val;
+        if (udig) {
+            char *u = udig + ((p * nt8 + t / 8) * (int64_t)ipad + iblk) * (8 * kPiece) + (t % 8) * kPiece + ko * kLBO +
+                      a * 16;
+            *reinterpret_cast<uint4 *>(u) = val;
+        }
     }
 }
 
@@ -396,6 +405,254 @@ __global__ void k_maxexp_finish(unsigned long long *scratch, int32_t *exps)
     scratch[b] = 0;                      // ready for the next use
 }
 
+// ---------------------------------------------------------------------------------
+// Block update out = base - sign' * V_{0..nblk-1} H on the tensor cores (W -= V H of the
+// Gram-Schmidt passes, U = V Y of the solution update), same digit scheme.  The MMA's M
+// dimension is 128 rows of V, K runs over basis columns (16 = two blocks per MMA), N over
+// H's digit planes x 8 columns.  V's pieces are read MN-major (8 basis columns x 8
+// contiguous rows per core matrix) from their row-tile-major copy; H's digits are built
+// per call by k_h_digits as K-major pieces, one 2304-byte group per 16 basis columns.
+// ---------------------------------------------------------------------------------
+constexpr int kUStageA = kDig * 2 * (8 * kPiece);          // 9 planes x 2 blocks x 2 KB
+constexpr int kUStage = kUStageA + kBBytes;                  // + 9 H digit pieces + zero group
+constexpr int kUSmemBar = kStages * kUStage;
+constexpr int kUSmemFlag = kUSmemBar + 2 * kStages * 8;
+constexpr int kUSmemTmem = kUSmemFlag + 8;
+constexpr int kUSmemTotal = kUSmemTmem + 16;
+static_assert(kUSmemTotal <= 227 * 1024, "shared memory");
+constexpr int kULBO = 8 * kPiece;  // MN-major: next 8 basis columns (next block)
+constexpr int kUSBO = 128;         // MN-major: next 8 rows
+
+__device__ __forceinline__ uint64_t make_desc_mn(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((kULBO >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((kUSBO >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// A (V) MN-major, B (H digits) K-major
+__host__ __device__ constexpr uint32_t make_idesc_amn(int M, int N) { return make_idesc(M, N) | (1u << 15); }
+
+// exact FP32 integer (|x| < 2^24) to int
+__device__ __forceinline__ int f2i_exact(uint32_t bits) { return __float2int_rz(__uint_as_float(bits)); }
+
+// Digits of H (nblk*8 basis columns x 8, H[c * 8 + b]) scaled per column b: piece (kappa, q)
+// at hdig + (kappa * 9 + q) * 256 holds columns 16 kappa .. 16 kappa + 15 (zero beyond
+// nblk * 8); hexp[b] = column exponent.  One CTA.
+__global__ void k_h_digits(int32_t nblk, const double *__restrict__ H, char *__restrict__ hdig,
+                           int32_t *__restrict__ hexp, int *err)
+{
+    __shared__ int32_t ex_s[kS];
+    const int ncol = nblk * kS;
+    if (threadIdx.x < kS) {
+        unsigned long long m = 0;
+        for (int c = 0; c < ncol; ++c) {
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(H[c * kS + threadIdx.x]));
+            m = bits > m ? bits : m;
+        }
+        const int ex = (int)((m >> 52) & 0x7FF);
+        ex_s[threadIdx.x] = ex == 0 ? 0 : ex - 1022;
+        hexp[threadIdx.x] = ex_s[threadIdx.x];
+    }
+    __syncthreads();
+    const int nk = (nblk + 1) / 2;
+    for (int item = threadIdx.x; item < nk * kS * 2; item += blockDim.x) {
+        const int b = item % kS, ko = (item / kS) % 2, kappa = item / (2 * kS);
+        uint64_t mag[8];
+        uint32_t neg[8];
+        bool bad = false;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int c = kappa * 16 + ko * 8 + u;
+            const double x = c < ncol ? H[c * kS + b] : 0.0;
+            if (!fixed_mag(x, ex_s[b], mag[u], neg[u])) bad = true;
+        }
+        if (bad) atomicOr(err, ERR_RANGE);
+#pragma unroll
+        for (int q = 0; q < kDig; ++q) {
+            const int sh = 6 * (8 - q);
+            uint32_t w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t lo = digit_bf16((uint32_t)(mag[2 * u] >> sh) & 63u, neg[2 * u]);
+                const uint32_t hi = digit_bf16((uint32_t)(mag[2 * u + 1] >> sh) & 63u, neg[2 * u + 1]);
+                w[u] = lo | (hi << 16);
+            }
+            *reinterpret_cast<uint4 *>(hdig + (kappa * kDig + q) * kPiece + ko * kLBO + b * 16) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+// Sum of the digit products of tensor-memory row `lane` for output column b:
+// sum_{p,q} D_p[q*8+b] 2^(-10-6(p+q)).  Products of equal weight are added as integers
+// (|D| < 2^24), three weights are merged in 64-bit integers, four FP64 terms remain.
+__device__ __forceinline__ void combine_row(const int S[10][kS], double out[kS])
+{
+#pragma unroll
+    for (int b = 0; b < kS; ++b) {
+        const long long g0 = ((long long)S[0][b] << 12) + ((long long)S[1][b] << 6) + S[2][b];
+        const long long g1 = ((long long)S[3][b] << 12) + ((long long)S[4][b] << 6) + S[5][b];
+        const long long g2 = ((long long)S[6][b] << 12) + ((long long)S[7][b] << 6) + S[8][b];
+        const long long g3 = S[9][b];
+        double v = (double)g3 * 0x1p-64;
+        v = fma((double)g2, 0x1p-58, v);
+        v = fma((double)g1, 0x1p-40, v);
+        v = fma((double)g0, 0x1p-22, v);
+        out[b] = v;
+    }
+}
+
+// read all digit-product columns of this thread's tensor-memory row, grouped by p + q
+__device__ __forceinline__ void drain_row(uint32_t tmem, int warp, int S[10][kS])
+{
+#pragma unroll
+    for (int s = 0; s < 10; ++s)
+#pragma unroll
+        for (int b = 0; b < kS; ++b) S[s][b] = 0;
+#pragma unroll
+    for (int p = 0; p < kDig; ++p) {
+#pragma unroll
+        for (int c0 = 0; c0 < nmma(p); c0 += 16) {
+            uint32_t v[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(tcol(p) + c0);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const int q = (c0 + c) >> 3, b = (c0 + c) & 7;
+                if (q < nq(p)) S[p + q][b] += f2i_exact(v[c]);
+            }
+        }
+    }
+}
+
+// out[r][b] = base[r][b] + sign * (V H)[r][b] (base == null: out = sign * V H).
+// grid = ceil(n / 128); thread 0 copies, thread 32 issues MMAs, all threads drain.
+__global__ void __launch_bounds__(kThreads, 1)
+    k_block_update_tc(int32_t n, int32_t nblk, const char *__restrict__ udig, int32_t ipad, int64_t nt8,
+                      const char *__restrict__ hdig, const int32_t *__restrict__ hexp, const char *__restrict__ zeros,
+                      const double *base, double *out, double sign, int *err)
+{
+    extern __shared__ __align__(128) char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t tile = blockIdx.x;  // rows 128 tile .. 128 tile + 127 = pieces 8 tile .. 8 tile + 7
+    const int nk = (nblk + 1) / 2;    // K steps of 16 basis columns
+    const uint32_t full0 = smem_u32(smem + kUSmemBar), empty0 = full0 + kStages * 8;
+    volatile int *flag = reinterpret_cast<volatile int *>(smem + kUSmemFlag);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kUSmemTmem);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8 * s));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty0 + 8 * s));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        *flag = 0;
+    }
+    for (int e = tid; e < kStages * (kPiece / 16); e += kThreads) {
+        const int s = e / (kPiece / 16), o = e % (kPiece / 16);
+        *reinterpret_cast<uint4 *>(smem + s * kUStage + kUStageA + kDig * kPiece + o * 16) = make_uint4(0, 0, 0, 0);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+
+    if (tid == 0) {  // ---- producer
+        int issued = 0;
+        for (int kk = 0; kk < nk; ++kk) {
+            const int s = kk % kStages;
+            if (kk >= kStages && !mbar_wait_bounded(empty0 + 8 * s, (uint32_t)(((kk - kStages) / kStages) & 1))) {
+                *flag = 1;
+                break;
+            }
+            if (*flag) break;
+            const int nbk = min(2, nblk - 2 * kk);
+            const uint32_t fb = full0 + 8 * s;
+            const uint32_t bytes = kDig * 2 * (8 * kPiece) + kDig * kPiece;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(bytes) : "memory");
+            char *st = smem + s * kUStage;
+#pragma unroll 1
+            for (int p = 0; p < kDig; ++p) {
+                const char *src = udig + ((p * nt8 + tile) * (int64_t)ipad + 2 * kk) * (8 * kPiece);
+                bulk_copy(smem_u32(st + p * 2 * (8 * kPiece)), src, (uint32_t)nbk * 8 * kPiece, fb);
+                if (nbk == 1)  // second block slot of an odd tail: zeros (its H digits are zero too)
+                    bulk_copy(smem_u32(st + p * 2 * (8 * kPiece) + 8 * kPiece), zeros, 8 * kPiece, fb);
+            }
+            bulk_copy(smem_u32(st + kUStageA), hdig + (int64_t)kk * kDig * kPiece, kDig * kPiece, fb);
+            issued = kk + 1;
+        }
+        for (int kk = issued - kStages < 0 ? 0 : issued - kStages; kk < issued; ++kk)
+            if (!mbar_wait_bounded(full0 + 8 * (kk % kStages), (uint32_t)((kk / kStages) & 1))) *flag = 1;
+    } else if (tid == 32) {  // ---- MMA issuer
+        int done = 0;
+        for (int kk = 0; kk < nk; ++kk) {
+            const int s = kk % kStages;
+            if (!mbar_wait_bounded(full0 + 8 * s, (uint32_t)((kk / kStages) & 1))) {
+                *flag = 1;
+                break;
+            }
+            if (*flag) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const char *st = smem + s * kUStage;
+#pragma unroll
+            for (int p = 0; p < kDig; ++p) {
+                const uint64_t da = make_desc_mn(smem_u32(st + p * 2 * (8 * kPiece)));
+                const uint64_t db = make_desc(smem_u32(st + kUStageA));
+                mma_bf16(tmem + tcol(p), da, db, make_idesc_amn(kM, nmma(p)), kk > 0 ? 1u : 0u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             empty0 + 8 * s)
+                         : "memory");
+            done = kk + 1;
+        }
+        if (done > 0) {
+            const int kk = done - 1;
+            if (!mbar_wait_bounded(empty0 + 8 * (kk % kStages), (uint32_t)((kk / kStages) & 1))) *flag = 1;
+        }
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const bool failed = *flag != 0;
+    if (failed && tid == 0) atomicOr(err, ERR_TIMEOUT);
+
+    if (!failed && nk > 0) {  // ---- drain: thread = row
+        int S[10][kS];
+        drain_row(tmem, warp, S);
+        double v[kS];
+        combine_row(S, v);
+        const int64_t r = tile * 128 + warp * 32 + lane;
+        if (r < n) {
+#pragma unroll
+            for (int b = 0; b < kS; ++b) {
+                const double vh = v[b] * __longlong_as_double((long long)(1023 + hexp[b]) << 52);
+                out[r * kS + b] = base ? fma(sign, vh, base[r * kS + b]) : sign * vh;
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    }
+}
+
 }  // namespace
 
 bool block_dot_tc_supported(int32_t s) { return s == kS; }
@@ -409,11 +666,12 @@ size_t tc_digit_bytes(int32_t n, int32_t nblocks)
 size_t tc_scratch_bytes() { return 256; }
 
 int launch_to_digits(cudaStream_t st, int32_t n, const double *X, const int32_t *exps, void *dig, int32_t ipad,
-                     int32_t iblk, int *d_err)
+                     int32_t iblk, int *d_err, void *udig)
 {
     const int64_t nt = ((int64_t)n + kKT - 1) / kKT;
     const int64_t work = nt * kS * (kKT / 8);
-    k_to_digits<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(n, X, exps, (char *)dig, ipad, iblk, d_err);
+    k_to_digits<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(n, X, exps, (char *)dig, ipad, iblk, d_err,
+                                                                  (char *)udig, (nt + 7) / 8);
     note_launches(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -428,7 +686,7 @@ int launch_w_digits(cudaStream_t st, int32_t n, const double *W, void *wdig, voi
     k_maxexp_finish<<<1, 32, 0, st>>>(mx, exps);
     note_launches(2);
     if (cudaGetLastError() != cudaSuccess) return -1;
-    return launch_to_digits(st, n, W, exps, wdig, 1, 0, d_err);
+    return launch_to_digits(st, n, W, exps, wdig, 1, 0, d_err, nullptr);
 }
 
 int tc_subs_per_chunk(int32_t n, int32_t nblk)
@@ -439,6 +697,37 @@ int tc_subs_per_chunk(int32_t n, int32_t nblk)
     if (want < 8) want = 8;
     if (want > kMaxRows / kKT) want = kMaxRows / kKT;
     return (int)want;
+}
+
+size_t tc_udig_bytes(int32_t n, int32_t nblocks)
+{
+    const int64_t nt = ((int64_t)n + kKT - 1) / kKT;
+    return (size_t)((nt + 7) / 8) * kDig * (size_t)nblocks * (8 * kPiece);
+}
+
+size_t tc_hdig_bytes(int32_t nblk) { return (size_t)((nblk + 1) / 2) * kDig * kPiece; }
+
+// the whole shared memory of an SM: every descriptor reading stays inside the allocation
+constexpr int kUSmemAlloc = 227 * 1024;
+static_assert(kUSmemAlloc >= kUSmemTotal, "update kernel shared memory");
+
+int launch_block_update_tc(cudaStream_t st, int32_t n, int32_t nblk, const void *udig, int32_t ipad,
+                           const double *H, void *hdig, int32_t *hexp, const void *zeros, const double *base,
+                           double *out, double sign, int *d_err)
+{
+    if (n <= 0 || nblk <= 0) return -1;
+    k_h_digits<<<1, 256, 0, st>>>(nblk, H, (char *)hdig, hexp, d_err);
+    note_launches(1);
+    if (cudaFuncSetAttribute(k_block_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kUSmemAlloc) !=
+        cudaSuccess)
+        return -1;
+    const int64_t nt = ((int64_t)n + kKT - 1) / kKT;
+    const int64_t tiles = (nt + 7) / 8;
+    k_block_update_tc<<<(unsigned)tiles, kThreads, kUSmemAlloc, st>>>(n, nblk, (const char *)udig, ipad, (nt + 7) / 8,
+                                                                       (const char *)hdig, hexp, (const char *)zeros,
+                                                                       base, out, sign, d_err);
+    note_launches(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 size_t tc_partial_elems(int32_t n, int32_t nblk)

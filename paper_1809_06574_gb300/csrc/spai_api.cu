@@ -892,6 +892,8 @@ struct SolveWs {
     int32_t *defl1, *defl2, *flag;
     void *tc_scratch;  // column exponents of the tensor-core Gram product (zeroed per solve)
     void *vdig, *wdig; // digit pieces of the basis blocks and of W (tensor-core Gram product)
+    void *udig, *hdig, *zeros;  // row-tile-major basis digits, H digits, 2 KB of zeros
+    int32_t *hexp;              // column exponents of H
 };
 
 size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks)
@@ -941,6 +943,10 @@ size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks
     const bool digits = block_dot_tc_supported(s);
     w.vdig = take(digits ? tc_digit_bytes(n, m + 1) : 16);
     w.wdig = take(digits ? tc_digit_bytes(n, 1) : 16);
+    w.udig = take(digits ? tc_udig_bytes(n, m + 1) : 16);
+    w.hdig = take(digits ? tc_hdig_bytes(m + 1) : 16);
+    w.zeros = take(2048);
+    w.hexp = (int32_t *)take(64);
     return off;
 }
 
@@ -994,12 +1000,28 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
     if (opts->orth < SPAI_ORTH_AUTO || opts->orth > SPAI_ORTH_TENSOR)
         return fail(ctx, SPAI_EINVAL, "unknown orthogonalisation method %d", opts->orth);
     CU(cudaMemsetAsync(w.tc_scratch, 0, tc_scratch_bytes(), cs), "clear scratch");
+    CU(cudaMemsetAsync(w.zeros, 0, 2048, cs), "clear zeros");
     // tensor-core Gram products need every basis block as digit pieces
     const bool use_digits = block_dot_tc_supported(s) && opts->orth != SPAI_ORTH_FP64;
     auto make_digits = [&](int blk) -> spai_status {
         if (!use_digits) return SPAI_OK;
         PKL("to_digits", 0.0, 26.0 * n * s,
-            launch_to_digits(cs, n, w.V + (size_t)blk * n * s, nullptr, w.vdig, m + 1, blk, ctx->d_err), "digits");
+            launch_to_digits(cs, n, w.V + (size_t)blk * n * s, nullptr, w.vdig, m + 1, blk, ctx->d_err, w.udig),
+            "digits");
+        return SPAI_OK;
+    };
+    // out = base + sign * V_{0..nb-1} H: tensor-core digits when available, else FP64
+    auto vupdate = [&](int nb, const double *H, const double *basep, double *out, double sign) -> spai_status {
+        const double f = 2.0 * n * s * s * nb;
+        if (use_digits && (opts->orth == SPAI_ORTH_TENSOR || nb >= 2)) {
+            PKL("block_update_tc", f, 18.0 * n * s * nb + 16.0 * n * s,
+                launch_block_update_tc(cs, n, nb, w.udig, m + 1, H, w.hdig, w.hexp, w.zeros, basep, out, sign,
+                                       ctx->d_err),
+                "block update");
+        } else {
+            PKL("block_update", f, 8.0 * n * s * (nb + 2),
+                launch_block_update(cs, s, n, nb, w.V, H, basep, out, sign), "block update");
+        }
         return SPAI_OK;
     };
 
@@ -1075,8 +1097,7 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
                 PKL("block_dot", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
                     launch_block_dot(cs, s, n, j + 1, w.V, w.W, w.partial, w.H1, chunks), "H1");
             }
-            PKL("block_update", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 2),
-                launch_block_update(cs, s, n, j + 1, w.V, w.H1, w.W, w.W, -1.0), "W -= V H1");
+            if ((st = vupdate(j + 1, w.H1, w.W, w.W, -1.0))) return st;
             if (tc) {
                 PKL("w_digits", 0.0, 16.0 * nsd + 18.0 * nsd,
                     launch_w_digits(cs, n, w.W, w.wdig, w.tc_scratch, ctx->d_err), "W digits");
@@ -1088,8 +1109,7 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
                 PKL("block_dot", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
                     launch_block_dot(cs, s, n, j + 1, w.V, w.W, w.partial, w.H2, chunks), "H2");
             }
-            PKL("block_update", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 2),
-                launch_block_update(cs, s, n, j + 1, w.V, w.H2, w.W, w.W, -1.0), "W -= V H2");
+            if ((st = vupdate(j + 1, w.H2, w.W, w.W, -1.0))) return st;
             PKL("small_dense", 0.0, 0.0, launch_add_small(cs, (j + 1) * s * s, w.H1, w.H2, w.Hup), "H1 + H2");
             double *Vn = w.V + (size_t)(j + 1) * blk_elems;
             if ((st = cholqr2(ctx, w, n, s, chunks, w.W, Vn, w.Rn, w.ref2))) return st;
@@ -1107,8 +1127,7 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
         // X += P (V Y)
         PKL("backsolve", (double)J * s * J * s * s, 0.0, launch_backsolve(cs, s, J, (m + 1) * s, w.Rtri, w.G, w.Y),
             "back substitution");
-        PKL("block_update", 2.0 * nsd * s * J, 8.0 * nsd * (J + 1), launch_block_update(cs, s, n, J, w.V, w.Y, nullptr, w.W, 1.0),
-            "V Y");
+        if ((st = vupdate(J, w.Y, nullptr, w.W, 1.0))) return st;
         const double *U = w.W;
         if (P) {
             if ((st = apply_rm(ctx, P, s, w.W, w.Z, w.T0, w.T1))) return st;
@@ -1191,6 +1210,45 @@ extern "C" spai_status spai_block_gram(spai_ctx ctx, int32_t s, int32_t n, int32
     int h = 0;
     if ((st = read_err(ctx, &h))) return st;
     if (h & ERR_TIMEOUT) return fail(ctx, SPAI_ETIMEOUT, "a bounded wait in the tensor-core Gram product gave up");
+    if (h & ERR_RANGE) return fail(ctx, SPAI_EINVAL, "a V entry is out of the digit range (|v| >= 2)");
+    return SPAI_OK;
+}
+
+extern "C" spai_status spai_block_update(spai_ctx ctx, int32_t s, int32_t n, int32_t nblk, const double *V,
+                                         const double *H, double *W, double sign, int32_t method)
+{
+    if (!ctx) return SPAI_EINVAL;
+    if (!valid_s(s) || n < 1 || nblk < 1 || !V || !W || !H) return fail(ctx, SPAI_EINVAL, "bad arguments");
+    if (!is_device_ptr(V) || !is_device_ptr(W) || !is_device_ptr(H))
+        return fail(ctx, SPAI_EINVAL, "V, W and H must be device memory");
+    if (method != SPAI_ORTH_FP64 && method != SPAI_ORTH_TENSOR) return fail(ctx, SPAI_EINVAL, "unknown method");
+    if (method == SPAI_ORTH_TENSOR && !block_dot_tc_supported(s))
+        return fail(ctx, SPAI_EINVAL, "the tensor-core block update needs s == 8");
+    if (((uintptr_t)V | (uintptr_t)W | (uintptr_t)H) & 15)
+        return fail(ctx, SPAI_EINVAL, "V, W and H must be 16-byte aligned");
+    if (method == SPAI_ORTH_FP64) {
+        KL(launch_block_update(ctx->stream, s, n, nblk, V, H, W, W, sign), "block update");
+    } else {
+        auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+        const size_t vd = r256(tc_digit_bytes(n, nblk)), ud = r256(tc_udig_bytes(n, nblk));
+        const size_t hd = r256(tc_hdig_bytes(nblk));
+        void *ws = nullptr;
+        spai_status st = temp_blocks(ctx, vd + ud + hd + 2048 + 256, &ws);
+        if (st) return st;
+        char *base = (char *)ws;
+        void *vdig = base, *udig = base + vd, *hdig = base + vd + ud, *zeros = base + vd + ud + hd;
+        int32_t *hexp = (int32_t *)(base + vd + ud + hd + 2048);
+        CU(cudaMemsetAsync(zeros, 0, 2048, ctx->stream), "clear zeros");
+        for (int i = 0; i < nblk; ++i)
+            KL(launch_to_digits(ctx->stream, n, V + (size_t)i * n * s, nullptr, vdig, nblk, i, ctx->d_err, udig),
+               "digits");
+        KL(launch_block_update_tc(ctx->stream, n, nblk, udig, nblk, H, hdig, hexp, zeros, W, W, sign, ctx->d_err),
+           "tensor block update");
+    }
+    int h = 0;
+    spai_status st = read_err(ctx, &h);
+    if (st) return st;
+    if (h & ERR_TIMEOUT) return fail(ctx, SPAI_ETIMEOUT, "a bounded wait in the tensor-core block update gave up");
     if (h & ERR_RANGE) return fail(ctx, SPAI_EINVAL, "a V entry is out of the digit range (|v| >= 2)");
     return SPAI_OK;
 }

@@ -143,8 +143,16 @@ bool block_dot_tc_supported(int32_t s);
 size_t tc_digit_bytes(int32_t n, int32_t nblocks);
 size_t tc_scratch_bytes();
 size_t tc_partial_elems(int32_t n, int32_t nblk);
+// (udig != null: also the row-tile-major copy read by the update kernel, tc_udig_bytes)
 int launch_to_digits(cudaStream_t st, int32_t n, const double *X, const int32_t *exps, void *dig, int32_t ipad,
-                     int32_t iblk, int *d_err);
+                     int32_t iblk, int *d_err, void *udig = nullptr);
+// out = base + sign * V_{0..nblk-1} H on the tensor cores (base may be null): H is
+// nblk*8 x 8 ([i][a][b]); hdig needs tc_hdig_bytes(nblk), hexp 8 ints, zeros 2048 zero bytes
+size_t tc_udig_bytes(int32_t n, int32_t nblocks);
+size_t tc_hdig_bytes(int32_t nblk);
+int launch_block_update_tc(cudaStream_t st, int32_t n, int32_t nblk, const void *udig, int32_t ipad,
+                           const double *H, void *hdig, int32_t *hexp, const void *zeros, const double *base,
+                           double *out, double sign, int *d_err);
 int launch_w_digits(cudaStream_t st, int32_t n, const double *W, void *wdig, void *scratch, int *d_err);
 int launch_block_dot_tc(cudaStream_t st, int32_t n, int32_t nblk, const void *vdig, int32_t ipad, const void *wdig,
                         const void *scratch, double *partial, double *out, int *d_err);

@@ -62,6 +62,33 @@ def test_tensor_gram_as_accurate_as_fp64(n, nblk):
     assert np.max(np.abs(outs[sg.ORTH_TENSOR] - outs[sg.ORTH_FP64]) / scale) <= 2e-14
 
 
+@pytest.mark.parametrize("n,nblk,sign", [(1000, 1, -1.0), (4999, 3, -1.0), (20000, 16, 1.0), (70001, 51, -1.0)])
+def test_tensor_block_update_as_accurate_as_fp64(n, nblk, sign):
+    import torch
+    import paper_1809_06574_gb300 as sg
+    Q, W = _blocks(n, nblk, seed=7 * n + nblk)
+    rng = np.random.default_rng(n)
+    H = rng.standard_normal((nblk * 8, 8)) * np.array([1.0, 1e-3, 1e4, 0.0, 1e-9, 2.0, 5.0, 1.0])
+    rows = np.r_[0:257, n - 300:n]  # extended-precision reference on a subset of rows
+    ref = (W[rows].astype(np.longdouble) +
+           sign * (Q[rows].astype(np.longdouble) @ H.astype(np.longdouble))).astype(np.float64)
+    scale = np.linalg.norm(H, axis=0) + np.abs(W[rows]).max(axis=0)
+    scale = np.where(scale > 0, scale, 1.0)
+    outs = {}
+    with context() as ctx:
+        Vd = _to_dev_blocks(Q, n, nblk)
+        Hd = torch.as_tensor(np.ascontiguousarray(H), device="cuda:0")
+        for method in (sg.ORTH_FP64, sg.ORTH_TENSOR):
+            Wd = torch.as_tensor(np.ascontiguousarray(W), device="cuda:0")
+            sg.spai_block_update(ctx, 8, n, nblk, Vd, Hd, Wd, sign, method)
+            outs[method] = Wd.cpu().numpy()
+    e64 = np.max(np.abs(outs[sg.ORTH_FP64][rows] - ref) / scale)
+    etc = np.max(np.abs(outs[sg.ORTH_TENSOR][rows] - ref) / scale)
+    assert e64 <= 1e-14 and etc <= 1e-14, (e64, etc)
+    assert etc <= 4 * max(e64, 1e-16), (e64, etc)
+    assert np.max(np.abs(outs[sg.ORTH_TENSOR] - outs[sg.ORTH_FP64]) / scale) <= 2e-14
+
+
 def test_tensor_gram_rejects_out_of_range_basis():
     import torch
     import paper_1809_06574_gb300 as sg
