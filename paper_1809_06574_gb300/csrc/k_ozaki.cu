@@ -536,18 +536,74 @@ __device__ __forceinline__ void drain_row(uint32_t tmem, int warp, int S[10][kS]
     }
 }
 
-// out[r][b] = base[r][b] + sign * (V H)[r][b] (base == null: out = sign * V H).
-// grid = ceil(n / 128); thread 0 copies, thread 32 issues MMAs, all threads drain.
-__global__ void __launch_bounds__(kThreads, 1)
+
+// Value of row `lane`'s digit products for output column b times 2^e_b, from the
+// equal-weight integer sums S[p+q][b] (|S| < 2^28): two 64-bit integers carry
+// S_0..S_4 (weights 2^-10..2^-34 -> hi * 2^-34) and S_5..S_9 (2^-40..2^-64 -> lo * 2^-64),
+// each converted once; the power-of-two scale is added to the exponent fields.
+__device__ __forceinline__ double combine_scaled(const int S[10][kS], int b, int e)
+{
+    long long hi = S[0][b];
+#pragma unroll
+    for (int s = 1; s < 5; ++s) hi = (hi << 6) + S[s][b];
+    long long lo = S[5][b];
+#pragma unroll
+    for (int s = 6; s < 10; ++s) lo = (lo << 6) + S[s][b];
+    // |hi|, |lo| < 2^53: exact conversions; 2^e is a normal double for the exponents of
+    // finite nonzero columns (e >= -1021), and a zero column has e = 0
+    const double v = fma((double)hi, 0x1p-34, (double)lo * 0x1p-64);
+    return v * __longlong_as_double((long long)(1023 + e) << 52);
+}
+
+// Update drain: |D| < 2^22 here (K <= 1024 columns), so a D value's integer is read by
+// adding 1.5 * 2^23 in FP32 (exact) instead of a conversion instruction.
+__device__ __forceinline__ void drain_row_small(uint32_t tmem, int quarter, int S[10][kS])
+{
+#pragma unroll
+    for (int s = 0; s < 10; ++s)
+#pragma unroll
+        for (int b = 0; b < kS; ++b) S[s][b] = 0;
+#pragma unroll
+    for (int p = 0; p < kDig; ++p) {
+#pragma unroll
+        for (int c0 = 0; c0 < nmma(p); c0 += 16) {
+            uint32_t v[16];
+            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tcol(p) + c0);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const int q = (c0 + c) >> 3, b = (c0 + c) & 7;
+                if (q < nq(p))
+                    S[p + q][b] += __float_as_int(__uint_as_float(v[c]) + 12582912.0f) - 0x4B400000;
+            }
+        }
+    }
+}
+
+constexpr int kUThreads = 192;  // warp 0 copies, warp 1 issues MMAs, warps 2..5 drain
+
+// Persistent block update: out[r][b] = base[r][b] + sign * (V H)[r][b] (base == null:
+// sign * V H).  One CTA per SM walks 128-row tiles; the copy warp streams stages ahead
+// across tiles, the MMA warp waits for the drain warps to hand tensor memory back before
+// starting the next tile.
+__global__ void __launch_bounds__(kUThreads, 1)
     k_block_update_tc(int32_t n, int32_t nblk, const char *__restrict__ udig, int32_t ipad, int64_t nt8,
                       const char *__restrict__ hdig, const int32_t *__restrict__ hexp, const char *__restrict__ zeros,
                       const double *base, double *out, double sign, int *err)
 {
     extern __shared__ __align__(128) char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t tile = blockIdx.x;  // rows 128 tile .. 128 tile + 127 = pieces 8 tile .. 8 tile + 7
-    const int nk = (nblk + 1) / 2;    // K steps of 16 basis columns
+    const int nk = (nblk + 1) / 2;  // K steps of 16 basis columns
+    const int64_t ntiles = nt8;
     const uint32_t full0 = smem_u32(smem + kUSmemBar), empty0 = full0 + kStages * 8;
+    const uint32_t tdone = smem_u32(smem + kUSmemFlag + 16), tfree = tdone + 8;
     volatile int *flag = reinterpret_cast<volatile int *>(smem + kUSmemFlag);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kUSmemTmem);
 
@@ -561,10 +617,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8 * s));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty0 + 8 * s));
         }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tdone));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(tfree));
         asm volatile("fence.mbarrier_init.release.cluster;");
         *flag = 0;
     }
-    for (int e = tid; e < kStages * (kPiece / 16); e += kThreads) {
+    for (int e = tid; e < kStages * (kPiece / 16); e += kUThreads) {
         const int s = e / (kPiece / 16), o = e % (kPiece / 16);
         *reinterpret_cast<uint4 *>(smem + s * kUStage + kUStageA + kDig * kPiece + o * 16) = make_uint4(0, 0, 0, 0);
     }
@@ -574,78 +632,101 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
 
-    if (tid == 0) {  // ---- producer
-        int issued = 0;
-        for (int kk = 0; kk < nk; ++kk) {
-            const int s = kk % kStages;
-            if (kk >= kStages && !mbar_wait_bounded(empty0 + 8 * s, (uint32_t)(((kk - kStages) / kStages) & 1))) {
-                *flag = 1;
-                break;
-            }
-            if (*flag) break;
-            const int nbk = min(2, nblk - 2 * kk);
-            const uint32_t fb = full0 + 8 * s;
-            const uint32_t bytes = kDig * 2 * (8 * kPiece) + kDig * kPiece;
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(bytes) : "memory");
-            char *st = smem + s * kUStage;
+    if (warp == 0) {
+        if (lane == 0) {  // ---- copy thread
+            int64_t g = 0, issued = 0;
+            for (int64_t tile = blockIdx.x; tile < ntiles && !*flag; tile += gridDim.x) {
+                for (int kk = 0; kk < nk; ++kk, ++g) {
+                    const int s = (int)(g % kStages);
+                    if (g >= kStages &&
+                        !mbar_wait_bounded(empty0 + 8 * s, (uint32_t)(((g - kStages) / kStages) & 1))) {
+                        *flag = 1;
+                        break;
+                    }
+                    const int nbk = min(2, nblk - 2 * kk);
+                    const uint32_t fb = full0 + 8 * s;
+                    const uint32_t bytes = kDig * 2 * (8 * kPiece) + kDig * kPiece;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(bytes)
+                                 : "memory");
+                    char *st = smem + s * kUStage;
 #pragma unroll 1
-            for (int p = 0; p < kDig; ++p) {
-                const char *src = udig + ((p * nt8 + tile) * (int64_t)ipad + 2 * kk) * (8 * kPiece);
-                bulk_copy(smem_u32(st + p * 2 * (8 * kPiece)), src, (uint32_t)nbk * 8 * kPiece, fb);
-                if (nbk == 1)  // second block slot of an odd tail: zeros (its H digits are zero too)
-                    bulk_copy(smem_u32(st + p * 2 * (8 * kPiece) + 8 * kPiece), zeros, 8 * kPiece, fb);
+                    for (int p = 0; p < kDig; ++p) {
+                        const char *src = udig + ((p * nt8 + tile) * (int64_t)ipad + 2 * kk) * (8 * kPiece);
+                        bulk_copy(smem_u32(st + p * 2 * (8 * kPiece)), src, (uint32_t)nbk * 8 * kPiece, fb);
+                        if (nbk == 1)  // second block slot of an odd tail: zeros (its H digits are zero)
+                            bulk_copy(smem_u32(st + p * 2 * (8 * kPiece) + 8 * kPiece), zeros, 8 * kPiece, fb);
+                    }
+                    bulk_copy(smem_u32(st + kUStageA), hdig + (int64_t)kk * kDig * kPiece, kDig * kPiece, fb);
+                    issued = g + 1;
+                }
             }
-            bulk_copy(smem_u32(st + kUStageA), hdig + (int64_t)kk * kDig * kPiece, kDig * kPiece, fb);
-            issued = kk + 1;
+            // copies in flight must land before shared memory is released
+            for (int64_t u = issued - kStages < 0 ? 0 : issued - kStages; u < issued; ++u)
+                if (!mbar_wait_bounded(full0 + 8 * (int)(u % kStages), (uint32_t)((u / kStages) & 1))) *flag = 1;
         }
-        for (int kk = issued - kStages < 0 ? 0 : issued - kStages; kk < issued; ++kk)
-            if (!mbar_wait_bounded(full0 + 8 * (kk % kStages), (uint32_t)((kk / kStages) & 1))) *flag = 1;
-    } else if (tid == 32) {  // ---- MMA issuer
-        int done = 0;
-        for (int kk = 0; kk < nk; ++kk) {
-            const int s = kk % kStages;
-            if (!mbar_wait_bounded(full0 + 8 * s, (uint32_t)((kk / kStages) & 1))) {
+    } else if (warp == 1) {
+        if (lane == 0) {  // ---- MMA thread
+            int64_t g = 0, t = 0;
+            for (int64_t tile = blockIdx.x; tile < ntiles && !*flag; tile += gridDim.x, ++t) {
+                if (t > 0 && !mbar_wait_bounded(tfree, (uint32_t)((t - 1) & 1))) {
+                    *flag = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                bool ok = true;
+                for (int kk = 0; kk < nk; ++kk, ++g) {
+                    const int s = (int)(g % kStages);
+                    if (!mbar_wait_bounded(full0 + 8 * s, (uint32_t)((g / kStages) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const char *st = smem + s * kUStage;
+#pragma unroll
+                    for (int p = 0; p < kDig; ++p) {
+                        const uint64_t da = make_desc_mn(smem_u32(st + p * 2 * (8 * kPiece)));
+                        const uint64_t db = make_desc(smem_u32(st + kUStageA));
+                        mma_bf16(tmem + tcol(p), da, db, make_idesc_amn(kM, nmma(p)), kk > 0 ? 1u : 0u);
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     empty0 + 8 * s)
+                                 : "memory");
+                }
+                if (!ok) {
+                    *flag = 1;
+                    break;
+                }
+                // tile finished: the drain warps may read tensor memory
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 tdone)
+                             : "memory");
+            }
+        }
+    } else {  // ---- drain warps 2..5: tensor-memory lane quarter = warp % 4
+        const int quarter = warp & 3;
+        int64_t t = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++t) {
+            if (!mbar_wait_bounded(tdone, (uint32_t)(t & 1)) || *flag) {
                 *flag = 1;
                 break;
             }
-            if (*flag) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const char *st = smem + s * kUStage;
+            int S[10][kS];
+            drain_row_small(tmem, quarter, S);
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tfree) : "memory");
+            const int64_t r = tile * 128 + quarter * 32 + lane;
+            if (r < n) {
 #pragma unroll
-            for (int p = 0; p < kDig; ++p) {
-                const uint64_t da = make_desc_mn(smem_u32(st + p * 2 * (8 * kPiece)));
-                const uint64_t db = make_desc(smem_u32(st + kUStageA));
-                mma_bf16(tmem + tcol(p), da, db, make_idesc_amn(kM, nmma(p)), kk > 0 ? 1u : 0u);
+                for (int b = 0; b < kS; ++b) {
+                    const double vh = combine_scaled(S, b, hexp[b]);
+                    out[r * kS + b] = base ? fma(sign, vh, base[r * kS + b]) : sign * vh;
+                }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             empty0 + 8 * s)
-                         : "memory");
-            done = kk + 1;
-        }
-        if (done > 0) {
-            const int kk = done - 1;
-            if (!mbar_wait_bounded(empty0 + 8 * (kk % kStages), (uint32_t)((kk / kStages) & 1))) *flag = 1;
         }
     }
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    const bool failed = *flag != 0;
-    if (failed && tid == 0) atomicOr(err, ERR_TIMEOUT);
-
-    if (!failed && nk > 0) {  // ---- drain: thread = row
-        int S[10][kS];
-        drain_row(tmem, warp, S);
-        double v[kS];
-        combine_row(S, v);
-        const int64_t r = tile * 128 + warp * 32 + lane;
-        if (r < n) {
-#pragma unroll
-            for (int b = 0; b < kS; ++b) {
-                const double vh = v[b] * __longlong_as_double((long long)(1023 + hexp[b]) << 52);
-                out[r * kS + b] = base ? fma(sign, vh, base[r * kS + b]) : sign * vh;
-            }
-        }
-    }
+    if (*flag && tid == 0) atomicOr(err, ERR_TIMEOUT);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) {
@@ -707,6 +788,8 @@ size_t tc_udig_bytes(int32_t n, int32_t nblocks)
 
 size_t tc_hdig_bytes(int32_t nblk) { return (size_t)((nblk + 1) / 2) * kDig * kPiece; }
 
+int block_update_tc_max_blocks() { return 1024 / kS; }
+
 // the whole shared memory of an SM: every descriptor reading stays inside the allocation
 constexpr int kUSmemAlloc = 227 * 1024;
 static_assert(kUSmemAlloc >= kUSmemTotal, "update kernel shared memory");
@@ -715,17 +798,22 @@ int launch_block_update_tc(cudaStream_t st, int32_t n, int32_t nblk, const void 
                            const double *H, void *hdig, int32_t *hexp, const void *zeros, const double *base,
                            double *out, double sign, int *d_err)
 {
-    if (n <= 0 || nblk <= 0) return -1;
+    // the drain reads the FP32 sums as integers below 2^22: at most 1024 basis columns
+    if (n <= 0 || nblk <= 0 || nblk > block_update_tc_max_blocks()) return -1;
     k_h_digits<<<1, 256, 0, st>>>(nblk, H, (char *)hdig, hexp, d_err);
     note_launches(1);
     if (cudaFuncSetAttribute(k_block_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kUSmemAlloc) !=
         cudaSuccess)
         return -1;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t nt = ((int64_t)n + kKT - 1) / kKT;
     const int64_t tiles = (nt + 7) / 8;
-    k_block_update_tc<<<(unsigned)tiles, kThreads, kUSmemAlloc, st>>>(n, nblk, (const char *)udig, ipad, (nt + 7) / 8,
-                                                                       (const char *)hdig, hexp, (const char *)zeros,
-                                                                       base, out, sign, d_err);
+    const int grid = (int)(tiles < sms ? tiles : sms);
+    k_block_update_tc<<<grid, kUThreads, kUSmemAlloc, st>>>(n, nblk, (const char *)udig, ipad, (nt + 7) / 8,
+                                                             (const char *)hdig, hexp, (const char *)zeros, base, out,
+                                                             sign, d_err);
     note_launches(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

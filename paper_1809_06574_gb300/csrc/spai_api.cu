@@ -1013,7 +1013,7 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
     // out = base + sign * V_{0..nb-1} H: tensor-core digits when available, else FP64
     auto vupdate = [&](int nb, const double *H, const double *basep, double *out, double sign) -> spai_status {
         const double f = 2.0 * n * s * s * nb;
-        if (use_digits && (opts->orth == SPAI_ORTH_TENSOR || nb >= 2)) {
+        if (use_digits && nb <= block_update_tc_max_blocks() && (opts->orth == SPAI_ORTH_TENSOR || nb >= 2)) {
             PKL("block_update_tc", f, 18.0 * n * s * nb + 16.0 * n * s,
                 launch_block_update_tc(cs, n, nb, w.udig, m + 1, H, w.hdig, w.hexp, w.zeros, basep, out, sign,
                                        ctx->d_err),
@@ -1222,8 +1222,9 @@ extern "C" spai_status spai_block_update(spai_ctx ctx, int32_t s, int32_t n, int
     if (!is_device_ptr(V) || !is_device_ptr(W) || !is_device_ptr(H))
         return fail(ctx, SPAI_EINVAL, "V, W and H must be device memory");
     if (method != SPAI_ORTH_FP64 && method != SPAI_ORTH_TENSOR) return fail(ctx, SPAI_EINVAL, "unknown method");
-    if (method == SPAI_ORTH_TENSOR && !block_dot_tc_supported(s))
-        return fail(ctx, SPAI_EINVAL, "the tensor-core block update needs s == 8");
+    if (method == SPAI_ORTH_TENSOR && (!block_dot_tc_supported(s) || nblk > block_update_tc_max_blocks()))
+        return fail(ctx, SPAI_EINVAL, "the tensor-core block update needs s == 8 and at most %d blocks",
+                    block_update_tc_max_blocks());
     if (((uintptr_t)V | (uintptr_t)W | (uintptr_t)H) & 15)
         return fail(ctx, SPAI_EINVAL, "V, W and H must be 16-byte aligned");
     if (method == SPAI_ORTH_FP64) {

@@ -149,6 +149,7 @@ int launch_to_digits(cudaStream_t st, int32_t n, const double *X, const int32_t 
 // out = base + sign * V_{0..nblk-1} H on the tensor cores (base may be null): H is
 // nblk*8 x 8 ([i][a][b]); hdig needs tc_hdig_bytes(nblk), hexp 8 ints, zeros 2048 zero bytes
 size_t tc_udig_bytes(int32_t n, int32_t nblocks);
+int block_update_tc_max_blocks();
 size_t tc_hdig_bytes(int32_t nblk);
 int launch_block_update_tc(cudaStream_t st, int32_t n, int32_t nblk, const void *udig, int32_t ipad,
                            const double *H, void *hdig, int32_t *hexp, const void *zeros, const double *base,
