@@ -134,6 +134,42 @@ __global__ void __launch_bounds__(kThreads) k_block_dot(int32_t n, const double 
 }
 
 // ---------------------------------------------------------------------------------
+// G = W^T W (S x S): only the S(S+1)/2 pairs a <= b are summed (one per thread, rows
+// unrolled by two); partial[chunk][a][b] holds both (a, b) and (b, a)
+// ---------------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_gram_sym(int32_t n, const double *__restrict__ W,
+                                                       double *__restrict__ partial)
+{
+    constexpr int NP = S * (S + 1) / 2;
+    constexpr int RG = kThreads / NP;
+    __shared__ double red[kThreads];
+    const int p = threadIdx.x % NP, g = threadIdx.x / NP;
+    int a = 0, rem = p;
+    while (rem >= S - a) { rem -= S - a; ++a; }
+    const int b = a + rem;
+    int64_t r0, r1;
+    chunk_rows(n, blockIdx.x, gridDim.x, r0, r1);
+    double acc0 = 0.0, acc1 = 0.0;
+    if (g < RG) {
+        int64_t r = r0 + g;
+        for (; r + RG < r1; r += 2 * RG) {
+            acc0 = fma(__ldg(W + r * S + a), __ldg(W + r * S + b), acc0);
+            acc1 = fma(__ldg(W + (r + RG) * S + a), __ldg(W + (r + RG) * S + b), acc1);
+        }
+        if (r < r1) acc0 = fma(__ldg(W + r * S + a), __ldg(W + r * S + b), acc0);
+    }
+    red[threadIdx.x] = acc0 + acc1;
+    __syncthreads();
+    if (g == 0) {
+        double acc = red[p];
+        for (int h = 1; h < RG; ++h) acc += red[h * NP + p];
+        partial[(int64_t)blockIdx.x * S * S + a * S + b] = acc;
+        partial[(int64_t)blockIdx.x * S * S + b * S + a] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------------
 // out = base + sign * sum_i V_i H_i  (H_i = S x S, [i][a][b]); thread per (row, b)
 // ---------------------------------------------------------------------------------
 template <int S>
@@ -509,6 +545,17 @@ int dot_chunks(int32_t n, int32_t nblk)
 size_t dot_partial_elems(int32_t s, int32_t nblk_max)
 {
     return (size_t)(kDotBlocks + nblk_max + 1) * s * s;
+}
+
+int launch_gram_sym(cudaStream_t st, int32_t s, int32_t n, const double *W, double *partial, double *out)
+{
+    int chunks = (int)(((int64_t)n + 1023) / 1024);
+    if (chunks > 1216) chunks = 1216;
+    if (chunks < 1) chunks = 1;
+    SPAI_DISPATCH_S(s, (k_gram_sym<S><<<chunks, kThreads, 0, st>>>(n, W, partial)));
+    const int count = s * s;
+    k_reduce_chunks<<<(unsigned)(((int64_t)count * 32 + 255) / 256), 256, 0, st>>>(count, chunks, partial, out);
+    return check_launch(2);
 }
 
 int launch_reduce_chunks(cudaStream_t st, int32_t count, int chunks, const double *partial, double *out)

@@ -209,6 +209,9 @@ __global__ void k_to_digits(int32_t n, const double *__restrict__ X, const int32
     }
 }
 
+__device__ __forceinline__ void drain_row(uint32_t tmem, int warp, int S[10][kS]);
+__device__ __forceinline__ double combine_scaled(const int S[10][kS], int b, int e);
+
 // Gram product from digit pieces.  grid = (row chunks, M tiles of 16 blocks); a chunk is
 // a whole number of 16-row sub-tiles, at most 4096 rows.  Thread 0 copies, thread 32
 // issues MMAs, warps 0..3 drain tensor memory.
@@ -316,39 +319,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---- drain: warp w owns tensor-memory lanes 32w..32w+31 = basis columns
     if (!failed && work) {
         const int m = warp * 32 + lane;
-        double h[kS];
-#pragma unroll
-        for (int b = 0; b < kS; ++b) h[b] = 0.0;
-#pragma unroll
-        for (int p = kDig - 1; p >= 0; --p) {
-#pragma unroll
-            for (int c0 = 0; c0 < nmma(p); c0 += 16) {
-                uint32_t v[16];
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(tcol(p) + c0);
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                    "[%16];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                      "=r"(v[14]), "=r"(v[15])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    const int q = (c0 + c) >> 3, b = (c0 + c) & 7;
-                    if (q < nq(p)) {
-                        // weight 2^(-10 - 6(p+q)), an exact power of two
-                        const double wgt = __longlong_as_double((long long)(1023 - 10 - 6 * (p + q)) << 52);
-                        h[b] = fma((double)__uint_as_float(v[c]), wgt, h[b]);
-                    }
-                }
-            }
-        }
+        int S[10][kS];
+        drain_row(tmem, warp, S);
         if (m < nvb * kS) {
             const int gm = blk0 * kS + m;
             double *dst = partial + ((int64_t)chunk * nblk + (gm >> 3)) * (kS * kS) + (gm & 7) * kS;
 #pragma unroll
-            for (int b = 0; b < kS; ++b) dst[b] = h[b] * __longlong_as_double((long long)(1023 + wexp[b]) << 52);
+            for (int b = 0; b < kS; ++b) dst[b] = combine_scaled(S, b, wexp[b]);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");

@@ -956,10 +956,10 @@ spai_status cholqr2(spai_ctx ctx, SolveWs &w, int32_t n, int32_t s, int chunks, 
 {
     cudaStream_t st = ctx->stream;
     const double nsd = (double)n * s;
-    PKL("block_dot", 2.0 * nsd * s, 8.0 * nsd, launch_block_dot(st, s, n, 1, Win, Win, w.partial, w.G1, chunks), "gram");
+    PKL("gram", nsd * (s + 1), 8.0 * nsd, launch_gram_sym(st, s, n, Win, w.partial, w.G1), "gram");
     PKL("small_dense", 0.0, 0.0, launch_chol_small(st, s, w.G1, ref2, 1e-24, w.R1, w.defl1), "chol");
     PKL("trsm_rows", nsd * s, 16.0 * nsd, launch_trsm_rows(st, s, n, Win, w.R1, w.defl1, Qout), "trsm");
-    PKL("block_dot", 2.0 * nsd * s, 8.0 * nsd, launch_block_dot(st, s, n, 1, Qout, Qout, w.partial, w.G1, chunks), "gram");
+    PKL("gram", nsd * (s + 1), 8.0 * nsd, launch_gram_sym(st, s, n, Qout, w.partial, w.G1), "gram");
     PKL("small_dense", 0.0, 0.0, launch_chol_small(st, s, w.G1, nullptr, 0.0, w.R2, w.defl2), "chol");
     PKL("trsm_rows", nsd * s, 16.0 * nsd, launch_trsm_rows(st, s, n, Qout, w.R2, w.defl2, Qout), "trsm");
     PKL("small_dense", 0.0, 0.0, launch_triu_mul(st, s, w.R2, w.R1, Rout), "triu");

@@ -130,6 +130,8 @@ int launch_residual(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr
                     const int32_t *colind, const double *val, const double *X, const double *B,
                     double *R);
 int launch_zero(cudaStream_t st, int64_t count, double *dst);
+// G = W^T W (s x s) summing only the pairs a <= b; partial needs 1216 * s * s doubles
+int launch_gram_sym(cudaStream_t st, int32_t s, int32_t n, const double *W, double *partial, double *out);
 // out[p] = sum over chunks of partial[chunk * count + p] (deterministic)
 int launch_reduce_chunks(cudaStream_t st, int32_t count, int chunks, const double *partial, double *out);
 
