@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--nparams", type=int, default=20)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    # single-kernel case (for profiler captures): H = V^T W or W -= V H at n = side^3, s = 8
+    ap.add_argument("--kernel", default=None, choices=["dot", "update"])
+    ap.add_argument("--nblk", type=int, default=16)
+    ap.add_argument("--orth", default="tensor", choices=["tensor", "fp64"])
     return ap.parse_args()
 
 
@@ -112,6 +116,108 @@ class ClockSampler:
                 "sm_max_mhz": max(smax) if smax else None,
                 "power_w_max": max(power) if power else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------ rooflines
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    pk = json.load(open(path)) if os.path.exists(path) else {}
+    src = "measured" if pk else "fallback"
+    return (pk.get("hbm_gbs", 6800.0), pk.get("bf16_tflops", 1900.0),
+            pk.get("bf16_tflops_sustained", 1700.0), src)
+
+
+# FP64 ALU peak from unit counts and clock: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2.07 GHz
+FP64_NOMINAL_TFLOPS = 152 * 4 * 2070e6 / 1e12
+# one FP64-accurate product of the digit kernels costs 53 BF16 digit-pair products
+DIGIT_PRODUCTS = 53
+# how each kernel family computes: FP64 ALUs, tensor cores (digit products), or neither
+FAMILY_UNIT = {
+    "block_dot_tc": "tensor", "block_update_tc": "tensor", "to_digits": "none", "w_digits": "none",
+    "axpy": "none", "gather_csc": "none", "small_dense": "latency", "arnoldi_ls": "latency",
+    "backsolve": "latency",
+}
+# DRAM bytes per launch, (a * blocks + b) * n * s, fitted to one ncu capture of each kernel
+# at n = 262,144, s = 8, 16 basis blocks (profiles/k_block_{dot,update}_tc_3d64.md):
+# dot 645.5 MB over 17 blocks; update 636.9 MB = (18 * 16 + 16) B per row entry, 18 blocks
+NCU_TRAFFIC = {"block_dot_tc": (18.1, 0.0), "block_update_tc": (18.0, -20.0)}
+
+
+def roofline_entry(f, n, s, fp64_probe=None):
+    """Binding roof of one kernel family: max(bytes / HBM, flops / compute peak).
+
+    Bytes and flops are the algorithmic figures of the method (FP64 operands), credited per
+    launch by the library's profiler.  Compute peak: the FP64 ALUs for FP64 kernels, the
+    BF16 tensor peak / 53 for the digit-product kernels (FP64-equivalent flops)."""
+    hbm, bf16, bf16_sus, src = _peaks()
+    unit = FAMILY_UNIT.get(f["name"], "fp64")
+    launches = max(f["launches"], 1)
+    sec = f["ms"] * 1e-3
+    out = {"kernel": f["name"], "launches": f["launches"], "avg_launch_ms": f["ms"] / launches,
+           "algorithmic_bytes_per_launch": f["bytes"] / launches,
+           "algorithmic_flops_per_launch": f["flops"] / launches}
+    if unit == "latency" or sec <= 0:
+        out.update({"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
+                    "traffic": None})
+        return out
+    cpeak = FP64_NOMINAL_TFLOPS if unit == "fp64" else (bf16_sus / DIGIT_PRODUCTS if unit == "tensor" else 0.0)
+    t_hbm = f["bytes"] / (hbm * 1e9)
+    t_alu = f["flops"] / (cpeak * 1e12) if cpeak > 0 else 0.0
+    if t_hbm >= t_alu:
+        ach = f["bytes"] / sec / 1e9
+        out.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                    "peak_source": f"{src} copy bandwidth"})
+    else:
+        ach = f["flops"] / sec / 1e12
+        out.update({"bound": "alu", "achieved": ach, "peak": cpeak, "unit": "TFLOP/s", "frac": ach / cpeak,
+                    "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz"
+                    + (f"; FMA probe measured {fp64_probe:.3f} TFLOP/s in this run" if fp64_probe else "")})
+    out["traffic"] = None
+    if f["name"] in NCU_TRAFFIC and f["bytes"] > 0:
+        a, b = NCU_TRAFFIC[f["name"]]
+        # blocks per launch recovered from the algorithmic bytes (8 B per element per block)
+        blocks = f["bytes"] / launches / (8.0 * n * s)
+        out["traffic"] = (a * blocks + b) * n * s
+    if unit == "tensor" and f["name"] == "block_dot_tc":
+        # what the kernel itself streams: 9 BF16 digits (18 B) per element of V and W
+        out["implementation_bytes_per_launch"] = 18.0 / 8.0 * f["bytes"] / launches
+    elif unit == "tensor":
+        nb = f["bytes"] / launches / (8.0 * n * s) - 2
+        out["implementation_bytes_per_launch"] = (18.0 * nb + 16.0) * n * s
+    return out
+
+
+def run_kernel_case(args):
+    """One kernel on its own at the sweep's size: H = V^T W (dot) or W -= V H (update)."""
+    import torch
+    import paper_1809_06574_gb300 as sg
+    n, s, nb = args.side ** 3, 8, args.nblk
+    g = torch.Generator(device="cpu").manual_seed(0)
+    # basis-like blocks: entries of unit-norm columns (the digit kernels take |v| < 2)
+    V = (torch.randn(nb, n, s, dtype=torch.float64, generator=g) / n ** 0.5).cuda()
+    W = torch.randn(n, s, dtype=torch.float64, generator=g).cuda()
+    H = torch.randn(nb * s, s, dtype=torch.float64, generator=g).cuda()
+    stream = torch.cuda.current_stream()
+    ctx = sg.spai_ctx_create(stream.cuda_stream, 0)
+    method = sg.ORTH_TENSOR if args.orth == "tensor" else sg.ORTH_FP64
+
+    def once():
+        if args.kernel == "dot":
+            sg.spai_block_gram(ctx, s, n, nb, V, W, H, method)
+        else:
+            sg.spai_block_update(ctx, s, n, nb, V, H, W, -1.0, method)
+    for _ in range(max(args.warmup, 1)):
+        once()
+    sg.spai_ctx_profile(ctx, 1)
+    for _ in range(args.steps):
+        once()
+    torch.cuda.synchronize()
+    prof = [sg.spai_ctx_profile_entry(ctx, i) for i in range(sg.spai_ctx_profile_count(ctx))]
+    prof = [f for f in prof if not f["name"].startswith("idle:")]
+    sg.spai_ctx_destroy(ctx)
+    fams = {f["name"]: roofline_entry(f, n=n, s=s) for f in prof}
+    print(json.dumps({"kernel_case": args.kernel, "n": n, "s": s, "nblk": nb, "orth": args.orth,
+                      "steps": args.steps, "families": fams}), flush=True)
 
 
 # ------------------------------------------------------------------------------- oracle
@@ -270,6 +376,10 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
+    if args.kernel:
+        if rank == 0:
+            run_kernel_case(args)
+        return
 
     import synth
     w = synth.grid3d_7pt(side=args.side, nparams=args.nparams, seed=rank)
@@ -316,8 +426,11 @@ def main():
     launches = sg.spai_launch_count() - l0
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    prof = [sg.spai_ctx_profile_entry(ctx, i) for i in range(sg.spai_ctx_profile_count(ctx))]
+    prof_all = [sg.spai_ctx_profile_entry(ctx, i) for i in range(sg.spai_ctx_profile_count(ctx))]
     sg.spai_ctx_profile(ctx, 0)
+    prof = [f for f in prof_all if not f["name"].startswith("idle:")]
+    idle = sorted(((f["name"][5:], f["ms"]) for f in prof_all if f["name"].startswith("idle:")),
+                  key=lambda x: -x[1])
     solves = sweep.solves
     iters = list(sweep.iters)
     t_local = ms / 1e3
@@ -354,29 +467,15 @@ def main():
     if rank == 0:
         total_ms = sum(f["ms"] for f in prof) or 1.0
         dom = max(prof, key=lambda f: f["ms"])
-        avg_ms = dom["ms"] / max(dom["launches"], 1)
-        ach_tflops = dom["flops"] / (dom["ms"] * 1e-3) / 1e12 if dom["ms"] else 0.0
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
-            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-        # FP64 ALU peak from unit counts and clock: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop
-        # x 2.07 GHz (the nominal 1.25 TFLOP/s of GB300)
-        nominal_fp64 = 152 * 4 * 2070e6 / 1e12
-        roofline = {
-            "kernel": dom["name"], "bound": "alu", "achieved": ach_tflops,
-            "peak": nominal_fp64, "unit": "TFLOP/s", "frac": ach_tflops / nominal_fp64,
-            "traffic": None,
-            "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz; cross-check: FMA probe "
-                           f"measured {fp64_tflops:.3f} TFLOP/s in this run",
-            "avg_launch_ms": avg_ms, "launches": dom["launches"],
-            "algorithmic_bytes_per_launch": dom["bytes"] / max(dom["launches"], 1),
-            "achieved_gbs": dom["bytes"] / (dom["ms"] * 1e-3) / 1e9 if dom["ms"] else 0.0,
-            "hbm_peak_gbs": peaks.get("hbm_gbs"),
-        }
-        kernels = {f["name"]: {"launches": f["launches"], "ms": round(f["ms"], 3),
-                               "share": round(f["ms"] / total_ms, 4),
-                               "tflops": round(f["flops"] / (f["ms"] * 1e-3) / 1e12, 4) if f["ms"] else 0,
-                               "gbs": round(f["bytes"] / (f["ms"] * 1e-3) / 1e9, 1) if f["ms"] else 0}
-                   for f in sorted(prof, key=lambda f: -f["ms"])}
+        roofline = roofline_entry(dom, n=w.n, s=int(w.B.shape[1]), fp64_probe=fp64_tflops)
+        kernels = {}
+        for f in sorted(prof, key=lambda f: -f["ms"]):
+            r = roofline_entry(f, n=w.n, s=int(w.B.shape[1]))
+            kernels[f["name"]] = {
+                "launches": f["launches"], "ms": round(f["ms"], 3), "share": round(f["ms"] / total_ms, 4),
+                "tflops": round(f["flops"] / (f["ms"] * 1e-3) / 1e12, 4) if f["ms"] else 0,
+                "gbs": round(f["bytes"] / (f["ms"] * 1e-3) / 1e9, 1) if f["ms"] else 0,
+                "bound": r["bound"], "frac": None if r["frac"] is None else round(r["frac"], 4)}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
@@ -388,6 +487,9 @@ def main():
             "gmres_iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)),
                                  "max": int(max(iters))},
             "kernels": kernels,
+            # stream time with no profiled kernel running, by the kernel family that followed
+            "idle_ms": {"total": round(sum(v for _, v in idle), 3),
+                        **{k: round(v, 3) for k, v in idle[:8]}},
         }
         print(json.dumps(line), flush=True)
     sg.spai_ctx_destroy(ctx)

@@ -110,6 +110,9 @@ SPAI_API spai_status spai_ctx_profile(spai_ctx ctx, int32_t enable);
 /* Number of kernel families recorded so far (synchronises the stream). */
 SPAI_API int32_t spai_ctx_profile_count(spai_ctx ctx);
 /* Totals of family i: launches, summed event time (ms), algorithmic flops and bytes.
+ * A family named "idle:<family>" is not a kernel: it sums the stream time between the
+ * previous profiled launch and each launch of <family> (other work on the stream, or the
+ * device waiting for the host), with zero flops and bytes.
  * *name stays valid until the next spai_ctx_profile call. */
 SPAI_API spai_status spai_ctx_profile_entry(spai_ctx ctx, int32_t i, const char **name,
                                             int64_t *launches, double *ms, double *flops,
@@ -217,7 +220,7 @@ SPAI_API spai_status spai_pc_apply_noalloc(spai_ctx ctx, spai_pc pc, int32_t s, 
  * ---------------------------------------------------------------------------------- */
 
 /* How the block Gram products V^T W of the orthogonalisation are computed. */
-#define SPAI_ORTH_AUTO 0    /* tensor-core digits when s == 8 and j + 1 >= 4 blocks, else FP64 */
+#define SPAI_ORTH_AUTO 0    /* tensor-core digits when s == 8 and the product has >= 2 blocks, else FP64 */
 #define SPAI_ORTH_FP64 1    /* FP64 fused multiply-adds on the CUDA cores */
 #define SPAI_ORTH_TENSOR 2  /* tensor-core digits whenever s == 8 */
 

@@ -271,156 +271,164 @@ __global__ void k_triu_mul(const double *__restrict__ R2, const double *__restri
     out[a * S + b] = acc;
 }
 
-__global__ void k_add_small(int32_t count, const double *a, const double *b, double *out)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < count) out[i] = a[i] + b[i];
-}
-
-// Hcol (column-major, leading dim ldh): rows [0,(j+1)S) from Hup[i][a][b]
-// (row i*S + a, column b), rows [(j+1)S, (j+2)S) from Rsub[a][b]
-__global__ void k_copy_hcol(int32_t S, int32_t j, int32_t ldh, const double *__restrict__ Hup,
-                            const double *__restrict__ Rsub, double *__restrict__ Hcol)
-{
-    const int rows = (j + 2) * S;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rows * S; e += gridDim.x * blockDim.x) {
-        const int row = e / S, b = e % S;
-        double v = (row < (j + 1) * S) ? Hup[(int64_t)row * S + b] : Rsub[(row - (j + 1) * S) * S + b];
-        Hcol[(int64_t)b * ldh + row] = v;
-    }
-}
-
 // ---------------------------------------------------------------------------------
 // Projected least squares, updated one block column at a time (one CTA).
-//  Hcol: new block column (column-major, ld = (m+1)S), rows [0, (j+2)S).
+//  New block column of the block Hessenberg matrix, rows [0, (j+2)S), built here:
+//    rows [0, (j+1)S) = H1 + H2 (the two Gram-Schmidt passes, [row][b] row-major),
+//    rows [(j+1)S, (j+2)S) = Rsub (S x S, the new block's triangular factor).
 //  Qs:   for every earlier step j' the 2S x 2S orthogonal matrix M_j' (row-major) that
-//        triangularised block column j' on rows [j'S, j'S + 2S).
+//        triangularised block column j' on rows [j'S, j'S + 2S); M_j is written here.
 //  Rtri: triangular factor, column-major, ld = (m+1)S; block column j is written here.
 //  G:    transformed right-hand side ((m+1)S x S, row-major).
 //  est:  per-column least-squares residual norm = || G[(j+1)S : (j+2)S, i] ||.
 // A zero column (deflated basis vector) gets an identity reflector and R_cc = 0.
+//
+// The earlier factors are applied through a 2S-row window that slides down the column
+// (rows above the window are final and go straight to Rtri), the next factor's row
+// prefetched into registers.  The S reflectors of this step are then applied to the
+// augmented block [X | G rows | I] (2S x 4S): a group of TPC threads per column, dot
+// products reduced with shuffles.  The identity part ends as M_j.
 // ---------------------------------------------------------------------------------
 template <int S>
-__global__ void k_arnoldi_ls(int32_t j, int32_t m, double *__restrict__ Hcol,
-                             double *__restrict__ Qs, double *__restrict__ Rtri,
-                             double *__restrict__ G, const double *__restrict__ thresh,
-                             double *__restrict__ est, int32_t *__restrict__ flag)
-{
-    constexpr int S2 = 2 * S;
-    const int ld = (m + 1) * S;
-    __shared__ double X[S2][S];     // working rows of the new column block
-    __shared__ double Mq[S2][S2];   // orthogonal factor being formed
-    __shared__ double Vr[S][S2];    // reflectors of this step
-    __shared__ double beta[S];      // 2 / v^T v (0 = identity)
-    __shared__ double rdiag[S];     // R_cc
-    __shared__ double Gx[S2][S];
-    __shared__ double Gy[S2][S];
-    const int tid = threadIdx.x, nt = blockDim.x;
+struct LsCfg {
+    static constexpr int S2 = 2 * S;
+    static constexpr int NT = (2 * S * S < 32) ? 32 : 2 * S * S;  // threads
+    static constexpr int NC = 4 * S;                               // augmented columns
+    static constexpr int TPC = (NT / NC < S2) ? NT / NC : S2;      // threads per column
+    static constexpr int RPT = S2 / TPC;                           // rows per thread
+    static_assert(TPC >= 1 && TPC <= 32 && S2 % TPC == 0 && NC * TPC <= NT, "layout");
+};
 
-    // (a) apply the earlier steps' orthogonal factors
-    for (int jp = 0; jp < j; ++jp) {
-        const double *M = Qs + (int64_t)jp * S2 * S2;
-        for (int e = tid; e < S2 * S; e += nt) {
-            const int r = e / S, t = e % S;
-            X[r][t] = Hcol[(int64_t)t * ld + jp * S + r];
-        }
-        __syncthreads();
-        for (int e = tid; e < S2 * S; e += nt) {
-            const int r = e / S, t = e % S;
-            double acc = 0.0;
-            for (int q = 0; q < S2; ++q) acc = fma(M[r * S2 + q], X[q][t], acc);
-            Hcol[(int64_t)t * ld + jp * S + r] = acc;
-        }
-        __syncthreads();
-    }
-    // (b) Householder QR of rows [jS, jS + 2S)
-    for (int e = tid; e < S2 * S; e += nt) {
-        const int r = e / S, t = e % S;
-        X[r][t] = Hcol[(int64_t)t * ld + j * S + r];
+template <int S>
+__global__ void __launch_bounds__(LsCfg<S>::NT)
+    k_arnoldi_ls(int32_t j, int32_t m, const double *__restrict__ H1, const double *__restrict__ H2,
+                 const double *__restrict__ Rsub, double *__restrict__ Qs, double *__restrict__ Rtri,
+                 double *__restrict__ G, const double *__restrict__ thresh, double *__restrict__ est,
+                 int32_t *__restrict__ flag)
+{
+    using C = LsCfg<S>;
+    constexpr int S2 = C::S2, NC = C::NC, TPC = C::TPC, RPT = C::RPT;
+    const int ld = (m + 1) * S;
+    __shared__ double Aug[S2][NC + 1];
+    __shared__ double Vr[S2];
+    __shared__ double sest[S];
+    __shared__ double sbeta, srd;
+    const int tid = threadIdx.x;
+    const int hrows = (j + 1) * S;
+    auto orig = [&](int row, int col) -> double {
+        if (row < hrows) return H1[row * S + col] + (H2 ? H2[row * S + col] : 0.0);
+        return Rsub[(row - hrows) * S + col];
+    };
+
+    // (a) earlier factors on the window rows [jp S, jp S + 2S); thread = (r, t)
+    const bool act = tid < S2 * S;
+    const int r = tid / S, t = tid % S;
+    if (act) Aug[r][t] = orig(r, t);
+    double mrow[S2];
+    if (act && j > 0) {
+#pragma unroll
+        for (int q = 0; q < S2; ++q) mrow[q] = __ldg(Qs + r * S2 + q);
     }
     __syncthreads();
+    for (int jp = 0; jp < j; ++jp) {
+        double acc = 0.0, nxt = 0.0;
+        if (act) {
+#pragma unroll
+            for (int q = 0; q < S2; ++q) acc = fma(mrow[q], Aug[q][t], acc);
+            if (r >= S) nxt = orig((jp + 2) * S + r - S, t);
+            if (jp + 1 < j) {
+#pragma unroll
+                for (int q = 0; q < S2; ++q) mrow[q] = __ldg(Qs + ((int64_t)(jp + 1) * S2 + r) * S2 + q);
+            }
+        }
+        __syncthreads();
+        if (act) {
+            if (r < S) {
+                Rtri[(int64_t)(j * S + t) * ld + jp * S + r] = acc;
+            } else {
+                Aug[r - S][t] = acc;
+                Aug[r][t] = nxt;
+            }
+        }
+        __syncthreads();
+    }
+
+    // (b) this step's reflectors on [X | G rows | I]
+    for (int e = tid; e < S2 * 3 * S; e += C::NT) {
+        const int rr = e / (3 * S), cc = e % (3 * S);
+        Aug[rr][S + cc] = (cc < S) ? G[(int64_t)(j * S + rr) * S + cc] : ((cc - S == rr) ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    const int col = tid / TPC, k = tid % TPC;
+    const bool cact = tid < NC * TPC;
     for (int c = 0; c < S; ++c) {
-        // warp 0 forms reflector c from X[c:, c]
         if (tid < 32) {
-            const int r = tid;
-            double x = (r >= c && r < S2) ? X[r][c] : 0.0;
+            const double x = (tid >= c && tid < S2) ? Aug[tid][c] : 0.0;
             double ss = x * x;
+#pragma unroll
             for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
             const double alpha = sqrt(ss);
-            const double xc = X[c][c];
+            const double xc = Aug[c][c];
             const double sgn = (xc >= 0.0) ? 1.0 : -1.0;
-            double v = x;
-            if (r == c) v += sgn * alpha;
-            if (r < S2) Vr[c][r] = (alpha > 0.0) ? v : 0.0;
-            if (r == 0) {
-                beta[c] = (alpha > 0.0) ? 1.0 / (alpha * (alpha + fabs(xc))) : 0.0;
-                rdiag[c] = (alpha > 0.0) ? -sgn * alpha : 0.0;
+            if (tid < S2) Vr[tid] = (alpha > 0.0) ? ((tid == c) ? x + sgn * alpha : x) : 0.0;
+            if (tid == 0) {
+                sbeta = (alpha > 0.0) ? 1.0 / (alpha * (alpha + fabs(xc))) : 0.0;
+                srd = (alpha > 0.0) ? -sgn * alpha : 0.0;
             }
         }
         __syncthreads();
-        // apply to columns t > c of X (thread per column t, serial over 2S rows)
-        if (beta[c] != 0.0) {
-            for (int t = c + 1 + tid; t < S; t += nt) {
-                double d = 0.0;
-                for (int r = c; r < S2; ++r) d = fma(Vr[c][r], X[r][t], d);
-                const double g = d * beta[c];
-                for (int r = c; r < S2; ++r) X[r][t] = fma(-g, Vr[c][r], X[r][t]);
+        const double b = sbeta;
+        const bool upd = cact && col > c && b != 0.0;
+        double d = 0.0;
+        if (upd) {
+#pragma unroll
+            for (int u = 0; u < RPT; ++u) {
+                const int rr = k + u * TPC;
+                if (rr >= c) d = fma(Vr[rr], Aug[rr][col], d);
             }
         }
-        __syncthreads();
-        // column c itself becomes (R_cc, 0, ..., 0)
-        if (tid == c) X[c][c] = rdiag[c];
-        if (tid < S2 && tid > c) X[tid][c] = 0.0;
+#pragma unroll
+        for (int o = TPC / 2; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (upd) {
+            const double g = d * b;
+#pragma unroll
+            for (int u = 0; u < RPT; ++u) {
+                const int rr = k + u * TPC;
+                if (rr >= c) Aug[rr][col] = fma(-g, Vr[rr], Aug[rr][col]);
+            }
+        }
+        if (cact && col == c) {
+#pragma unroll
+            for (int u = 0; u < RPT; ++u) {
+                const int rr = k + u * TPC;
+                if (rr == c) Aug[rr][c] = srd;
+                else if (rr > c) Aug[rr][c] = 0.0;
+            }
+        }
         __syncthreads();
     }
-    // (c) M = H_{S-1} ... H_0 (so that M X_original = R)
-    for (int e = tid; e < S2 * S2; e += nt) Mq[e / S2][e % S2] = (e / S2 == e % S2) ? 1.0 : 0.0;
-    __syncthreads();
-    for (int c = 0; c < S; ++c) {
-        if (beta[c] != 0.0) {
-            for (int col = tid; col < S2; col += nt) {
-                double d = 0.0;
-                for (int r = c; r < S2; ++r) d = fma(Vr[c][r], Mq[r][col], d);
-                const double g = d * beta[c];
-                for (int r = c; r < S2; ++r) Mq[r][col] = fma(-g, Vr[c][r], Mq[r][col]);
-            }
-        }
-        __syncthreads();
-    }
+
+    // (c) outputs: M_j, block column j of R (rows [jS, jS + S)), G rows, estimates
     double *Mj = Qs + (int64_t)j * S2 * S2;
-    for (int e = tid; e < S2 * S2; e += nt) Mj[e] = Mq[e / S2][e % S2];
-    // (d) write the triangularised block column: rows [0, (j+1)S)
-    for (int e = tid; e < (j + 1) * S * S; e += nt) {
-        const int row = e / S, t = e % S;
-        double v;
-        if (row < j * S) v = Hcol[(int64_t)t * ld + row];
-        else v = (row - j * S <= t) ? X[row - j * S][t] : 0.0;
-        Rtri[(int64_t)(j * S + t) * ld + row] = v;
+    for (int e = tid; e < S2 * S2; e += C::NT) Mj[e] = Aug[e / S2][2 * S + e % S2];
+    for (int e = tid; e < S * S; e += C::NT) {
+        const int rr = e / S, tt = e % S;
+        Rtri[(int64_t)(j * S + tt) * ld + j * S + rr] = (rr <= tt) ? Aug[rr][tt] : 0.0;
     }
-    // (e) transform G rows [jS, jS + 2S)
-    for (int e = tid; e < S2 * S; e += nt) {
-        const int r = e / S, i = e % S;
-        Gx[r][i] = G[(int64_t)(j * S + r) * S + i];
+    for (int e = tid; e < S2 * S; e += C::NT) {
+        const int rr = e / S, i = e % S;
+        G[(int64_t)(j * S + rr) * S + i] = Aug[rr][S + i];
     }
-    __syncthreads();
-    for (int e = tid; e < S2 * S; e += nt) {
-        const int r = e / S, i = e % S;
-        double acc = 0.0;
-        for (int q = 0; q < S2; ++q) acc = fma(Mq[r][q], Gx[q][i], acc);
-        G[(int64_t)(j * S + r) * S + i] = acc;
-        Gy[r][i] = acc;
-    }
-    __syncthreads();
-    // (f) residual estimates
     if (tid < S) {
         double ss = 0.0;
-        for (int r = S; r < S2; ++r) ss += Gy[r][tid] * Gy[r][tid];
-        est[tid] = sqrt(ss);
+        for (int rr = S; rr < S2; ++rr) ss += Aug[rr][S + tid] * Aug[rr][S + tid];
+        sest[tid] = sqrt(ss);
+        est[tid] = sest[tid];
     }
     __syncthreads();
     if (tid == 0) {
         int ok = 1;
-        for (int i = 0; i < S; ++i) ok &= (est[i] <= thresh[i]);
+        for (int i = 0; i < S; ++i) ok &= (sest[i] <= thresh[i]);
         *flag = ok;
     }
 }
@@ -605,25 +613,12 @@ int launch_triu_mul(cudaStream_t st, int32_t s, const double *R2, const double *
     return check_launch();
 }
 
-int launch_add_small(cudaStream_t st, int32_t count, const double *a, const double *b, double *out)
+int launch_arnoldi_ls(cudaStream_t st, int32_t s, int32_t j, int32_t m, const double *H1, const double *H2,
+                      const double *Rsub, double *Qs, double *Rtri, double *G, const double *thresh, double *est,
+                      int32_t *flag)
 {
-    k_add_small<<<(count + 255) / 256, 256, 0, st>>>(count, a, b, out);
-    return check_launch();
-}
-
-int launch_copy_hcol(cudaStream_t st, int32_t s, int32_t j, int32_t ldh, const double *Hup,
-                     const double *Rsub, double *Hcol)
-{
-    const int count = (j + 2) * s * s;
-    k_copy_hcol<<<cap_grid((count + 255) / 256), 256, 0, st>>>(s, j, ldh, Hup, Rsub, Hcol);
-    return check_launch();
-}
-
-int launch_arnoldi_ls(cudaStream_t st, int32_t s, int32_t j, int32_t m, double *Hcol, double *Qs,
-                      double *Rtri, double *G, const double *thresh, double *est, int32_t *flag)
-{
-    SPAI_DISPATCH_S(s, (k_arnoldi_ls<S><<<1, 256, 0, st>>>(j, m, Hcol, Qs, Rtri, G, thresh, est,
-                                                          flag)));
+    SPAI_DISPATCH_S(s, (k_arnoldi_ls<S><<<1, LsCfg<S>::NT, 0, st>>>(j, m, H1, H2, Rsub, Qs, Rtri, G, thresh,
+                                                                   est, flag)));
     return check_launch();
 }
 

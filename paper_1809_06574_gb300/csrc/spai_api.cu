@@ -44,6 +44,7 @@ struct spai_ctx_s {
         double ms = 0.0, flops = 0.0, bytes = 0.0;
     };
     bool prof_on = false;
+    cudaEvent_t prof_last = nullptr;  // end event of the latest resolved launch
     std::vector<ProfRec> prof_recs;
     std::vector<cudaEvent_t> prof_pool;
     std::vector<ProfFamily> prof_fam;
@@ -156,8 +157,18 @@ void prof_flush(spai_ctx ctx)
         f.ms += ms;
         f.flops += r.flops;
         f.bytes += r.bytes;
+        if (ctx->prof_last) {
+            // stream time between the previous profiled launch and this one: other work on
+            // the stream (copies, memsets, foreign kernels) or the device waiting for the host
+            float gap = 0.f;
+            cudaEventElapsedTime(&gap, ctx->prof_last, r.a);
+            const int gi = prof_family(ctx, ("idle:" + ctx->prof_fam[r.family].name).c_str());
+            ctx->prof_fam[gi].launches += 1;
+            ctx->prof_fam[gi].ms += gap > 0.f ? gap : 0.f;
+            ctx->prof_pool.push_back(ctx->prof_last);
+        }
+        ctx->prof_last = r.b;
         ctx->prof_pool.push_back(r.a);
-        ctx->prof_pool.push_back(r.b);
     }
     ctx->prof_recs.clear();
 }
@@ -530,6 +541,7 @@ extern "C" spai_status spai_ctx_destroy(spai_ctx ctx)
     cudaStreamSynchronize(ctx->stream);
     prof_flush(ctx);
     for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
+    if (ctx->prof_last) cudaEventDestroy(ctx->prof_last);
     cudaFree(ctx->d_err);
     cudaFreeHost(ctx->h_pinned);
     delete ctx;
@@ -577,6 +589,8 @@ extern "C" spai_status spai_ctx_profile(spai_ctx ctx, int32_t enable)
     if (!ctx) return SPAI_EINVAL;
     prof_flush(ctx);
     ctx->prof_fam.clear();
+    if (ctx->prof_last) ctx->prof_pool.push_back(ctx->prof_last);
+    ctx->prof_last = nullptr;
     ctx->prof_on = enable != 0;
     return SPAI_OK;
 }
@@ -888,7 +902,7 @@ namespace {
 
 struct SolveWs {
     double *Bw, *Xw, *W, *Z, *T0, *T1, *V;
-    double *partial, *H1, *H2, *Hup, *G1, *R1, *R2, *Rn, *ref2, *nrm2, *thresh, *Hcol, *Qs, *Rtri, *G, *Y, *est;
+    double *partial, *H1, *H2, *G1, *R1, *R2, *Rn, *ref2, *nrm2, *thresh, *Qs, *Rtri, *G, *Y, *est;
     int32_t *defl1, *defl2, *flag;
     void *tc_scratch;  // column exponents of the tensor-core Gram product (zeroed per solve)
     void *vdig, *wdig; // digit pieces of the basis blocks and of W (tensor-core Gram product)
@@ -922,7 +936,6 @@ size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks
     }
     w.H1 = (double *)take((m + 1) * ss);
     w.H2 = (double *)take((m + 1) * ss);
-    w.Hup = (double *)take((m + 1) * ss);
     w.G1 = (double *)take(ss);
     w.R1 = (double *)take(ss);
     w.R2 = (double *)take(ss);
@@ -930,7 +943,6 @@ size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks
     w.ref2 = (double *)take(s * 8);
     w.nrm2 = (double *)take(s * 8);
     w.thresh = (double *)take(s * 8);
-    w.Hcol = (double *)take((size_t)(m + 1) * s * s * 8);
     w.Qs = (double *)take((size_t)m * 4 * ss);
     w.Rtri = (double *)take((size_t)(m + 1) * s * m * s * 8);
     w.G = (double *)take((m + 1) * ss);
@@ -1014,7 +1026,7 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
     auto vupdate = [&](int nb, const double *H, const double *basep, double *out, double sign) -> spai_status {
         const double f = 2.0 * n * s * s * nb;
         if (use_digits && nb <= block_update_tc_max_blocks() && (opts->orth == SPAI_ORTH_TENSOR || nb >= 2)) {
-            PKL("block_update_tc", f, 18.0 * n * s * nb + 16.0 * n * s,
+            PKL("block_update_tc", f, 8.0 * n * s * (nb + 2),
                 launch_block_update_tc(cs, n, nb, w.udig, m + 1, H, w.hdig, w.hexp, w.zeros, basep, out, sign,
                                        ctx->d_err),
                 "block update");
@@ -1089,7 +1101,7 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
             if (tc) {
                 PKL("w_digits", 0.0, 16.0 * nsd + 18.0 * nsd,
                     launch_w_digits(cs, n, w.W, w.wdig, w.tc_scratch, ctx->d_err), "W digits");
-                PKL("block_dot_tc", 2.0 * nsd * s * nb, 18.0 * nsd * (nb + 1),
+                PKL("block_dot_tc", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
                     launch_block_dot_tc(cs, n, j + 1, w.vdig, m + 1, w.wdig, w.tc_scratch, w.partial, w.H1,
                                         ctx->d_err),
                     "H1");
@@ -1101,7 +1113,7 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
             if (tc) {
                 PKL("w_digits", 0.0, 16.0 * nsd + 18.0 * nsd,
                     launch_w_digits(cs, n, w.W, w.wdig, w.tc_scratch, ctx->d_err), "W digits");
-                PKL("block_dot_tc", 2.0 * nsd * s * nb, 18.0 * nsd * (nb + 1),
+                PKL("block_dot_tc", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
                     launch_block_dot_tc(cs, n, j + 1, w.vdig, m + 1, w.wdig, w.tc_scratch, w.partial, w.H2,
                                         ctx->d_err),
                     "H2");
@@ -1110,13 +1122,11 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
                     launch_block_dot(cs, s, n, j + 1, w.V, w.W, w.partial, w.H2, chunks), "H2");
             }
             if ((st = vupdate(j + 1, w.H2, w.W, w.W, -1.0))) return st;
-            PKL("small_dense", 0.0, 0.0, launch_add_small(cs, (j + 1) * s * s, w.H1, w.H2, w.Hup), "H1 + H2");
             double *Vn = w.V + (size_t)(j + 1) * blk_elems;
             if ((st = cholqr2(ctx, w, n, s, chunks, w.W, Vn, w.Rn, w.ref2))) return st;
             if (j + 1 < m && (st = make_digits(j + 1))) return st;
-            PKL("small_dense", 0.0, 0.0, launch_copy_hcol(cs, s, j, (m + 1) * s, w.Hup, w.Rn, w.Hcol), "H column");
             PKL("arnoldi_ls", 16.0 * s * s * s * (j + 1), 0.0,
-                launch_arnoldi_ls(cs, s, j, m, w.Hcol, w.Qs, w.Rtri, w.G, w.thresh, w.est, w.flag), "least squares");
+                launch_arnoldi_ls(cs, s, j, m, w.H1, w.H2, w.Rn, w.Qs, w.Rtri, w.G, w.thresh, w.est, w.flag), "least squares");
             CU(cudaMemcpyAsync(h + 32, w.est, s * 8, cudaMemcpyDeviceToHost, cs), "read estimates");
             CU(cudaMemcpyAsync(h + 48, w.flag, 4, cudaMemcpyDeviceToHost, cs), "read flag");
             CU(cudaStreamSynchronize(cs), "sync");
@@ -1199,13 +1209,19 @@ extern "C" spai_status spai_block_gram(spai_ctx ctx, int32_t s, int32_t n, int32
     void *vdig = base + scratch + pbytes, *wdig = base + scratch + pbytes + vd;
     const int chunks = krylov_chunks(n);
     if (!tcm) {
-        KL(launch_block_dot(ctx->stream, s, n, nblk, V, W, partial, H, chunks), "gram");
+        const double nsd = (double)n * s;
+        PKL("block_dot", 2.0 * nsd * s * nblk, 8.0 * nsd * (nblk + 1),
+            launch_block_dot(ctx->stream, s, n, nblk, V, W, partial, H, chunks), "gram");
     } else {
         CU(cudaMemsetAsync(ws, 0, scratch, ctx->stream), "clear scratch");
+        const double nsd = (double)n * s;
         for (int i = 0; i < nblk; ++i)
-            KL(launch_to_digits(ctx->stream, n, V + (size_t)i * n * s, nullptr, vdig, nblk, i, ctx->d_err), "digits");
-        KL(launch_w_digits(ctx->stream, n, W, wdig, ws, ctx->d_err), "W digits");
-        KL(launch_block_dot_tc(ctx->stream, n, nblk, vdig, nblk, wdig, ws, partial, H, ctx->d_err), "tensor gram");
+            PKL("to_digits", 0.0, 26.0 * nsd,
+                launch_to_digits(ctx->stream, n, V + (size_t)i * n * s, nullptr, vdig, nblk, i, ctx->d_err),
+                "digits");
+        PKL("w_digits", 0.0, 34.0 * nsd, launch_w_digits(ctx->stream, n, W, wdig, ws, ctx->d_err), "W digits");
+        PKL("block_dot_tc", 2.0 * nsd * s * nblk, 8.0 * nsd * (nblk + 1),
+            launch_block_dot_tc(ctx->stream, n, nblk, vdig, nblk, wdig, ws, partial, H, ctx->d_err), "tensor gram");
     }
     int h = 0;
     if ((st = read_err(ctx, &h))) return st;
@@ -1228,7 +1244,9 @@ extern "C" spai_status spai_block_update(spai_ctx ctx, int32_t s, int32_t n, int
     if (((uintptr_t)V | (uintptr_t)W | (uintptr_t)H) & 15)
         return fail(ctx, SPAI_EINVAL, "V, W and H must be 16-byte aligned");
     if (method == SPAI_ORTH_FP64) {
-        KL(launch_block_update(ctx->stream, s, n, nblk, V, H, W, W, sign), "block update");
+        const double nsd = (double)n * s;
+        PKL("block_update", 2.0 * nsd * s * nblk, 8.0 * nsd * (nblk + 2),
+            launch_block_update(ctx->stream, s, n, nblk, V, H, W, W, sign), "block update");
     } else {
         auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
         const size_t vd = r256(tc_digit_bytes(n, nblk)), ud = r256(tc_udig_bytes(n, nblk));
@@ -1240,11 +1258,14 @@ extern "C" spai_status spai_block_update(spai_ctx ctx, int32_t s, int32_t n, int
         void *vdig = base, *udig = base + vd, *hdig = base + vd + ud, *zeros = base + vd + ud + hd;
         int32_t *hexp = (int32_t *)(base + vd + ud + hd + 2048);
         CU(cudaMemsetAsync(zeros, 0, 2048, ctx->stream), "clear zeros");
+        const double nsd = (double)n * s;
         for (int i = 0; i < nblk; ++i)
-            KL(launch_to_digits(ctx->stream, n, V + (size_t)i * n * s, nullptr, vdig, nblk, i, ctx->d_err, udig),
-               "digits");
-        KL(launch_block_update_tc(ctx->stream, n, nblk, udig, nblk, H, hdig, hexp, zeros, W, W, sign, ctx->d_err),
-           "tensor block update");
+            PKL("to_digits", 0.0, 26.0 * nsd,
+                launch_to_digits(ctx->stream, n, V + (size_t)i * n * s, nullptr, vdig, nblk, i, ctx->d_err, udig),
+                "digits");
+        PKL("block_update_tc", 2.0 * nsd * s * nblk, 8.0 * nsd * (nblk + 2),
+            launch_block_update_tc(ctx->stream, n, nblk, udig, nblk, H, hdig, hexp, zeros, W, W, sign, ctx->d_err),
+            "tensor block update");
     }
     int h = 0;
     spai_status st = read_err(ctx, &h);

@@ -116,11 +116,9 @@ int launch_chol_small(cudaStream_t st, int32_t s, const double *G, const double 
 int launch_trsm_rows(cudaStream_t st, int32_t s, int32_t n, const double *W, const double *R,
                      const int32_t *deflated, double *out);
 int launch_triu_mul(cudaStream_t st, int32_t s, const double *R2, const double *R1, double *out);
-int launch_add_small(cudaStream_t st, int32_t count, const double *a, const double *b, double *out);
-int launch_copy_hcol(cudaStream_t st, int32_t s, int32_t j, int32_t ldh, const double *Hup,
-                     const double *Rsub, double *Hcol);
-int launch_arnoldi_ls(cudaStream_t st, int32_t s, int32_t j, int32_t m, double *Hcol,
-                      double *Qs, double *Rtri, double *G, const double *thresh, double *est,
+// projected least squares of block column j (Hessenberg column = H1 + H2 over Rsub)
+int launch_arnoldi_ls(cudaStream_t st, int32_t s, int32_t j, int32_t m, const double *H1, const double *H2,
+                      const double *Rsub, double *Qs, double *Rtri, double *G, const double *thresh, double *est,
                       int32_t *flag);
 int launch_set_rhs(cudaStream_t st, int32_t s, int32_t m, const double *S0, double *G);
 int launch_backsolve(cudaStream_t st, int32_t s, int32_t J, int32_t ldr, const double *Rtri,
