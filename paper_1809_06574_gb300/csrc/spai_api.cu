@@ -904,10 +904,8 @@ struct SolveWs {
     double *Bw, *Xw, *W, *Z, *T0, *T1, *V;
     double *partial, *H1, *H2, *G1, *R1, *R2, *Rn, *ref2, *nrm2, *thresh, *Qs, *Rtri, *G, *Y, *est;
     int32_t *defl1, *defl2, *flag;
-    void *tc_scratch;  // column exponents of the tensor-core Gram product (zeroed per solve)
-    void *vdig, *wdig; // digit pieces of the basis blocks and of W (tensor-core Gram product)
-    void *udig, *hdig, *zeros;  // row-tile-major basis digits, H digits, 2 KB of zeros
-    int32_t *hexp;              // column exponents of H
+    void *hdig;     // digit pieces of H (tensor-core block update)
+    int32_t *hexp;  // column exponents of H
 };
 
 size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks)
@@ -951,13 +949,8 @@ size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks
     w.defl1 = (int32_t *)take(s * 4);
     w.defl2 = (int32_t *)take(s * 4);
     w.flag = (int32_t *)take(64);
-    w.tc_scratch = take(tc_scratch_bytes());
     const bool digits = block_dot_tc_supported(s);
-    w.vdig = take(digits ? tc_digit_bytes(n, m + 1) : 16);
-    w.wdig = take(digits ? tc_digit_bytes(n, 1) : 16);
-    w.udig = take(digits ? tc_udig_bytes(n, m + 1) : 16);
     w.hdig = take(digits ? tc_hdig_bytes(m + 1) : 16);
-    w.zeros = take(2048);
     w.hexp = (int32_t *)take(64);
     return off;
 }
@@ -1011,23 +1004,13 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
     const bool b_dev = is_device_ptr(B), x_dev = is_device_ptr(X);
     if (opts->orth < SPAI_ORTH_AUTO || opts->orth > SPAI_ORTH_TENSOR)
         return fail(ctx, SPAI_EINVAL, "unknown orthogonalisation method %d", opts->orth);
-    CU(cudaMemsetAsync(w.tc_scratch, 0, tc_scratch_bytes(), cs), "clear scratch");
-    CU(cudaMemsetAsync(w.zeros, 0, 2048, cs), "clear zeros");
-    // tensor-core Gram products need every basis block as digit pieces
     const bool use_digits = block_dot_tc_supported(s) && opts->orth != SPAI_ORTH_FP64;
-    auto make_digits = [&](int blk) -> spai_status {
-        if (!use_digits) return SPAI_OK;
-        PKL("to_digits", 0.0, 26.0 * n * s,
-            launch_to_digits(cs, n, w.V + (size_t)blk * n * s, nullptr, w.vdig, m + 1, blk, ctx->d_err, w.udig),
-            "digits");
-        return SPAI_OK;
-    };
     // out = base + sign * V_{0..nb-1} H: tensor-core digits when available, else FP64
     auto vupdate = [&](int nb, const double *H, const double *basep, double *out, double sign) -> spai_status {
         const double f = 2.0 * n * s * s * nb;
         if (use_digits && nb <= block_update_tc_max_blocks() && (opts->orth == SPAI_ORTH_TENSOR || nb >= 2)) {
             PKL("block_update_tc", f, 8.0 * n * s * (nb + 2),
-                launch_block_update_tc(cs, n, nb, w.udig, m + 1, H, w.hdig, w.hexp, w.zeros, basep, out, sign,
+                launch_block_update_tc(cs, n, nb, w.V, H, w.hdig, w.hexp, basep, out, sign,
                                        ctx->d_err),
                 "block update");
         } else {
@@ -1082,7 +1065,6 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
         ++cycles;
         // V_0 S_0 = R (ref2 holds the residual norms^2)
         if ((st = cholqr2(ctx, w, n, s, chunks, w.W, w.V, w.Rn, w.ref2))) return st;
-        if ((st = make_digits(0))) return st;
         PKL("small_dense", 0.0, 0.0, launch_set_rhs(cs, s, m, w.Rn, w.G), "rhs");
         int J = 0;
         for (int j = 0; j < m; ++j) {
@@ -1099,24 +1081,16 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
             const double nb = j + 1;
             const bool tc = use_digits && (opts->orth == SPAI_ORTH_TENSOR || j + 1 >= 2);
             if (tc) {
-                PKL("w_digits", 0.0, 16.0 * nsd + 18.0 * nsd,
-                    launch_w_digits(cs, n, w.W, w.wdig, w.tc_scratch, ctx->d_err), "W digits");
                 PKL("block_dot_tc", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
-                    launch_block_dot_tc(cs, n, j + 1, w.vdig, m + 1, w.wdig, w.tc_scratch, w.partial, w.H1,
-                                        ctx->d_err),
-                    "H1");
+                    launch_block_dot_tc(cs, n, j + 1, w.V, w.W, w.partial, w.H1, ctx->d_err), "H1");
             } else {
                 PKL("block_dot", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
                     launch_block_dot(cs, s, n, j + 1, w.V, w.W, w.partial, w.H1, chunks), "H1");
             }
             if ((st = vupdate(j + 1, w.H1, w.W, w.W, -1.0))) return st;
             if (tc) {
-                PKL("w_digits", 0.0, 16.0 * nsd + 18.0 * nsd,
-                    launch_w_digits(cs, n, w.W, w.wdig, w.tc_scratch, ctx->d_err), "W digits");
                 PKL("block_dot_tc", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
-                    launch_block_dot_tc(cs, n, j + 1, w.vdig, m + 1, w.wdig, w.tc_scratch, w.partial, w.H2,
-                                        ctx->d_err),
-                    "H2");
+                    launch_block_dot_tc(cs, n, j + 1, w.V, w.W, w.partial, w.H2, ctx->d_err), "H2");
             } else {
                 PKL("block_dot", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
                     launch_block_dot(cs, s, n, j + 1, w.V, w.W, w.partial, w.H2, chunks), "H2");
@@ -1124,7 +1098,6 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
             if ((st = vupdate(j + 1, w.H2, w.W, w.W, -1.0))) return st;
             double *Vn = w.V + (size_t)(j + 1) * blk_elems;
             if ((st = cholqr2(ctx, w, n, s, chunks, w.W, Vn, w.Rn, w.ref2))) return st;
-            if (j + 1 < m && (st = make_digits(j + 1))) return st;
             PKL("arnoldi_ls", 16.0 * s * s * s * (j + 1), 0.0,
                 launch_arnoldi_ls(cs, s, j, m, w.H1, w.H2, w.Rn, w.Qs, w.Rtri, w.G, w.thresh, w.est, w.flag), "least squares");
             CU(cudaMemcpyAsync(h + 32, w.est, s * 8, cudaMemcpyDeviceToHost, cs), "read estimates");
@@ -1158,7 +1131,7 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
         int h_err = 0;
         if ((st = read_err(ctx, &h_err))) return st;
         if (h_err & ERR_TIMEOUT) return fail(ctx, SPAI_ETIMEOUT, "a bounded wait in the tensor-core Gram product gave up");
-        if (h_err & ERR_RANGE) return fail(ctx, SPAI_EINVAL, "basis entry out of the digit range (|v| >= 2)");
+        if (h_err & ERR_RANGE) return fail(ctx, SPAI_EINVAL, "basis entry out of the digit range (|v| >= 2) or a non-finite block");
     }
     int worst = 0;
     double worst_rel = -1.0;
@@ -1194,39 +1167,25 @@ extern "C" spai_status spai_block_gram(spai_ctx ctx, int32_t s, int32_t n, int32
         return fail(ctx, SPAI_EINVAL, "the tensor-core Gram product needs s == 8");
     if (((uintptr_t)V | (uintptr_t)W | (uintptr_t)H) & 15)
         return fail(ctx, SPAI_EINVAL, "V, W and H must be 16-byte aligned");
-    auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t a = dot_partial_elems(s, nblk) * 8;
     const bool tcm = method == SPAI_ORTH_TENSOR;
     const size_t c = tcm ? tc_partial_elems(n, nblk) * 8 : 0;
-    const size_t scratch = r256(tc_scratch_bytes());
-    const size_t pbytes = r256(a > c ? a : c);
-    const size_t vd = tcm ? r256(tc_digit_bytes(n, nblk)) : 0, wd = tcm ? r256(tc_digit_bytes(n, 1)) : 0;
     void *ws = nullptr;
-    spai_status st = temp_blocks(ctx, scratch + pbytes + vd + wd, &ws);
+    spai_status st = temp_blocks(ctx, a > c ? a : c, &ws);
     if (st) return st;
-    char *base = (char *)ws;
-    double *partial = (double *)(base + scratch);
-    void *vdig = base + scratch + pbytes, *wdig = base + scratch + pbytes + vd;
-    const int chunks = krylov_chunks(n);
+    double *partial = (double *)ws;
+    const double nsd = (double)n * s;
     if (!tcm) {
-        const double nsd = (double)n * s;
         PKL("block_dot", 2.0 * nsd * s * nblk, 8.0 * nsd * (nblk + 1),
-            launch_block_dot(ctx->stream, s, n, nblk, V, W, partial, H, chunks), "gram");
+            launch_block_dot(ctx->stream, s, n, nblk, V, W, partial, H, krylov_chunks(n)), "gram");
     } else {
-        CU(cudaMemsetAsync(ws, 0, scratch, ctx->stream), "clear scratch");
-        const double nsd = (double)n * s;
-        for (int i = 0; i < nblk; ++i)
-            PKL("to_digits", 0.0, 26.0 * nsd,
-                launch_to_digits(ctx->stream, n, V + (size_t)i * n * s, nullptr, vdig, nblk, i, ctx->d_err),
-                "digits");
-        PKL("w_digits", 0.0, 34.0 * nsd, launch_w_digits(ctx->stream, n, W, wdig, ws, ctx->d_err), "W digits");
         PKL("block_dot_tc", 2.0 * nsd * s * nblk, 8.0 * nsd * (nblk + 1),
-            launch_block_dot_tc(ctx->stream, n, nblk, vdig, nblk, wdig, ws, partial, H, ctx->d_err), "tensor gram");
+            launch_block_dot_tc(ctx->stream, n, nblk, V, W, partial, H, ctx->d_err), "tensor gram");
     }
     int h = 0;
     if ((st = read_err(ctx, &h))) return st;
     if (h & ERR_TIMEOUT) return fail(ctx, SPAI_ETIMEOUT, "a bounded wait in the tensor-core Gram product gave up");
-    if (h & ERR_RANGE) return fail(ctx, SPAI_EINVAL, "a V entry is out of the digit range (|v| >= 2)");
+    if (h & ERR_RANGE) return fail(ctx, SPAI_EINVAL, "a V entry is out of the digit range (|v| >= 2) or W is not finite");
     return SPAI_OK;
 }
 
@@ -1248,23 +1207,15 @@ extern "C" spai_status spai_block_update(spai_ctx ctx, int32_t s, int32_t n, int
         PKL("block_update", 2.0 * nsd * s * nblk, 8.0 * nsd * (nblk + 2),
             launch_block_update(ctx->stream, s, n, nblk, V, H, W, W, sign), "block update");
     } else {
-        auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
-        const size_t vd = r256(tc_digit_bytes(n, nblk)), ud = r256(tc_udig_bytes(n, nblk));
-        const size_t hd = r256(tc_hdig_bytes(nblk));
+        const size_t hd = (tc_hdig_bytes(nblk) + 255) / 256 * 256;
         void *ws = nullptr;
-        spai_status st = temp_blocks(ctx, vd + ud + hd + 2048 + 256, &ws);
+        spai_status st = temp_blocks(ctx, hd + 256, &ws);
         if (st) return st;
-        char *base = (char *)ws;
-        void *vdig = base, *udig = base + vd, *hdig = base + vd + ud, *zeros = base + vd + ud + hd;
-        int32_t *hexp = (int32_t *)(base + vd + ud + hd + 2048);
-        CU(cudaMemsetAsync(zeros, 0, 2048, ctx->stream), "clear zeros");
+        void *hdig = ws;
+        int32_t *hexp = (int32_t *)((char *)ws + hd);
         const double nsd = (double)n * s;
-        for (int i = 0; i < nblk; ++i)
-            PKL("to_digits", 0.0, 26.0 * nsd,
-                launch_to_digits(ctx->stream, n, V + (size_t)i * n * s, nullptr, vdig, nblk, i, ctx->d_err, udig),
-                "digits");
         PKL("block_update_tc", 2.0 * nsd * s * nblk, 8.0 * nsd * (nblk + 2),
-            launch_block_update_tc(ctx->stream, n, nblk, udig, nblk, H, hdig, hexp, zeros, W, W, sign, ctx->d_err),
+            launch_block_update_tc(ctx->stream, n, nblk, V, H, hdig, hexp, W, W, sign, ctx->d_err),
             "tensor block update");
     }
     int h = 0;

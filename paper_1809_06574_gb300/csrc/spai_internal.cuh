@@ -134,29 +134,19 @@ int launch_gram_sym(cudaStream_t st, int32_t s, int32_t n, const double *W, doub
 int launch_reduce_chunks(cudaStream_t st, int32_t count, int chunks, const double *partial, double *out);
 
 // ---------------------------------------------------------------------- k_ozaki.cu
-// H = V_{0..nblk-1}^T W on the tensor cores with FP64-accurate digit products (s == 8).
-// Basis blocks are turned into digit pieces once (launch_to_digits, block iblk of an
-// array of ipad blocks, tc_digit_bytes(n, ipad) bytes); W per product (launch_w_digits,
-// tc_digit_bytes(n, 1) bytes, column exponents in scratch: tc_scratch_bytes(), zeroed
-// once before first use).  partial needs tc_partial_elems(n, nblk) doubles.
+// FP64-accurate products on the tensor cores (s == 8): the kernels read the FP64 blocks
+// and cut BF16 digits in shared memory.
 bool block_dot_tc_supported(int32_t s);
-size_t tc_digit_bytes(int32_t n, int32_t nblocks);
-size_t tc_scratch_bytes();
 size_t tc_partial_elems(int32_t n, int32_t nblk);
-// (udig != null: also the row-tile-major copy read by the update kernel, tc_udig_bytes)
-int launch_to_digits(cudaStream_t st, int32_t n, const double *X, const int32_t *exps, void *dig, int32_t ipad,
-                     int32_t iblk, int *d_err, void *udig = nullptr);
-// out = base + sign * V_{0..nblk-1} H on the tensor cores (base may be null): H is
-// nblk*8 x 8 ([i][a][b]); hdig needs tc_hdig_bytes(nblk), hexp 8 ints, zeros 2048 zero bytes
-size_t tc_udig_bytes(int32_t n, int32_t nblocks);
+// H = V_{0..nblk-1}^T W (H[i][a][b]); partial needs tc_partial_elems(n, nblk) doubles
+int launch_block_dot_tc(cudaStream_t st, int32_t n, int32_t nblk, const double *V, const double *W, double *partial,
+                        double *out, int *d_err);
+// out = base + sign * V_{0..nblk-1} H (base may be null, may equal out): H is nblk*8 x 8
+// ([i][a][b]); hdig needs tc_hdig_bytes(nblk) bytes, hexp 8 ints
 int block_update_tc_max_blocks();
 size_t tc_hdig_bytes(int32_t nblk);
-int launch_block_update_tc(cudaStream_t st, int32_t n, int32_t nblk, const void *udig, int32_t ipad,
-                           const double *H, void *hdig, int32_t *hexp, const void *zeros, const double *base,
-                           double *out, double sign, int *d_err);
-int launch_w_digits(cudaStream_t st, int32_t n, const double *W, void *wdig, void *scratch, int *d_err);
-int launch_block_dot_tc(cudaStream_t st, int32_t n, int32_t nblk, const void *vdig, int32_t ipad, const void *wdig,
-                        const void *scratch, double *partial, double *out, int *d_err);
+int launch_block_update_tc(cudaStream_t st, int32_t n, int32_t nblk, const double *V, const double *H, void *hdig,
+                           int32_t *hexp, const double *base, double *out, double sign, int *d_err);
 // FP64 FMA throughput probe: blocks x threads x 8 chains x iters FMAs
 int launch_fp64_probe(cudaStream_t st, int blocks, int threads, int iters, double *sink);
 
