@@ -9,20 +9,27 @@
 //  * every value is written in fixed point with 54 bits below 2^1 (V's columns are unit
 //    vectors, so |v| <= 1; W's columns are scaled by a power of two 2^-e_b so that
 //    |w| < 1) and rounded to nearest: x = sign * sum_p d_p 2^(6(8-p)-53), d_p in [0, 63];
-//  * each digit is exact in BF16; a digit product is < 2^12 and a sum of at most 4096 of
-//    them is < 2^24, so FP32 accumulation in tensor memory stays exact over a CTA's rows;
+//  * each digit is exact in BF16; the products of digits p and q are accumulated in FP32
+//    in tensor memory by weight class c = p + q (the MMA for digit p writes its products
+//    with W digit q into the columns of class p + q); a class collects at most 9 products
+//    of at most 63^2 per row, so sums over at most 464 rows stay below 2^24 and exact;
 //  * digit pairs with p + q <= 9 are kept (53 products); the dropped pairs weigh < 2^-58
 //    relative, below FP64 rounding of the same dot products;
-//  * the exact FP32 sums are combined in FP64 with their powers of two.
+//  * every <= 464 rows (a segment) four drain warps read the exact class sums out of tensor
+//    memory into two exact 64-bit integers per output, hi = sum_{c<=4} S_c 2^(6(4-c)) and
+//    lo = sum_{c>=5} S_c 2^(6(9-c)), and at the end combine them in FP64 with the scale.
+//    Four accumulator buffers of 128 columns let the MMAs of the next segment run while a
+//    segment is drained.
 //
-// Both kernels stream the FP64 operands from global memory (8 bytes per value) and cut
-// the digits in shared memory: one thread issues cp.async.bulk copies of raw FP64 row
-// tiles into a ring of stages (completion counted on mbarriers), eight converter warps
-// turn each raw stage into nine BF16 digit planes laid out as the MMA's shared-memory
-// operand (a second ring), one thread issues the tcgen05.mma of every stage into tensor
-// memory and frees the digit stage with tcgen05.commit, and four warps drain tensor memory
-// into FP64.  Every wait is bounded: on time-out the kernel raises an error bit, waits
-// (bounded) for its copies in flight, frees its tensor memory and returns.
+// Every basis block is kept, besides its FP64 copy, as sign-magnitude 54-bit fixed point
+// (8 bytes per value, made once by k_to_fixed when the block is created); W is read as
+// FP64 and scaled per CTA.  Both kernels stream these 8-byte values and cut the digits in
+// shared memory: one thread issues cp.async.bulk copies of raw row tiles into a ring of
+// stages (completion counted on mbarriers), eight converter warps turn each raw stage into
+// nine BF16 digit planes laid out as the MMA's shared-memory operand (a second ring), one
+// thread issues the tcgen05.mma of every stage and frees the digit stage with
+// tcgen05.commit.  Every wait is bounded in time (1 s): on time-out the kernel raises an
+// error bit, waits (bounded) for its copies in flight, frees its tensor memory and returns.
 #include <cstdint>
 
 #include "spai_internal.cuh"
@@ -40,43 +47,53 @@ constexpr int kPiece = kS * kKT * 2;             // 256 bytes: 8 columns x 16 ro
 constexpr int kLBO = 128;                        // next core matrix along K
 constexpr int kSBO = kPiece;                     // next 8-row group (next block / digit)
 constexpr int kTmemCols = 512;
-constexpr unsigned kWaitLimit = 1u << 22;
-constexpr int kMaxRows = 4096;     // exactness bound of the FP32 sums
+constexpr int kBufCols = 128;      // one class accumulator: classes 0..10 x 8 columns
+constexpr int kBufs = kTmemCols / kBufCols;
+constexpr int kClsCols = 80;       // classes 0..9 are read; class 10 only collects padding
+constexpr int kSegK = 464;         // rows (Gram) / basis columns (update) per accumulation
+constexpr int kMaxRows = 4096;     // rows per Gram CTA: hi, lo stay below 2^53
 constexpr int kCW = 8;             // converter warps
 constexpr int kCT = 32 * kCW;      // converter threads
+constexpr int kThreadsTC = 64 + 128 + kCT;  // copy warp, MMA warp, 4 drain warps, converters
 constexpr int kRawRow = kS * 8;    // 64 bytes: one row of an n x 8 block
+constexpr unsigned long long kWaitNs = 1000000000ull;  // a bounded wait gives up after 1 s
+constexpr unsigned kSuspendNs = 20000;                  // suspend hint of one try_wait
+static_assert(9 * 63 * 63 * kSegK < (1 << 24), "exact FP32 class sums");
+static_assert(kClsCols == 5 * 16, "drain_classes reads five 16-column groups");
 
 // number of W digits q used with V digit p (q <= min(8, 9 - p)), MMA N (padded to 16)
 __host__ __device__ constexpr int nq(int p) { return (9 - p < 8 ? 9 - p : 8) + 1; }
 __host__ __device__ constexpr int nmma(int p) { return ((8 * nq(p) + 15) / 16) * 16; }
-__host__ __device__ constexpr int tcol(int p)
-{
-    int c = 0;
-    for (int i = 0; i < p; ++i) c += nmma(i);
-    return c;
-}
-static_assert(tcol(8) + nmma(8) <= kTmemCols, "tensor memory columns");
+static_assert(8 * 8 + nmma(8) <= kBufCols && 8 * 7 + nmma(7) <= kBufCols, "class columns");
 static_assert(nmma(0) <= 8 * (kDig + 1), "B row groups");
 
-// ---- Gram kernel shared memory: raw ring | digit ring | barriers | flag | tmem | exps | maxima
-constexpr int kDThreads = 64 + kCT;                         // copy warp, MMA warp, converters
-constexpr int kRawBlk = kKT * kRawRow;                      // 1 KB: 16 rows of one block
-constexpr int kRawStage = (kBlocksPerTile + 1) * kRawBlk;   // 16 V blocks + W
-constexpr int kRawStages = 5;
-constexpr int kAPlane = kBlocksPerTile * kPiece;            // 4 KB
-constexpr int kABytes = kDig * kAPlane;                     // 36 KB
-constexpr int kBBytes = (kDig + 1) * kPiece;                // 9 W digits + a zero row group
-constexpr int kDigStage = kABytes + kBBytes;                // 39424
-constexpr int kDigStages = 3;
-constexpr int kDOffDig = kRawStages * kRawStage;
-constexpr int kDOffBar = kDOffDig + kDigStages * kDigStage;
-constexpr int kDOffFlag = kDOffBar + 2 * (kRawStages + kDigStages) * 8;
+// ---- Gram kernel shared memory: raw ring | digit ring | slack | barriers | flag | tmem | exps | maxima
+constexpr int kDRawStage = 24 * 1024;   // raw rows of S sub-tiles x (blocks + W)
+constexpr int kDRawStages = 3;
+constexpr int kDDigStage = 42 * 1024;   // digit pieces of S sub-tiles
+constexpr int kDDigStages = 3;
+constexpr int kDOffDig = kDRawStages * kDRawStage;
+constexpr int kDOffBar = kDOffDig + kDDigStages * kDDigStage + 4096;  // + slack read by M = 128 MMAs
+constexpr int kDBars = 2 * (kDRawStages + kDDigStages + kBufs);
+constexpr int kDOffFlag = kDOffBar + kDBars * 8;
 constexpr int kDOffTmem = kDOffFlag + 8;
 constexpr int kDOffExp = kDOffTmem + 8;
 constexpr int kDOffMax = kDOffExp + kS * 4;
 constexpr int kDSmem = kDOffMax + kCW * kS * 8;
 static_assert(kDSmem <= 227 * 1024, "Gram kernel shared memory");
-static_assert(kDOffDig % 16 == 0 && kDigStage % 16 == 0 && kDOffBar % 8 == 0, "alignment");
+static_assert(kDOffDig % 16 == 0 && kDDigStage % 16 == 0 && kDOffBar % 8 == 0, "alignment");
+
+// bytes of one sub-tile's digit pieces for nvb blocks: A planes + 9 W digits + a zero group
+__host__ __device__ constexpr int dsub_bytes(int nvb) { return kDig * nvb * kPiece + (kDig + 1) * kPiece; }
+// sub-tiles per stage: the stage carries >= ~240 digit groups of 8 values when it can
+__host__ __device__ inline int dsubs_per_stage(int nvb)
+{
+    const int a = kDDigStage / dsub_bytes(nvb), b = kDRawStage / ((nvb + 1) * kKT * kRawRow);
+    const int s = a < b ? a : b;
+    return s < 1 ? 1 : s;
+}
+static_assert(kDDigStage >= dsub_bytes(kBlocksPerTile) && kDRawStage >= (kBlocksPerTile + 1) * kKT * kRawRow,
+              "one full sub-tile per stage");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -109,25 +126,125 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t 
         "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
 }
 
+
+__host__ __device__ constexpr uint32_t make_idesc_amn(int M, int N) { return make_idesc(M, N) | (1u << 15); }
+
+// MN-major descriptor of the update kernel's A operand (basis rows): next 8 basis columns
+// (next block) 2 KB on, next 8 rows 128 bytes on
+__device__ __forceinline__ uint64_t make_desc_mn(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(((8 * kPiece) >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((128 >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred P1;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2, %3;\n\t"
         "selp.b32 %0, 1, 0, P1;\n\t}\n"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
 
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// wait for the phase of the given parity; false after kWaitNs without it
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
 {
-    unsigned it = 0;
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(bar, parity))
-        if (++it >= kWaitLimit) return false;
+        if (global_ns() - t0 > kWaitNs) return false;
     return true;
+}
+
+// a warp's bounded wait on one mbarrier phase; the verdict is the same in every lane
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity)
+{
+    return __all_sync(0xffffffffu, mbar_wait_bounded(bar, parity)) != 0;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t v[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+
+// Add the class sums of one accumulator buffer (this thread's tensor-memory row) into the
+// exact integers hi, lo of its 8 output columns.  |S_c| < 2^24: exact FP32 integers.
+__device__ __forceinline__ void drain_classes(uint32_t tbuf, long long hi[kS], long long lo[kS])
+{
+    uint32_t v[3][16];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) tmem_ld16(tbuf + 16 * k, v[k]);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const int col = 16 * k + c, cls = col >> 3, b = col & 7;
+            const long long d = (long long)__float2int_rz(__uint_as_float(v[k][c]));
+            if (cls <= 4) hi[b] += d << (6 * (4 - cls));
+            else lo[b] += d << (6 * (9 - cls));
+        }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) tmem_ld16(tbuf + 48 + 16 * k, v[k]);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const int col = 48 + 16 * k + c, cls = col >> 3, b = col & 7;
+            const long long d = (long long)__float2int_rz(__uint_as_float(v[k][c]));
+            if (cls <= 4) hi[b] += d << (6 * (4 - cls));
+            else lo[b] += d << (6 * (9 - cls));
+        }
+}
+
+// value of the digit products times 2^e: hi carries weights 2^-10..2^-34 (-> hi 2^-34),
+// lo 2^-40..2^-64 (-> lo 2^-64); |hi|, |lo| < 2^53 convert exactly, and 2^e is a normal
+// double for the exponents of finite nonzero columns (a zero column has e = 0)
+__device__ __forceinline__ double combine_hilo(long long hi, long long lo, int e)
+{
+    const double v = fma((double)hi, 0x1p-34, (double)lo * 0x1p-64);
+    return v * __longlong_as_double((long long)(1023 + e) << 52);
 }
 
 __device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
@@ -173,70 +290,78 @@ __device__ __forceinline__ uint32_t digit_bf16(uint32_t d, uint32_t neg)
     return (__float_as_uint(f) >> 16) | (neg << 15);
 }
 
-
-// Digits of 8 values (8 consecutive rows of one column, scaled by 2^-e) as one 16-byte
-// chunk per digit plane at dst + p * pstride (8 BF16 along the rows).  False if a value
-// is out of range (|x| 2^-e >= 2, or not finite).
-__device__ __forceinline__ bool convert8(const double x[8], int e, char *dst, int pstride)
+// Sign-magnitude fixed point of x: bit 63 = sign, bits 0..53 = round(|x| 2^(53-e)).
+// False if |x| 2^-e >= 2 or x is not finite.
+__device__ __forceinline__ bool to_fixed(double x, int e, uint64_t &f)
 {
-    uint64_t mag[8];
-    uint32_t neg[8];
-    bool ok = true;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) ok &= fixed_mag(x[u], e, mag[u], neg[u]);
-#pragma unroll
-    for (int p = 0; p < kDig; ++p) {
-        const int sh = 6 * (8 - p);
-        uint32_t w[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const uint32_t lo = digit_bf16((uint32_t)(mag[2 * u] >> sh) & 63u, neg[2 * u]);
-            const uint32_t hi = digit_bf16((uint32_t)(mag[2 * u + 1] >> sh) & 63u, neg[2 * u + 1]);
-            w[u] = lo | (hi << 16);
-        }
-        *reinterpret_cast<uint4 *>(dst + p * pstride) = make_uint4(w[0], w[1], w[2], w[3]);
-    }
+    uint64_t mag;
+    uint32_t neg;
+    const bool ok = fixed_mag(x, e, mag, neg);
+    f = ((uint64_t)neg << 63) | mag;
     return ok;
 }
 
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+// Nine BF16 digit planes of 8 fixed-point values (8 consecutive rows of one column), one
+// 16-byte chunk per plane at dst + p * pstride.  A digit d becomes the float 2^23 + d (its
+// bits OR-ed into the exponent pattern of 2^23, sign included) minus 2^23, both exact; the
+// BF16 is the float's upper half, and two of them are packed with one byte permute.
+__device__ __forceinline__ void expand8(const uint64_t f[8], char *dst, int pstride)
 {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+    uint32_t hi[8], lo[8], mg[8];
+    float bs[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        lo[u] = (uint32_t)f[u];
+        hi[u] = (uint32_t)(f[u] >> 32);
+        mg[u] = 0x4B000000u | (hi[u] & 0x80000000u);
+        bs[u] = (hi[u] >> 31) ? 8388608.0f : -8388608.0f;
+    }
+#pragma unroll
+    for (int p = 0; p < kDig; ++p) {
+        const int sh = 6 * (8 - p);
+        uint32_t fb[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            uint32_t d;
+            if (sh >= 32)
+                d = hi[u] >> (sh - 32);
+            else if (sh > 26)
+                d = __funnelshift_r(lo[u], hi[u], sh);
+            else
+                d = lo[u] >> sh;
+            fb[u] = __float_as_uint(__uint_as_float((d & 63u) | mg[u]) + bs[u]);
+        }
+        uint4 w;
+        w.x = __byte_perm(fb[0], fb[1], 0x7632);
+        w.y = __byte_perm(fb[2], fb[3], 0x7632);
+        w.z = __byte_perm(fb[4], fb[5], 0x7632);
+        w.w = __byte_perm(fb[6], fb[7], 0x7632);
+        *reinterpret_cast<uint4 *>(dst + p * pstride) = w;
+    }
 }
 
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+// fixed-point copy of n x 8 blocks (count values): |x| < 2 required (ERR_RANGE otherwise)
+__global__ void k_to_fixed(int64_t count, const double *__restrict__ X, uint64_t *__restrict__ F, int *err)
 {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t f;
+        if (!to_fixed(X[i], 0, f)) bad = true;
+        F[i] = f;
+    }
+    if (bad) atomicOr(err, ERR_RANGE);
 }
 
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
 
-__device__ __forceinline__ void mma_commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-// a warp's bounded wait on one mbarrier phase; the verdict is the same in every lane
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity)
-{
-    return __all_sync(0xffffffffu, mbar_wait_bounded(bar, parity)) != 0;
-}
-
-template <bool kSmall>
-__device__ __forceinline__ void drain_hilo(uint32_t tmem, int quarter, long long hi[kS], long long lo[kS]);
-__device__ __forceinline__ double combine_hilo(long long hi, long long lo, int e);
-
-// Gram product H_i = V_i^T W from FP64 operands.  grid = (row chunks, M tiles of 16
-// blocks); a chunk is a whole number of 16-row sub-tiles, at most 4096 rows.  Warp 0
-// copies, warp 1 issues MMAs, warps 2..9 convert (and 2..5 drain tensor memory at the
-// end).  W's columns are scaled by powers of two from this chunk's own column maxima, so
-// the chunk's partial sums carry their own scale.
-__global__ void __launch_bounds__(kDThreads, 1)
-    k_block_dot_tc(int32_t n, int32_t nblk, int32_t subs_per_chunk, const double *__restrict__ V,
+// Gram product H_i = V_i^T W.  grid = (row chunks, M tiles of 16 blocks); a chunk is a
+// whole number of 16-row sub-tiles, at most 4096 rows.  A stage carries S sub-tiles (S
+// from the tile's block count, so that small products still fill the converters); a
+// segment of whole stages covers at most 464 rows and owns one accumulator buffer.
+// Warp 0 copies, warp 1 issues MMAs, warps 2..5 drain, warps 6..13 convert.  W's columns
+// are scaled by powers of two from this chunk's own column maxima, so the chunk's partial
+// sums carry their own scale.
+__global__ void __launch_bounds__(kThreadsTC, 1)
+    k_block_dot_tc(int32_t n, int32_t nblk, int32_t subs_per_chunk, const uint64_t *__restrict__ Vf,
                    const double *__restrict__ W, double *__restrict__ partial, int *err)
 {
     extern __shared__ __align__(128) char smem[];
@@ -247,8 +372,15 @@ __global__ void __launch_bounds__(kDThreads, 1)
     const int nsub = (int)min((int64_t)subs_per_chunk, nt - t0);
     const int blk0 = mt * kBlocksPerTile;
     const int nvb = min(kBlocksPerTile, nblk - blk0);  // valid blocks in this tile
-    const uint32_t rfull0 = smem_u32(smem + kDOffBar), rempty0 = rfull0 + kRawStages * 8;
-    const uint32_t dfull0 = rempty0 + kRawStages * 8, dempty0 = dfull0 + kDigStages * 8;
+    const int S = dsubs_per_stage(nvb);
+    const int sub_bytes = dsub_bytes(nvb), plane = nvb * kPiece;
+    const int nst = (nsub + S - 1) / S;                // stages
+    const int sps = (kSegK / kKT) / S;                 // stages per segment (>= 2: S <= 12)
+    const int nseg = (nst + sps - 1) / sps;
+    const uint32_t bar0 = smem_u32(smem + kDOffBar);
+    const uint32_t rfull0 = bar0, rempty0 = rfull0 + kDRawStages * 8;
+    const uint32_t dfull0 = rempty0 + kDRawStages * 8, dempty0 = dfull0 + kDDigStages * 8;
+    const uint32_t bfull0 = dempty0 + kDDigStages * 8, bfree0 = bfull0 + kBufs * 8;
     volatile int *flag = reinterpret_cast<volatile int *>(smem + kDOffFlag);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kDOffTmem);
     int32_t *wexp = reinterpret_cast<int32_t *>(smem + kDOffExp);
@@ -260,22 +392,28 @@ __global__ void __launch_bounds__(kDThreads, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int s = 0; s < kRawStages; ++s) {
+        for (int s = 0; s < kDRawStages; ++s) {
             mbar_init(rfull0 + 8 * s, 1);
             mbar_init(rempty0 + 8 * s, kCW);
         }
-        for (int s = 0; s < kDigStages; ++s) {
+        for (int s = 0; s < kDDigStages; ++s) {
             mbar_init(dfull0 + 8 * s, kCW);
             mbar_init(dempty0 + 8 * s, 1);
+        }
+        for (int b = 0; b < kBufs; ++b) {
+            mbar_init(bfull0 + 8 * b, 1);
+            mbar_init(bfree0 + 8 * b, 128);
         }
         asm volatile("fence.mbarrier_init.release.cluster;");
         *flag = 0;
     }
-    // zero row group 9 of every B stage (MMAs with N = 80 read it; converters never write it)
-    for (int e = tid; e < kDigStages * (kPiece / 16); e += kDThreads) {
-        const int s = e / (kPiece / 16), o = e % (kPiece / 16);
-        *reinterpret_cast<uint4 *>(smem + kDOffDig + s * kDigStage + kABytes + kDig * kPiece + o * 16) =
-            make_uint4(0, 0, 0, 0);
+    // zero row group 9 of every sub-tile's B operand (MMAs with N = 80 read it; the
+    // converters never write it)
+    for (int e = tid; e < kDDigStages * S * (kPiece / 16); e += kThreadsTC) {
+        const int o = e % (kPiece / 16), sd = e / (kPiece / 16);
+        const int d = sd / S, sg = sd % S;
+        *reinterpret_cast<uint4 *>(smem + kDOffDig + d * kDDigStage + sg * sub_bytes + kDig * plane + kDig * kPiece +
+                                   o * 16) = make_uint4(0, 0, 0, 0);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -285,60 +423,111 @@ __global__ void __launch_bounds__(kDThreads, 1)
     const bool work = nvb > 0 && nsub > 0;
 
     if (warp == 0) {
-        if (lane == 0 && work) {  // ---- copies of sub-tile u into raw stage u % kRawStages
+        if (lane == 0 && work) {  // ---- copies of stage k into raw stage k % kDRawStages
             int issued = 0;
-            for (int u = 0; u < nsub; ++u) {
-                const int s = u % kRawStages;
-                if (u >= kRawStages &&
-                    !mbar_wait_bounded(rempty0 + 8 * s, (uint32_t)(((u - kRawStages) / kRawStages) & 1))) {
+            for (int k = 0; k < nst; ++k) {
+                const int s = k % kDRawStages;
+                if (k >= kDRawStages &&
+                    !mbar_wait_bounded(rempty0 + 8 * s, (uint32_t)(((k - kDRawStages) / kDRawStages) & 1))) {
                     *flag = 1;
                     break;
                 }
                 if (*flag) break;
-                const int64_t t = t0 + u;
-                const uint32_t bytes = (uint32_t)min((int64_t)kKT, (int64_t)n - t * kKT) * kRawRow;
+                const int ns = min(S, nsub - k * S);
+                uint32_t total = 0;
+                for (int sg = 0; sg < ns; ++sg) {
+                    const int64_t t = t0 + (int64_t)k * S + sg;
+                    total += (uint32_t)(nvb + 1) * (uint32_t)min((int64_t)kKT, (int64_t)n - t * kKT) * kRawRow;
+                }
                 const uint32_t fb = rfull0 + 8 * s;
-                mbar_expect_tx(fb, (uint32_t)(nvb + 1) * bytes);
-                char *st = smem + s * kRawStage;
+                mbar_expect_tx(fb, total);
+                char *st = smem + s * kDRawStage;
 #pragma unroll 1
-                for (int i = 0; i < nvb; ++i)
-                    bulk_copy(smem_u32(st + i * kRawBlk), V + ((int64_t)(blk0 + i) * n + t * kKT) * kS, bytes, fb);
-                bulk_copy(smem_u32(st + kBlocksPerTile * kRawBlk), W + t * kKT * kS, bytes, fb);
-                issued = u + 1;
+                for (int sg = 0; sg < ns; ++sg) {
+                    const int64_t t = t0 + (int64_t)k * S + sg;
+                    const uint32_t bytes = (uint32_t)min((int64_t)kKT, (int64_t)n - t * kKT) * kRawRow;
+                    char *sb = st + sg * (nvb + 1) * (kKT * kRawRow);
+#pragma unroll 1
+                    for (int i = 0; i < nvb; ++i)
+                        bulk_copy(smem_u32(sb + i * (kKT * kRawRow)), Vf + ((int64_t)(blk0 + i) * n + t * kKT) * kS,
+                                  bytes, fb);
+                    bulk_copy(smem_u32(sb + nvb * (kKT * kRawRow)), W + t * kKT * kS, bytes, fb);
+                }
+                issued = k + 1;
             }
             // every copy issued must have landed before shared memory is released
-            for (int u = issued - kRawStages < 0 ? 0 : issued - kRawStages; u < issued; ++u)
-                if (!mbar_wait_bounded(rfull0 + 8 * (u % kRawStages), (uint32_t)((u / kRawStages) & 1))) *flag = 1;
+            for (int k = issued - kDRawStages < 0 ? 0 : issued - kDRawStages; k < issued; ++k)
+                if (!mbar_wait_bounded(rfull0 + 8 * (k % kDRawStages), (uint32_t)((k / kDRawStages) & 1))) *flag = 1;
         }
     } else if (warp == 1) {
         if (lane == 0 && work) {  // ---- MMA issuer
             int done = 0;
-            for (int u = 0; u < nsub; ++u) {
-                const int d = u % kDigStages;
-                if (!mbar_wait_bounded(dfull0 + 8 * d, (uint32_t)((u / kDigStages) & 1))) {
+            for (int k = 0; k < nst; ++k) {
+                const int d = k % kDDigStages, seg = k / sps, buf = seg % kBufs;
+                const bool first = k % sps == 0;
+                if (first && seg >= kBufs &&
+                    !mbar_wait_bounded(bfree0 + 8 * buf, (uint32_t)((seg / kBufs - 1) & 1))) {
                     *flag = 1;
                     break;
                 }
-                if (*flag) break;
+                if (!mbar_wait_bounded(dfull0 + 8 * d, (uint32_t)((k / kDDigStages) & 1)) || *flag) {
+                    *flag = 1;
+                    break;
+                }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const char *st = smem + kDOffDig + d * kDigStage;
+                const char *st = smem + kDOffDig + d * kDDigStage;
+                const int ns = min(S, nsub - k * S);
+                for (int sg = 0; sg < ns; ++sg) {
+                    const char *sb = st + sg * sub_bytes;
+                    const uint64_t db = make_desc(smem_u32(sb + kDig * plane));
 #pragma unroll
-                for (int p = 0; p < kDig; ++p) {
-                    const uint64_t da = make_desc(smem_u32(st + p * kAPlane));
-                    const uint64_t db = make_desc(smem_u32(st + kABytes));
-                    mma_bf16(tmem + tcol(p), da, db, make_idesc(kM, nmma(p)), u > 0 ? 1u : 0u);
+                    for (int p = 0; p < kDig; ++p) {
+                        const uint64_t da = make_desc(smem_u32(sb + p * plane));
+                        mma_bf16(tmem + buf * kBufCols + 8 * p, da, db, make_idesc(kM, nmma(p)),
+                                 (first && sg == 0 && p == 0) ? 0u : 1u);
+                    }
                 }
                 mma_commit(dempty0 + 8 * d);
-                done = u + 1;
+                if (k % sps == sps - 1 || k == nst - 1) mma_commit(bfull0 + 8 * buf);
+                done = k + 1;
             }
-            // the last commit: all MMAs done before tensor memory is read
+            // the last commit: all MMAs done before shared memory is released
             if (done > 0) {
-                const int u = done - 1;
-                if (!mbar_wait_bounded(dempty0 + 8 * (u % kDigStages), (uint32_t)((u / kDigStages) & 1))) *flag = 1;
+                const int k = done - 1;
+                if (!mbar_wait_bounded(dempty0 + 8 * (k % kDDigStages), (uint32_t)((k / kDDigStages) & 1))) *flag = 1;
+            }
+        }
+    } else if (warp < 6) {  // ---- drain warps: tensor-memory lanes 32 (warp % 4) .. + 31 = basis columns
+        if (work) {
+            const int quarter = warp & 3;
+            long long hi[kS], lo[kS];
+#pragma unroll
+            for (int b = 0; b < kS; ++b) hi[b] = lo[b] = 0;
+            bool ok = true;
+            for (int seg = 0; seg < nseg; ++seg) {
+                const int buf = seg % kBufs;
+                if (!mbar_wait_bounded(bfull0 + 8 * buf, (uint32_t)((seg / kBufs) & 1)) || *flag) {
+                    *flag = 1;
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                drain_classes(tmem + ((uint32_t)(quarter * 32) << 16) + buf * kBufCols, hi, lo);
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                mbar_arrive(bfree0 + 8 * buf);
+            }
+            // the chunk's W scale is known once the converters have started (named barrier 1)
+            asm volatile("bar.sync 2, %0;" ::"r"(128 + kCT) : "memory");
+            const int m = quarter * 32 + lane;
+            if (ok && m < nvb * kS) {
+                const int gm = blk0 * kS + m;
+                double *dst = partial + ((int64_t)chunk * nblk + (gm >> 3)) * (kS * kS) + (gm & 7) * kS;
+#pragma unroll
+                for (int b = 0; b < kS; ++b) dst[b] = combine_hilo(hi[b], lo[b], wexp[b]);
             }
         }
     } else if (work) {  // ---- converters
-        const int ct = tid - 64, cw = warp - 2;
+        const int ct = tid - 192, cw = warp - 6;
         // W column maxima over this chunk's rows -> exponents e_b with |w| < 2^e_b
         {
             unsigned long long mx[kS];
@@ -375,33 +564,44 @@ __global__ void __launch_bounds__(kDThreads, 1)
                 wexp[ct] = (ex == 0 || ex == 0x7FF) ? 0 : ex - 1022;
             }
             asm volatile("bar.sync 1, %0;" ::"r"(kCT) : "memory");
+            asm volatile("bar.arrive 2, %0;" ::"r"(128 + kCT) : "memory");  // exps ready for the drain warps
         }
-        const int groups = (nvb + 1) * 16;  // (block slot, 8-row half, column); slot nvb = W
+        const int gps = 16 * (nvb + 1);  // digit groups per sub-tile: (block slot, 8-row half, column)
         bool bad = false;
-        for (int u = 0; u < nsub; ++u) {
-            const int s = u % kRawStages, d = u % kDigStages;
-            bool ok = warp_wait(rfull0 + 8 * s, (uint32_t)((u / kRawStages) & 1));
-            if (ok && u >= kDigStages) ok = warp_wait(dempty0 + 8 * d, (uint32_t)(((u - kDigStages) / kDigStages) & 1));
+        for (int k = 0; k < nst; ++k) {
+            const int s = k % kDRawStages, d = k % kDDigStages;
+            bool ok = warp_wait(rfull0 + 8 * s, (uint32_t)((k / kDRawStages) & 1));
+            if (ok && k >= kDDigStages)
+                ok = warp_wait(dempty0 + 8 * d, (uint32_t)(((k - kDDigStages) / kDDigStages) & 1));
             if (!ok || *flag) {
                 if (lane == 0) *flag = 1;
                 break;
             }
-            const int64_t t = t0 + u;
-            const int rv = (int)min((int64_t)kKT, (int64_t)n - t * kKT);
-            const char *raw = smem + s * kRawStage;
-            char *dig = smem + kDOffDig + d * kDigStage;
-            const int rot = (u * 16) & (kCT - 1);  // spreads the extra groups over the warps
-            for (int g = (ct - rot) & (kCT - 1); g < groups; g += kCT) {
-                const int i = g >> 4, ko = (g >> 3) & 1, a = g & 7;
-                const bool isw = i == nvb;
-                const double *src =
-                    reinterpret_cast<const double *>(raw + (isw ? kBlocksPerTile : i) * kRawBlk) + ko * 8 * kS + a;
-                double x[8];
+            const int ns = min(S, nsub - k * S);
+            const char *raw = smem + s * kDRawStage;
+            char *dig = smem + kDOffDig + d * kDDigStage;
+            const int rot = (k * 32) & (kCT - 1);  // spreads the extra groups over the warps
+            for (int g = (ct - rot) & (kCT - 1); g < ns * gps; g += kCT) {
+                const int sg = g / gps, r = g % gps;
+                const int i = r >> 4, ko = (r >> 3) & 1, a = r & 7;
+                const int64_t t = t0 + (int64_t)k * S + sg;
+                const int rv = (int)min((int64_t)kKT, (int64_t)n - t * kKT);
+                const char *sb = raw + (sg * (nvb + 1) + i) * (kKT * kRawRow);
+                char *db = dig + sg * sub_bytes;
+                uint64_t f[8];
+                if (i == nvb) {  // W: FP64 -> fixed point with this chunk's column scale
+                    const double *src = reinterpret_cast<const double *>(sb) + ko * 8 * kS + a;
+                    const int e = wexp[a];
 #pragma unroll
-                for (int v = 0; v < 8; ++v) x[v] = (ko * 8 + v < rv) ? src[v * kS] : 0.0;
-                char *dst = isw ? dig + kABytes + ko * kLBO + a * 16
-                                : dig + i * kPiece + ko * kLBO + a * 16;
-                if (!convert8(x, isw ? wexp[a] : 0, dst, isw ? kPiece : kAPlane)) bad = true;
+                    for (int v = 0; v < 8; ++v)
+                        if (!to_fixed((ko * 8 + v < rv) ? src[v * kS] : 0.0, e, f[v])) bad = true;
+                    expand8(f, db + kDig * plane + ko * kLBO + a * 16, kPiece);
+                } else {
+                    const uint64_t *src = reinterpret_cast<const uint64_t *>(sb) + ko * 8 * kS + a;
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) f[v] = (ko * 8 + v < rv) ? src[v * kS] : 0ull;
+                    expand8(f, db + i * kPiece + ko * kLBO + a * 16, plane);
+                }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
@@ -414,72 +614,13 @@ __global__ void __launch_bounds__(kDThreads, 1)
     }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const bool failed = *flag != 0;
-    if (failed && tid == 0) atomicOr(err, ERR_TIMEOUT);
-
-    // ---- drain: warps 2..5, warp w owns tensor-memory lanes 32 (w % 4) .. + 31 = basis columns
-    if (!failed && work && warp >= 2 && warp < 6) {
-        const int quarter = warp & 3;
-        const int m = quarter * 32 + lane;
-        long long hi[kS], lo[kS];
-        drain_hilo<false>(tmem, quarter, hi, lo);
-        if (m < nvb * kS) {
-            const int gm = blk0 * kS + m;
-            double *dst = partial + ((int64_t)chunk * nblk + (gm >> 3)) * (kS * kS) + (gm & 7) * kS;
-#pragma unroll
-            for (int b = 0; b < kS; ++b) dst[b] = combine_hilo(hi[b], lo[b], wexp[b]);
-        }
-    }
+    if (*flag && tid == 0) atomicOr(err, ERR_TIMEOUT);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
     }
 }
-
-
-// ---------------------------------------------------------------------------------
-// Block update out = base + sign * V_{0..nblk-1} H on the tensor cores (W -= V H of the
-// Gram-Schmidt passes, U = V Y of the solution update), same digit scheme.  The MMA's M
-// dimension is 128 rows of V, K runs over basis columns (16 = two blocks per MMA), N over
-// H's digit planes x 8 columns.  V's digits are cut per stage from its FP64 rows and laid
-// out MN-major (8 basis columns x 8 contiguous rows per core matrix); H's digits are built
-// once per call by k_h_digits as K-major pieces, one 2304-byte group per 16 basis columns.
-// ---------------------------------------------------------------------------------
-constexpr int kUThreads = 64 + 128 + kCT;     // copy warp, MMA warp, 4 drain warps, converters
-constexpr int kURawBlk = 128 * kRawRow;       // 8 KB: 128 rows of one block
-constexpr int kURawStage = 2 * kURawBlk;      // two blocks = one K step
-constexpr int kURawStages = 5;
-constexpr int kUPlane = 2 * (8 * kPiece);     // one digit plane of a stage: 2 blocks x 2 KB
-constexpr int kUStageA = kDig * kUPlane;      // 36 KB
-constexpr int kUDigStage = kUStageA + kBBytes;  // + 9 H digit pieces + zero group
-constexpr int kUDigStages = 3;
-constexpr int kUOffDig = kURawStages * kURawStage;
-constexpr int kUOffBar = kUOffDig + kUDigStages * kUDigStage;
-constexpr int kUOffTdone = kUOffBar + 2 * (kURawStages + kUDigStages) * 8;
-constexpr int kUOffFlag = kUOffTdone + 16;
-constexpr int kUOffTmem = kUOffFlag + 8;
-constexpr int kUSmem = kUOffTmem + 16;
-static_assert(kUSmem <= 227 * 1024, "update kernel shared memory");
-static_assert(kUOffDig % 16 == 0 && kUDigStage % 16 == 0 && kUOffBar % 8 == 0, "alignment");
-constexpr int kULBO = 8 * kPiece;  // MN-major: next 8 basis columns (next block)
-constexpr int kUSBO = 128;         // MN-major: next 8 rows
-
-__device__ __forceinline__ uint64_t make_desc_mn(uint32_t saddr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((kULBO >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((kUSBO >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
-// A (V) MN-major, B (H digits) K-major
-__host__ __device__ constexpr uint32_t make_idesc_amn(int M, int N) { return make_idesc(M, N) | (1u << 15); }
-
-// exact FP32 integer (|x| < 2^24) to int
-__device__ __forceinline__ int f2i_exact(uint32_t bits) { return __float2int_rz(__uint_as_float(bits)); }
 
 // Digits of H (nblk*8 basis columns x 8, H[c * 8 + b]) scaled per column b: piece (kappa, q)
 // at hdig + (kappa * 9 + q) * 256 holds columns 16 kappa .. 16 kappa + 15 (zero beyond
@@ -529,67 +670,52 @@ __global__ void k_h_digits(int32_t nblk, const double *__restrict__ H, char *__r
     }
 }
 
-// Drain straight into two exact integers per output column: hi = sum_{c<=4} S_c 2^(6(4-c)),
-// lo = sum_{c>=5} S_c 2^(6(9-c)) (|S_c| < 2^28, so |hi|, |lo| < 2^53).  kSmall: |D| < 2^22,
-// read by the FP32 magic-number add instead of a conversion instruction.
-template <bool kSmall>
-__device__ __forceinline__ void drain_hilo(uint32_t tmem, int quarter, long long hi[kS], long long lo[kS])
-{
-#pragma unroll
-    for (int b = 0; b < kS; ++b) hi[b] = lo[b] = 0;
-#pragma unroll
-    for (int p = 0; p < kDig; ++p) {
-#pragma unroll
-        for (int c0 = 0; c0 < nmma(p); c0 += 16) {
-            uint32_t v[16];
-            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tcol(p) + c0);
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                "[%16];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                const int q = (c0 + c) >> 3, b = (c0 + c) & 7, cls = p + q;
-                if (q < nq(p)) {
-                    const long long d =
-                        kSmall ? (long long)(__float_as_int(__uint_as_float(v[c]) + 12582912.0f) - 0x4B400000)
-                               : (long long)f2i_exact(v[c]);
-                    if (cls <= 4)
-                        hi[b] += d << (6 * (4 - cls));
-                    else
-                        lo[b] += d << (6 * (9 - cls));
-                }
-            }
-        }
-    }
-}
 
-__device__ __forceinline__ double combine_hilo(long long hi, long long lo, int e)
-{
-    const double v = fma((double)hi, 0x1p-34, (double)lo * 0x1p-64);
-    return v * __longlong_as_double((long long)(1023 + e) << 52);
-}
+// ---------------------------------------------------------------------------------
+// Block update out = base + sign * V_{0..nblk-1} H on the tensor cores (W -= V H of the
+// Gram-Schmidt passes, U = V Y of the solution update), same digit scheme.  The MMA's M
+// dimension is 128 rows of V, K runs over basis columns (16 = two blocks per MMA), N over
+// H's digit planes x 8 columns.  V's digits are cut per stage from its fixed-point rows
+// and laid out MN-major (8 basis columns x 8 contiguous rows per core matrix); H's digits
+// are built once per call by k_h_digits as K-major pieces, one 2304-byte group per 16
+// basis columns.  A segment of at most 29 K steps (464 basis columns) owns one accumulator
+// buffer; a 128-row tile has at most three segments.
+// ---------------------------------------------------------------------------------
+constexpr int kURawBlk = 128 * kRawRow;       // 8 KB: 128 rows of one block
+constexpr int kURawStage = 2 * kURawBlk;      // two blocks = one K step
+constexpr int kURawStages = 5;
+constexpr int kUPlane = 2 * (8 * kPiece);     // one digit plane of a stage: 2 blocks x 2 KB
+constexpr int kUStageA = kDig * kUPlane;      // 36 KB
+constexpr int kUDigStage = kUStageA + (kDig + 1) * kPiece;  // + 9 H digit pieces + zero group
+constexpr int kUDigStages = 3;
+constexpr int kUSegSteps = kSegK / 16;        // K steps per segment
+constexpr int kUOffDig = kURawStages * kURawStage;
+constexpr int kUOffBar = kUOffDig + kUDigStages * kUDigStage;
+constexpr int kUBars = 2 * (kURawStages + kUDigStages + kBufs);
+constexpr int kUOffFlag = kUOffBar + kUBars * 8;
+constexpr int kUOffTmem = kUOffFlag + 8;
+constexpr int kUSmem = kUOffTmem + 16;
+static_assert(kUSmem <= 227 * 1024, "update kernel shared memory");
+static_assert(kUOffDig % 16 == 0 && kUDigStage % 16 == 0 && kUOffBar % 8 == 0, "alignment");
 
 // Persistent block update: out[r][b] = base[r][b] + sign * (V H)[r][b] (base == null:
 // sign * V H).  One CTA per SM walks 128-row tiles, one stage per K step of two basis
 // blocks.  Warp 0 copies raw rows, warps 6..13 cut digits (and copy H's digit pieces of
-// the step), warp 1 issues the MMAs and waits for the drain warps 2..5 to hand tensor
-// memory back before starting the next tile.
-__global__ void __launch_bounds__(kUThreads, 1)
-    k_block_update_tc(int32_t n, int32_t nblk, const double *__restrict__ V, const char *__restrict__ hdig,
+// the step), warp 1 issues the MMAs, warps 2..5 drain the accumulator buffers and write
+// the tile's rows.
+__global__ void __launch_bounds__(kThreadsTC, 1)
+    k_block_update_tc(int32_t n, int32_t nblk, const uint64_t *__restrict__ Vf, const char *__restrict__ hdig,
                       const int32_t *__restrict__ hexp, const double *base, double *out, double sign, int *err)
 {
     extern __shared__ __align__(128) char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nk = (nblk + 1) / 2;  // K steps of 16 basis columns
+    const int nsegt = (nk + kUSegSteps - 1) / kUSegSteps;  // segments per tile
     const int64_t ntiles = ((int64_t)n + 127) / 128;
-    const uint32_t rfull0 = smem_u32(smem + kUOffBar), rempty0 = rfull0 + kURawStages * 8;
+    const uint32_t bar0 = smem_u32(smem + kUOffBar);
+    const uint32_t rfull0 = bar0, rempty0 = rfull0 + kURawStages * 8;
     const uint32_t dfull0 = rempty0 + kURawStages * 8, dempty0 = dfull0 + kUDigStages * 8;
-    const uint32_t tdone = smem_u32(smem + kUOffTdone), tfree = tdone + 8;
+    const uint32_t bfull0 = dempty0 + kUDigStages * 8, bfree0 = bfull0 + kBufs * 8;
     volatile int *flag = reinterpret_cast<volatile int *>(smem + kUOffFlag);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kUOffTmem);
 
@@ -607,12 +733,14 @@ __global__ void __launch_bounds__(kUThreads, 1)
             mbar_init(dfull0 + 8 * s, kCW);
             mbar_init(dempty0 + 8 * s, 1);
         }
-        mbar_init(tdone, 1);
-        mbar_init(tfree, 128);
+        for (int b = 0; b < kBufs; ++b) {
+            mbar_init(bfull0 + 8 * b, 1);
+            mbar_init(bfree0 + 8 * b, 128);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
         *flag = 0;
     }
-    for (int e = tid; e < kUDigStages * (kPiece / 16); e += kUThreads) {
+    for (int e = tid; e < kUDigStages * (kPiece / 16); e += kThreadsTC) {
         const int s = e / (kPiece / 16), o = e % (kPiece / 16);
         *reinterpret_cast<uint4 *>(smem + kUOffDig + s * kUDigStage + kUStageA + kDig * kPiece + o * 16) =
             make_uint4(0, 0, 0, 0);
@@ -641,7 +769,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
                     char *st = smem + s * kURawStage;
 #pragma unroll 1
                     for (int i = 0; i < nbk; ++i)
-                        bulk_copy(smem_u32(st + i * kURawBlk), V + ((int64_t)(2 * kk + i) * n + tile * 128) * kS,
+                        bulk_copy(smem_u32(st + i * kURawBlk), Vf + ((int64_t)(2 * kk + i) * n + tile * 128) * kS,
                                   bytes, fb);
                     issued = g + 1;
                 }
@@ -653,53 +781,70 @@ __global__ void __launch_bounds__(kUThreads, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {  // ---- MMA thread
-            int64_t g = 0, t = 0;
-            for (int64_t tile = blockIdx.x; tile < ntiles && !*flag; tile += gridDim.x, ++t) {
-                if (t > 0 && !mbar_wait_bounded(tfree, (uint32_t)((t - 1) & 1))) {
-                    *flag = 1;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;");
+            int64_t g = 0, gs = 0;
+            int64_t last = -1;  // last digit stage consumed
+            for (int64_t tile = blockIdx.x; tile < ntiles && !*flag; tile += gridDim.x) {
                 bool ok = true;
-                for (int kk = 0; kk < nk; ++kk, ++g) {
-                    const int d = (int)(g % kUDigStages);
-                    if (!mbar_wait_bounded(dfull0 + 8 * d, (uint32_t)((g / kUDigStages) & 1))) {
+                for (int sgm = 0; sgm < nsegt && ok; ++sgm, ++gs) {
+                    const int buf = (int)(gs % kBufs);
+                    if (gs >= kBufs && !mbar_wait_bounded(bfree0 + 8 * buf, (uint32_t)((gs / kBufs - 1) & 1))) {
                         ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;");
-                    const char *st = smem + kUOffDig + d * kUDigStage;
-#pragma unroll
-                    for (int p = 0; p < kDig; ++p) {
-                        const uint64_t da = make_desc_mn(smem_u32(st + p * kUPlane));
+                    const int k0 = sgm * kUSegSteps, k1 = min(nk, k0 + kUSegSteps);
+                    for (int kk = k0; kk < k1; ++kk, ++g) {
+                        const int d = (int)(g % kUDigStages);
+                        if (!mbar_wait_bounded(dfull0 + 8 * d, (uint32_t)((g / kUDigStages) & 1))) {
+                            ok = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                        const char *st = smem + kUOffDig + d * kUDigStage;
                         const uint64_t db = make_desc(smem_u32(st + kUStageA));
-                        mma_bf16(tmem + tcol(p), da, db, make_idesc_amn(kM, nmma(p)), kk > 0 ? 1u : 0u);
+#pragma unroll
+                        for (int p = 0; p < kDig; ++p) {
+                            const uint64_t da = make_desc_mn(smem_u32(st + p * kUPlane));
+                            mma_bf16(tmem + buf * kBufCols + 8 * p, da, db, make_idesc_amn(kM, nmma(p)),
+                                     (kk == k0 && p == 0) ? 0u : 1u);
+                        }
+                        mma_commit(dempty0 + 8 * d);
+                        last = g;
                     }
-                    mma_commit(dempty0 + 8 * d);
+                    if (ok) mma_commit(bfull0 + 8 * buf);  // segment finished: the drain may read it
                 }
                 if (!ok) {
                     *flag = 1;
                     break;
                 }
-                // tile finished: the drain warps may read tensor memory
-                mma_commit(tdone);
             }
+            // all MMAs done before shared memory is released
+            if (last >= 0 &&
+                !mbar_wait_bounded(dempty0 + 8 * (int)(last % kUDigStages), (uint32_t)((last / kUDigStages) & 1)))
+                *flag = 1;
         }
     } else if (warp < 6) {  // ---- drain warps 2..5: tensor-memory lane quarter = warp % 4
         const int quarter = warp & 3;
-        int64_t t = 0;
-        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++t) {
-            if (!mbar_wait_bounded(tdone, (uint32_t)(t & 1)) || *flag) {
-                *flag = 1;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;");
+        int64_t gs = 0;
+        bool ok = true;
+        for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             long long hi[kS], lo[kS];
-            drain_hilo<true>(tmem, quarter, hi, lo);
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            mbar_arrive(tfree);
+#pragma unroll
+            for (int b = 0; b < kS; ++b) hi[b] = lo[b] = 0;
+            for (int sgm = 0; sgm < nsegt; ++sgm, ++gs) {
+                const int buf = (int)(gs % kBufs);
+                if (!mbar_wait_bounded(bfull0 + 8 * buf, (uint32_t)((gs / kBufs) & 1)) || *flag) {
+                    *flag = 1;
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                drain_classes(tmem + ((uint32_t)(quarter * 32) << 16) + buf * kBufCols, hi, lo);
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                mbar_arrive(bfree0 + 8 * buf);
+            }
             const int64_t r = tile * 128 + quarter * 32 + lane;
-            if (r < n) {
+            if (ok && r < n) {
 #pragma unroll
                 for (int b = 0; b < kS; ++b) {
                     const double vh = combine_hilo(hi[b], lo[b], hexp[b]);
@@ -711,11 +856,10 @@ __global__ void __launch_bounds__(kUThreads, 1)
         const int ct = tid - 192;
         const int i = ct >> 7, t8 = (ct >> 4) & 7, ko = (ct >> 3) & 1, a = ct & 7;
         const int rloc = t8 * kKT + ko * 8;
-        bool bad = false;
         int64_t g = 0;
-        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        bool stop = false;
+        for (int64_t tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x) {
             const int rv = (int)min((int64_t)128, (int64_t)n - tile * 128);
-            bool stop = false;
             for (int kk = 0; kk < nk; ++kk, ++g) {
                 const int s = (int)(g % kURawStages), d = (int)(g % kUDigStages);
                 bool ok = warp_wait(rfull0 + 8 * s, (uint32_t)((g / kURawStages) & 1));
@@ -727,13 +871,13 @@ __global__ void __launch_bounds__(kUThreads, 1)
                     break;
                 }
                 const int nbk = min(2, nblk - 2 * kk);
-                const double *src =
-                    reinterpret_cast<const double *>(smem + s * kURawStage + i * kURawBlk) + rloc * kS + a;
+                const uint64_t *src =
+                    reinterpret_cast<const uint64_t *>(smem + s * kURawStage + i * kURawBlk) + rloc * kS + a;
                 char *dig = smem + kUOffDig + d * kUDigStage;
-                double x[8];
+                uint64_t f[8];
 #pragma unroll
-                for (int v = 0; v < 8; ++v) x[v] = (i < nbk && rloc + v < rv) ? src[v * kS] : 0.0;
-                if (!convert8(x, 0, dig + i * (8 * kPiece) + t8 * kPiece + ko * kLBO + a * 16, kUPlane)) bad = true;
+                for (int v = 0; v < 8; ++v) f[v] = (i < nbk && rloc + v < rv) ? src[v * kS] : 0ull;
+                expand8(f, dig + i * (8 * kPiece) + t8 * kPiece + ko * kLBO + a * 16, kUPlane);
                 if (ct < kDig * kPiece / 16)  // H's digit pieces of this K step
                     reinterpret_cast<uint4 *>(dig + kUStageA)[ct] =
                         reinterpret_cast<const uint4 *>(hdig + (int64_t)kk * kDig * kPiece)[ct];
@@ -744,9 +888,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
                     mbar_arrive(dfull0 + 8 * d);
                 }
             }
-            if (stop) break;
         }
-        if (bad) atomicOr(err, ERR_RANGE);
     }
     __syncthreads();
     if (*flag && tid == 0) atomicOr(err, ERR_TIMEOUT);
@@ -763,7 +905,7 @@ bool block_dot_tc_supported(int32_t s) { return s == kS; }
 
 size_t tc_hdig_bytes(int32_t nblk) { return (size_t)((nblk + 1) / 2) * kDig * kPiece; }
 
-int block_update_tc_max_blocks() { return 1024 / kS; }
+int block_update_tc_max_blocks() { return 128; }
 
 int tc_subs_per_chunk(int32_t n, int32_t nblk)
 {
@@ -781,10 +923,19 @@ size_t tc_partial_elems(int32_t n, int32_t nblk)
     return (size_t)((nt + 7) / 8) * nblk * kS * kS;  // chunks hold at least 8 sub-tiles
 }
 
-int launch_block_update_tc(cudaStream_t st, int32_t n, int32_t nblk, const double *V, const double *H, void *hdig,
+int launch_to_fixed(cudaStream_t st, int64_t count, const double *X, uint64_t *F, int *d_err)
+{
+    if (count <= 0) return 0;
+    int64_t g = (count + 255) / 256;
+    if (g > 4 * 152) g = 4 * 152;
+    k_to_fixed<<<(unsigned)g, 256, 0, st>>>(count, X, F, d_err);
+    note_launches(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_block_update_tc(cudaStream_t st, int32_t n, int32_t nblk, const uint64_t *Vf, const double *H, void *hdig,
                            int32_t *hexp, const double *base, double *out, double sign, int *d_err)
 {
-    // the drain reads the FP32 sums as integers below 2^22: at most 1024 basis columns
     if (n <= 0 || nblk <= 0 || nblk > block_update_tc_max_blocks()) return -1;
     k_h_digits<<<1, 256, 0, st>>>(nblk, H, (char *)hdig, hexp, d_err);
     note_launches(1);
@@ -795,12 +946,13 @@ int launch_block_update_tc(cudaStream_t st, int32_t n, int32_t nblk, const doubl
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t tiles = ((int64_t)n + 127) / 128;
     const int grid = (int)(tiles < sms ? tiles : sms);
-    k_block_update_tc<<<grid, kUThreads, kUSmem, st>>>(n, nblk, V, (const char *)hdig, hexp, base, out, sign, d_err);
+    k_block_update_tc<<<grid, kThreadsTC, kUSmem, st>>>(n, nblk, Vf, (const char *)hdig, hexp, base, out, sign,
+                                                         d_err);
     note_launches(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_block_dot_tc(cudaStream_t st, int32_t n, int32_t nblk, const double *V, const double *W, double *partial,
+int launch_block_dot_tc(cudaStream_t st, int32_t n, int32_t nblk, const uint64_t *Vf, const double *W, double *partial,
                         double *out, int *d_err)
 {
     if (n <= 0 || nblk <= 0) return -1;
@@ -811,7 +963,7 @@ int launch_block_dot_tc(cudaStream_t st, int32_t n, int32_t nblk, const double *
     const int chunks = (int)((nt + spc - 1) / spc);
     const int mtiles = (nblk + kBlocksPerTile - 1) / kBlocksPerTile;
     dim3 grid(chunks, mtiles);
-    k_block_dot_tc<<<grid, kDThreads, kDSmem, st>>>(n, nblk, spc, V, W, partial, d_err);
+    k_block_dot_tc<<<grid, kThreadsTC, kDSmem, st>>>(n, nblk, spc, Vf, W, partial, d_err);
     note_launches(1);
     if (cudaGetLastError() != cudaSuccess) return -1;
     return launch_reduce_chunks(st, nblk * kS * kS, chunks, partial, out);

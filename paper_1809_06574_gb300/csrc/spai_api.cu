@@ -904,6 +904,7 @@ struct SolveWs {
     double *Bw, *Xw, *W, *Z, *T0, *T1, *V;
     double *partial, *H1, *H2, *G1, *R1, *R2, *Rn, *ref2, *nrm2, *thresh, *Qs, *Rtri, *G, *Y, *est;
     int32_t *defl1, *defl2, *flag;
+    uint64_t *vfix; // fixed-point copies of the basis blocks (tensor-core products)
     void *hdig;     // digit pieces of H (tensor-core block update)
     int32_t *hexp;  // column exponents of H
 };
@@ -950,6 +951,7 @@ size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks
     w.defl2 = (int32_t *)take(s * 4);
     w.flag = (int32_t *)take(64);
     const bool digits = block_dot_tc_supported(s);
+    w.vfix = (uint64_t *)take(digits ? blk * (m + 1) : 16);
     w.hdig = take(digits ? tc_hdig_bytes(m + 1) : 16);
     w.hexp = (int32_t *)take(64);
     return off;
@@ -1005,12 +1007,20 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
     if (opts->orth < SPAI_ORTH_AUTO || opts->orth > SPAI_ORTH_TENSOR)
         return fail(ctx, SPAI_EINVAL, "unknown orthogonalisation method %d", opts->orth);
     const bool use_digits = block_dot_tc_supported(s) && opts->orth != SPAI_ORTH_FP64;
+    // fixed-point copy of basis block blk for the tensor-core products
+    auto make_fixed = [&](int blk) -> spai_status {
+        if (!use_digits) return SPAI_OK;
+        PKL("to_fixed", 0.0, 16.0 * n * s,
+            launch_to_fixed(cs, (int64_t)n * s, w.V + (size_t)blk * n * s, w.vfix + (size_t)blk * n * s, ctx->d_err),
+            "fixed point");
+        return SPAI_OK;
+    };
     // out = base + sign * V_{0..nb-1} H: tensor-core digits when available, else FP64
     auto vupdate = [&](int nb, const double *H, const double *basep, double *out, double sign) -> spai_status {
         const double f = 2.0 * n * s * s * nb;
         if (use_digits && nb <= block_update_tc_max_blocks() && (opts->orth == SPAI_ORTH_TENSOR || nb >= 2)) {
             PKL("block_update_tc", f, 8.0 * n * s * (nb + 2),
-                launch_block_update_tc(cs, n, nb, w.V, H, w.hdig, w.hexp, basep, out, sign,
+                launch_block_update_tc(cs, n, nb, w.vfix, H, w.hdig, w.hexp, basep, out, sign,
                                        ctx->d_err),
                 "block update");
         } else {
@@ -1065,6 +1075,7 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
         ++cycles;
         // V_0 S_0 = R (ref2 holds the residual norms^2)
         if ((st = cholqr2(ctx, w, n, s, chunks, w.W, w.V, w.Rn, w.ref2))) return st;
+        if ((st = make_fixed(0))) return st;
         PKL("small_dense", 0.0, 0.0, launch_set_rhs(cs, s, m, w.Rn, w.G), "rhs");
         int J = 0;
         for (int j = 0; j < m; ++j) {
@@ -1082,7 +1093,7 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
             const bool tc = use_digits && (opts->orth == SPAI_ORTH_TENSOR || j + 1 >= 2);
             if (tc) {
                 PKL("block_dot_tc", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
-                    launch_block_dot_tc(cs, n, j + 1, w.V, w.W, w.partial, w.H1, ctx->d_err), "H1");
+                    launch_block_dot_tc(cs, n, j + 1, w.vfix, w.W, w.partial, w.H1, ctx->d_err), "H1");
             } else {
                 PKL("block_dot", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
                     launch_block_dot(cs, s, n, j + 1, w.V, w.W, w.partial, w.H1, chunks), "H1");
@@ -1090,7 +1101,7 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
             if ((st = vupdate(j + 1, w.H1, w.W, w.W, -1.0))) return st;
             if (tc) {
                 PKL("block_dot_tc", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
-                    launch_block_dot_tc(cs, n, j + 1, w.V, w.W, w.partial, w.H2, ctx->d_err), "H2");
+                    launch_block_dot_tc(cs, n, j + 1, w.vfix, w.W, w.partial, w.H2, ctx->d_err), "H2");
             } else {
                 PKL("block_dot", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
                     launch_block_dot(cs, s, n, j + 1, w.V, w.W, w.partial, w.H2, chunks), "H2");
@@ -1098,6 +1109,7 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
             if ((st = vupdate(j + 1, w.H2, w.W, w.W, -1.0))) return st;
             double *Vn = w.V + (size_t)(j + 1) * blk_elems;
             if ((st = cholqr2(ctx, w, n, s, chunks, w.W, Vn, w.Rn, w.ref2))) return st;
+            if (j + 1 < m && (st = make_fixed(j + 1))) return st;
             PKL("arnoldi_ls", 16.0 * s * s * s * (j + 1), 0.0,
                 launch_arnoldi_ls(cs, s, j, m, w.H1, w.H2, w.Rn, w.Qs, w.Rtri, w.G, w.thresh, w.est, w.flag), "least squares");
             CU(cudaMemcpyAsync(h + 32, w.est, s * 8, cudaMemcpyDeviceToHost, cs), "read estimates");
@@ -1167,20 +1179,24 @@ extern "C" spai_status spai_block_gram(spai_ctx ctx, int32_t s, int32_t n, int32
         return fail(ctx, SPAI_EINVAL, "the tensor-core Gram product needs s == 8");
     if (((uintptr_t)V | (uintptr_t)W | (uintptr_t)H) & 15)
         return fail(ctx, SPAI_EINVAL, "V, W and H must be 16-byte aligned");
-    const size_t a = dot_partial_elems(s, nblk) * 8;
+    const size_t a = (dot_partial_elems(s, nblk) * 8 + 255) / 256 * 256;
     const bool tcm = method == SPAI_ORTH_TENSOR;
-    const size_t c = tcm ? tc_partial_elems(n, nblk) * 8 : 0;
+    const size_t c = tcm ? (tc_partial_elems(n, nblk) * 8 + 255) / 256 * 256 : 0;
+    const size_t fx = tcm ? (size_t)nblk * n * s * 8 : 0;
     void *ws = nullptr;
-    spai_status st = temp_blocks(ctx, a > c ? a : c, &ws);
+    spai_status st = temp_blocks(ctx, (a > c ? a : c) + fx, &ws);
     if (st) return st;
     double *partial = (double *)ws;
+    uint64_t *vfix = (uint64_t *)((char *)ws + (a > c ? a : c));
     const double nsd = (double)n * s;
     if (!tcm) {
         PKL("block_dot", 2.0 * nsd * s * nblk, 8.0 * nsd * (nblk + 1),
             launch_block_dot(ctx->stream, s, n, nblk, V, W, partial, H, krylov_chunks(n)), "gram");
     } else {
+        PKL("to_fixed", 0.0, 16.0 * nsd * nblk, launch_to_fixed(ctx->stream, (int64_t)nblk * n * s, V, vfix, ctx->d_err),
+            "fixed point");
         PKL("block_dot_tc", 2.0 * nsd * s * nblk, 8.0 * nsd * (nblk + 1),
-            launch_block_dot_tc(ctx->stream, n, nblk, V, W, partial, H, ctx->d_err), "tensor gram");
+            launch_block_dot_tc(ctx->stream, n, nblk, vfix, W, partial, H, ctx->d_err), "tensor gram");
     }
     int h = 0;
     if ((st = read_err(ctx, &h))) return st;
@@ -1209,13 +1225,16 @@ extern "C" spai_status spai_block_update(spai_ctx ctx, int32_t s, int32_t n, int
     } else {
         const size_t hd = (tc_hdig_bytes(nblk) + 255) / 256 * 256;
         void *ws = nullptr;
-        spai_status st = temp_blocks(ctx, hd + 256, &ws);
+        spai_status st = temp_blocks(ctx, hd + 256 + (size_t)nblk * n * s * 8, &ws);
         if (st) return st;
         void *hdig = ws;
         int32_t *hexp = (int32_t *)((char *)ws + hd);
+        uint64_t *vfix = (uint64_t *)((char *)ws + hd + 256);
         const double nsd = (double)n * s;
+        PKL("to_fixed", 0.0, 16.0 * nsd * nblk, launch_to_fixed(ctx->stream, (int64_t)nblk * n * s, V, vfix, ctx->d_err),
+            "fixed point");
         PKL("block_update_tc", 2.0 * nsd * s * nblk, 8.0 * nsd * (nblk + 2),
-            launch_block_update_tc(ctx->stream, n, nblk, V, H, hdig, hexp, W, W, sign, ctx->d_err),
+            launch_block_update_tc(ctx->stream, n, nblk, vfix, H, hdig, hexp, W, W, sign, ctx->d_err),
             "tensor block update");
     }
     int h = 0;

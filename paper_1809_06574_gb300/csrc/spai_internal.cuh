@@ -134,18 +134,19 @@ int launch_gram_sym(cudaStream_t st, int32_t s, int32_t n, const double *W, doub
 int launch_reduce_chunks(cudaStream_t st, int32_t count, int chunks, const double *partial, double *out);
 
 // ---------------------------------------------------------------------- k_ozaki.cu
-// FP64-accurate products on the tensor cores (s == 8): the kernels read the FP64 blocks
-// and cut BF16 digits in shared memory.
+// FP64-accurate products on the tensor cores (s == 8): basis blocks as fixed point (Vf,
+// from launch_to_fixed, |v| < 2), W as FP64; BF16 digits are cut in shared memory.
 bool block_dot_tc_supported(int32_t s);
 size_t tc_partial_elems(int32_t n, int32_t nblk);
+int launch_to_fixed(cudaStream_t st, int64_t count, const double *X, uint64_t *F, int *d_err);
 // H = V_{0..nblk-1}^T W (H[i][a][b]); partial needs tc_partial_elems(n, nblk) doubles
-int launch_block_dot_tc(cudaStream_t st, int32_t n, int32_t nblk, const double *V, const double *W, double *partial,
-                        double *out, int *d_err);
+int launch_block_dot_tc(cudaStream_t st, int32_t n, int32_t nblk, const uint64_t *Vf, const double *W,
+                        double *partial, double *out, int *d_err);
 // out = base + sign * V_{0..nblk-1} H (base may be null, may equal out): H is nblk*8 x 8
 // ([i][a][b]); hdig needs tc_hdig_bytes(nblk) bytes, hexp 8 ints
 int block_update_tc_max_blocks();
 size_t tc_hdig_bytes(int32_t nblk);
-int launch_block_update_tc(cudaStream_t st, int32_t n, int32_t nblk, const double *V, const double *H, void *hdig,
+int launch_block_update_tc(cudaStream_t st, int32_t n, int32_t nblk, const uint64_t *Vf, const double *H, void *hdig,
                            int32_t *hexp, const double *base, double *out, double sign, int *d_err);
 // FP64 FMA throughput probe: blocks x threads x 8 chains x iters FMAs
 int launch_fp64_probe(cudaStream_t st, int blocks, int threads, int iters, double *sink);
