@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--nparams", type=int, default=20)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    # host threads (each with its own stream and context) sharing a shift's independent solves
+    ap.add_argument("--workers", type=int, default=4)
     # single-kernel case (for profiler captures): H = V^T W or W -= V H at n = side^3, s = 8
     ap.add_argument("--kernel", default=None, choices=["dot", "update"])
     ap.add_argument("--nblk", type=int, default=16)
@@ -294,8 +296,27 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------------------- GPU sweep
+class Worker:
+    """One host thread's share of the sweep: its own stream, context and buffers."""
+
+    def __init__(self, sg, torch, n, s, nnz, dev, host_inputs):
+        self.stream = torch.cuda.Stream(device=dev)
+        self.ctx = sg.spai_ctx_create(self.stream.cuda_stream, 0)
+        with torch.cuda.stream(self.stream):
+            self.va = torch.empty(nnz, dtype=torch.float64, device=dev)
+            if host_inputs:
+                self.X = torch.zeros((s, n), dtype=torch.float64).pin_memory()
+            else:
+                self.X = torch.zeros((s, n), dtype=torch.float64, device=dev)
+
+
 class Sweep:
-    def __init__(self, sg, torch, ctx, w, host_inputs=False):
+    """One step = the whole parameter sweep: for every shift s a SPAI build at the first p,
+    then (Table 1, first approach) an update per further p, and a block GMRES solve of
+    every system.  After each build the shift's solves are independent; `workers` host
+    threads, each with its own stream and context, take them round-robin."""
+
+    def __init__(self, sg, torch, ctx, w, host_inputs=False, workers=1):
         self.sg, self.torch, self.ctx, self.w = sg, torch, ctx, w
         n = w.n
         self.n = n
@@ -309,17 +330,29 @@ class Sweep:
             for t in w.terms:
                 self.h_terms.append(tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
                                           for a in t))
-            self.h_B = torch.from_numpy(np.ascontiguousarray(w.B.T)).pin_memory()
-            self.h_X = torch.zeros((self.s, n), dtype=torch.float64).pin_memory()
+            self.B = torch.from_numpy(np.ascontiguousarray(w.B.T)).pin_memory()
             self.aff = None
         else:
             self.d_terms = [tuple(torch.as_tensor(np.ascontiguousarray(a), device=dev) for a in t)
                             for t in w.terms]
             self.aff = sg.spai_affine_create(ctx, [sg.csr(n, *t) for t in self.d_terms])
-            self.d_B = torch.as_tensor(np.ascontiguousarray(w.B.T), device=dev)
-            self.d_X = torch.zeros((self.s, n), dtype=torch.float64, device=dev)
+            self.B = torch.as_tensor(np.ascontiguousarray(w.B.T), device=dev)
+        nnz = sum(len(t[1]) for t in w.terms)  # upper bound of the union pattern
+        self.vb = torch.empty(nnz, dtype=torch.float64, device=dev)
+        self.workers = [Worker(sg, torch, n, self.s, nnz, dev, host_inputs) for _ in range(workers)]
+        self.pool = None
+        if workers > 1:
+            from concurrent.futures import ThreadPoolExecutor
+            self.pool = ThreadPoolExecutor(max_workers=workers)
         self.solves = 0
         self.iters = []
+        self.errors = []
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.shutdown()
+        for wk in self.workers:
+            self.sg.spai_ctx_destroy(wk.ctx)
 
     def h2d_bytes(self):
         tb = sum(a.numel() * a.element_size() for t in self.h_terms for a in t)
@@ -330,42 +363,73 @@ class Sweep:
     def d2h_bytes(self):
         return len(self.w.params) * len(self.w.shifts) * self.n * self.s * 8
 
+    def _solve(self, wk, k, s, base, A0, rp, ci, nnz):
+        """Systems k, k + W, ... of shift s on worker wk (system 0 uses the base)."""
+        sg, torch, w, n = self.sg, self.torch, self.w, self.n
+        out = []
+        for i in range(k, len(w.params), len(self.workers)):
+            if i == 0:
+                A, pc = A0, base
+            else:
+                sg.spai_assemble(wk.ctx, self.aff_now, sg.affine_coefficients(w.params[i], s), wk.va)
+                A = sg.csr(n, rp, ci, wk.va, nnz)
+                pc, _ = sg.spai_update(wk.ctx, base, A, sg.UPDATE_FIRST)
+            with torch.cuda.stream(wk.stream):
+                wk.X.zero_()
+            st, info, rel = sg.block_solve(wk.ctx, A, pc, self.s, self.B, n, wk.X, n,
+                                           w.restart, w.tol, 50)
+            if i > 0:
+                sg.spai_pc_destroy(pc)
+            if not info["converged"]:
+                raise RuntimeError(f"solve did not converge: p={w.params[i]} s={s} {info}")
+            out.append(info["iterations"])
+        return out
+
     def step(self):
         sg, torch, ctx, w, n = self.sg, self.torch, self.ctx, self.w, self.n
         aff = self.aff
         if self.host_inputs:
             aff = sg.spai_affine_create(ctx, [sg.csr(n, *t) for t in self.h_terms])
+        self.aff_now = aff
         _, nnz, rp, ci = sg.spai_affine_pattern(aff)
-        vb = torch.empty(nnz, dtype=torch.float64, device=self.dev)
-        va = torch.empty(nnz, dtype=torch.float64, device=self.dev)
         for s in w.shifts:
-            base = None
-            for i, p in enumerate(w.params):
-                buf = vb if i == 0 else va
-                sg.spai_assemble(ctx, aff, sg.affine_coefficients(p, s), buf)
-                A = sg.csr(n, rp, ci, buf, nnz)
-                if i == 0:
-                    base, _ = sg.spai_build(ctx, A, sg.PATTERN_A)
-                    pc = base
-                else:
-                    pc, _ = sg.spai_update(ctx, base, A, sg.UPDATE_FIRST)
-                if self.host_inputs:
-                    self.h_X.zero_()
-                    st, info, rel = sg.block_solve(ctx, A, pc, self.s, self.h_B, n, self.h_X, n,
-                                                   w.restart, w.tol, 50)
-                else:
-                    self.d_X.zero_()
-                    st, info, rel = sg.block_solve(ctx, A, pc, self.s, self.d_B, n, self.d_X, n,
-                                                   w.restart, w.tol, 50)
-                if not info["converged"]:
-                    raise RuntimeError(f"solve did not converge: p={p} s={s} {info}")
-                self.solves += 1
-                self.iters.append(info["iterations"])
-                if i > 0:
-                    sg.spai_pc_destroy(pc)
+            sg.spai_assemble(ctx, aff, sg.affine_coefficients(w.params[0], s), self.vb)
+            A0 = sg.csr(n, rp, ci, self.vb, nnz)
+            base, _ = sg.spai_build(ctx, A0, sg.PATTERN_A)  # returns with the build complete
+            if self.pool is None:
+                res = [self._solve(self.workers[0], 0, s, base, A0, rp, ci, nnz)]
+            else:
+                futs = [self.pool.submit(self._solve, wk, k, s, base, A0, rp, ci, nnz)
+                        for k, wk in enumerate(self.workers)]
+                res = [f.result() for f in futs]
+            for r in res:
+                self.solves += len(r)
+                self.iters.extend(r)
             sg.spai_pc_destroy(base)
         if self.host_inputs:
             sg.spai_affine_destroy(aff)
+
+    def profile(self, enable):
+        for c in [self.ctx] + [wk.ctx for wk in self.workers]:
+            self.sg.spai_ctx_profile(c, enable)
+
+    def profile_entries(self):
+        """Per-family totals summed over the step's contexts.  Idle families ("idle:...")
+        are kept for the workers' streams only, averaged over the workers (the main
+        context's stream waits between shifts by design)."""
+        fam = {}
+        nw = len(self.workers)
+        for c in [self.ctx] + [wk.ctx for wk in self.workers]:
+            for i in range(self.sg.spai_ctx_profile_count(c)):
+                e = self.sg.spai_ctx_profile_entry(c, i)
+                idle = e["name"].startswith("idle:")
+                if idle and c == self.ctx:
+                    continue
+                f = fam.setdefault(e["name"], {"name": e["name"], "launches": 0, "ms": 0.0, "flops": 0.0,
+                                               "bytes": 0.0})
+                for k in ("launches", "ms", "flops", "bytes"):
+                    f[k] += e[k] / (nw if idle else 1)
+        return list(fam.values())
 
 
 def main():
@@ -401,7 +465,8 @@ def main():
     ctx = sg.spai_ctx_create(stream.cuda_stream, 0)
     fp64_tflops = max(sg.spai_measure_fp64_rate(ctx) for _ in range(3))
 
-    sweep = Sweep(sg, torch, ctx, w)
+    sweep = Sweep(sg, torch, ctx, w, workers=args.workers)
+    sweep.profile(1)  # the warm-up also fills the profiler's pools of CUDA events
     for _ in range(args.warmup):
         sweep.step()
     sweep.solves, sweep.iters = 0, []
@@ -415,19 +480,23 @@ def main():
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    sg.spai_ctx_profile(ctx, 1)
+    sweep.profile(1)  # clears the warm-up's totals
     l0 = sg.spai_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
         sweep.step()
+    for wk in sweep.workers:  # the workers' streams end before e1
+        ev = torch.cuda.Event()
+        ev.record(wk.stream)
+        stream.wait_event(ev)
     e1.record(stream)
     barrier()
     launches = sg.spai_launch_count() - l0
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    prof_all = [sg.spai_ctx_profile_entry(ctx, i) for i in range(sg.spai_ctx_profile_count(ctx))]
-    sg.spai_ctx_profile(ctx, 0)
+    prof_all = sweep.profile_entries()
+    sweep.profile(0)
     prof = [f for f in prof_all if not f["name"].startswith("idle:")]
     idle = sorted(((f["name"][5:], f["ms"]) for f in prof_all if f["name"].startswith("idle:")),
                   key=lambda x: -x[1])
@@ -445,10 +514,22 @@ def main():
         t_max, total_solves = t_local, float(solves)
     value = total_solves / t_max
 
+    # the dominant kernels once more with one solve at a time (no other stream sharing the
+    # GPU): their own speed, beside the timed region's contended launch durations
+    iso_prof = None
+    if rank == 0 and args.workers > 1:
+        s1 = Sweep(sg, torch, ctx, w, workers=1)
+        s1.step()
+        s1.profile(1)
+        s1.step()
+        iso_prof = [f for f in s1.profile_entries() if not f["name"].startswith("idle:")]
+        s1.profile(0)
+        s1.close()
+
     # end-to-end through the C ABI with pinned host buffers (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
-        hs = Sweep(sg, torch, ctx, w, host_inputs=True)
+        hs = Sweep(sg, torch, ctx, w, host_inputs=True, workers=args.workers)
         hs.step()  # warm-up
         hs.solves = 0
         barrier()
@@ -463,11 +544,19 @@ def main():
             dt = t.item()
         e2e = {"value": total_solves / dt, "unit": UNIT, "h2d_bytes_per_step": hs.h2d_bytes(),
                "d2h_bytes_per_step": hs.d2h_bytes()}
+        hs.close()
 
     if rank == 0:
         total_ms = sum(f["ms"] for f in prof) or 1.0
         dom = max(prof, key=lambda f: f["ms"])
         roofline = roofline_entry(dom, n=w.n, s=int(w.B.shape[1]), fp64_probe=fp64_tflops)
+        roofline_iso = None
+        if iso_prof:
+            same = [f for f in iso_prof if f["name"] == dom["name"]]
+            if same:
+                roofline_iso = roofline_entry(same[0], n=w.n, s=int(w.B.shape[1]), fp64_probe=fp64_tflops)
+                roofline_iso["note"] = ("same kernel family, one extra step with a single worker after the "
+                                        "timed region (no concurrent stream)")
         kernels = {}
         for f in sorted(prof, key=lambda f: -f["ms"]):
             r = roofline_entry(f, n=w.n, s=int(w.B.shape[1]))
@@ -481,17 +570,20 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {**workload_config(w, nnz_expected),
-                                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                                            "workers": args.workers},
+            "roofline": roofline, "roofline_isolated": roofline_iso, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "fp64_tflops_measured": fp64_tflops,
             "gmres_iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)),
                                  "max": int(max(iters))},
             "kernels": kernels,
-            # stream time with no profiled kernel running, by the kernel family that followed
+            # a worker stream's time with none of its kernels running (mean over the workers),
+            # by the kernel family that followed
             "idle_ms": {"total": round(sum(v for _, v in idle), 3),
                         **{k: round(v, 3) for k, v in idle[:8]}},
         }
         print(json.dumps(line), flush=True)
+    sweep.close()
     sg.spai_ctx_destroy(ctx)
     if dist is not None:
         dist.destroy_process_group()

@@ -78,7 +78,14 @@ typedef struct spai_pc_s *spai_pc;
 /* Create a context bound to the current CUDA device and to `stream` (a cudaStream_t;
  * NULL = the legacy default stream).  `mem_budget` caps the device bytes the library
  * holds at once (0 = no cap); exceeding it returns SPAI_ENOMEM.  The stream is not
- * owned.  *out is NULL on failure. */
+ * owned.  *out is NULL on failure.
+ *
+ * Threads: one context serves one host thread at a time.  Several contexts (each with its
+ * own stream, used from its own thread) may share read-only handles: an spai_affine, or
+ * an spai_pc once the call that made it has returned, can be passed to spai_assemble,
+ * spai_update, spai_pc_apply and block_solve on another context concurrently.  A handle
+ * must not be destroyed while another call uses it; an update made on context B from a
+ * base made on context A belongs to B and is destroyed by B's thread. */
 SPAI_API spai_status spai_ctx_create(spai_ctx *out, void *stream, size_t mem_budget);
 
 /* Release the context's workspace.  Every spai_affine / spai_pc made with it must have

@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -26,6 +27,7 @@ struct spai_ctx_s {
     size_t budget = 0;
     size_t in_use = 0;
     std::unordered_map<void *, size_t> sizes;
+    std::mutex mu;  // guards budget and sizes: a pattern analysis may be released from another context's thread
     std::string err;
     int *d_err = nullptr;      // device error word
     int32_t *d_scalar = nullptr;  // small device scratch for host read-backs
@@ -53,7 +55,7 @@ struct spai_ctx_s {
 namespace {
 
 struct Sym {
-    int refs = 1;
+    std::atomic<int> refs{1};  // handles on other contexts (host threads) may share it
     spai_ctx ctx = nullptr;
     int32_t n = 0, nnzA = 0, kind = 0;
     int32_t *a_rowptr = nullptr, *a_colind = nullptr;            // copy of A's CSR pattern
@@ -144,12 +146,22 @@ int prof_family(spai_ctx ctx, const char *name)
     return (int)ctx->prof_fam.size() - 1;
 }
 
-// Resolve recorded event pairs into the per-family totals (synchronises the stream).
-void prof_flush(spai_ctx ctx)
+// Resolve recorded event pairs into the per-family totals.  wait: synchronise the stream
+// and resolve all; otherwise resolve the completed prefix only (never blocks).
+void prof_flush(spai_ctx ctx, bool wait = true)
 {
     if (ctx->prof_recs.empty()) return;
-    cudaStreamSynchronize(ctx->stream);
-    for (auto &r : ctx->prof_recs) {
+    size_t done = ctx->prof_recs.size();
+    if (wait) {
+        cudaStreamSynchronize(ctx->stream);
+    } else {
+        done = 0;
+        while (done < ctx->prof_recs.size() && cudaEventQuery(ctx->prof_recs[done].b) == cudaSuccess) ++done;
+        cudaGetLastError();  // cudaErrorNotReady is not an error here
+        if (done == 0) return;
+    }
+    for (size_t k = 0; k < done; ++k) {
+        auto &r = ctx->prof_recs[k];
         float ms = 0.f;
         cudaEventElapsedTime(&ms, r.a, r.b);
         auto &f = ctx->prof_fam[r.family];
@@ -170,7 +182,7 @@ void prof_flush(spai_ctx ctx)
         ctx->prof_last = r.b;
         ctx->prof_pool.push_back(r.a);
     }
-    ctx->prof_recs.clear();
+    ctx->prof_recs.erase(ctx->prof_recs.begin(), ctx->prof_recs.begin() + (ptrdiff_t)done);
 }
 
 // RAII timing of the launches issued inside its scope (no-op unless profiling is on).
@@ -192,7 +204,7 @@ struct ProfScope {
         cudaEvent_t b = prof_event(ctx);
         cudaEventRecord(b, ctx->stream);
         ctx->prof_recs.push_back({fam, a, b, flops, bytes});
-        if (ctx->prof_recs.size() > 4096) prof_flush(ctx);
+        if (ctx->prof_recs.size() > 4096) prof_flush(ctx, false);
     }
 };
 
@@ -207,13 +219,18 @@ spai_status dalloc(spai_ctx ctx, void **p, size_t bytes)
     *p = nullptr;
     if (bytes == 0) bytes = 16;
     bytes = (bytes + 255) / 256 * 256;
-    if (ctx->budget && ctx->in_use + bytes > ctx->budget)
-        return fail(ctx, SPAI_ENOMEM, "memory budget exceeded: %zu in use + %zu requested > %zu",
-                    ctx->in_use, bytes, ctx->budget);
+    std::unique_lock<std::mutex> lock(ctx->mu);
+    if (ctx->budget && ctx->in_use + bytes > ctx->budget) {
+        const size_t used = ctx->in_use;
+        lock.unlock();
+        return fail(ctx, SPAI_ENOMEM, "memory budget exceeded: %zu in use + %zu requested > %zu", used, bytes,
+                    ctx->budget);
+    }
     cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
+        lock.unlock();
         return fail(ctx, SPAI_ENOMEM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
     }
     ctx->in_use += bytes;
@@ -233,6 +250,7 @@ spai_status dalloc_n(spai_ctx ctx, Tp **p, int64_t count)
 void dfree(spai_ctx ctx, void *p)
 {
     if (!p) return;
+    std::lock_guard<std::mutex> lock(ctx->mu);
     auto it = ctx->sizes.find(p);
     if (it != ctx->sizes.end()) {
         ctx->in_use -= it->second;
@@ -295,7 +313,7 @@ spai_status validate_device_csr(spai_ctx ctx, const spai_csr *A, const char *nam
 
 void sym_release(Sym *s)
 {
-    if (!s || --s->refs > 0) return;
+    if (!s || s->refs.fetch_sub(1) > 1) return;
     spai_ctx ctx = s->ctx;
     dfree(ctx, s->a_rowptr);
     dfree(ctx, s->a_colind);
@@ -557,7 +575,12 @@ extern "C" spai_status spai_ctx_sync(spai_ctx ctx)
     return SPAI_OK;
 }
 
-extern "C" size_t spai_ctx_mem_in_use(spai_ctx ctx) { return ctx ? ctx->in_use : 0; }
+extern "C" size_t spai_ctx_mem_in_use(spai_ctx ctx)
+{
+    if (!ctx) return 0;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    return ctx->in_use;
+}
 
 extern "C" int64_t spai_launch_count(void) { return spai::launches_total(); }
 
