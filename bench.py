@@ -135,14 +135,14 @@ FP64_NOMINAL_TFLOPS = 152 * 4 * 2070e6 / 1e12
 DIGIT_PRODUCTS = 53
 # how each kernel family computes: FP64 ALUs, tensor cores (digit products), or neither
 FAMILY_UNIT = {
-    "block_dot_tc": "tensor", "block_update_tc": "tensor", "to_digits": "none", "w_digits": "none",
+    "block_dot_tc": "tensor", "block_update_tc": "tensor", "to_fixed": "none",
     "axpy": "none", "gather_csc": "none", "small_dense": "latency", "arnoldi_ls": "latency",
     "backsolve": "latency",
 }
 # DRAM bytes per launch, (a * blocks + b) * n * s, fitted to one ncu capture of each kernel
-# at n = 262,144, s = 8, 16 basis blocks (profiles/k_block_{dot,update}_tc_3d64.md):
-# dot 645.5 MB over 17 blocks; update 636.9 MB = (18 * 16 + 16) B per row entry, 18 blocks
-NCU_TRAFFIC = {"block_dot_tc": (18.1, 0.0), "block_update_tc": (18.0, -20.0)}
+# at n = 262,144, s = 8 (profiles/k_block_dot_tc_3d64.md, profiles/k_block_update_tc_3d64.md):
+# Gram, 16 basis blocks + W (17 blocks): 299.9 MB; update, 8 blocks + W in and out (10): 157.8 MB
+NCU_TRAFFIC = {"block_dot_tc": (8.41, 0.0), "block_update_tc": (7.52, 0.0)}
 
 
 def roofline_entry(f, n, s, fp64_probe=None):
@@ -180,12 +180,6 @@ def roofline_entry(f, n, s, fp64_probe=None):
         # blocks per launch recovered from the algorithmic bytes (8 B per element per block)
         blocks = f["bytes"] / launches / (8.0 * n * s)
         out["traffic"] = (a * blocks + b) * n * s
-    if unit == "tensor" and f["name"] == "block_dot_tc":
-        # what the kernel itself streams: 9 BF16 digits (18 B) per element of V and W
-        out["implementation_bytes_per_launch"] = 18.0 / 8.0 * f["bytes"] / launches
-    elif unit == "tensor":
-        nb = f["bytes"] / launches / (8.0 * n * s) - 2
-        out["implementation_bytes_per_launch"] = (18.0 * nb + 16.0) * n * s
     return out
 
 
