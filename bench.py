@@ -544,6 +544,9 @@ def main():
         total_ms = sum(f["ms"] for f in prof) or 1.0
         dom = max(prof, key=lambda f: f["ms"])
         roofline = roofline_entry(dom, n=w.n, s=int(w.B.shape[1]), fp64_probe=fp64_tflops)
+        if args.workers > 1:
+            roofline["note"] = (f"launch durations of the timed region, where {args.workers} solves share the "
+                                f"GPU at a time; roofline_isolated times the same family alone")
         roofline_iso = None
         if iso_prof:
             same = [f for f in iso_prof if f["name"] == dom["name"]]
