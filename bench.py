@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--nparams", type=int, default=20)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     # host threads (each with its own stream and context) sharing a shift's independent solves
     ap.add_argument("--workers", type=int, default=4)
     # single-kernel case (for profiler captures): H = V^T W or W -= V H at n = side^3, s = 8
@@ -310,8 +311,9 @@ class Sweep:
     every system.  After each build the shift's solves are independent; `workers` host
     threads, each with its own stream and context, take them round-robin."""
 
-    def __init__(self, sg, torch, ctx, w, host_inputs=False, workers=1):
+    def __init__(self, sg, torch, ctx, w, host_inputs=False, workers=1, prec=0):
         self.sg, self.torch, self.ctx, self.w = sg, torch, ctx, w
+        self.prec = prec  # 0: FP64 factors; sg.PREC_FP32: FP32 least squares and factors
         n = w.n
         self.n = n
         self.s = w.B.shape[1]
@@ -367,7 +369,7 @@ class Sweep:
             else:
                 sg.spai_assemble(wk.ctx, self.aff_now, sg.affine_coefficients(w.params[i], s), wk.va)
                 A = sg.csr(n, rp, ci, wk.va, nnz)
-                pc, _ = sg.spai_update(wk.ctx, base, A, sg.UPDATE_FIRST)
+                pc, _ = sg.spai_update(wk.ctx, base, A, sg.UPDATE_FIRST | self.prec)
             with torch.cuda.stream(wk.stream):
                 wk.X.zero_()
             st, info, rel = sg.block_solve(wk.ctx, A, pc, self.s, self.B, n, wk.X, n,
@@ -389,7 +391,7 @@ class Sweep:
         for s in w.shifts:
             sg.spai_assemble(ctx, aff, sg.affine_coefficients(w.params[0], s), self.vb)
             A0 = sg.csr(n, rp, ci, self.vb, nnz)
-            base, _ = sg.spai_build(ctx, A0, sg.PATTERN_A)  # returns with the build complete
+            base, _ = sg.spai_build(ctx, A0, sg.PATTERN_A | self.prec)  # returns with the build complete
             if self.pool is None:
                 res = [self._solve(self.workers[0], 0, s, base, A0, rp, ci, nnz)]
             else:
@@ -508,6 +510,38 @@ def main():
         t_max, total_solves = t_local, float(solves)
     value = total_solves / t_max
 
+    # the same sweep with FP32 SPAI factors (SPAI_PREC_FP32: FP32 least squares and factor
+    # storage, FP64 apply arithmetic, FP64 solve and true residuals to the same tolerance)
+    mixed = None
+    if not args.no_mixed:
+        ms_ = Sweep(sg, torch, ctx, w, workers=args.workers, prec=sg.PREC_FP32)
+        for _ in range(max(1, args.warmup)):
+            ms_.step()
+        ms_.solves, ms_.iters = 0, []
+        barrier()
+        m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        m0.record(stream)
+        for _ in range(args.steps):
+            ms_.step()
+        for wk in ms_.workers:
+            ev = torch.cuda.Event()
+            ev.record(wk.stream)
+            stream.wait_event(ev)
+        m1.record(stream)
+        barrier()
+        mt = m0.elapsed_time(m1) / 1e3
+        if dist is not None:
+            t = torch.tensor([mt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            mt = t.item()
+        mixed = {"value": ms_.solves * world / mt, "unit": UNIT, "ms_per_step": 1e3 * mt / args.steps,
+                 "dtype": "f64 solve (Gram-Schmidt f64-accurate on tensor cores), f32 SPAI factors",
+                 "gmres_iterations": {"mean": float(np.mean(ms_.iters)), "min": int(min(ms_.iters)),
+                                      "max": int(max(ms_.iters))},
+                 "note": "same sweep and true-residual tolerance; SPAI build/update solved and stored in "
+                         "FP32, applied with FP64 products and sums"}
+        ms_.close()
+
     # the dominant kernels once more with one solve at a time (no other stream sharing the
     # GPU): their own speed, beside the timed region's contended launch durations
     iso_prof = None
@@ -569,7 +603,8 @@ def main():
             "data": "synthetic", "config": {**workload_config(w, nnz_expected),
                                             "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                                             "workers": args.workers},
-            "roofline": roofline, "roofline_isolated": roofline_iso, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "roofline": roofline, "roofline_isolated": roofline_iso, "mixed_precision": mixed,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "fp64_tflops_measured": fp64_tflops,
             "gmres_iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)),
                                  "max": int(max(iters))},

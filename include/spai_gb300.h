@@ -67,6 +67,14 @@ typedef struct spai_pc_s *spai_pc;
 #define SPAI_PATTERN_A 0   /* J_k = rows of column k of A */
 #define SPAI_PATTERN_A2 1  /* J_k = rows of column k of A^2 (structural) */
 
+/* Working precision of a factor, OR-ed into spai_build's pattern_kind or spai_update's
+ * approach.  Default FP64.  SPAI_PREC_FP32: the column least-squares problems are solved
+ * in FP32 (A's values rounded once) and the factor is stored in FP32; every apply reads
+ * the FP32 values and forms products and sums in FP64, so the preconditioner stays an
+ * exactly linear operator and block_solve's FP64 residuals and tolerance are unchanged.
+ * No counterpart in the paper: the mixed-precision form of its preconditioner. */
+#define SPAI_PREC_FP32 0x100
+
 /* Update approaches of Table 1 (Sec. 2.3). */
 #define SPAI_UPDATE_FIRST 1    /* min ||A(1) - A(l) Q||_F, P_l = Q_l P_1 (proposed, Sec. 2.4) */
 #define SPAI_UPDATE_CHAINED 2  /* min ||A(l-1) - A(l) Q||_F, P_l = Q_l P_{l-1} */
@@ -162,7 +170,9 @@ SPAI_API spai_status spai_affine_destroy(spai_affine aff);
  * ---------------------------------------------------------------------------------- */
 
 /* Build P for A (device CSR, values read during the call).  pattern_kind is
- * SPAI_PATTERN_A or SPAI_PATTERN_A2.  The handle keeps the pattern analysis (I_k, J_k),
+ * SPAI_PATTERN_A or SPAI_PATTERN_A2, optionally OR SPAI_PREC_FP32 (FP32 least squares
+ * and factor, rank-deficiency test |R_cc| <= 1e-5 max|R_tt|).  The handle keeps the
+ * pattern analysis (I_k, J_k),
  * A's values in column order (for later updates) and P in row order (for the apply).
  * Synchronises once (reads index-set sizes and the column status).  Returns
  * SPAI_ESINGULAR if some column problem is rank deficient (|I_k| < |J_k| or
@@ -176,7 +186,8 @@ SPAI_API spai_status spai_build(spai_ctx ctx, const spai_csr *A, int32_t pattern
  * SPAI_UPDATE_CHAINED: A(1) is `base`'s own matrix).  The preconditioner of A(l) is
  * P_l = Q_l P_base, applied factored as Q_l (P_base X).  No pattern analysis is redone.
  * `base` must stay alive while the result is used.  Synchronises once (column status).
- * Returns SPAI_ESINGULAR like spai_build. */
+ * approach may be OR-ed with SPAI_PREC_FP32 (this factor in FP32; the chain may mix
+ * precisions).  Returns SPAI_ESINGULAR like spai_build. */
 SPAI_API spai_status spai_update(spai_ctx ctx, spai_pc base, const spai_csr *A_new, int32_t approach,
                         spai_pc *out);
 

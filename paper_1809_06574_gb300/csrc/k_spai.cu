@@ -37,21 +37,29 @@ __device__ __forceinline__ int bsearch_i32(const int32_t *__restrict__ a, int32_
     return -1;
 }
 
-template <int T>
-__device__ __forceinline__ double team_sum(double v, unsigned mask)
+template <int T, typename R>
+__device__ __forceinline__ R team_sum(R v, unsigned mask)
 {
 #pragma unroll
     for (int o = T / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
     return v;
 }
 
+// rank-deficiency threshold on |R_cc| / max |R_tt| for the working precision
+template <typename R> __device__ __forceinline__ R singular_rel();
+template <> __device__ __forceinline__ double singular_rel<double>() { return 1e-14; }
+template <> __device__ __forceinline__ float singular_rel<float>() { return 1e-5f; }
+
 constexpr int kBlock = 128;
 
 // per-column shared-memory region: Ahat (maxJ x ld, column-major) | rhs (ld) | rdiag (maxJ)
-template <int T>
+// R: working precision (double, or float for SPAI_PREC_FP32); A's values are read in FP64
+// and rounded once to R; the result is written to out_val (R = double) or out_val32.
+template <int T, typename R>
 __global__ void __launch_bounds__(kBlock) k_spai_columns(ColumnProblem cp, int ld, int maxJ, int L)
 {
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *smem = reinterpret_cast<R *>(smem_raw);
     const int lane = threadIdx.x & 31;
     const int team = threadIdx.x / T, tl = threadIdx.x % T;
     const int teams = blockDim.x / T;
@@ -59,9 +67,9 @@ __global__ void __launch_bounds__(kBlock) k_spai_columns(ColumnProblem cp, int l
     const int64_t k = (int64_t)blockIdx.x * teams + team;
     if (k >= cp.n) return;  // whole team leaves together
 
-    double *Ah = smem + (size_t)team * L;
-    double *rhs = Ah + (size_t)maxJ * ld;
-    double *rdiag = rhs + ld;
+    R *Ah = smem + (size_t)team * L;
+    R *rhs = Ah + (size_t)maxJ * ld;
+    R *rdiag = rhs + ld;
 
     const int32_t ia = __ldg(cp.Iptr + k), ni = __ldg(cp.Iptr + k + 1) - ia;
     const int32_t ja = __ldg(cp.Jptr + k), nj = __ldg(cp.Jptr + k + 1) - ja;
@@ -73,8 +81,8 @@ __global__ void __launch_bounds__(kBlock) k_spai_columns(ColumnProblem cp, int l
         }
         return;
     }
-    for (int e = tl; e < nj * ld; e += T) Ah[e] = 0.0;
-    for (int r = tl; r < ni; r += T) rhs[r] = 0.0;
+    for (int e = tl; e < nj * ld; e += T) Ah[e] = R(0);
+    for (int r = tl; r < ni; r += T) rhs[r] = R(0);
     __syncwarp(mask);
 
     // ---- gather Ahat = A(I_k, J_k) and the right-hand side
@@ -83,19 +91,19 @@ __global__ void __launch_bounds__(kBlock) k_spai_columns(ColumnProblem cp, int l
         const int32_t a = __ldg(cp.colptr + j), b = __ldg(cp.colptr + j + 1);
         for (int32_t q = a + tl; q < b; q += T) {
             const int pos = bsearch_i32(Ik, ni, __ldg(cp.rowind + q));
-            if (pos >= 0) Ah[c * ld + pos] = __ldg(cp.cval + q);
+            if (pos >= 0) Ah[c * ld + pos] = (R)__ldg(cp.cval + q);
         }
     }
     if (cp.mode == 0) {
         if (tl == 0) {
             const int pos = bsearch_i32(Ik, ni, (int32_t)k);
-            if (pos >= 0) rhs[pos] = 1.0;
+            if (pos >= 0) rhs[pos] = R(1);
         }
     } else {
         const int32_t a = __ldg(cp.r_colptr + k), b = __ldg(cp.r_colptr + k + 1);
         for (int32_t q = a + tl; q < b; q += T) {
             const int pos = bsearch_i32(Ik, ni, __ldg(cp.r_rowind + q));
-            if (pos >= 0) rhs[pos] = __ldg(cp.r_val + q);
+            if (pos >= 0) rhs[pos] = (R)__ldg(cp.r_val + q);
         }
     }
     __syncwarp(mask);
@@ -103,66 +111,72 @@ __global__ void __launch_bounds__(kBlock) k_spai_columns(ColumnProblem cp, int l
     // ---- Householder QR; column c keeps its reflector v below (and on) the diagonal
     bool singular = ni < nj;
     for (int c = 0; c < nj && !singular; ++c) {
-        const double *vc = Ah + c * ld;
-        double ss = 0.0;
+        const R *vc = Ah + c * ld;
+        R ss = R(0);
         for (int r = c + tl; r < ni; r += T) ss = fma(vc[r], vc[r], ss);
-        ss = team_sum<T>(ss, mask);
-        const double alpha = sqrt(ss);
-        if (!(alpha > 0.0)) {
+        ss = team_sum<T, R>(ss, mask);
+        const R alpha = sqrt(ss);
+        if (!(alpha > R(0))) {
             singular = true;
             break;
         }
-        const double xc = vc[c];
-        const double sgn = (xc >= 0.0) ? 1.0 : -1.0;
-        const double inv = 1.0 / (alpha * (alpha + fabs(xc)));  // 2 / v^T v
+        const R xc = vc[c];
+        const R sgn = (xc >= R(0)) ? R(1) : R(-1);
+        const R inv = R(1) / (alpha * (alpha + fabs(xc)));  // 2 / v^T v
         __syncwarp(mask);
         if (tl == (c % T)) Ah[c * ld + c] = xc + sgn * alpha;
         if (tl == 0) rdiag[c] = -sgn * alpha;
         __syncwarp(mask);
         for (int t = c + 1; t <= nj; ++t) {  // t == nj is the right-hand side
-            double *col = (t < nj) ? (Ah + t * ld) : rhs;
-            double d = 0.0;
+            R *col = (t < nj) ? (Ah + t * ld) : rhs;
+            R d = R(0);
             for (int r = c + tl; r < ni; r += T) d = fma(vc[r], col[r], d);
-            const double g = team_sum<T>(d, mask) * inv;
+            const R g = team_sum<T, R>(d, mask) * inv;
             for (int r = c + tl; r < ni; r += T) col[r] = fma(-g, vc[r], col[r]);
         }
         __syncwarp(mask);
     }
     if (!singular) {
-        double rmax = 0.0;
+        R rmax = R(0);
         for (int c = 0; c < nj; ++c) rmax = fmax(rmax, fabs(rdiag[c]));
         for (int c = 0; c < nj; ++c)
-            if (fabs(rdiag[c]) <= 1e-14 * rmax) singular = true;
+            if (fabs(rdiag[c]) <= singular_rel<R>() * rmax) singular = true;
     }
     if (singular) {
-        for (int c = tl; c < nj; c += T) cp.out_val[cp.out_map[ja + c]] = 0.0;
+        for (int c = tl; c < nj; c += T) {
+            if (cp.out_val32) cp.out_val32[cp.out_map[ja + c]] = 0.0f;
+            else cp.out_val[cp.out_map[ja + c]] = 0.0;
+        }
         if (tl == 0) cp.col_status[k] = 1;
         return;
     }
 
     // ---- back substitution R m = (Q^T rhs)(0:nj); m overwrites rhs(0:nj)
     for (int c = nj - 1; c >= 0; --c) {
-        double acc = 0.0;
+        R acc = R(0);
         for (int t = c + 1 + tl; t < nj; t += T) acc = fma(Ah[t * ld + c], rhs[t], acc);
-        acc = team_sum<T>(acc, mask);
+        acc = team_sum<T, R>(acc, mask);
         if (tl == 0) rhs[c] = (rhs[c] - acc) / rdiag[c];
         __syncwarp(mask);
     }
-    for (int c = tl; c < nj; c += T) cp.out_val[cp.out_map[ja + c]] = rhs[c];
+    for (int c = tl; c < nj; c += T) {
+        if (cp.out_val32) cp.out_val32[cp.out_map[ja + c]] = (float)rhs[c];
+        else cp.out_val[cp.out_map[ja + c]] = (double)rhs[c];
+    }
     if (tl == 0) cp.col_status[k] = 0;
 }
 
-template <int T>
+template <int T, typename R>
 int launch_team(cudaStream_t st, const ColumnProblem &cp, int ld, int maxJ, int L, int threads)
 {
     const int teams = threads / T;
-    const size_t smem = (size_t)teams * L * sizeof(double);
+    const size_t smem = (size_t)teams * L * sizeof(R);
     if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(k_spai_columns<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_spai_columns<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return -1;
     const int64_t blocks = ((int64_t)cp.n + teams - 1) / teams;
-    k_spai_columns<T><<<(unsigned)blocks, threads, smem, st>>>(cp, ld, maxJ, L);
+    k_spai_columns<T, R><<<(unsigned)blocks, threads, smem, st>>>(cp, ld, maxJ, L);
     note_launches(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -175,15 +189,17 @@ bool spai_columns_fit(int32_t maxI, int32_t maxJ)
     return L * sizeof(double) <= 220 * 1024;
 }
 
-int launch_spai_columns(cudaStream_t st, const ColumnProblem &cp, int32_t maxI, int32_t maxJ)
+namespace {
+
+template <typename R>
+int launch_columns(cudaStream_t st, const ColumnProblem &cp, int32_t maxI, int32_t maxJ)
 {
-    if (cp.n <= 0) return 0;
     const int ld = maxI < 1 ? 1 : maxI;
     const int mj = maxJ < 1 ? 1 : maxJ;
     int L = mj * ld + ld + mj;
-    L |= 1;  // odd stride in doubles spreads the teams over the shared-memory banks
+    L |= 1;  // odd stride spreads the teams over the shared-memory banks
     // smallest team whose 128-thread block fits in ~110 KB (two blocks per SM)
-    const size_t per = (size_t)L * sizeof(double);
+    const size_t per = (size_t)L * sizeof(R);
     int T = 1;
     while (T < 32 && (size_t)(kBlock / T) * per > 110 * 1024) T *= 2;
     int threads = kBlock;
@@ -191,13 +207,21 @@ int launch_spai_columns(cudaStream_t st, const ColumnProblem &cp, int32_t maxI, 
     if (T == 32 && (size_t)(threads / 32) * per > 200 * 1024) threads = 32;
     if ((size_t)(threads / T) * per > 220 * 1024) return -1;
     switch (T) {
-    case 1: return launch_team<1>(st, cp, ld, mj, L, threads);
-    case 2: return launch_team<2>(st, cp, ld, mj, L, threads);
-    case 4: return launch_team<4>(st, cp, ld, mj, L, threads);
-    case 8: return launch_team<8>(st, cp, ld, mj, L, threads);
-    case 16: return launch_team<16>(st, cp, ld, mj, L, threads);
-    default: return launch_team<32>(st, cp, ld, mj, L, threads);
+    case 1: return launch_team<1, R>(st, cp, ld, mj, L, threads);
+    case 2: return launch_team<2, R>(st, cp, ld, mj, L, threads);
+    case 4: return launch_team<4, R>(st, cp, ld, mj, L, threads);
+    case 8: return launch_team<8, R>(st, cp, ld, mj, L, threads);
+    case 16: return launch_team<16, R>(st, cp, ld, mj, L, threads);
+    default: return launch_team<32, R>(st, cp, ld, mj, L, threads);
     }
+}
+
+}  // namespace
+
+int launch_spai_columns(cudaStream_t st, const ColumnProblem &cp, int32_t maxI, int32_t maxJ)
+{
+    if (cp.n <= 0) return 0;
+    return cp.out_val32 ? launch_columns<float>(st, cp, maxI, maxJ) : launch_columns<double>(st, cp, maxI, maxJ);
 }
 
 }  // namespace spai

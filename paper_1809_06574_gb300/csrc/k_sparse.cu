@@ -294,6 +294,14 @@ __global__ void k_gather_f64(int64_t count, const int32_t *__restrict__ idx,
         dst[i] = src[idx[i]];
 }
 
+__global__ void k_gather_f32_f64(int64_t count, const int32_t *__restrict__ idx, const float *__restrict__ src,
+                                 double *__restrict__ dst)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (double)src[idx[i]];
+}
+
 __global__ void k_invert_perm(int64_t count, const int32_t *__restrict__ perm,
                               int32_t *__restrict__ inv)
 {
@@ -340,10 +348,10 @@ __global__ void k_fill_i32(int64_t count, int32_t v, int32_t *dst)
 // ---------------------------------------------------------------------------------
 // CSR times row-major block: S consecutive lanes per row, lane c owns column c
 // ---------------------------------------------------------------------------------
-template <int S>
+template <int S, typename V>
 __global__ void __launch_bounds__(kThreads) k_spmm(int32_t n, const int32_t *__restrict__ rowptr,
                                                    const int32_t *__restrict__ colind,
-                                                   const double *__restrict__ val,
+                                                   const V *__restrict__ val,
                                                    const double *__restrict__ X,
                                                    double *__restrict__ Y)
 {
@@ -354,7 +362,7 @@ __global__ void __launch_bounds__(kThreads) k_spmm(int32_t n, const int32_t *__r
     int32_t a = __ldg(rowptr + row), b = __ldg(rowptr + row + 1);
     double acc = 0.0;
     for (int32_t q = a; q < b; ++q)
-        acc = fma(__ldg(val + q), __ldg(X + (int64_t)__ldg(colind + q) * S + c), acc);
+        acc = fma((double)__ldg(val + q), __ldg(X + (int64_t)__ldg(colind + q) * S + c), acc);
     Y[row * S + c] = acc;
 }
 
@@ -505,6 +513,13 @@ int launch_gather_f64(cudaStream_t st, int64_t count, const int32_t *idx, const 
     return check_launch();
 }
 
+int launch_gather_f32_f64(cudaStream_t st, int64_t count, const int32_t *idx, const float *src, double *dst)
+{
+    if (count <= 0) return 0;
+    k_gather_f32_f64<<<grid_for(count), kThreads, 0, st>>>(count, idx, src, dst);
+    return check_launch();
+}
+
 int launch_invert_perm(cudaStream_t st, int64_t count, const int32_t *perm, int32_t *inv)
 {
     if (count <= 0) return 0;
@@ -548,20 +563,37 @@ int launch_compare_i32(cudaStream_t st, int64_t count, const int32_t *a, const i
     return check_launch();
 }
 
-int launch_spmm(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr,
-                const int32_t *colind, const double *val, const double *X, double *Y)
+namespace {
+
+template <typename V>
+int spmm_any(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr, const int32_t *colind, const V *val,
+             const double *X, double *Y)
 {
     if (n <= 0) return 0;
     int g = grid_for((int64_t)n * s);
     switch (s) {
-    case 1: k_spmm<1><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, Y); break;
-    case 2: k_spmm<2><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, Y); break;
-    case 4: k_spmm<4><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, Y); break;
-    case 8: k_spmm<8><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, Y); break;
-    case 16: k_spmm<16><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, Y); break;
+    case 1: k_spmm<1, V><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, Y); break;
+    case 2: k_spmm<2, V><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, Y); break;
+    case 4: k_spmm<4, V><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, Y); break;
+    case 8: k_spmm<8, V><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, Y); break;
+    case 16: k_spmm<16, V><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, Y); break;
     default: return -1;
     }
     return check_launch();
+}
+
+}  // namespace
+
+int launch_spmm(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr,
+                const int32_t *colind, const double *val, const double *X, double *Y)
+{
+    return spmm_any<double>(st, s, n, rowptr, colind, val, X, Y);
+}
+
+int launch_spmm_f32v(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr, const int32_t *colind,
+                     const float *val, const double *X, double *Y)
+{
+    return spmm_any<float>(st, s, n, rowptr, colind, val, X, Y);
 }
 
 int launch_pack(cudaStream_t st, int32_t s, int32_t n, const double *src, int64_t ld, double *dst)

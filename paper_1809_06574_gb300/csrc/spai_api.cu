@@ -78,7 +78,8 @@ struct spai_pc_s {
     spai_pc parent = nullptr;
     spai_pc root = nullptr;
     int depth = 0;
-    double *fval = nullptr;    // own factor, P's CSR order
+    double *fval = nullptr;    // own factor, P's CSR order (FP64 factors)
+    float *fval32 = nullptr;   // the same for SPAI_PREC_FP32 factors
     double *a_cval = nullptr;  // this matrix's values in CSC order
     int32_t *status = nullptr;
 };
@@ -462,6 +463,7 @@ spai_status run_columns(spai_ctx ctx, spai_pc pc, int mode, const double *rhs_cv
     cp.r_val = rhs_cval;
     cp.out_map = s->p_map;
     cp.out_val = pc->fval;
+    cp.out_val32 = pc->fval32;
     cp.col_status = pc->status;
     cp.d_err = ctx->d_err;
     if (s->n == 0) return SPAI_OK;
@@ -484,21 +486,23 @@ spai_status run_columns(spai_ctx ctx, spai_pc pc, int mode, const double *rhs_cv
     return SPAI_OK;
 }
 
-spai_status pc_alloc(spai_ctx ctx, Sym *s, spai_pc *out)
+spai_status pc_alloc(spai_ctx ctx, Sym *s, bool fp32, spai_pc *out)
 {
     spai_pc pc = new spai_pc_s();
     pc->ctx = ctx;
     pc->sym = s;
     spai_status st;
-    if ((st = dalloc_n(ctx, &pc->fval, s->nnzP)) || (st = dalloc_n(ctx, &pc->a_cval, s->nnzA)) ||
-        (st = dalloc_n(ctx, &pc->status, s->n))) {
+    if ((fp32 ? (st = dalloc_n(ctx, &pc->fval32, s->nnzP)) : (st = dalloc_n(ctx, &pc->fval, s->nnzP))) ||
+        (st = dalloc_n(ctx, &pc->a_cval, s->nnzA)) || (st = dalloc_n(ctx, &pc->status, s->n))) {
         dfree(ctx, pc->fval);
+        dfree(ctx, pc->fval32);
         dfree(ctx, pc->a_cval);
         dfree(ctx, pc->status);
         delete pc;
         return st;
     }
-    if (s->nnzP) CU(cudaMemsetAsync(pc->fval, 0, (size_t)s->nnzP * 8, ctx->stream), "memset");
+    if (s->nnzP && pc->fval) CU(cudaMemsetAsync(pc->fval, 0, (size_t)s->nnzP * 8, ctx->stream), "memset");
+    if (s->nnzP && pc->fval32) CU(cudaMemsetAsync(pc->fval32, 0, (size_t)s->nnzP * 4, ctx->stream), "memset");
     *out = pc;
     return SPAI_OK;
 }
@@ -514,9 +518,15 @@ spai_status apply_rm(spai_ctx ctx, spai_pc pc, int32_t s, const double *X, doubl
         spai_pc h = chain[i];
         double *dst = (i == 0) ? Y : bufs[(chain.size() - 1 - i) & 1];
         const double nz = h->sym->nnzP, nn = h->sym->n;
-        PKL("spmm_P", 2.0 * nz * s, 12.0 * nz + 4.0 * (nn + 1) + 16.0 * nn * s,
-            launch_spmm(ctx->stream, s, h->sym->n, h->sym->p_rowptr, h->sym->p_colind, h->fval, cur, dst),
-            "preconditioner apply");
+        if (h->fval32) {
+            PKL("spmm_P", 2.0 * nz * s, 8.0 * nz + 4.0 * (nn + 1) + 16.0 * nn * s,
+                launch_spmm_f32v(ctx->stream, s, h->sym->n, h->sym->p_rowptr, h->sym->p_colind, h->fval32, cur, dst),
+                "preconditioner apply");
+        } else {
+            PKL("spmm_P", 2.0 * nz * s, 12.0 * nz + 4.0 * (nn + 1) + 16.0 * nn * s,
+                launch_spmm(ctx->stream, s, h->sym->n, h->sym->p_rowptr, h->sym->p_colind, h->fval, cur, dst),
+                "preconditioner apply");
+        }
         cur = dst;
     }
     return SPAI_OK;
@@ -765,6 +775,8 @@ extern "C" spai_status spai_build(spai_ctx ctx, const spai_csr *A, int32_t patte
 {
     if (!ctx || !out) return fail(ctx, SPAI_EINVAL, "NULL argument");
     *out = nullptr;
+    const bool fp32 = (pattern_kind & SPAI_PREC_FP32) != 0;
+    pattern_kind &= ~SPAI_PREC_FP32;
     if (pattern_kind != SPAI_PATTERN_A && pattern_kind != SPAI_PATTERN_A2)
         return fail(ctx, SPAI_EINVAL, "unknown pattern kind %d", pattern_kind);
     spai_status st = validate_device_csr(ctx, A, "A");
@@ -772,7 +784,7 @@ extern "C" spai_status spai_build(spai_ctx ctx, const spai_csr *A, int32_t patte
     Sym *s = nullptr;
     if ((st = sym_create(ctx, A, pattern_kind, &s))) return st;
     spai_pc pc = nullptr;
-    if ((st = pc_alloc(ctx, s, &pc))) { sym_release(s); return st; }
+    if ((st = pc_alloc(ctx, s, fp32, &pc))) { sym_release(s); return st; }
     pc->root = pc;
     if (s->nnzA)
         PKL("gather_csc", 0.0, 20.0 * s->nnzA, launch_gather_f64(ctx->stream, s->nnzA, s->a_perm, A->val, pc->a_cval),
@@ -787,6 +799,8 @@ extern "C" spai_status spai_update(spai_ctx ctx, spai_pc base, const spai_csr *A
 {
     if (!ctx || !out || !base) return fail(ctx, SPAI_EINVAL, "NULL argument");
     *out = nullptr;
+    const bool fp32 = (approach & SPAI_PREC_FP32) != 0;
+    approach &= ~SPAI_PREC_FP32;
     if (approach != SPAI_UPDATE_FIRST && approach != SPAI_UPDATE_CHAINED)
         return fail(ctx, SPAI_EINVAL, "unknown update approach %d", approach);
     spai_status st = check_csr_args(ctx, A_new, "A_new");
@@ -805,7 +819,7 @@ extern "C" spai_status spai_update(spai_ctx ctx, spai_pc base, const spai_csr *A
         if (h) return fail(ctx, SPAI_EINVAL, "A_new does not have the base matrix's sparsity pattern");
     }
     spai_pc pc = nullptr;
-    if ((st = pc_alloc(ctx, s, &pc))) return st;
+    if ((st = pc_alloc(ctx, s, fp32, &pc))) return st;
     s->refs++;
     spai_pc from = (approach == SPAI_UPDATE_FIRST) ? base->root : base;
     pc->parent = from;
@@ -838,7 +852,12 @@ extern "C" spai_status spai_pc_export(spai_ctx ctx, spai_pc pc, int32_t *Jptr, i
     const int32_t n = s->n;
     if (Jptr) CU(cudaMemcpyAsync(Jptr, s->Jptr, ((size_t)n + 1) * 4, cudaMemcpyDeviceToDevice, ctx->stream), "export");
     if (Jind && s->nnzP) CU(cudaMemcpyAsync(Jind, s->Jind, (size_t)s->nnzP * 4, cudaMemcpyDeviceToDevice, ctx->stream), "export");
-    if (val && s->nnzP) KL(launch_gather_f64(ctx->stream, s->nnzP, s->p_map, pc->fval, val), "export values");
+    if (val && s->nnzP) {
+        if (pc->fval32)
+            KL(launch_gather_f32_f64(ctx->stream, s->nnzP, s->p_map, pc->fval32, val), "export values");
+        else
+            KL(launch_gather_f64(ctx->stream, s->nnzP, s->p_map, pc->fval, val), "export values");
+    }
     if (Iptr) CU(cudaMemcpyAsync(Iptr, s->Iptr, ((size_t)n + 1) * 4, cudaMemcpyDeviceToDevice, ctx->stream), "export");
     if (Ilist && s->nI) CU(cudaMemcpyAsync(Ilist, s->Ilist, (size_t)s->nI * 4, cudaMemcpyDeviceToDevice, ctx->stream), "export");
     if (col_status && n) CU(cudaMemcpyAsync(col_status, pc->status, (size_t)n * 4, cudaMemcpyDeviceToDevice, ctx->stream), "export");
@@ -850,6 +869,7 @@ extern "C" spai_status spai_pc_destroy(spai_pc pc)
     if (!pc) return SPAI_EINVAL;
     spai_ctx ctx = pc->ctx;
     dfree(ctx, pc->fval);
+    dfree(ctx, pc->fval32);
     dfree(ctx, pc->a_cval);
     dfree(ctx, pc->status);
     sym_release(pc->sym);
@@ -1335,8 +1355,12 @@ extern "C" spai_status spai_pc_apply_noalloc(spai_ctx ctx, spai_pc pc, int32_t s
         spai_pc h = pc;
         for (int hop = 0; hop < i; ++hop) h = h->parent;
         double *dst = (i == 0) ? yr : bufs[(len - 1 - i) & 1];
-        KL(launch_spmm(ctx->stream, s, n, h->sym->p_rowptr, h->sym->p_colind, h->fval, cur, dst),
-           "preconditioner apply");
+        if (h->fval32)
+            KL(launch_spmm_f32v(ctx->stream, s, n, h->sym->p_rowptr, h->sym->p_colind, h->fval32, cur, dst),
+               "preconditioner apply");
+        else
+            KL(launch_spmm(ctx->stream, s, n, h->sym->p_rowptr, h->sym->p_colind, h->fval, cur, dst),
+               "preconditioner apply");
         cur = dst;
     }
     KL(launch_unpack(ctx->stream, s, n, yr, Y, ldy), "unpack");

@@ -66,6 +66,7 @@ int launch_colunion_fill(cudaStream_t st, int32_t n, const int32_t *Lptr, const 
                          int32_t *out_list, int *d_err);
 int launch_gather_f64(cudaStream_t st, int64_t count, const int32_t *idx, const double *src,
                       double *dst);
+int launch_gather_f32_f64(cudaStream_t st, int64_t count, const int32_t *idx, const float *src, double *dst);
 int launch_invert_perm(cudaStream_t st, int64_t count, const int32_t *perm, int32_t *inv);
 int launch_max_i32_diff(cudaStream_t st, int32_t n, const int32_t *ptr, int32_t *d_max);
 int launch_fill_i32(cudaStream_t st, int64_t count, int32_t v, int32_t *dst);
@@ -76,6 +77,9 @@ int launch_compare_i32(cudaStream_t st, int64_t count, const int32_t *a, const i
 // row-major blocks: X[r * s + c]
 int launch_spmm(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr,
                 const int32_t *colind, const double *val, const double *X, double *Y);
+// same with FP32 values (products and sums in FP64)
+int launch_spmm_f32v(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr, const int32_t *colind,
+                     const float *val, const double *X, double *Y);
 int launch_pack(cudaStream_t st, int32_t s, int32_t n, const double *src, int64_t ld, double *dst);
 int launch_unpack(cudaStream_t st, int32_t s, int32_t n, const double *src, double *dst,
                   int64_t ld);
@@ -92,6 +96,7 @@ struct ColumnProblem {
     const double *r_val;             // rhs matrix (CSC values) in update mode
     const int32_t *out_map;          // J position -> position in the output array
     double *out_val;
+    float *out_val32;                // non-null: solve in FP32 and write here instead
     int32_t *col_status;             // 0 ok, 1 singular
     int *d_err;
 };
