@@ -67,21 +67,23 @@ __host__ __device__ constexpr int nmma(int p) { return ((8 * nq(p) + 15) / 16) *
 static_assert(8 * 8 + nmma(8) <= kBufCols && 8 * 7 + nmma(7) <= kBufCols, "class columns");
 static_assert(nmma(0) <= 8 * (kDig + 1), "B row groups");
 
-// ---- Gram kernel shared memory: raw ring | digit ring | slack | barriers | flag | tmem | exps | maxima
-constexpr int kDRawStage = 24 * 1024;   // raw rows of S sub-tiles x (blocks + W)
-constexpr int kDRawStages = 3;
-constexpr int kDDigStage = 42 * 1024;   // digit pieces of S sub-tiles
+// ---- Gram kernel shared memory: raw ring | digit ring | slack | ... | barriers, flag, tmem, exps,
+// maxima at the end of the allocation.  The ring depths follow the tile's block count: a
+// stage carries S sub-tiles (<= kDDigStage / kDRawStage bytes), three digit stages, and as
+// many raw stages (up to 8) as the rest holds, so that the copies run well ahead.
+constexpr int kDRawStage = 24 * 1024;   // cap of one raw stage: S sub-tiles x (blocks + W)
+constexpr int kDRawMax = 8;
+constexpr int kDDigStage = 42 * 1024;   // cap of one digit stage
 constexpr int kDDigStages = 3;
-constexpr int kDOffDig = kDRawStages * kDRawStage;
-constexpr int kDOffBar = kDOffDig + kDDigStages * kDDigStage + 4096;  // + slack read by M = 128 MMAs
-constexpr int kDBars = 2 * (kDRawStages + kDDigStages + kBufs);
+constexpr int kDSmem = 227 * 1024;
+constexpr int kDOffBar = kDSmem - 1024;
+constexpr int kDBars = 2 * (kDRawMax + kDDigStages + kBufs);
 constexpr int kDOffFlag = kDOffBar + kDBars * 8;
 constexpr int kDOffTmem = kDOffFlag + 8;
 constexpr int kDOffExp = kDOffTmem + 8;
 constexpr int kDOffMax = kDOffExp + kS * 4;
-constexpr int kDSmem = kDOffMax + kCW * kS * 8;
-static_assert(kDSmem <= 227 * 1024, "Gram kernel shared memory");
-static_assert(kDOffDig % 16 == 0 && kDDigStage % 16 == 0 && kDOffBar % 8 == 0, "alignment");
+static_assert(kDOffMax + kCW * kS * 8 <= kDSmem, "Gram kernel shared memory");
+static_assert(2 * kDRawStage + kDDigStages * kDDigStage + 4096 <= kDOffBar, "two raw stages at least");
 
 // bytes of one sub-tile's digit pieces for nvb blocks: A planes + 9 W digits + a zero group
 __host__ __device__ constexpr int dsub_bytes(int nvb) { return kDig * nvb * kPiece + (kDig + 1) * kPiece; }
@@ -340,14 +342,28 @@ __device__ __forceinline__ void expand8(const uint64_t f[8], char *dst, int pstr
     }
 }
 
-// fixed-point copy of n x 8 blocks (count values): |x| < 2 required (ERR_RANGE otherwise)
-__global__ void k_to_fixed(int64_t count, const double *__restrict__ X, uint64_t *__restrict__ F, int *err)
+// Fixed-point copies of nblocks n x 8 row-major blocks X (|x| < 2, else ERR_RANGE), in
+// one or both layouts: F_row like X (the update kernel's rows), F_sub sub-tile-major
+// across blocks -- block iblk0 + b, 16-row sub-tile t at ((t * ipad + iblk0 + b) * 16) * 8,
+// 1 KB per (sub-tile, block), rows past n zero -- so that the Gram kernel fetches a
+// sub-tile of all its blocks in one copy.
+__global__ void k_to_fixed(int32_t n, int32_t nblocks, const double *__restrict__ X, uint64_t *__restrict__ F_row,
+                           uint64_t *__restrict__ F_sub, int32_t ipad, int32_t iblk0, int *err)
 {
+    const int64_t nt = ((int64_t)n + kKT - 1) / kKT;
+    const int64_t per = nt * kKT * kS;  // padded entries per block
     bool bad = false;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t f;
-        if (!to_fixed(X[i], 0, f)) bad = true;
-        F[i] = f;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < per * nblocks;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = g / per, e = g - b * per;
+        const int64_t r = e / kS;
+        const int a = (int)(e - r * kS);
+        uint64_t f = 0;
+        if (r < n) {
+            if (!to_fixed(X[(b * n + r) * kS + a], 0, f)) bad = true;
+            if (F_row) F_row[(b * n + r) * kS + a] = f;
+        }
+        if (F_sub) F_sub[(((r / kKT) * ipad + iblk0 + b) * kKT + (r % kKT)) * kS + a] = f;
     }
     if (bad) atomicOr(err, ERR_RANGE);
 }
@@ -361,7 +377,7 @@ __global__ void k_to_fixed(int64_t count, const double *__restrict__ X, uint64_t
 // are scaled by powers of two from this chunk's own column maxima, so the chunk's partial
 // sums carry their own scale.
 __global__ void __launch_bounds__(kThreadsTC, 1)
-    k_block_dot_tc(int32_t n, int32_t nblk, int32_t subs_per_chunk, const uint64_t *__restrict__ Vf,
+    k_block_dot_tc(int32_t n, int32_t nblk, int32_t subs_per_chunk, const uint64_t *__restrict__ Vfs, int32_t ipad,
                    const double *__restrict__ W, double *__restrict__ partial, int *err)
 {
     extern __shared__ __align__(128) char smem[];
@@ -377,9 +393,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     const int nst = (nsub + S - 1) / S;                // stages
     const int sps = (kSegK / kKT) / S;                 // stages per segment (>= 2: S <= 12)
     const int nseg = (nst + sps - 1) / sps;
+    const int rsb = S * (nvb + 1) * kKT * kRawRow, dsb = S * sub_bytes;  // stage bytes
+    const int dig_off = ((kDOffBar - 4096 - kDDigStages * dsb) / rsb < kDRawMax
+                             ? (kDOffBar - 4096 - kDDigStages * dsb) / rsb
+                             : kDRawMax) * rsb;
+    const int R = dig_off / rsb;  // raw stages
     const uint32_t bar0 = smem_u32(smem + kDOffBar);
-    const uint32_t rfull0 = bar0, rempty0 = rfull0 + kDRawStages * 8;
-    const uint32_t dfull0 = rempty0 + kDRawStages * 8, dempty0 = dfull0 + kDDigStages * 8;
+    const uint32_t rfull0 = bar0, rempty0 = rfull0 + kDRawMax * 8;
+    const uint32_t dfull0 = rempty0 + kDRawMax * 8, dempty0 = dfull0 + kDDigStages * 8;
     const uint32_t bfull0 = dempty0 + kDDigStages * 8, bfree0 = bfull0 + kBufs * 8;
     volatile int *flag = reinterpret_cast<volatile int *>(smem + kDOffFlag);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kDOffTmem);
@@ -392,7 +413,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int s = 0; s < kDRawStages; ++s) {
+        for (int s = 0; s < R; ++s) {
             mbar_init(rfull0 + 8 * s, 1);
             mbar_init(rempty0 + 8 * s, kCW);
         }
@@ -412,7 +433,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     for (int e = tid; e < kDDigStages * S * (kPiece / 16); e += kThreadsTC) {
         const int o = e % (kPiece / 16), sd = e / (kPiece / 16);
         const int d = sd / S, sg = sd % S;
-        *reinterpret_cast<uint4 *>(smem + kDOffDig + d * kDDigStage + sg * sub_bytes + kDig * plane + kDig * kPiece +
+        *reinterpret_cast<uint4 *>(smem + dig_off + d * dsb + sg * sub_bytes + kDig * plane + kDig * kPiece +
                                    o * 16) = make_uint4(0, 0, 0, 0);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -423,41 +444,31 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     const bool work = nvb > 0 && nsub > 0;
 
     if (warp == 0) {
-        if (lane == 0 && work) {  // ---- copies of stage k into raw stage k % kDRawStages
+        if (lane == 0 && work) {  // ---- copies of stage k into raw stage k % R
             int issued = 0;
             for (int k = 0; k < nst; ++k) {
-                const int s = k % kDRawStages;
-                if (k >= kDRawStages &&
-                    !mbar_wait_bounded(rempty0 + 8 * s, (uint32_t)(((k - kDRawStages) / kDRawStages) & 1))) {
+                const int s = k % R;
+                if (k >= R && !mbar_wait_bounded(rempty0 + 8 * s, (uint32_t)(((k - R) / R) & 1))) {
                     *flag = 1;
                     break;
                 }
                 if (*flag) break;
                 const int ns = min(S, nsub - k * S);
-                uint32_t total = 0;
-                for (int sg = 0; sg < ns; ++sg) {
-                    const int64_t t = t0 + (int64_t)k * S + sg;
-                    total += (uint32_t)(nvb + 1) * (uint32_t)min((int64_t)kKT, (int64_t)n - t * kKT) * kRawRow;
-                }
+                const int64_t tf = t0 + (int64_t)k * S;  // first sub-tile of the stage
+                const uint32_t wbytes = (uint32_t)min((int64_t)ns * kKT, (int64_t)n - tf * kKT) * kRawRow;
                 const uint32_t fb = rfull0 + 8 * s;
-                mbar_expect_tx(fb, total);
-                char *st = smem + s * kDRawStage;
+                mbar_expect_tx(fb, (uint32_t)(ns * nvb * kKT * kRawRow) + wbytes);
+                char *st = smem + s * rsb;
 #pragma unroll 1
-                for (int sg = 0; sg < ns; ++sg) {
-                    const int64_t t = t0 + (int64_t)k * S + sg;
-                    const uint32_t bytes = (uint32_t)min((int64_t)kKT, (int64_t)n - t * kKT) * kRawRow;
-                    char *sb = st + sg * (nvb + 1) * (kKT * kRawRow);
-#pragma unroll 1
-                    for (int i = 0; i < nvb; ++i)
-                        bulk_copy(smem_u32(sb + i * (kKT * kRawRow)), Vf + ((int64_t)(blk0 + i) * n + t * kKT) * kS,
-                                  bytes, fb);
-                    bulk_copy(smem_u32(sb + nvb * (kKT * kRawRow)), W + t * kKT * kS, bytes, fb);
-                }
+                for (int sg = 0; sg < ns; ++sg)  // all nvb blocks of sub-tile tf + sg: one copy
+                    bulk_copy(smem_u32(st + sg * nvb * (kKT * kRawRow)),
+                              Vfs + (((tf + sg) * ipad + blk0) * kKT) * kS, (uint32_t)(nvb * kKT * kRawRow), fb);
+                bulk_copy(smem_u32(st + S * nvb * (kKT * kRawRow)), W + tf * kKT * kS, wbytes, fb);
                 issued = k + 1;
             }
             // every copy issued must have landed before shared memory is released
-            for (int k = issued - kDRawStages < 0 ? 0 : issued - kDRawStages; k < issued; ++k)
-                if (!mbar_wait_bounded(rfull0 + 8 * (k % kDRawStages), (uint32_t)((k / kDRawStages) & 1))) *flag = 1;
+            for (int k = issued - R < 0 ? 0 : issued - R; k < issued; ++k)
+                if (!mbar_wait_bounded(rfull0 + 8 * (k % R), (uint32_t)((k / R) & 1))) *flag = 1;
         }
     } else if (warp == 1) {
         if (lane == 0 && work) {  // ---- MMA issuer
@@ -475,7 +486,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const char *st = smem + kDOffDig + d * kDDigStage;
+                const char *st = smem + dig_off + d * dsb;
                 const int ns = min(S, nsub - k * S);
                 for (int sg = 0; sg < ns; ++sg) {
                     const char *sb = st + sg * sub_bytes;
@@ -569,8 +580,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         const int gps = 16 * (nvb + 1);  // digit groups per sub-tile: (block slot, 8-row half, column)
         bool bad = false;
         for (int k = 0; k < nst; ++k) {
-            const int s = k % kDRawStages, d = k % kDDigStages;
-            bool ok = warp_wait(rfull0 + 8 * s, (uint32_t)((k / kDRawStages) & 1));
+            const int s = k % R, d = k % kDDigStages;
+            bool ok = warp_wait(rfull0 + 8 * s, (uint32_t)((k / R) & 1));
             if (ok && k >= kDDigStages)
                 ok = warp_wait(dempty0 + 8 * d, (uint32_t)(((k - kDDigStages) / kDDigStages) & 1));
             if (!ok || *flag) {
@@ -578,28 +589,29 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 break;
             }
             const int ns = min(S, nsub - k * S);
-            const char *raw = smem + s * kDRawStage;
-            char *dig = smem + kDOffDig + d * kDDigStage;
+            const char *raw = smem + s * rsb;
+            char *dig = smem + dig_off + d * dsb;
             const int rot = (k * 32) & (kCT - 1);  // spreads the extra groups over the warps
             for (int g = (ct - rot) & (kCT - 1); g < ns * gps; g += kCT) {
                 const int sg = g / gps, r = g % gps;
                 const int i = r >> 4, ko = (r >> 3) & 1, a = r & 7;
                 const int64_t t = t0 + (int64_t)k * S + sg;
                 const int rv = (int)min((int64_t)kKT, (int64_t)n - t * kKT);
-                const char *sb = raw + (sg * (nvb + 1) + i) * (kKT * kRawRow);
                 char *db = dig + sg * sub_bytes;
                 uint64_t f[8];
                 if (i == nvb) {  // W: FP64 -> fixed point with this chunk's column scale
-                    const double *src = reinterpret_cast<const double *>(sb) + ko * 8 * kS + a;
+                    const double *src =
+                        reinterpret_cast<const double *>(raw + (S * nvb + sg) * (kKT * kRawRow)) + ko * 8 * kS + a;
                     const int e = wexp[a];
 #pragma unroll
                     for (int v = 0; v < 8; ++v)
                         if (!to_fixed((ko * 8 + v < rv) ? src[v * kS] : 0.0, e, f[v])) bad = true;
                     expand8(f, db + kDig * plane + ko * kLBO + a * 16, kPiece);
-                } else {
-                    const uint64_t *src = reinterpret_cast<const uint64_t *>(sb) + ko * 8 * kS + a;
+                } else {  // rows past n are zero in the sub-tile layout
+                    const uint64_t *src =
+                        reinterpret_cast<const uint64_t *>(raw + (sg * nvb + i) * (kKT * kRawRow)) + ko * 8 * kS + a;
 #pragma unroll
-                    for (int v = 0; v < 8; ++v) f[v] = (ko * 8 + v < rv) ? src[v * kS] : 0ull;
+                    for (int v = 0; v < 8; ++v) f[v] = src[v * kS];
                     expand8(f, db + i * kPiece + ko * kLBO + a * 16, plane);
                 }
             }
@@ -683,7 +695,7 @@ __global__ void k_h_digits(int32_t nblk, const double *__restrict__ H, char *__r
 // ---------------------------------------------------------------------------------
 constexpr int kURawBlk = 128 * kRawRow;       // 8 KB: 128 rows of one block
 constexpr int kURawStage = 2 * kURawBlk;      // two blocks = one K step
-constexpr int kURawStages = 5;
+constexpr int kURawStages = 6;
 constexpr int kUPlane = 2 * (8 * kPiece);     // one digit plane of a stage: 2 blocks x 2 KB
 constexpr int kUStageA = kDig * kUPlane;      // 36 KB
 constexpr int kUDigStage = kUStageA + (kDig + 1) * kPiece;  // + 9 H digit pieces + zero group
@@ -923,12 +935,20 @@ size_t tc_partial_elems(int32_t n, int32_t nblk)
     return (size_t)((nt + 7) / 8) * nblk * kS * kS;  // chunks hold at least 8 sub-tiles
 }
 
-int launch_to_fixed(cudaStream_t st, int64_t count, const double *X, uint64_t *F, int *d_err)
+size_t tc_fixed_sub_bytes(int32_t n, int32_t nblocks)
 {
-    if (count <= 0) return 0;
+    const int64_t nt = ((int64_t)n + kKT - 1) / kKT;
+    return (size_t)nt * nblocks * kKT * kS * 8;
+}
+
+int launch_to_fixed(cudaStream_t st, int32_t n, int32_t nblocks, const double *X, uint64_t *F_row, uint64_t *F_sub,
+                    int32_t ipad, int32_t iblk0, int *d_err)
+{
+    if (n <= 0 || nblocks <= 0) return 0;
+    const int64_t count = (((int64_t)n + kKT - 1) / kKT) * kKT * kS * nblocks;
     int64_t g = (count + 255) / 256;
     if (g > 4 * 152) g = 4 * 152;
-    k_to_fixed<<<(unsigned)g, 256, 0, st>>>(count, X, F, d_err);
+    k_to_fixed<<<(unsigned)g, 256, 0, st>>>(n, nblocks, X, F_row, F_sub, ipad, iblk0, d_err);
     note_launches(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -952,8 +972,8 @@ int launch_block_update_tc(cudaStream_t st, int32_t n, int32_t nblk, const uint6
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_block_dot_tc(cudaStream_t st, int32_t n, int32_t nblk, const uint64_t *Vf, const double *W, double *partial,
-                        double *out, int *d_err)
+int launch_block_dot_tc(cudaStream_t st, int32_t n, int32_t nblk, const uint64_t *Vfs, int32_t ipad, const double *W,
+                        double *partial, double *out, int *d_err)
 {
     if (n <= 0 || nblk <= 0) return -1;
     if (cudaFuncSetAttribute(k_block_dot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kDSmem) != cudaSuccess)
@@ -963,7 +983,7 @@ int launch_block_dot_tc(cudaStream_t st, int32_t n, int32_t nblk, const uint64_t
     const int chunks = (int)((nt + spc - 1) / spc);
     const int mtiles = (nblk + kBlocksPerTile - 1) / kBlocksPerTile;
     dim3 grid(chunks, mtiles);
-    k_block_dot_tc<<<grid, kThreadsTC, kDSmem, st>>>(n, nblk, spc, Vf, W, partial, d_err);
+    k_block_dot_tc<<<grid, kThreadsTC, kDSmem, st>>>(n, nblk, spc, Vfs, ipad, W, partial, d_err);
     note_launches(1);
     if (cudaGetLastError() != cudaSuccess) return -1;
     return launch_reduce_chunks(st, nblk * kS * kS, chunks, partial, out);

@@ -947,7 +947,8 @@ struct SolveWs {
     double *Bw, *Xw, *W, *Z, *T0, *T1, *V;
     double *partial, *H1, *H2, *G1, *R1, *R2, *Rn, *ref2, *nrm2, *thresh, *Qs, *Rtri, *G, *Y, *est;
     int32_t *defl1, *defl2, *flag;
-    uint64_t *vfix; // fixed-point copies of the basis blocks (tensor-core products)
+    uint64_t *vfix;     // fixed-point copies of the basis blocks, row layout (block update)
+    uint64_t *vfix_sub; // the same, sub-tile layout across blocks (Gram product)
     void *hdig;     // digit pieces of H (tensor-core block update)
     int32_t *hexp;  // column exponents of H
 };
@@ -995,6 +996,7 @@ size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks
     w.flag = (int32_t *)take(64);
     const bool digits = block_dot_tc_supported(s);
     w.vfix = (uint64_t *)take(digits ? blk * (m + 1) : 16);
+    w.vfix_sub = (uint64_t *)take(digits ? tc_fixed_sub_bytes(n, m + 1) : 16);
     w.hdig = take(digits ? tc_hdig_bytes(m + 1) : 16);
     w.hexp = (int32_t *)take(64);
     return off;
@@ -1053,8 +1055,9 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
     // fixed-point copy of basis block blk for the tensor-core products
     auto make_fixed = [&](int blk) -> spai_status {
         if (!use_digits) return SPAI_OK;
-        PKL("to_fixed", 0.0, 16.0 * n * s,
-            launch_to_fixed(cs, (int64_t)n * s, w.V + (size_t)blk * n * s, w.vfix + (size_t)blk * n * s, ctx->d_err),
+        PKL("to_fixed", 0.0, 24.0 * n * s,
+            launch_to_fixed(cs, n, 1, w.V + (size_t)blk * n * s, w.vfix + (size_t)blk * n * s, w.vfix_sub, m + 1, blk,
+                            ctx->d_err),
             "fixed point");
         return SPAI_OK;
     };
@@ -1136,7 +1139,7 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
             const bool tc = use_digits && (opts->orth == SPAI_ORTH_TENSOR || j + 1 >= 2);
             if (tc) {
                 PKL("block_dot_tc", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
-                    launch_block_dot_tc(cs, n, j + 1, w.vfix, w.W, w.partial, w.H1, ctx->d_err), "H1");
+                    launch_block_dot_tc(cs, n, j + 1, w.vfix_sub, m + 1, w.W, w.partial, w.H1, ctx->d_err), "H1");
             } else {
                 PKL("block_dot", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
                     launch_block_dot(cs, s, n, j + 1, w.V, w.W, w.partial, w.H1, chunks), "H1");
@@ -1144,7 +1147,7 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
             if ((st = vupdate(j + 1, w.H1, w.W, w.W, -1.0))) return st;
             if (tc) {
                 PKL("block_dot_tc", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
-                    launch_block_dot_tc(cs, n, j + 1, w.vfix, w.W, w.partial, w.H2, ctx->d_err), "H2");
+                    launch_block_dot_tc(cs, n, j + 1, w.vfix_sub, m + 1, w.W, w.partial, w.H2, ctx->d_err), "H2");
             } else {
                 PKL("block_dot", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
                     launch_block_dot(cs, s, n, j + 1, w.V, w.W, w.partial, w.H2, chunks), "H2");
@@ -1225,7 +1228,7 @@ extern "C" spai_status spai_block_gram(spai_ctx ctx, int32_t s, int32_t n, int32
     const size_t a = (dot_partial_elems(s, nblk) * 8 + 255) / 256 * 256;
     const bool tcm = method == SPAI_ORTH_TENSOR;
     const size_t c = tcm ? (tc_partial_elems(n, nblk) * 8 + 255) / 256 * 256 : 0;
-    const size_t fx = tcm ? (size_t)nblk * n * s * 8 : 0;
+    const size_t fx = tcm ? tc_fixed_sub_bytes(n, nblk) : 0;
     void *ws = nullptr;
     spai_status st = temp_blocks(ctx, (a > c ? a : c) + fx, &ws);
     if (st) return st;
@@ -1236,10 +1239,10 @@ extern "C" spai_status spai_block_gram(spai_ctx ctx, int32_t s, int32_t n, int32
         PKL("block_dot", 2.0 * nsd * s * nblk, 8.0 * nsd * (nblk + 1),
             launch_block_dot(ctx->stream, s, n, nblk, V, W, partial, H, krylov_chunks(n)), "gram");
     } else {
-        PKL("to_fixed", 0.0, 16.0 * nsd * nblk, launch_to_fixed(ctx->stream, (int64_t)nblk * n * s, V, vfix, ctx->d_err),
-            "fixed point");
+        PKL("to_fixed", 0.0, 16.0 * nsd * nblk,
+            launch_to_fixed(ctx->stream, n, nblk, V, nullptr, vfix, nblk, 0, ctx->d_err), "fixed point");
         PKL("block_dot_tc", 2.0 * nsd * s * nblk, 8.0 * nsd * (nblk + 1),
-            launch_block_dot_tc(ctx->stream, n, nblk, vfix, W, partial, H, ctx->d_err), "tensor gram");
+            launch_block_dot_tc(ctx->stream, n, nblk, vfix, nblk, W, partial, H, ctx->d_err), "tensor gram");
     }
     int h = 0;
     if ((st = read_err(ctx, &h))) return st;
@@ -1274,8 +1277,8 @@ extern "C" spai_status spai_block_update(spai_ctx ctx, int32_t s, int32_t n, int
         int32_t *hexp = (int32_t *)((char *)ws + hd);
         uint64_t *vfix = (uint64_t *)((char *)ws + hd + 256);
         const double nsd = (double)n * s;
-        PKL("to_fixed", 0.0, 16.0 * nsd * nblk, launch_to_fixed(ctx->stream, (int64_t)nblk * n * s, V, vfix, ctx->d_err),
-            "fixed point");
+        PKL("to_fixed", 0.0, 16.0 * nsd * nblk,
+            launch_to_fixed(ctx->stream, n, nblk, V, vfix, nullptr, 0, 0, ctx->d_err), "fixed point");
         PKL("block_update_tc", 2.0 * nsd * s * nblk, 8.0 * nsd * (nblk + 2),
             launch_block_update_tc(ctx->stream, n, nblk, vfix, H, hdig, hexp, W, W, sign, ctx->d_err),
             "tensor block update");

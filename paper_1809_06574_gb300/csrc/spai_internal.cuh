@@ -143,9 +143,14 @@ int launch_reduce_chunks(cudaStream_t st, int32_t count, int chunks, const doubl
 // from launch_to_fixed, |v| < 2), W as FP64; BF16 digits are cut in shared memory.
 bool block_dot_tc_supported(int32_t s);
 size_t tc_partial_elems(int32_t n, int32_t nblk);
-int launch_to_fixed(cudaStream_t st, int64_t count, const double *X, uint64_t *F, int *d_err);
-// H = V_{0..nblk-1}^T W (H[i][a][b]); partial needs tc_partial_elems(n, nblk) doubles
-int launch_block_dot_tc(cudaStream_t st, int32_t n, int32_t nblk, const uint64_t *Vf, const double *W,
+// fixed point of nblocks blocks in the row layout (F_row, like X) and/or the sub-tile
+// layout (F_sub: block slots iblk0.. of an array of ipad slots, tc_fixed_sub_bytes(n, ipad))
+size_t tc_fixed_sub_bytes(int32_t n, int32_t nblocks);
+int launch_to_fixed(cudaStream_t st, int32_t n, int32_t nblocks, const double *X, uint64_t *F_row, uint64_t *F_sub,
+                    int32_t ipad, int32_t iblk0, int *d_err);
+// H = V_{0..nblk-1}^T W (H[i][a][b]) from the sub-tile layout of ipad slots; partial needs
+// tc_partial_elems(n, nblk) doubles
+int launch_block_dot_tc(cudaStream_t st, int32_t n, int32_t nblk, const uint64_t *Vfs, int32_t ipad, const double *W,
                         double *partial, double *out, int *d_err);
 // out = base + sign * V_{0..nblk-1} H (base may be null, may equal out): H is nblk*8 x 8
 // ([i][a][b]); hdig needs tc_hdig_bytes(nblk) bytes, hexp 8 ints
