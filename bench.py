@@ -217,6 +217,20 @@ def run_kernel_case(args):
                       "steps": args.steps, "families": fams}), flush=True)
 
 
+# ------------------------------------------------------------------------------ replicas
+def aggregate_replicas(dist, torch, device, t_local, solves):
+    """Whole-job figures of N independent replicas (one per rank, no data exchange):
+    the slowest rank's time and the solves of all ranks.  dist None: one process."""
+    if dist is None:
+        return t_local, float(solves)
+    t = torch.tensor([t_local, float(solves)], dtype=torch.float64, device=device)
+    tm = t.clone()
+    dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+    ts = t.clone()
+    dist.all_reduce(ts, op=dist.ReduceOp.SUM)
+    return tm[0].item(), ts[1].item()
+
+
 # ------------------------------------------------------------------------------- oracle
 def oracle_sample(side, nparams, nsys, seed=0):
     """Time the CPU oracle on the first `nsys` systems of the sweep (build, then updates)."""
@@ -499,15 +513,7 @@ def main():
     solves = sweep.solves
     iters = list(sweep.iters)
     t_local = ms / 1e3
-    if dist is not None:
-        t = torch.tensor([t_local, float(solves)], device="cuda")
-        tm = t.clone()
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        ts = t.clone()
-        dist.all_reduce(ts, op=dist.ReduceOp.SUM)
-        t_max, total_solves = tm[0].item(), ts[1].item()
-    else:
-        t_max, total_solves = t_local, float(solves)
+    t_max, total_solves = aggregate_replicas(dist, torch, "cuda", t_local, solves)
     value = total_solves / t_max
 
     # the same sweep with FP32 SPAI factors (SPAI_PREC_FP32: FP32 least squares and factor
