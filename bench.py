@@ -52,6 +52,13 @@ def parse():
     ap.add_argument("--kernel", default=None, choices=["dot", "update"])
     ap.add_argument("--nblk", type=int, default=16)
     ap.add_argument("--orth", default="tensor", choices=["tensor", "fp64"])
+    # serving: Poisson arrivals over a pool of 16 3D 7-point grids (sides 24-96)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-only", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-fifo-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-slots", type=int, default=4)
     return ap.parse_args()
 
 
@@ -304,6 +311,121 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------------- serving
+SERVE_SIDES = [round(24 + 72 * i / 15) for i in range(16)]  # 24 ... 96: n = 13,824 ... 884,736
+
+
+def serving_trace(rate, seconds, nsys, seed=0):
+    """Poisson arrivals at `rate` per second for `seconds`: (t, system, p, s, nrhs).  70 % of
+    the requests lie within 0.05 of an already-served (system, s, p); the others draw a
+    system, p ~ U[0.1, 1] and s in {0.5, 1, 2}; nrhs in {1, 4, 8}."""
+    rng = np.random.default_rng(np.random.SeedSequence(seed).spawn(4)[3])
+    out, seen, t = [], [], 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= seconds:
+            return out
+        if seen and rng.random() < 0.7:
+            sy, p0, s = seen[int(rng.integers(len(seen)))]
+            p = float(np.clip(p0 + rng.uniform(-0.05, 0.05), 0.1, 1.0))
+        else:
+            sy, p, s = int(rng.integers(nsys)), float(rng.uniform(0.1, 1.0)), float(rng.choice([0.5, 1.0, 2.0]))
+        seen.append((sy, p, s))
+        out.append((t, sy, p, s, int(rng.choice([1, 4, 8]))))
+
+
+def serve_trace(sg, torch, systems, Bs, trace, **opts):
+    """Replay `trace` open-loop against a fresh server: each request is submitted at its
+    arrival time (latency counts from that time, however late the submit), the solution
+    is returned to host memory.  Returns the per-request results and the server stats."""
+    srv = sg.spai_server_create(**opts)
+    try:
+        ids = [sg.spai_server_add_system(srv, [sg.csr(w.n, *t) for t in w.terms]) for w in systems]
+        tickets = []
+        done = []
+        import queue as _q
+        pending = _q.Queue()
+
+        def collect():
+            while True:
+                item = pending.get()
+                if item is None:
+                    return
+                tk, X = item
+                done.append(sg.spai_server_wait(srv, tk))
+                del X
+
+        col = threading.Thread(target=collect, daemon=True)
+        col.start()
+        t0 = sg.spai_server_clock(srv) + 0.05
+        for (ta, sy, p, s, nrhs) in trace:
+            delay = t0 + ta - sg.spai_server_clock(srv)
+            if delay > 0:
+                time.sleep(delay)
+            w = systems[sy]
+            X = np.empty((w.n, nrhs), order="F")
+            tk = sg.spai_server_submit(srv, ids[sy], nrhs, p, s, sg.affine_coefficients(p, s), Bs[sy], X,
+                                       t_arrival=t0 + ta)
+            tickets.append(tk)
+            pending.put((tk, X))
+        pending.put(None)
+        col.join()
+        stats = sg.spai_server_stats_get(srv)
+    finally:
+        sg.spai_server_destroy(srv)
+    return done, stats
+
+
+def serving_summary(res, stats, n_of):
+    lat = np.array([r["t_done"] - r["t_arrival"] for r in res])
+    ok = [r for r in res if r["status"] == 0]
+    span = max(r["t_done"] for r in res) - min(r["t_arrival"] for r in res)
+    routes = {"build": 0, "update": 0, "reuse": 0}
+    for r in res:
+        routes[("build", "update", "reuse")[r["route"]]] += 1
+    return {"requests": len(res), "completed_ok": len(ok), "value": len(ok) / span, "unit": UNIT,
+            "span_s": round(span, 3),
+            "latency_ms": {"p50": round(1e3 * float(np.percentile(lat, 50)), 2),
+                           "p90": round(1e3 * float(np.percentile(lat, 90)), 2),
+                           "p99": round(1e3 * float(np.percentile(lat, 99)), 2),
+                           "max": round(1e3 * float(lat.max()), 2)},
+            "routes": routes, "max_rel_residual": max(r["max_rel_residual"] for r in ok) if ok else None,
+            "mem_peak_gb": round(stats["mem_peak"] / 1e9, 3), "evictions": stats["evictions"],
+            "waits_for_memory": stats["waits_for_memory"]}
+
+
+def run_serving(args, sg, torch):
+    """Served (concurrent slots, cached builds routed to updates, FP32 factors) against FIFO
+    plain FP64 (one slot, a SPAI build per request) on the same Poisson trace."""
+    import synth
+    systems = [synth.grid_workload((d, d, d), "7pt", seed=100 + i, nrhs=8, params=[0.5])
+               for i, d in enumerate(SERVE_SIDES)]
+    Bs = [torch.from_numpy(np.asfortranarray(w.B).T.copy()).pin_memory() for w in systems]  # (8, n): column-major n x 8
+    trace = serving_trace(args.serve_rate, args.serve_seconds, len(systems))
+    common = dict(restart=30, max_cycles=100, tol=1e-8)
+    served = dict(slots=args.serve_slots, reuse=True, radius=0.05, pattern_kind=sg.PREC_FP32,
+                  mem_budget=40 << 30, **common)
+    # warm-up on a discarded server (module load, allocator pools); the timed server starts cold
+    serve_trace(sg, torch, systems, Bs, [(0.0, i, 0.5, 1.0, 8) for i in range(len(systems))], **served)
+    res, st = serve_trace(sg, torch, systems, Bs, trace, **served)
+    out = serving_summary(res, st, None)
+    fifo_trace = [r for r in trace if r[0] < args.serve_fifo_seconds]
+    res_f, st_f = serve_trace(sg, torch, systems, Bs, fifo_trace, slots=1, reuse=False, mem_budget=40 << 30,
+                              **common)
+    fifo = serving_summary(res_f, st_f, None)
+    nbar = float(np.mean([systems[sy].n for _, sy, _, _, _ in trace]))
+    return {
+        "workload": f"Poisson {args.serve_rate:g} req/s for {args.serve_seconds:g} s over 16 3D 7-point grids "
+                    f"(sides {SERVE_SIDES[0]}-{SERVE_SIDES[-1]}, mean n of the requests {nbar:.0f}); 70 % within "
+                    f"0.05 of a served p; s in {{0.5,1,2}}; nrhs in {{1,4,8}}; block GMRES(30) to 1e-8; "
+                    f"40 GB budget; solutions returned to host memory",
+        "served": {**out, "slots": args.serve_slots, "factors": "f32 (FP64 solve)", "reuse_radius": 0.05},
+        "fifo_plain_fp64": {**fifo, "slots": 1, "factors": "f64", "reuse": False,
+                            "trace": f"the first {args.serve_fifo_seconds:g} s of the same arrivals"},
+        "served_over_fifo": out["value"] / fifo["value"] if fifo["value"] else None,
+    }
+
+
 # ------------------------------------------------------------------------------- GPU sweep
 class Worker:
     """One host thread's share of the sweep: its own stream, context and buffers."""
@@ -472,6 +594,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
+    if args.serve_only:
+        if rank == 0:
+            print(json.dumps({"serving": run_serving(args, sg, torch)}), flush=True)
+        return
     ctx = sg.spai_ctx_create(stream.cuda_stream, 0)
     fp64_tflops = max(sg.spai_measure_fp64_rate(ctx) for _ in range(3))
 
@@ -580,6 +706,11 @@ def main():
                "d2h_bytes_per_step": hs.d2h_bytes()}
         hs.close()
 
+    # served (continuous admission, update routing, FP32 factors) vs FIFO plain FP64
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        serving = run_serving(args, sg, torch)
+
     if rank == 0:
         total_ms = sum(f["ms"] for f in prof) or 1.0
         dom = max(prof, key=lambda f: f["ms"])
@@ -610,7 +741,7 @@ def main():
                                             "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                                             "workers": args.workers},
             "roofline": roofline, "roofline_isolated": roofline_iso, "mixed_precision": mixed,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "gpu_launches": int(launches),
             "clocks": clk, "fp64_tflops_measured": fp64_tflops,
             "gmres_iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)),
                                  "max": int(max(iters))},

@@ -109,6 +109,11 @@ SPAI_API spai_status spai_ctx_sync(spai_ctx ctx);
 /* Device bytes currently held by the library for this context (handles + workspace). */
 SPAI_API size_t spai_ctx_mem_in_use(spai_ctx ctx);
 
+/* Release the context's grow-only workspace (the Krylov basis and blocks of block_solve,
+ * staging blocks of the product calls); the next call that needs it allocates it again.
+ * The memory is returned in stream order on the context's stream. */
+SPAI_API spai_status spai_ctx_trim(spai_ctx ctx);
+
 /* Number of kernels the library has launched in this process (all contexts). */
 SPAI_API int64_t spai_launch_count(void);
 
@@ -201,6 +206,11 @@ SPAI_API spai_status spai_pc_info(spai_pc pc, int32_t *n, int32_t *nnz, int64_t 
 SPAI_API spai_status spai_pc_export(spai_ctx ctx, spai_pc pc, int32_t *Jptr, int32_t *Jind, double *val,
                            int32_t *Iptr, int32_t *Ilist, int32_t *col_status);
 
+/* Device bytes held by this handle's own factor and matrix values; with_analysis != 0
+ * adds its pattern analysis (I_k, J_k, transposed pattern), which a build shares with
+ * every update made from it and which is released with the last of them. */
+SPAI_API size_t spai_pc_mem_size(spai_pc pc, int32_t with_analysis);
+
 SPAI_API spai_status spai_pc_destroy(spai_pc pc);
 
 /* ----------------------------------------------------------------------------------
@@ -277,6 +287,10 @@ typedef struct {
     double max_rel_residual;   /* that residual, ||b_i - A x_i|| / ||b_i|| (FP64) */
 } spai_solve_info;
 
+/* Device bytes of the workspace block_solve uses for n unknowns, s right-hand sides and
+ * restart length m = restart (the context keeps it between calls; 0 for invalid sizes). */
+SPAI_API size_t spai_solve_workspace_size(int32_t n, int32_t s, int32_t restart);
+
 /* Solve A X = B for s right-hand sides at once.  P may be NULL (no preconditioner).
  * B (n x s, ldb) and X (n x s, ldx) may be HOST or DEVICE memory; X holds the initial
  * guess on entry and the solution on return.  rel_residual: HOST array of s doubles
@@ -286,6 +300,111 @@ typedef struct {
 SPAI_API spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, int32_t s, const double *B,
                         int64_t ldb, double *X, int64_t ldx, const spai_solve_opts *opts,
                         spai_solve_info *info, double *rel_residual);
+
+/* ----------------------------------------------------------------------------------
+ * Serving.  The paper's setting is a sequence of linear systems A(p_j) X_j = B_j that
+ * differ only in the parameter (Sec. 1.3), whose SPAI preconditioner is updated cheaply
+ * from an earlier build instead of being rebuilt (Sec. 2.3, Table 1; Sec. 2.4).  A server
+ * takes such solves as requests, as they arrive, for several registered systems:
+ *  - it keeps every system (its affine terms), its cached SPAI builds and the Krylov
+ *    workspaces resident on the device;
+ *  - it runs up to `slots` requests at once, each on its own CUDA stream and context, so
+ *    the kernels of different requests overlap on the GPU; a request is admitted when a
+ *    slot is free and its device memory fits the budget (least recently used cached
+ *    builds are evicted, idle workspaces released, else it waits for running requests);
+ *  - with `reuse`, a request whose parameter p lies within `radius` of a cached build's
+ *    parameter, for the same system and the same shift s, is served by spai_update
+ *    (SPAI_UPDATE_FIRST from that build) instead of a new build; at p equal to the
+ *    build's it reuses the build itself; otherwise it builds and caches a new base.
+ *    Without `reuse` every request builds its own factor (the plain method);
+ *  - each request is solved by block_solve from X0 = 0 to the server's tolerance.
+ * Results do not depend on what else runs: every kernel reduces in a fixed order, so a
+ * request gives the same bits as the same route (build at the same base p, update,
+ * solve) run alone through the calls above.
+ * ---------------------------------------------------------------------------------- */
+typedef struct spai_server_s *spai_server;
+
+typedef struct {
+    int32_t slots;         /* requests on the GPU at once, 1..64 */
+    int32_t pattern_kind;  /* SPAI_PATTERN_A or SPAI_PATTERN_A2, optionally | SPAI_PREC_FP32 */
+    int32_t reuse;         /* 1: cache builds and route nearby requests to spai_update; 0: build per request */
+    int32_t restart;       /* block GMRES(m) restart length m */
+    int32_t max_cycles;    /* restart cycles before a request fails with SPAI_ENOTCONV */
+    int32_t orth;          /* SPAI_ORTH_* of the solves */
+    double radius;         /* route to an update when |p - p_build| <= radius (same system and shift) */
+    double tol;            /* every column's true relative residual <= tol */
+    size_t mem_budget;     /* device bytes for systems, cached builds and in-flight requests (0: no cap);
+                              a request counts its slot's workspace and buffers, its factor and,
+                              for a build, 16 nnz + 16 (n + 1) + 1 MiB of pattern-analysis buffers */
+} spai_server_opts;
+
+typedef struct {
+    int32_t system;        /* id from spai_server_add_system */
+    int32_t nrhs;          /* right-hand sides: 1, 2, 4, 8 or 16 */
+    double p;              /* parameter value (routing distance) */
+    double s;              /* shift (routing key: only builds at exactly this shift are reused) */
+    const double *coef;    /* HOST, nterms doubles: A = sum_t coef[t] * term_t; copied at submit.
+                              Requests with equal (system, s, p) must pass equal coefficients */
+    const double *B;       /* HOST or DEVICE, n x nrhs column-major, leading dimension n; read
+                              while the request runs, so it must stay valid until it completes */
+    double *X;             /* HOST or DEVICE, n x nrhs, leading dimension n: the solution, written
+                              when the request completes; NULL: the solution is not returned */
+    double t_arrival;      /* arrival time on the server clock (spai_server_clock); < 0: now */
+} spai_request;
+
+#define SPAI_ROUTE_BUILD 0   /* a new SPAI build (cached when reuse is on) */
+#define SPAI_ROUTE_UPDATE 1  /* spai_update from a cached build */
+#define SPAI_ROUTE_REUSE 2   /* a cached build at the same p, used as it is */
+
+typedef struct {
+    int32_t status;            /* spai_status of the request */
+    int32_t route;             /* SPAI_ROUTE_* */
+    int32_t slot;              /* slot that ran it */
+    int32_t iterations;        /* block Arnoldi steps */
+    double base_p;             /* p of the build it used */
+    double max_rel_residual;   /* largest true relative residual over its columns */
+    double t_arrival, t_start, t_done;  /* server clock, seconds */
+} spai_result;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int64_t builds, updates, reuses, evictions, waits_for_memory;
+    size_t mem_in_use;        /* bytes accounted now (systems, cache, slots, reservations) */
+    size_t mem_peak;          /* the largest such figure so far */
+    int32_t cached_builds;    /* cache entries now */
+    int32_t reserved;
+} spai_server_stats;
+
+/* Create a server on the current device with `opts` (copied).  It starts `slots` host
+ * worker threads, each with its own non-blocking stream and context.  Device inputs of a
+ * request must be complete (synchronised) before it is submitted. */
+SPAI_API spai_status spai_server_create(const spai_server_opts *opts, spai_server *out);
+
+/* Register a system A = sum_t coef[t] term_t (spai_affine_create's rules: 1..16 CSR terms
+ * of equal n, HOST or DEVICE arrays, copied); at most 1024 systems per server (SPAI_EINVAL
+ * beyond).  *id receives its id (0, 1, ...).  Counts
+ * against the memory budget (SPAI_ENOMEM if it does not fit).  Synchronises. */
+SPAI_API spai_status spai_server_add_system(spai_server srv, int32_t nterms, const spai_csr *terms, int32_t *id);
+
+/* Queue a request; *ticket identifies it for spai_server_wait.  Never blocks on the GPU. */
+SPAI_API spai_status spai_server_submit(spai_server srv, const spai_request *req, int64_t *ticket);
+
+/* Block until request `ticket` has completed, copy its result to *out (may be NULL) and
+ * forget the ticket.  Returns SPAI_EINVAL for an unknown ticket, else SPAI_OK (the
+ * request's own status is out->status). */
+SPAI_API spai_status spai_server_wait(spai_server srv, int64_t ticket, spai_result *out);
+
+/* Seconds since the server was created (steady clock): the time base of the results. */
+SPAI_API double spai_server_clock(spai_server srv);
+
+SPAI_API spai_status spai_server_stats_get(spai_server srv, spai_server_stats *out);
+
+/* Message of the last failed server call or request ("" if none). */
+SPAI_API const char *spai_server_last_error(spai_server srv);
+
+/* Finish every queued request, stop the workers and release all device memory.  Results
+ * not collected with spai_server_wait are dropped. */
+SPAI_API spai_status spai_server_destroy(spai_server srv);
 
 #ifdef __cplusplus
 }

@@ -24,7 +24,11 @@ __all__ = [
     "spai_assemble", "spai_affine_export", "spai_affine_destroy", "spai_build", "spai_update", "spai_pc_info",
     "spai_pc_export", "spai_pc_destroy", "spai_spmm", "spai_pc_apply", "block_solve",
     "affine_coefficients", "PATTERN_A", "PATTERN_A2", "UPDATE_FIRST", "UPDATE_CHAINED", "PREC_FP32",
-    "LIB_PATH",
+    "LIB_PATH", "spai_ctx_trim", "spai_solve_workspace_size", "spai_pc_mem_size",
+    "spai_server_opts", "spai_request", "spai_result", "spai_server_stats", "spai_server_create",
+    "spai_server_add_system", "spai_server_submit", "spai_server_wait", "spai_server_clock",
+    "spai_server_stats_get", "spai_server_last_error", "spai_server_destroy",
+    "ROUTE_BUILD", "ROUTE_UPDATE", "ROUTE_REUSE",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -66,6 +70,39 @@ class spai_solve_info(C.Structure):
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
+
+class spai_server_opts(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("pattern_kind", C.c_int32), ("reuse", C.c_int32),
+                ("restart", C.c_int32), ("max_cycles", C.c_int32), ("orth", C.c_int32),
+                ("radius", C.c_double), ("tol", C.c_double), ("mem_budget", C.c_size_t)]
+
+
+class spai_request(C.Structure):
+    _fields_ = [("system", C.c_int32), ("nrhs", C.c_int32), ("p", C.c_double), ("s", C.c_double),
+                ("coef", C.c_void_p), ("B", C.c_void_p), ("X", C.c_void_p), ("t_arrival", C.c_double)]
+
+
+class spai_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("route", C.c_int32), ("slot", C.c_int32),
+                ("iterations", C.c_int32), ("base_p", C.c_double), ("max_rel_residual", C.c_double),
+                ("t_arrival", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class spai_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("builds", C.c_int64), ("updates", C.c_int64), ("reuses", C.c_int64),
+                ("evictions", C.c_int64), ("waits_for_memory", C.c_int64),
+                ("mem_in_use", C.c_size_t), ("mem_peak", C.c_size_t),
+                ("cached_builds", C.c_int32), ("reserved", C.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+ROUTE_BUILD, ROUTE_UPDATE, ROUTE_REUSE = 0, 1, 2
 
 _lib = None
 
@@ -109,6 +146,17 @@ def lib():
         "spai_block_update": (i32, [vp, i32, i32, i32, vp, vp, vp, dbl, i32]),
         "block_solve": (i32, [vp, P(spai_csr), vp, i32, vp, i64, vp, i64, P(spai_solve_opts),
                               P(spai_solve_info), P(dbl)]),
+        "spai_ctx_trim": (i32, [vp]),
+        "spai_solve_workspace_size": (sz, [i32, i32, i32]),
+        "spai_pc_mem_size": (sz, [vp, i32]),
+        "spai_server_create": (i32, [P(spai_server_opts), P(vp)]),
+        "spai_server_add_system": (i32, [vp, i32, P(spai_csr), P(i32)]),
+        "spai_server_submit": (i32, [vp, P(spai_request), P(i64)]),
+        "spai_server_wait": (i32, [vp, i64, P(spai_result)]),
+        "spai_server_clock": (dbl, [vp]),
+        "spai_server_stats_get": (i32, [vp, P(spai_server_stats)]),
+        "spai_server_last_error": (C.c_char_p, [vp]),
+        "spai_server_destroy": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -333,3 +381,78 @@ def block_solve(ctx, A, P, s, B, ldb, X, ldx, restart, tol, max_cycles, allow_no
         raise SpaiError(st, spai_last_error(ctx), result)
     _check(ctx, st, allow=(SPAI_ENOTCONV,))
     return result
+
+
+def spai_ctx_trim(ctx):
+    return _check(ctx, lib().spai_ctx_trim(ctx))
+
+
+def spai_solve_workspace_size(n, s, restart):
+    return int(lib().spai_solve_workspace_size(int(n), int(s), int(restart)))
+
+
+def spai_pc_mem_size(pc, with_analysis=True):
+    return int(lib().spai_pc_mem_size(pc, int(bool(with_analysis))))
+
+
+# ------------------------------------------------------------------ serving
+def _server_check(srv, st):
+    if st != SPAI_OK:
+        raise SpaiError(st, spai_server_last_error(srv) if srv else "")
+    return st
+
+
+def spai_server_create(slots=4, pattern_kind=PATTERN_A, reuse=True, restart=30, max_cycles=50,
+                       orth=ORTH_AUTO, radius=0.05, tol=1e-8, mem_budget=0):
+    o = spai_server_opts(int(slots), int(pattern_kind), int(bool(reuse)), int(restart), int(max_cycles),
+                         int(orth), float(radius), float(tol), int(mem_budget))
+    out = C.c_void_p()
+    st = lib().spai_server_create(C.byref(o), C.byref(out))
+    if st != SPAI_OK:
+        raise SpaiError(st, "spai_server_create failed")
+    return out
+
+
+def spai_server_add_system(srv, terms):
+    """terms: list of spai_csr (host or device arrays).  Returns the system id."""
+    arr = (spai_csr * len(terms))(*terms)
+    sid = C.c_int32()
+    _server_check(srv, lib().spai_server_add_system(srv, len(terms), arr, C.byref(sid)))
+    return sid.value
+
+
+def spai_server_submit(srv, system, nrhs, p, s, coef, B, X=None, t_arrival=-1.0):
+    """Queue one solve; B / X host or device, n x nrhs column-major (leading dimension n).
+    Returns the ticket.  B (and X) must stay alive until the request completes."""
+    cf = (C.c_double * len(coef))(*[float(c) for c in coef])
+    r = spai_request(int(system), int(nrhs), float(p), float(s), C.cast(cf, C.c_void_p), _ptr(B), _ptr(X),
+                     float(t_arrival))
+    t = C.c_int64()
+    _server_check(srv, lib().spai_server_submit(srv, C.byref(r), C.byref(t)))
+    return t.value
+
+
+def spai_server_wait(srv, ticket):
+    """Block until the request completes; returns its result as a dict."""
+    res = spai_result()
+    _server_check(srv, lib().spai_server_wait(srv, int(ticket), C.byref(res)))
+    return res.as_dict()
+
+
+def spai_server_clock(srv):
+    return float(lib().spai_server_clock(srv))
+
+
+def spai_server_stats_get(srv):
+    out = spai_server_stats()
+    _server_check(srv, lib().spai_server_stats_get(srv, C.byref(out)))
+    return out.as_dict()
+
+
+def spai_server_last_error(srv):
+    r = lib().spai_server_last_error(srv)
+    return r.decode() if r else ""
+
+
+def spai_server_destroy(srv):
+    return _server_check(None, lib().spai_server_destroy(srv))

@@ -844,6 +844,20 @@ extern "C" spai_status spai_pc_info(spai_pc pc, int32_t *n, int32_t *nnz, int64_
     return SPAI_OK;
 }
 
+extern "C" size_t spai_pc_mem_size(spai_pc pc, int32_t with_analysis)
+{
+    if (!pc) return 0;
+    auto r = [](size_t b) { return ((b ? b : 16) + 255) / 256 * 256; };  // as dalloc rounds
+    const Sym *s = pc->sym;
+    const size_t n1 = (size_t)s->n + 1;
+    size_t b = r((size_t)s->nnzP * (pc->fval32 ? 4 : 8)) + r((size_t)s->nnzA * 8) + r((size_t)s->n * 4);
+    if (with_analysis) {
+        b += 2 * r(n1 * 4) + 3 * r((size_t)s->nnzA * 4) + r(n1 * 4) + r((size_t)s->nI * 4);
+        if (!s->alias) b += 2 * r(n1 * 4) + 3 * r((size_t)s->nnzP * 4);
+    }
+    return b;
+}
+
 extern "C" spai_status spai_pc_export(spai_ctx ctx, spai_pc pc, int32_t *Jptr, int32_t *Jind, double *val,
                                       int32_t *Iptr, int32_t *Ilist, int32_t *col_status)
 {
@@ -1019,6 +1033,24 @@ spai_status cholqr2(spai_ctx ctx, SolveWs &w, int32_t n, int32_t s, int chunks, 
 }
 
 }  // namespace
+
+extern "C" size_t spai_solve_workspace_size(int32_t n, int32_t s, int32_t restart)
+{
+    if (n < 1 || !valid_s(s) || restart < 1) return 0;
+    SolveWs w{};
+    return carve(w, nullptr, n, s, restart, krylov_chunks(n));
+}
+
+extern "C" spai_status spai_ctx_trim(spai_ctx ctx)
+{
+    if (!ctx) return SPAI_EINVAL;
+    if (ctx->ws) {
+        dfree(ctx, ctx->ws);
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+    }
+    return SPAI_OK;
+}
 
 extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, int32_t s, const double *B,
                                    int64_t ldb, double *X, int64_t ldx, const spai_solve_opts *opts,
