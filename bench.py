@@ -59,6 +59,11 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-fifo-seconds", type=float, default=2.0)
     ap.add_argument("--serve-slots", type=int, default=4)
+    # large workload: 3D 128^3 27-point grid, 16 RHS, BF16-stored SPAI, update vs rebuild
+    ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--large-only", action="store_true")
+    ap.add_argument("--large-side", type=int, default=128)
+    ap.add_argument("--large-params", type=int, default=3)
     return ap.parse_args()
 
 
@@ -426,6 +431,73 @@ def run_serving(args, sg, torch):
     }
 
 
+# ------------------------------------------------------------------------------- large
+def run_large(args, sg, torch):
+    """3D side^3 27-point workload (side 128: n = 2,097,152, 27 nnz per column, 16 RHS):
+    SPAI in FP32 stored as BF16 at the first p, then for a sample of the other p an update
+    (Table 1, first approach) + block GMRES(30) solve, against a rebuild + solve at the
+    same p; the FP64 build is timed once beside them."""
+    import synth
+    w = synth.grid3d_27pt(side=args.large_side, nparams=50)
+    n, s = w.n, int(w.B.shape[1])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    ctx = sg.spai_ctx_create(stream.cuda_stream, 0)
+    d_terms = [tuple(torch.as_tensor(np.ascontiguousarray(a), device=dev) for a in t) for t in w.terms]
+    aff = sg.spai_affine_create(ctx, [sg.csr(n, *t) for t in d_terms])
+    _, nnz, rp, ci = sg.spai_affine_pattern(aff)
+    va = [torch.empty(nnz, dtype=torch.float64, device=dev) for _ in range(2)]
+    B = torch.as_tensor(np.ascontiguousarray(w.B.T), device=dev)
+    X = torch.zeros((s, n), dtype=torch.float64, device=dev)
+
+    def timed(f):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = f()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    def solve(A, pc):
+        X.zero_()
+        st, info, rel = sg.block_solve(ctx, A, pc, s, B, n, X, n, 30, 1e-8, 100)
+        assert info["converged"], info
+        return info
+
+    sg.spai_assemble(ctx, aff, sg.affine_coefficients(w.params[0], 1.0), va[0])
+    A1 = sg.csr(n, rp, ci, va[0], nnz)
+    pc64, t_b64 = timed(lambda: sg.spai_build(ctx, A1, sg.PATTERN_A)[0])
+    sg.spai_pc_destroy(pc64)
+    sg.spai_pc_destroy(sg.spai_build(ctx, A1, sg.PATTERN_A | sg.PREC_BF16)[0])  # warm-up
+    base, t_b16 = timed(lambda: sg.spai_build(ctx, A1, sg.PATTERN_A | sg.PREC_BF16)[0])
+    solve(A1, base)  # warm-up of the solve path at this size
+    rows = []
+    for p in w.params[1:1 + args.large_params]:
+        sg.spai_assemble(ctx, aff, sg.affine_coefficients(p, 1.0), va[1])
+        A = sg.csr(n, rp, ci, va[1], nnz)
+        upd, t_u = timed(lambda: sg.spai_update(ctx, base, A, sg.UPDATE_FIRST | sg.PREC_BF16)[0])
+        iu, t_su = timed(lambda: solve(A, upd))
+        sg.spai_pc_destroy(upd)
+        reb, t_r = timed(lambda: sg.spai_build(ctx, A, sg.PATTERN_A | sg.PREC_BF16)[0])
+        ir, t_sr = timed(lambda: solve(A, reb))
+        sg.spai_pc_destroy(reb)
+        rows.append({"p": round(p, 4), "update_ms": 1e3 * t_u, "solve_after_update_ms": 1e3 * t_su,
+                     "iterations_update": iu["iterations"], "rebuild_ms": 1e3 * t_r,
+                     "solve_after_rebuild_ms": 1e3 * t_sr, "iterations_rebuild": ir["iterations"],
+                     "max_rel_residual": max(iu["max_rel_residual"], ir["max_rel_residual"])})
+    sg.spai_pc_destroy(base)
+    sg.spai_affine_destroy(aff)
+    sg.spai_ctx_destroy(ctx)
+    upd_s = sum(r["update_ms"] + r["solve_after_update_ms"] for r in rows) / 1e3
+    reb_s = sum(r["rebuild_ms"] + r["solve_after_rebuild_ms"] for r in rows) / 1e3
+    return {
+        "workload": f"3d-{args.large_side}^3-27pt, n={n}, nnz={nnz}, {s} RHS, SPAI(pattern A) FP32 stored "
+                    f"as BF16, block GMRES(30) to 1e-8 in FP64; {len(rows)} of the 49 further p",
+        "build_fp64_ms": 1e3 * t_b64, "build_bf16_ms": 1e3 * t_b16, "per_parameter": rows,
+        "update_path_solves_per_s": len(rows) / upd_s, "rebuild_path_solves_per_s": len(rows) / reb_s,
+        "update_saving": 1.0 - upd_s / reb_s,
+    }
+
+
 # ------------------------------------------------------------------------------- GPU sweep
 class Worker:
     """One host thread's share of the sweep: its own stream, context and buffers."""
@@ -598,6 +670,10 @@ def main():
         if rank == 0:
             print(json.dumps({"serving": run_serving(args, sg, torch)}), flush=True)
         return
+    if args.large_only:
+        if rank == 0:
+            print(json.dumps({"large": run_large(args, sg, torch)}), flush=True)
+        return
     ctx = sg.spai_ctx_create(stream.cuda_stream, 0)
     fp64_tflops = max(sg.spai_measure_fp64_rate(ctx) for _ in range(3))
 
@@ -710,6 +786,9 @@ def main():
     serving = None
     if rank == 0 and world == 1 and not args.no_serve:
         serving = run_serving(args, sg, torch)
+    large = None
+    if rank == 0 and world == 1 and not args.no_large:
+        large = run_large(args, sg, torch)
 
     if rank == 0:
         total_ms = sum(f["ms"] for f in prof) or 1.0
@@ -741,7 +820,7 @@ def main():
                                             "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                                             "workers": args.workers},
             "roofline": roofline, "roofline_isolated": roofline_iso, "mixed_precision": mixed,
-            "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "gpu_launches": int(launches),
+            "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "large": large, "gpu_launches": int(launches),
             "clocks": clk, "fp64_tflops_measured": fp64_tflops,
             "gmres_iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)),
                                  "max": int(max(iters))},

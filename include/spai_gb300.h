@@ -74,6 +74,11 @@ typedef struct spai_pc_s *spai_pc;
  * exactly linear operator and block_solve's FP64 residuals and tolerance are unchanged.
  * No counterpart in the paper: the mixed-precision form of its preconditioner. */
 #define SPAI_PREC_FP32 0x100
+/* SPAI_PREC_BF16: the least-squares problems are solved in FP32 as for SPAI_PREC_FP32 and
+ * each factor entry is rounded to nearest-even BF16 for storage (2 bytes per entry); the
+ * apply converts exactly to FP64 and forms products and sums in FP64.  Exclusive with
+ * SPAI_PREC_FP32 (SPAI_EINVAL if both are set). */
+#define SPAI_PREC_BF16 0x200
 
 /* Update approaches of Table 1 (Sec. 2.3). */
 #define SPAI_UPDATE_FIRST 1    /* min ||A(1) - A(l) Q||_F, P_l = Q_l P_1 (proposed, Sec. 2.4) */
@@ -176,7 +181,8 @@ SPAI_API spai_status spai_affine_destroy(spai_affine aff);
 
 /* Build P for A (device CSR, values read during the call).  pattern_kind is
  * SPAI_PATTERN_A or SPAI_PATTERN_A2, optionally OR SPAI_PREC_FP32 (FP32 least squares
- * and factor, rank-deficiency test |R_cc| <= 1e-5 max|R_tt|).  The handle keeps the
+ * and factor, rank-deficiency test |R_cc| <= 1e-5 max|R_tt|) or SPAI_PREC_BF16 (the same,
+ * factor stored in BF16).  The handle keeps the
  * pattern analysis (I_k, J_k),
  * A's values in column order (for later updates) and P in row order (for the apply).
  * Synchronises once (reads index-set sizes and the column status).  Returns
@@ -326,7 +332,7 @@ typedef struct spai_server_s *spai_server;
 
 typedef struct {
     int32_t slots;         /* requests on the GPU at once, 1..64 */
-    int32_t pattern_kind;  /* SPAI_PATTERN_A or SPAI_PATTERN_A2, optionally | SPAI_PREC_FP32 */
+    int32_t pattern_kind;  /* SPAI_PATTERN_A or SPAI_PATTERN_A2, optionally | SPAI_PREC_FP32 or SPAI_PREC_BF16 */
     int32_t reuse;         /* 1: cache builds and route nearby requests to spai_update; 0: build per request */
     int32_t restart;       /* block GMRES(m) restart length m */
     int32_t max_cycles;    /* restart cycles before a request fails with SPAI_ENOTCONV */

@@ -223,11 +223,18 @@ def _columns(A_csc, n, Jptr, Jind, Iptr, Ilist, mode, R_csc=None, k0=0, k1=None)
     return val[:len(Jind)], status[:k1 - k0]
 
 
-def spai_build(A, n, kind=PATTERN_A, k0=0, k1=None):
-    """SPAI of A (Sec. 2.2): column k = argmin over supp in J_k of ||e_k - A m||_2."""
+def spai_build(A, n, kind=PATTERN_A, k0=0, k1=None, sets=None):
+    """SPAI of A (Sec. 2.2): column k = argmin over supp in J_k of ||e_k - A m||_2.
+
+    Columns k0 <= k < k1 only, if given (the others stay 0).  ``sets`` = (Jptr, Jind,
+    Iptr, Ilist) as returned by ``pattern`` and ``index_sets`` for this A and kind, to
+    reuse them across calls on the same matrix."""
     A_csc = csr_to_csc(A, n)
-    Jptr, Jind = pattern(A, n, kind)
-    Iptr, Ilist = index_sets(A, n, Jptr, Jind)
+    if sets is None:
+        Jptr, Jind = pattern(A, n, kind)
+        Iptr, Ilist = index_sets(A, n, Jptr, Jind)
+    else:
+        Jptr, Jind, Iptr, Ilist = (_i32(a) for a in sets)
     val, status = _columns(A_csc, n, Jptr, Jind, Iptr, Ilist, 0, None, k0, k1)
     return Precond(n, Jptr, Jind, Iptr, Ilist, val, status, None, A_csc)
 

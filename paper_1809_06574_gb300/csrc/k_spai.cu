@@ -17,6 +17,8 @@
 // FP64 throughput is the limit on GB300 (about 1.1 TFLOP/s), so small tiles use small
 // teams: a shuffle reduction spends log2(T) FP64 adds per dot product, and lanes beyond
 // |I_k| idle.  Large tiles (the 27-point stencil's 125 x 27) use whole warps.
+#include <cuda_bf16.h>
+
 #include <cmath>
 
 #include "spai_internal.cuh"
@@ -53,8 +55,9 @@ template <> __device__ __forceinline__ float singular_rel<float>() { return 1e-5
 constexpr int kBlock = 128;
 
 // per-column shared-memory region: Ahat (maxJ x ld, column-major) | rhs (ld) | rdiag (maxJ)
-// R: working precision (double, or float for SPAI_PREC_FP32); A's values are read in FP64
-// and rounded once to R; the result is written to out_val (R = double) or out_val32.
+// R: working precision (double, or float for SPAI_PREC_FP32 / SPAI_PREC_BF16); A's values
+// are read in FP64 and rounded once to R; the result is written to out_val (R = double),
+// out_val32, or rounded to nearest-even BF16 into out_val16.
 template <int T, typename R>
 __global__ void __launch_bounds__(kBlock) k_spai_columns(ColumnProblem cp, int ld, int maxJ, int L)
 {
@@ -144,7 +147,8 @@ __global__ void __launch_bounds__(kBlock) k_spai_columns(ColumnProblem cp, int l
     }
     if (singular) {
         for (int c = tl; c < nj; c += T) {
-            if (cp.out_val32) cp.out_val32[cp.out_map[ja + c]] = 0.0f;
+            if (cp.out_val16) cp.out_val16[cp.out_map[ja + c]] = 0;
+            else if (cp.out_val32) cp.out_val32[cp.out_map[ja + c]] = 0.0f;
             else cp.out_val[cp.out_map[ja + c]] = 0.0;
         }
         if (tl == 0) cp.col_status[k] = 1;
@@ -160,7 +164,8 @@ __global__ void __launch_bounds__(kBlock) k_spai_columns(ColumnProblem cp, int l
         __syncwarp(mask);
     }
     for (int c = tl; c < nj; c += T) {
-        if (cp.out_val32) cp.out_val32[cp.out_map[ja + c]] = (float)rhs[c];
+        if (cp.out_val16) cp.out_val16[cp.out_map[ja + c]] = __bfloat16_as_ushort(__float2bfloat16_rn((float)rhs[c]));
+        else if (cp.out_val32) cp.out_val32[cp.out_map[ja + c]] = (float)rhs[c];
         else cp.out_val[cp.out_map[ja + c]] = (double)rhs[c];
     }
     if (tl == 0) cp.col_status[k] = 0;
@@ -221,7 +226,8 @@ int launch_columns(cudaStream_t st, const ColumnProblem &cp, int32_t maxI, int32
 int launch_spai_columns(cudaStream_t st, const ColumnProblem &cp, int32_t maxI, int32_t maxJ)
 {
     if (cp.n <= 0) return 0;
-    return cp.out_val32 ? launch_columns<float>(st, cp, maxI, maxJ) : launch_columns<double>(st, cp, maxI, maxJ);
+    return (cp.out_val32 || cp.out_val16) ? launch_columns<float>(st, cp, maxI, maxJ)
+                                          : launch_columns<double>(st, cp, maxI, maxJ);
 }
 
 }  // namespace spai

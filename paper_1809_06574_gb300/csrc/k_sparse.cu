@@ -5,6 +5,8 @@
 //    Sec. 2.2) and the row sets I_k = union of rows(A(:,j)), j in J_k;
 //  * the CSR sparse-times-block product used for A P V in the block Krylov method
 //    (Sec. 2.1) and for the preconditioner apply (Sec. 2.2 footnote).
+#include <cuda_bf16.h>
+
 #include <atomic>
 #include <climits>
 
@@ -302,6 +304,14 @@ __global__ void k_gather_f32_f64(int64_t count, const int32_t *__restrict__ idx,
         dst[i] = (double)src[idx[i]];
 }
 
+__global__ void k_gather_bf16_f64(int64_t count, const int32_t *__restrict__ idx, const uint16_t *__restrict__ src,
+                                  double *__restrict__ dst)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (double)__bfloat162float(__ushort_as_bfloat16(src[idx[i]]));
+}
+
 __global__ void k_invert_perm(int64_t count, const int32_t *__restrict__ perm,
                               int32_t *__restrict__ inv)
 {
@@ -348,6 +358,11 @@ __global__ void k_fill_i32(int64_t count, int32_t v, int32_t *dst)
 // ---------------------------------------------------------------------------------
 // CSR times row-major block: S consecutive lanes per row, lane c owns column c
 // ---------------------------------------------------------------------------------
+// a stored factor value as FP64 (FP64, FP32 or BF16 bits): conversions are exact
+__device__ __forceinline__ double as_f64(double v) { return v; }
+__device__ __forceinline__ double as_f64(float v) { return (double)v; }
+__device__ __forceinline__ double as_f64(uint16_t b) { return (double)__bfloat162float(__ushort_as_bfloat16(b)); }
+
 template <int S, typename V>
 __global__ void __launch_bounds__(kThreads) k_spmm(int32_t n, const int32_t *__restrict__ rowptr,
                                                    const int32_t *__restrict__ colind,
@@ -362,7 +377,7 @@ __global__ void __launch_bounds__(kThreads) k_spmm(int32_t n, const int32_t *__r
     int32_t a = __ldg(rowptr + row), b = __ldg(rowptr + row + 1);
     double acc = 0.0;
     for (int32_t q = a; q < b; ++q)
-        acc = fma((double)__ldg(val + q), __ldg(X + (int64_t)__ldg(colind + q) * S + c), acc);
+        acc = fma(as_f64(__ldg(val + q)), __ldg(X + (int64_t)__ldg(colind + q) * S + c), acc);
     Y[row * S + c] = acc;
 }
 
@@ -520,6 +535,13 @@ int launch_gather_f32_f64(cudaStream_t st, int64_t count, const int32_t *idx, co
     return check_launch();
 }
 
+int launch_gather_bf16_f64(cudaStream_t st, int64_t count, const int32_t *idx, const uint16_t *src, double *dst)
+{
+    if (count <= 0) return 0;
+    k_gather_bf16_f64<<<grid_for(count), kThreads, 0, st>>>(count, idx, src, dst);
+    return check_launch();
+}
+
 int launch_invert_perm(cudaStream_t st, int64_t count, const int32_t *perm, int32_t *inv)
 {
     if (count <= 0) return 0;
@@ -594,6 +616,12 @@ int launch_spmm_f32v(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowpt
                      const float *val, const double *X, double *Y)
 {
     return spmm_any<float>(st, s, n, rowptr, colind, val, X, Y);
+}
+
+int launch_spmm_bf16v(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr, const int32_t *colind,
+                      const uint16_t *val, const double *X, double *Y)
+{
+    return spmm_any<uint16_t>(st, s, n, rowptr, colind, val, X, Y);
 }
 
 int launch_pack(cudaStream_t st, int32_t s, int32_t n, const double *src, int64_t ld, double *dst)

@@ -80,6 +80,7 @@ struct spai_pc_s {
     int depth = 0;
     double *fval = nullptr;    // own factor, P's CSR order (FP64 factors)
     float *fval32 = nullptr;   // the same for SPAI_PREC_FP32 factors
+    uint16_t *fval16 = nullptr;  // the same for SPAI_PREC_BF16 factors (BF16 bit patterns)
     double *a_cval = nullptr;  // this matrix's values in CSC order
     int32_t *status = nullptr;
 };
@@ -464,6 +465,7 @@ spai_status run_columns(spai_ctx ctx, spai_pc pc, int mode, const double *rhs_cv
     cp.out_map = s->p_map;
     cp.out_val = pc->fval;
     cp.out_val32 = pc->fval32;
+    cp.out_val16 = pc->fval16;
     cp.col_status = pc->status;
     cp.d_err = ctx->d_err;
     if (s->n == 0) return SPAI_OK;
@@ -486,16 +488,29 @@ spai_status run_columns(spai_ctx ctx, spai_pc pc, int mode, const double *rhs_cv
     return SPAI_OK;
 }
 
-spai_status pc_alloc(spai_ctx ctx, Sym *s, bool fp32, spai_pc *out)
+// factor storage precision from the SPAI_PREC_* bits: 0 FP64, 1 FP32, 2 BF16, -1 invalid
+int prec_of(int32_t flags)
+{
+    const int32_t p = flags & (SPAI_PREC_FP32 | SPAI_PREC_BF16);
+    if (p == 0) return 0;
+    if (p == SPAI_PREC_FP32) return 1;
+    if (p == SPAI_PREC_BF16) return 2;
+    return -1;
+}
+
+spai_status pc_alloc(spai_ctx ctx, Sym *s, int prec, spai_pc *out)
 {
     spai_pc pc = new spai_pc_s();
     pc->ctx = ctx;
     pc->sym = s;
     spai_status st;
-    if ((fp32 ? (st = dalloc_n(ctx, &pc->fval32, s->nnzP)) : (st = dalloc_n(ctx, &pc->fval, s->nnzP))) ||
+    if ((prec == 1   ? (st = dalloc_n(ctx, &pc->fval32, s->nnzP))
+         : prec == 2 ? (st = dalloc_n(ctx, &pc->fval16, s->nnzP))
+                     : (st = dalloc_n(ctx, &pc->fval, s->nnzP))) ||
         (st = dalloc_n(ctx, &pc->a_cval, s->nnzA)) || (st = dalloc_n(ctx, &pc->status, s->n))) {
         dfree(ctx, pc->fval);
         dfree(ctx, pc->fval32);
+        dfree(ctx, pc->fval16);
         dfree(ctx, pc->a_cval);
         dfree(ctx, pc->status);
         delete pc;
@@ -503,6 +518,7 @@ spai_status pc_alloc(spai_ctx ctx, Sym *s, bool fp32, spai_pc *out)
     }
     if (s->nnzP && pc->fval) CU(cudaMemsetAsync(pc->fval, 0, (size_t)s->nnzP * 8, ctx->stream), "memset");
     if (s->nnzP && pc->fval32) CU(cudaMemsetAsync(pc->fval32, 0, (size_t)s->nnzP * 4, ctx->stream), "memset");
+    if (s->nnzP && pc->fval16) CU(cudaMemsetAsync(pc->fval16, 0, (size_t)s->nnzP * 2, ctx->stream), "memset");
     *out = pc;
     return SPAI_OK;
 }
@@ -518,7 +534,11 @@ spai_status apply_rm(spai_ctx ctx, spai_pc pc, int32_t s, const double *X, doubl
         spai_pc h = chain[i];
         double *dst = (i == 0) ? Y : bufs[(chain.size() - 1 - i) & 1];
         const double nz = h->sym->nnzP, nn = h->sym->n;
-        if (h->fval32) {
+        if (h->fval16) {
+            PKL("spmm_P", 2.0 * nz * s, 6.0 * nz + 4.0 * (nn + 1) + 16.0 * nn * s,
+                launch_spmm_bf16v(ctx->stream, s, h->sym->n, h->sym->p_rowptr, h->sym->p_colind, h->fval16, cur, dst),
+                "preconditioner apply");
+        } else if (h->fval32) {
             PKL("spmm_P", 2.0 * nz * s, 8.0 * nz + 4.0 * (nn + 1) + 16.0 * nn * s,
                 launch_spmm_f32v(ctx->stream, s, h->sym->n, h->sym->p_rowptr, h->sym->p_colind, h->fval32, cur, dst),
                 "preconditioner apply");
@@ -775,8 +795,9 @@ extern "C" spai_status spai_build(spai_ctx ctx, const spai_csr *A, int32_t patte
 {
     if (!ctx || !out) return fail(ctx, SPAI_EINVAL, "NULL argument");
     *out = nullptr;
-    const bool fp32 = (pattern_kind & SPAI_PREC_FP32) != 0;
-    pattern_kind &= ~SPAI_PREC_FP32;
+    const int prec = prec_of(pattern_kind);
+    if (prec < 0) return fail(ctx, SPAI_EINVAL, "SPAI_PREC_FP32 and SPAI_PREC_BF16 are exclusive");
+    pattern_kind &= ~(SPAI_PREC_FP32 | SPAI_PREC_BF16);
     if (pattern_kind != SPAI_PATTERN_A && pattern_kind != SPAI_PATTERN_A2)
         return fail(ctx, SPAI_EINVAL, "unknown pattern kind %d", pattern_kind);
     spai_status st = validate_device_csr(ctx, A, "A");
@@ -784,7 +805,7 @@ extern "C" spai_status spai_build(spai_ctx ctx, const spai_csr *A, int32_t patte
     Sym *s = nullptr;
     if ((st = sym_create(ctx, A, pattern_kind, &s))) return st;
     spai_pc pc = nullptr;
-    if ((st = pc_alloc(ctx, s, fp32, &pc))) { sym_release(s); return st; }
+    if ((st = pc_alloc(ctx, s, prec, &pc))) { sym_release(s); return st; }
     pc->root = pc;
     if (s->nnzA)
         PKL("gather_csc", 0.0, 20.0 * s->nnzA, launch_gather_f64(ctx->stream, s->nnzA, s->a_perm, A->val, pc->a_cval),
@@ -799,8 +820,9 @@ extern "C" spai_status spai_update(spai_ctx ctx, spai_pc base, const spai_csr *A
 {
     if (!ctx || !out || !base) return fail(ctx, SPAI_EINVAL, "NULL argument");
     *out = nullptr;
-    const bool fp32 = (approach & SPAI_PREC_FP32) != 0;
-    approach &= ~SPAI_PREC_FP32;
+    const int prec = prec_of(approach);
+    if (prec < 0) return fail(ctx, SPAI_EINVAL, "SPAI_PREC_FP32 and SPAI_PREC_BF16 are exclusive");
+    approach &= ~(SPAI_PREC_FP32 | SPAI_PREC_BF16);
     if (approach != SPAI_UPDATE_FIRST && approach != SPAI_UPDATE_CHAINED)
         return fail(ctx, SPAI_EINVAL, "unknown update approach %d", approach);
     spai_status st = check_csr_args(ctx, A_new, "A_new");
@@ -819,7 +841,7 @@ extern "C" spai_status spai_update(spai_ctx ctx, spai_pc base, const spai_csr *A
         if (h) return fail(ctx, SPAI_EINVAL, "A_new does not have the base matrix's sparsity pattern");
     }
     spai_pc pc = nullptr;
-    if ((st = pc_alloc(ctx, s, fp32, &pc))) return st;
+    if ((st = pc_alloc(ctx, s, prec, &pc))) return st;
     s->refs++;
     spai_pc from = (approach == SPAI_UPDATE_FIRST) ? base->root : base;
     pc->parent = from;
@@ -850,7 +872,7 @@ extern "C" size_t spai_pc_mem_size(spai_pc pc, int32_t with_analysis)
     auto r = [](size_t b) { return ((b ? b : 16) + 255) / 256 * 256; };  // as dalloc rounds
     const Sym *s = pc->sym;
     const size_t n1 = (size_t)s->n + 1;
-    size_t b = r((size_t)s->nnzP * (pc->fval32 ? 4 : 8)) + r((size_t)s->nnzA * 8) + r((size_t)s->n * 4);
+    size_t b = r((size_t)s->nnzP * (pc->fval16 ? 2 : pc->fval32 ? 4 : 8)) + r((size_t)s->nnzA * 8) + r((size_t)s->n * 4);
     if (with_analysis) {
         b += 2 * r(n1 * 4) + 3 * r((size_t)s->nnzA * 4) + r(n1 * 4) + r((size_t)s->nI * 4);
         if (!s->alias) b += 2 * r(n1 * 4) + 3 * r((size_t)s->nnzP * 4);
@@ -867,7 +889,9 @@ extern "C" spai_status spai_pc_export(spai_ctx ctx, spai_pc pc, int32_t *Jptr, i
     if (Jptr) CU(cudaMemcpyAsync(Jptr, s->Jptr, ((size_t)n + 1) * 4, cudaMemcpyDeviceToDevice, ctx->stream), "export");
     if (Jind && s->nnzP) CU(cudaMemcpyAsync(Jind, s->Jind, (size_t)s->nnzP * 4, cudaMemcpyDeviceToDevice, ctx->stream), "export");
     if (val && s->nnzP) {
-        if (pc->fval32)
+        if (pc->fval16)
+            KL(launch_gather_bf16_f64(ctx->stream, s->nnzP, s->p_map, pc->fval16, val), "export values");
+        else if (pc->fval32)
             KL(launch_gather_f32_f64(ctx->stream, s->nnzP, s->p_map, pc->fval32, val), "export values");
         else
             KL(launch_gather_f64(ctx->stream, s->nnzP, s->p_map, pc->fval, val), "export values");
@@ -884,6 +908,7 @@ extern "C" spai_status spai_pc_destroy(spai_pc pc)
     spai_ctx ctx = pc->ctx;
     dfree(ctx, pc->fval);
     dfree(ctx, pc->fval32);
+    dfree(ctx, pc->fval16);
     dfree(ctx, pc->a_cval);
     dfree(ctx, pc->status);
     sym_release(pc->sym);
@@ -1390,7 +1415,10 @@ extern "C" spai_status spai_pc_apply_noalloc(spai_ctx ctx, spai_pc pc, int32_t s
         spai_pc h = pc;
         for (int hop = 0; hop < i; ++hop) h = h->parent;
         double *dst = (i == 0) ? yr : bufs[(len - 1 - i) & 1];
-        if (h->fval32)
+        if (h->fval16)
+            KL(launch_spmm_bf16v(ctx->stream, s, n, h->sym->p_rowptr, h->sym->p_colind, h->fval16, cur, dst),
+               "preconditioner apply");
+        else if (h->fval32)
             KL(launch_spmm_f32v(ctx->stream, s, n, h->sym->p_rowptr, h->sym->p_colind, h->fval32, cur, dst),
                "preconditioner apply");
         else

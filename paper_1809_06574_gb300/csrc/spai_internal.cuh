@@ -77,6 +77,10 @@ int launch_compare_i32(cudaStream_t st, int64_t count, const int32_t *a, const i
 // row-major blocks: X[r * s + c]
 int launch_spmm(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr,
                 const int32_t *colind, const double *val, const double *X, double *Y);
+// same with BF16 values (bit patterns; products and sums in FP64)
+int launch_spmm_bf16v(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr, const int32_t *colind,
+                      const uint16_t *val, const double *X, double *Y);
+int launch_gather_bf16_f64(cudaStream_t st, int64_t count, const int32_t *idx, const uint16_t *src, double *dst);
 // same with FP32 values (products and sums in FP64)
 int launch_spmm_f32v(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr, const int32_t *colind,
                      const float *val, const double *X, double *Y);
@@ -97,6 +101,7 @@ struct ColumnProblem {
     const int32_t *out_map;          // J position -> position in the output array
     double *out_val;
     float *out_val32;                // non-null: solve in FP32 and write here instead
+    uint16_t *out_val16;             // non-null: solve in FP32 and write BF16 bits here instead
     int32_t *col_status;             // 0 ok, 1 singular
     int *d_err;
 };

@@ -43,6 +43,8 @@ size_t round256(size_t b) { return ((b ? b : 16) + 255) / 256 * 256; }
 // without the lock while add_system appends
 constexpr size_t kMaxSystems = 1024;
 
+constexpr int32_t kPrecBits = SPAI_PREC_FP32 | SPAI_PREC_BF16;
+
 struct System {
     spai_affine aff = nullptr;
     int32_t n = 0, nnz = 0, nterms = 0, max_row = 0;
@@ -151,7 +153,7 @@ size_t build_estimate(const spai_server_s *S, const System &y)
 {
     if (y.build_bytes) return y.build_bytes;
     const size_t n1 = (size_t)y.n + 1, nz = (size_t)y.nnz, mr = (size_t)(y.max_row > 0 ? y.max_row : 1);
-    const bool a2 = (S->o.pattern_kind & ~SPAI_PREC_FP32) == SPAI_PATTERN_A2;
+    const bool a2 = (S->o.pattern_kind & ~kPrecBits) == SPAI_PATTERN_A2;
     const size_t nzP = a2 ? nz * mr : nz;
     size_t b = 3 * round256(n1 * 4) + 3 * round256(nz * 4) + round256(nzP * mr * 4);
     if (a2) b += 2 * round256(n1 * 4) + 3 * round256(nzP * 4);
@@ -164,10 +166,11 @@ size_t analysis_transient(const System &y) { return 16 * (size_t)y.nnz + 16 * ((
 
 size_t update_estimate(const spai_server_s *S, const System &y)
 {
-    const bool a2 = (S->o.pattern_kind & ~SPAI_PREC_FP32) == SPAI_PATTERN_A2;
-    const bool f32 = (S->o.pattern_kind & SPAI_PREC_FP32) != 0;
+    const bool a2 = (S->o.pattern_kind & ~kPrecBits) == SPAI_PATTERN_A2;
+    const int32_t prec = S->o.pattern_kind & kPrecBits;
     const size_t nzP = a2 ? (size_t)y.nnz * (size_t)(y.max_row > 0 ? y.max_row : 1) : (size_t)y.nnz;
-    return round256(nzP * (f32 ? 4 : 8)) + round256((size_t)y.nnz * 8) + round256((size_t)y.n * 4);
+    const size_t vb = prec == SPAI_PREC_BF16 ? 2 : prec == SPAI_PREC_FP32 ? 4 : 8;
+    return round256(nzP * vb) + round256((size_t)y.nnz * 8) + round256((size_t)y.n * 4);
 }
 
 // nearest cached build for (system, s) within the radius (ready or in progress)
@@ -342,7 +345,7 @@ int run(spai_server_s *S, int k, const Job &job, spai_pc *built, std::string *ms
     if (st) { *msg = spai_last_error(ctx); return st; }
     spai_csr A{n, y.nnz, y.rowptr, y.colind, sl.A};
     spai_pc pc = nullptr, own = nullptr;
-    const int32_t prec = S->o.pattern_kind & SPAI_PREC_FP32;
+    const int32_t prec = S->o.pattern_kind & kPrecBits;
     if (job.route == SPAI_ROUTE_BUILD) {
         st = spai_build(ctx, &A, S->o.pattern_kind, &own);
         if (st) {
@@ -453,10 +456,11 @@ extern "C" spai_status spai_server_create(const spai_server_opts *opts, spai_ser
 {
     if (!opts || !out) return SPAI_EINVAL;
     *out = nullptr;
-    const int32_t kind = opts->pattern_kind & ~SPAI_PREC_FP32;
+    const int32_t kind = opts->pattern_kind & ~kPrecBits;
     if (opts->slots < 1 || opts->slots > 64 || opts->restart < 1 || opts->max_cycles < 1 || !(opts->tol >= 0.0) ||
         !(opts->radius >= 0.0) || (kind != SPAI_PATTERN_A && kind != SPAI_PATTERN_A2) ||
-        (opts->pattern_kind & ~(SPAI_PREC_FP32 | 1)) || opts->orth < SPAI_ORTH_AUTO || opts->orth > SPAI_ORTH_TENSOR)
+        (opts->pattern_kind & ~(kPrecBits | 1)) || (opts->pattern_kind & kPrecBits) == kPrecBits ||
+        opts->orth < SPAI_ORTH_AUTO || opts->orth > SPAI_ORTH_TENSOR)
         return SPAI_EINVAL;
     spai_server_s *S = new spai_server_s();
     S->o = *opts;

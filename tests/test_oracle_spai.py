@@ -212,3 +212,17 @@ def test_lu_matches_numpy():
     D = rng.standard_normal((25, 25))
     B = rng.standard_normal((25, 3))
     assert np.allclose(oracle.lu_solve(D, B), np.linalg.solve(D, B), rtol=1e-10, atol=1e-12)
+
+
+def test_build_with_precomputed_sets_and_column_range():
+    """spai_build(sets=..., k0, k1) reuses the given pattern / index sets and fills only
+    the requested columns: identical to the full build there, zero elsewhere."""
+    A, _ = synth.random_sparse(60, 0.06, seed=4)
+    n = 60
+    full = oracle.spai_build(A, n, oracle.PATTERN_A2)
+    Jptr, Jind = oracle.pattern(A, n, oracle.PATTERN_A2)
+    Iptr, Ilist = oracle.index_sets(A, n, Jptr, Jind)
+    part = oracle.spai_build(A, n, oracle.PATTERN_A2, k0=10, k1=25, sets=(Jptr, Jind, Iptr, Ilist))
+    sl = slice(Jptr[10], Jptr[25])
+    assert np.array_equal(part.val[sl], full.val[sl])
+    assert not part.val[:Jptr[10]].any() and not part.val[Jptr[25]:].any()
