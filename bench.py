@@ -64,6 +64,10 @@ def parse():
     ap.add_argument("--large-only", action="store_true")
     ap.add_argument("--large-side", type=int, default=128)
     ap.add_argument("--large-params", type=int, default=3)
+    # batched workload: 256 independent 2D 5-point systems, sides 48-256
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-only", action="store_true")
+    ap.add_argument("--batched-systems", type=int, default=256)
     return ap.parse_args()
 
 
@@ -431,6 +435,88 @@ def run_serving(args, sg, torch):
     }
 
 
+# ------------------------------------------------------------------------------- batched
+def run_batched(args, sg, torch):
+    """256 independent 2D 5-point systems (grid sides ~ U{48..256}, each with its own seed,
+    p ~ U[0.1, 1], s = 1), SPAI pattern of A for half of them and of A^2 for the other half,
+    FP32 factors: all SPAI builds in one spai_build_batch call (one persistent launch per
+    tile shape), then every system solved (4 RHS, block GMRES(30) to 1e-8 in FP64) on
+    `workers` streams.  Beside it: the same builds one spai_build call at a time."""
+    import synth
+    from concurrent.futures import ThreadPoolExecutor
+    rng = np.random.default_rng(np.random.SeedSequence(0).spawn(5)[4])
+    nsys = args.batched_systems
+    sides = rng.integers(48, 257, size=nsys)
+    ps = rng.uniform(0.1, 1.0, size=nsys)
+    kinds = [(sg.PATTERN_A if i % 2 == 0 else sg.PATTERN_A2) | sg.PREC_FP32 for i in range(nsys)]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    ctx = sg.spai_ctx_create(stream.cuda_stream, 0)
+    systems = []
+    for i in range(nsys):
+        w = synth.grid_workload((int(sides[i]), int(sides[i])), "5pt", seed=1000 + i, nrhs=4, params=[float(ps[i])])
+        aff = sg.spai_affine_create(ctx, [sg.csr(w.n, *t) for t in w.terms])
+        _, nnz, rp, ci = sg.spai_affine_pattern(aff)
+        va = torch.empty(nnz, dtype=torch.float64, device=dev)
+        sg.spai_assemble(ctx, aff, sg.affine_coefficients(float(ps[i]), 1.0), va)
+        B = torch.as_tensor(np.ascontiguousarray(w.B.T), device=dev)
+        systems.append({"w": w, "aff": aff, "va": va, "A": sg.csr(w.n, rp, ci, va, nnz), "B": B})
+    As = [y["A"] for y in systems]
+    # tune the tile shapes once (a small batch with both shapes), as a long-running process would
+    for pc in sg.spai_build_batch(ctx, As[:2], kinds[:2])[0]:
+        sg.spai_pc_destroy(pc)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pcs, _ = sg.spai_build_batch(ctx, As, kinds)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for A, k in zip(As, kinds):
+        sg.spai_pc_destroy(sg.spai_build(ctx, A, k)[0])
+    torch.cuda.synchronize()
+    t_loop = time.perf_counter() - t0
+
+    workers = [(torch.cuda.Stream(device=dev),) for _ in range(args.workers)]
+    wctx = [sg.spai_ctx_create(st.cuda_stream, 0) for (st,) in workers]
+    Xs = [torch.zeros((4, y["w"].n), dtype=torch.float64, device=dev) for y in systems]
+    iters = [0] * nsys
+
+    def solve_share(k):
+        for i in range(k, nsys, len(workers)):
+            y = systems[i]
+            n = y["w"].n
+            with torch.cuda.stream(workers[k][0]):
+                Xs[i].zero_()
+            st, info, rel = sg.block_solve(wctx[k], y["A"], pcs[i], 4, y["B"], n, Xs[i], n, 30, 1e-8, 100)
+            if not info["converged"]:
+                raise RuntimeError(f"batched system {i} did not converge: {info}")
+            iters[i] = info["iterations"]
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=len(workers)) as ex:
+        list(ex.map(solve_share, range(len(workers))))
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    for c in wctx:
+        sg.spai_ctx_destroy(c)
+    for pc in pcs:
+        sg.spai_pc_destroy(pc)
+    for y in systems:
+        sg.spai_affine_destroy(y["aff"])
+    sg.spai_ctx_destroy(ctx)
+    ncols = int(sum(y["w"].n for y in systems))
+    return {
+        "workload": f"{nsys} independent 2D 5-point systems, sides U{{48..256}} (n {min(y['w'].n for y in systems)}-"
+                    f"{max(y['w'].n for y in systems)}, {ncols} columns in all), p ~ U[0.1,1], s=1, SPAI pattern of A "
+                    f"(half) / A^2 (half), FP32 factors, 4 RHS, block GMRES(30) to 1e-8 in FP64",
+        "build_batch_ms": 1e3 * t_batch, "build_one_by_one_ms": 1e3 * t_loop, "batch_speedup": t_loop / t_batch,
+        "solve_all_ms": 1e3 * t_solve, "workers": len(workers),
+        "value": nsys / (t_batch + t_solve), "unit": UNIT,
+        "gmres_iterations": {"mean": float(np.mean(iters)), "max": int(max(iters))},
+    }
+
+
 # ------------------------------------------------------------------------------- large
 def run_large(args, sg, torch):
     """3D side^3 27-point workload (side 128: n = 2,097,152, 27 nnz per column, 16 RHS):
@@ -674,6 +760,10 @@ def main():
         if rank == 0:
             print(json.dumps({"large": run_large(args, sg, torch)}), flush=True)
         return
+    if args.batched_only:
+        if rank == 0:
+            print(json.dumps({"batched": run_batched(args, sg, torch)}), flush=True)
+        return
     ctx = sg.spai_ctx_create(stream.cuda_stream, 0)
     fp64_tflops = max(sg.spai_measure_fp64_rate(ctx) for _ in range(3))
 
@@ -789,6 +879,9 @@ def main():
     large = None
     if rank == 0 and world == 1 and not args.no_large:
         large = run_large(args, sg, torch)
+    batched = None
+    if rank == 0 and world == 1 and not args.no_batched:
+        batched = run_batched(args, sg, torch)
 
     if rank == 0:
         total_ms = sum(f["ms"] for f in prof) or 1.0
@@ -820,7 +913,7 @@ def main():
                                             "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                                             "workers": args.workers},
             "roofline": roofline, "roofline_isolated": roofline_iso, "mixed_precision": mixed,
-            "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "large": large, "gpu_launches": int(launches),
+            "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "large": large, "batched": batched, "gpu_launches": int(launches),
             "clocks": clk, "fp64_tflops_measured": fp64_tflops,
             "gmres_iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)),
                                  "max": int(max(iters))},

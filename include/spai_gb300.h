@@ -191,6 +191,23 @@ SPAI_API spai_status spai_affine_destroy(spai_affine aff);
  * and spai_pc_export reports them. */
 SPAI_API spai_status spai_build(spai_ctx ctx, const spai_csr *A, int32_t pattern_kind, spai_pc *out);
 
+/* Build the SPAI preconditioners of nsys independent systems at once (Sec. 2.2: every
+ * column of every system is an independent least-squares problem).  A[i] and
+ * pattern_kind[i] are as for spai_build (the pattern and the precision may differ between
+ * systems); out[i] receives system i's handle, the same kind of handle spai_build returns
+ * (update, apply, solve and destroy it on its own).  The pattern analyses of all systems
+ * run phase by phase with one host read-back per phase for all of them (at most five
+ * synchronisations whatever nsys is), and the column problems of all systems run in one
+ * persistent launch per tile shape -- systems are grouped by working precision, max |J_k|
+ * and max |I_k| rounded up to 8.  Team size (lanes per column problem): the first batch
+ * of the process that meets a shape times every team size whose block fits and keeps the
+ * fastest; later batches reuse it (team sizes change the rounding of the reductions only,
+ * results stay within the FP64 bar of spai_build).  1 <= nsys <= 65536.  Synchronises.
+ * Returns SPAI_ESINGULAR (handles still returned) if some column of some system is rank
+ * deficient; on any other error no handle is returned. */
+SPAI_API spai_status spai_build_batch(spai_ctx ctx, int32_t nsys, const spai_csr *A, const int32_t *pattern_kind,
+                                      spai_pc *out);
+
 /* Cheap update, Table 1 and Sec. 2.4: for A_new = A(l) on the SAME pattern as the base
  * matrix, column k of Q_l = argmin_{supp q in J_k} ||a1_k - A(l) q||_2 with a1_k column
  * k of A(1) (approach SPAI_UPDATE_FIRST: A(1) is the root build's matrix; approach

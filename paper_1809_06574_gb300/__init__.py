@@ -22,7 +22,7 @@ __all__ = [
     "spai_ctx_mem_in_use", "spai_launch_count", "spai_ctx_profile", "spai_ctx_profile_count", "spai_measure_fp64_rate",
     "spai_ctx_profile_entry", "spai_affine_create", "spai_affine_pattern",
     "spai_assemble", "spai_affine_export", "spai_affine_destroy", "spai_build", "spai_update", "spai_pc_info",
-    "spai_pc_export", "spai_pc_destroy", "spai_spmm", "spai_pc_apply", "block_solve",
+    "spai_pc_export", "spai_pc_destroy", "spai_build_batch", "spai_spmm", "spai_pc_apply", "block_solve",
     "affine_coefficients", "PATTERN_A", "PATTERN_A2", "UPDATE_FIRST", "UPDATE_CHAINED", "PREC_FP32", "PREC_BF16",
     "LIB_PATH", "spai_ctx_trim", "spai_solve_workspace_size", "spai_pc_mem_size",
     "spai_server_opts", "spai_request", "spai_result", "spai_server_stats", "spai_server_create",
@@ -148,6 +148,7 @@ def lib():
         "block_solve": (i32, [vp, P(spai_csr), vp, i32, vp, i64, vp, i64, P(spai_solve_opts),
                               P(spai_solve_info), P(dbl)]),
         "spai_ctx_trim": (i32, [vp]),
+        "spai_build_batch": (i32, [vp, i32, P(spai_csr), P(i32), P(vp)]),
         "spai_solve_workspace_size": (sz, [i32, i32, i32]),
         "spai_pc_mem_size": (sz, [vp, i32]),
         "spai_server_create": (i32, [P(spai_server_opts), P(vp)]),
@@ -304,6 +305,25 @@ def spai_build(ctx, A, pattern_kind=PATTERN_A, allow_singular=False):
         raise SpaiError(st, msg)
     _check(ctx, st, allow=(SPAI_ESINGULAR,))
     return out, st
+
+
+def spai_build_batch(ctx, As, pattern_kinds, allow_singular=False):
+    """SPAI of many systems at once: As list of spai_csr (device), pattern_kinds list of ints.
+    Returns (list of handles, status)."""
+    m = len(As)
+    arr = (spai_csr * m)(*As)
+    kinds = (C.c_int32 * m)(*[int(k) for k in pattern_kinds])
+    out = (C.c_void_p * m)()
+    st = lib().spai_build_batch(ctx, m, arr, kinds, out)
+    pcs = [C.c_void_p(out[i]) if out[i] else None for i in range(m)]
+    if st == SPAI_ESINGULAR and not allow_singular:
+        msg = spai_last_error(ctx)
+        for pc in pcs:
+            if pc:
+                lib().spai_pc_destroy(pc)
+        raise SpaiError(st, msg)
+    _check(ctx, st, allow=(SPAI_ESINGULAR,))
+    return pcs, st
 
 
 def spai_update(ctx, base, A_new, approach=UPDATE_FIRST, allow_singular=False):

@@ -58,19 +58,9 @@ constexpr int kBlock = 128;
 // R: working precision (double, or float for SPAI_PREC_FP32 / SPAI_PREC_BF16); A's values
 // are read in FP64 and rounded once to R; the result is written to out_val (R = double),
 // out_val32, or rounded to nearest-even BF16 into out_val16.
-template <int T, typename R>
-__global__ void __launch_bounds__(kBlock) k_spai_columns(ColumnProblem cp, int ld, int maxJ, int L)
+template <int T, typename R, typename P>
+__device__ __forceinline__ void column_ls(const P &cp, int64_t k, R *Ah, int ld, int maxJ, int tl, unsigned mask)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *smem = reinterpret_cast<R *>(smem_raw);
-    const int lane = threadIdx.x & 31;
-    const int team = threadIdx.x / T, tl = threadIdx.x % T;
-    const int teams = blockDim.x / T;
-    const unsigned mask = (T == 32) ? 0xffffffffu : (((1u << T) - 1u) << ((lane / T) * T));
-    const int64_t k = (int64_t)blockIdx.x * teams + team;
-    if (k >= cp.n) return;  // whole team leaves together
-
-    R *Ah = smem + (size_t)team * L;
     R *rhs = Ah + (size_t)maxJ * ld;
     R *rdiag = rhs + ld;
 
@@ -171,8 +161,40 @@ __global__ void __launch_bounds__(kBlock) k_spai_columns(ColumnProblem cp, int l
     if (tl == 0) cp.col_status[k] = 0;
 }
 
+
+// One team per column problem, persistent over the columns: column g of a batch belongs to
+// the system i with start[i] <= g < start[i + 1] (its local column g - start[i]); without
+// a batch table the columns are those of cp0.
 template <int T, typename R>
-int launch_team(cudaStream_t st, const ColumnProblem &cp, int ld, int maxJ, int L, int threads)
+__global__ void __launch_bounds__(kBlock) k_spai_columns(ColumnProblem cp0, ColumnBatch bt, int ld, int maxJ, int L)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *smem = reinterpret_cast<R *>(smem_raw);
+    const int lane = threadIdx.x & 31;
+    const int team = threadIdx.x / T, tl = threadIdx.x % T;
+    const int teams = blockDim.x / T;
+    const unsigned mask = (T == 32) ? 0xffffffffu : (((1u << T) - 1u) << ((lane / T) * T));
+    R *Ah = smem + (size_t)team * L;
+    const int64_t total = bt.tab ? bt.total : (int64_t)cp0.n;
+    // the whole team takes the same columns and leaves together
+    for (int64_t g = (int64_t)blockIdx.x * teams + team; g < total; g += (int64_t)gridDim.x * teams) {
+        if (bt.tab) {
+            int lo = 0, hi = bt.nsys - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(bt.start + mid) <= g) lo = mid; else hi = mid - 1;
+            }
+            column_ls<T, R>(bt.tab[lo], g - __ldg(bt.start + lo), Ah, ld, maxJ, tl, mask);
+        } else {
+            column_ls<T, R>(cp0, g, Ah, ld, maxJ, tl, mask);
+        }
+        __syncwarp(mask);
+    }
+}
+
+template <int T, typename R>
+int launch_team(cudaStream_t st, const ColumnProblem &cp, const ColumnBatch &bt, int ld, int maxJ, int L,
+                int threads)
 {
     const int teams = threads / T;
     const size_t smem = (size_t)teams * L * sizeof(R);
@@ -180,8 +202,20 @@ int launch_team(cudaStream_t st, const ColumnProblem &cp, int ld, int maxJ, int 
         cudaFuncSetAttribute(k_spai_columns<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return -1;
-    const int64_t blocks = ((int64_t)cp.n + teams - 1) / teams;
-    k_spai_columns<T, R><<<(unsigned)blocks, threads, smem, st>>>(cp, ld, maxJ, L);
+    const int64_t total = bt.tab ? bt.total : (int64_t)cp.n;
+    int64_t blocks = (total + teams - 1) / teams;
+    if (bt.tab) {
+        // persistent: as many blocks as are resident at once
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spai_columns<T, R>, threads, smem) != cudaSuccess)
+            return -1;
+        const int64_t resident = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+        if (blocks > resident) blocks = resident;
+    }
+    if (blocks < 1) blocks = 1;
+    k_spai_columns<T, R><<<(unsigned)blocks, threads, smem, st>>>(cp, bt, ld, maxJ, L);
     note_launches(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -196,28 +230,49 @@ bool spai_columns_fit(int32_t maxI, int32_t maxJ)
 
 namespace {
 
+// Shared-memory stride of one problem (odd: spreads the teams over the banks).
+int tile_stride(int32_t maxI, int32_t maxJ)
+{
+    const int ld = maxI < 1 ? 1 : maxI, mj = maxJ < 1 ? 1 : maxJ;
+    return (mj * ld + ld + mj) | 1;
+}
+
+// Threads per block for team size T, or 0 if one block of that team size does not fit.
+int threads_for(int T, size_t per)
+{
+    int threads = kBlock;
+    while (threads > T && (size_t)(threads / T) * per > 200 * 1024) threads /= 2;
+    return (threads >= 32 && (size_t)(threads / T) * per <= 220 * 1024) ? threads : 0;
+}
+
+// Default team size: the smallest team whose 128-thread block fits in ~110 KB (two blocks
+// per SM).
+int default_team(size_t per)
+{
+    int T = 1;
+    while (T < 32 && (size_t)(kBlock / T) * per > 110 * 1024) T *= 2;
+    return T;
+}
+
 template <typename R>
-int launch_columns(cudaStream_t st, const ColumnProblem &cp, int32_t maxI, int32_t maxJ)
+int launch_columns(cudaStream_t st, const ColumnProblem &cp, const ColumnBatch &bt, int32_t maxI, int32_t maxJ,
+                   int T)
 {
     const int ld = maxI < 1 ? 1 : maxI;
     const int mj = maxJ < 1 ? 1 : maxJ;
-    int L = mj * ld + ld + mj;
-    L |= 1;  // odd stride spreads the teams over the shared-memory banks
-    // smallest team whose 128-thread block fits in ~110 KB (two blocks per SM)
+    const int L = tile_stride(maxI, maxJ);
     const size_t per = (size_t)L * sizeof(R);
-    int T = 1;
-    while (T < 32 && (size_t)(kBlock / T) * per > 110 * 1024) T *= 2;
-    int threads = kBlock;
-    if (T == 32 && (size_t)(threads / 32) * per > 200 * 1024) threads = 64;
-    if (T == 32 && (size_t)(threads / 32) * per > 200 * 1024) threads = 32;
-    if ((size_t)(threads / T) * per > 220 * 1024) return -1;
+    if (T == 0) T = default_team(per);
+    const int threads = threads_for(T, per);
+    if (!threads) return -1;
     switch (T) {
-    case 1: return launch_team<1, R>(st, cp, ld, mj, L, threads);
-    case 2: return launch_team<2, R>(st, cp, ld, mj, L, threads);
-    case 4: return launch_team<4, R>(st, cp, ld, mj, L, threads);
-    case 8: return launch_team<8, R>(st, cp, ld, mj, L, threads);
-    case 16: return launch_team<16, R>(st, cp, ld, mj, L, threads);
-    default: return launch_team<32, R>(st, cp, ld, mj, L, threads);
+    case 1: return launch_team<1, R>(st, cp, bt, ld, mj, L, threads);
+    case 2: return launch_team<2, R>(st, cp, bt, ld, mj, L, threads);
+    case 4: return launch_team<4, R>(st, cp, bt, ld, mj, L, threads);
+    case 8: return launch_team<8, R>(st, cp, bt, ld, mj, L, threads);
+    case 16: return launch_team<16, R>(st, cp, bt, ld, mj, L, threads);
+    case 32: return launch_team<32, R>(st, cp, bt, ld, mj, L, threads);
+    default: return -1;
     }
 }
 
@@ -226,8 +281,29 @@ int launch_columns(cudaStream_t st, const ColumnProblem &cp, int32_t maxI, int32
 int launch_spai_columns(cudaStream_t st, const ColumnProblem &cp, int32_t maxI, int32_t maxJ)
 {
     if (cp.n <= 0) return 0;
-    return (cp.out_val32 || cp.out_val16) ? launch_columns<float>(st, cp, maxI, maxJ)
-                                          : launch_columns<double>(st, cp, maxI, maxJ);
+    const ColumnBatch none{};
+    return (cp.out_val32 || cp.out_val16) ? launch_columns<float>(st, cp, none, maxI, maxJ, 0)
+                                          : launch_columns<double>(st, cp, none, maxI, maxJ, 0);
+}
+
+int spai_columns_teams(int32_t maxI, int32_t maxJ, bool low_precision, int *teams)
+{
+    const size_t per = (size_t)tile_stride(maxI, maxJ) * (low_precision ? sizeof(float) : sizeof(double));
+    int k = 0;
+    const int def = default_team(per);
+    teams[k++] = def;  // the default first
+    for (int T = 1; T <= 32; T *= 2)
+        if (T != def && threads_for(T, per)) teams[k++] = T;
+    return k;
+}
+
+int launch_spai_columns_batch(cudaStream_t st, const ColumnBatch &bt, bool low_precision, int32_t maxI,
+                              int32_t maxJ, int team)
+{
+    if (bt.total <= 0) return 0;
+    const ColumnProblem none{};
+    return low_precision ? launch_columns<float>(st, none, bt, maxI, maxJ, team)
+                         : launch_columns<double>(st, none, bt, maxI, maxJ, team);
 }
 
 }  // namespace spai

@@ -6,11 +6,14 @@
 // memory and turns failures into status codes.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <tuple>
 #include <atomic>
 #include <mutex>
 #include <string>
@@ -334,116 +337,185 @@ void sym_release(Sym *s)
     delete s;
 }
 
-// sorted unions over columns of A: out_k = U_{j in L_k} rows(A(:,j))
-spai_status column_union(spai_ctx ctx, Sym *s, const int32_t *Lptr, const int32_t *Lind,
-                         int32_t **out_ptr, int32_t **out_list, int32_t *total, int32_t *maxlen)
+// Pattern analyses of nsys matrices (Sec. 2.2: the column patterns J_k and the row sets
+// I_k = union of rows(A(:,j)), j in J_k), run phase by phase over all systems so that each
+// host read-back of sizes covers every system at once: at most five synchronisations
+// whatever nsys is.  kinds[i] is SPAI_PATTERN_A or SPAI_PATTERN_A2.
+spai_status sym_create_batch(spai_ctx ctx, int32_t nsys, const spai_csr *A, const int32_t *kinds, Sym **out)
 {
-    const int32_t n = s->n;
-    int32_t maxL = 0;
-    KL(launch_max_i32_diff(ctx->stream, n, Lptr, ctx->d_scalar), "max list length");
-    spai_status st = read_i32(ctx, ctx->d_scalar, &maxL);
-    if (st) return st;
-    if (maxL > colunion_max_lists())
-        return fail(ctx, SPAI_EINVAL, "a column pattern has %d entries; at most %d are supported", maxL,
-                    colunion_max_lists());
-    int32_t *counts = nullptr;
-    void *stemp = nullptr;
-    if ((st = dalloc_n(ctx, &counts, (int64_t)n + 1))) return st;
-    if ((st = dalloc(ctx, &stemp, scan_temp_bytes(n)))) { dfree(ctx, counts); return st; }
-    if ((st = dalloc_n(ctx, out_ptr, (int64_t)n + 1))) { dfree(ctx, counts); dfree(ctx, stemp); return st; }
-    KL(launch_colunion_count(ctx->stream, n, Lptr, Lind, s->a_colptr, s->a_rowind, counts, ctx->d_err), "union count");
-    KL(launch_exclusive_scan(ctx->stream, counts, *out_ptr, n, stemp, ctx->d_err), "scan");
-    int h = 0;
-    if ((st = read_err(ctx, &h))) return st;
-    if (h & ERR_OVERFLOW) return fail(ctx, SPAI_EINVAL, "index sets exceed 2^31 entries");
-    if ((st = read_i32(ctx, *out_ptr + n, total))) return st;
-    if ((st = dalloc_n(ctx, out_list, *total))) return st;
-    KL(launch_colunion_fill(ctx->stream, n, Lptr, Lind, s->a_colptr, s->a_rowind, *out_ptr, *out_list,
-                            ctx->d_err), "union fill");
-    KL(launch_max_i32_diff(ctx->stream, n, *out_ptr, ctx->d_scalar), "max set size");
-    if ((st = read_i32(ctx, ctx->d_scalar, maxlen))) return st;
-    dfree(ctx, counts);
-    dfree(ctx, stemp);
-    return SPAI_OK;
+    std::vector<Sym *> S((size_t)nsys, nullptr);
+    int32_t *d_vals = nullptr;  // [4][nsys]: max column length / max |J|, total |J|, total |I|, max |I|
+    void *temp = nullptr, *temp2 = nullptr;
+    spai_status st = SPAI_OK;
+    auto cleanup = [&](spai_status rc) {
+        dfree(ctx, d_vals);
+        dfree(ctx, temp);
+        dfree(ctx, temp2);
+        if (rc) {
+            for (Sym *s : S) sym_release(s);
+        }
+        return rc;
+    };
+#define TRY(x)                              \
+    do {                                    \
+        if ((st = (x)) != SPAI_OK) return cleanup(st); \
+    } while (0)
+#define TRYK(call, what)                                                                  \
+    do {                                                                                  \
+        if ((call) != 0) return cleanup(fail(ctx, SPAI_ECUDA, "%s: kernel launch failed (%s)", what, \
+                                             cudaGetErrorString(cudaGetLastError())));   \
+    } while (0)
+    std::vector<int32_t> h((size_t)4 * nsys, 0);
+    auto readback = [&](int field) -> spai_status {
+        CU(cudaMemcpyAsync(h.data() + (size_t)field * nsys, d_vals + (size_t)field * nsys, (size_t)nsys * 4,
+                           cudaMemcpyDeviceToHost, ctx->stream), "read back");
+        CU(cudaStreamSynchronize(ctx->stream), "stream sync");
+        return SPAI_OK;
+    };
+    TRY(dalloc_n(ctx, &d_vals, (int64_t)4 * nsys));
+    CU(cudaMemsetAsync(d_vals, 0, (size_t)16 * nsys, ctx->stream), "memset");
+    // scratch shared by the systems (stream order serialises its reuse)
+    size_t tbytes = 0, cbytes = 0;
+    for (int i = 0; i < nsys; ++i) {
+        tbytes = std::max(tbytes, transpose_temp_bytes(A[i].n, A[i].nnz));
+        cbytes = std::max(cbytes, ((size_t)A[i].n + 1) * 4 + 256 + scan_temp_bytes(A[i].n));
+    }
+    TRY(dalloc(ctx, &temp, std::max(tbytes, cbytes)));
+    int32_t *counts = (int32_t *)temp;
+    auto scan_temp = [&](int32_t n) { return (void *)((char *)temp + ((((size_t)n + 1) * 4 + 255) / 256 * 256)); };
+
+    // ---- phase A: copy A's pattern, transpose it (CSC + position map), longest column
+    for (int i = 0; i < nsys; ++i) {
+        Sym *s = new Sym();
+        S[i] = s;
+        s->ctx = ctx;
+        s->n = A[i].n;
+        s->nnzA = A[i].nnz;
+        s->kind = kinds[i];
+        const int32_t n = A[i].n, nnz = A[i].nnz;
+        TRY(dalloc_n(ctx, &s->a_rowptr, (int64_t)n + 1));
+        TRY(dalloc_n(ctx, &s->a_colind, nnz));
+        TRY(dalloc_n(ctx, &s->a_colptr, (int64_t)n + 1));
+        TRY(dalloc_n(ctx, &s->a_rowind, nnz));
+        TRY(dalloc_n(ctx, &s->a_perm, nnz));
+        CU(cudaMemcpyAsync(s->a_rowptr, A[i].rowptr, ((size_t)n + 1) * 4, cudaMemcpyDeviceToDevice, ctx->stream), "copy");
+        if (nnz)
+            CU(cudaMemcpyAsync(s->a_colind, A[i].colind, (size_t)nnz * 4, cudaMemcpyDeviceToDevice, ctx->stream), "copy");
+        TRYK(launch_transpose(ctx->stream, n, nnz, s->a_rowptr, s->a_colind, s->a_colptr, s->a_rowind, s->a_perm,
+                              temp, ctx->d_err), "transpose");
+        TRYK(launch_max_i32_diff(ctx->stream, n, s->a_colptr, d_vals + i), "longest column");
+        if (kinds[i] == SPAI_PATTERN_A) {
+            s->alias = true;
+            s->Jptr = s->a_colptr;
+            s->Jind = s->a_rowind;
+            s->nnzP = nnz;
+            s->p_rowptr = s->a_rowptr;
+            s->p_colind = s->a_colind;
+            s->p_map = s->a_perm;
+        } else {
+            s->alias = false;
+        }
+    }
+    TRY(readback(0));
+    bool any_a2 = false;
+    for (int i = 0; i < nsys; ++i) {
+        if (h[i] > colunion_max_lists())
+            return cleanup(fail(ctx, SPAI_EINVAL, "system %d: a column has %d entries; at most %d are supported", i,
+                                h[i], colunion_max_lists()));
+        if (kinds[i] == SPAI_PATTERN_A) S[i]->maxJ = h[i];
+        else any_a2 = true;
+    }
+    // ---- phase B (pattern of A^2): J_k = union over j in rows(A(:,k)) of rows(A(:,j))
+    if (any_a2) {
+        for (int i = 0; i < nsys; ++i) {
+            Sym *s = S[i];
+            if (s->alias) continue;
+            const int32_t n = s->n;
+            TRY(dalloc_n(ctx, &s->Jptr, (int64_t)n + 1));
+            TRYK(launch_colunion_count(ctx->stream, n, s->a_colptr, s->a_rowind, s->a_colptr, s->a_rowind, counts,
+                                       ctx->d_err), "pattern count");
+            TRYK(launch_exclusive_scan(ctx->stream, counts, s->Jptr, n, scan_temp(n), ctx->d_err), "scan");
+            CU(cudaMemcpyAsync(d_vals + nsys + i, s->Jptr + n, 4, cudaMemcpyDeviceToDevice, ctx->stream), "total");
+        }
+        TRY(readback(1));
+        size_t t2 = 0;
+        for (int i = 0; i < nsys; ++i)
+            if (!S[i]->alias) t2 = std::max(t2, transpose_temp_bytes(S[i]->n, h[nsys + i]));
+        TRY(dalloc(ctx, &temp2, t2));
+        for (int i = 0; i < nsys; ++i) {
+            Sym *s = S[i];
+            if (s->alias) continue;
+            const int32_t n = s->n;
+            s->nnzP = h[nsys + i];
+            int32_t *perm_rows = nullptr;
+            TRY(dalloc_n(ctx, &s->Jind, s->nnzP));
+            TRYK(launch_colunion_fill(ctx->stream, n, s->a_colptr, s->a_rowind, s->a_colptr, s->a_rowind, s->Jptr,
+                                      s->Jind, ctx->d_err), "pattern fill");
+            TRYK(launch_max_i32_diff(ctx->stream, n, s->Jptr, d_vals + i), "max |J|");
+            // row-wise pattern of P and the map from column positions to row positions
+            TRY(dalloc_n(ctx, &s->p_rowptr, (int64_t)n + 1));
+            TRY(dalloc_n(ctx, &s->p_colind, s->nnzP));
+            TRY(dalloc_n(ctx, &s->p_map, s->nnzP));
+            TRY(dalloc_n(ctx, &perm_rows, s->nnzP));
+            TRYK(launch_transpose(ctx->stream, n, s->nnzP, s->Jptr, s->Jind, s->p_rowptr, s->p_colind, perm_rows, temp2,
+                                  ctx->d_err), "transpose pattern");
+            TRYK(launch_invert_perm(ctx->stream, s->nnzP, perm_rows, s->p_map), "invert");
+            dfree(ctx, perm_rows);
+        }
+        TRY(readback(0));
+        for (int i = 0; i < nsys; ++i) {
+            if (S[i]->alias) continue;
+            S[i]->maxJ = h[i];
+            if (h[i] > colunion_max_lists())
+                return cleanup(fail(ctx, SPAI_EINVAL, "system %d: a column pattern has %d entries; at most %d are "
+                                    "supported", i, h[i], colunion_max_lists()));
+        }
+    }
+    // ---- phase C: I_k = union over j in J_k of rows(A(:,j))
+    for (int i = 0; i < nsys; ++i) {
+        Sym *s = S[i];
+        const int32_t n = s->n;
+        TRY(dalloc_n(ctx, &s->Iptr, (int64_t)n + 1));
+        TRYK(launch_colunion_count(ctx->stream, n, s->Jptr, s->Jind, s->a_colptr, s->a_rowind, counts, ctx->d_err),
+             "index set count");
+        TRYK(launch_exclusive_scan(ctx->stream, counts, s->Iptr, n, scan_temp(n), ctx->d_err), "scan");
+        CU(cudaMemcpyAsync(d_vals + 2 * nsys + i, s->Iptr + n, 4, cudaMemcpyDeviceToDevice, ctx->stream), "total");
+    }
+    CU(cudaMemcpyAsync(h.data() + 2 * nsys, d_vals + 2 * nsys, (size_t)nsys * 4, cudaMemcpyDeviceToHost, ctx->stream),
+       "read back");
+    int herr = 0;
+    TRY(read_err(ctx, &herr));  // synchronises
+    if (herr & ERR_OVERFLOW) return cleanup(fail(ctx, SPAI_EINVAL, "index sets exceed 2^31 entries"));
+    if (herr) return cleanup(fail(ctx, SPAI_EINVAL, "pattern analysis failed (device error 0x%x)", herr));
+    for (int i = 0; i < nsys; ++i) {
+        Sym *s = S[i];
+        s->nI = h[2 * nsys + i];
+        TRY(dalloc_n(ctx, &s->Ilist, s->nI));
+        TRYK(launch_colunion_fill(ctx->stream, s->n, s->Jptr, s->Jind, s->a_colptr, s->a_rowind, s->Iptr, s->Ilist,
+                                  ctx->d_err), "index set fill");
+        TRYK(launch_max_i32_diff(ctx->stream, s->n, s->Iptr, d_vals + 3 * nsys + i), "max |I|");
+    }
+    CU(cudaMemcpyAsync(h.data() + 3 * nsys, d_vals + 3 * nsys, (size_t)nsys * 4, cudaMemcpyDeviceToHost, ctx->stream),
+       "read back");
+    TRY(read_err(ctx, &herr));
+    if (herr) return cleanup(fail(ctx, SPAI_EINVAL, "pattern analysis failed (device error 0x%x)", herr));
+    for (int i = 0; i < nsys; ++i) {
+        Sym *s = S[i];
+        s->maxI = h[3 * nsys + i];
+        if (!spai_columns_fit(s->maxI, s->maxJ))
+            return cleanup(fail(ctx, SPAI_EINVAL, "system %d: column problem of %d x %d exceeds the shared-memory tile",
+                                i, s->maxI, s->maxJ));
+    }
+#undef TRY
+#undef TRYK
+    for (int i = 0; i < nsys; ++i) out[i] = S[i];
+    return cleanup(SPAI_OK);
 }
 
 spai_status sym_create(spai_ctx ctx, const spai_csr *A, int32_t kind, Sym **out)
 {
     *out = nullptr;
-    Sym *s = new Sym();
-    s->ctx = ctx;
-    s->n = A->n;
-    s->nnzA = A->nnz;
-    s->kind = kind;
-    const int32_t n = A->n, nnz = A->nnz;
-    spai_status st;
-    void *temp = nullptr;
-#define TRY(x)                 \
-    do {                       \
-        st = (x);              \
-        if (st) {              \
-            dfree(ctx, temp);  \
-            sym_release(s);    \
-            return st;         \
-        }                      \
-    } while (0)
-    TRY(dalloc_n(ctx, &s->a_rowptr, (int64_t)n + 1));
-    TRY(dalloc_n(ctx, &s->a_colind, nnz));
-    TRY(dalloc_n(ctx, &s->a_colptr, (int64_t)n + 1));
-    TRY(dalloc_n(ctx, &s->a_rowind, nnz));
-    TRY(dalloc_n(ctx, &s->a_perm, nnz));
-    CU(cudaMemcpyAsync(s->a_rowptr, A->rowptr, ((size_t)n + 1) * 4, cudaMemcpyDeviceToDevice, ctx->stream), "copy");
-    if (nnz) CU(cudaMemcpyAsync(s->a_colind, A->colind, (size_t)nnz * 4, cudaMemcpyDeviceToDevice, ctx->stream), "copy");
-    TRY(dalloc(ctx, &temp, transpose_temp_bytes(n, nnz)));
-    KL(launch_transpose(ctx->stream, n, nnz, s->a_rowptr, s->a_colind, s->a_colptr, s->a_rowind, s->a_perm,
-                        temp, ctx->d_err), "transpose");
-    if (kind == SPAI_PATTERN_A) {
-        s->alias = true;
-        s->Jptr = s->a_colptr;
-        s->Jind = s->a_rowind;
-        s->nnzP = nnz;
-        s->p_rowptr = s->a_rowptr;
-        s->p_colind = s->a_colind;
-        s->p_map = s->a_perm;
-        KL(launch_max_i32_diff(ctx->stream, n, s->Jptr, ctx->d_scalar), "max |J|");
-        TRY(read_i32(ctx, ctx->d_scalar, &s->maxJ));
-    } else {
-        s->alias = false;
-        // J_k = union over j in rows(A(:,k)) of rows(A(:,j)): the structural pattern of A^2
-        TRY(column_union(ctx, s, s->a_colptr, s->a_rowind, &s->Jptr, &s->Jind, &s->nnzP, &s->maxJ));
-        // row-wise pattern of P and the map from column positions to row positions
-        int32_t *perm_rows = nullptr;
-        TRY(dalloc_n(ctx, &s->p_rowptr, (int64_t)n + 1));
-        TRY(dalloc_n(ctx, &s->p_colind, s->nnzP));
-        TRY(dalloc_n(ctx, &s->p_map, s->nnzP));
-        TRY(dalloc_n(ctx, &perm_rows, s->nnzP));
-        dfree(ctx, temp);
-        temp = nullptr;
-        TRY(dalloc(ctx, &temp, transpose_temp_bytes(n, s->nnzP)));
-        KL(launch_transpose(ctx->stream, n, s->nnzP, s->Jptr, s->Jind, s->p_rowptr, s->p_colind, perm_rows,
-                            temp, ctx->d_err), "transpose pattern");
-        KL(launch_invert_perm(ctx->stream, s->nnzP, perm_rows, s->p_map), "invert");
-        dfree(ctx, perm_rows);
-    }
-    TRY(column_union(ctx, s, s->Jptr, s->Jind, &s->Iptr, &s->Ilist, &s->nI, &s->maxI));
-    int h = 0;
-    TRY(read_err(ctx, &h));
-    if (h) {
-        st = fail(ctx, SPAI_EINVAL, "pattern analysis failed (device error 0x%x)", h);
-        dfree(ctx, temp);
-        sym_release(s);
-        return st;
-    }
-    if (!spai_columns_fit(s->maxI, s->maxJ)) {
-        st = fail(ctx, SPAI_EINVAL, "column problem of %d x %d exceeds the shared-memory tile", s->maxI, s->maxJ);
-        dfree(ctx, temp);
-        sym_release(s);
-        return st;
-    }
-    dfree(ctx, temp);
-#undef TRY
-    *out = s;
-    return SPAI_OK;
+    return sym_create_batch(ctx, 1, A, &kind, out);
 }
 
 spai_status run_columns(spai_ctx ctx, spai_pc pc, int mode, const double *rhs_cval)
@@ -853,6 +925,196 @@ extern "C" spai_status spai_update(spai_ctx ctx, spai_pc base, const spai_csr *A
     st = run_columns(ctx, pc, 1, from->a_cval);
     if (st && st != SPAI_ESINGULAR) { spai_pc_destroy(pc); return st; }
     *out = pc;
+    return st;
+}
+
+// ===================================================================================
+// Batched build: many independent systems at once
+// ===================================================================================
+namespace {
+
+// Team size chosen per (working precision, tile rows, tile columns), process-wide: the first
+// batch that meets a shape times every fitting team size on its own columns and keeps the
+// fastest; later batches reuse it.  Team sizes change the rounding of the reductions only.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tune;
+
+spai_status run_columns_batch(spai_ctx ctx, int32_t nsys, spai_pc *pcs)
+{
+    // buckets of systems whose problems share a tile: (low precision, max |J|, max |I| rounded up to 8)
+    std::map<std::tuple<int, int, int>, std::vector<int>> buckets;
+    for (int i = 0; i < nsys; ++i) {
+        const Sym *s = pcs[i]->sym;
+        if (s->n == 0) continue;
+        buckets[std::make_tuple(pcs[i]->fval ? 0 : 1, s->maxJ, (s->maxI + 7) / 8 * 8)].push_back(i);
+    }
+    spai_status st = SPAI_OK;
+    for (auto &b : buckets) {
+        const int low = std::get<0>(b.first), maxJ = std::get<1>(b.first);
+        const std::vector<int> &mem = b.second;
+        const int m = (int)mem.size();
+        int maxI = 0;  // tile rows: the bucket's class (a multiple of 8) when it fits, else its largest |I_k|
+        std::vector<ColumnProblem> tab((size_t)m);
+        std::vector<int64_t> start((size_t)m + 1, 0);
+        double fl = 0.0, by = 0.0;
+        for (int t = 0; t < m; ++t) {
+            spai_pc pc = pcs[mem[t]];
+            const Sym *s = pc->sym;
+            maxI = std::max(maxI, s->maxI);
+            ColumnProblem &cp = tab[t];
+            cp = ColumnProblem{};
+            cp.n = s->n;
+            cp.colptr = s->a_colptr;
+            cp.rowind = s->a_rowind;
+            cp.cval = pc->a_cval;
+            cp.Jptr = s->Jptr;
+            cp.Jind = s->Jind;
+            cp.Iptr = s->Iptr;
+            cp.Ilist = s->Ilist;
+            cp.mode = 0;
+            cp.r_colptr = s->a_colptr;
+            cp.r_rowind = s->a_rowind;
+            cp.out_map = s->p_map;
+            cp.out_val = pc->fval;
+            cp.out_val32 = pc->fval32;
+            cp.out_val16 = pc->fval16;
+            cp.col_status = pc->status;
+            cp.d_err = ctx->d_err;
+            start[t + 1] = start[t] + s->n;
+            const double aI = (double)s->nI / s->n, aJ = (double)s->nnzP / s->n;
+            fl += (double)s->n * (2 * aJ * aJ * (aI - aJ / 3) + 4 * aI * aJ + aJ * aJ);
+            by += 12.0 * s->nnzA + 8.0 * (s->n + 1) + 4.0 * s->nI + 16.0 * s->nnzP;
+        }
+        ColumnProblem *d_tab = nullptr;
+        int64_t *d_start = nullptr;
+        if ((st = dalloc_n(ctx, &d_tab, m)) || (st = dalloc_n(ctx, &d_start, (int64_t)m + 1))) {
+            dfree(ctx, d_tab);
+            return st;
+        }
+        CU(cudaMemcpyAsync(d_tab, tab.data(), sizeof(ColumnProblem) * m, cudaMemcpyHostToDevice, ctx->stream), "table");
+        CU(cudaMemcpyAsync(d_start, start.data(), sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, ctx->stream),
+           "table");
+        const ColumnBatch bt{d_tab, d_start, m, start[m]};
+        if (spai_columns_fit(std::get<2>(b.first), maxJ)) maxI = std::get<2>(b.first);
+        const auto key = std::make_tuple(low, maxI, maxJ);
+        int team = 0;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune.find(key);
+            if (it != g_tune.end()) team = it->second;
+        }
+        if (!team) {
+            // first meeting of this shape: time every fitting team size on these columns
+            int cand[8];
+            const int nc = spai_columns_teams(maxI, maxJ, low != 0, cand);
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            CU(cudaEventCreate(&e0), "event");
+            CU(cudaEventCreate(&e1), "event");
+            float best_ms = 0.f;
+            int last = 0;
+            for (int c = 0; c < nc; ++c) {
+                cudaEventRecord(e0, ctx->stream);
+                if (launch_spai_columns_batch(ctx->stream, bt, low != 0, maxI, maxJ, cand[c])) {
+                    cudaGetLastError();
+                    continue;
+                }
+                cudaEventRecord(e1, ctx->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                last = cand[c];
+                if (!team || ms < best_ms) { team = cand[c]; best_ms = ms; }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (!team) {
+                dfree(ctx, d_tab);
+                dfree(ctx, d_start);
+                return fail(ctx, SPAI_EINVAL, "no team size fits column problems of %d x %d", maxI, maxJ);
+            }
+            {
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                g_tune.emplace(key, team);
+            }
+            if (last == team) {  // the result of the chosen size is already in place
+                dfree(ctx, d_tab);
+                dfree(ctx, d_start);
+                continue;
+            }
+        }
+        PKL("spai_columns", fl, by, launch_spai_columns_batch(ctx->stream, bt, low != 0, maxI, maxJ, team),
+            "batched column least squares");
+        dfree(ctx, d_tab);
+        dfree(ctx, d_start);
+    }
+    // first singular column of every system (INT_MAX if none), one read-back for all
+    int32_t *d_first = nullptr;
+    if ((st = dalloc_n(ctx, &d_first, nsys))) return st;
+    for (int i = 0; i < nsys; ++i)
+        if (pcs[i]->sym->n) KL(launch_first_nonzero(ctx->stream, pcs[i]->sym->n, pcs[i]->status, d_first + i), "status scan");
+    std::vector<int32_t> first((size_t)nsys);
+    CU(cudaMemcpyAsync(first.data(), d_first, (size_t)nsys * 4, cudaMemcpyDeviceToHost, ctx->stream), "read back");
+    int h = 0;
+    st = read_err(ctx, &h);
+    dfree(ctx, d_first);
+    if (st) return st;
+    if (h) return fail(ctx, SPAI_EINVAL, "batched column least squares failed (device error 0x%x)", h);
+    for (int i = 0; i < nsys; ++i)
+        if (pcs[i]->sym->n && first[i] != INT_MAX)
+            return fail(ctx, SPAI_ESINGULAR, "system %d, column %d: rank-deficient least-squares problem (column set "
+                        "to 0)", i, first[i]);
+    return SPAI_OK;
+}
+
+}  // namespace
+
+extern "C" spai_status spai_build_batch(spai_ctx ctx, int32_t nsys, const spai_csr *A, const int32_t *pattern_kind,
+                                        spai_pc *out)
+{
+    if (!ctx || !A || !pattern_kind || !out) return fail(ctx, SPAI_EINVAL, "NULL argument");
+    if (nsys < 1 || nsys > 65536) return fail(ctx, SPAI_EINVAL, "nsys must be in 1..65536");
+    for (int i = 0; i < nsys; ++i) out[i] = nullptr;
+    std::vector<int32_t> kinds((size_t)nsys), precs((size_t)nsys);
+    spai_status st;
+    for (int i = 0; i < nsys; ++i) {
+        precs[i] = prec_of(pattern_kind[i]);
+        if (precs[i] < 0) return fail(ctx, SPAI_EINVAL, "system %d: SPAI_PREC_FP32 and SPAI_PREC_BF16 are exclusive", i);
+        kinds[i] = pattern_kind[i] & ~(SPAI_PREC_FP32 | SPAI_PREC_BF16);
+        if (kinds[i] != SPAI_PATTERN_A && kinds[i] != SPAI_PATTERN_A2)
+            return fail(ctx, SPAI_EINVAL, "system %d: unknown pattern kind %d", i, kinds[i]);
+        if ((st = check_csr_args(ctx, &A[i], "A"))) return st;
+        if (A[i].n == 0) continue;
+        if (!is_device_ptr(A[i].rowptr) ||
+            (A[i].nnz > 0 && (!is_device_ptr(A[i].colind) || !is_device_ptr(A[i].val))))
+            return fail(ctx, SPAI_EINVAL, "system %d: arrays must be device memory", i);
+        KL(launch_validate_csr(ctx->stream, A[i].n, A[i].nnz, A[i].rowptr, A[i].colind, ctx->d_err), "validate");
+    }
+    int h = 0;
+    if ((st = read_err(ctx, &h))) return st;
+    if (h) return fail(ctx, SPAI_EINVAL, "a matrix of the batch is not a valid CSR matrix (device error 0x%x)", h);
+    std::vector<Sym *> syms((size_t)nsys, nullptr);
+    if ((st = sym_create_batch(ctx, nsys, A, kinds.data(), syms.data()))) return st;
+    std::vector<spai_pc> pcs((size_t)nsys, nullptr);
+    for (int i = 0; i < nsys; ++i) {
+        if ((st = pc_alloc(ctx, syms[i], precs[i], &pcs[i]))) {
+            for (int k = 0; k < nsys; ++k) {
+                if (pcs[k]) spai_pc_destroy(pcs[k]);  // releases its analysis too
+                else sym_release(syms[k]);
+            }
+            return st;
+        }
+        pcs[i]->root = pcs[i];
+        if (syms[i]->nnzA)
+            PKL("gather_csc", 0.0, 20.0 * syms[i]->nnzA,
+                launch_gather_f64(ctx->stream, syms[i]->nnzA, syms[i]->a_perm, A[i].val, pcs[i]->a_cval),
+                "gather values");
+    }
+    st = run_columns_batch(ctx, nsys, pcs.data());
+    if (st && st != SPAI_ESINGULAR) {
+        for (spai_pc pc : pcs) spai_pc_destroy(pc);
+        return st;
+    }
+    for (int i = 0; i < nsys; ++i) out[i] = pcs[i];
     return st;
 }
 

@@ -105,10 +105,24 @@ struct ColumnProblem {
     int32_t *col_status;             // 0 ok, 1 singular
     int *d_err;
 };
+// Column problems of several systems: column g (0 <= g < total) is local column
+// g - start[i] of system i, start[i] <= g < start[i + 1]; tab[i] is its problem (device).
+struct ColumnBatch {
+    const ColumnProblem *tab;
+    const int64_t *start;  // nsys + 1 entries, device
+    int32_t nsys;
+    int64_t total;
+};
 // true if one column problem of maxI x maxJ fits the kernel's shared-memory tile
 bool spai_columns_fit(int32_t maxI, int32_t maxJ);
 // Picks the team size by the largest |I_k|, |J_k|; returns 0 or -1 if no tile fits.
 int launch_spai_columns(cudaStream_t st, const ColumnProblem &cp, int32_t maxI, int32_t maxJ);
+// Team sizes that fit a maxI x maxJ problem (the default choice first); returns how many.
+int spai_columns_teams(int32_t maxI, int32_t maxJ, bool low_precision, int *teams);
+// All columns of a batch in one persistent launch with team size `team` (FP32 working
+// precision if low_precision); every problem must fit maxI x maxJ.
+int launch_spai_columns_batch(cudaStream_t st, const ColumnBatch &bt, bool low_precision, int32_t maxI,
+                              int32_t maxJ, int team);
 
 // ---------------------------------------------------------------------- k_krylov.cu
 struct KrylovWs;

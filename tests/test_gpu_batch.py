@@ -1,0 +1,120 @@
+"""Batched SPAI build (spai_build_batch): the column problems of many independent systems
+in one persistent launch per tile shape, with the team size picked by the autotuner.
+
+Bars: patterns, index sets and column status bit-exact against the oracle; entries within
+1e-10 of the largest oracle entry of their column (FP64), within the FP32 / BF16 bars of
+the mixed-precision tests otherwise; and against the single-system spai_build of the same
+matrix, which may use another team size, within 1e-13 (rounding of the reductions only).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import column_rel_err, context, dev_csr, export
+
+pytestmark = pytest.mark.gpu
+
+
+def _sg():
+    import paper_1809_06574_gb300 as sg
+    return sg
+
+
+def _systems():
+    """(name, A, n, kind, precision flag) of a heterogeneous batch."""
+    sg = _sg()
+    out = []
+    rng = np.random.default_rng(3)
+    for i, side in enumerate((8, 13, 21, 34, 40, 17)):
+        w = synth.grid_workload((side, side), "5pt", seed=i, nrhs=4, params=[0.5])
+        A = oracle.assemble(w.terms, oracle.coefficients(float(rng.uniform(0.1, 1.0)), 1.0), w.n)
+        kind = oracle.PATTERN_A if i % 2 == 0 else oracle.PATTERN_A2
+        out.append((f"2d-{side}-{'A' if kind == 0 else 'A2'}", A, w.n, kind, 0))
+    for seed in (0, 1):
+        A, _ = synth.random_sparse(90 + 17 * seed, 0.04, seed=seed)
+        out.append((f"random-{seed}", A, 90 + 17 * seed, oracle.PATTERN_A2 if seed else oracle.PATTERN_A, 0))
+    w = synth.grid3d_7pt(side=9, nparams=2)
+    out.append(("3d-9-7pt", oracle.assemble(w.terms, oracle.coefficients(0.4, 2.0), w.n), w.n, oracle.PATTERN_A, 0))
+    w = synth.grid3d_27pt(side=5, nparams=2)
+    out.append(("3d-5-27pt", oracle.assemble(w.terms, oracle.coefficients(0.4, 1.0), w.n), w.n, oracle.PATTERN_A, 0))
+    # the same shapes again in FP32 and BF16
+    out.append(("2d-21-A-fp32", out[2][1], out[2][2], oracle.PATTERN_A, sg.PREC_FP32))
+    out.append(("2d-34-A2-bf16", out[3][1], out[3][2], oracle.PATTERN_A2, sg.PREC_BF16))
+    return out
+
+
+def test_batch_matches_oracle_and_single_builds():
+    sg = _sg()
+    systems = _systems()
+    with context() as ctx:
+        Ads = [dev_csr(A, n) for _, A, n, _, _ in systems]
+        pcs, st = sg.spai_build_batch(ctx, Ads, [k | p for _, _, _, k, p in systems])
+        assert st == 0
+        got = [export(ctx, pc) for pc in pcs]
+        single = []
+        for (name, A, n, k, p), Ad in zip(systems, Ads):
+            pc, _ = sg.spai_build(ctx, Ad, k | p)
+            single.append(export(ctx, pc))
+            sg.spai_pc_destroy(pc)
+        # a second batch reuses the tuned team sizes: identical bits
+        pcs2, _ = sg.spai_build_batch(ctx, Ads, [k | p for _, _, _, k, p in systems])
+        again = [export(ctx, pc) for pc in pcs2]
+        for pc in pcs + pcs2:
+            sg.spai_pc_destroy(pc)
+    for (name, A, n, k, p), g, g1, g2 in zip(systems, got, single, again):
+        ref = oracle.spai_build(A, n, k)
+        for key in ("Jptr", "Jind", "Iptr", "Ilist", "status"):
+            assert np.array_equal(g[key], getattr(ref, key)), (name, key)
+            assert np.array_equal(g[key], g1[key]), (name, key)
+        assert np.array_equal(g["val"], g2["val"]), name
+        err = column_rel_err(ref.Jptr, g["val"], ref.val)
+        bar = {0: 1e-10, sg.PREC_FP32: 1e-4, sg.PREC_BF16: 2 * 2.0 ** -8 + 1e-4}[p]
+        print(f"batch {name}: column-relative error vs oracle {err:.2e}")
+        assert err <= bar, name
+        if p == 0:
+            assert column_rel_err(ref.Jptr, g["val"], g1["val"]) <= 1e-13, name
+
+
+def test_batch_handles_update_and_solve():
+    import torch
+    sg = _sg()
+    ws = [synth.grid_workload((s, s), "5pt", seed=10 + s, nrhs=4, params=[0.2, 0.3]) for s in (20, 31, 26)]
+    kinds = [oracle.PATTERN_A, oracle.PATTERN_A2, oracle.PATTERN_A]
+    with context() as ctx:
+        A1 = [oracle.assemble(w.terms, oracle.coefficients(w.params[0], 1.0), w.n) for w in ws]
+        A2 = [oracle.assemble(w.terms, oracle.coefficients(w.params[1], 1.0), w.n) for w in ws]
+        d1 = [dev_csr(A, w.n) for A, w in zip(A1, ws)]
+        d2 = [dev_csr(A, w.n) for A, w in zip(A2, ws)]
+        pcs, _ = sg.spai_build_batch(ctx, d1, kinds)
+        for w, a1, a2, dd2, pc, k in zip(ws, A1, A2, d2, pcs, kinds):
+            q, _ = sg.spai_update(ctx, pc, dd2)
+            Bd = torch.as_tensor(np.ascontiguousarray(w.B.T), device="cuda:0")
+            Xd = torch.zeros((4, w.n), dtype=torch.float64, device="cuda:0")
+            st, info, rel = sg.block_solve(ctx, dd2, q, 4, Bd, w.n, Xd, w.n, 30, 1e-8, 50)
+            X = Xd.cpu().numpy().T
+            sg.spai_pc_destroy(q)
+            sg.spai_pc_destroy(pc)
+            Q = oracle.spai_update(oracle.spai_build(a1, w.n, k), a2, w.n)
+            Xo, io = oracle.block_gmres(oracle.csr_apply(a2, w.n), Q.apply, w.B, 30, 1e-8, 50)
+            assert info["converged"] and io["converged"]
+            assert np.linalg.norm(X - Xo) <= 1e-6 * np.linalg.norm(Xo)
+
+
+def test_batch_reports_singular_system():
+    sg = _sg()
+    w = synth.grid_workload((10, 10), "5pt", seed=1, nrhs=4, params=[0.5])
+    A = oracle.assemble(w.terms, oracle.coefficients(0.5, 1.0), w.n)
+    # a matrix with an empty column 7 (its values zeroed, pattern kept)
+    rp, ci, va = A
+    Z = (rp, ci, np.where(ci == 7, 0.0, va))
+    with context() as ctx:
+        pcs, st = sg.spai_build_batch(ctx, [dev_csr(A, w.n), dev_csr(Z, w.n)], [0, 0], allow_singular=True)
+        assert st == sg.SPAI_ESINGULAR and "system 1" in sg.spai_last_error(ctx)
+        g0, g1 = export(ctx, pcs[0]), export(ctx, pcs[1])
+        for pc in pcs:
+            sg.spai_pc_destroy(pc)
+    ref = oracle.spai_build(Z, w.n)
+    assert not g0["status"].any()
+    assert np.array_equal(g1["status"], ref.status) and g1["status"][7] == 1
