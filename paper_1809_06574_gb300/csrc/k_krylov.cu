@@ -233,12 +233,13 @@ __global__ void k_chol_small(const double *__restrict__ G, const double *__restr
         for (int i = 0; i < S; ++i) R[i * S + lane] = Rs[i][lane];
 }
 
-// out[r] = W[r] R^{-1} (R upper triangular, deflated columns -> 0); thread per row
+// out[r] = W[r] R^{-1} (R upper triangular, deflated columns -> 0); thread per row; out
+// may be W (each thread reads its row before writing it)
 template <int S>
-__global__ void __launch_bounds__(kThreads) k_trsm_rows(int32_t n, const double *__restrict__ W,
+__global__ void __launch_bounds__(kThreads) k_trsm_rows(int32_t n, const double *W,
                                                         const double *__restrict__ R,
                                                         const int32_t *__restrict__ deflated,
-                                                        double *__restrict__ out)
+                                                        double *out)
 {
     __shared__ double Rs[S * S];
     __shared__ double rinv[S];  // 1 / R_bb, 0 for deflated columns
@@ -249,15 +250,91 @@ __global__ void __launch_bounds__(kThreads) k_trsm_rows(int32_t n, const double 
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n) return;
     double x[S];
+    row_load<S>(W, r, x);
+    trsm_row<S>(x, Rs, rinv);
+    row_store<S>(out, r, x);
+}
+
+// ---------------------------------------------------------------------------------
+// Cholesky-QR kernels for S <= 8.  A block of 256 threads walks its row chunk (one tile
+// where n allows) in tiles of 256 rows: each thread loads one row with 16-byte loads (k_trsm_gram also solves it
+// against R and stores it as Q1) into a shared-memory tile; then thread (pair p = (a, b),
+// a <= b; row group g) adds x_a x_b over rows g, g + RG, ... of the tile.  The FP64
+// reduction at the end is one sum over the RG groups per pair (FP64 adds are as dear as
+// FMAs on this GPU, so no per-thread butterflies).
+//   k_gram_rows:  partial[chunk] of G = W^T W
+//   k_trsm_gram:  Q1 = W R^{-1} written, and partial[chunk] of G2 = Q1^T Q1, one pass
+// ---------------------------------------------------------------------------------
+template <int S, bool SOLVE>
+__device__ __forceinline__ void gram_tiles(int32_t n, const double *__restrict__ W, const double *Rs,
+                                           const double *rinv, double *__restrict__ Q1,
+                                           double *__restrict__ partial)
+{
+    constexpr int NP = S * (S + 1) / 2;
+    constexpr int RG = kThreads / NP;
+    constexpr int LD = S + 1;  // padded tile row
+    __shared__ double tile[kThreads * LD];
+    __shared__ double red[kThreads];
+    const int p = threadIdx.x % NP, g = threadIdx.x / NP;
+    int a = 0, rem = p;
+    while (rem >= S - a) { rem -= S - a; ++a; }
+    const int b = a + rem;
+    int64_t r0, r1;
+    chunk_rows(n, blockIdx.x, gridDim.x, r0, r1);
+    double acc0 = 0.0, acc1 = 0.0;
+    for (int64_t t0 = r0; t0 < r1; t0 += kThreads) {
+        const int rows = (int)((r1 - t0) < kThreads ? (r1 - t0) : kThreads);
+        if (threadIdx.x < rows) {
+            double x[S];
+            row_load<S>(W, t0 + threadIdx.x, x);
+            if constexpr (SOLVE) {
+                trsm_row<S>(x, Rs, rinv);
+                row_store<S>(Q1, t0 + threadIdx.x, x);
+            }
 #pragma unroll
-    for (int b = 0; b < S; ++b) {
-        double acc = W[r * S + b];
-#pragma unroll
-        for (int a = 0; a < b; ++a) acc = fma(-x[a], Rs[a * S + b], acc);
-        x[b] = acc * rinv[b];
+            for (int k = 0; k < S; ++k) tile[threadIdx.x * LD + k] = x[k];
+        }
+        __syncthreads();
+        if (g < RG) {
+            int r = g;
+            for (; r + RG < rows; r += 2 * RG) {
+                acc0 = fma(tile[r * LD + a], tile[r * LD + b], acc0);
+                acc1 = fma(tile[(r + RG) * LD + a], tile[(r + RG) * LD + b], acc1);
+            }
+            if (r < rows) acc0 = fma(tile[r * LD + a], tile[r * LD + b], acc0);
+        }
+        __syncthreads();
     }
-#pragma unroll
-    for (int b = 0; b < S; ++b) out[r * S + b] = x[b];
+    red[threadIdx.x] = acc0 + acc1;
+    __syncthreads();
+    if (g == 0) {
+        double acc = red[p];
+        for (int h = 1; h < RG; ++h) acc += red[h * NP + p];
+        partial[(int64_t)blockIdx.x * S * S + a * S + b] = acc;
+        partial[(int64_t)blockIdx.x * S * S + b * S + a] = acc;
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_gram_rows(int32_t n, const double *__restrict__ W,
+                                                        double *__restrict__ partial)
+{
+    gram_tiles<S, false>(n, W, nullptr, nullptr, nullptr, partial);
+}
+
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_trsm_gram(int32_t n, const double *__restrict__ W,
+                                                        const double *__restrict__ R,
+                                                        const int32_t *__restrict__ deflated,
+                                                        double *__restrict__ Q1, double *__restrict__ partial)
+{
+    __shared__ double Rs[S * S];
+    __shared__ double rinv[S];
+    for (int e = threadIdx.x; e < S * S; e += blockDim.x) Rs[e] = R[e];
+    if (threadIdx.x < S)
+        rinv[threadIdx.x] = deflated[threadIdx.x] ? 0.0 : 1.0 / R[threadIdx.x * S + threadIdx.x];
+    __syncthreads();
+    gram_tiles<S, true>(n, W, Rs, rinv, Q1, partial);
 }
 
 template <int S>
@@ -563,6 +640,46 @@ int launch_gram_sym(cudaStream_t st, int32_t s, int32_t n, const double *W, doub
     SPAI_DISPATCH_S(s, (k_gram_sym<S><<<chunks, kThreads, 0, st>>>(n, W, partial)));
     const int count = s * s;
     k_reduce_chunks<<<(unsigned)(((int64_t)count * 32 + 255) / 256), 256, 0, st>>>(count, chunks, partial, out);
+    return check_launch(2);
+}
+
+bool gram_rows_supported(int32_t s) { return s == 1 || s == 2 || s == 4 || s == 8; }
+
+// row chunks of the tiled Gram kernels: one 256-row tile per block where n allows, so that
+// several blocks per SM hide each other's load latency (<= 1216, the partial buffer's size)
+int gram_rows_chunks(int32_t n)
+{
+    int64_t c = ((int64_t)n + 255) / 256;
+    if (c > 1216) c = 1216;
+    if (c < 1) c = 1;
+    return (int)c;
+}
+
+#define SPAI_DISPATCH_S8(s, CALL)         \
+    switch (s) {                          \
+    case 1: { constexpr int S = 1; CALL; } break;   \
+    case 2: { constexpr int S = 2; CALL; } break;   \
+    case 4: { constexpr int S = 4; CALL; } break;   \
+    case 8: { constexpr int S = 8; CALL; } break;   \
+    default: return -1;                   \
+    }
+
+int launch_gram_rows(cudaStream_t st, int32_t s, int32_t n, const double *W, double *partial, double *out)
+{
+    const int chunks = gram_rows_chunks(n);
+    SPAI_DISPATCH_S8(s, (k_gram_rows<S><<<chunks, kThreads, 0, st>>>(n, W, partial)));
+    const int count = s * s;
+    k_reduce_chunks<<<(unsigned)(((int64_t)count * 32 + 255) / 256), 256, 0, st>>>(count, chunks, partial, out);
+    return check_launch(2);
+}
+
+int launch_trsm_gram(cudaStream_t st, int32_t s, int32_t n, const double *W, const double *R,
+                     const int32_t *deflated, double *Q1, double *partial, double *G2)
+{
+    const int chunks = gram_rows_chunks(n);
+    SPAI_DISPATCH_S8(s, (k_trsm_gram<S><<<chunks, kThreads, 0, st>>>(n, W, R, deflated, Q1, partial)));
+    const int count = s * s;
+    k_reduce_chunks<<<(unsigned)(((int64_t)count * 32 + 255) / 256), 256, 0, st>>>(count, chunks, partial, G2);
     return check_launch(2);
 }
 

@@ -368,6 +368,43 @@ __global__ void k_to_fixed(int32_t n, int32_t nblocks, const double *__restrict_
     if (bad) atomicOr(err, ERR_RANGE);
 }
 
+// Last step of Cholesky-QR for an 8-column basis block: Q := Q R^{-1} in place (the row
+// solve every orthogonalisation kernel shares; deflated columns -> 0), and the block's
+// fixed point written as k_to_fixed writes it (row layout; sub-tile layout at slot blk,
+// padding rows of the last sub-tile zero), saving a pass over the new block.
+__global__ void __launch_bounds__(256) k_trsm_fixed(int32_t n, double *__restrict__ Q, const double *__restrict__ R,
+                                                    const int32_t *__restrict__ deflated, uint64_t *__restrict__ F_row,
+                                                    uint64_t *__restrict__ F_sub, int32_t ipad, int32_t blk, int *err)
+{
+    __shared__ double Rs[kS * kS];
+    __shared__ double rinv[kS];
+    for (int e = threadIdx.x; e < kS * kS; e += blockDim.x) Rs[e] = R[e];
+    if (threadIdx.x < kS) rinv[threadIdx.x] = deflated[threadIdx.x] ? 0.0 : 1.0 / R[threadIdx.x * kS + threadIdx.x];
+    __syncthreads();
+    const int64_t nt = ((int64_t)n + kKT - 1) / kKT * kKT;
+    bool bad = false;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nt; r += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t f[kS];
+#pragma unroll
+        for (int a = 0; a < kS; ++a) f[a] = 0;
+        if (r < n) {
+            double x[kS];
+            row_load<kS>(Q, r, x);
+            trsm_row<kS>(x, Rs, rinv);
+            row_store<kS>(Q, r, x);
+#pragma unroll
+            for (int a = 0; a < kS; ++a)
+                if (!to_fixed(x[a], 0, f[a])) bad = true;
+            ulonglong2 *fr = reinterpret_cast<ulonglong2 *>(F_row + r * kS);
+#pragma unroll
+            for (int k = 0; k < kS / 2; ++k) fr[k] = make_ulonglong2(f[2 * k], f[2 * k + 1]);
+        }
+        ulonglong2 *fs = reinterpret_cast<ulonglong2 *>(F_sub + (((r / kKT) * ipad + blk) * kKT + (r % kKT)) * kS);
+#pragma unroll
+        for (int k = 0; k < kS / 2; ++k) fs[k] = make_ulonglong2(f[2 * k], f[2 * k + 1]);
+    }
+    if (bad) atomicOr(err, ERR_RANGE);
+}
 
 // Gram product H_i = V_i^T W.  grid = (row chunks, M tiles of 16 blocks); a chunk is a
 // whole number of 16-row sub-tiles, at most 4096 rows.  A stage carries S sub-tiles (S
@@ -949,6 +986,18 @@ int launch_to_fixed(cudaStream_t st, int32_t n, int32_t nblocks, const double *X
     int64_t g = (count + 255) / 256;
     if (g > 4 * 152) g = 4 * 152;
     k_to_fixed<<<(unsigned)g, 256, 0, st>>>(n, nblocks, X, F_row, F_sub, ipad, iblk0, d_err);
+    note_launches(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_trsm_fixed(cudaStream_t st, int32_t n, double *Q, const double *R, const int32_t *deflated, uint64_t *F_row,
+                      uint64_t *F_sub, int32_t ipad, int32_t blk, int *d_err)
+{
+    if (n <= 0) return 0;
+    const int64_t rows = ((int64_t)n + kKT - 1) / kKT * kKT;
+    int64_t g = (rows + 255) / 256;
+    if (g > 8 * 152) g = 8 * 152;
+    k_trsm_fixed<<<(unsigned)g, 256, 0, st>>>(n, Q, R, deflated, F_row, F_sub, ipad, blk, d_err);
     note_launches(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

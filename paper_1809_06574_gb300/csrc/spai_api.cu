@@ -1303,18 +1303,44 @@ size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks
     return off;
 }
 
-// W = Q R with Q orthonormal (deflated columns zero), two passes of Cholesky QR
-spai_status cholqr2(spai_ctx ctx, SolveWs &w, int32_t n, int32_t s, int chunks, const double *Win, double *Qout,
-                    double *Rout, const double *ref2)
+// W = Q R with Q orthonormal (deflated columns zero), two passes of Cholesky QR:
+//   G1 = W^T W, R1 = chol(G1); Q1 = W R1^{-1}; G2 = Q1^T Q1, R2 = chol(G2); Q = Q1 R2^{-1};
+//   R = R2 R1.
+// For s <= 8 the rows stay in registers: Q1 and G2 come from one pass over W, and with
+// fix_blk >= 0 (s == 8) the last pass also writes Q's fixed-point copies (basis slot fix_blk
+// of ipad) for the tensor-core products.
+spai_status cholqr2(spai_ctx ctx, SolveWs &w, int32_t n, int32_t s, const double *Win, double *Qout, double *Rout,
+                    const double *ref2, int fix_blk, int32_t ipad)
 {
     cudaStream_t st = ctx->stream;
     const double nsd = (double)n * s;
-    PKL("gram", nsd * (s + 1), 8.0 * nsd, launch_gram_sym(st, s, n, Win, w.partial, w.G1), "gram");
-    PKL("small_dense", 0.0, 0.0, launch_chol_small(st, s, w.G1, ref2, 1e-24, w.R1, w.defl1), "chol");
-    PKL("trsm_rows", nsd * s, 16.0 * nsd, launch_trsm_rows(st, s, n, Win, w.R1, w.defl1, Qout), "trsm");
-    PKL("gram", nsd * (s + 1), 8.0 * nsd, launch_gram_sym(st, s, n, Qout, w.partial, w.G1), "gram");
-    PKL("small_dense", 0.0, 0.0, launch_chol_small(st, s, w.G1, nullptr, 0.0, w.R2, w.defl2), "chol");
-    PKL("trsm_rows", nsd * s, 16.0 * nsd, launch_trsm_rows(st, s, n, Qout, w.R2, w.defl2, Qout), "trsm");
+    if (gram_rows_supported(s)) {
+        PKL("gram", nsd * (s + 1), 8.0 * nsd, launch_gram_rows(st, s, n, Win, w.partial, w.G1), "gram");
+        PKL("small_dense", 0.0, 0.0, launch_chol_small(st, s, w.G1, ref2, 1e-24, w.R1, w.defl1), "chol");
+        PKL("trsm_gram", nsd * s + nsd * (s + 1), 16.0 * nsd,
+            launch_trsm_gram(st, s, n, Win, w.R1, w.defl1, Qout, w.partial, w.G1), "trsm gram");
+        PKL("small_dense", 0.0, 0.0, launch_chol_small(st, s, w.G1, nullptr, 0.0, w.R2, w.defl2), "chol");
+        if (fix_blk >= 0) {
+            PKL("trsm_fixed", nsd * s, 32.0 * nsd,
+                launch_trsm_fixed(st, n, Qout, w.R2, w.defl2, w.vfix + (size_t)fix_blk * n * s, w.vfix_sub, ipad,
+                                  fix_blk, ctx->d_err),
+                "trsm fixed point");
+        } else {
+            PKL("trsm_rows", nsd * s, 16.0 * nsd, launch_trsm_rows(st, s, n, Qout, w.R2, w.defl2, Qout), "trsm");
+        }
+    } else {
+        PKL("gram", nsd * (s + 1), 8.0 * nsd, launch_gram_sym(st, s, n, Win, w.partial, w.G1), "gram");
+        PKL("small_dense", 0.0, 0.0, launch_chol_small(st, s, w.G1, ref2, 1e-24, w.R1, w.defl1), "chol");
+        PKL("trsm_rows", nsd * s, 16.0 * nsd, launch_trsm_rows(st, s, n, Win, w.R1, w.defl1, Qout), "trsm");
+        PKL("gram", nsd * (s + 1), 8.0 * nsd, launch_gram_sym(st, s, n, Qout, w.partial, w.G1), "gram");
+        PKL("small_dense", 0.0, 0.0, launch_chol_small(st, s, w.G1, nullptr, 0.0, w.R2, w.defl2), "chol");
+        PKL("trsm_rows", nsd * s, 16.0 * nsd, launch_trsm_rows(st, s, n, Qout, w.R2, w.defl2, Qout), "trsm");
+        if (fix_blk >= 0)
+            PKL("to_fixed", 0.0, 24.0 * nsd,
+                launch_to_fixed(st, n, 1, Qout, w.vfix + (size_t)fix_blk * n * s, w.vfix_sub, ipad, fix_blk,
+                                ctx->d_err),
+                "fixed point");
+    }
     PKL("small_dense", 0.0, 0.0, launch_triu_mul(st, s, w.R2, w.R1, Rout), "triu");
     return SPAI_OK;
 }
@@ -1371,15 +1397,6 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
     if (opts->orth < SPAI_ORTH_AUTO || opts->orth > SPAI_ORTH_TENSOR)
         return fail(ctx, SPAI_EINVAL, "unknown orthogonalisation method %d", opts->orth);
     const bool use_digits = block_dot_tc_supported(s) && opts->orth != SPAI_ORTH_FP64;
-    // fixed-point copy of basis block blk for the tensor-core products
-    auto make_fixed = [&](int blk) -> spai_status {
-        if (!use_digits) return SPAI_OK;
-        PKL("to_fixed", 0.0, 24.0 * n * s,
-            launch_to_fixed(cs, n, 1, w.V + (size_t)blk * n * s, w.vfix + (size_t)blk * n * s, w.vfix_sub, m + 1, blk,
-                            ctx->d_err),
-            "fixed point");
-        return SPAI_OK;
-    };
     // out = base + sign * V_{0..nb-1} H: tensor-core digits when available, else FP64
     auto vupdate = [&](int nb, const double *H, const double *basep, double *out, double sign) -> spai_status {
         const double f = 2.0 * n * s * s * nb;
@@ -1439,8 +1456,7 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
     while (!converged() && cycles < opts->max_cycles) {
         ++cycles;
         // V_0 S_0 = R (ref2 holds the residual norms^2)
-        if ((st = cholqr2(ctx, w, n, s, chunks, w.W, w.V, w.Rn, w.ref2))) return st;
-        if ((st = make_fixed(0))) return st;
+        if ((st = cholqr2(ctx, w, n, s, w.W, w.V, w.Rn, w.ref2, use_digits ? 0 : -1, m + 1))) return st;
         PKL("small_dense", 0.0, 0.0, launch_set_rhs(cs, s, m, w.Rn, w.G), "rhs");
         int J = 0;
         for (int j = 0; j < m; ++j) {
@@ -1473,8 +1489,9 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
             }
             if ((st = vupdate(j + 1, w.H2, w.W, w.W, -1.0))) return st;
             double *Vn = w.V + (size_t)(j + 1) * blk_elems;
-            if ((st = cholqr2(ctx, w, n, s, chunks, w.W, Vn, w.Rn, w.ref2))) return st;
-            if (j + 1 < m && (st = make_fixed(j + 1))) return st;
+            // the new block's fixed point (for the products of the next steps) comes with it
+            if ((st = cholqr2(ctx, w, n, s, w.W, Vn, w.Rn, w.ref2, (use_digits && j + 1 < m) ? j + 1 : -1, m + 1)))
+                return st;
             PKL("arnoldi_ls", 16.0 * s * s * s * (j + 1), 0.0,
                 launch_arnoldi_ls(cs, s, j, m, w.H1, w.H2, w.Rn, w.Qs, w.Rtri, w.G, w.thresh, w.est, w.flag), "least squares");
             CU(cudaMemcpyAsync(h + 32, w.est, s * 8, cudaMemcpyDeviceToHost, cs), "read estimates");

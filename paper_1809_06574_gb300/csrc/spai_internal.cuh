@@ -124,6 +124,56 @@ int spai_columns_teams(int32_t maxI, int32_t maxJ, bool low_precision, int *team
 int launch_spai_columns_batch(cudaStream_t st, const ColumnBatch &bt, bool low_precision, int32_t maxI,
                               int32_t maxJ, int team);
 
+// ---------------------------------------------------------------------- shared device code
+#ifdef __CUDACC__
+// x := x R^{-1} for one row (R upper triangular S x S, row-major; rinv[b] = 1 / R_bb, or 0
+// for a deflated column).  Every row-wise triangular solve of the block orthogonalisation
+// uses this one sequence, so a row solved in different kernels gets the same bits.
+template <int S>
+__device__ __forceinline__ void trsm_row(double (&x)[S], const double *Rs, const double *rinv)
+{
+#pragma unroll
+    for (int b = 0; b < S; ++b) {
+        double acc = x[b];
+#pragma unroll
+        for (int a = 0; a < b; ++a) acc = fma(-x[a], Rs[a * S + b], acc);
+        x[b] = acc * rinv[b];
+    }
+}
+
+// one row of an n x S row-major block, 16-byte loads / stores when S is even (plain
+// loads: the in-place kernels read a row and then overwrite it)
+template <int S>
+__device__ __forceinline__ void row_load(const double *W, int64_t r, double (&x)[S])
+{
+    if constexpr (S % 2 == 0) {
+        const double2 *p = reinterpret_cast<const double2 *>(W + r * S);
+#pragma unroll
+        for (int k = 0; k < S / 2; ++k) {
+            const double2 v = p[k];
+            x[2 * k] = v.x;
+            x[2 * k + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < S; ++k) x[k] = W[r * S + k];
+    }
+}
+
+template <int S>
+__device__ __forceinline__ void row_store(double *W, int64_t r, const double (&x)[S])
+{
+    if constexpr (S % 2 == 0) {
+        double2 *p = reinterpret_cast<double2 *>(W + r * S);
+#pragma unroll
+        for (int k = 0; k < S / 2; ++k) p[k] = make_double2(x[2 * k], x[2 * k + 1]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < S; ++k) W[r * S + k] = x[k];
+    }
+}
+#endif
+
 // ---------------------------------------------------------------------- k_krylov.cu
 struct KrylovWs;
 int krylov_chunks(int32_t n);
@@ -139,6 +189,12 @@ int launch_chol_small(cudaStream_t st, int32_t s, const double *G, const double 
                       double tau2, double *R, int32_t *deflated);
 int launch_trsm_rows(cudaStream_t st, int32_t s, int32_t n, const double *W, const double *R,
                      const int32_t *deflated, double *out);
+// Cholesky-QR pieces with rows held in registers (s <= 8): G = W^T W; and Q1 = W R^{-1}
+// written to Q1 together with G2 = Q1^T Q1.  partial needs 1216 * s * s doubles.
+bool gram_rows_supported(int32_t s);
+int launch_gram_rows(cudaStream_t st, int32_t s, int32_t n, const double *W, double *partial, double *out);
+int launch_trsm_gram(cudaStream_t st, int32_t s, int32_t n, const double *W, const double *R,
+                     const int32_t *deflated, double *Q1, double *partial, double *G2);
 int launch_triu_mul(cudaStream_t st, int32_t s, const double *R2, const double *R1, double *out);
 // projected least squares of block column j (Hessenberg column = H1 + H2 over Rsub)
 int launch_arnoldi_ls(cudaStream_t st, int32_t s, int32_t j, int32_t m, const double *H1, const double *H2,
@@ -177,6 +233,10 @@ int block_update_tc_max_blocks();
 size_t tc_hdig_bytes(int32_t nblk);
 int launch_block_update_tc(cudaStream_t st, int32_t n, int32_t nblk, const uint64_t *Vf, const double *H, void *hdig,
                            int32_t *hexp, const double *base, double *out, double sign, int *d_err);
+// Q := Q R^{-1} in place (s == 8, deflated columns -> 0) and the new basis block's fixed
+// point: row layout at F_row (n x 8), sub-tile layout at slot blk of ipad slots of F_sub
+int launch_trsm_fixed(cudaStream_t st, int32_t n, double *Q, const double *R, const int32_t *deflated, uint64_t *F_row,
+                      uint64_t *F_sub, int32_t ipad, int32_t blk, int *d_err);
 // FP64 FMA throughput probe: blocks x threads x 8 chains x iters FMAs
 int launch_fp64_probe(cudaStream_t st, int blocks, int threads, int iters, double *sink);
 
