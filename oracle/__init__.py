@@ -14,7 +14,8 @@ What it computes, with the passage of arXiv 1809.06574 it writes out:
   and row sets I_k of the column least-squares problems of Sec. 2.2.
 * ``spai_build`` -- min_P ||I - A P||_F, column by column (Sec. 2.2), by Householder QR.
 * ``spai_update`` -- min_Q ||A(1) - A(l) Q||_F (Table 1 first approach, Sec. 2.4),
-  P_l = Q_l P_1 kept factored; ``spai_update_chained`` is Table 1's second approach.
+  P_l = Q_l P_1 kept factored; ``spai_update_chained`` is Table 1's second approach;
+  ``spai_update_diagonal`` takes Q_l diagonal (the same least squares on J_k = {k}).
 * ``block_gmres`` -- the right-preconditioned (Sec. 2.2 footnote) block Krylov solve
   of Sec. 2.1: block GMRES(m) over span{R0, AP R0, (AP)^2 R0, ...}.
 * ``lu_solve`` -- dense LU with partial pivoting for tiny reference solves.
@@ -260,6 +261,22 @@ def spai_update_chained(prev: Precond, A_new, n):
     A_csc = csr_to_csc(A_new, n)
     val, status = _columns(A_csc, n, prev.Jptr, prev.Jind, prev.Iptr, prev.Ilist, 1, prev.A_csc)
     return Precond(n, prev.Jptr, prev.Jind, prev.Iptr, prev.Ilist, val, status, prev, A_csc)
+
+
+def spai_update_diagonal(base: Precond, A_new, n):
+    """Update with a diagonal Q_l (Table 1 first approach; Q_l's pattern is not stated in
+    Sec. 2.4, this is the diagonal reading): column k of Q_l is argmin over supp in {k} of
+    ||a1_k - A(l) q||_2, the same column least squares as ``spai_update`` on the pattern
+    J_k = {k}, whose rows are I_k = rows(A(l)(:,k)).  P_l = Q_l P_1, applied factored."""
+    root = base
+    while root.base is not None:
+        root = root.base
+    Jptr = np.arange(n + 1, dtype=np.int32)
+    Jind = np.arange(n, dtype=np.int32)
+    Iptr, Ilist = index_sets(A_new, n, Jptr, Jind)
+    A_csc = csr_to_csc(A_new, n)
+    val, status = _columns(A_csc, n, Jptr, Jind, Iptr, Ilist, 1, root.A_csc)
+    return Precond(n, Jptr, Jind, Iptr, Ilist, val, status, root, A_csc)
 
 
 def spmm(A, X, n):

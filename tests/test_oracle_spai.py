@@ -226,3 +226,31 @@ def test_build_with_precomputed_sets_and_column_range():
     sl = slice(Jptr[10], Jptr[25])
     assert np.array_equal(part.val[sl], full.val[sl])
     assert not part.val[:Jptr[10]].any() and not part.val[Jptr[25]:].any()
+
+
+def test_diagonal_update_closed_form_and_invariants():
+    """Diagonal Q_l: the least squares over one unknown has the closed form
+    q_kk = <A(l)(:,k), a1_k> / ||A(l)(:,k)||^2 (brute force on dense columns here); an
+    unchanged matrix gives Q = I, A(l) = c A(1) gives Q = I / c, and for a diagonal A the
+    diagonal update equals the full-pattern update."""
+    A1, D1 = synth.random_sparse(40, 0.1, seed=6)
+    rng = np.random.default_rng(7)
+    D2 = D1 + np.where(D1 != 0, 0.05 * rng.standard_normal(D1.shape), 0.0)
+    n = 40
+    A2 = _csr(D2, D1 != 0)
+    P1 = oracle.spai_build(A1, n)
+    Q = oracle.spai_update_diagonal(P1, A2, n)
+    want = np.einsum("ik,ik->k", D2, D1) / np.einsum("ik,ik->k", D2, D2)
+    assert np.allclose(Q.val, want, rtol=1e-14, atol=0)
+    assert np.array_equal(Q.Jptr, np.arange(n + 1)) and np.array_equal(Q.Jind, np.arange(n))
+    # factored apply: P_l X = Q_l (P_1 X)
+    X = rng.standard_normal((n, 3))
+    assert np.allclose(Q.apply(X), want[:, None] * P1.apply(X), rtol=1e-14, atol=1e-15)
+    assert np.allclose(oracle.spai_update_diagonal(P1, A1, n).val, 1.0, rtol=1e-14)
+    A3 = _csr(2.5 * D1, D1 != 0)
+    assert np.allclose(oracle.spai_update_diagonal(P1, A3, n).val, 1 / 2.5, rtol=1e-14)
+    d = rng.uniform(1.0, 2.0, n)
+    Ad1, Ad2 = synth.diag_csr(d), synth.diag_csr(1.3 * d + 0.1)
+    Pd = oracle.spai_build(Ad1, n)
+    assert np.allclose(oracle.spai_update_diagonal(Pd, Ad2, n).val, oracle.spai_update(Pd, Ad2, n).val,
+                       rtol=1e-15)
