@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-only", action="store_true")
     ap.add_argument("--batched-systems", type=int, default=256)
+    ap.add_argument("--batched-workers", type=int, default=8)
     return ap.parse_args()
 
 
@@ -476,7 +477,7 @@ def run_batched(args, sg, torch):
     torch.cuda.synchronize()
     t_loop = time.perf_counter() - t0
 
-    workers = [(torch.cuda.Stream(device=dev),) for _ in range(args.workers)]
+    workers = [(torch.cuda.Stream(device=dev),) for _ in range(args.batched_workers)]
     wctx = [sg.spai_ctx_create(st.cuda_stream, 0) for (st,) in workers]
     Xs = [torch.zeros((4, y["w"].n), dtype=torch.float64, device=dev) for y in systems]
     iters = [0] * nsys
@@ -563,17 +564,25 @@ def run_large(args, sg, torch):
         upd, t_u = timed(lambda: sg.spai_update(ctx, base, A, sg.UPDATE_FIRST | sg.PREC_BF16)[0])
         iu, t_su = timed(lambda: solve(A, upd))
         sg.spai_pc_destroy(upd)
+        dgu, t_d = timed(lambda: sg.spai_update(ctx, base, A, sg.UPDATE_FIRST | sg.UPDATE_DIAGONAL |
+                                                sg.PREC_BF16)[0])
+        idg, t_sd = timed(lambda: solve(A, dgu))
+        sg.spai_pc_destroy(dgu)
         reb, t_r = timed(lambda: sg.spai_build(ctx, A, sg.PATTERN_A | sg.PREC_BF16)[0])
         ir, t_sr = timed(lambda: solve(A, reb))
         sg.spai_pc_destroy(reb)
         rows.append({"p": round(p, 4), "update_ms": 1e3 * t_u, "solve_after_update_ms": 1e3 * t_su,
-                     "iterations_update": iu["iterations"], "rebuild_ms": 1e3 * t_r,
+                     "iterations_update": iu["iterations"],
+                     "diagonal_update_ms": 1e3 * t_d, "solve_after_diagonal_update_ms": 1e3 * t_sd,
+                     "iterations_diagonal_update": idg["iterations"], "rebuild_ms": 1e3 * t_r,
                      "solve_after_rebuild_ms": 1e3 * t_sr, "iterations_rebuild": ir["iterations"],
-                     "max_rel_residual": max(iu["max_rel_residual"], ir["max_rel_residual"])})
+                     "max_rel_residual": max(iu["max_rel_residual"], idg["max_rel_residual"],
+                                             ir["max_rel_residual"])})
     sg.spai_pc_destroy(base)
     sg.spai_affine_destroy(aff)
     sg.spai_ctx_destroy(ctx)
     upd_s = sum(r["update_ms"] + r["solve_after_update_ms"] for r in rows) / 1e3
+    dg_s = sum(r["diagonal_update_ms"] + r["solve_after_diagonal_update_ms"] for r in rows) / 1e3
     reb_s = sum(r["rebuild_ms"] + r["solve_after_rebuild_ms"] for r in rows) / 1e3
     return {
         "workload": f"3d-{args.large_side}^3-27pt, n={n}, nnz={nnz}, {s} RHS, SPAI(pattern A) FP32 stored "
@@ -581,6 +590,7 @@ def run_large(args, sg, torch):
         "build_fp64_ms": 1e3 * t_b64, "build_bf16_ms": 1e3 * t_b16, "per_parameter": rows,
         "update_path_solves_per_s": len(rows) / upd_s, "rebuild_path_solves_per_s": len(rows) / reb_s,
         "update_saving": 1.0 - upd_s / reb_s,
+        "diagonal_update_path_solves_per_s": len(rows) / dg_s, "diagonal_update_saving": 1.0 - dg_s / reb_s,
     }
 
 

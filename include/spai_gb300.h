@@ -83,6 +83,12 @@ typedef struct spai_pc_s *spai_pc;
 /* Update approaches of Table 1 (Sec. 2.3). */
 #define SPAI_UPDATE_FIRST 1    /* min ||A(1) - A(l) Q||_F, P_l = Q_l P_1 (proposed, Sec. 2.4) */
 #define SPAI_UPDATE_CHAINED 2  /* min ||A(l-1) - A(l) Q||_F, P_l = Q_l P_{l-1} */
+/* OR-ed into either approach: Q_l diagonal (Sec. 2.4 states no pattern for Q_l; this is
+ * the diagonal reading): the column least squares over J_k = {k}, whose rows are
+ * I_k = rows(A(l)(:,k)), q_kk = <A(l)(:,k), a_k> / ||A(l)(:,k)||^2 with a_k the base
+ * column; a zero column of A(l) is rank deficient (q_kk = 0, SPAI_ESINGULAR).  One dot
+ * product per column instead of a QR; applied as a row scaling. */
+#define SPAI_UPDATE_DIAGONAL 4
 
 /* ----------------------------------------------------------------------------------
  * Context
@@ -219,13 +225,14 @@ SPAI_API spai_status spai_build_batch(spai_ctx ctx, int32_t nsys, const spai_csr
 SPAI_API spai_status spai_update(spai_ctx ctx, spai_pc base, const spai_csr *A_new, int32_t approach,
                         spai_pc *out);
 
-/* Sizes: n, nnz of this handle's own factor (P or Q_l), total length of the I_k lists,
- * and depth (0 = built, 1 = updated from a build, ...).  Host outputs, any may be NULL. */
+/* Sizes: n, nnz of this handle's own factor (P or Q_l; n for a diagonal update), total
+ * length of the I_k lists, and depth (0 = built, 1 = updated from a build, ...).  Host outputs, any may be NULL. */
 SPAI_API spai_status spai_pc_info(spai_pc pc, int32_t *n, int32_t *nnz, int64_t *nI, int32_t *depth);
 
 /* Copy out this handle's own factor in column order on its pattern -- Jptr[n+1],
  * Jind[nnz], val[nnz] -- the row sets Iptr[n+1], Ilist[nI], and col_status[n] (0 ok, 1
- * singular).  DEVICE pointers; any may be NULL.  Asynchronous. */
+ * singular).  A diagonal update exports J_k = {k}, its values, and I_k = rows(A(:,k))
+ * (Ilist then holds nnz(A) entries).  DEVICE pointers; any may be NULL.  Asynchronous. */
 SPAI_API spai_status spai_pc_export(spai_ctx ctx, spai_pc pc, int32_t *Jptr, int32_t *Jind, double *val,
                            int32_t *Iptr, int32_t *Ilist, int32_t *col_status);
 

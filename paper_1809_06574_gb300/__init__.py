@@ -23,7 +23,7 @@ __all__ = [
     "spai_ctx_profile_entry", "spai_affine_create", "spai_affine_pattern",
     "spai_assemble", "spai_affine_export", "spai_affine_destroy", "spai_build", "spai_update", "spai_pc_info",
     "spai_pc_export", "spai_pc_destroy", "spai_build_batch", "spai_spmm", "spai_pc_apply", "block_solve",
-    "affine_coefficients", "PATTERN_A", "PATTERN_A2", "UPDATE_FIRST", "UPDATE_CHAINED", "PREC_FP32", "PREC_BF16",
+    "affine_coefficients", "PATTERN_A", "PATTERN_A2", "UPDATE_FIRST", "UPDATE_CHAINED", "UPDATE_DIAGONAL", "PREC_FP32", "PREC_BF16",
     "LIB_PATH", "spai_ctx_trim", "spai_solve_workspace_size", "spai_pc_mem_size",
     "spai_server_opts", "spai_request", "spai_result", "spai_server_stats", "spai_server_create",
     "spai_server_add_system", "spai_server_submit", "spai_server_wait", "spai_server_clock",
@@ -39,6 +39,7 @@ STATUS_NAMES = {0: "SPAI_OK", 1: "SPAI_EINVAL", 2: "SPAI_ENOMEM", 3: "SPAI_ECUDA
                 4: "SPAI_ESINGULAR", 5: "SPAI_ENOTCONV", 6: "SPAI_ETIMEOUT"}
 PATTERN_A, PATTERN_A2 = 0, 1
 UPDATE_FIRST, UPDATE_CHAINED = 1, 2
+UPDATE_DIAGONAL = 4  # OR into an approach: diagonal Q_l
 PREC_FP32 = 0x100  # OR into a pattern kind or an update approach: FP32 least squares and factor
 PREC_BF16 = 0x200  # the same least squares, factor stored in BF16
 

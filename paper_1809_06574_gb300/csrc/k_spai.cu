@@ -220,7 +220,45 @@ int launch_team(cudaStream_t st, const ColumnProblem &cp, const ColumnBatch &bt,
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+// Diagonal update (J_k = {k}): the column least squares over one unknown,
+// q_kk = <A(l)(:,k), a1_k> / ||A(l)(:,k)||^2 in the working precision R, both columns on
+// A's CSC pattern (cval: A(l), rval: A(1)); a zero column is rank deficient (q = 0,
+// status 1).  One thread per column.
+template <typename R>
+__global__ void k_diag_update(int32_t n, const int32_t *__restrict__ colptr, const double *__restrict__ cval,
+                              const double *__restrict__ rval, double *__restrict__ out, float *__restrict__ out32,
+                              uint16_t *__restrict__ out16, int32_t *__restrict__ status)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    R dot = R(0), nrm = R(0);
+    for (int32_t q = __ldg(colptr + k); q < __ldg(colptr + k + 1); ++q) {
+        const R a = (R)__ldg(cval + q);
+        dot = fma(a, (R)__ldg(rval + q), dot);
+        nrm = fma(a, a, nrm);
+    }
+    const bool sing = !(nrm > R(0));
+    const R v = sing ? R(0) : dot / nrm;
+    if (out16) out16[k] = __bfloat16_as_ushort(__float2bfloat16_rn((float)v));
+    else if (out32) out32[k] = (float)v;
+    else out[k] = (double)v;
+    status[k] = sing ? 1 : 0;
+}
+
 }  // namespace
+
+int launch_diag_update(cudaStream_t st, int32_t n, const int32_t *colptr, const double *cval, const double *rval,
+                       double *out, float *out32, uint16_t *out16, int32_t *status)
+{
+    if (n <= 0) return 0;
+    const unsigned g = (unsigned)(((int64_t)n + 255) / 256);
+    if (out32 || out16)
+        k_diag_update<float><<<g, 256, 0, st>>>(n, colptr, cval, rval, out, out32, out16, status);
+    else
+        k_diag_update<double><<<g, 256, 0, st>>>(n, colptr, cval, rval, out, out32, out16, status);
+    note_launches(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
 
 bool spai_columns_fit(int32_t maxI, int32_t maxJ)
 {

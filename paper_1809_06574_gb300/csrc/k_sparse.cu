@@ -301,7 +301,7 @@ __global__ void k_gather_f32_f64(int64_t count, const int32_t *__restrict__ idx,
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = (double)src[idx[i]];
+        dst[i] = (double)src[idx ? idx[i] : i];
 }
 
 __global__ void k_gather_bf16_f64(int64_t count, const int32_t *__restrict__ idx, const uint16_t *__restrict__ src,
@@ -309,7 +309,14 @@ __global__ void k_gather_bf16_f64(int64_t count, const int32_t *__restrict__ idx
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = (double)__bfloat162float(__ushort_as_bfloat16(src[idx[i]]));
+        dst[i] = (double)__bfloat162float(__ushort_as_bfloat16(src[idx ? idx[i] : i]));
+}
+
+__global__ void k_iota_i32(int64_t count, int32_t *__restrict__ dst)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (int32_t)i;
 }
 
 __global__ void k_invert_perm(int64_t count, const int32_t *__restrict__ perm,
@@ -379,6 +386,15 @@ __global__ void __launch_bounds__(kThreads) k_spmm(int32_t n, const int32_t *__r
     for (int32_t q = a; q < b; ++q)
         acc = fma(as_f64(__ldg(val + q)), __ldg(X + (int64_t)__ldg(colind + q) * S + c), acc);
     Y[row * S + c] = acc;
+}
+
+template <int S, typename V>
+__global__ void k_scale_rows(int32_t n, const V *__restrict__ q, const double *__restrict__ X,
+                             double *__restrict__ Y)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= (int64_t)n * S) return;
+    Y[g] = as_f64(__ldg(q + g / S)) * X[g];
 }
 
 template <int S>
@@ -535,6 +551,13 @@ int launch_gather_f32_f64(cudaStream_t st, int64_t count, const int32_t *idx, co
     return check_launch();
 }
 
+int launch_iota_i32(cudaStream_t st, int64_t count, int32_t *dst)
+{
+    if (count <= 0) return 0;
+    k_iota_i32<<<grid_for(count), kThreads, 0, st>>>(count, dst);
+    return check_launch();
+}
+
 int launch_gather_bf16_f64(cudaStream_t st, int64_t count, const int32_t *idx, const uint16_t *src, double *dst)
 {
     if (count <= 0) return 0;
@@ -622,6 +645,32 @@ int launch_spmm_bf16v(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowp
                       const uint16_t *val, const double *X, double *Y)
 {
     return spmm_any<uint16_t>(st, s, n, rowptr, colind, val, X, Y);
+}
+
+namespace {
+template <typename V>
+int scale_rows_any(cudaStream_t st, int32_t s, int32_t n, const V *q, const double *X, double *Y)
+{
+    if (n <= 0) return 0;
+    const int g = grid_for((int64_t)n * s);
+    switch (s) {
+    case 1: k_scale_rows<1, V><<<g, kThreads, 0, st>>>(n, q, X, Y); break;
+    case 2: k_scale_rows<2, V><<<g, kThreads, 0, st>>>(n, q, X, Y); break;
+    case 4: k_scale_rows<4, V><<<g, kThreads, 0, st>>>(n, q, X, Y); break;
+    case 8: k_scale_rows<8, V><<<g, kThreads, 0, st>>>(n, q, X, Y); break;
+    case 16: k_scale_rows<16, V><<<g, kThreads, 0, st>>>(n, q, X, Y); break;
+    default: return -1;
+    }
+    return check_launch();
+}
+}  // namespace
+
+int launch_scale_rows(cudaStream_t st, int32_t s, int32_t n, const double *q, const float *q32, const uint16_t *q16,
+                      const double *X, double *Y)
+{
+    if (q16) return scale_rows_any<uint16_t>(st, s, n, q16, X, Y);
+    if (q32) return scale_rows_any<float>(st, s, n, q32, X, Y);
+    return scale_rows_any<double>(st, s, n, q, X, Y);
 }
 
 int launch_pack(cudaStream_t st, int32_t s, int32_t n, const double *src, int64_t ld, double *dst)

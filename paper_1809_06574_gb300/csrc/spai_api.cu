@@ -86,6 +86,7 @@ struct spai_pc_s {
     uint16_t *fval16 = nullptr;  // the same for SPAI_PREC_BF16 factors (BF16 bit patterns)
     double *a_cval = nullptr;  // this matrix's values in CSC order
     int32_t *status = nullptr;
+    bool diag = false;         // diagonal factor (n values, SPAI_UPDATE_DIAGONAL)
 };
 
 struct spai_affine_s {
@@ -570,15 +571,18 @@ int prec_of(int32_t flags)
     return -1;
 }
 
-spai_status pc_alloc(spai_ctx ctx, Sym *s, int prec, spai_pc *out)
+// a factor on P's pattern, or (diag) a diagonal factor of n values
+spai_status pc_alloc(spai_ctx ctx, Sym *s, int prec, spai_pc *out, bool diag = false)
 {
     spai_pc pc = new spai_pc_s();
     pc->ctx = ctx;
     pc->sym = s;
+    pc->diag = diag;
+    const int64_t nf = diag ? (int64_t)s->n : (int64_t)s->nnzP;
     spai_status st;
-    if ((prec == 1   ? (st = dalloc_n(ctx, &pc->fval32, s->nnzP))
-         : prec == 2 ? (st = dalloc_n(ctx, &pc->fval16, s->nnzP))
-                     : (st = dalloc_n(ctx, &pc->fval, s->nnzP))) ||
+    if ((prec == 1   ? (st = dalloc_n(ctx, &pc->fval32, nf))
+         : prec == 2 ? (st = dalloc_n(ctx, &pc->fval16, nf))
+                     : (st = dalloc_n(ctx, &pc->fval, nf))) ||
         (st = dalloc_n(ctx, &pc->a_cval, s->nnzA)) || (st = dalloc_n(ctx, &pc->status, s->n))) {
         dfree(ctx, pc->fval);
         dfree(ctx, pc->fval32);
@@ -588,9 +592,9 @@ spai_status pc_alloc(spai_ctx ctx, Sym *s, int prec, spai_pc *out)
         delete pc;
         return st;
     }
-    if (s->nnzP && pc->fval) CU(cudaMemsetAsync(pc->fval, 0, (size_t)s->nnzP * 8, ctx->stream), "memset");
-    if (s->nnzP && pc->fval32) CU(cudaMemsetAsync(pc->fval32, 0, (size_t)s->nnzP * 4, ctx->stream), "memset");
-    if (s->nnzP && pc->fval16) CU(cudaMemsetAsync(pc->fval16, 0, (size_t)s->nnzP * 2, ctx->stream), "memset");
+    if (nf && pc->fval) CU(cudaMemsetAsync(pc->fval, 0, (size_t)nf * 8, ctx->stream), "memset");
+    if (nf && pc->fval32) CU(cudaMemsetAsync(pc->fval32, 0, (size_t)nf * 4, ctx->stream), "memset");
+    if (nf && pc->fval16) CU(cudaMemsetAsync(pc->fval16, 0, (size_t)nf * 2, ctx->stream), "memset");
     *out = pc;
     return SPAI_OK;
 }
@@ -606,7 +610,11 @@ spai_status apply_rm(spai_ctx ctx, spai_pc pc, int32_t s, const double *X, doubl
         spai_pc h = chain[i];
         double *dst = (i == 0) ? Y : bufs[(chain.size() - 1 - i) & 1];
         const double nz = h->sym->nnzP, nn = h->sym->n;
-        if (h->fval16) {
+        if (h->diag) {
+            PKL("scale_rows", nn * s, (h->fval16 ? 2.0 : h->fval32 ? 4.0 : 8.0) * nn + 16.0 * nn * s,
+                launch_scale_rows(ctx->stream, s, h->sym->n, h->fval, h->fval32, h->fval16, cur, dst),
+                "diagonal factor apply");
+        } else if (h->fval16) {
             PKL("spmm_P", 2.0 * nz * s, 6.0 * nz + 4.0 * (nn + 1) + 16.0 * nn * s,
                 launch_spmm_bf16v(ctx->stream, s, h->sym->n, h->sym->p_rowptr, h->sym->p_colind, h->fval16, cur, dst),
                 "preconditioner apply");
@@ -894,7 +902,8 @@ extern "C" spai_status spai_update(spai_ctx ctx, spai_pc base, const spai_csr *A
     *out = nullptr;
     const int prec = prec_of(approach);
     if (prec < 0) return fail(ctx, SPAI_EINVAL, "SPAI_PREC_FP32 and SPAI_PREC_BF16 are exclusive");
-    approach &= ~(SPAI_PREC_FP32 | SPAI_PREC_BF16);
+    const bool diag = (approach & SPAI_UPDATE_DIAGONAL) != 0;
+    approach &= ~(SPAI_PREC_FP32 | SPAI_PREC_BF16 | SPAI_UPDATE_DIAGONAL);
     if (approach != SPAI_UPDATE_FIRST && approach != SPAI_UPDATE_CHAINED)
         return fail(ctx, SPAI_EINVAL, "unknown update approach %d", approach);
     spai_status st = check_csr_args(ctx, A_new, "A_new");
@@ -913,7 +922,7 @@ extern "C" spai_status spai_update(spai_ctx ctx, spai_pc base, const spai_csr *A
         if (h) return fail(ctx, SPAI_EINVAL, "A_new does not have the base matrix's sparsity pattern");
     }
     spai_pc pc = nullptr;
-    if ((st = pc_alloc(ctx, s, prec, &pc))) return st;
+    if ((st = pc_alloc(ctx, s, prec, &pc, diag))) return st;
     s->refs++;
     spai_pc from = (approach == SPAI_UPDATE_FIRST) ? base->root : base;
     pc->parent = from;
@@ -922,7 +931,24 @@ extern "C" spai_status spai_update(spai_ctx ctx, spai_pc base, const spai_csr *A
     if (s->nnzA)
         PKL("gather_csc", 0.0, 20.0 * s->nnzA,
             launch_gather_f64(ctx->stream, s->nnzA, s->a_perm, A_new->val, pc->a_cval), "gather values");
-    st = run_columns(ctx, pc, 1, from->a_cval);
+    if (diag) {
+        // one unknown per column: rows I_k = rows(A(l)(:,k)), A(1)'s column on the same pattern
+        if (s->n)
+            PKL("spai_columns", 4.0 * s->nnzA + s->n, 16.0 * s->nnzA + 4.0 * (s->n + 1) + 12.0 * s->n,
+                launch_diag_update(ctx->stream, s->n, s->a_colptr, pc->a_cval, from->a_cval, pc->fval, pc->fval32,
+                                   pc->fval16, pc->status),
+                "diagonal update");
+        st = SPAI_OK;
+        if (s->n) {
+            KL(launch_first_nonzero(ctx->stream, s->n, pc->status, ctx->d_scalar), "status scan");
+            int32_t first = INT_MAX;
+            if ((st = read_i32(ctx, ctx->d_scalar, &first))) { spai_pc_destroy(pc); return st; }
+            if (first != INT_MAX)
+                st = fail(ctx, SPAI_ESINGULAR, "column %d: zero column, diagonal update entry set to 0", first);
+        }
+    } else {
+        st = run_columns(ctx, pc, 1, from->a_cval);
+    }
     if (st && st != SPAI_ESINGULAR) { spai_pc_destroy(pc); return st; }
     *out = pc;
     return st;
@@ -1122,8 +1148,8 @@ extern "C" spai_status spai_pc_info(spai_pc pc, int32_t *n, int32_t *nnz, int64_
 {
     if (!pc) return SPAI_EINVAL;
     if (n) *n = pc->sym->n;
-    if (nnz) *nnz = pc->sym->nnzP;
-    if (nI) *nI = pc->sym->nI;
+    if (nnz) *nnz = pc->diag ? pc->sym->n : pc->sym->nnzP;
+    if (nI) *nI = pc->diag ? (int64_t)pc->sym->nnzA : pc->sym->nI;
     if (depth) *depth = pc->depth;
     return SPAI_OK;
 }
@@ -1134,7 +1160,8 @@ extern "C" size_t spai_pc_mem_size(spai_pc pc, int32_t with_analysis)
     auto r = [](size_t b) { return ((b ? b : 16) + 255) / 256 * 256; };  // as dalloc rounds
     const Sym *s = pc->sym;
     const size_t n1 = (size_t)s->n + 1;
-    size_t b = r((size_t)s->nnzP * (pc->fval16 ? 2 : pc->fval32 ? 4 : 8)) + r((size_t)s->nnzA * 8) + r((size_t)s->n * 4);
+    const size_t nf = pc->diag ? (size_t)s->n : (size_t)s->nnzP;
+    size_t b = r(nf * (pc->fval16 ? 2 : pc->fval32 ? 4 : 8)) + r((size_t)s->nnzA * 8) + r((size_t)s->n * 4);
     if (with_analysis) {
         b += 2 * r(n1 * 4) + 3 * r((size_t)s->nnzA * 4) + r(n1 * 4) + r((size_t)s->nI * 4);
         if (!s->alias) b += 2 * r(n1 * 4) + 3 * r((size_t)s->nnzP * 4);
@@ -1148,6 +1175,21 @@ extern "C" spai_status spai_pc_export(spai_ctx ctx, spai_pc pc, int32_t *Jptr, i
     if (!ctx || !pc) return fail(ctx, SPAI_EINVAL, "NULL argument");
     Sym *s = pc->sym;
     const int32_t n = s->n;
+    if (pc->diag) {
+        // J_k = {k}, I_k = rows(A(:,k)), values in column order already
+        if (Jptr) KL(launch_iota_i32(ctx->stream, (int64_t)n + 1, Jptr), "export");
+        if (Jind && n) KL(launch_iota_i32(ctx->stream, n, Jind), "export");
+        if (val && n) {
+            if (pc->fval16) KL(launch_gather_bf16_f64(ctx->stream, n, nullptr, pc->fval16, val), "export values");
+            else if (pc->fval32) KL(launch_gather_f32_f64(ctx->stream, n, nullptr, pc->fval32, val), "export values");
+            else CU(cudaMemcpyAsync(val, pc->fval, (size_t)n * 8, cudaMemcpyDeviceToDevice, ctx->stream), "export");
+        }
+        if (Iptr) CU(cudaMemcpyAsync(Iptr, s->a_colptr, ((size_t)n + 1) * 4, cudaMemcpyDeviceToDevice, ctx->stream), "export");
+        if (Ilist && s->nnzA)
+            CU(cudaMemcpyAsync(Ilist, s->a_rowind, (size_t)s->nnzA * 4, cudaMemcpyDeviceToDevice, ctx->stream), "export");
+        if (col_status && n) CU(cudaMemcpyAsync(col_status, pc->status, (size_t)n * 4, cudaMemcpyDeviceToDevice, ctx->stream), "export");
+        return SPAI_OK;
+    }
     if (Jptr) CU(cudaMemcpyAsync(Jptr, s->Jptr, ((size_t)n + 1) * 4, cudaMemcpyDeviceToDevice, ctx->stream), "export");
     if (Jind && s->nnzP) CU(cudaMemcpyAsync(Jind, s->Jind, (size_t)s->nnzP * 4, cudaMemcpyDeviceToDevice, ctx->stream), "export");
     if (val && s->nnzP) {
@@ -1694,7 +1736,9 @@ extern "C" spai_status spai_pc_apply_noalloc(spai_ctx ctx, spai_pc pc, int32_t s
         spai_pc h = pc;
         for (int hop = 0; hop < i; ++hop) h = h->parent;
         double *dst = (i == 0) ? yr : bufs[(len - 1 - i) & 1];
-        if (h->fval16)
+        if (h->diag)
+            KL(launch_scale_rows(ctx->stream, s, n, h->fval, h->fval32, h->fval16, cur, dst), "diagonal factor apply");
+        else if (h->fval16)
             KL(launch_spmm_bf16v(ctx->stream, s, n, h->sym->p_rowptr, h->sym->p_colind, h->fval16, cur, dst),
                "preconditioner apply");
         else if (h->fval32)

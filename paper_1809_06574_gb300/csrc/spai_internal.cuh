@@ -81,10 +81,15 @@ int launch_spmm(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr,
 int launch_spmm_bf16v(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr, const int32_t *colind,
                       const uint16_t *val, const double *X, double *Y);
 int launch_gather_bf16_f64(cudaStream_t st, int64_t count, const int32_t *idx, const uint16_t *src, double *dst);
+// dst[i] = i; the FP32 / BF16 gathers take idx = NULL for the identity
+int launch_iota_i32(cudaStream_t st, int64_t count, int32_t *dst);
 // same with FP32 values (products and sums in FP64)
 int launch_spmm_f32v(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr, const int32_t *colind,
                      const float *val, const double *X, double *Y);
 int launch_pack(cudaStream_t st, int32_t s, int32_t n, const double *src, int64_t ld, double *dst);
+// Y[r][c] = q[r] X[r][c] (a diagonal factor; q FP64, FP32 or BF16 bits, one of them given)
+int launch_scale_rows(cudaStream_t st, int32_t s, int32_t n, const double *q, const float *q32, const uint16_t *q16,
+                      const double *X, double *Y);
 int launch_unpack(cudaStream_t st, int32_t s, int32_t n, const double *src, double *dst,
                   int64_t ld);
 
@@ -113,6 +118,10 @@ struct ColumnBatch {
     int32_t nsys;
     int64_t total;
 };
+// diagonal update: out[k] = <cval(:,k), rval(:,k)> / ||cval(:,k)||^2 on the CSC pattern
+// colptr (FP32 working precision when out32 or out16 is given, else FP64)
+int launch_diag_update(cudaStream_t st, int32_t n, const int32_t *colptr, const double *cval, const double *rval,
+                       double *out, float *out32, uint16_t *out16, int32_t *status);
 // true if one column problem of maxI x maxJ fits the kernel's shared-memory tile
 bool spai_columns_fit(int32_t maxI, int32_t maxJ);
 // Picks the team size by the largest |I_k|, |J_k|; returns 0 or -1 if no tile fits.

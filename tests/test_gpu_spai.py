@@ -246,3 +246,61 @@ def test_memory_budget_refusal():
             sg.spai_build(ctx, dev_csr(A, w.n))
         assert ei.value.status == sg.SPAI_ENOMEM
         assert sg.spai_ctx_mem_in_use(ctx) == 0
+
+
+@pytest.mark.parametrize("prec", [0, 0x100, 0x200])
+def test_diagonal_update_against_oracle(prec):
+    """SPAI_UPDATE_DIAGONAL: q_kk of the one-unknown column least squares, bit-exact
+    pattern and row sets, values within the FP64 bar (FP32 / BF16 bars otherwise), and
+    the factored apply Q_l (P_1 X) against the oracle's."""
+    import torch
+    sg = _sg()
+    w = synth.grid3d_7pt(side=11, nparams=3, seed=2)
+    n = w.n
+    A1 = oracle.assemble(w.terms, oracle.coefficients(0.2, 1.0), n)
+    A2 = oracle.assemble(w.terms, oracle.coefficients(0.7, 1.0), n)
+    P1 = oracle.spai_build(A1, n)
+    Q = oracle.spai_update_diagonal(P1, A2, n)
+    X = np.random.default_rng(1).standard_normal((n, 8))
+    with context() as ctx:
+        pc1, _ = sg.spai_build(ctx, dev_csr(A1, n), sg.PATTERN_A | prec)
+        q, st = sg.spai_update(ctx, pc1, dev_csr(A2, n), sg.UPDATE_FIRST | sg.UPDATE_DIAGONAL | prec)
+        g = export(ctx, q)
+        Xd = torch.as_tensor(np.ascontiguousarray(X.T), device="cuda:0")
+        Yd = torch.zeros((8, n), dtype=torch.float64, device="cuda:0")
+        sg.spai_pc_apply(ctx, q, 8, Xd, n, Yd, n)
+        sg.spai_ctx_sync(ctx)
+        Y = Yd.cpu().numpy().T
+        sg.spai_pc_destroy(q)
+        sg.spai_pc_destroy(pc1)
+    assert st == 0 and g["nnz"] == n and g["depth"] == 1
+    assert np.array_equal(g["Jptr"], Q.Jptr) and np.array_equal(g["Jind"], Q.Jind)
+    assert np.array_equal(g["Iptr"], Q.Iptr) and np.array_equal(g["Ilist"], Q.Ilist)
+    assert not g["status"].any()
+    rel = np.max(np.abs(g["val"] - Q.val) / np.abs(Q.val))
+    bar = {0: 1e-14, 0x100: 1e-6, 0x200: 2.0 ** -8 + 1e-6}[prec]
+    assert rel <= bar, rel
+    Yref = Q.apply(X)
+    bar_apply = {0: 1e-12, 0x100: 1e-4, 0x200: 2e-2}[prec]
+    assert np.max(np.abs(Y - Yref)) <= bar_apply * np.max(np.abs(Yref))
+
+
+def test_diagonal_update_solve_converges():
+    import torch
+    sg = _sg()
+    w = synth.grid3d_7pt(side=14, nparams=3, seed=4)
+    n = w.n
+    A1 = oracle.assemble(w.terms, oracle.coefficients(w.params[0], 1.0), n)
+    A2 = oracle.assemble(w.terms, oracle.coefficients(w.params[1], 1.0), n)
+    Q = oracle.spai_update_diagonal(oracle.spai_build(A1, n), A2, n)
+    Xo, io = oracle.block_gmres(oracle.csr_apply(A2, n), Q.apply, w.B, 30, 1e-8, 50)
+    with context() as ctx:
+        d2 = dev_csr(A2, n)
+        pc1, _ = sg.spai_build(ctx, dev_csr(A1, n))
+        q, _ = sg.spai_update(ctx, pc1, d2, sg.UPDATE_FIRST | sg.UPDATE_DIAGONAL)
+        X = np.zeros((n, w.B.shape[1]), order="F")
+        st, info, rel = sg.block_solve(ctx, d2, q, w.B.shape[1], np.asfortranarray(w.B), n, X, n, 30, 1e-8, 50)
+        sg.spai_pc_destroy(q)
+        sg.spai_pc_destroy(pc1)
+    assert info["converged"] and io["converged"]
+    assert np.linalg.norm(X - Xo) <= 1e-6 * np.linalg.norm(Xo)
