@@ -337,6 +337,37 @@ __global__ void __launch_bounds__(kThreads) k_trsm_gram(int32_t n, const double 
     gram_tiles<S, true>(n, W, Rs, rinv, Q1, partial);
 }
 
+// ---------------------------------------------------------------------------------
+// 16-column blocks on the 8-column tensor-core kernels: column halves and the matching
+// pieces of the small S x S blocks
+// ---------------------------------------------------------------------------------
+// Wl[r] = W[r][0..8), Wr[r] = W[r][8..16) (Wr = Wl + 8 n), or back when merge
+__global__ void k_halves16(int32_t n, double *__restrict__ W, double *__restrict__ Wl, bool merge)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= (int64_t)n * 8) return;  // g = (row, pair of columns)
+    const int64_t r = g >> 3;
+    const int c = (int)(g & 7) * 2;      // columns c, c+1 of 16
+    const int h = c >> 3, cc = c & 7;
+    double2 *full = reinterpret_cast<double2 *>(W + r * 16 + c);
+    double2 *half = reinterpret_cast<double2 *>(Wl + (int64_t)h * n * 8 + r * 8 + cc);
+    if (merge) *full = *half;
+    else *half = *full;
+}
+
+// H[i][a][b] (16 x 16 per block) <-> HL / HR[2i + a / 8][a % 8][b % 8] (b < 8: HL, else HR)
+__global__ void k_pieces16(int32_t nb, double *__restrict__ H, double *__restrict__ HL, double *__restrict__ HR,
+                           bool merge)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= (int64_t)nb * 256) return;
+    const int64_t i = g >> 8;
+    const int a = (int)(g >> 4) & 15, b = (int)g & 15;
+    double *piece = (b < 8 ? HL : HR) + ((2 * i + (a >> 3)) * 8 + (a & 7)) * 8 + (b & 7);
+    if (merge) H[g] = *piece;
+    else *piece = H[g];
+}
+
 template <int S>
 __global__ void k_triu_mul(const double *__restrict__ R2, const double *__restrict__ R1,
                            double *__restrict__ out)
@@ -721,6 +752,20 @@ int launch_trsm_rows(cudaStream_t st, int32_t s, int32_t n, const double *W, con
 {
     if (n <= 0) return 0;
     SPAI_DISPATCH_S(s, (k_trsm_rows<S><<<grid_for(n), kThreads, 0, st>>>(n, W, R, deflated, out)));
+    return check_launch();
+}
+
+int launch_halves16(cudaStream_t st, int32_t n, double *W, double *Wl, bool merge)
+{
+    if (n <= 0) return 0;
+    k_halves16<<<grid_for((int64_t)n * 8), kThreads, 0, st>>>(n, W, Wl, merge);
+    return check_launch();
+}
+
+int launch_pieces16(cudaStream_t st, int32_t nb, double *H, double *HL, double *HR, bool merge)
+{
+    if (nb <= 0) return 0;
+    k_pieces16<<<grid_for((int64_t)nb * 256), kThreads, 0, st>>>(nb, H, HL, HR, merge);
     return check_launch();
 }
 

@@ -1294,7 +1294,16 @@ struct SolveWs {
     uint64_t *vfix_sub; // the same, sub-tile layout across blocks (Gram product)
     void *hdig;     // digit pieces of H (tensor-core block update)
     int32_t *hexp;  // column exponents of H
+    double *Wh;     // s == 16: column halves of a block (n x 8 each, back to back)
+    double *HL, *HR;  // s == 16: 8 x 8 pieces of the small blocks, per half-block
 };
+
+// Block widths whose Gram-Schmidt products can run on the tensor-core digit kernels: 8
+// directly, 16 as two 8-column halves (2 (m + 1) half-blocks within the update kernel's limit)
+bool digits_for(int32_t s, int32_t m)
+{
+    return block_dot_tc_supported(s) || (s == 16 && 2 * (m + 1) <= block_update_tc_max_blocks());
+}
 
 size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks)
 {
@@ -1314,9 +1323,11 @@ size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks
     w.T0 = (double *)take(blk);
     w.T1 = (double *)take(blk);
     w.V = (double *)take(blk * (m + 1));
+    const bool digits = digits_for(s, m);
+    const int32_t nh = (s == 16 ? 2 : 1) * (m + 1);  // basis (half-)blocks of the digit kernels
     {
         const size_t a = (size_t)chunks * s * 8, b = dot_partial_elems(s, m + 1) * 8;
-        const size_t c = tc_partial_elems(n, m + 1) * 8;  // tensor-core row chunks
+        const size_t c = tc_partial_elems(n, nh) * 8;  // tensor-core row chunks
         size_t mx = a > b ? a : b;
         w.partial = (double *)take(mx > c ? mx : c);
     }
@@ -1337,11 +1348,14 @@ size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks
     w.defl1 = (int32_t *)take(s * 4);
     w.defl2 = (int32_t *)take(s * 4);
     w.flag = (int32_t *)take(64);
-    const bool digits = block_dot_tc_supported(s);
     w.vfix = (uint64_t *)take(digits ? blk * (m + 1) : 16);
-    w.vfix_sub = (uint64_t *)take(digits ? tc_fixed_sub_bytes(n, m + 1) : 16);
-    w.hdig = take(digits ? tc_hdig_bytes(m + 1) : 16);
+    w.vfix_sub = (uint64_t *)take(digits ? tc_fixed_sub_bytes(n, nh) : 16);
+    w.hdig = take(digits ? tc_hdig_bytes(nh) : 16);
     w.hexp = (int32_t *)take(64);
+    const bool halves = digits && s == 16;
+    w.Wh = (double *)take(halves ? blk : 16);
+    w.HL = (double *)take(halves ? (size_t)nh * 64 * 8 : 16);
+    w.HR = (double *)take(halves ? (size_t)nh * 64 * 8 : 16);
     return off;
 }
 
@@ -1438,15 +1452,59 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
     const bool b_dev = is_device_ptr(B), x_dev = is_device_ptr(X);
     if (opts->orth < SPAI_ORTH_AUTO || opts->orth > SPAI_ORTH_TENSOR)
         return fail(ctx, SPAI_EINVAL, "unknown orthogonalisation method %d", opts->orth);
-    const bool use_digits = block_dot_tc_supported(s) && opts->orth != SPAI_ORTH_FP64;
+    const bool use_digits = digits_for(s, m) && opts->orth != SPAI_ORTH_FP64;
+    const bool halves = use_digits && s == 16;  // 16 columns as two 8-column halves
+    const int32_t ipad = (halves ? 2 : 1) * (m + 1);
+    const size_t half_elems = (size_t)n * 8;
+    // H = V_{0..nb-1}^T Wsrc on the tensor cores: a 16-column block as two halves against
+    // all 2 nb half-blocks of the basis, the two 8-column results merged into 16 x 16 blocks
+    auto gram_tc = [&](int nb, double *Wsrc, double *H) -> spai_status {
+        const double f = 2.0 * n * s * s * nb, by = 8.0 * n * s * (nb + 1);
+        if (!halves) {
+            PKL("block_dot_tc", f, by, launch_block_dot_tc(cs, n, nb, w.vfix_sub, ipad, Wsrc, w.partial, H, ctx->d_err),
+                "block Gram product");
+            return SPAI_OK;
+        }
+        ProfScope ps(ctx, "block_dot_tc", f, by);
+        KL(launch_halves16(cs, n, Wsrc, w.Wh, false), "column halves");
+        KL(launch_block_dot_tc(cs, n, 2 * nb, w.vfix_sub, ipad, w.Wh, w.partial, w.HL, ctx->d_err), "block Gram product");
+        KL(launch_block_dot_tc(cs, n, 2 * nb, w.vfix_sub, ipad, w.Wh + half_elems, w.partial, w.HR, ctx->d_err),
+           "block Gram product");
+        KL(launch_pieces16(cs, nb, H, w.HL, w.HR, true), "merge pieces");
+        return SPAI_OK;
+    };
+    // fixed point of basis block blk of a 16-column basis: its two halves as half-blocks
+    // 2 blk and 2 blk + 1 (8-column blocks get theirs from the Cholesky-QR pass)
+    auto fixed16 = [&](int blk) -> spai_status {
+        if (!halves) return SPAI_OK;
+        ProfScope ps(ctx, "to_fixed", 0.0, 24.0 * n * s);
+        KL(launch_halves16(cs, n, w.V + (size_t)blk * n * s, w.Wh, false), "column halves");
+        KL(launch_to_fixed(cs, n, 2, w.Wh, w.vfix + (size_t)2 * blk * half_elems, w.vfix_sub, ipad, 2 * blk, ctx->d_err),
+           "fixed point");
+        return SPAI_OK;
+    };
     // out = base + sign * V_{0..nb-1} H: tensor-core digits when available, else FP64
     auto vupdate = [&](int nb, const double *H, const double *basep, double *out, double sign) -> spai_status {
         const double f = 2.0 * n * s * s * nb;
-        if (use_digits && nb <= block_update_tc_max_blocks() && (opts->orth == SPAI_ORTH_TENSOR || nb >= 2)) {
-            PKL("block_update_tc", f, 8.0 * n * s * (nb + 2),
-                launch_block_update_tc(cs, n, nb, w.vfix, H, w.hdig, w.hexp, basep, out, sign,
-                                       ctx->d_err),
-                "block update");
+        if (use_digits && (halves ? 2 : 1) * nb <= block_update_tc_max_blocks() &&
+            (opts->orth == SPAI_ORTH_TENSOR || nb >= 2)) {
+            if (!halves) {
+                PKL("block_update_tc", f, 8.0 * n * s * (nb + 2),
+                    launch_block_update_tc(cs, n, nb, w.vfix, H, w.hdig, w.hexp, basep, out, sign, ctx->d_err),
+                    "block update");
+                return SPAI_OK;
+            }
+            // each output half: base half + sign * sum over half-blocks of V_hb times its piece of H
+            ProfScope ps(ctx, "block_update_tc", f, 8.0 * n * s * (nb + 2));
+            KL(launch_pieces16(cs, nb, const_cast<double *>(H), w.HL, w.HR, false), "split pieces");
+            if (basep) KL(launch_halves16(cs, n, const_cast<double *>(basep), w.Wh, false), "column halves");
+            for (int h = 0; h < 2; ++h) {
+                double *wh = w.Wh + h * half_elems;
+                KL(launch_block_update_tc(cs, n, 2 * nb, w.vfix, h ? w.HR : w.HL, w.hdig, w.hexp, basep ? wh : nullptr, wh,
+                                          sign, ctx->d_err),
+                   "block update");
+            }
+            KL(launch_halves16(cs, n, out, w.Wh, true), "merge halves");
         } else {
             PKL("block_update", f, 8.0 * n * s * (nb + 2),
                 launch_block_update(cs, s, n, nb, w.V, H, basep, out, sign), "block update");
@@ -1498,7 +1556,8 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
     while (!converged() && cycles < opts->max_cycles) {
         ++cycles;
         // V_0 S_0 = R (ref2 holds the residual norms^2)
-        if ((st = cholqr2(ctx, w, n, s, w.W, w.V, w.Rn, w.ref2, use_digits ? 0 : -1, m + 1))) return st;
+        if ((st = cholqr2(ctx, w, n, s, w.W, w.V, w.Rn, w.ref2, (use_digits && !halves) ? 0 : -1, ipad))) return st;
+        if ((st = fixed16(0))) return st;
         PKL("small_dense", 0.0, 0.0, launch_set_rhs(cs, s, m, w.Rn, w.G), "rhs");
         int J = 0;
         for (int j = 0; j < m; ++j) {
@@ -1515,16 +1574,14 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
             const double nb = j + 1;
             const bool tc = use_digits && (opts->orth == SPAI_ORTH_TENSOR || j + 1 >= 2);
             if (tc) {
-                PKL("block_dot_tc", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
-                    launch_block_dot_tc(cs, n, j + 1, w.vfix_sub, m + 1, w.W, w.partial, w.H1, ctx->d_err), "H1");
+                if ((st = gram_tc(j + 1, w.W, w.H1))) return st;
             } else {
                 PKL("block_dot", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
                     launch_block_dot(cs, s, n, j + 1, w.V, w.W, w.partial, w.H1, chunks), "H1");
             }
             if ((st = vupdate(j + 1, w.H1, w.W, w.W, -1.0))) return st;
             if (tc) {
-                PKL("block_dot_tc", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
-                    launch_block_dot_tc(cs, n, j + 1, w.vfix_sub, m + 1, w.W, w.partial, w.H2, ctx->d_err), "H2");
+                if ((st = gram_tc(j + 1, w.W, w.H2))) return st;
             } else {
                 PKL("block_dot", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
                     launch_block_dot(cs, s, n, j + 1, w.V, w.W, w.partial, w.H2, chunks), "H2");
@@ -1532,8 +1589,10 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
             if ((st = vupdate(j + 1, w.H2, w.W, w.W, -1.0))) return st;
             double *Vn = w.V + (size_t)(j + 1) * blk_elems;
             // the new block's fixed point (for the products of the next steps) comes with it
-            if ((st = cholqr2(ctx, w, n, s, w.W, Vn, w.Rn, w.ref2, (use_digits && j + 1 < m) ? j + 1 : -1, m + 1)))
+            if ((st = cholqr2(ctx, w, n, s, w.W, Vn, w.Rn, w.ref2, (use_digits && !halves && j + 1 < m) ? j + 1 : -1,
+                              ipad)))
                 return st;
+            if (j + 1 < m && (st = fixed16(j + 1))) return st;
             PKL("arnoldi_ls", 16.0 * s * s * s * (j + 1), 0.0,
                 launch_arnoldi_ls(cs, s, j, m, w.H1, w.H2, w.Rn, w.Qs, w.Rtri, w.G, w.thresh, w.est, w.flag), "least squares");
             CU(cudaMemcpyAsync(h + 32, w.est, s * 8, cudaMemcpyDeviceToHost, cs), "read estimates");

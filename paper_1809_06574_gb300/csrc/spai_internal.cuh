@@ -198,6 +198,10 @@ int launch_chol_small(cudaStream_t st, int32_t s, const double *G, const double 
                       double tau2, double *R, int32_t *deflated);
 int launch_trsm_rows(cudaStream_t st, int32_t s, int32_t n, const double *W, const double *R,
                      const int32_t *deflated, double *out);
+// 16-column blocks on the 8-column tensor-core kernels: W (n x 16) <-> halves Wl, Wr = Wl +
+// 8 n (n x 8 each); H (nb blocks of 16 x 16) <-> 8 x 8 pieces HL / HR of the 2 nb half-blocks
+int launch_halves16(cudaStream_t st, int32_t n, double *W, double *Wl, bool merge);
+int launch_pieces16(cudaStream_t st, int32_t nb, double *H, double *HL, double *HR, bool merge);
 // Cholesky-QR pieces with rows held in registers (s <= 8): G = W^T W; and Q1 = W R^{-1}
 // written to Q1 together with G2 = Q1^T Q1.  partial needs 1216 * s * s doubles.
 bool gram_rows_supported(int32_t s);

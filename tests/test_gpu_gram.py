@@ -104,20 +104,23 @@ def test_tensor_gram_rejects_out_of_range_basis():
         assert ei.value.status == sg.SPAI_EINVAL
 
 
-def test_solve_with_tensor_orthogonalisation_matches_fp64():
+@pytest.mark.parametrize("nrhs,restart", [(8, 50), (16, 30)])
+def test_solve_with_tensor_orthogonalisation_matches_fp64(nrhs, restart):
+    """8 columns run on the digit kernels directly, 16 columns as two 8-column halves
+    against all half-blocks of the basis; both must give the FP64 iterates to rounding."""
     import paper_1809_06574_gb300 as sg
-    w = synth.grid3d_7pt(side=24, nparams=2, nrhs=8)
+    w = synth.grid3d_7pt(side=24, nparams=2, nrhs=nrhs)
     n = w.n
     A = oracle.assemble(w.terms, oracle.coefficients(w.params[0], 0.5), n)
     P = oracle.spai_build(A, n)
-    Xo, io = oracle.block_gmres(oracle.csr_apply(A, n), P.apply, w.B, 50, 1e-8, 20)
+    Xo, io = oracle.block_gmres(oracle.csr_apply(A, n), P.apply, w.B, restart, 1e-8, 20)
     res = {}
     with context() as ctx:
         Ad = dev_csr(A, n)
         pc, _ = sg.spai_build(ctx, Ad)
         for orth in (sg.ORTH_FP64, sg.ORTH_TENSOR, sg.ORTH_AUTO):
-            X = np.zeros((n, 8), order="F")
-            st, info, rel = sg.block_solve(ctx, Ad, pc, 8, np.asfortranarray(w.B), n, X, n, 50, 1e-8, 20,
+            X = np.zeros((n, nrhs), order="F")
+            st, info, rel = sg.block_solve(ctx, Ad, pc, nrhs, np.asfortranarray(w.B), n, X, n, restart, 1e-8, 20,
                                            orth=orth)
             res[orth] = (X, info)
         sg.spai_pc_destroy(pc)
