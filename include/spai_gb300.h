@@ -321,6 +321,26 @@ typedef struct {
  * restart length m = restart (the context keeps it between calls; 0 for invalid sizes). */
 SPAI_API size_t spai_solve_workspace_size(int32_t n, int32_t s, int32_t restart);
 
+/* Solve nsys independent systems A_i X_i = B_i (s right-hand sides each) at once, each by
+ * the right-preconditioned block GMRES(m) of block_solve, all of them in lockstep: the
+ * matrix and preconditioner products run on the block-diagonal union of the systems, the
+ * Gram-Schmidt products, Cholesky-QR and projected least squares per system (segmented
+ * reductions, one CTA per system for the small blocks), and one read-back per Arnoldi step
+ * covers every system's convergence test -- so the launches and synchronisations of a
+ * step do not grow with nsys.  A system whose columns have converged keeps iterating with
+ * the others (each step can only lower its residual) until all have, or max_cycles runs
+ * out.  A[i]: DEVICE CSR (n_i >= 1, sum of n_i and of nnz below 2^31); P: NULL (no
+ * preconditioner) or nsys handles whose chains have the same depth, each level of the
+ * same kind (full or diagonal) and precision in every system; B[i], X[i]: DEVICE arrays
+ * (host array of device pointers), n_i x s column-major, leading dimension n_i; X[i]
+ * holds the initial guess on entry.  info: nsys entries (iterations = Arnoldi steps until
+ * the system's own estimate met tol; cycles = the cycle after which its true residual did).
+ * Orthogonalisation in FP64 (opts->orth ignored).  1 <= nsys <= 65536.  Synchronises.
+ * Returns SPAI_ENOTCONV if some system did not converge. */
+SPAI_API spai_status block_solve_batch(spai_ctx ctx, int32_t nsys, const spai_csr *A, const spai_pc *P, int32_t s,
+                                       const double *const *B, double *const *X, const spai_solve_opts *opts,
+                                       spai_solve_info *info);
+
 /* Solve A X = B for s right-hand sides at once.  P may be NULL (no preconditioner).
  * B (n x s, ldb) and X (n x s, ldx) may be HOST or DEVICE memory; X holds the initial
  * guess on entry and the solution on return.  rel_residual: HOST array of s doubles

@@ -22,7 +22,7 @@ __all__ = [
     "spai_ctx_mem_in_use", "spai_launch_count", "spai_ctx_profile", "spai_ctx_profile_count", "spai_measure_fp64_rate",
     "spai_ctx_profile_entry", "spai_affine_create", "spai_affine_pattern",
     "spai_assemble", "spai_affine_export", "spai_affine_destroy", "spai_build", "spai_update", "spai_pc_info",
-    "spai_pc_export", "spai_pc_destroy", "spai_build_batch", "spai_spmm", "spai_pc_apply", "block_solve",
+    "spai_pc_export", "spai_pc_destroy", "spai_build_batch", "block_solve_batch", "spai_spmm", "spai_pc_apply", "block_solve",
     "affine_coefficients", "PATTERN_A", "PATTERN_A2", "UPDATE_FIRST", "UPDATE_CHAINED", "UPDATE_DIAGONAL", "PREC_FP32", "PREC_BF16",
     "LIB_PATH", "spai_ctx_trim", "spai_solve_workspace_size", "spai_pc_mem_size",
     "spai_server_opts", "spai_request", "spai_result", "spai_server_stats", "spai_server_create",
@@ -150,6 +150,8 @@ def lib():
                               P(spai_solve_info), P(dbl)]),
         "spai_ctx_trim": (i32, [vp]),
         "spai_build_batch": (i32, [vp, i32, P(spai_csr), P(i32), P(vp)]),
+        "block_solve_batch": (i32, [vp, i32, P(spai_csr), P(vp), i32, P(vp), P(vp), P(spai_solve_opts),
+                                    P(spai_solve_info)]),
         "spai_solve_workspace_size": (sz, [i32, i32, i32]),
         "spai_pc_mem_size": (sz, [vp, i32]),
         "spai_server_create": (i32, [P(spai_server_opts), P(vp)]),
@@ -478,3 +480,22 @@ def spai_server_last_error(srv):
 
 def spai_server_destroy(srv):
     return _server_check(None, lib().spai_server_destroy(srv))
+
+
+def block_solve_batch(ctx, As, Ps, s, Bs, Xs, restart, tol, max_cycles, allow_notconv=False):
+    """Solve the systems As[i] X_i = Bs[i] (device, column-major n_i x s) at once in lockstep.
+    Ps: list of handles or None.  Xs hold the initial guesses and receive the solutions.
+    Returns (status, list of info dicts)."""
+    m = len(As)
+    arr = (spai_csr * m)(*As)
+    pcs = (C.c_void_p * m)(*[p.value if hasattr(p, "value") else p for p in Ps]) if Ps is not None else None
+    bp = (C.c_void_p * m)(*[_ptr(b) for b in Bs])
+    xp = (C.c_void_p * m)(*[_ptr(x) for x in Xs])
+    opts = spai_solve_opts(int(restart), int(max_cycles), float(tol), 0, 0)
+    infos = (spai_solve_info * m)()
+    st = lib().block_solve_batch(ctx, m, arr, pcs, int(s), bp, xp, C.byref(opts), infos)
+    result = (st, [infos[i].as_dict() for i in range(m)])
+    if st == SPAI_ENOTCONV and not allow_notconv:
+        raise SpaiError(st, spai_last_error(ctx), result)
+    _check(ctx, st, allow=(SPAI_ENOTCONV,))
+    return result

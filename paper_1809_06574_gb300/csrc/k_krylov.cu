@@ -201,8 +201,8 @@ __global__ void __launch_bounds__(kThreads) k_block_update(int32_t n, int nblk,
 // d_k <= 1e-15 * G_kk, or d_k <= 0 marks column k as deflated: row k of R = 0.
 // ---------------------------------------------------------------------------------
 template <int S>
-__global__ void k_chol_small(const double *__restrict__ G, const double *__restrict__ ref2,
-                             double tau2, double *__restrict__ R, int32_t *__restrict__ deflated)
+__device__ __forceinline__ void chol_small_body(const double *__restrict__ G, const double *__restrict__ ref2,
+                                                double tau2, double *__restrict__ R, int32_t *__restrict__ deflated)
 {
     __shared__ double A[S][S];
     __shared__ double Rs[S][S];
@@ -231,6 +231,22 @@ __global__ void k_chol_small(const double *__restrict__ G, const double *__restr
     }
     if (lane < S)
         for (int i = 0; i < S; ++i) R[i * S + lane] = Rs[i][lane];
+}
+
+template <int S>
+__global__ void k_chol_small(const double *__restrict__ G, const double *__restrict__ ref2, double tau2,
+                             double *__restrict__ R, int32_t *__restrict__ deflated)
+{
+    chol_small_body<S>(G, ref2, tau2, R, deflated);
+}
+
+// one CTA per system of a batch: system b's blocks at b times the strides
+template <int S>
+__global__ void k_chol_small_b(const double *__restrict__ G, const double *__restrict__ ref2, double tau2,
+                               double *__restrict__ R, int32_t *__restrict__ deflated)
+{
+    const int64_t b = blockIdx.x;
+    chol_small_body<S>(G + b * S * S, ref2 ? ref2 + b * S : nullptr, tau2, R + b * S * S, deflated + b * S);
 }
 
 // out[r] = W[r] R^{-1} (R upper triangular, deflated columns -> 0); thread per row; out
@@ -266,9 +282,9 @@ __global__ void __launch_bounds__(kThreads) k_trsm_rows(int32_t n, const double 
 //   k_trsm_gram:  Q1 = W R^{-1} written, and partial[chunk] of G2 = Q1^T Q1, one pass
 // ---------------------------------------------------------------------------------
 template <int S, bool SOLVE>
-__device__ __forceinline__ void gram_tiles(int32_t n, const double *__restrict__ W, const double *Rs,
+__device__ __forceinline__ void gram_tiles(int64_t r0, int64_t r1, const double *__restrict__ W, const double *Rs,
                                            const double *rinv, double *__restrict__ Q1,
-                                           double *__restrict__ partial)
+                                           double *__restrict__ partial_chunk)
 {
     constexpr int NP = S * (S + 1) / 2;
     constexpr int RG = kThreads / NP;
@@ -279,8 +295,6 @@ __device__ __forceinline__ void gram_tiles(int32_t n, const double *__restrict__
     int a = 0, rem = p;
     while (rem >= S - a) { rem -= S - a; ++a; }
     const int b = a + rem;
-    int64_t r0, r1;
-    chunk_rows(n, blockIdx.x, gridDim.x, r0, r1);
     double acc0 = 0.0, acc1 = 0.0;
     for (int64_t t0 = r0; t0 < r1; t0 += kThreads) {
         const int rows = (int)((r1 - t0) < kThreads ? (r1 - t0) : kThreads);
@@ -310,8 +324,8 @@ __device__ __forceinline__ void gram_tiles(int32_t n, const double *__restrict__
     if (g == 0) {
         double acc = red[p];
         for (int h = 1; h < RG; ++h) acc += red[h * NP + p];
-        partial[(int64_t)blockIdx.x * S * S + a * S + b] = acc;
-        partial[(int64_t)blockIdx.x * S * S + b * S + a] = acc;
+        partial_chunk[a * S + b] = acc;
+        partial_chunk[b * S + a] = acc;
     }
 }
 
@@ -319,7 +333,9 @@ template <int S>
 __global__ void __launch_bounds__(kThreads) k_gram_rows(int32_t n, const double *__restrict__ W,
                                                         double *__restrict__ partial)
 {
-    gram_tiles<S, false>(n, W, nullptr, nullptr, nullptr, partial);
+    int64_t r0, r1;
+    chunk_rows(n, blockIdx.x, gridDim.x, r0, r1);
+    gram_tiles<S, false>(r0, r1, W, nullptr, nullptr, nullptr, partial + (int64_t)blockIdx.x * S * S);
 }
 
 template <int S>
@@ -334,7 +350,157 @@ __global__ void __launch_bounds__(kThreads) k_trsm_gram(int32_t n, const double 
     if (threadIdx.x < S)
         rinv[threadIdx.x] = deflated[threadIdx.x] ? 0.0 : 1.0 / R[threadIdx.x * S + threadIdx.x];
     __syncthreads();
-    gram_tiles<S, true>(n, W, Rs, rinv, Q1, partial);
+    int64_t r0, r1;
+    chunk_rows(n, blockIdx.x, gridDim.x, r0, r1);
+    gram_tiles<S, true>(r0, r1, W, Rs, rinv, Q1, partial + (int64_t)blockIdx.x * S * S);
+}
+
+// ---------------------------------------------------------------------------------
+// Batches of independent systems stacked row-wise (system b owns a contiguous row range
+// of every n_tot x S block).  Row chunks never straddle two systems: chunk c covers rows
+// [r0[c], r1[c]) of system sys[c], the chunks of system b are c0[b] .. c0[b+1] - 1, and
+// partial sums per chunk are added per system in chunk order (deterministic).  One block
+// per chunk.
+// ---------------------------------------------------------------------------------
+template <int S>
+__global__ void k_colnorm2_seg(const double *__restrict__ W, SegChunks sc, double *__restrict__ partial)
+{
+    constexpr int RG = kThreads / S;
+    __shared__ double red[kThreads];
+    const int c = threadIdx.x % S, g = threadIdx.x / S;
+    const int64_t r0 = sc.r0[blockIdx.x], r1 = sc.r1[blockIdx.x];
+    double acc = 0.0;
+    for (int64_t r = r0 + g; r < r1; r += RG) {
+        const double w = W[r * S + c];
+        acc = fma(w, w, acc);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = RG / 2; h > 0; h >>= 1) {
+        if (g < h) red[threadIdx.x] += red[threadIdx.x + h * S];
+        __syncthreads();
+    }
+    if (g == 0) partial[(int64_t)blockIdx.x * S + c] = red[c];
+}
+
+// out[b * ostride + p] = sum over the chunks of system b of partial[chunk * count + p]:
+// one warp per (b, p), lanes over the chunks in order, then a fixed butterfly
+__global__ void k_reduce_seg(int32_t count, SegChunks sc, const double *__restrict__ partial, double *__restrict__ out,
+                             int64_t ostride)
+{
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= (int64_t)sc.nsys * count) return;
+    const int b = (int)(w / count), p = (int)(w % count);
+    double acc = 0.0;
+    for (int c = sc.c0[b] + lane; c < sc.c0[b + 1]; c += 32) acc += partial[(int64_t)c * count + p];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[b * ostride + p] = acc;
+}
+
+// partial[chunk][i][a][b] of H_i = V_i^T W for every system; grid (chunks, nblk)
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_block_dot_seg(int64_t ntot, const double *__restrict__ V,
+                                                            const double *__restrict__ W, SegChunks sc,
+                                                            double *__restrict__ partial, int nblk)
+{
+    constexpr int P = S * S;
+    constexpr int RG = kThreads / P >= 1 ? kThreads / P : 1;
+    __shared__ double red[kThreads];
+    const int i = blockIdx.y;
+    const int p = threadIdx.x % P, g = threadIdx.x / P;
+    const int a = p / S, b = p % S;
+    const double *Vi = V + (int64_t)i * ntot * S;
+    const int64_t r0 = sc.r0[blockIdx.x], r1 = sc.r1[blockIdx.x];
+    double acc0 = 0.0, acc1 = 0.0;
+    if (g < RG) {
+        int64_t r = r0 + g;
+        for (; r + RG < r1; r += 2 * RG) {
+            acc0 = fma(__ldg(Vi + r * S + a), __ldg(W + r * S + b), acc0);
+            acc1 = fma(__ldg(Vi + (r + RG) * S + a), __ldg(W + (r + RG) * S + b), acc1);
+        }
+        if (r < r1) acc0 = fma(__ldg(Vi + r * S + a), __ldg(W + r * S + b), acc0);
+    }
+    red[threadIdx.x] = acc0 + acc1;
+    __syncthreads();
+    if (g == 0 && p < P) {
+        double acc = red[p];
+        for (int h = 1; h < RG; ++h) acc += red[h * P + p];
+        partial[((int64_t)blockIdx.x * nblk + i) * P + p] = acc;
+    }
+}
+
+// out = base + sign * sum_i V_i H_i with each row's own system's H (H + b * hstride)
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_block_update_seg(int64_t ntot, int nblk, const double *__restrict__ V,
+                                                               const double *__restrict__ H, int64_t hstride,
+                                                               const double *base, double *out, double sign,
+                                                               SegChunks sc)
+{
+    const int64_t r0 = sc.r0[blockIdx.x], r1 = sc.r1[blockIdx.x];
+    const double *Hs = H + (int64_t)sc.sys[blockIdx.x] * hstride;
+    for (int64_t g = threadIdx.x; g < (r1 - r0) * S; g += blockDim.x) {
+        const int64_t r = r0 + g / S;
+        const int b = (int)(g % S);
+        double acc = 0.0;
+        for (int i = 0; i < nblk; ++i) {
+            const double *vr = V + ((int64_t)i * ntot + r) * S;
+            const double *hi = Hs + (int64_t)i * S * S;
+#pragma unroll
+            for (int a = 0; a < S; ++a) acc = fma(__ldg(vr + a), __ldg(hi + a * S + b), acc);
+        }
+        double o = sign * acc;
+        if (base) o += base[r * S + b];
+        out[r * S + b] = o;
+    }
+}
+
+template <int S>
+__device__ __forceinline__ void load_r(const double *R, const int32_t *deflated, double *Rs, double *rinv)
+{
+    for (int e = threadIdx.x; e < S * S; e += blockDim.x) Rs[e] = R[e];
+    if (threadIdx.x < S) rinv[threadIdx.x] = deflated[threadIdx.x] ? 0.0 : 1.0 / R[threadIdx.x * S + threadIdx.x];
+    __syncthreads();
+}
+
+// Cholesky-QR pieces per system: G = W^T W; Q1 = W R^{-1} with G2 = Q1^T Q1; out = W R^{-1}
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_gram_seg(const double *__restrict__ W, SegChunks sc,
+                                                       double *__restrict__ partial)
+{
+    gram_tiles<S, false>(sc.r0[blockIdx.x], sc.r1[blockIdx.x], W, nullptr, nullptr, nullptr,
+                         partial + (int64_t)blockIdx.x * S * S);
+}
+
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_trsm_gram_seg(const double *__restrict__ W, const double *__restrict__ R,
+                                                            const int32_t *__restrict__ deflated,
+                                                            double *__restrict__ Q1, SegChunks sc,
+                                                            double *__restrict__ partial)
+{
+    __shared__ double Rs[S * S];
+    __shared__ double rinv[S];
+    const int64_t b = sc.sys[blockIdx.x];
+    load_r<S>(R + b * S * S, deflated + b * S, Rs, rinv);
+    gram_tiles<S, true>(sc.r0[blockIdx.x], sc.r1[blockIdx.x], W, Rs, rinv, Q1, partial + (int64_t)blockIdx.x * S * S);
+}
+
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_trsm_rows_seg(const double *W, const double *__restrict__ R,
+                                                            const int32_t *__restrict__ deflated, double *out,
+                                                            SegChunks sc)
+{
+    __shared__ double Rs[S * S];
+    __shared__ double rinv[S];
+    const int64_t b = sc.sys[blockIdx.x];
+    load_r<S>(R + b * S * S, deflated + b * S, Rs, rinv);
+    for (int64_t r = sc.r0[blockIdx.x] + threadIdx.x; r < sc.r1[blockIdx.x]; r += blockDim.x) {
+        double x[S];
+        row_load<S>(W, r, x);
+        trsm_row<S>(x, Rs, rinv);
+        row_store<S>(out, r, x);
+    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -369,14 +535,27 @@ __global__ void k_pieces16(int32_t nb, double *__restrict__ H, double *__restric
 }
 
 template <int S>
-__global__ void k_triu_mul(const double *__restrict__ R2, const double *__restrict__ R1,
-                           double *__restrict__ out)
+__device__ __forceinline__ void triu_mul_body(const double *__restrict__ R2, const double *__restrict__ R1,
+                                              double *__restrict__ out)
 {
     const int a = threadIdx.x / S, b = threadIdx.x % S;
     if (threadIdx.x >= S * S) return;
     double acc = 0.0;
     for (int c = a; c <= b; ++c) acc = fma(R2[a * S + c], R1[c * S + b], acc);
     out[a * S + b] = acc;
+}
+
+template <int S>
+__global__ void k_triu_mul(const double *__restrict__ R2, const double *__restrict__ R1, double *__restrict__ out)
+{
+    triu_mul_body<S>(R2, R1, out);
+}
+
+template <int S>
+__global__ void k_triu_mul_b(const double *__restrict__ R2, const double *__restrict__ R1, double *__restrict__ out)
+{
+    const int64_t b = blockIdx.x;
+    triu_mul_body<S>(R2 + b * S * S, R1 + b * S * S, out + b * S * S);
 }
 
 // ---------------------------------------------------------------------------------
@@ -408,11 +587,11 @@ struct LsCfg {
 };
 
 template <int S>
-__global__ void __launch_bounds__(LsCfg<S>::NT)
-    k_arnoldi_ls(int32_t j, int32_t m, const double *__restrict__ H1, const double *__restrict__ H2,
-                 const double *__restrict__ Rsub, double *__restrict__ Qs, double *__restrict__ Rtri,
-                 double *__restrict__ G, const double *__restrict__ thresh, double *__restrict__ est,
-                 int32_t *__restrict__ flag)
+__device__ __forceinline__ void arnoldi_ls_body(int32_t j, int32_t m, const double *__restrict__ H1,
+                                                const double *__restrict__ H2, const double *__restrict__ Rsub,
+                                                double *__restrict__ Qs, double *__restrict__ Rtri,
+                                                double *__restrict__ G, const double *__restrict__ thresh,
+                                                double *__restrict__ est, int32_t *__restrict__ flag)
 {
     using C = LsCfg<S>;
     constexpr int S2 = C::S2, NC = C::NC, TPC = C::TPC, RPT = C::RPT;
@@ -541,6 +720,32 @@ __global__ void __launch_bounds__(LsCfg<S>::NT)
     }
 }
 
+template <int S>
+__global__ void __launch_bounds__(LsCfg<S>::NT)
+    k_arnoldi_ls(int32_t j, int32_t m, const double *__restrict__ H1, const double *__restrict__ H2,
+                 const double *__restrict__ Rsub, double *__restrict__ Qs, double *__restrict__ Rtri,
+                 double *__restrict__ G, const double *__restrict__ thresh, double *__restrict__ est,
+                 int32_t *__restrict__ flag)
+{
+    arnoldi_ls_body<S>(j, m, H1, H2, Rsub, Qs, Rtri, G, thresh, est, flag);
+}
+
+// one CTA per system; per-system strides follow from m and S
+template <int S>
+__global__ void __launch_bounds__(LsCfg<S>::NT)
+    k_arnoldi_ls_b(int32_t j, int32_t m, const double *__restrict__ H1, const double *__restrict__ H2,
+                   const double *__restrict__ Rsub, double *__restrict__ Qs, double *__restrict__ Rtri,
+                   double *__restrict__ G, const double *__restrict__ thresh, double *__restrict__ est,
+                   int32_t *__restrict__ flag)
+{
+    const int64_t b = blockIdx.x;
+    const int64_t hs = (int64_t)(m + 1) * S * S;
+    const int64_t qs = (int64_t)m * 4 * S * S;
+    const int64_t rs = (int64_t)(m + 1) * S * m * S;
+    arnoldi_ls_body<S>(j, m, H1 + b * hs, H2 ? H2 + b * hs : nullptr, Rsub + b * S * S, Qs + b * qs, Rtri + b * rs,
+                       G + b * hs, thresh + b * S, est + b * S, flag + b);
+}
+
 // G = 0; G[0:S] = S0 (S x S row-major)
 template <int S>
 __global__ void k_set_rhs(int32_t m, const double *__restrict__ S0, double *__restrict__ G)
@@ -550,11 +755,20 @@ __global__ void k_set_rhs(int32_t m, const double *__restrict__ S0, double *__re
         G[e] = (e < S * S) ? S0[e] : 0.0;
 }
 
+template <int S>
+__global__ void k_set_rhs_b(int32_t m, const double *__restrict__ S0, double *__restrict__ G)
+{
+    const int64_t b = blockIdx.x;
+    const int count = (m + 1) * S * S;
+    for (int e = threadIdx.x; e < count; e += blockDim.x)
+        G[b * count + e] = (e < S * S) ? S0[b * S * S + e] : 0.0;
+}
+
 // Solve R Y = G[0:JS] (R = Rtri, upper, column-major ld); zero diagonal -> y = 0.
 // One CTA; Y row-major (JS x S).
 template <int S>
-__global__ void k_backsolve(int32_t J, int32_t ldr, const double *__restrict__ Rtri,
-                            const double *__restrict__ G, double *__restrict__ Y)
+__device__ __forceinline__ void backsolve_body(int32_t J, int32_t ldr, const double *__restrict__ Rtri,
+                                               const double *__restrict__ G, double *__restrict__ Y)
 {
     const int N = J * S;
     __shared__ double yc[S];
@@ -574,6 +788,24 @@ __global__ void k_backsolve(int32_t J, int32_t ldr, const double *__restrict__ R
         }
         __syncthreads();
     }
+}
+
+template <int S>
+__global__ void k_backsolve(int32_t J, int32_t ldr, const double *__restrict__ Rtri, const double *__restrict__ G,
+                            double *__restrict__ Y)
+{
+    backsolve_body<S>(J, ldr, Rtri, G, Y);
+}
+
+// one CTA per system (m: restart length, for the per-system strides)
+template <int S>
+__global__ void k_backsolve_b(int32_t J, int32_t m, const double *__restrict__ Rtri, const double *__restrict__ G,
+                              double *__restrict__ Y)
+{
+    const int64_t b = blockIdx.x;
+    const int ldr = (m + 1) * S;
+    backsolve_body<S>(J, ldr, Rtri + b * (int64_t)(m + 1) * S * m * S, G + b * (int64_t)(m + 1) * S * S,
+                      Y + b * (int64_t)m * S * S);
 }
 
 __global__ void k_axpy(int64_t count, double alpha, const double *__restrict__ x,
@@ -712,6 +944,98 @@ int launch_trsm_gram(cudaStream_t st, int32_t s, int32_t n, const double *W, con
     const int count = s * s;
     k_reduce_chunks<<<(unsigned)(((int64_t)count * 32 + 255) / 256), 256, 0, st>>>(count, chunks, partial, G2);
     return check_launch(2);
+}
+
+// ---- batches of systems (segmented row chunks, one CTA per system for the small blocks)
+namespace {
+int reduce_seg(cudaStream_t st, int32_t count, const SegChunks &sc, const double *partial, double *out,
+               int64_t ostride)
+{
+    const int64_t warps = (int64_t)sc.nsys * count;
+    k_reduce_seg<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(count, sc, partial, out, ostride);
+    return 0;
+}
+}  // namespace
+
+int launch_colnorm2_seg(cudaStream_t st, int32_t s, const double *W, const SegChunks &sc, double *partial, double *out)
+{
+    SPAI_DISPATCH_S(s, (k_colnorm2_seg<S><<<sc.nchunks, kThreads, 0, st>>>(W, sc, partial)));
+    reduce_seg(st, s, sc, partial, out, s);
+    return check_launch(2);
+}
+
+int launch_block_dot_seg(cudaStream_t st, int32_t s, int64_t ntot, int32_t nblk, const double *V, const double *W,
+                         const SegChunks &sc, double *partial, double *out, int64_t ostride)
+{
+    dim3 grid(sc.nchunks, nblk);
+    SPAI_DISPATCH_S(s, (k_block_dot_seg<S><<<grid, kThreads, 0, st>>>(ntot, V, W, sc, partial, nblk)));
+    reduce_seg(st, nblk * s * s, sc, partial, out, ostride);
+    return check_launch(2);
+}
+
+int launch_block_update_seg(cudaStream_t st, int32_t s, int64_t ntot, int32_t nblk, const double *V, const double *H,
+                            int64_t hstride, const double *base, double *out, double sign, const SegChunks &sc)
+{
+    SPAI_DISPATCH_S(s, (k_block_update_seg<S><<<sc.nchunks, kThreads, 0, st>>>(ntot, nblk, V, H, hstride, base, out,
+                                                                               sign, sc)));
+    return check_launch();
+}
+
+int launch_gram_seg(cudaStream_t st, int32_t s, const double *W, const SegChunks &sc, double *partial, double *G)
+{
+    SPAI_DISPATCH_S(s, (k_gram_seg<S><<<sc.nchunks, kThreads, 0, st>>>(W, sc, partial)));
+    reduce_seg(st, s * s, sc, partial, G, (int64_t)s * s);
+    return check_launch(2);
+}
+
+int launch_trsm_gram_seg(cudaStream_t st, int32_t s, const double *W, const double *R, const int32_t *deflated,
+                         double *Q1, const SegChunks &sc, double *partial, double *G2)
+{
+    SPAI_DISPATCH_S(s, (k_trsm_gram_seg<S><<<sc.nchunks, kThreads, 0, st>>>(W, R, deflated, Q1, sc, partial)));
+    reduce_seg(st, s * s, sc, partial, G2, (int64_t)s * s);
+    return check_launch(2);
+}
+
+int launch_trsm_rows_seg(cudaStream_t st, int32_t s, const double *W, const double *R, const int32_t *deflated,
+                         double *out, const SegChunks &sc)
+{
+    SPAI_DISPATCH_S(s, (k_trsm_rows_seg<S><<<sc.nchunks, kThreads, 0, st>>>(W, R, deflated, out, sc)));
+    return check_launch();
+}
+
+int launch_chol_small_b(cudaStream_t st, int32_t s, int32_t nsys, const double *G, const double *ref2, double tau2,
+                        double *R, int32_t *deflated)
+{
+    SPAI_DISPATCH_S(s, (k_chol_small_b<S><<<nsys, 32, 0, st>>>(G, ref2, tau2, R, deflated)));
+    return check_launch();
+}
+
+int launch_triu_mul_b(cudaStream_t st, int32_t s, int32_t nsys, const double *R2, const double *R1, double *out)
+{
+    SPAI_DISPATCH_S(s, (k_triu_mul_b<S><<<nsys, S * S < 32 ? 32 : S * S, 0, st>>>(R2, R1, out)));
+    return check_launch();
+}
+
+int launch_arnoldi_ls_b(cudaStream_t st, int32_t s, int32_t nsys, int32_t j, int32_t m, const double *H1,
+                        const double *H2, const double *Rsub, double *Qs, double *Rtri, double *G, const double *thresh,
+                        double *est, int32_t *flag)
+{
+    SPAI_DISPATCH_S(s, (k_arnoldi_ls_b<S><<<nsys, LsCfg<S>::NT, 0, st>>>(j, m, H1, H2, Rsub, Qs, Rtri, G, thresh, est,
+                                                                         flag)));
+    return check_launch();
+}
+
+int launch_set_rhs_b(cudaStream_t st, int32_t s, int32_t nsys, int32_t m, const double *S0, double *G)
+{
+    SPAI_DISPATCH_S(s, (k_set_rhs_b<S><<<nsys, 256, 0, st>>>(m, S0, G)));
+    return check_launch();
+}
+
+int launch_backsolve_b(cudaStream_t st, int32_t s, int32_t nsys, int32_t J, int32_t m, const double *Rtri,
+                       const double *G, double *Y)
+{
+    SPAI_DISPATCH_S(s, (k_backsolve_b<S><<<nsys, 512, 0, st>>>(J, m, Rtri, G, Y)));
+    return check_launch();
 }
 
 int launch_reduce_chunks(cudaStream_t st, int32_t count, int chunks, const double *partial, double *out)

@@ -312,6 +312,13 @@ __global__ void k_gather_bf16_f64(int64_t count, const int32_t *__restrict__ idx
         dst[i] = (double)__bfloat162float(__ushort_as_bfloat16(src[idx ? idx[i] : i]));
 }
 
+__global__ void k_add_i32(int64_t count, const int32_t *__restrict__ src, int32_t add, int32_t *__restrict__ dst)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i] + add;
+}
+
 __global__ void k_iota_i32(int64_t count, int32_t *__restrict__ dst)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
@@ -548,6 +555,15 @@ int launch_gather_f32_f64(cudaStream_t st, int64_t count, const int32_t *idx, co
 {
     if (count <= 0) return 0;
     k_gather_f32_f64<<<grid_for(count), kThreads, 0, st>>>(count, idx, src, dst);
+    return check_launch();
+}
+
+int launch_add_i32(cudaStream_t st, int64_t count, const int32_t *src, int32_t add, int32_t *dst)
+{
+    if (count <= 0) return 0;
+    int g = grid_for(count);
+    if (g > 8192) g = 8192;
+    k_add_i32<<<g, kThreads, 0, st>>>(count, src, add, dst);
     return check_launch();
 }
 

@@ -1650,6 +1650,340 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
     return SPAI_OK;
 }
 
+// ===================================================================================
+// Batched block GMRES: many independent systems in lockstep
+// ===================================================================================
+namespace {
+
+// Device memory of one batched solve, released together.
+struct Allocs {
+    spai_ctx ctx;
+    std::vector<void *> ptrs;
+    explicit Allocs(spai_ctx c) : ctx(c) {}
+    ~Allocs()
+    {
+        for (void *p : ptrs) dfree(ctx, p);
+    }
+    template <class Tp>
+    spai_status get(Tp **p, int64_t count)
+    {
+        spai_status st = dalloc_n(ctx, p, count);
+        if (!st) ptrs.push_back((void *)*p);
+        return st;
+    }
+};
+
+// one level of the stacked preconditioner chain: the factors of every system at that depth
+struct StackedFactor {
+    bool diag = false;
+    int prec = 0;  // 0 FP64, 1 FP32, 2 BF16
+    int32_t *rowptr = nullptr, *colind = nullptr;
+    void *val = nullptr;
+    int64_t nnz = 0;
+};
+
+}  // namespace
+
+extern "C" spai_status block_solve_batch(spai_ctx ctx, int32_t nsys, const spai_csr *A, const spai_pc *P, int32_t s,
+                                         const double *const *B, double *const *X, const spai_solve_opts *opts,
+                                         spai_solve_info *info)
+{
+    if (!ctx) return SPAI_EINVAL;
+    if (!A || !B || !X || !opts || !info) return fail(ctx, SPAI_EINVAL, "NULL argument");
+    if (nsys < 1 || nsys > 65536) return fail(ctx, SPAI_EINVAL, "nsys must be in 1..65536");
+    if (!valid_s(s)) return fail(ctx, SPAI_EINVAL, "s must be 1, 2, 4, 8 or 16");
+    const int32_t m = opts->restart;
+    if (m < 1 || opts->max_cycles < 1 || !(opts->tol >= 0.0))
+        return fail(ctx, SPAI_EINVAL, "restart and max_cycles must be >= 1 and tol >= 0");
+    spai_status st;
+    std::vector<int64_t> off((size_t)nsys + 1, 0), nzoff((size_t)nsys + 1, 0);
+    int depth = -1;
+    for (int i = 0; i < nsys; ++i) {
+        if ((st = check_csr_args(ctx, &A[i], "A"))) return st;
+        if (A[i].n < 1) return fail(ctx, SPAI_EINVAL, "system %d is empty", i);
+        if (!is_device_ptr(A[i].rowptr) || !is_device_ptr(A[i].colind) || !is_device_ptr(A[i].val))
+            return fail(ctx, SPAI_EINVAL, "system %d: A arrays must be device memory", i);
+        if (!B[i] || !X[i] || !is_device_ptr(B[i]) || !is_device_ptr(X[i]))
+            return fail(ctx, SPAI_EINVAL, "system %d: B and X must be device memory", i);
+        off[i + 1] = off[i] + A[i].n;
+        nzoff[i + 1] = nzoff[i] + A[i].nnz;
+        const int d = P ? (P[i] ? P[i]->depth : -2) : -1;
+        if (P && (!P[i] || P[i]->sym->n != A[i].n))
+            return fail(ctx, SPAI_EINVAL, "system %d: preconditioner missing or of another size", i);
+        if (i == 0) depth = d;
+        else if (d != depth) return fail(ctx, SPAI_EINVAL, "all preconditioners must have the same depth");
+    }
+    if (off[nsys] >= INT32_MAX || nzoff[nsys] >= INT32_MAX)
+        return fail(ctx, SPAI_EINVAL, "the stacked batch exceeds 2^31 rows or nonzeros");
+    const int32_t ntot = (int32_t)off[nsys];
+    const int64_t nnz = nzoff[nsys];
+    memset(info, 0, sizeof(spai_solve_info) * (size_t)nsys);
+    cudaStream_t cs = ctx->stream;
+    Allocs al(ctx);
+
+    // ---- the block-diagonal union of the systems (CSR, global row and column indices)
+    int32_t *rp = nullptr, *ci = nullptr;
+    double *va = nullptr;
+    if ((st = al.get(&rp, (int64_t)ntot + 1)) || (st = al.get(&ci, nnz)) || (st = al.get(&va, nnz))) return st;
+    for (int i = 0; i < nsys; ++i) {
+        KL(launch_add_i32(cs, (int64_t)A[i].n + 1, A[i].rowptr, (int32_t)nzoff[i], rp + off[i]), "stack rows");
+        KL(launch_add_i32(cs, A[i].nnz, A[i].colind, (int32_t)off[i], ci + nzoff[i]), "stack columns");
+        if (A[i].nnz)
+            CU(cudaMemcpyAsync(va + nzoff[i], A[i].val, (size_t)A[i].nnz * 8, cudaMemcpyDeviceToDevice, cs), "stack");
+    }
+    // ---- the preconditioner chains, level by level from the root (P_l X = Q_l (P_1 X))
+    std::vector<StackedFactor> levels;
+    if (P) {
+        std::vector<std::vector<spai_pc>> chains((size_t)nsys);
+        for (int i = 0; i < nsys; ++i)
+            for (spai_pc p = P[i]; p; p = p->parent) chains[i].insert(chains[i].begin(), p);
+        const int L = (int)chains[0].size();
+        for (int l = 0; l < L; ++l) {
+            StackedFactor f;
+            const spai_pc h0 = chains[0][l];
+            f.diag = h0->diag;
+            f.prec = h0->fval16 ? 2 : h0->fval32 ? 1 : 0;
+            int64_t tot = 0;
+            std::vector<int64_t> foff((size_t)nsys + 1, 0);
+            for (int i = 0; i < nsys; ++i) {
+                const spai_pc h = chains[i][l];
+                if ((int)chains[i].size() != L || h->diag != f.diag || (h->fval16 ? 2 : h->fval32 ? 1 : 0) != f.prec)
+                    return fail(ctx, SPAI_EINVAL, "preconditioner level %d differs between systems (kind or precision)", l);
+                foff[i + 1] = foff[i] + (f.diag ? h->sym->n : h->sym->nnzP);
+            }
+            tot = foff[nsys];
+            if (tot >= INT32_MAX) return fail(ctx, SPAI_EINVAL, "the stacked preconditioner exceeds 2^31 entries");
+            f.nnz = tot;
+            const size_t vb = f.prec == 2 ? 2 : f.prec == 1 ? 4 : 8;
+            char *v = nullptr;
+            if ((st = al.get(&v, tot * (int64_t)vb))) return st;
+            f.val = v;
+            if (!f.diag && ((st = al.get(&f.rowptr, (int64_t)ntot + 1)) || (st = al.get(&f.colind, tot)))) return st;
+            for (int i = 0; i < nsys; ++i) {
+                const spai_pc h = chains[i][l];
+                const Sym *sy = h->sym;
+                const int64_t cnt = foff[i + 1] - foff[i];
+                const void *src = f.prec == 2 ? (const void *)h->fval16 : f.prec == 1 ? (const void *)h->fval32
+                                                                                      : (const void *)h->fval;
+                if (cnt) CU(cudaMemcpyAsync(v + foff[i] * vb, src, (size_t)cnt * vb, cudaMemcpyDeviceToDevice, cs), "stack");
+                if (!f.diag) {
+                    KL(launch_add_i32(cs, (int64_t)sy->n + 1, sy->p_rowptr, (int32_t)foff[i], f.rowptr + off[i]), "stack rows");
+                    KL(launch_add_i32(cs, sy->nnzP, sy->p_colind, (int32_t)off[i], f.colind + foff[i]), "stack columns");
+                }
+            }
+            levels.push_back(f);
+        }
+    }
+    // ---- row chunks that never straddle two systems
+    constexpr int64_t kChunkRows = 1024;
+    std::vector<int32_t> csys, c0((size_t)nsys + 1, 0);
+    std::vector<int64_t> cr0, cr1;
+    for (int i = 0; i < nsys; ++i) {
+        c0[i] = (int32_t)csys.size();
+        for (int64_t r = off[i]; r < off[i + 1]; r += kChunkRows) {
+            csys.push_back(i);
+            cr0.push_back(r);
+            cr1.push_back(std::min(r + kChunkRows, off[i + 1]));
+        }
+    }
+    c0[nsys] = (int32_t)csys.size();
+    const int32_t nch = (int32_t)csys.size();
+    int32_t *d_csys = nullptr, *d_c0 = nullptr;
+    int64_t *d_r0 = nullptr, *d_r1 = nullptr;
+    if ((st = al.get(&d_csys, nch)) || (st = al.get(&d_c0, (int64_t)nsys + 1)) || (st = al.get(&d_r0, nch)) ||
+        (st = al.get(&d_r1, nch)))
+        return st;
+    CU(cudaMemcpyAsync(d_csys, csys.data(), (size_t)nch * 4, cudaMemcpyHostToDevice, cs), "chunks");
+    CU(cudaMemcpyAsync(d_c0, c0.data(), ((size_t)nsys + 1) * 4, cudaMemcpyHostToDevice, cs), "chunks");
+    CU(cudaMemcpyAsync(d_r0, cr0.data(), (size_t)nch * 8, cudaMemcpyHostToDevice, cs), "chunks");
+    CU(cudaMemcpyAsync(d_r1, cr1.data(), (size_t)nch * 8, cudaMemcpyHostToDevice, cs), "chunks");
+    const SegChunks sc{d_csys, d_r0, d_r1, d_c0, nch, nsys};
+
+    // ---- workspace: n_tot x s blocks, the basis, and every system's small blocks
+    const int64_t blk = (int64_t)ntot * s, ss = (int64_t)s * s;
+    double *Bw, *Xw, *W, *Z, *T0, *T1, *V, *partial;
+    double *H1, *H2, *G1, *R1, *R2, *Rn, *ref2, *thresh, *Qs, *Rtri, *Gv, *Y, *est;
+    int32_t *defl1, *defl2, *flag;
+    if ((st = al.get(&Bw, blk)) || (st = al.get(&Xw, blk)) || (st = al.get(&W, blk)) || (st = al.get(&Z, blk)) ||
+        (st = al.get(&T0, blk)) || (st = al.get(&T1, blk)) || (st = al.get(&V, blk * (m + 1))) ||
+        (st = al.get(&partial, (int64_t)nch * std::max<int64_t>((int64_t)(m + 1) * ss, s))) ||
+        (st = al.get(&H1, nsys * (m + 1) * ss)) || (st = al.get(&H2, nsys * (m + 1) * ss)) ||
+        (st = al.get(&G1, nsys * ss)) || (st = al.get(&R1, nsys * ss)) || (st = al.get(&R2, nsys * ss)) ||
+        (st = al.get(&Rn, nsys * ss)) || (st = al.get(&ref2, (int64_t)nsys * s)) ||
+        (st = al.get(&thresh, (int64_t)nsys * s)) || (st = al.get(&Qs, nsys * (int64_t)m * 4 * ss)) ||
+        (st = al.get(&Rtri, nsys * (int64_t)(m + 1) * s * m * s)) || (st = al.get(&Gv, nsys * (m + 1) * ss)) ||
+        (st = al.get(&Y, nsys * (int64_t)m * ss)) || (st = al.get(&est, (int64_t)nsys * s)) ||
+        (st = al.get(&defl1, (int64_t)nsys * s)) || (st = al.get(&defl2, (int64_t)nsys * s)) ||
+        (st = al.get(&flag, nsys)))
+        return st;
+
+    // Y = P X through the stacked chain (T0 / T1 between levels)
+    auto apply_P = [&](const double *Xin, double *Yout) -> spai_status {
+        const double *cur = Xin;
+        for (size_t l = 0; l < levels.size(); ++l) {
+            const StackedFactor &f = levels[l];
+            double *dst = (l + 1 == levels.size()) ? Yout : ((l & 1) ? T1 : T0);
+            const double fl = 2.0 * (double)f.nnz * s;
+            if (f.diag) {
+                PKL("scale_rows", (double)ntot * s, 8.0 * ntot + 16.0 * blk,
+                    launch_scale_rows(cs, s, ntot, f.prec == 0 ? (const double *)f.val : nullptr,
+                                      f.prec == 1 ? (const float *)f.val : nullptr,
+                                      f.prec == 2 ? (const uint16_t *)f.val : nullptr, cur, dst),
+                    "diagonal factor apply");
+            } else if (f.prec == 2) {
+                PKL("spmm_P", fl, 6.0 * f.nnz + 4.0 * (ntot + 1) + 16.0 * blk,
+                    launch_spmm_bf16v(cs, s, ntot, f.rowptr, f.colind, (const uint16_t *)f.val, cur, dst), "apply");
+            } else if (f.prec == 1) {
+                PKL("spmm_P", fl, 8.0 * f.nnz + 4.0 * (ntot + 1) + 16.0 * blk,
+                    launch_spmm_f32v(cs, s, ntot, f.rowptr, f.colind, (const float *)f.val, cur, dst), "apply");
+            } else {
+                PKL("spmm_P", fl, 12.0 * f.nnz + 4.0 * (ntot + 1) + 16.0 * blk,
+                    launch_spmm(cs, s, ntot, f.rowptr, f.colind, (const double *)f.val, cur, dst), "apply");
+            }
+            cur = dst;
+        }
+        return SPAI_OK;
+    };
+    // W = Q R per system, two passes of Cholesky QR (the block_solve sequence, per system)
+    auto cholqr2_b = [&](const double *Win, double *Qout) -> spai_status {
+        const double nsd = (double)blk;
+        PKL("gram", nsd * (s + 1), 8.0 * nsd, launch_gram_seg(cs, s, Win, sc, partial, G1), "gram");
+        PKL("small_dense", 0.0, 0.0, launch_chol_small_b(cs, s, nsys, G1, ref2, 1e-24, R1, defl1), "chol");
+        PKL("trsm_gram", nsd * s + nsd * (s + 1), 16.0 * nsd,
+            launch_trsm_gram_seg(cs, s, Win, R1, defl1, Qout, sc, partial, G1), "trsm gram");
+        PKL("small_dense", 0.0, 0.0, launch_chol_small_b(cs, s, nsys, G1, nullptr, 0.0, R2, defl2), "chol");
+        PKL("trsm_rows", nsd * s, 16.0 * nsd, launch_trsm_rows_seg(cs, s, Qout, R2, defl2, Qout, sc), "trsm");
+        PKL("small_dense", 0.0, 0.0, launch_triu_mul_b(cs, s, nsys, R2, R1, Rn), "triu");
+        return SPAI_OK;
+    };
+
+    // inputs -> stacked row-major blocks
+    for (int i = 0; i < nsys; ++i) {
+        KL(launch_pack(cs, s, A[i].n, B[i], A[i].n, Bw + off[i] * s), "pack B");
+        KL(launch_pack(cs, s, A[i].n, X[i], A[i].n, Xw + off[i] * s), "pack X");
+    }
+    std::vector<double> hb((size_t)nsys * s), hr((size_t)nsys * s), bnorm((size_t)nsys * s), th((size_t)nsys * s);
+    std::vector<int32_t> hflag((size_t)nsys);
+    KL(launch_colnorm2_seg(cs, s, Bw, sc, partial, ref2), "norm B");
+    CU(cudaMemcpyAsync(hb.data(), ref2, hb.size() * 8, cudaMemcpyDeviceToHost, cs), "read norms");
+    CU(cudaStreamSynchronize(cs), "sync");
+    for (size_t k = 0; k < hb.size(); ++k) {
+        bnorm[k] = sqrt(hb[k]);
+        th[k] = opts->tol * bnorm[k];
+    }
+    CU(cudaMemcpyAsync(thresh, th.data(), th.size() * 8, cudaMemcpyHostToDevice, cs), "thresholds");
+    CU(cudaStreamSynchronize(cs), "sync");  // th is read by the copy above
+    auto residual = [&]() -> spai_status {
+        PKL("residual", 2.0 * nnz * s + blk, 12.0 * nnz + 4.0 * (ntot + 1) + 24.0 * blk,
+            launch_residual(cs, s, ntot, rp, ci, va, Xw, Bw, W), "residual");
+        PKL("colnorm2", 2.0 * blk, 8.0 * blk, launch_colnorm2_seg(cs, s, W, sc, partial, ref2), "residual norms");
+        CU(cudaMemcpyAsync(hr.data(), ref2, hr.size() * 8, cudaMemcpyDeviceToHost, cs), "read norms");
+        CU(cudaStreamSynchronize(cs), "sync");
+        return SPAI_OK;
+    };
+    auto sys_converged = [&](int i) {
+        for (int c = 0; c < s; ++c)
+            if (!(sqrt(hr[(size_t)i * s + c]) <= th[(size_t)i * s + c])) return false;
+        return true;
+    };
+    auto all_converged = [&]() {
+        for (int i = 0; i < nsys; ++i)
+            if (!sys_converged(i)) return false;
+        return true;
+    };
+    if ((st = residual())) return st;
+    // per system: the cycle after which its true residual met tol (0: at the start), and
+    // the Arnoldi steps up to the step whose estimate met tol in that cycle
+    std::vector<int> conv_cycle((size_t)nsys, -1), done_it((size_t)nsys, -1);
+    int cycles = 0, iters = 0;
+    for (int i = 0; i < nsys; ++i)
+        if (sys_converged(i)) conv_cycle[i] = 0, done_it[i] = 0;
+    while (!all_converged() && cycles < opts->max_cycles) {
+        ++cycles;
+        if ((st = cholqr2_b(W, V))) return st;
+        PKL("small_dense", 0.0, 0.0, launch_set_rhs_b(cs, s, nsys, m, Rn, Gv), "rhs");
+        int J = 0;
+        for (int j = 0; j < m; ++j) {
+            const double *Vj = V + (int64_t)j * blk;
+            const double *Zj = Vj;
+            if (!levels.empty()) {
+                if ((st = apply_P(Vj, Z))) return st;
+                Zj = Z;
+            }
+            PKL("spmm_A", 2.0 * nnz * s, 12.0 * nnz + 4.0 * (ntot + 1) + 16.0 * blk,
+                launch_spmm(cs, s, ntot, rp, ci, va, Zj, W), "A Z");
+            PKL("colnorm2", 2.0 * blk, 8.0 * blk, launch_colnorm2_seg(cs, s, W, sc, partial, ref2), "norms");
+            const double nb = j + 1, f = 2.0 * blk * s * nb, by = 8.0 * blk * (nb + 1);
+            const int64_t hs = (int64_t)(m + 1) * ss;
+            PKL("block_dot", f, by, launch_block_dot_seg(cs, s, ntot, j + 1, V, W, sc, partial, H1, hs), "H1");
+            PKL("block_update", f, 8.0 * blk * (nb + 2),
+                launch_block_update_seg(cs, s, ntot, j + 1, V, H1, hs, W, W, -1.0, sc), "update");
+            PKL("block_dot", f, by, launch_block_dot_seg(cs, s, ntot, j + 1, V, W, sc, partial, H2, hs), "H2");
+            PKL("block_update", f, 8.0 * blk * (nb + 2),
+                launch_block_update_seg(cs, s, ntot, j + 1, V, H2, hs, W, W, -1.0, sc), "update");
+            if ((st = cholqr2_b(W, V + (int64_t)(j + 1) * blk))) return st;
+            PKL("arnoldi_ls", 16.0 * ss * s * (j + 1) * nsys, 0.0,
+                launch_arnoldi_ls_b(cs, s, nsys, j, m, H1, H2, Rn, Qs, Rtri, Gv, thresh, est, flag), "least squares");
+            CU(cudaMemcpyAsync(hflag.data(), flag, (size_t)nsys * 4, cudaMemcpyDeviceToHost, cs), "read flags");
+            CU(cudaStreamSynchronize(cs), "sync");
+            ++iters;
+            J = j + 1;
+            bool all = true;
+            for (int i = 0; i < nsys; ++i) {
+                if (hflag[i] && conv_cycle[i] < 0 && done_it[i] < 0) done_it[i] = iters;
+                all = all && hflag[i];
+            }
+            if (all) break;
+        }
+        // X += P (V Y), every system with its own Y
+        PKL("backsolve", (double)J * s * J * s * s * nsys, 0.0, launch_backsolve_b(cs, s, nsys, J, m, Rtri, Gv, Y),
+            "back substitution");
+        PKL("block_update", 2.0 * blk * s * J, 8.0 * blk * (J + 2),
+            launch_block_update_seg(cs, s, ntot, J, V, Y, (int64_t)m * ss, nullptr, W, 1.0, sc), "V Y");
+        const double *U = W;
+        if (!levels.empty()) {
+            if ((st = apply_P(W, Z))) return st;
+            U = Z;
+        }
+        PKL("axpy", 2.0 * blk, 24.0 * blk, launch_axpy(cs, blk, 1.0, U, Xw), "X update");
+        if ((st = residual())) return st;
+        for (int i = 0; i < nsys; ++i) {
+            if (conv_cycle[i] >= 0) continue;
+            if (sys_converged(i)) {
+                conv_cycle[i] = cycles;
+                if (done_it[i] < 0) done_it[i] = iters;
+            } else {
+                done_it[i] = -1;  // not there yet: its step is counted again in the next cycle
+            }
+        }
+    }
+    for (int i = 0; i < nsys; ++i) KL(launch_unpack(cs, s, A[i].n, Xw + off[i] * s, X[i], A[i].n), "unpack X");
+    CU(cudaStreamSynchronize(cs), "sync");
+    int h_err = 0;
+    if ((st = read_err(ctx, &h_err))) return st;
+    bool all = true;
+    for (int i = 0; i < nsys; ++i) {
+        int worst = 0;
+        double wr = -1.0;
+        bool conv = true;
+        for (int c = 0; c < s; ++c) {
+            const size_t k = (size_t)i * s + c;
+            const double rn = sqrt(hr[k]);
+            const double rel = bnorm[k] > 0 ? rn / bnorm[k] : rn;
+            if (rel > wr) { wr = rel; worst = c; }
+            if (!(rn <= th[k])) conv = false;
+        }
+        info[i].iterations = done_it[i] >= 0 ? done_it[i] : iters;
+        info[i].cycles = conv_cycle[i] >= 0 ? conv_cycle[i] : cycles;
+        info[i].converged = conv ? 1 : 0;
+        info[i].worst_column = worst;
+        info[i].max_rel_residual = wr;
+        all = all && conv;
+    }
+    if (!all) return fail(ctx, SPAI_ENOTCONV, "not every system of the batch converged after %d cycles", cycles);
+    return SPAI_OK;
+}
+
 extern "C" spai_status spai_block_gram(spai_ctx ctx, int32_t s, int32_t n, int32_t nblk, const double *V,
                                        const double *W, double *H, int32_t method)
 {

@@ -81,6 +81,8 @@ int launch_spmm(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr,
 int launch_spmm_bf16v(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr, const int32_t *colind,
                       const uint16_t *val, const double *X, double *Y);
 int launch_gather_bf16_f64(cudaStream_t st, int64_t count, const int32_t *idx, const uint16_t *src, double *dst);
+// dst[i] = src[i] + add
+int launch_add_i32(cudaStream_t st, int64_t count, const int32_t *src, int32_t add, int32_t *dst);
 // dst[i] = i; the FP32 / BF16 gathers take idx = NULL for the identity
 int launch_iota_i32(cudaStream_t st, int64_t count, int32_t *dst);
 // same with FP32 values (products and sums in FP64)
@@ -185,6 +187,36 @@ __device__ __forceinline__ void row_store(double *W, int64_t r, const double (&x
 
 // ---------------------------------------------------------------------- k_krylov.cu
 struct KrylovWs;
+// Row chunks of a batch of systems stacked row-wise (device arrays): chunk c covers rows
+// [r0[c], r1[c]) of system sys[c]; system b's chunks are c0[b] .. c0[b + 1] - 1.
+struct SegChunks {
+    const int32_t *sys;
+    const int64_t *r0, *r1;
+    const int32_t *c0;
+    int32_t nchunks, nsys;
+};
+// per-system versions of the block-GMRES pieces (outputs of system b at b * stride)
+int launch_colnorm2_seg(cudaStream_t st, int32_t s, const double *W, const SegChunks &sc, double *partial,
+                        double *out);
+// partial: nchunks * nblk * s * s doubles
+int launch_block_dot_seg(cudaStream_t st, int32_t s, int64_t ntot, int32_t nblk, const double *V, const double *W,
+                         const SegChunks &sc, double *partial, double *out, int64_t ostride);
+int launch_block_update_seg(cudaStream_t st, int32_t s, int64_t ntot, int32_t nblk, const double *V, const double *H,
+                            int64_t hstride, const double *base, double *out, double sign, const SegChunks &sc);
+int launch_gram_seg(cudaStream_t st, int32_t s, const double *W, const SegChunks &sc, double *partial, double *G);
+int launch_trsm_gram_seg(cudaStream_t st, int32_t s, const double *W, const double *R, const int32_t *deflated,
+                         double *Q1, const SegChunks &sc, double *partial, double *G2);
+int launch_trsm_rows_seg(cudaStream_t st, int32_t s, const double *W, const double *R, const int32_t *deflated,
+                         double *out, const SegChunks &sc);
+int launch_chol_small_b(cudaStream_t st, int32_t s, int32_t nsys, const double *G, const double *ref2, double tau2,
+                        double *R, int32_t *deflated);
+int launch_triu_mul_b(cudaStream_t st, int32_t s, int32_t nsys, const double *R2, const double *R1, double *out);
+int launch_arnoldi_ls_b(cudaStream_t st, int32_t s, int32_t nsys, int32_t j, int32_t m, const double *H1,
+                        const double *H2, const double *Rsub, double *Qs, double *Rtri, double *G, const double *thresh,
+                        double *est, int32_t *flag);
+int launch_set_rhs_b(cudaStream_t st, int32_t s, int32_t nsys, int32_t m, const double *S0, double *G);
+int launch_backsolve_b(cudaStream_t st, int32_t s, int32_t nsys, int32_t J, int32_t m, const double *Rtri,
+                       const double *G, double *Y);
 int krylov_chunks(int32_t n);
 // doubles needed for the partial sums of launch_block_dot with up to nblk_max blocks
 size_t dot_partial_elems(int32_t s, int32_t nblk_max);
