@@ -901,6 +901,10 @@ def main():
                "d2h_bytes_per_step": hs.d2h_bytes()}
         hs.close()
 
+    # many small systems: batched build and lockstep solves
+    batched = None
+    if rank == 0 and world == 1 and not args.no_batched:
+        batched = run_batched(args, sg, torch)
     # served (continuous admission, update routing, FP32 factors) vs FIFO plain FP64
     serving = None
     if rank == 0 and world == 1 and not args.no_serve:
@@ -908,9 +912,6 @@ def main():
     large = None
     if rank == 0 and world == 1 and not args.no_large:
         large = run_large(args, sg, torch)
-    batched = None
-    if rank == 0 and world == 1 and not args.no_batched:
-        batched = run_batched(args, sg, torch)
 
     if rank == 0:
         total_ms = sum(f["ms"] for f in prof) or 1.0
