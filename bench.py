@@ -157,10 +157,15 @@ FAMILY_UNIT = {
     "axpy": "none", "gather_csc": "none", "small_dense": "latency", "arnoldi_ls": "latency",
     "backsolve": "latency",
 }
-# DRAM bytes per launch, (a * blocks + b) * n * s, fitted to one ncu capture of each kernel
-# at n = 262,144, s = 8; a family is left out (traffic null) while its kernel has changed
-# since its capture
-NCU_TRAFFIC = {}
+# DRAM bytes per launch, (a * blocks + b) * n * s, where blocks = algorithmic bytes per launch
+# / (8 n s) (the Gram product: basis blocks + W; the update: basis blocks + W read and
+# written): a = 8 B per entry, b fitted to one ncu capture of the kernel at n = 262,144,
+# s = 8, 16 basis blocks (read + write bytes; summarised under profiles/).  A family is
+# left out (traffic null) while its kernel has changed since its capture.
+NCU_TRAFFIC = {
+    "block_dot_tc": (8.0, (296.106e6 + 3.083e6) / 2097152 - 8.0 * 17),
+    "block_update_tc": (8.0, (285.292e6 + 11.469e6) / 2097152 - 8.0 * 18),
+}
 
 
 def roofline_entry(f, n, s, fp64_probe=None):
