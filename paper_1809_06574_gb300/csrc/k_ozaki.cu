@@ -582,6 +582,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 #pragma unroll
             for (int b = 0; b < kS; ++b) mx[b] = 0;
             const int64_t r1 = min((int64_t)n, (t0 + nsub) * kKT);
+#pragma unroll 4
             for (int64_t r = t0 * kKT + ct; r < r1; r += kCT) {
                 const double2 *row = reinterpret_cast<const double2 *>(W + r * kS);
 #pragma unroll
@@ -678,13 +679,23 @@ __global__ void k_h_digits(int32_t nblk, const double *__restrict__ H, char *__r
                            int32_t *__restrict__ hexp, int *err)
 {
     __shared__ int32_t ex_s[kS];
+    __shared__ unsigned long long mx_s[256];
     const int ncol = nblk * kS;
-    if (threadIdx.x < kS) {
+    {
+        // column maxima: thread t scans column t % 8 at rows t / 8, t / 8 + 32, ... (the
+        // block has 256 threads), then one thread per column combines the 32 partial maxima
         unsigned long long m = 0;
-        for (int c = 0; c < ncol; ++c) {
-            const unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(H[c * kS + threadIdx.x]));
+        for (int c = threadIdx.x / kS; c < ncol; c += 256 / kS) {
+            const unsigned long long bits =
+                (unsigned long long)__double_as_longlong(fabs(H[c * kS + threadIdx.x % kS]));
             m = bits > m ? bits : m;
         }
+        mx_s[threadIdx.x] = m;
+    }
+    __syncthreads();
+    if (threadIdx.x < kS) {
+        unsigned long long m = 0;
+        for (int g = 0; g < 256 / kS; ++g) m = mx_s[g * kS + threadIdx.x] > m ? mx_s[g * kS + threadIdx.x] : m;
         const int ex = (int)((m >> 52) & 0x7FF);
         ex_s[threadIdx.x] = ex == 0 ? 0 : ex - 1022;
         hexp[threadIdx.x] = ex_s[threadIdx.x];
