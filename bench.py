@@ -327,28 +327,6 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------------------- serving
-SERVE_SIDES = [round(24 + 72 * i / 15) for i in range(16)]  # 24 ... 96: n = 13,824 ... 884,736
-
-
-def serving_trace(rate, seconds, nsys, seed=0):
-    """Poisson arrivals at `rate` per second for `seconds`: (t, system, p, s, nrhs).  70 % of
-    the requests lie within 0.05 of an already-served (system, s, p); the others draw a
-    system, p ~ U[0.1, 1] and s in {0.5, 1, 2}; nrhs in {1, 4, 8}."""
-    rng = np.random.default_rng(np.random.SeedSequence(seed).spawn(4)[3])
-    out, seen, t = [], [], 0.0
-    while True:
-        t += rng.exponential(1.0 / rate)
-        if t >= seconds:
-            return out
-        if seen and rng.random() < 0.7:
-            sy, p0, s = seen[int(rng.integers(len(seen)))]
-            p = float(np.clip(p0 + rng.uniform(-0.05, 0.05), 0.1, 1.0))
-        else:
-            sy, p, s = int(rng.integers(nsys)), float(rng.uniform(0.1, 1.0)), float(rng.choice([0.5, 1.0, 2.0]))
-        seen.append((sy, p, s))
-        out.append((t, sy, p, s, int(rng.choice([1, 4, 8]))))
-
-
 def serve_trace(sg, torch, systems, Bs, trace, **opts):
     """Replay `trace` open-loop against a fresh server: each request is submitted at its
     arrival time (latency counts from that time, however late the submit), the solution
@@ -413,10 +391,9 @@ def run_serving(args, sg, torch):
     """Served (concurrent slots, cached builds routed to updates, FP32 factors) against FIFO
     plain FP64 (one slot, a SPAI build per request) on the same Poisson trace."""
     import synth
-    systems = [synth.grid_workload((d, d, d), "7pt", seed=100 + i, nrhs=8, params=[0.5])
-               for i, d in enumerate(SERVE_SIDES)]
+    systems = synth.serving_pool()
     Bs = [torch.from_numpy(np.asfortranarray(w.B).T.copy()).pin_memory() for w in systems]  # (8, n): column-major n x 8
-    trace = serving_trace(args.serve_rate, args.serve_seconds, len(systems))
+    trace = synth.serving_trace(args.serve_rate, args.serve_seconds, len(systems))
     common = dict(restart=30, max_cycles=100, tol=1e-8)
     served = dict(slots=args.serve_slots, reuse=True, radius=0.05, pattern_kind=sg.PREC_FP32,
                   mem_budget=40 << 30, **common)
@@ -431,7 +408,7 @@ def run_serving(args, sg, torch):
     nbar = float(np.mean([systems[sy].n for _, sy, _, _, _ in trace]))
     return {
         "workload": f"Poisson {args.serve_rate:g} req/s for {args.serve_seconds:g} s over 16 3D 7-point grids "
-                    f"(sides {SERVE_SIDES[0]}-{SERVE_SIDES[-1]}, mean n of the requests {nbar:.0f}); 70 % within "
+                    f"(sides {synth.SERVE_SIDES[0]}-{synth.SERVE_SIDES[-1]}, mean n of the requests {nbar:.0f}); 70 % within "
                     f"0.05 of a served p; s in {{0.5,1,2}}; nrhs in {{1,4,8}}; block GMRES(30) to 1e-8; "
                     f"40 GB budget; solutions returned to host memory",
         "served": {**out, "slots": args.serve_slots, "factors": "f32 (FP64 solve)", "reuse_radius": 0.05},
@@ -452,21 +429,18 @@ def run_batched(args, sg, torch):
     `batched_workers` streams."""
     import synth
     from concurrent.futures import ThreadPoolExecutor
-    rng = np.random.default_rng(np.random.SeedSequence(0).spawn(5)[4])
     nsys = args.batched_systems
-    sides = rng.integers(48, 257, size=nsys)
-    ps = rng.uniform(0.1, 1.0, size=nsys)
-    kinds = [(sg.PATTERN_A if i % 2 == 0 else sg.PATTERN_A2) | sg.PREC_FP32 for i in range(nsys)]
+    ws = synth.batched_2d(nsys)
+    kinds = [(sg.PATTERN_A if w.extra["pattern"] == "A" else sg.PATTERN_A2) | sg.PREC_FP32 for w in ws]
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
     ctx = sg.spai_ctx_create(stream.cuda_stream, 0)
     systems = []
-    for i in range(nsys):
-        w = synth.grid_workload((int(sides[i]), int(sides[i])), "5pt", seed=1000 + i, nrhs=4, params=[float(ps[i])])
+    for w in ws:
         aff = sg.spai_affine_create(ctx, [sg.csr(w.n, *t) for t in w.terms])
         _, nnz, rp, ci = sg.spai_affine_pattern(aff)
         va = torch.empty(nnz, dtype=torch.float64, device=dev)
-        sg.spai_assemble(ctx, aff, sg.affine_coefficients(float(ps[i]), 1.0), va)
+        sg.spai_assemble(ctx, aff, sg.affine_coefficients(w.params[0], 1.0), va)
         B = torch.as_tensor(np.ascontiguousarray(w.B.T), device=dev)
         systems.append({"w": w, "aff": aff, "va": va, "A": sg.csr(w.n, rp, ci, va, nnz), "B": B})
     As = [y["A"] for y in systems]

@@ -244,3 +244,46 @@ def random_sparse(n, density, seed, *, symmetric_pattern=False, diag_shift=None)
 def rhs_block(n, s, seed):
     rng = np.random.default_rng(np.random.SeedSequence(seed).spawn(3)[1])
     return np.asfortranarray(rng.standard_normal((n, s)))
+
+
+def batched_2d(nsys=256, seed=0):
+    """The many-small-systems workload: nsys 2D 5-point grids with sides ~ U{48..256}
+    (n = 2,304 .. 65,536), system i seeded with 1000 + i, its parameter p ~ U[0.1, 1] and
+    shift 1, 4 right-hand sides; even-numbered systems take the SPAI pattern of A, odd ones
+    that of A^2 (recorded in ``extra["pattern"]``)."""
+    rng = np.random.default_rng(np.random.SeedSequence(seed).spawn(5)[4])
+    sides = rng.integers(48, 257, size=nsys)
+    ps = rng.uniform(0.1, 1.0, size=nsys)
+    out = []
+    for i in range(nsys):
+        w = grid_workload((int(sides[i]), int(sides[i])), "5pt", seed=1000 + i, nrhs=4, params=[float(ps[i])])
+        w.extra["pattern"] = "A" if i % 2 == 0 else "A2"
+        out.append(w)
+    return out
+
+
+SERVE_SIDES = [round(24 + 72 * i / 15) for i in range(16)]  # 24 ... 96: n = 13,824 ... 884,736
+
+
+def serving_pool(seed=100):
+    """The serving workload's pool of 16 3D 7-point grids (sides 24 .. 96), 8 RHS each."""
+    return [grid_workload((d, d, d), "7pt", seed=seed + i, nrhs=8, params=[0.5]) for i, d in enumerate(SERVE_SIDES)]
+
+
+def serving_trace(rate, seconds, nsys, seed=0):
+    """Poisson arrivals at `rate` per second for `seconds`: (t, system, p, s, nrhs).  70 % of
+    the requests lie within 0.05 of an already-served (system, s, p); the others draw a
+    system, p ~ U[0.1, 1] and s in {0.5, 1, 2}; nrhs in {1, 4, 8}."""
+    rng = np.random.default_rng(np.random.SeedSequence(seed).spawn(4)[3])
+    out, seen, t = [], [], 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= seconds:
+            return out
+        if seen and rng.random() < 0.7:
+            sy, p0, s = seen[int(rng.integers(len(seen)))]
+            p = float(np.clip(p0 + rng.uniform(-0.05, 0.05), 0.1, 1.0))
+        else:
+            sy, p, s = int(rng.integers(nsys)), float(rng.uniform(0.1, 1.0)), float(rng.choice([0.5, 1.0, 2.0]))
+        seen.append((sy, p, s))
+        out.append((t, sy, p, s, int(rng.choice([1, 4, 8]))))

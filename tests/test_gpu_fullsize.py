@@ -123,3 +123,46 @@ def test_fullsize_27pt_128_bf16_build_update_solve():
     assert info["converged"]
     true_rel = np.linalg.norm(w.B - oracle.spmm(A2, X, n), axis=0) / np.linalg.norm(w.B, axis=0)
     assert np.all(true_rel <= 1e-8), true_rel
+
+
+def test_fullsize_batched_256_systems():
+    """The many-small-systems workload at full size: 256 2D 5-point systems (sides 48..256,
+    6.47 M unknowns), all FP32-factor SPAIs from one spai_build_batch call and all solves
+    from one block_solve_batch call, as bench.py runs them.  Every system's true residual is
+    recomputed on the host in FP64; three sampled systems (the smallest, the largest, one of
+    pattern A^2) are compared with the oracle: index sets bit-exact, factor entries within
+    the FP32 bar, solutions within 1e-6 of the oracle's all-FP64 solve."""
+    import torch
+    import paper_1809_06574_gb300 as sg
+    ws = synth.batched_2d(256)
+    kinds = [(sg.PATTERN_A if w.extra["pattern"] == "A" else sg.PATTERN_A2) | sg.PREC_FP32 for w in ws]
+    As = [oracle.assemble(w.terms, oracle.coefficients(w.params[0], 1.0), w.n) for w in ws]
+    sizes = [w.n for w in ws]
+    sample = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), next(i for i, w in enumerate(ws)
+                                                                       if w.extra["pattern"] == "A2")})
+    with context() as ctx:
+        from gpu_util import dev_csr
+        ds = [dev_csr(A, w.n) for A, w in zip(As, ws)]
+        pcs, st = sg.spai_build_batch(ctx, ds, kinds)
+        assert st == 0
+        got = {i: export(ctx, pcs[i]) for i in sample}
+        Bd = [torch.as_tensor(np.ascontiguousarray(w.B.T), device="cuda:0") for w in ws]
+        Xd = [torch.zeros((4, w.n), dtype=torch.float64, device="cuda:0") for w in ws]
+        st, infos = sg.block_solve_batch(ctx, ds, pcs, 4, Bd, Xd, 30, 1e-8, 100)
+        Xs = [x.cpu().numpy().T.copy() for x in Xd]
+        for pc in pcs:
+            sg.spai_pc_destroy(pc)
+    assert st == 0 and all(i["converged"] for i in infos)
+    for w, A, X in zip(ws, As, Xs):
+        rel = np.linalg.norm(w.B - oracle.spmm(A, X, w.n), axis=0) / np.linalg.norm(w.B, axis=0)
+        assert np.all(rel <= 1e-8)
+    for i in sample:
+        w, A = ws[i], As[i]
+        ref = oracle.spai_build(A, w.n, oracle.PATTERN_A if w.extra["pattern"] == "A" else oracle.PATTERN_A2)
+        g = got[i]
+        for key in ("Jptr", "Jind", "Iptr", "Ilist", "status"):
+            assert np.array_equal(g[key], getattr(ref, key)), (i, key)
+        assert column_rel_err_vec(ref.Jptr, g["val"], ref.val) <= 5e-6, i
+        Xo, io = oracle.block_gmres(oracle.csr_apply(A, w.n), ref.apply, w.B, 30, 1e-8, 100)
+        assert io["converged"]
+        assert np.linalg.norm(Xs[i] - Xo) <= 1e-6 * np.linalg.norm(Xo), i
