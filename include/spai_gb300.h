@@ -360,8 +360,9 @@ SPAI_API spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, int
  *    workspaces resident on the device;
  *  - it runs up to `slots` requests at once, each on its own CUDA stream and context, so
  *    the kernels of different requests overlap on the GPU; a request is admitted when a
- *    slot is free and its device memory fits the budget (least recently used cached
- *    builds are evicted, idle workspaces released, else it waits for running requests);
+ *    slot is free and its device memory fits the budget (idle slots' workspaces are
+ *    released first, then least recently used cached builds evicted, else it waits for
+ *    running requests);
  *  - with `reuse`, a request whose parameter p lies within `radius` of a cached build's
  *    parameter, for the same system and the same shift s, is served by spai_update
  *    (SPAI_UPDATE_FIRST from that build) instead of a new build; at p equal to the

@@ -11,8 +11,9 @@
 // request routed to a build still in progress on another slot is passed over until the
 // build is cached).  Its device memory -- growth of the slot's workspace and buffers
 // plus the factor it will create -- must fit the budget next to the systems, the cached
-// builds and the other slots; if it does not, least recently used idle builds are
-// evicted, then idle slots' workspaces released; if it still does not fit the slot
+// builds and the other slots; if it does not, idle slots' workspaces are released
+// (largest first; they are cheap to allocate again), then least recently used idle
+// builds evicted (each costs a build to get back); if it still does not fit the slot
 // waits for a running request to finish (a request that cannot fit even on an empty
 // server fails with SPAI_ENOMEM).
 #include <cuda_runtime.h>
@@ -201,6 +202,24 @@ bool make_room(spai_server_s *S, size_t need, const Entry *keep, int slot)
 {
     const size_t budget = S->o.mem_budget;
     if (!budget) return true;
+    // first the idle slots' workspaces and buffers (not this slot's: it is about to use
+    // them), largest first -- they are allocated again on demand -- then cached builds,
+    // least recently used first, which cost a build to get back
+    while (mem_now(S) + need > budget) {
+        int big = -1;
+        size_t big_b = 0;
+        for (int k = 0; k < (int)S->slots.size(); ++k) {
+            const Slot &sl = S->slots[k];
+            const size_t b = sl.ws_cap + sl.A_cap + sl.X_cap;
+            if (k != slot && !sl.busy && b > big_b) { big = k; big_b = b; }
+        }
+        if (big < 0) break;
+        Slot &sl = S->slots[big];
+        if (sl.ws_cap) { spai_ctx_trim(sl.ctx); sl.ws_cap = 0; }
+        if (sl.A) { cudaFreeAsync(sl.A, sl.stream); sl.A = nullptr; }
+        if (sl.X) { cudaFreeAsync(sl.X, sl.stream); sl.X = nullptr; }
+        sl.A_alloc = sl.A_cap = sl.X_alloc = sl.X_cap = 0;
+    }
     while (mem_now(S) + need > budget) {
         Entry *lru = nullptr;
         for (Entry *e : S->cache)
@@ -208,16 +227,6 @@ bool make_room(spai_server_s *S, size_t need, const Entry *keep, int slot)
         if (!lru) break;
         destroy_entry(S, lru);
         S->st.evictions++;
-    }
-    if (mem_now(S) + need <= budget) return true;
-    // release idle slots' workspaces and buffers (not this slot's: it is about to use them)
-    for (int k = 0; k < (int)S->slots.size(); ++k) {
-        Slot &sl = S->slots[k];
-        if (k == slot || sl.busy) continue;
-        if (sl.ws_cap) { spai_ctx_trim(sl.ctx); sl.ws_cap = 0; }
-        if (sl.A) { cudaFreeAsync(sl.A, sl.stream); sl.A = nullptr; sl.A_alloc = sl.A_cap = 0; }
-        if (sl.X) { cudaFreeAsync(sl.X, sl.stream); sl.X = nullptr; sl.X_alloc = sl.X_cap = 0; }
-        if (mem_now(S) + need <= budget) return true;
     }
     return mem_now(S) + need <= budget;
 }

@@ -138,19 +138,20 @@ def test_memory_budget_evicts_and_refuses():
     w = systems[0]
     # distinct p far apart (radius 0.01): every request builds and caches its own base
     trace = [(0, p, 1.0, 4) for p in (0.1, 0.3, 0.5, 0.7, 0.9, 0.2, 0.4)]
-    res0, _, st0 = _serve(sg, systems, trace, slots=2, reuse=True, radius=0.01)
+    res0, _, st0 = _serve(sg, systems, trace, slots=1, reuse=True, radius=0.01)
     assert st0["cached_builds"] == len(trace) and st0["evictions"] == 0
     with context() as ctx:
         pc, _ = sg.spai_build(ctx, dev_csr(oracle.assemble(w.terms, oracle.coefficients(0.1, 1.0), w.n), w.n))
         build_bytes = sg.spai_pc_mem_size(pc, True)
         sg.spai_pc_destroy(pc)
-    fixed = st0["mem_in_use"] - len(trace) * build_bytes  # systems and the slots' buffers
-    # room for four builds and the transient pattern-analysis reservation of two builds in
-    # flight (16 nnz + 16 (n + 1) + 1 MiB each): at most three cached while one is built
+    fixed = st0["mem_in_use"] - len(trace) * build_bytes  # the system and the slot's buffers
+    # one slot (no idle workspace to release): room for four builds and the transient
+    # pattern-analysis reservation of the build in flight (16 nnz + 16 (n + 1) + 1 MiB):
+    # at most three cached while one is built
     nnz = int(oracle.assemble(w.terms, oracle.coefficients(0.1, 1.0), w.n)[0][-1])
     transient = 16 * nnz + 16 * (w.n + 1) + (1 << 20)
-    budget = fixed + 4 * build_bytes + 2 * transient
-    res, Xs, stats = _serve(sg, systems, trace, slots=2, reuse=True, radius=0.01, mem_budget=budget)
+    budget = fixed + 4 * build_bytes + transient
+    res, Xs, stats = _serve(sg, systems, trace, slots=1, reuse=True, radius=0.01, mem_budget=budget)
     assert all(r["status"] == 0 for r in res), res
     assert stats["mem_peak"] <= budget
     assert stats["evictions"] >= 3 and stats["cached_builds"] <= 4
@@ -161,3 +162,63 @@ def test_memory_budget_evicts_and_refuses():
     res2, _, stats2 = _serve(sg, systems, trace[:2], slots=2, reuse=True, mem_budget=ws // 2)
     assert all(r["status"] == sg.SPAI_ENOMEM for r in res2)
     assert stats2["failed"] == 2
+
+
+def test_fullsize_served_trace():
+    """The serving workload at full size for one second of arrivals (200 requests/s over the
+    16-grid pool, n up to 884,736, FP32 factors, 40 GiB budget, 4 slots), submitted at once:
+    every request converges; for a sample (one per system that has a request) the
+    solution's true residual is recomputed on the host and the route is checked."""
+    import paper_1809_06574_gb300 as sg
+    pool = synth.serving_pool()
+    trace = synth.serving_trace(200.0, 1.0, len(pool))
+    srv = sg.spai_server_create(slots=4, reuse=True, radius=0.05, pattern_kind=sg.PREC_FP32, restart=30,
+                                max_cycles=100, tol=TOL, mem_budget=40 << 30)
+    try:
+        ids = [sg.spai_server_add_system(srv, [sg.csr(w.n, *t) for t in w.terms]) for w in pool]
+        Bs = [np.asfortranarray(w.B) for w in pool]
+        sampled, tickets, Xs = set(), [], {}
+        for k, (_, sy, p, s, nrhs) in enumerate(trace):
+            X = None
+            if sy not in sampled:
+                sampled.add(sy)
+                X = np.zeros((pool[sy].n, nrhs), order="F")
+                Xs[k] = X
+            tickets.append(sg.spai_server_submit(srv, ids[sy], nrhs, p, s, sg.affine_coefficients(p, s), Bs[sy], X))
+        res = [sg.spai_server_wait(srv, t) for t in tickets]
+        stats = sg.spai_server_stats_get(srv)
+    finally:
+        sg.spai_server_destroy(srv)
+    assert stats["failed"] == 0 and stats["mem_peak"] <= 40 << 30
+    assert all(r["status"] == 0 and r["max_rel_residual"] <= TOL for r in res)
+    assert stats["updates"] > 0
+    for k, X in Xs.items():
+        _, sy, p, s, nrhs = trace[k]
+        w, r = pool[sy], res[k]
+        assert r["route"] == sg.ROUTE_BUILD and r["base_p"] == p  # first request of its system builds
+        A = oracle.assemble(w.terms, oracle.coefficients(p, s), w.n)
+        rel = np.linalg.norm(w.B[:, :nrhs] - oracle.spmm(A, X, w.n), axis=0) / np.linalg.norm(w.B[:, :nrhs], axis=0)
+        assert np.all(rel <= TOL), (k, rel)
+
+
+def test_failed_requests_do_not_stop_the_server():
+    """A restart length and cycle cap too small to reach the tolerance: every request
+    completes with SPAI_ENOTCONV and its residual report, the server keeps serving, and a
+    second server with the normal settings solves the same requests."""
+    import paper_1809_06574_gb300 as sg
+    systems = _systems(sides=(8, 9))
+    trace = _trace(6, len(systems), seed=9)
+    srv = sg.spai_server_create(slots=2, restart=1, max_cycles=1, tol=1e-12, reuse=True)
+    try:
+        ids = [sg.spai_server_add_system(srv, [sg.csr(w.n, *t) for t in w.terms]) for w in systems]
+        tickets = [sg.spai_server_submit(srv, ids[sy], nrhs, p, s, sg.affine_coefficients(p, s),
+                                         np.asfortranarray(systems[sy].B)) for sy, p, s, nrhs in trace]
+        res = [sg.spai_server_wait(srv, t) for t in tickets]
+        stats = sg.spai_server_stats_get(srv)
+        assert "request" in sg.spai_server_last_error(srv)
+    finally:
+        sg.spai_server_destroy(srv)
+    assert all(r["status"] == sg.SPAI_ENOTCONV and r["max_rel_residual"] > 1e-12 for r in res)
+    assert stats["failed"] == len(trace) and stats["completed"] == len(trace)
+    res2, _, st2 = _serve(sg, systems, trace, slots=2, reuse=True)
+    assert all(r["status"] == 0 for r in res2) and st2["failed"] == 0
