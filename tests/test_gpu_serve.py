@@ -211,8 +211,9 @@ def test_failed_requests_do_not_stop_the_server():
     srv = sg.spai_server_create(slots=2, restart=1, max_cycles=1, tol=1e-12, reuse=True)
     try:
         ids = [sg.spai_server_add_system(srv, [sg.csr(w.n, *t) for t in w.terms]) for w in systems]
-        tickets = [sg.spai_server_submit(srv, ids[sy], nrhs, p, s, sg.affine_coefficients(p, s),
-                                         np.asfortranarray(systems[sy].B)) for sy, p, s, nrhs in trace]
+        Bs = [np.asfortranarray(w.B) for w in systems]  # read by the workers: kept alive here
+        tickets = [sg.spai_server_submit(srv, ids[sy], nrhs, p, s, sg.affine_coefficients(p, s), Bs[sy])
+                   for sy, p, s, nrhs in trace]
         res = [sg.spai_server_wait(srv, t) for t in tickets]
         stats = sg.spai_server_stats_get(srv)
         assert "request" in sg.spai_server_last_error(srv)
