@@ -979,7 +979,7 @@ spai_status run_columns_batch(spai_ctx ctx, int32_t nsys, spai_pc *pcs)
         const int low = std::get<0>(b.first), maxJ = std::get<1>(b.first);
         const std::vector<int> &mem = b.second;
         const int m = (int)mem.size();
-        int maxI = 0;  // tile rows: the bucket's class (a multiple of 8) when it fits, else its largest |I_k|
+        int maxI = 0;  // tile rows: the bucket's largest |I_k| (its class, a multiple of 8, keys the tuning)
         std::vector<ColumnProblem> tab((size_t)m);
         std::vector<int64_t> start((size_t)m + 1, 0);
         double fl = 0.0, by = 0.0;
@@ -1021,8 +1021,7 @@ spai_status run_columns_batch(spai_ctx ctx, int32_t nsys, spai_pc *pcs)
         CU(cudaMemcpyAsync(d_start, start.data(), sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, ctx->stream),
            "table");
         const ColumnBatch bt{d_tab, d_start, m, start[m]};
-        if (spai_columns_fit(std::get<2>(b.first), maxJ)) maxI = std::get<2>(b.first);
-        const auto key = std::make_tuple(low, maxI, maxJ);
+        const auto key = std::make_tuple(low, std::get<2>(b.first), maxJ);
         int team = 0;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
