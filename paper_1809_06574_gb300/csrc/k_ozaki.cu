@@ -30,6 +30,8 @@
 // thread issues the tcgen05.mma of every stage and frees the digit stage with
 // tcgen05.commit.  Every wait is bounded in time (1 s): on time-out the kernel raises an
 // error bit, waits (bounded) for its copies in flight, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+
 #include <cstdint>
 
 #include "spai_internal.cuh"
@@ -304,41 +306,49 @@ __device__ __forceinline__ bool to_fixed(double x, int e, uint64_t &f)
 }
 
 // Nine BF16 digit planes of 8 fixed-point values (8 consecutive rows of one column), one
-// 16-byte chunk per plane at dst + p * pstride.  A digit d becomes the float 2^23 + d (its
-// bits OR-ed into the exponent pattern of 2^23, sign included) minus 2^23, both exact; the
-// BF16 is the float's upper half, and two of them are packed with one byte permute.
+// 16-byte chunk per plane at dst + p * pstride.  Two values at a time: their digits (6-bit
+// fields of the magnitudes) go into the two halves of one word OR-ed with the BF16 pattern
+// of 128, so each half is the BF16 number 128 + d, exactly; one BF16x2 fused multiply-add
+// (s (128 + d) - 128 s, s = +-1 the value's sign) leaves the signed digit s d in each half,
+// exactly (an integer below 64).
+__device__ __forceinline__ uint32_t digit_field(uint32_t lo, uint32_t hi, int sh)
+{
+    if (sh >= 32) return hi >> (sh - 32);
+    if (sh > 26) return __funnelshift_r(lo, hi, sh);
+    return lo >> sh;
+}
+
 __device__ __forceinline__ void expand8(const uint64_t f[8], char *dst, int pstride)
 {
-    uint32_t hi[8], lo[8], mg[8];
-    float bs[8];
+    uint32_t hi[8], lo[8];
+    __nv_bfloat162 sgn[4], off[4];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
         lo[u] = (uint32_t)f[u];
         hi[u] = (uint32_t)(f[u] >> 32);
-        mg[u] = 0x4B000000u | (hi[u] & 0x80000000u);
-        bs[u] = (hi[u] >> 31) ? 8388608.0f : -8388608.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t n0 = hi[2 * q] >> 31, n1 = hi[2 * q + 1] >> 31;
+        // s = +-1 and -128 s for both halves (BF16 bit patterns)
+        const uint32_t sb = (0x3F80u | (n0 << 15)) | ((0x3F80u | (n1 << 15)) << 16);
+        const uint32_t cb = (0x4300u | ((n0 ^ 1u) << 15)) | ((0x4300u | ((n1 ^ 1u) << 15)) << 16);
+        sgn[q] = *reinterpret_cast<const __nv_bfloat162 *>(&sb);
+        off[q] = *reinterpret_cast<const __nv_bfloat162 *>(&cb);
     }
 #pragma unroll
     for (int p = 0; p < kDig; ++p) {
         const int sh = 6 * (8 - p);
-        uint32_t fb[8];
+        uint32_t w[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            uint32_t d;
-            if (sh >= 32)
-                d = hi[u] >> (sh - 32);
-            else if (sh > 26)
-                d = __funnelshift_r(lo[u], hi[u], sh);
-            else
-                d = lo[u] >> sh;
-            fb[u] = __float_as_uint(__uint_as_float((d & 63u) | mg[u]) + bs[u]);
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t a = digit_field(lo[2 * q], hi[2 * q], sh);
+            const uint32_t b = digit_field(lo[2 * q + 1], hi[2 * q + 1], sh);
+            const uint32_t t = (__byte_perm(a, b, 0x5410) & 0x003F003Fu) | 0x43004300u;
+            const __nv_bfloat162 r = __hfma2(*reinterpret_cast<const __nv_bfloat162 *>(&t), sgn[q], off[q]);
+            w[q] = *reinterpret_cast<const uint32_t *>(&r);
         }
-        uint4 w;
-        w.x = __byte_perm(fb[0], fb[1], 0x7632);
-        w.y = __byte_perm(fb[2], fb[3], 0x7632);
-        w.z = __byte_perm(fb[4], fb[5], 0x7632);
-        w.w = __byte_perm(fb[6], fb[7], 0x7632);
-        *reinterpret_cast<uint4 *>(dst + p * pstride) = w;
+        *reinterpret_cast<uint4 *>(dst + p * pstride) = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
 
