@@ -304,3 +304,29 @@ def test_diagonal_update_solve_converges():
         sg.spai_pc_destroy(pc1)
     assert info["converged"] and io["converged"]
     assert np.linalg.norm(X - Xo) <= 1e-6 * np.linalg.norm(Xo)
+
+
+def test_update_across_shifts():
+    """Update over the shift (Sec. 2.4 also reuses a factor across expansion points): the
+    base is built at (p1, s1) and updated for (p2, s2) with s2 != s1 -- the same column
+    least squares against A(p1, s1)'s columns; entries and the solve against the oracle."""
+    import torch
+    sg = _sg()
+    w = synth.grid3d_7pt(side=12, nparams=3, seed=8)
+    n = w.n
+    A1 = oracle.assemble(w.terms, oracle.coefficients(0.3, 0.5), n)
+    A2 = oracle.assemble(w.terms, oracle.coefficients(0.4, 2.0), n)
+    Q = oracle.spai_update(oracle.spai_build(A1, n), A2, n)
+    Xo, io = oracle.block_gmres(oracle.csr_apply(A2, n), Q.apply, w.B, 30, 1e-8, 50)
+    with context() as ctx:
+        d1, d2 = dev_csr(A1, n), dev_csr(A2, n)
+        pc1, _ = sg.spai_build(ctx, d1)
+        q, _ = sg.spai_update(ctx, pc1, d2)
+        g = export(ctx, q)
+        X = np.zeros((n, w.B.shape[1]), order="F")
+        st, info, rel = sg.block_solve(ctx, d2, q, w.B.shape[1], np.asfortranarray(w.B), n, X, n, 30, 1e-8, 50)
+        sg.spai_pc_destroy(q)
+        sg.spai_pc_destroy(pc1)
+    assert column_rel_err(Q.Jptr, g["val"], Q.val) <= TOL_FACTOR
+    assert info["converged"] and io["converged"]
+    assert np.linalg.norm(X - Xo) <= 1e-6 * np.linalg.norm(Xo)
