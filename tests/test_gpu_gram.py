@@ -104,12 +104,13 @@ def test_tensor_gram_rejects_out_of_range_basis():
         assert ei.value.status == sg.SPAI_EINVAL
 
 
-@pytest.mark.parametrize("nrhs,restart", [(8, 50), (16, 30)])
-def test_solve_with_tensor_orthogonalisation_matches_fp64(nrhs, restart):
+@pytest.mark.parametrize("nrhs,restart,side", [(8, 50, 24), (16, 30, 24), (16, 20, 23)])
+def test_solve_with_tensor_orthogonalisation_matches_fp64(nrhs, restart, side):
     """8 columns run on the digit kernels directly, 16 columns as two 8-column halves
-    against all half-blocks of the basis; both must give the FP64 iterates to rounding."""
+    against all half-blocks of the basis (side 23: n = 12,167, a ragged last sub-tile);
+    both must give the FP64 iterates to rounding."""
     import paper_1809_06574_gb300 as sg
-    w = synth.grid3d_7pt(side=24, nparams=2, nrhs=nrhs)
+    w = synth.grid3d_7pt(side=side, nparams=2, nrhs=nrhs)
     n = w.n
     A = oracle.assemble(w.terms, oracle.coefficients(w.params[0], 0.5), n)
     P = oracle.spai_build(A, n)
