@@ -163,8 +163,8 @@ FAMILY_UNIT = {
 # s = 8, 16 basis blocks (read + write bytes; summarised under profiles/).  A family is
 # left out (traffic null) while its kernel has changed since its capture.
 NCU_TRAFFIC = {
-    "block_dot_tc": (8.0, (296.106e6 + 3.083e6) / 2097152 - 8.0 * 17),
-    "block_update_tc": (8.0, (285.292e6 + 11.469e6) / 2097152 - 8.0 * 18),
+    "block_dot_tc": (8.0, (296.057e6 + 3.242e6) / 2097152 - 8.0 * 17),
+    "block_update_tc": (8.0, (285.324e6 + 11.673e6) / 2097152 - 8.0 * 18),
 }
 
 
