@@ -516,6 +516,58 @@ def run_batched(args, sg, torch):
     }
 
 
+# --------------------------------------------------------------------- block vs single RHS
+def run_block_vs_single(sg, torch, ctx, w, nsys=5):
+    """Block GMRES(m) with all 8 right-hand sides at once against 8 single-RHS GMRES(m)
+    solves of the same systems (Sec. 2.1: block methods share one Krylov space), on the
+    first `nsys` parameters of the shift s = 1 (SPAI build at the first, updates after),
+    one stream, FP64 throughout."""
+    n, nr = w.n, int(w.B.shape[1])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d_terms = [tuple(torch.as_tensor(np.ascontiguousarray(a), device=dev) for a in t) for t in w.terms]
+    aff = sg.spai_affine_create(ctx, [sg.csr(n, *t) for t in d_terms])
+    _, nnz, rp, ci = sg.spai_affine_pattern(aff)
+    vals = [torch.empty(nnz, dtype=torch.float64, device=dev) for _ in range(nsys)]
+    As, pcs = [], []
+    for i in range(nsys):
+        sg.spai_assemble(ctx, aff, sg.affine_coefficients(w.params[i], 1.0), vals[i])
+        As.append(sg.csr(n, rp, ci, vals[i], nnz))
+        pcs.append(sg.spai_build(ctx, As[0])[0] if i == 0 else sg.spai_update(ctx, pcs[0], As[i])[0])
+    B = torch.as_tensor(np.ascontiguousarray(w.B.T), device=dev)  # (8, n): column c at row c
+    X = torch.zeros((nr, n), dtype=torch.float64, device=dev)
+
+    def block():
+        its = 0
+        for A, pc in zip(As, pcs):
+            X.zero_()
+            its += sg.block_solve(ctx, A, pc, nr, B, n, X, n, w.restart, w.tol, 50)[1]["iterations"]
+        return its
+
+    def single():
+        its = 0
+        for A, pc in zip(As, pcs):
+            X.zero_()
+            for c in range(nr):
+                its += sg.block_solve(ctx, A, pc, 1, B[c], n, X[c], n, w.restart, w.tol, 200)[1]["iterations"]
+        return its
+
+    out = {}
+    for name, f in (("block", block), ("single", single)):
+        f()  # warm-up (workspace sizes)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its = f()
+        torch.cuda.synchronize()
+        out[name] = {"ms_per_system": 1e3 * (time.perf_counter() - t0) / nsys, "iterations_per_system": its / nsys}
+    for i in range(nsys - 1, -1, -1):
+        sg.spai_pc_destroy(pcs[i])
+    sg.spai_affine_destroy(aff)
+    return {"systems": nsys, "shift": 1.0, **out,
+            "block_saving": 1.0 - out["block"]["ms_per_system"] / out["single"]["ms_per_system"],
+            "note": "one stream; block = one s = 8 solve per system, single = eight s = 1 solves; "
+                    "iterations are Arnoldi steps (block steps for the block solve)"}
+
+
 # ------------------------------------------------------------------------------- large
 def run_large(args, sg, torch):
     """3D side^3 27-point workload (side 128: n = 2,097,152, 27 nnz per column, 16 RHS):
@@ -942,6 +994,10 @@ def main():
                "d2h_bytes_per_step": hs.d2h_bytes()}
         hs.close()
 
+    # block GMRES with 8 RHS against 8 single-RHS solves (the paper's block vs non-block)
+    bvs = None
+    if rank == 0 and world == 1 and not args.no_mixed:
+        bvs = run_block_vs_single(sg, torch, ctx, w)
     # many small systems: batched build and lockstep solves
     batched = None
     if rank == 0 and world == 1 and not args.no_batched:
@@ -984,7 +1040,7 @@ def main():
                                             "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                                             "workers": args.workers},
             "roofline": roofline, "roofline_isolated": roofline_iso, "mixed_precision": mixed,
-            "warm_start": warm,
+            "warm_start": warm, "block_vs_single_rhs": bvs,
             "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "large": large, "batched": batched, "gpu_launches": int(launches),
             "clocks": clk, "fp64_tflops_measured": fp64_tflops,
             "gmres_iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)),
