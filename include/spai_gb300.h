@@ -201,11 +201,16 @@ SPAI_API spai_status spai_build(spai_ctx ctx, const spai_csr *A, int32_t pattern
  * column of every system is an independent least-squares problem).  A[i] and
  * pattern_kind[i] are as for spai_build (the pattern and the precision may differ between
  * systems); out[i] receives system i's handle, the same kind of handle spai_build returns
- * (update, apply, solve and destroy it on its own).  The pattern analyses of all systems
- * run phase by phase with one host read-back per phase for all of them (at most five
- * synchronisations whatever nsys is), and the column problems of all systems run in one
- * persistent launch per tile shape -- systems are grouped by working precision, max |J_k|
- * and max |I_k| rounded up to 8.  Team size (lanes per column problem): the first batch
+ * (update, apply, solve and destroy it on its own).  With two or more systems, none of
+ * them empty, the systems are stacked into one block-diagonal matrix and each phase of the
+ * pattern analysis (transposition, the unions J_k and I_k, the row pattern of P) is one
+ * launch over all of them; the per-system arrays of the analyses and the factors are carved
+ * from ONE device allocation shared by the batch's handles, which is freed when the last
+ * of them (and of the updates that share their analyses) is destroyed -- so destroying
+ * some handles of a batch returns no memory until the rest go too.  Otherwise (one system,
+ * or an empty one) the analyses run phase by phase per system with one host read-back per
+ * phase.  The column problems of all systems run in one persistent launch per tile shape --
+ * systems are grouped by working precision, max |J_k| and max |I_k| rounded up to 8.  Team size (lanes per column problem): the first batch
  * of the process that meets a shape times every team size whose block fits and keeps the
  * fastest; later batches reuse it (team sizes change the rounding of the reductions only,
  * results stay within the FP64 bar of spai_build).  1 <= nsys <= 65536.  Synchronises.

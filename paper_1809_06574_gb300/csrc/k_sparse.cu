@@ -312,6 +312,127 @@ __global__ void k_gather_bf16_f64(int64_t count, const int32_t *__restrict__ idx
         dst[i] = (double)__bfloat162float(__ushort_as_bfloat16(src[idx ? idx[i] : i]));
 }
 
+// ---------------------------------------------------------------------------------
+// Batches of matrices stacked into one block-diagonal matrix: segment g of a list laid end
+// to end covers elements start[g] <= e < start[g + 1] (empty segments allowed)
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ int seg_of(const int64_t *__restrict__ start, int nseg, int64_t e)
+{
+    int lo = 0, hi = nseg - 1;  // the last g with start[g] <= e
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(start + mid) <= e) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// rp[r] = rowptr_sys[r - off_sys] + nzoff_sys for the stacked rows (and rp[ntot] = nnz_tot),
+// checking every system's row pointer (starts at 0, monotone, ends at its nnz)
+__global__ void k_stack_rows(int32_t nsys, const int64_t *__restrict__ off, const int64_t *__restrict__ nzoff,
+                             const int32_t *const *__restrict__ rowptr, int32_t *__restrict__ rp, int *err)
+{
+    const int64_t ntot = off[nsys];
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r <= ntot;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        if (r == ntot) {
+            rp[r] = (int32_t)nzoff[nsys];
+            continue;
+        }
+        const int g = seg_of(off, nsys, r);
+        const int64_t lr = r - off[g], ng = off[g + 1] - off[g], nz = nzoff[g + 1] - nzoff[g];
+        const int32_t *p = rowptr[g];
+        const int32_t a = p[lr], b = p[lr + 1];
+        if ((lr == 0 && a != 0) || b < a || (lr == ng - 1 && b != nz)) atomicOr(err, ERR_ROWPTR);
+        rp[r] = (int32_t)(a + nzoff[g]);
+    }
+}
+
+// ci[q] = colind_sys[q - nzoff_sys] + off_sys, checking 0 <= colind < n_sys
+__global__ void k_stack_cols(int32_t nsys, const int64_t *__restrict__ off, const int64_t *__restrict__ nzoff,
+                             const int32_t *const *__restrict__ colind, int32_t *__restrict__ ci, int *err)
+{
+    const int64_t nnz = nzoff[nsys];
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x) {
+        const int g = seg_of(nzoff, nsys, q);
+        const int32_t c = colind[g][q - nzoff[g]];
+        if (c < 0 || c >= off[g + 1] - off[g]) atomicOr(err, ERR_COLIND);
+        ci[q] = (int32_t)(c + off[g]);
+    }
+}
+
+// lists L_k of the column unions: {k} for a system of kind 0 (pattern of A), the rows of
+// column k for kind 1 (pattern of A^2); counts, then the lists
+__global__ void k_list_counts(int32_t nsys, const int64_t *__restrict__ off, const int32_t *__restrict__ kind,
+                              const int32_t *__restrict__ colptr, int32_t *__restrict__ counts)
+{
+    const int64_t ntot = off[nsys];
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ntot; k += (int64_t)gridDim.x * blockDim.x)
+        counts[k] = kind[seg_of(off, nsys, k)] ? colptr[k + 1] - colptr[k] : 1;
+}
+
+__global__ void k_list_fill(int32_t nsys, const int64_t *__restrict__ off, const int32_t *__restrict__ kind,
+                            const int32_t *__restrict__ colptr, const int32_t *__restrict__ rowind,
+                            const int32_t *__restrict__ Lptr, int32_t *__restrict__ Lind)
+{
+    const int64_t ntot = off[nsys];
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ntot; k += (int64_t)gridDim.x * blockDim.x) {
+        if (!kind[seg_of(off, nsys, k)]) {
+            Lind[Lptr[k]] = (int32_t)k;
+        } else {
+            for (int32_t q = colptr[k]; q < colptr[k + 1]; ++q) Lind[Lptr[k] + (q - colptr[k])] = rowind[q];
+        }
+    }
+}
+
+// per system: tot[g] = ptr[off[g+1]] - ptr[off[g]], mx[g] = max over its columns of
+// ptr[k+1] - ptr[k] (mx zeroed first)
+__global__ void k_seg_ptr_stats(int32_t nsys, const int64_t *__restrict__ off, const int32_t *__restrict__ ptr,
+                                int64_t *__restrict__ tot, int32_t *__restrict__ mx)
+{
+    const int64_t ntot = off[nsys];
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ntot; k += (int64_t)gridDim.x * blockDim.x) {
+        const int g = seg_of(off, nsys, k);
+        atomicMax(mx + g, ptr[k + 1] - ptr[k]);
+        if (k == off[g]) tot[g] = (int64_t)ptr[off[g + 1]] - ptr[k];
+    }
+}
+
+// dst_g[j] = src_g[j] - sub_g over segments laid end to end
+__global__ void k_unstack(int32_t nseg, const int64_t *__restrict__ start, const int32_t *const *__restrict__ src,
+                          int32_t *const *__restrict__ dst, const int32_t *__restrict__ sub)
+{
+    const int64_t total = start[nseg];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int g = seg_of(start, nseg, e);
+        const int64_t j = e - start[g];
+        dst[g][j] = src[g][j] - sub[g];
+    }
+}
+
+// dst_g[j] = val_g[perm_g[j]] over segments laid end to end
+__global__ void k_gather_seg(int32_t nseg, const int64_t *__restrict__ start, const double *const *__restrict__ val,
+                             const int32_t *const *__restrict__ perm, double *const *__restrict__ dst)
+{
+    const int64_t total = start[nseg];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int g = seg_of(start, nseg, e);
+        const int64_t j = e - start[g];
+        dst[g][j] = val[g][perm[g][j]];
+    }
+}
+
+// out[g] = smallest j with a_g[j] != 0 (INT_MAX if none; out filled with INT_MAX first)
+__global__ void k_first_nonzero_seg(int32_t nseg, const int64_t *__restrict__ start, const int32_t *const *__restrict__ a,
+                                    int32_t *__restrict__ out)
+{
+    const int64_t total = start[nseg];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int g = seg_of(start, nseg, e);
+        const int64_t j = e - start[g];
+        if (a[g][j] != 0) atomicMin(out + g, (int32_t)j);
+    }
+}
+
 __global__ void k_add_i32(int64_t count, const int32_t *__restrict__ src, int32_t add, int32_t *__restrict__ dst)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
@@ -556,6 +677,58 @@ int launch_gather_f32_f64(cudaStream_t st, int64_t count, const int32_t *idx, co
     if (count <= 0) return 0;
     k_gather_f32_f64<<<grid_for(count), kThreads, 0, st>>>(count, idx, src, dst);
     return check_launch();
+}
+
+namespace {
+inline int grid_cap(int64_t work) { int g = grid_for(work); return g > 8 * 1216 ? 8 * 1216 : g; }
+}  // namespace
+
+int launch_stack_csr(cudaStream_t st, int32_t nsys, int64_t ntot, int64_t nnz, const int64_t *off, const int64_t *nzoff,
+                     const int32_t *const *rowptr, const int32_t *const *colind, int32_t *rp, int32_t *ci, int *d_err)
+{
+    k_stack_rows<<<grid_cap(ntot + 1), kThreads, 0, st>>>(nsys, off, nzoff, rowptr, rp, d_err);
+    if (nnz > 0) k_stack_cols<<<grid_cap(nnz), kThreads, 0, st>>>(nsys, off, nzoff, colind, ci, d_err);
+    return check_launch(2);
+}
+
+int launch_union_lists(cudaStream_t st, int32_t nsys, int64_t ntot, const int64_t *off, const int32_t *kind,
+                       const int32_t *colptr, const int32_t *rowind, int32_t *counts, const int32_t *Lptr, int32_t *Lind)
+{
+    if (!Lptr) k_list_counts<<<grid_cap(ntot), kThreads, 0, st>>>(nsys, off, kind, colptr, counts);
+    else k_list_fill<<<grid_cap(ntot), kThreads, 0, st>>>(nsys, off, kind, colptr, rowind, Lptr, Lind);
+    return check_launch();
+}
+
+int launch_seg_ptr_stats(cudaStream_t st, int32_t nsys, int64_t ntot, const int64_t *off, const int32_t *ptr,
+                         int64_t *tot, int32_t *mx)
+{
+    if (cudaMemsetAsync(mx, 0, (size_t)nsys * sizeof(int32_t), st) != cudaSuccess) return -1;
+    k_seg_ptr_stats<<<grid_cap(ntot), kThreads, 0, st>>>(nsys, off, ptr, tot, mx);
+    return check_launch();
+}
+
+int launch_unstack(cudaStream_t st, int32_t nseg, int64_t total, const int64_t *start, const int32_t *const *src,
+                   int32_t *const *dst, const int32_t *sub)
+{
+    if (total <= 0) return 0;
+    k_unstack<<<grid_cap(total), kThreads, 0, st>>>(nseg, start, src, dst, sub);
+    return check_launch();
+}
+
+int launch_gather_seg(cudaStream_t st, int32_t nseg, int64_t total, const int64_t *start, const double *const *val,
+                      const int32_t *const *perm, double *const *dst)
+{
+    if (total <= 0) return 0;
+    k_gather_seg<<<grid_cap(total), kThreads, 0, st>>>(nseg, start, val, perm, dst);
+    return check_launch();
+}
+
+int launch_first_nonzero_seg(cudaStream_t st, int32_t nseg, int64_t total, const int64_t *start,
+                             const int32_t *const *a, int32_t *out)
+{
+    k_fill_i32<<<grid_for(nseg), kThreads, 0, st>>>(nseg, INT_MAX, out);
+    if (total > 0) k_first_nonzero_seg<<<grid_cap(total), kThreads, 0, st>>>(nseg, start, a, out);
+    return check_launch(2);
 }
 
 int launch_add_i32(cudaStream_t st, int64_t count, const int32_t *src, int32_t add, int32_t *dst)

@@ -57,8 +57,19 @@ struct spai_ctx_s {
 
 namespace {
 
+// One device allocation holding the arrays of many handles (a batched build): released
+// when the last handle that points into it is.
+struct Arena {
+    std::atomic<int> refs{0};
+    spai_ctx ctx = nullptr;
+    void *mem = nullptr;
+};
+
+void arena_release(Arena *a);
+
 struct Sym {
     std::atomic<int> refs{1};  // handles on other contexts (host threads) may share it
+    Arena *arena = nullptr;    // non-null: the arrays live in this arena, not in own allocations
     spai_ctx ctx = nullptr;
     int32_t n = 0, nnzA = 0, kind = 0;
     int32_t *a_rowptr = nullptr, *a_colind = nullptr;            // copy of A's CSR pattern
@@ -87,6 +98,7 @@ struct spai_pc_s {
     double *a_cval = nullptr;  // this matrix's values in CSC order
     int32_t *status = nullptr;
     bool diag = false;         // diagonal factor (n values, SPAI_UPDATE_DIAGONAL)
+    Arena *arena = nullptr;    // non-null: fval*, a_cval and status live in this arena
 };
 
 struct spai_affine_s {
@@ -317,9 +329,21 @@ spai_status validate_device_csr(spai_ctx ctx, const spai_csr *A, const char *nam
     return SPAI_OK;
 }
 
+void arena_release(Arena *a)
+{
+    if (!a || a->refs.fetch_sub(1) > 1) return;
+    dfree(a->ctx, a->mem);
+    delete a;
+}
+
 void sym_release(Sym *s)
 {
     if (!s || s->refs.fetch_sub(1) > 1) return;
+    if (s->arena) {
+        arena_release(s->arena);
+        delete s;
+        return;
+    }
     spai_ctx ctx = s->ctx;
     dfree(ctx, s->a_rowptr);
     dfree(ctx, s->a_colind);
@@ -1073,15 +1097,30 @@ spai_status run_columns_batch(spai_ctx ctx, int32_t nsys, spai_pc *pcs)
         dfree(ctx, d_start);
     }
     // first singular column of every system (INT_MAX if none), one read-back for all
-    int32_t *d_first = nullptr;
-    if ((st = dalloc_n(ctx, &d_first, nsys))) return st;
-    for (int i = 0; i < nsys; ++i)
-        if (pcs[i]->sym->n) KL(launch_first_nonzero(ctx->stream, pcs[i]->sym->n, pcs[i]->status, d_first + i), "status scan");
+    // (a segmented scan over the systems' status arrays: two launches for the whole batch)
+    std::vector<int64_t> sstart((size_t)nsys + 1, 0);
+    std::vector<const int32_t *> sptr((size_t)nsys);
+    for (int i = 0; i < nsys; ++i) {
+        sstart[i + 1] = sstart[i] + pcs[i]->sym->n;
+        sptr[i] = pcs[i]->status;
+    }
+    const size_t o_ptr = ((size_t)nsys + 1) * 8, o_first = o_ptr + (size_t)nsys * 8;
+    char *d_scan = nullptr;
+    if ((st = dalloc(ctx, (void **)&d_scan, o_first + (size_t)nsys * 4))) return st;
+    int32_t *d_first = (int32_t *)(d_scan + o_first);
     std::vector<int32_t> first((size_t)nsys);
-    CU(cudaMemcpyAsync(first.data(), d_first, (size_t)nsys * 4, cudaMemcpyDeviceToHost, ctx->stream), "read back");
+    cudaError_t ce = cudaMemcpyAsync(d_scan, sstart.data(), o_ptr, cudaMemcpyHostToDevice, ctx->stream);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(d_scan + o_ptr, sptr.data(), (size_t)nsys * 8, cudaMemcpyHostToDevice, ctx->stream);
+    if (ce == cudaSuccess &&
+        launch_first_nonzero_seg(ctx->stream, nsys, sstart[nsys], (const int64_t *)d_scan,
+                                 (const int32_t *const *)(d_scan + o_ptr), d_first))
+        ce = cudaGetLastError();
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(first.data(), d_first, (size_t)nsys * 4, cudaMemcpyDeviceToHost, ctx->stream);
     int h = 0;
-    st = read_err(ctx, &h);
-    dfree(ctx, d_first);
+    st = ce == cudaSuccess ? read_err(ctx, &h) : cuda_fail(ctx, ce, "status scan");
+    dfree(ctx, d_scan);
     if (st) return st;
     if (h) return fail(ctx, SPAI_EINVAL, "batched column least squares failed (device error 0x%x)", h);
     for (int i = 0; i < nsys; ++i)
@@ -1089,6 +1128,364 @@ spai_status run_columns_batch(spai_ctx ctx, int32_t nsys, spai_pc *pcs)
             return fail(ctx, SPAI_ESINGULAR, "system %d, column %d: rank-deficient least-squares problem (column set "
                         "to 0)", i, first[i]);
     return SPAI_OK;
+}
+
+// Pattern analyses and factor storage of a batch of systems at once: the systems are
+// stacked into one block-diagonal matrix (global indices), each phase of the analysis --
+// transposition, the column lists of the unions, the unions J_k and I_k, the row pattern of
+// P -- runs once over the stacked matrix (its unions never leave a diagonal block), and the
+// per-system arrays (local indices, as spai_build makes them) are carved from one arena by
+// a single unstacking launch.  The CUDA calls do not grow with nsys except for a few small
+// host-to-device tables.  Every system must have n >= 1.
+spai_status build_batch_stacked(spai_ctx ctx, int32_t nsys, const spai_csr *A, const int32_t *kinds,
+                                const int32_t *precs, std::vector<spai_pc> &pcs)
+{
+    cudaStream_t cs = ctx->stream;
+    spai_status st = SPAI_OK;
+    std::vector<int64_t> off((size_t)nsys + 1, 0), nzoff((size_t)nsys + 1, 0);
+    for (int i = 0; i < nsys; ++i) {
+        off[i + 1] = off[i] + A[i].n;
+        nzoff[i + 1] = nzoff[i] + A[i].nnz;
+    }
+    const int64_t ntot = off[nsys], nnz = nzoff[nsys];
+    if (ntot >= INT32_MAX || nnz >= INT32_MAX)
+        return fail(ctx, SPAI_EINVAL, "the stacked batch exceeds 2^31 rows or nonzeros");
+    std::vector<void *> tmp;  // stacked temporaries, freed at the end
+    auto cleanup = [&](spai_status rc) {  // on failure the handles made so far go too
+        for (void *p : tmp) dfree(ctx, p);
+        if (rc != SPAI_OK) {
+            for (spai_pc pc : pcs)
+                if (pc) spai_pc_destroy(pc);
+            pcs.clear();
+        }
+        return rc;
+    };
+    auto talloc = [&](auto **p, int64_t count) -> spai_status {
+        spai_status s2 = dalloc_n(ctx, p, count);
+        if (!s2) tmp.push_back((void *)*p);
+        return s2;
+    };
+#define TRY(x)                                          \
+    do {                                                \
+        if ((st = (x)) != SPAI_OK) return cleanup(st);  \
+    } while (0)
+#define TRYC(call, what)                                            \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cleanup(cuda_fail(ctx, e_, what)); \
+    } while (0)
+#define TRYK(call, what)                                                                                    \
+    do {                                                                                                    \
+        if ((call) != 0)                                                                                    \
+            return cleanup(fail(ctx, SPAI_ECUDA, "%s: kernel launch failed (%s)", what,                     \
+                                cudaGetErrorString(cudaGetLastError())));                                   \
+    } while (0)
+    // ---- system table: offsets, kinds, the callers' pattern arrays
+    int64_t *d_off = nullptr, *d_nzoff = nullptr;
+    int32_t *d_kind = nullptr;
+    const int32_t **d_rp = nullptr, **d_ci = nullptr;
+    TRY(talloc(&d_off, nsys + 1));
+    TRY(talloc(&d_nzoff, nsys + 1));
+    TRY(talloc(&d_kind, nsys));
+    TRY(talloc(&d_rp, nsys));
+    TRY(talloc(&d_ci, nsys));
+    {
+        std::vector<const int32_t *> hrp((size_t)nsys), hci((size_t)nsys);
+        for (int i = 0; i < nsys; ++i) {
+            hrp[i] = A[i].rowptr;
+            hci[i] = A[i].colind;
+        }
+        TRYC(cudaMemcpyAsync(d_off, off.data(), off.size() * 8, cudaMemcpyHostToDevice, cs), "table");
+        TRYC(cudaMemcpyAsync(d_nzoff, nzoff.data(), nzoff.size() * 8, cudaMemcpyHostToDevice, cs), "table");
+        TRYC(cudaMemcpyAsync(d_kind, kinds, (size_t)nsys * 4, cudaMemcpyHostToDevice, cs), "table");
+        TRYC(cudaMemcpyAsync(d_rp, hrp.data(), (size_t)nsys * 8, cudaMemcpyHostToDevice, cs), "table");
+        TRYC(cudaMemcpyAsync(d_ci, hci.data(), (size_t)nsys * 8, cudaMemcpyHostToDevice, cs), "table");
+        TRYC(cudaStreamSynchronize(cs), "sync");  // the host tables are read by the copies above
+    }
+    // ---- stacked CSR (checked per system), its transpose
+    int32_t *rp = nullptr, *ci = nullptr, *colptr = nullptr, *rowind = nullptr, *perm = nullptr;
+    void *ttemp = nullptr;
+    TRY(talloc(&rp, ntot + 1));
+    TRY(talloc(&ci, nnz));
+    TRY(talloc(&colptr, ntot + 1));
+    TRY(talloc(&rowind, nnz));
+    TRY(talloc(&perm, nnz));
+    {
+        ProfScope ps_(ctx, "analysis:stack", 0.0, 0.0);
+        TRYK(launch_stack_csr(cs, nsys, ntot, nnz, d_off, d_nzoff, d_rp, d_ci, rp, ci, ctx->d_err), "stack");
+        TRYK(launch_validate_csr(cs, (int32_t)ntot, (int32_t)nnz, rp, ci, ctx->d_err), "validate");
+    }
+    int herr = 0;
+    TRY(read_err(ctx, &herr));
+    if (herr & ERR_ROWPTR) return cleanup(fail(ctx, SPAI_EINVAL, "a matrix of the batch has an invalid row pointer array"));
+    if (herr) return cleanup(fail(ctx, SPAI_EINVAL, "a matrix of the batch has column indices out of range or not "
+                                  "strictly increasing in a row (device error 0x%x)", herr));
+    {
+        char *t = nullptr;
+        TRY(talloc(&t, (int64_t)transpose_temp_bytes((int32_t)ntot, (int32_t)std::max<int64_t>(nnz, 1))));
+        ttemp = t;
+    }
+    {
+        ProfScope ps_(ctx, "analysis:transpose", 0.0, 0.0);
+        TRYK(launch_transpose(cs, (int32_t)ntot, (int32_t)nnz, rp, ci, colptr, rowind, perm, ttemp, ctx->d_err), "transpose");
+    }
+    // ---- union lists L_k ({k} or the rows of column k) and their longest
+    int32_t *counts = nullptr, *Lptr = nullptr, *Lind = nullptr, *Jptr = nullptr, *Jind = nullptr, *Iptr = nullptr,
+            *Ilist = nullptr, *d_scal = nullptr;
+    char *stemp = nullptr;
+    TRY(talloc(&counts, ntot + 1));
+    TRY(talloc(&Lptr, ntot + 1));
+    TRY(talloc(&stemp, (int64_t)scan_temp_bytes(ntot)));
+    TRY(talloc(&d_scal, 4));
+    {
+        ProfScope ps_(ctx, "analysis:lists", 0.0, 0.0);
+        TRYK(launch_union_lists(cs, nsys, ntot, d_off, d_kind, colptr, rowind, counts, nullptr, nullptr), "list counts");
+        TRYK(launch_exclusive_scan(cs, counts, Lptr, ntot, stemp, ctx->d_err), "scan");
+        TRYK(launch_max_i32_diff(cs, (int32_t)ntot, Lptr, d_scal), "longest list");
+    }
+    int32_t h2[2] = {0, 0};
+    TRYC(cudaMemcpyAsync(&h2[0], Lptr + ntot, 4, cudaMemcpyDeviceToHost, cs), "read back");
+    TRYC(cudaMemcpyAsync(&h2[1], d_scal, 4, cudaMemcpyDeviceToHost, cs), "read back");
+    TRY(read_err(ctx, &herr));
+    if (herr) return cleanup(fail(ctx, SPAI_EINVAL, "pattern analysis failed (device error 0x%x)", herr));
+    if (h2[1] > colunion_max_lists())
+        return cleanup(fail(ctx, SPAI_EINVAL, "a column has %d entries; at most %d are supported", h2[1],
+                            colunion_max_lists()));
+    TRY(talloc(&Lind, h2[0]));
+    TRYK(launch_union_lists(cs, nsys, ntot, d_off, d_kind, colptr, rowind, nullptr, Lptr, Lind), "list fill");
+    // ---- J_k = union over L_k of rows(A(:,j)); per system its total and longest column
+    int64_t *d_tot = nullptr;
+    int32_t *d_mx = nullptr;
+    TRY(talloc(&d_tot, 2 * (int64_t)nsys));
+    TRY(talloc(&d_mx, 2 * (int64_t)nsys));
+    TRY(talloc(&Jptr, ntot + 1));
+    {
+        ProfScope ps_(ctx, "analysis:J", 0.0, 0.0);
+        TRYK(launch_colunion_count(cs, (int32_t)ntot, Lptr, Lind, colptr, rowind, counts, ctx->d_err), "J count");
+        TRYK(launch_exclusive_scan(cs, counts, Jptr, ntot, stemp, ctx->d_err), "scan");
+        TRYK(launch_seg_ptr_stats(cs, nsys, ntot, d_off, Jptr, d_tot, d_mx), "J sizes");
+    }
+    std::vector<int64_t> totJ((size_t)nsys), totI((size_t)nsys);
+    std::vector<int32_t> mxJ((size_t)nsys), mxI((size_t)nsys);
+    TRYC(cudaMemcpyAsync(totJ.data(), d_tot, (size_t)nsys * 8, cudaMemcpyDeviceToHost, cs), "read back");
+    TRYC(cudaMemcpyAsync(mxJ.data(), d_mx, (size_t)nsys * 4, cudaMemcpyDeviceToHost, cs), "read back");
+    TRY(read_err(ctx, &herr));
+    if (herr & ERR_OVERFLOW) return cleanup(fail(ctx, SPAI_EINVAL, "index sets exceed 2^31 entries"));
+    if (herr) return cleanup(fail(ctx, SPAI_EINVAL, "pattern analysis failed (device error 0x%x)", herr));
+    int64_t nJ = 0;
+    for (int i = 0; i < nsys; ++i) {
+        nJ += totJ[i];
+        if (mxJ[i] > colunion_max_lists())
+            return cleanup(fail(ctx, SPAI_EINVAL, "system %d: a column pattern has %d entries; at most %d are supported",
+                                i, mxJ[i], colunion_max_lists()));
+    }
+    if (nJ >= INT32_MAX) return cleanup(fail(ctx, SPAI_EINVAL, "the stacked pattern of P exceeds 2^31 entries"));
+    TRY(talloc(&Jind, nJ));
+    {
+        ProfScope ps_(ctx, "analysis:J", 0.0, 0.0);
+        TRYK(launch_colunion_fill(cs, (int32_t)ntot, Lptr, Lind, colptr, rowind, Jptr, Jind, ctx->d_err), "J fill");
+    }
+    // ---- rows of P (the transpose of the J pattern) and the map J position -> P row position
+    int32_t *prp = nullptr, *pci = nullptr, *pperm = nullptr, *pmap = nullptr;
+    TRY(talloc(&prp, ntot + 1));
+    TRY(talloc(&pci, nJ));
+    TRY(talloc(&pperm, nJ));
+    TRY(talloc(&pmap, nJ));
+    {
+        char *t = nullptr;
+        TRY(talloc(&t, (int64_t)transpose_temp_bytes((int32_t)ntot, (int32_t)std::max<int64_t>(nJ, 1))));
+        {
+            ProfScope ps_(ctx, "analysis:P_rows", 0.0, 0.0);
+            TRYK(launch_transpose(cs, (int32_t)ntot, (int32_t)nJ, Jptr, Jind, prp, pci, pperm, t, ctx->d_err),
+                 "transpose pattern");
+        }
+    }
+    {
+        ProfScope ps_(ctx, "analysis:P_rows", 0.0, 0.0);
+        TRYK(launch_invert_perm(cs, nJ, pperm, pmap), "invert");
+    }
+    // ---- I_k = union over J_k of rows(A(:,j))
+    TRY(talloc(&Iptr, ntot + 1));
+    {
+        ProfScope ps_(ctx, "analysis:I", 0.0, 0.0);
+        TRYK(launch_colunion_count(cs, (int32_t)ntot, Jptr, Jind, colptr, rowind, counts, ctx->d_err), "I count");
+        TRYK(launch_exclusive_scan(cs, counts, Iptr, ntot, stemp, ctx->d_err), "scan");
+        TRYK(launch_seg_ptr_stats(cs, nsys, ntot, d_off, Iptr, d_tot + nsys, d_mx + nsys), "I sizes");
+    }
+    TRYC(cudaMemcpyAsync(totI.data(), d_tot + nsys, (size_t)nsys * 8, cudaMemcpyDeviceToHost, cs), "read back");
+    TRYC(cudaMemcpyAsync(mxI.data(), d_mx + nsys, (size_t)nsys * 4, cudaMemcpyDeviceToHost, cs), "read back");
+    TRY(read_err(ctx, &herr));
+    if (herr & ERR_OVERFLOW) return cleanup(fail(ctx, SPAI_EINVAL, "index sets exceed 2^31 entries"));
+    if (herr) return cleanup(fail(ctx, SPAI_EINVAL, "pattern analysis failed (device error 0x%x)", herr));
+    int64_t nIt = 0;
+    for (int i = 0; i < nsys; ++i) {
+        nIt += totI[i];
+        if (!spai_columns_fit(mxI[i], mxJ[i]))
+            return cleanup(fail(ctx, SPAI_EINVAL, "system %d: column problem of %d x %d exceeds the shared-memory tile",
+                                i, mxI[i], mxJ[i]));
+    }
+    if (nIt >= INT32_MAX) return cleanup(fail(ctx, SPAI_EINVAL, "the stacked index sets exceed 2^31 entries"));
+    TRY(talloc(&Ilist, nIt));
+    {
+        ProfScope ps_(ctx, "analysis:I", 0.0, 0.0);
+        TRYK(launch_colunion_fill(cs, (int32_t)ntot, Jptr, Jind, colptr, rowind, Iptr, Ilist, ctx->d_err), "I fill");
+    }
+
+    // ---- the arena: every system's analysis (local indices) and factor storage
+    auto r256 = [](size_t b) { return ((b ? b : 16) + 255) / 256 * 256; };
+    std::vector<size_t> base((size_t)nsys);
+    size_t abytes = 0;
+    std::vector<int64_t> jb((size_t)nsys + 1, 0), ib((size_t)nsys + 1, 0);
+    for (int i = 0; i < nsys; ++i) {
+        jb[i + 1] = jb[i] + totJ[i];
+        ib[i + 1] = ib[i] + totI[i];
+        const size_t n1 = (size_t)A[i].n + 1, nz = (size_t)A[i].nnz, nzP = (size_t)totJ[i];
+        const size_t vb = precs[i] == 2 ? 2 : precs[i] == 1 ? 4 : 8;
+        base[i] = abytes;
+        abytes += 2 * r256(n1 * 4) + 3 * r256(nz * 4);  // a_rowptr, a_colptr; a_colind, a_rowind, a_perm
+        if (kinds[i]) abytes += 2 * r256(n1 * 4) + 3 * r256(nzP * 4);  // Jptr, p_rowptr; Jind, p_colind, p_map
+        abytes += r256(n1 * 4) + r256((size_t)totI[i] * 4);          // Iptr, Ilist
+        abytes += r256(nzP * vb) + r256(nz * 8) + r256((size_t)A[i].n * 4);  // factor, a_cval, status
+    }
+    Arena *arena = new Arena();
+    arena->ctx = ctx;
+    if ((st = dalloc(ctx, &arena->mem, abytes))) {
+        delete arena;
+        return cleanup(st);
+    }
+    char *am = (char *)arena->mem;
+    TRYC(cudaMemsetAsync(am, 0, abytes, cs), "zero arena");  // factors and status start at zero
+    // segments of the unstacking: (source, destination, count, subtracted offset)
+    std::vector<const int32_t *> usrc;
+    std::vector<int32_t *> udst;
+    std::vector<int32_t> usub;
+    std::vector<int64_t> ustart(1, 0);
+    auto seg = [&](const int32_t *src, int32_t *dst, int64_t count, int64_t sub) {
+        usrc.push_back(src);
+        udst.push_back(dst);
+        usub.push_back((int32_t)sub);
+        ustart.push_back(ustart.back() + count);
+    };
+    std::vector<const double *> gval;
+    std::vector<const int32_t *> gperm;
+    std::vector<double *> gdst;
+    std::vector<int64_t> gstart(1, 0);
+    std::vector<const int32_t *> sstat;
+    std::vector<int64_t> sstart(1, 0);
+    pcs.assign((size_t)nsys, nullptr);
+    for (int i = 0; i < nsys; ++i) {
+        const int32_t n = A[i].n;
+        const size_t n1 = (size_t)n + 1, nz = (size_t)A[i].nnz, nzP = (size_t)totJ[i];
+        char *p = am + base[i];
+        auto take = [&](size_t bytes) {
+            char *r = p;
+            p += r256(bytes);
+            return r;
+        };
+        Sym *s = new Sym();
+        s->ctx = ctx;
+        s->arena = arena;
+        arena->refs++;
+        s->n = n;
+        s->nnzA = (int32_t)nz;
+        s->kind = kinds[i];
+        s->a_rowptr = (int32_t *)take(n1 * 4);
+        s->a_colptr = (int32_t *)take(n1 * 4);
+        s->a_colind = (int32_t *)take(nz * 4);
+        s->a_rowind = (int32_t *)take(nz * 4);
+        s->a_perm = (int32_t *)take(nz * 4);
+        seg(rp + off[i], s->a_rowptr, (int64_t)n1, nzoff[i]);
+        seg(ci + nzoff[i], s->a_colind, (int64_t)nz, off[i]);
+        seg(colptr + off[i], s->a_colptr, (int64_t)n1, nzoff[i]);
+        seg(rowind + nzoff[i], s->a_rowind, (int64_t)nz, off[i]);
+        seg(perm + nzoff[i], s->a_perm, (int64_t)nz, nzoff[i]);
+        s->nnzP = (int32_t)nzP;
+        if (kinds[i]) {
+            s->alias = false;
+            s->Jptr = (int32_t *)take(n1 * 4);
+            s->p_rowptr = (int32_t *)take(n1 * 4);
+            s->Jind = (int32_t *)take(nzP * 4);
+            s->p_colind = (int32_t *)take(nzP * 4);
+            s->p_map = (int32_t *)take(nzP * 4);
+            seg(Jptr + off[i], s->Jptr, (int64_t)n1, jb[i]);
+            seg(Jind + jb[i], s->Jind, (int64_t)nzP, off[i]);
+            seg(prp + off[i], s->p_rowptr, (int64_t)n1, jb[i]);
+            seg(pci + jb[i], s->p_colind, (int64_t)nzP, off[i]);
+            seg(pmap + jb[i], s->p_map, (int64_t)nzP, jb[i]);
+        } else {
+            s->alias = true;  // P's pattern is A's: the same arrays as spai_build uses
+            s->Jptr = s->a_colptr;
+            s->Jind = s->a_rowind;
+            s->p_rowptr = s->a_rowptr;
+            s->p_colind = s->a_colind;
+            s->p_map = s->a_perm;
+        }
+        s->Iptr = (int32_t *)take(n1 * 4);
+        s->Ilist = (int32_t *)take((size_t)totI[i] * 4);
+        s->nI = (int32_t)totI[i];
+        seg(Iptr + off[i], s->Iptr, (int64_t)n1, ib[i]);
+        seg(Ilist + ib[i], s->Ilist, totI[i], off[i]);
+        s->maxI = mxI[i];
+        s->maxJ = mxJ[i];
+        spai_pc pc = new spai_pc_s();
+        pc->ctx = ctx;
+        pc->sym = s;
+        pc->root = pc;
+        pc->arena = arena;
+        arena->refs++;
+        const size_t vb = precs[i] == 2 ? 2 : precs[i] == 1 ? 4 : 8;
+        char *fv = take(nzP * vb);
+        if (precs[i] == 2) pc->fval16 = (uint16_t *)fv;
+        else if (precs[i] == 1) pc->fval32 = (float *)fv;
+        else pc->fval = (double *)fv;
+        pc->a_cval = (double *)take(nz * 8);
+        pc->status = (int32_t *)take((size_t)n * 4);
+        pcs[i] = pc;
+        gval.push_back(A[i].val);
+        gperm.push_back(s->a_perm);
+        gdst.push_back(pc->a_cval);
+        gstart.push_back(gstart.back() + (int64_t)nz);
+    }
+    // device copies of the segment tables (one buffer), the unstacking and the value gathers
+    const int nu = (int)usrc.size();
+    const size_t tbytes = (size_t)(nu + 1) * 8 + (size_t)nu * 8 * 2 + r256((size_t)nu * 4) + (size_t)(nsys + 1) * 8 +
+                          (size_t)nsys * 8 * 3 + 256;
+    char *d_tab = nullptr;
+    TRY(talloc(&d_tab, (int64_t)tbytes));
+    {
+        std::vector<char> h(tbytes, 0);
+        size_t o = 0;
+        auto put = [&](const void *src, size_t bytes) {
+            memcpy(h.data() + o, src, bytes);
+            const size_t at = o;
+            o += (bytes + 15) / 16 * 16;
+            return at;
+        };
+        const size_t o_us = put(ustart.data(), ustart.size() * 8), o_src = put(usrc.data(), usrc.size() * 8),
+                     o_dst = put(udst.data(), udst.size() * 8), o_sub = put(usub.data(), usub.size() * 4),
+                     o_gs = put(gstart.data(), gstart.size() * 8), o_gv = put(gval.data(), gval.size() * 8),
+                     o_gp = put(gperm.data(), gperm.size() * 8), o_gd = put(gdst.data(), gdst.size() * 8);
+        TRYC(cudaMemcpyAsync(d_tab, h.data(), o, cudaMemcpyHostToDevice, cs), "tables");
+        TRYC(cudaStreamSynchronize(cs), "sync");  // h is read by the copy above
+        {
+            ProfScope ps_(ctx, "analysis:unstack", 0.0, 0.0);
+            TRYK(launch_unstack(cs, nu, ustart.back(), (const int64_t *)(d_tab + o_us), (const int32_t *const *)(d_tab + o_src),
+                                (int32_t *const *)(d_tab + o_dst), (const int32_t *)(d_tab + o_sub)),
+                 "unstack");
+        }
+        {
+            ProfScope ps_(ctx, "gather_csc", 0.0, 20.0 * (double)nnz);
+            TRYK(launch_gather_seg(cs, nsys, gstart.back(), (const int64_t *)(d_tab + o_gs),
+                                   (const double *const *)(d_tab + o_gv), (const int32_t *const *)(d_tab + o_gp),
+                                   (double *const *)(d_tab + o_gd)),
+                 "gather values");
+        }
+    }
+    TRYC(cudaStreamSynchronize(cs), "sync");  // the stacked temporaries are released after their last use
+#undef TRY
+#undef TRYC
+#undef TRYK
+    return cleanup(SPAI_OK);
 }
 
 }  // namespace
@@ -1112,8 +1509,31 @@ extern "C" spai_status spai_build_batch(spai_ctx ctx, int32_t nsys, const spai_c
         if (!is_device_ptr(A[i].rowptr) ||
             (A[i].nnz > 0 && (!is_device_ptr(A[i].colind) || !is_device_ptr(A[i].val))))
             return fail(ctx, SPAI_EINVAL, "system %d: arrays must be device memory", i);
-        KL(launch_validate_csr(ctx->stream, A[i].n, A[i].nnz, A[i].rowptr, A[i].colind, ctx->d_err), "validate");
     }
+    // two or more systems, none empty: the stacked analysis (its CUDA calls do not grow with
+    // the number of systems); otherwise one analysis per system
+    bool stacked = nsys >= 2;
+    int64_t ntot = 0, nnztot = 0;
+    for (int i = 0; i < nsys; ++i) {
+        stacked = stacked && A[i].n >= 1;
+        ntot += A[i].n;
+        nnztot += A[i].nnz;
+    }
+    stacked = stacked && ntot < INT32_MAX && nnztot < INT32_MAX;
+    if (stacked) {
+        std::vector<spai_pc> pcs;
+        if ((st = build_batch_stacked(ctx, nsys, A, kinds.data(), precs.data(), pcs))) return st;
+        st = run_columns_batch(ctx, nsys, pcs.data());
+        if (st && st != SPAI_ESINGULAR) {
+            for (spai_pc pc : pcs) spai_pc_destroy(pc);
+            return st;
+        }
+        for (int i = 0; i < nsys; ++i) out[i] = pcs[i];
+        return st;
+    }
+    for (int i = 0; i < nsys; ++i)
+        if (A[i].n)
+            KL(launch_validate_csr(ctx->stream, A[i].n, A[i].nnz, A[i].rowptr, A[i].colind, ctx->d_err), "validate");
     int h = 0;
     if ((st = read_err(ctx, &h))) return st;
     if (h) return fail(ctx, SPAI_EINVAL, "a matrix of the batch is not a valid CSR matrix (device error 0x%x)", h);
@@ -1209,11 +1629,15 @@ extern "C" spai_status spai_pc_destroy(spai_pc pc)
 {
     if (!pc) return SPAI_EINVAL;
     spai_ctx ctx = pc->ctx;
-    dfree(ctx, pc->fval);
-    dfree(ctx, pc->fval32);
-    dfree(ctx, pc->fval16);
-    dfree(ctx, pc->a_cval);
-    dfree(ctx, pc->status);
+    if (pc->arena) {
+        arena_release(pc->arena);
+    } else {
+        dfree(ctx, pc->fval);
+        dfree(ctx, pc->fval32);
+        dfree(ctx, pc->fval16);
+        dfree(ctx, pc->a_cval);
+        dfree(ctx, pc->status);
+    }
     sym_release(pc->sym);
     delete pc;
     return SPAI_OK;

@@ -81,6 +81,25 @@ int launch_spmm(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr,
 int launch_spmm_bf16v(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr, const int32_t *colind,
                       const uint16_t *val, const double *X, double *Y);
 int launch_gather_bf16_f64(cudaStream_t st, int64_t count, const int32_t *idx, const uint16_t *src, double *dst);
+// ---- batches of matrices stacked into one block-diagonal matrix (device tables; systems
+// laid end to end: off / nzoff hold nsys + 1 row / nonzero offsets, start nseg + 1)
+// rp[ntot + 1], ci[nnz] of the stacked CSR; checks each system's rows (ERR_ROWPTR) and
+// column indices (ERR_COLIND)
+int launch_stack_csr(cudaStream_t st, int32_t nsys, int64_t ntot, int64_t nnz, const int64_t *off, const int64_t *nzoff,
+                     const int32_t *const *rowptr, const int32_t *const *colind, int32_t *rp, int32_t *ci, int *d_err);
+// union lists L_k: {k} (kind 0) or the rows of column k (kind 1): counts (Lptr NULL) or fill
+int launch_union_lists(cudaStream_t st, int32_t nsys, int64_t ntot, const int64_t *off, const int32_t *kind,
+                       const int32_t *colptr, const int32_t *rowind, int32_t *counts, const int32_t *Lptr, int32_t *Lind);
+// per system: total entries of a pointer array over its rows and its longest row
+int launch_seg_ptr_stats(cudaStream_t st, int32_t nsys, int64_t ntot, const int64_t *off, const int32_t *ptr,
+                         int64_t *tot, int32_t *mx);
+// dst_g[j] = src_g[j] - sub_g; val gather dst_g[j] = val_g[perm_g[j]]; first nonzero per segment
+int launch_unstack(cudaStream_t st, int32_t nseg, int64_t total, const int64_t *start, const int32_t *const *src,
+                   int32_t *const *dst, const int32_t *sub);
+int launch_gather_seg(cudaStream_t st, int32_t nseg, int64_t total, const int64_t *start, const double *const *val,
+                      const int32_t *const *perm, double *const *dst);
+int launch_first_nonzero_seg(cudaStream_t st, int32_t nseg, int64_t total, const int64_t *start,
+                             const int32_t *const *a, int32_t *out);
 // dst[i] = src[i] + add
 int launch_add_i32(cudaStream_t st, int64_t count, const int32_t *src, int32_t add, int32_t *dst);
 // dst[i] = i; the FP32 / BF16 gathers take idx = NULL for the identity

@@ -183,3 +183,99 @@ def test_batched_solve_restarts_without_preconditioner():
         Xo, io = oracle.block_gmres(oracle.csr_apply(A, w.n), None, w.B, 4, 1e-8, 200)
         assert inf["converged"] and io["converged"]
         assert np.linalg.norm(X - Xo) <= 1e-6 * np.linalg.norm(Xo)
+
+
+def test_stacked_batch_handles_outlive_each_other():
+    """The stacked analysis carves every handle of a batch from one allocation: destroying
+    some handles of the batch leaves the others intact (exports and products against the
+    oracle after the others are gone), and an update, which shares its base's analysis, may
+    be destroyed after its base (a base must stay alive while its update is USED; the
+    shared allocation goes with the last handle)."""
+    import torch
+    sg = _sg()
+    ws = [synth.grid_workload((d, d), "5pt", seed=60 + d, nrhs=4, params=[0.25, 0.4]) for d in (14, 27, 19)]
+    kinds = [oracle.PATTERN_A2, oracle.PATTERN_A, oracle.PATTERN_A2]
+    A1 = [oracle.assemble(w.terms, oracle.coefficients(w.params[0], 1.0), w.n) for w in ws]
+    A2 = [oracle.assemble(w.terms, oracle.coefficients(w.params[1], 1.0), w.n) for w in ws]
+    X = [np.asfortranarray(np.random.default_rng(d).standard_normal((w.n, 4))) for d, w in enumerate(ws)]
+    with context() as ctx:
+        d1 = [dev_csr(A, w.n) for A, w in zip(A1, ws)]
+        d2 = [dev_csr(A, w.n) for A, w in zip(A2, ws)]
+        pcs, _ = sg.spai_build_batch(ctx, d1, kinds)
+        q1, _ = sg.spai_update(ctx, pcs[1], d2[1])
+
+        def apply(h, x, w):
+            Xd = torch.as_tensor(x.T.copy(), device="cuda:0")
+            Yd = torch.empty_like(Xd)
+            sg.spai_pc_apply(ctx, h, 4, Xd, w.n, Yd, w.n)
+            sg.spai_ctx_sync(ctx)
+            return Yd.cpu().numpy().T
+
+        sg.spai_pc_destroy(pcs[0])
+        g2 = export(ctx, pcs[2])
+        Y = [apply(pcs[2], X[2], ws[2])]
+        sg.spai_pc_destroy(pcs[2])
+        gq = export(ctx, q1)
+        Y.append(apply(q1, X[1], ws[1]))
+        sg.spai_pc_destroy(pcs[1])  # the base first: its update still holds the shared allocation
+        sg.spai_pc_destroy(q1)
+    P2 = oracle.spai_build(A1[2], ws[2].n, kinds[2])
+    Q1 = oracle.spai_update(oracle.spai_build(A1[1], ws[1].n, kinds[1]), A2[1], ws[1].n)
+    for g, ref in ((g2, P2), (gq, Q1)):
+        for key in ("Jptr", "Jind", "Iptr", "Ilist", "status"):
+            assert np.array_equal(g[key], getattr(ref, key)), key
+        assert column_rel_err(ref.Jptr, g["val"], ref.val) <= 1e-10
+    for y, ref, x in ((Y[0], P2, X[2]), (Y[1], Q1, X[1])):
+        yr = ref.apply(x)
+        assert np.max(np.abs(y - yr)) <= 1e-10 * np.max(np.abs(yr))
+
+
+def test_stacked_batch_checks_every_system():
+    """Each system's CSR arrays are checked in its own index range: a column index equal to
+    that system's n (inside the stacked matrix's range) and a row pointer that does not end
+    at its nnz are both rejected, with no handle returned."""
+    sg = _sg()
+    ws = [synth.grid_workload((d, d), "5pt", seed=d, nrhs=4, params=[0.5]) for d in (9, 12)]
+    As = [oracle.assemble(w.terms, oracle.coefficients(0.5, 1.0), w.n) for w in ws]
+    rp, ci, va = As[0]
+    bad_col = (rp, np.concatenate([ci[:-1], [ws[0].n]]).astype(np.int32), va)
+    bad_ptr = (np.concatenate([rp[:-1], [rp[-1] - 1]]).astype(np.int32), ci, va)
+    with context() as ctx:
+        good = dev_csr(As[1], ws[1].n)
+        for bad in (bad_col, bad_ptr):
+            with pytest.raises(sg.SpaiError) as e:
+                sg.spai_build_batch(ctx, [dev_csr(bad, ws[0].n), good], [0, 0])
+            assert e.value.status == sg.SPAI_EINVAL
+        # the context stays usable
+        pcs, st = sg.spai_build_batch(ctx, [dev_csr(As[0], ws[0].n), good], [0, 1])
+        g = [export(ctx, pc) for pc in pcs]
+        for pc in pcs:
+            sg.spai_pc_destroy(pc)
+    assert st == 0
+    for gg, A, w, k in zip(g, As, ws, (0, 1)):
+        ref = oracle.spai_build(A, w.n, k)
+        assert np.array_equal(gg["Jind"], ref.Jind) and np.array_equal(gg["Ilist"], ref.Ilist)
+        assert column_rel_err(ref.Jptr, gg["val"], ref.val) <= 1e-10
+
+
+def test_batch_with_an_empty_system():
+    """A batch that holds an n = 0 system takes the per-system analysis; the other systems'
+    results are those of the oracle and the empty system's handle is valid (n = 0)."""
+    import torch
+    sg = _sg()
+    ws = [synth.grid_workload((d, d), "5pt", seed=d, nrhs=4, params=[0.5]) for d in (10, 15)]
+    As = [oracle.assemble(w.terms, oracle.coefficients(0.3, 1.0), w.n) for w in ws]
+    with context() as ctx:
+        rp0 = torch.zeros(1, dtype=torch.int32, device="cuda:0")
+        empty = sg.csr(0, rp0, None, None, nnz=0)
+        pcs, st = sg.spai_build_batch(ctx, [dev_csr(As[0], ws[0].n), empty, dev_csr(As[1], ws[1].n)], [0, 0, 1])
+        assert st == 0
+        info = sg.spai_pc_info(pcs[1])
+        g = [export(ctx, pcs[0]), export(ctx, pcs[2])]
+        for pc in pcs:
+            sg.spai_pc_destroy(pc)
+    assert info["n"] == 0 and info["nnz"] == 0
+    for gg, A, w, k in zip(g, As, ws, (0, 1)):
+        ref = oracle.spai_build(A, w.n, k)
+        assert np.array_equal(gg["Jind"], ref.Jind) and np.array_equal(gg["Ilist"], ref.Ilist)
+        assert column_rel_err(ref.Jptr, gg["val"], ref.val) <= 1e-10
