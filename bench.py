@@ -49,7 +49,7 @@ def parse():
     # host threads (each with its own stream and context) sharing a shift's independent solves
     ap.add_argument("--workers", type=int, default=4)
     # single-kernel case (for profiler captures): H = V^T W or W -= V H at n = side^3, s = 8
-    ap.add_argument("--kernel", default=None, choices=["dot", "update"])
+    ap.add_argument("--kernel", default=None, choices=["dot", "update", "columns"])
     ap.add_argument("--nblk", type=int, default=16)
     ap.add_argument("--orth", default="tensor", choices=["tensor", "fp64"])
     # serving: Poisson arrivals over a pool of 16 3D 7-point grids (sides 24-96)
@@ -206,10 +206,57 @@ def roofline_entry(f, n, s, fp64_probe=None):
     return out
 
 
+def run_columns_case(args):
+    """The batched build on its own (`--kernel columns`): spai_build_batch of the
+    many-small-systems workload (`--batched-systems` 2D 5-point systems, FP32 factors),
+    warm-up builds (the first one tunes the team sizes) then timed builds, with the
+    library's per-phase device times."""
+    import torch
+    import synth
+    import paper_1809_06574_gb300 as sg
+    ws = synth.batched_2d(args.batched_systems)
+    kinds = [(sg.PATTERN_A if w.extra["pattern"] == "A" else sg.PATTERN_A2) | sg.PREC_FP32 for w in ws]
+    stream = torch.cuda.current_stream()
+    ctx = sg.spai_ctx_create(stream.cuda_stream, 0)
+    As, keep = [], []
+    for w in ws:
+        aff = sg.spai_affine_create(ctx, [sg.csr(w.n, *t) for t in w.terms])
+        _, nnz, rp, ci = sg.spai_affine_pattern(aff)
+        va = torch.empty(nnz, dtype=torch.float64, device="cuda")
+        sg.spai_assemble(ctx, aff, sg.affine_coefficients(w.params[0], 1.0), va)
+        As.append(sg.csr(w.n, rp, ci, va, nnz))
+        keep.append((aff, va))
+
+    def once():
+        for pc in sg.spai_build_batch(ctx, As, kinds)[0]:
+            sg.spai_pc_destroy(pc)
+    for _ in range(max(args.warmup, 1)):
+        once()
+    torch.cuda.synchronize()
+    sg.spai_ctx_profile(ctx, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        once()
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) / max(args.steps, 1)
+    prof = [sg.spai_ctx_profile_entry(ctx, i) for i in range(sg.spai_ctx_profile_count(ctx))]
+    sg.spai_ctx_profile(ctx, 0)
+    for aff, _ in keep:
+        sg.spai_affine_destroy(aff)
+    sg.spai_ctx_destroy(ctx)
+    print(json.dumps({"kernel_case": "columns", "systems": len(ws), "columns": sum(w.n for w in ws),
+                      "steps": args.steps, "build_ms": 1e3 * wall,
+                      "device_ms_per_build": {f["name"]: round(f["ms"] / max(args.steps, 1), 3) for f in prof}}),
+          flush=True)
+
+
 def run_kernel_case(args):
     """One kernel on its own at the sweep's size: H = V^T W (dot) or W -= V H (update)."""
     import torch
     import paper_1809_06574_gb300 as sg
+    if args.kernel == "columns":
+        run_columns_case(args)
+        return
     n, s, nb = args.side ** 3, 8, args.nblk
     g = torch.Generator(device="cpu").manual_seed(0)
     # basis-like blocks: entries of unit-norm columns (the digit kernels take |v| < 2)

@@ -235,47 +235,67 @@ __global__ void k_rank_sort_cols(int32_t n, const int32_t *__restrict__ colptr,
 }
 
 // ---------------------------------------------------------------------------------
-// column unions (row sets): warp per output column, warp-wide minimum merge of the
-// sorted row lists of the columns in L_k (at most 4 lists per lane)
+// column unions (row sets): a team of T lanes per output column (T = 4, 8 or 32: the
+// narrowest that holds L_k at 4 lists per lane, so that short lists put several columns
+// in one warp), team-wide minimum merge of the sorted row lists of the columns in L_k
 // ---------------------------------------------------------------------------------
 constexpr int kListsPerLane = 4;
 
-template <bool FILL>
+template <int T>
+__device__ __forceinline__ int32_t team_min(int32_t v)
+{
+    if constexpr (T == 32) {
+        return __reduce_min_sync(0xffffffffu, v);
+    } else {
+#pragma unroll
+        for (int o = T / 2; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));  // stays in the team
+        return v;
+    }
+}
+
+template <bool FILL, int T>
 __global__ void k_colunion(int32_t n, const int32_t *__restrict__ Lptr,
                            const int32_t *__restrict__ Lind, const int32_t *__restrict__ colptr,
                            const int32_t *__restrict__ rowind, const int32_t *__restrict__ out_ptr,
                            int32_t *__restrict__ out, int *err)
 {
-    int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (k >= n) return;
-    int32_t a = Lptr[k], L = Lptr[k + 1] - a;
-    if (L > 32 * kListsPerLane) {
-        if (lane == 0 && err) atomicOr(err, ERR_TOO_WIDE);
-        return;
+    // every lane of the warp takes part in every step (full-mask shuffles); lanes past the
+    // last column merge nothing
+    const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / T;
+    const int sub = threadIdx.x % T;
+    if ((blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31)) / T >= n) return;  // the whole warp is past the end
+    int32_t a = 0, L = 0;
+    if (k < n) {
+        a = Lptr[k];
+        L = Lptr[k + 1] - a;
+        if (L > T * kListsPerLane) {
+            if (sub == 0 && err) atomicOr(err, ERR_TOO_WIDE);
+            L = 0;
+        }
     }
     int32_t pos[kListsPerLane], end[kListsPerLane], head[kListsPerLane];
 #pragma unroll
     for (int u = 0; u < kListsPerLane; ++u) {
-        int32_t c = lane + 32 * u;
+        const int32_t c = sub + T * u;
         pos[u] = end[u] = 0;
         head[u] = INT_MAX;
         if (c < L) {
-            int32_t j = Lind[a + c];
+            const int32_t j = Lind[a + c];
             pos[u] = colptr[j];
             end[u] = colptr[j + 1];
             if (pos[u] < end[u]) head[u] = rowind[pos[u]];
         }
     }
-    int64_t ob = FILL ? (int64_t)out_ptr[k] : 0;
+    const int64_t ob = (FILL && k < n) ? (int64_t)out_ptr[k] : 0;
     int32_t cnt = 0;
     while (true) {
         int32_t cand = head[0];
 #pragma unroll
         for (int u = 1; u < kListsPerLane; ++u) cand = min(cand, head[u]);
-        int32_t m = __reduce_min_sync(0xffffffffu, cand);
-        if (m == INT_MAX) break;
-        if (FILL && lane == 0) out[ob + cnt] = m;
+        const int32_t m = team_min<T>(cand);
+        if (!__any_sync(0xffffffffu, m != INT_MAX)) break;  // every team of the warp is done
+        if (m == INT_MAX) continue;                           // this team is done, others are not
+        if (FILL && sub == 0) out[ob + cnt] = m;
 #pragma unroll
         for (int u = 0; u < kListsPerLane; ++u) {
             if (head[u] == m) {
@@ -285,7 +305,7 @@ __global__ void k_colunion(int32_t n, const int32_t *__restrict__ Lptr,
         }
         ++cnt;
     }
-    if (!FILL && lane == 0) out[k] = cnt;
+    if (!FILL && sub == 0 && k < n) out[k] = cnt;
 }
 
 __global__ void k_gather_f64(int64_t count, const int32_t *__restrict__ idx,
@@ -397,15 +417,25 @@ __global__ void k_seg_ptr_stats(int32_t nsys, const int64_t *__restrict__ off, c
     }
 }
 
+// Segmented element-wise passes walk a tile of kSegTile consecutive elements per block: the
+// segment of the tile's first element is found once (binary search), and each thread,
+// whose elements increase, steps its segment forward from there -- coalesced accesses and
+// no search per element.
+constexpr int kSegTile = 16 * 256;
+
 // dst_g[j] = src_g[j] - sub_g over segments laid end to end
 __global__ void k_unstack(int32_t nseg, const int64_t *__restrict__ start, const int32_t *const *__restrict__ src,
                           int32_t *const *__restrict__ dst, const int32_t *__restrict__ sub)
 {
     const int64_t total = start[nseg];
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int g = seg_of(start, nseg, e);
-        const int64_t j = e - start[g];
-        dst[g][j] = src[g][j] - sub[g];
+    for (int64_t t0 = (int64_t)blockIdx.x * kSegTile; t0 < total; t0 += (int64_t)gridDim.x * kSegTile) {
+        int g = seg_of(start, nseg, t0);
+        const int64_t t1 = min(t0 + (int64_t)kSegTile, total);
+        for (int64_t e = t0 + threadIdx.x; e < t1; e += blockDim.x) {
+            while (e >= __ldg(start + g + 1)) ++g;
+            const int64_t j = e - start[g];
+            dst[g][j] = src[g][j] - sub[g];
+        }
     }
 }
 
@@ -414,10 +444,14 @@ __global__ void k_gather_seg(int32_t nseg, const int64_t *__restrict__ start, co
                              const int32_t *const *__restrict__ perm, double *const *__restrict__ dst)
 {
     const int64_t total = start[nseg];
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int g = seg_of(start, nseg, e);
-        const int64_t j = e - start[g];
-        dst[g][j] = val[g][perm[g][j]];
+    for (int64_t t0 = (int64_t)blockIdx.x * kSegTile; t0 < total; t0 += (int64_t)gridDim.x * kSegTile) {
+        int g = seg_of(start, nseg, t0);
+        const int64_t t1 = min(t0 + (int64_t)kSegTile, total);
+        for (int64_t e = t0 + threadIdx.x; e < t1; e += blockDim.x) {
+            while (e >= __ldg(start + g + 1)) ++g;
+            const int64_t j = e - start[g];
+            dst[g][j] = val[g][perm[g][j]];
+        }
     }
 }
 
@@ -644,24 +678,36 @@ int launch_transpose(cudaStream_t st, int32_t n, int32_t nnz, const int32_t *row
 
 int colunion_max_lists() { return 32 * kListsPerLane; }
 
-int launch_colunion_count(cudaStream_t st, int32_t n, const int32_t *Lptr, const int32_t *Lind,
-                          const int32_t *colptr, const int32_t *rowind, int32_t *counts,
-                          int *d_err)
+namespace {
+template <bool FILL>
+int colunion_launch(cudaStream_t st, int32_t n, int32_t maxL, const int32_t *Lptr, const int32_t *Lind,
+                    const int32_t *colptr, const int32_t *rowind, const int32_t *out_ptr, int32_t *out, int *d_err)
 {
     if (n <= 0) return 0;
-    k_colunion<false><<<grid_for((int64_t)n * 32), kThreads, 0, st>>>(n, Lptr, Lind, colptr, rowind,
-                                                                       nullptr, counts, d_err);
+    if (maxL <= 4 * kListsPerLane)
+        k_colunion<FILL, 4><<<grid_for((int64_t)n * 4), kThreads, 0, st>>>(n, Lptr, Lind, colptr, rowind, out_ptr,
+                                                                             out, d_err);
+    else if (maxL <= 8 * kListsPerLane)
+        k_colunion<FILL, 8><<<grid_for((int64_t)n * 8), kThreads, 0, st>>>(n, Lptr, Lind, colptr, rowind, out_ptr,
+                                                                             out, d_err);
+    else
+        k_colunion<FILL, 32><<<grid_for((int64_t)n * 32), kThreads, 0, st>>>(n, Lptr, Lind, colptr, rowind, out_ptr,
+                                                                               out, d_err);
     return check_launch();
 }
+}  // namespace
 
-int launch_colunion_fill(cudaStream_t st, int32_t n, const int32_t *Lptr, const int32_t *Lind,
+int launch_colunion_count(cudaStream_t st, int32_t n, int32_t maxL, const int32_t *Lptr, const int32_t *Lind,
+                          const int32_t *colptr, const int32_t *rowind, int32_t *counts, int *d_err)
+{
+    return colunion_launch<false>(st, n, maxL, Lptr, Lind, colptr, rowind, nullptr, counts, d_err);
+}
+
+int launch_colunion_fill(cudaStream_t st, int32_t n, int32_t maxL, const int32_t *Lptr, const int32_t *Lind,
                          const int32_t *colptr, const int32_t *rowind, const int32_t *out_ptr,
                          int32_t *out_list, int *d_err)
 {
-    if (n <= 0) return 0;
-    k_colunion<true><<<grid_for((int64_t)n * 32), kThreads, 0, st>>>(n, Lptr, Lind, colptr, rowind,
-                                                                      out_ptr, out_list, d_err);
-    return check_launch();
+    return colunion_launch<true>(st, n, maxL, Lptr, Lind, colptr, rowind, out_ptr, out_list, d_err);
 }
 
 int launch_gather_f64(cudaStream_t st, int64_t count, const int32_t *idx, const double *src,
@@ -711,7 +757,7 @@ int launch_unstack(cudaStream_t st, int32_t nseg, int64_t total, const int64_t *
                    int32_t *const *dst, const int32_t *sub)
 {
     if (total <= 0) return 0;
-    k_unstack<<<grid_cap(total), kThreads, 0, st>>>(nseg, start, src, dst, sub);
+    k_unstack<<<grid_cap((total + kSegTile - 1) / kSegTile * kThreads), kThreads, 0, st>>>(nseg, start, src, dst, sub);
     return check_launch();
 }
 
@@ -719,7 +765,8 @@ int launch_gather_seg(cudaStream_t st, int32_t nseg, int64_t total, const int64_
                       const int32_t *const *perm, double *const *dst)
 {
     if (total <= 0) return 0;
-    k_gather_seg<<<grid_cap(total), kThreads, 0, st>>>(nseg, start, val, perm, dst);
+    k_gather_seg<<<grid_cap((total + kSegTile - 1) / kSegTile * kThreads), kThreads, 0, st>>>(nseg, start, val, perm,
+                                                                                               dst);
     return check_launch();
 }
 

@@ -457,7 +457,7 @@ spai_status sym_create_batch(spai_ctx ctx, int32_t nsys, const spai_csr *A, cons
             if (s->alias) continue;
             const int32_t n = s->n;
             TRY(dalloc_n(ctx, &s->Jptr, (int64_t)n + 1));
-            TRYK(launch_colunion_count(ctx->stream, n, s->a_colptr, s->a_rowind, s->a_colptr, s->a_rowind, counts,
+            TRYK(launch_colunion_count(ctx->stream, n, h[i], s->a_colptr, s->a_rowind, s->a_colptr, s->a_rowind, counts,
                                        ctx->d_err), "pattern count");
             TRYK(launch_exclusive_scan(ctx->stream, counts, s->Jptr, n, scan_temp(n), ctx->d_err), "scan");
             CU(cudaMemcpyAsync(d_vals + nsys + i, s->Jptr + n, 4, cudaMemcpyDeviceToDevice, ctx->stream), "total");
@@ -474,7 +474,7 @@ spai_status sym_create_batch(spai_ctx ctx, int32_t nsys, const spai_csr *A, cons
             s->nnzP = h[nsys + i];
             int32_t *perm_rows = nullptr;
             TRY(dalloc_n(ctx, &s->Jind, s->nnzP));
-            TRYK(launch_colunion_fill(ctx->stream, n, s->a_colptr, s->a_rowind, s->a_colptr, s->a_rowind, s->Jptr,
+            TRYK(launch_colunion_fill(ctx->stream, n, h[i], s->a_colptr, s->a_rowind, s->a_colptr, s->a_rowind, s->Jptr,
                                       s->Jind, ctx->d_err), "pattern fill");
             TRYK(launch_max_i32_diff(ctx->stream, n, s->Jptr, d_vals + i), "max |J|");
             // row-wise pattern of P and the map from column positions to row positions
@@ -501,7 +501,7 @@ spai_status sym_create_batch(spai_ctx ctx, int32_t nsys, const spai_csr *A, cons
         Sym *s = S[i];
         const int32_t n = s->n;
         TRY(dalloc_n(ctx, &s->Iptr, (int64_t)n + 1));
-        TRYK(launch_colunion_count(ctx->stream, n, s->Jptr, s->Jind, s->a_colptr, s->a_rowind, counts, ctx->d_err),
+        TRYK(launch_colunion_count(ctx->stream, n, s->maxJ, s->Jptr, s->Jind, s->a_colptr, s->a_rowind, counts, ctx->d_err),
              "index set count");
         TRYK(launch_exclusive_scan(ctx->stream, counts, s->Iptr, n, scan_temp(n), ctx->d_err), "scan");
         CU(cudaMemcpyAsync(d_vals + 2 * nsys + i, s->Iptr + n, 4, cudaMemcpyDeviceToDevice, ctx->stream), "total");
@@ -516,7 +516,7 @@ spai_status sym_create_batch(spai_ctx ctx, int32_t nsys, const spai_csr *A, cons
         Sym *s = S[i];
         s->nI = h[2 * nsys + i];
         TRY(dalloc_n(ctx, &s->Ilist, s->nI));
-        TRYK(launch_colunion_fill(ctx->stream, s->n, s->Jptr, s->Jind, s->a_colptr, s->a_rowind, s->Iptr, s->Ilist,
+        TRYK(launch_colunion_fill(ctx->stream, s->n, s->maxJ, s->Jptr, s->Jind, s->a_colptr, s->a_rowind, s->Iptr, s->Ilist,
                                   ctx->d_err), "index set fill");
         TRYK(launch_max_i32_diff(ctx->stream, s->n, s->Iptr, d_vals + 3 * nsys + i), "max |I|");
     }
@@ -1261,7 +1261,7 @@ spai_status build_batch_stacked(spai_ctx ctx, int32_t nsys, const spai_csr *A, c
     TRY(talloc(&Jptr, ntot + 1));
     {
         ProfScope ps_(ctx, "analysis:J", 0.0, 0.0);
-        TRYK(launch_colunion_count(cs, (int32_t)ntot, Lptr, Lind, colptr, rowind, counts, ctx->d_err), "J count");
+        TRYK(launch_colunion_count(cs, (int32_t)ntot, h2[1], Lptr, Lind, colptr, rowind, counts, ctx->d_err), "J count");
         TRYK(launch_exclusive_scan(cs, counts, Jptr, ntot, stemp, ctx->d_err), "scan");
         TRYK(launch_seg_ptr_stats(cs, nsys, ntot, d_off, Jptr, d_tot, d_mx), "J sizes");
     }
@@ -1273,8 +1273,10 @@ spai_status build_batch_stacked(spai_ctx ctx, int32_t nsys, const spai_csr *A, c
     if (herr & ERR_OVERFLOW) return cleanup(fail(ctx, SPAI_EINVAL, "index sets exceed 2^31 entries"));
     if (herr) return cleanup(fail(ctx, SPAI_EINVAL, "pattern analysis failed (device error 0x%x)", herr));
     int64_t nJ = 0;
+    int32_t mxJall = 0;
     for (int i = 0; i < nsys; ++i) {
         nJ += totJ[i];
+        mxJall = std::max(mxJall, mxJ[i]);
         if (mxJ[i] > colunion_max_lists())
             return cleanup(fail(ctx, SPAI_EINVAL, "system %d: a column pattern has %d entries; at most %d are supported",
                                 i, mxJ[i], colunion_max_lists()));
@@ -1283,7 +1285,7 @@ spai_status build_batch_stacked(spai_ctx ctx, int32_t nsys, const spai_csr *A, c
     TRY(talloc(&Jind, nJ));
     {
         ProfScope ps_(ctx, "analysis:J", 0.0, 0.0);
-        TRYK(launch_colunion_fill(cs, (int32_t)ntot, Lptr, Lind, colptr, rowind, Jptr, Jind, ctx->d_err), "J fill");
+        TRYK(launch_colunion_fill(cs, (int32_t)ntot, h2[1], Lptr, Lind, colptr, rowind, Jptr, Jind, ctx->d_err), "J fill");
     }
     // ---- rows of P (the transpose of the J pattern) and the map J position -> P row position
     int32_t *prp = nullptr, *pci = nullptr, *pperm = nullptr, *pmap = nullptr;
@@ -1308,7 +1310,7 @@ spai_status build_batch_stacked(spai_ctx ctx, int32_t nsys, const spai_csr *A, c
     TRY(talloc(&Iptr, ntot + 1));
     {
         ProfScope ps_(ctx, "analysis:I", 0.0, 0.0);
-        TRYK(launch_colunion_count(cs, (int32_t)ntot, Jptr, Jind, colptr, rowind, counts, ctx->d_err), "I count");
+        TRYK(launch_colunion_count(cs, (int32_t)ntot, mxJall, Jptr, Jind, colptr, rowind, counts, ctx->d_err), "I count");
         TRYK(launch_exclusive_scan(cs, counts, Iptr, ntot, stemp, ctx->d_err), "scan");
         TRYK(launch_seg_ptr_stats(cs, nsys, ntot, d_off, Iptr, d_tot + nsys, d_mx + nsys), "I sizes");
     }
@@ -1328,7 +1330,7 @@ spai_status build_batch_stacked(spai_ctx ctx, int32_t nsys, const spai_csr *A, c
     TRY(talloc(&Ilist, nIt));
     {
         ProfScope ps_(ctx, "analysis:I", 0.0, 0.0);
-        TRYK(launch_colunion_fill(cs, (int32_t)ntot, Jptr, Jind, colptr, rowind, Iptr, Ilist, ctx->d_err), "I fill");
+        TRYK(launch_colunion_fill(cs, (int32_t)ntot, mxJall, Jptr, Jind, colptr, rowind, Iptr, Ilist, ctx->d_err), "I fill");
     }
 
     // ---- the arena: every system's analysis (local indices) and factor storage

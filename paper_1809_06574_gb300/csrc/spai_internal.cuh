@@ -58,10 +58,11 @@ int launch_transpose(cudaStream_t st, int32_t n, int32_t nnz, const int32_t *row
 // out_k = sorted union over j in L_k of rows(colptr/rowind column j); two passes
 // (at most colunion_max_lists() columns in any L_k, else ERR_TOO_WIDE)
 int colunion_max_lists();
-int launch_colunion_count(cudaStream_t st, int32_t n, const int32_t *Lptr, const int32_t *Lind,
-                          const int32_t *colptr, const int32_t *rowind, int32_t *counts,
-                          int *d_err);
-int launch_colunion_fill(cudaStream_t st, int32_t n, const int32_t *Lptr, const int32_t *Lind,
+// maxL: an upper bound of every |L_k| (picks the team width; a longer list sets ERR_TOO_WIDE
+// when it exceeds the widest team's capacity, colunion_max_lists())
+int launch_colunion_count(cudaStream_t st, int32_t n, int32_t maxL, const int32_t *Lptr, const int32_t *Lind,
+                          const int32_t *colptr, const int32_t *rowind, int32_t *counts, int *d_err);
+int launch_colunion_fill(cudaStream_t st, int32_t n, int32_t maxL, const int32_t *Lptr, const int32_t *Lind,
                          const int32_t *colptr, const int32_t *rowind, const int32_t *out_ptr,
                          int32_t *out_list, int *d_err);
 int launch_gather_f64(cudaStream_t st, int64_t count, const int32_t *idx, const double *src,

@@ -40,6 +40,8 @@ def _systems():
     out.append(("3d-9-7pt", oracle.assemble(w.terms, oracle.coefficients(0.4, 2.0), w.n), w.n, oracle.PATTERN_A, 0))
     w = synth.grid3d_27pt(side=5, nparams=2)
     out.append(("3d-5-27pt", oracle.assemble(w.terms, oracle.coefficients(0.4, 1.0), w.n), w.n, oracle.PATTERN_A, 0))
+    # pattern A^2 of the 27-point grid: |J_k| up to 125, the widest union lists (32-lane teams)
+    out.append(("3d-5-27pt-A2", out[-1][1], w.n, oracle.PATTERN_A2, 0))
     # the same shapes again in FP32 and BF16
     out.append(("2d-21-A-fp32", out[2][1], out[2][2], oracle.PATTERN_A, sg.PREC_FP32))
     out.append(("2d-34-A2-bf16", out[3][1], out[3][2], oracle.PATTERN_A2, sg.PREC_BF16))
