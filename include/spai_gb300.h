@@ -191,6 +191,12 @@ SPAI_API spai_status spai_affine_destroy(spai_affine aff);
  * factor stored in BF16).  The handle keeps the
  * pattern analysis (I_k, J_k),
  * A's values in column order (for later updates) and P in row order (for the apply).
+ * Column kernel: the first build or update of the process that meets a tile shape
+ * (working precision, max |I_k| rounded up to 8, max |J_k|) times every fitting kernel
+ * variant -- shared-memory tiles with teams of 1 ... 32 lanes per column, and
+ * register-tiled variants for tiles up to 32 x 13 -- on up to 65,536 of its columns and
+ * keeps the fastest for the rest of the process (one thread tunes at a time; variants
+ * differ only in the rounding order of the reductions, within the FP64 bar).
  * Synchronises once (reads index-set sizes and the column status).  Returns
  * SPAI_ESINGULAR if some column problem is rank deficient (|I_k| < |J_k| or
  * |R_cc| <= 1e-14 max|R_tt|): the handle is still returned, those columns are zero,
@@ -210,10 +216,10 @@ SPAI_API spai_status spai_build(spai_ctx ctx, const spai_csr *A, int32_t pattern
  * some handles of a batch returns no memory until the rest go too.  Otherwise (one system,
  * or an empty one) the analyses run phase by phase per system with one host read-back per
  * phase.  The column problems of all systems run in one persistent launch per tile shape --
- * systems are grouped by working precision, max |J_k| and max |I_k| rounded up to 8.  Team size (lanes per column problem): the first batch
- * of the process that meets a shape times every team size whose block fits and keeps the
- * fastest; later batches reuse it (team sizes change the rounding of the reductions only,
- * results stay within the FP64 bar of spai_build).  1 <= nsys <= 65536.  Synchronises.
+ * systems are grouped by working precision, max |J_k| and max |I_k| rounded up to 8.
+ * Kernel variant per shape: chosen and cached as for spai_build (the same process-wide
+ * choice serves both; variants change the rounding of the reductions only, results stay
+ * within the FP64 bar of spai_build).  1 <= nsys <= 65536.  Synchronises.
  * Returns SPAI_ESINGULAR (handles still returned) if some column of some system is rank
  * deficient; on any other error no handle is returned. */
 SPAI_API spai_status spai_build_batch(spai_ctx ctx, int32_t nsys, const spai_csr *A, const int32_t *pattern_kind,

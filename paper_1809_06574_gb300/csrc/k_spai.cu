@@ -192,6 +192,214 @@ __global__ void __launch_bounds__(kBlock) k_spai_columns(ColumnProblem cp0, Colu
     }
 }
 
+// ---- register-tiled variant for small tiles: no shared memory, everything unrolled.
+// Lane tl of a team of T owns rows tl, tl + T, ..., tl + (RPL-1) T of the tile (RPL rows
+// per lane, up to T * RPL rows) for all MJ (>= |J_k|) columns and the right-hand side, in
+// registers.  The gather compares each lane's rows with the (sorted) row lists of the
+// columns of J_k, so it needs no search; the Householder sweep is the one of column_ls with
+// every loop bound a compile-time constant (columns past |J_k| are skipped by a team-uniform
+// predicate); the back substitution runs on the lane that owns each row of R and broadcasts
+// the solved value.  Same arithmetic as column_ls, in another order of the reductions.
+template <int T, int RPL, int MJ, typename R, typename P>
+__device__ __forceinline__ void column_ls_reg(const P &cp, int64_t k, int tl, unsigned mask)
+{
+    const int32_t ia = __ldg(cp.Iptr + k), ni = __ldg(cp.Iptr + k + 1) - ia;
+    const int32_t ja = __ldg(cp.Jptr + k), nj = __ldg(cp.Jptr + k + 1) - ja;
+    if (ni > T * RPL || nj > MJ) {
+        if (tl == 0) {
+            atomicOr(cp.d_err, ERR_TOO_WIDE);
+            cp.col_status[k] = 1;
+        }
+        return;
+    }
+    int32_t row[RPL];
+#pragma unroll
+    for (int i = 0; i < RPL; ++i) row[i] = (tl + T * i < ni) ? __ldg(cp.Ilist + ia + tl + T * i) : -1;
+    R a[MJ][RPL], b[RPL];
+#pragma unroll
+    for (int c = 0; c < MJ; ++c) {
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) a[c][i] = R(0);
+        if (c < nj) {
+            const int32_t j = __ldg(cp.Jind + ja + c);
+            const int32_t q1 = __ldg(cp.colptr + j + 1);
+            for (int32_t q = __ldg(cp.colptr + j); q < q1; ++q) {
+                const int32_t r = __ldg(cp.rowind + q);
+                const R v = (R)__ldg(cp.cval + q);
+#pragma unroll
+                for (int i = 0; i < RPL; ++i)
+                    if (row[i] == r) a[c][i] = v;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < RPL; ++i) b[i] = (cp.mode == 0 && row[i] == (int32_t)k) ? R(1) : R(0);
+    if (cp.mode != 0) {
+        const int32_t q1 = __ldg(cp.r_colptr + k + 1);
+        for (int32_t q = __ldg(cp.r_colptr + k); q < q1; ++q) {
+            const int32_t r = __ldg(cp.r_rowind + q);
+            const R v = (R)__ldg(cp.r_val + q);
+#pragma unroll
+            for (int i = 0; i < RPL; ++i)
+                if (row[i] == r) b[i] = v;
+        }
+    }
+
+    // ---- Householder QR, reflectors applied to the columns right of c and to b
+    R rd[MJ];
+    bool singular = ni < nj;
+#pragma unroll
+    for (int c = 0; c < MJ; ++c) {
+        rd[c] = R(1);
+        if (c < nj && !singular) {
+            R v[RPL];
+            R ss = R(0);
+#pragma unroll
+            for (int i = 0; i < RPL; ++i) {
+                v[i] = (tl + T * i >= c) ? a[c][i] : R(0);
+                ss = fma(v[i], v[i], ss);
+            }
+            ss = team_sum<T, R>(ss, mask);
+            const R alpha = sqrt(ss);
+            if (!(alpha > R(0))) {
+                singular = true;
+            } else {
+                const R xc = __shfl_sync(mask, a[c][c / T], c % T, T);
+                const R sgn = (xc >= R(0)) ? R(1) : R(-1);
+                const R inv = R(1) / (alpha * (alpha + fabs(xc)));  // 2 / v^T v
+                if (tl == c % T) v[c / T] = xc + sgn * alpha;
+                rd[c] = -sgn * alpha;
+#pragma unroll
+                for (int t = 1; t < MJ; ++t) {  // (a fixed range keeps the nest fully unrolled)
+                    if (t > c && t < nj) {
+                        R d = R(0);
+#pragma unroll
+                        for (int i = 0; i < RPL; ++i) d = fma(v[i], a[t][i], d);
+                        const R g = team_sum<T, R>(d, mask) * inv;
+#pragma unroll
+                        for (int i = 0; i < RPL; ++i) a[t][i] = fma(-g, v[i], a[t][i]);
+                    }
+                }
+                R d = R(0);
+#pragma unroll
+                for (int i = 0; i < RPL; ++i) d = fma(v[i], b[i], d);
+                const R g = team_sum<T, R>(d, mask) * inv;
+#pragma unroll
+                for (int i = 0; i < RPL; ++i) b[i] = fma(-g, v[i], b[i]);
+            }
+        }
+    }
+    if (!singular) {
+        R rmax = R(0);
+#pragma unroll
+        for (int c = 0; c < MJ; ++c)
+            if (c < nj) rmax = fmax(rmax, fabs(rd[c]));
+#pragma unroll
+        for (int c = 0; c < MJ; ++c)
+            if (c < nj && fabs(rd[c]) <= singular_rel<R>() * rmax) singular = true;
+    }
+    if (singular) {
+        for (int c = tl; c < nj; c += T) {
+            if (cp.out_val16) cp.out_val16[cp.out_map[ja + c]] = 0;
+            else if (cp.out_val32) cp.out_val32[cp.out_map[ja + c]] = 0.0f;
+            else cp.out_val[cp.out_map[ja + c]] = 0.0;
+        }
+        if (tl == 0) cp.col_status[k] = 1;
+        return;
+    }
+
+    // ---- back substitution: row c of R and of Q^T b live on lane c % T, slot c / T
+    R m[MJ];
+#pragma unroll
+    for (int c = MJ - 1; c >= 0; --c) {
+        m[c] = R(0);
+        if (c < nj) {
+            R acc = R(0);
+#pragma unroll
+            for (int t = 1; t < MJ; ++t)
+                if (t > c && t < nj) acc = fma(a[t][c / T], m[t], acc);
+            m[c] = __shfl_sync(mask, (b[c / T] - acc) / rd[c], c % T, T);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < MJ; ++c) {
+        if (c < nj && c % T == tl) {
+            if (cp.out_val16) cp.out_val16[cp.out_map[ja + c]] = __bfloat16_as_ushort(__float2bfloat16_rn((float)m[c]));
+            else if (cp.out_val32) cp.out_val32[cp.out_map[ja + c]] = (float)m[c];
+            else cp.out_val[cp.out_map[ja + c]] = (double)m[c];
+        }
+    }
+    if (tl == 0) cp.col_status[k] = 0;
+}
+
+template <int T, int RPL, int MJ, typename R>
+__global__ void __launch_bounds__(kBlock) k_spai_columns_reg(ColumnProblem cp0, ColumnBatch bt)
+{
+    const int lane = threadIdx.x & 31;
+    const int team = threadIdx.x / T, tl = threadIdx.x % T;
+    const int teams = blockDim.x / T;
+    const unsigned mask = (T == 32) ? 0xffffffffu : (((1u << T) - 1u) << ((lane / T) * T));
+    const int64_t total = bt.tab ? bt.total : (int64_t)cp0.n;
+    for (int64_t g = (int64_t)blockIdx.x * teams + team; g < total; g += (int64_t)gridDim.x * teams) {
+        if (bt.tab) {
+            int lo = 0, hi = bt.nsys - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(bt.start + mid) <= g) lo = mid; else hi = mid - 1;
+            }
+            column_ls_reg<T, RPL, MJ, R>(bt.tab[lo], g - __ldg(bt.start + lo), tl, mask);
+        } else {
+            column_ls_reg<T, RPL, MJ, R>(cp0, g, tl, mask);
+        }
+        __syncwarp(mask);
+    }
+}
+
+// the register-tiled shapes: team T, rows per lane RPL (tile rows <= T * RPL), columns MJ
+struct RegShape {
+    int T, RPL, MJ;
+};
+constexpr RegShape kRegShapes[] = {{4, 4, 5}, {8, 4, 8}, {4, 8, 8}, {8, 4, 13}};
+constexpr int kNumRegShapes = 4;
+constexpr int kRegTeamBase = 64;  // team codes kRegTeamBase + i select kRegShapes[i]
+
+template <int T, int RPL, int MJ, typename R>
+int launch_reg(cudaStream_t st, const ColumnProblem &cp, const ColumnBatch &bt)
+{
+    const int teams = kBlock / T;
+    const int64_t total = bt.tab ? bt.total : (int64_t)cp.n;
+    int64_t blocks = (total + teams - 1) / teams;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spai_columns_reg<T, RPL, MJ, R>, kBlock, 0) !=
+            cudaSuccess)
+        return -1;
+    const int64_t resident = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    if (blocks > resident) blocks = resident;
+    if (blocks < 1) blocks = 1;
+    k_spai_columns_reg<T, RPL, MJ, R><<<(unsigned)blocks, kBlock, 0, st>>>(cp, bt);
+    note_launches(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+bool reg_fits(int i, int32_t maxI, int32_t maxJ)
+{
+    return maxI <= kRegShapes[i].T * kRegShapes[i].RPL && maxJ <= kRegShapes[i].MJ;
+}
+
+template <typename R>
+int launch_reg_shape(cudaStream_t st, const ColumnProblem &cp, const ColumnBatch &bt, int i)
+{
+    switch (i) {
+    case 0: return launch_reg<4, 4, 5, R>(st, cp, bt);
+    case 1: return launch_reg<8, 4, 8, R>(st, cp, bt);
+    case 2: return launch_reg<4, 8, 8, R>(st, cp, bt);
+    case 3: return launch_reg<8, 4, 13, R>(st, cp, bt);
+    default: return -1;
+    }
+}
+
 template <int T, typename R>
 int launch_team(cudaStream_t st, const ColumnProblem &cp, const ColumnBatch &bt, int ld, int maxJ, int L,
                 int threads)
@@ -296,6 +504,11 @@ template <typename R>
 int launch_columns(cudaStream_t st, const ColumnProblem &cp, const ColumnBatch &bt, int32_t maxI, int32_t maxJ,
                    int T)
 {
+    if (T >= kRegTeamBase) {
+        const int i = T - kRegTeamBase;
+        if (i >= kNumRegShapes || !reg_fits(i, maxI, maxJ)) return -1;
+        return launch_reg_shape<R>(st, cp, bt, i);
+    }
     const int ld = maxI < 1 ? 1 : maxI;
     const int mj = maxJ < 1 ? 1 : maxJ;
     const int L = tile_stride(maxI, maxJ);
@@ -324,6 +537,15 @@ int launch_spai_columns(cudaStream_t st, const ColumnProblem &cp, int32_t maxI, 
                                           : launch_columns<double>(st, cp, none, maxI, maxJ, 0);
 }
 
+int launch_spai_columns_team(cudaStream_t st, const ColumnProblem &cp, bool low_precision, int32_t maxI,
+                             int32_t maxJ, int team)
+{
+    if (cp.n <= 0) return 0;
+    const ColumnBatch none{};
+    return low_precision ? launch_columns<float>(st, cp, none, maxI, maxJ, team)
+                         : launch_columns<double>(st, cp, none, maxI, maxJ, team);
+}
+
 int spai_columns_teams(int32_t maxI, int32_t maxJ, bool low_precision, int *teams)
 {
     const size_t per = (size_t)tile_stride(maxI, maxJ) * (low_precision ? sizeof(float) : sizeof(double));
@@ -332,6 +554,8 @@ int spai_columns_teams(int32_t maxI, int32_t maxJ, bool low_precision, int *team
     teams[k++] = def;  // the default first
     for (int T = 1; T <= 32; T *= 2)
         if (T != def && threads_for(T, per)) teams[k++] = T;
+    for (int i = 0; i < kNumRegShapes; ++i)
+        if (reg_fits(i, maxI, maxJ)) teams[k++] = kRegTeamBase + i;
     return k;
 }
 

@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <tuple>
 #include <atomic>
@@ -543,6 +544,80 @@ spai_status sym_create(spai_ctx ctx, const spai_csr *A, int32_t kind, Sym **out)
     return sym_create_batch(ctx, 1, A, &kind, out);
 }
 
+// Team size (or register-tiled shape) of the column kernel, chosen per (working precision,
+// tile rows rounded up to 8, tile columns) process-wide: the first call that meets a shape
+// -- a batch or a single build or update -- times every fitting candidate on its own
+// columns with CUDA events and keeps the fastest; later calls reuse it.  One thread tunes
+// at a time (others that meet the same shape wait and reuse its choice), so every call
+// after the first uses one team per shape.  Candidates change the rounding of the
+// reductions only.  Candidates are timed on the first kTuneColumns columns when there are
+// more (a bounded one-time cost: the 27-point 128^3 FP64 build would otherwise pay a dozen
+// full launches); when all columns were timed, each candidate wrote the complete result
+// and *done on return says the chosen candidate's result is already in place.
+std::mutex g_tune_mu;      // guards g_tune
+std::mutex g_tune_run_mu;  // one tuning run at a time
+std::map<std::tuple<int, int, int>, int> g_tune;
+
+constexpr int64_t kTuneColumns = 65536;
+
+spai_status tuned_team(spai_ctx ctx, bool low, int32_t maxI, int32_t maxJ, int64_t total,
+                       const std::function<int(int, int64_t)> &launch, int *team, bool *done)
+{
+    const int64_t sample = std::min(total, kTuneColumns);
+    const auto key = std::make_tuple(low ? 1 : 0, (maxI + 7) / 8 * 8, maxJ);
+    auto lookup = [&]() {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        return it == g_tune.end() ? 0 : it->second;
+    };
+    *done = false;
+    if ((*team = lookup())) return SPAI_OK;
+    std::lock_guard<std::mutex> run(g_tune_run_mu);
+    if ((*team = lookup())) return SPAI_OK;  // tuned by another thread meanwhile
+    int cand[16];
+    const int nc = spai_columns_teams(maxI, maxJ, low, cand);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CU(cudaEventCreate(&e0), "event");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(ctx, SPAI_ECUDA, "event");
+    }
+    // two timed runs per candidate, the faster one counts (the first launch of a kernel in
+    // the process, and the first candidate's cold caches, would otherwise bias the choice)
+    float best_ms = 0.f;
+    int best = 0, last = 0;
+    for (int c = 0; c < nc; ++c) {
+        float ms = -1.f;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaEventRecord(e0, ctx->stream);
+            if (launch(cand[c], sample)) {
+                cudaGetLastError();
+                break;
+            }
+            cudaEventRecord(e1, ctx->stream);
+            cudaEventSynchronize(e1);
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            last = cand[c];
+            if (ms < 0.f || t < ms) ms = t;
+        }
+        if (ms >= 0.f && (!best || ms < best_ms)) {
+            best = cand[c];
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!best) return fail(ctx, SPAI_EINVAL, "no team size fits column problems of %d x %d", maxI, maxJ);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune.emplace(key, best);
+    }
+    *team = best;
+    *done = last == best && sample == total;
+    return SPAI_OK;
+}
+
 spai_status run_columns(spai_ctx ctx, spai_pc pc, int mode, const double *rhs_cval)
 {
     Sym *s = pc->sym;
@@ -570,7 +645,17 @@ spai_status run_columns(spai_ctx ctx, spai_pc pc, int mode, const double *rhs_cv
         const double aI = (double)s->nI / s->n, aJ = (double)s->nnzP / s->n;
         const double fl = (double)s->n * (2 * aJ * aJ * (aI - aJ / 3) + 4 * aI * aJ + aJ * aJ);
         const double by = 12.0 * s->nnzA * (mode ? 2 : 1) + 8.0 * (s->n + 1) + 4.0 * s->nI + 16.0 * s->nnzP;
-        PKL("spai_columns", fl, by, launch_spai_columns(ctx->stream, cp, s->maxI, s->maxJ), "column least squares");
+        const bool low = cp.out_val32 || cp.out_val16;
+        auto launch = [&](int t, int64_t limit) {
+            ColumnProblem part = cp;
+            part.n = (int32_t)std::min<int64_t>(cp.n, limit);
+            return launch_spai_columns_team(ctx->stream, part, low, s->maxI, s->maxJ, t);
+        };
+        int team = 0;
+        bool done = false;
+        spai_status st = tuned_team(ctx, low, s->maxI, s->maxJ, cp.n, launch, &team, &done);
+        if (st) return st;
+        if (!done) PKL("spai_columns", fl, by, launch(team, cp.n), "column least squares");
     }
     // first singular column (or INT_MAX)
     KL(launch_first_nonzero(ctx->stream, s->n, pc->status, ctx->d_scalar), "status scan");
@@ -983,12 +1068,6 @@ extern "C" spai_status spai_update(spai_ctx ctx, spai_pc base, const spai_csr *A
 // ===================================================================================
 namespace {
 
-// Team size chosen per (working precision, tile rows, tile columns), process-wide: the first
-// batch that meets a shape times every fitting team size on its own columns and keeps the
-// fastest; later batches reuse it.  Team sizes change the rounding of the reductions only.
-std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, int> g_tune;
-
 spai_status run_columns_batch(spai_ctx ctx, int32_t nsys, spai_pc *pcs)
 {
     // buckets of systems whose problems share a tile: (low precision, max |J|, max |I| rounded up to 8)
@@ -1045,51 +1124,22 @@ spai_status run_columns_batch(spai_ctx ctx, int32_t nsys, spai_pc *pcs)
         CU(cudaMemcpyAsync(d_start, start.data(), sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, ctx->stream),
            "table");
         const ColumnBatch bt{d_tab, d_start, m, start[m]};
-        const auto key = std::make_tuple(low, std::get<2>(b.first), maxJ);
+        auto launch = [&](int t, int64_t limit) {
+            ColumnBatch part = bt;
+            part.total = std::min(bt.total, limit);
+            return launch_spai_columns_batch(ctx->stream, part, low != 0, maxI, maxJ, t);
+        };
         int team = 0;
-        {
-            std::lock_guard<std::mutex> lk(g_tune_mu);
-            auto it = g_tune.find(key);
-            if (it != g_tune.end()) team = it->second;
+        bool done = false;
+        if ((st = tuned_team(ctx, low != 0, maxI, maxJ, bt.total, launch, &team, &done))) {
+            dfree(ctx, d_tab);
+            dfree(ctx, d_start);
+            return st;
         }
-        if (!team) {
-            // first meeting of this shape: time every fitting team size on these columns
-            int cand[8];
-            const int nc = spai_columns_teams(maxI, maxJ, low != 0, cand);
-            cudaEvent_t e0 = nullptr, e1 = nullptr;
-            CU(cudaEventCreate(&e0), "event");
-            CU(cudaEventCreate(&e1), "event");
-            float best_ms = 0.f;
-            int last = 0;
-            for (int c = 0; c < nc; ++c) {
-                cudaEventRecord(e0, ctx->stream);
-                if (launch_spai_columns_batch(ctx->stream, bt, low != 0, maxI, maxJ, cand[c])) {
-                    cudaGetLastError();
-                    continue;
-                }
-                cudaEventRecord(e1, ctx->stream);
-                cudaEventSynchronize(e1);
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                last = cand[c];
-                if (!team || ms < best_ms) { team = cand[c]; best_ms = ms; }
-            }
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            if (!team) {
-                dfree(ctx, d_tab);
-                dfree(ctx, d_start);
-                return fail(ctx, SPAI_EINVAL, "no team size fits column problems of %d x %d", maxI, maxJ);
-            }
-            {
-                std::lock_guard<std::mutex> lk(g_tune_mu);
-                g_tune.emplace(key, team);
-            }
-            if (last == team) {  // the result of the chosen size is already in place
-                dfree(ctx, d_tab);
-                dfree(ctx, d_start);
-                continue;
-            }
+        if (done) {  // the result of the chosen candidate is already in place
+            dfree(ctx, d_tab);
+            dfree(ctx, d_start);
+            continue;
         }
         PKL("spai_columns", fl, by, launch_spai_columns_batch(ctx->stream, bt, low != 0, maxI, maxJ, team),
             "batched column least squares");

@@ -148,7 +148,11 @@ int launch_diag_update(cudaStream_t st, int32_t n, const int32_t *colptr, const 
 bool spai_columns_fit(int32_t maxI, int32_t maxJ);
 // Picks the team size by the largest |I_k|, |J_k|; returns 0 or -1 if no tile fits.
 int launch_spai_columns(cudaStream_t st, const ColumnProblem &cp, int32_t maxI, int32_t maxJ);
-// Team sizes that fit a maxI x maxJ problem (the default choice first); returns how many.
+// One problem's columns with team size (or register-tiled shape code) `team`.
+int launch_spai_columns_team(cudaStream_t st, const ColumnProblem &cp, bool low_precision, int32_t maxI,
+                             int32_t maxJ, int team);
+// Team sizes that fit a maxI x maxJ problem (the default choice first), then the codes
+// (64 + i) of the register-tiled shapes that fit; returns how many (at most 12).
 int spai_columns_teams(int32_t maxI, int32_t maxJ, bool low_precision, int *teams);
 // All columns of a batch in one persistent launch with team size `team` (FP32 working
 // precision if low_precision); every problem must fit maxI x maxJ.
