@@ -615,6 +615,62 @@ def run_block_vs_single(sg, torch, ctx, w, nsys=5):
                     "iterations are Arnoldi steps (block steps for the block solve)"}
 
 
+def run_update_order(sg, torch, ctx, w, nparams=4):
+    """The two update orders of Sec. 2.4 on the same systems (the first `nparams` parameters
+    x the three shifts), one stream, FP64: over p -- per shift, SPAI built at the first
+    parameter, Q_l updates for the others (the sweep's order) -- and over s -- per
+    parameter, SPAI built at the first shift, updates for the other shifts
+    (min ||A(s_1, p) - A(s_k, p) Q||_F, P = Q P_1).  Each system is then solved (block
+    GMRES(m), 8 RHS); reported: time per solve including builds and updates, and the mean
+    iteration count of each order."""
+    n, nr = w.n, int(w.B.shape[1])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d_terms = [tuple(torch.as_tensor(np.ascontiguousarray(a), device=dev) for a in t) for t in w.terms]
+    aff = sg.spai_affine_create(ctx, [sg.csr(n, *t) for t in d_terms])
+    _, nnz, rp, ci = sg.spai_affine_pattern(aff)
+    ps, ss = list(w.params[:nparams]), list(w.shifts)
+    vals = {}
+    for p in ps:
+        for sh in ss:
+            v = torch.empty(nnz, dtype=torch.float64, device=dev)
+            sg.spai_assemble(ctx, aff, sg.affine_coefficients(p, sh), v)
+            vals[(p, sh)] = sg.csr(n, rp, ci, v, nnz)
+    B = torch.as_tensor(np.ascontiguousarray(w.B.T), device=dev)
+    X = torch.zeros((nr, n), dtype=torch.float64, device=dev)
+
+    def run(groups):
+        """groups: lists of (p, s) keys; the first of a group is built, the rest updated."""
+        its = []
+        for g in groups:
+            base = sg.spai_build(ctx, vals[g[0]])[0]
+            for key in g:
+                pc = base if key == g[0] else sg.spai_update(ctx, base, vals[key])[0]
+                X.zero_()
+                info = sg.block_solve(ctx, vals[key], pc, nr, B, n, X, n, w.restart, w.tol, 50)[1]
+                assert info["converged"], info
+                its.append(info["iterations"])
+                if pc is not base:
+                    sg.spai_pc_destroy(pc)
+            sg.spai_pc_destroy(base)
+        return its
+
+    orders = {"over_p": [[(p, sh) for p in ps] for sh in ss], "over_s": [[(p, sh) for sh in ss] for p in ps]}
+    out = {}
+    for name, groups in orders.items():
+        run(groups)  # warm-up (workspaces, kernel choices)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its = run(groups)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[name] = {"builds": len(groups), "updates": len(its) - len(groups), "ms_per_solve": 1e3 * dt / len(its),
+                     "gmres_iterations_mean": float(np.mean(its)), "gmres_iterations_max": int(max(its))}
+    sg.spai_affine_destroy(aff)
+    return {"systems": len(ps) * len(ss), "params": ps, "shifts": ss, **out,
+            "note": "one stream, FP64; over_p = one SPAI per shift updated across p (the sweep's order), "
+                    "over_s = one SPAI per parameter updated across s"}
+
+
 # ------------------------------------------------------------------------------- large
 def run_large(args, sg, torch):
     """3D side^3 27-point workload (side 128: n = 2,097,152, 27 nnz per column, 16 RHS):
@@ -1054,8 +1110,10 @@ def main():
 
     # block GMRES with 8 RHS against 8 single-RHS solves (the paper's block vs non-block)
     bvs = None
+    order = None
     if rank == 0 and world == 1 and not args.no_mixed:
         bvs = run_block_vs_single(sg, torch, ctx, w)
+        order = run_update_order(sg, torch, ctx, w)
     # many small systems: batched build and lockstep solves
     batched = None
     if rank == 0 and world == 1 and not args.no_batched:
@@ -1098,7 +1156,7 @@ def main():
                                             "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                                             "workers": args.workers},
             "roofline": roofline, "roofline_isolated": roofline_iso, "mixed_precision": mixed,
-            "warm_start": warm, "block_vs_single_rhs": bvs,
+            "warm_start": warm, "block_vs_single_rhs": bvs, "update_order": order,
             "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "large": large, "batched": batched, "gpu_launches": int(launches),
             "clocks": clk, "fp64_tflops_measured": fp64_tflops,
             "gmres_iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)),
