@@ -236,6 +236,24 @@ SPAI_API spai_status spai_build_batch(spai_ctx ctx, int32_t nsys, const spai_csr
 SPAI_API spai_status spai_update(spai_ctx ctx, spai_pc base, const spai_csr *A_new, int32_t approach,
                         spai_pc *out);
 
+/* Kernel variants of the column least squares (process-wide; no device work).  A tile
+ * shape is (low_precision: 0 FP64 / 1 FP32 working precision, max |I_k|, max |J_k|); its
+ * variants are shared-memory tiles with teams of T = 1 ... 32 lanes per column (code T)
+ * and register-tiled kernels (codes >= 64).  Every variant solves the same column
+ * problems and differs only in the rounding order of the reductions.
+ *   spai_column_variants: writes the codes that fit the shape to codes[0 .. cap-1] and
+ *     returns how many fit (the first one is the untuned default).
+ *   spai_column_variant_get: the code the process uses for the shape (the tuned or pinned
+ *     one; max |I_k| counts rounded up to a multiple of 8), or 0 before the first build or
+ *     update of that shape.
+ *   spai_column_variant_set: pins the shape to `code` for the rest of the process (code 0
+ *     clears it: the next build or update of the shape tunes again) -- for results that
+ *     are bitwise reproducible across processes, or to test one variant.  SPAI_EINVAL if
+ *     the code does not fit the shape. */
+SPAI_API int32_t spai_column_variants(int32_t low_precision, int32_t maxI, int32_t maxJ, int32_t *codes, int32_t cap);
+SPAI_API int32_t spai_column_variant_get(int32_t low_precision, int32_t maxI, int32_t maxJ);
+SPAI_API spai_status spai_column_variant_set(int32_t low_precision, int32_t maxI, int32_t maxJ, int32_t code);
+
 /* Sizes: n, nnz of this handle's own factor (P or Q_l; n for a diagonal update), total
  * length of the I_k lists, and depth (0 = built, 1 = updated from a build, ...).  Host outputs, any may be NULL. */
 SPAI_API spai_status spai_pc_info(spai_pc pc, int32_t *n, int32_t *nnz, int64_t *nI, int32_t *depth);

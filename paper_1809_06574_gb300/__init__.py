@@ -162,6 +162,9 @@ def lib():
         "spai_server_stats_get": (i32, [vp, P(spai_server_stats)]),
         "spai_server_last_error": (C.c_char_p, [vp]),
         "spai_server_destroy": (i32, [vp]),
+        "spai_column_variants": (i32, [i32, i32, i32, P(i32), i32]),
+        "spai_column_variant_get": (i32, [i32, i32, i32]),
+        "spai_column_variant_set": (i32, [i32, i32, i32, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -405,6 +408,22 @@ def block_solve(ctx, A, P, s, B, ldb, X, ldx, restart, tol, max_cycles, allow_no
         raise SpaiError(st, spai_last_error(ctx), result)
     _check(ctx, st, allow=(SPAI_ENOTCONV,))
     return result
+
+
+def spai_column_variants(low_precision, maxI, maxJ):
+    """Codes of the column-kernel variants that fit the tile shape (default first)."""
+    buf = (C.c_int32 * 16)()
+    k = lib().spai_column_variants(int(bool(low_precision)), int(maxI), int(maxJ), buf, 16)
+    return [int(buf[i]) for i in range(min(k, 16))]
+
+
+def spai_column_variant_get(low_precision, maxI, maxJ):
+    return int(lib().spai_column_variant_get(int(bool(low_precision)), int(maxI), int(maxJ)))
+
+
+def spai_column_variant_set(low_precision, maxI, maxJ, code):
+    """Pin (code != 0) or clear (code 0) the column-kernel variant of a tile shape."""
+    return _check(None, lib().spai_column_variant_set(int(bool(low_precision)), int(maxI), int(maxJ), int(code)))
 
 
 def spai_ctx_trim(ctx):

@@ -1615,6 +1615,44 @@ extern "C" spai_status spai_build_batch(spai_ctx ctx, int32_t nsys, const spai_c
     return st;
 }
 
+extern "C" int32_t spai_column_variants(int32_t low_precision, int32_t maxI, int32_t maxJ, int32_t *codes, int32_t cap)
+{
+    if (maxI < 1 || maxJ < 1 || !spai_columns_fit(maxI, maxJ)) return 0;
+    int cand[16];
+    const int nc = spai_columns_teams(maxI, maxJ, low_precision != 0, cand);
+    for (int i = 0; i < nc && i < cap && codes; ++i) codes[i] = cand[i];
+    return nc;
+}
+
+extern "C" int32_t spai_column_variant_get(int32_t low_precision, int32_t maxI, int32_t maxJ)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(std::make_tuple(low_precision ? 1 : 0, (maxI + 7) / 8 * 8, maxJ));
+    return it == g_tune.end() ? 0 : it->second;
+}
+
+extern "C" spai_status spai_column_variant_set(int32_t low_precision, int32_t maxI, int32_t maxJ, int32_t code)
+{
+    if (maxI < 1 || maxJ < 1) return SPAI_EINVAL;
+    const auto key = std::make_tuple(low_precision ? 1 : 0, (maxI + 7) / 8 * 8, maxJ);
+    if (code == 0) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune.erase(key);
+        return SPAI_OK;
+    }
+    // the code must fit every shape of the class: the largest max |I_k| it holds
+    int cand[16];
+    const int nc = spai_columns_fit(std::get<1>(key), maxJ)
+                       ? spai_columns_teams(std::get<1>(key), maxJ, low_precision != 0, cand)
+                       : 0;
+    bool ok = false;
+    for (int i = 0; i < nc; ++i) ok = ok || cand[i] == code;
+    if (!ok) return SPAI_EINVAL;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = code;
+    return SPAI_OK;
+}
+
 extern "C" spai_status spai_pc_info(spai_pc pc, int32_t *n, int32_t *nnz, int64_t *nI, int32_t *depth)
 {
     if (!pc) return SPAI_EINVAL;

@@ -73,3 +73,26 @@ def test_affine_coefficients_match_oracle():
     import paper_1809_06574_gb300 as sg
     for p, s in ((0.1, 1.0), (0.7, 0.5), (1.0, 2.0)):
         assert sg.affine_coefficients(p, s) == pytest.approx(oracle.coefficients(p, s), rel=1e-15)
+
+
+def test_column_variant_table_is_host_logic(library):
+    """The column-kernel variant table needs no GPU: the register-tiled codes (>= 64) are
+    offered exactly for the small tiles they hold (rows <= 32, |J| <= 13), the default is
+    a shared-memory team, and pinning round-trips (code 0 clears; a code that does not
+    fit the shape is refused)."""
+    import paper_1809_06574_gb300 as sg
+    for low in (0, 1):
+        small = sg.spai_column_variants(low, 25, 13)
+        assert small and small[0] < 64 and any(c >= 64 for c in small)
+        wide = sg.spai_column_variants(low, 125, 27)
+        assert wide and all(c < 64 for c in wide)
+        assert sg.spai_column_variants(low, 3000, 3000) == []
+    assert sg.spai_column_variant_get(1, 25, 13) == 0
+    code = max(sg.spai_column_variants(1, 25, 13))
+    sg.spai_column_variant_set(1, 25, 13, code)
+    assert sg.spai_column_variant_get(1, 32, 13) == code  # the same row class (25 -> 32)
+    assert sg.spai_column_variant_get(1, 33, 13) == 0
+    with pytest.raises(sg.SpaiError):
+        sg.spai_column_variant_set(1, 125, 27, code)  # a register tile cannot hold 125 x 27
+    sg.spai_column_variant_set(1, 25, 13, 0)
+    assert sg.spai_column_variant_get(1, 25, 13) == 0
