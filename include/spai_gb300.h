@@ -194,7 +194,7 @@ SPAI_API spai_status spai_affine_destroy(spai_affine aff);
  * Column kernel: the first build or update of the process that meets a tile shape
  * (working precision, max |I_k| rounded up to 8, max |J_k|) times every fitting kernel
  * variant -- shared-memory tiles with teams of 1 ... 32 lanes per column, and
- * register-tiled variants for tiles up to 32 x 13 -- on up to 65,536 of its columns and
+ * register-tiled variants for tiles up to 32 x 13 -- on up to 262,144 of its columns and
  * keeps the fastest for the rest of the process (one thread tunes at a time; variants
  * differ only in the rounding order of the reductions, within the FP64 bar).
  * Synchronises once (reads index-set sizes and the column status).  Returns

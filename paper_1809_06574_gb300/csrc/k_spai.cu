@@ -252,12 +252,14 @@ __device__ __forceinline__ void column_ls_reg(const P &cp, int64_t k, int tl, un
     for (int c = 0; c < MJ; ++c) {
         rd[c] = R(1);
         if (c < nj && !singular) {
+            // slot i holds rows T*i .. T*i + T-1: slots wholly above row c (known at compile
+            // time) and slots wholly past the last row (team-uniform) take no part
             R v[RPL];
             R ss = R(0);
 #pragma unroll
             for (int i = 0; i < RPL; ++i) {
                 v[i] = (tl + T * i >= c) ? a[c][i] : R(0);
-                ss = fma(v[i], v[i], ss);
+                if (T * i + T - 1 >= c && T * i < ni) ss = fma(v[i], v[i], ss);
             }
             ss = team_sum<T, R>(ss, mask);
             const R alpha = sqrt(ss);
@@ -274,18 +276,22 @@ __device__ __forceinline__ void column_ls_reg(const P &cp, int64_t k, int tl, un
                     if (t > c && t < nj) {
                         R d = R(0);
 #pragma unroll
-                        for (int i = 0; i < RPL; ++i) d = fma(v[i], a[t][i], d);
+                        for (int i = 0; i < RPL; ++i)
+                            if (T * i + T - 1 >= c && T * i < ni) d = fma(v[i], a[t][i], d);
                         const R g = team_sum<T, R>(d, mask) * inv;
 #pragma unroll
-                        for (int i = 0; i < RPL; ++i) a[t][i] = fma(-g, v[i], a[t][i]);
+                        for (int i = 0; i < RPL; ++i)
+                            if (T * i + T - 1 >= c && T * i < ni) a[t][i] = fma(-g, v[i], a[t][i]);
                     }
                 }
                 R d = R(0);
 #pragma unroll
-                for (int i = 0; i < RPL; ++i) d = fma(v[i], b[i], d);
+                for (int i = 0; i < RPL; ++i)
+                    if (T * i + T - 1 >= c && T * i < ni) d = fma(v[i], b[i], d);
                 const R g = team_sum<T, R>(d, mask) * inv;
 #pragma unroll
-                for (int i = 0; i < RPL; ++i) b[i] = fma(-g, v[i], b[i]);
+                for (int i = 0; i < RPL; ++i)
+                    if (T * i + T - 1 >= c && T * i < ni) b[i] = fma(-g, v[i], b[i]);
             }
         }
     }

@@ -552,13 +552,14 @@ spai_status sym_create(spai_ctx ctx, const spai_csr *A, int32_t kind, Sym **out)
 // after the first uses one team per shape.  Candidates change the rounding of the
 // reductions only.  Candidates are timed on the first kTuneColumns columns when there are
 // more (a bounded one-time cost: the 27-point 128^3 FP64 build would otherwise pay a dozen
-// full launches); when all columns were timed, each candidate wrote the complete result
-// and *done on return says the chosen candidate's result is already in place.
+// full launches; smaller samples misjudged variants whose blocks hold different numbers
+// of columns by a few per cent); when all columns were timed, each candidate wrote the
+// complete result and *done on return says the chosen candidate's result is in place.
 std::mutex g_tune_mu;      // guards g_tune
 std::mutex g_tune_run_mu;  // one tuning run at a time
 std::map<std::tuple<int, int, int>, int> g_tune;
 
-constexpr int64_t kTuneColumns = 65536;
+constexpr int64_t kTuneColumns = 262144;
 
 spai_status tuned_team(spai_ctx ctx, bool low, int32_t maxI, int32_t maxJ, int64_t total,
                        const std::function<int(int, int64_t)> &launch, int *team, bool *done)
