@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--workers", type=int, default=4)
     # single-kernel case (for profiler captures): H = V^T W or W -= V H at n = side^3, s = 8
     ap.add_argument("--kernel", default=None, choices=["dot", "update", "columns"])
+    ap.add_argument("--columns-workload", default="batched2d", choices=["batched2d", "sweep3d"],
+                    help="--kernel columns: the batched 2D systems (FP32) or one FP64 SPAI of the 3D sweep")
     ap.add_argument("--nblk", type=int, default=16)
     ap.add_argument("--orth", default="tensor", choices=["tensor", "fp64"])
     # serving: Poisson arrivals over a pool of 16 3D 7-point grids (sides 24-96)
@@ -214,20 +216,30 @@ def run_columns_case(args):
     import torch
     import synth
     import paper_1809_06574_gb300 as sg
-    ws = synth.batched_2d(args.batched_systems)
-    kinds = [(sg.PATTERN_A if w.extra["pattern"] == "A" else sg.PATTERN_A2) | sg.PREC_FP32 for w in ws]
+    if args.columns_workload == "sweep3d":  # one FP64 SPAI (pattern of A) of the sweep's first system
+        ws = [synth.grid3d_7pt(side=args.side, nparams=args.nparams)]
+        kinds = [sg.PATTERN_A]
+        shifts = [ws[0].shifts[0]]
+    else:
+        ws = synth.batched_2d(args.batched_systems)
+        kinds = [(sg.PATTERN_A if w.extra["pattern"] == "A" else sg.PATTERN_A2) | sg.PREC_FP32 for w in ws]
+        shifts = [1.0] * len(ws)
     stream = torch.cuda.current_stream()
     ctx = sg.spai_ctx_create(stream.cuda_stream, 0)
     As, keep = [], []
-    for w in ws:
-        aff = sg.spai_affine_create(ctx, [sg.csr(w.n, *t) for t in w.terms])
+    for w, sh in zip(ws, shifts):
+        terms = [tuple(torch.as_tensor(np.ascontiguousarray(a), device="cuda") for a in t) for t in w.terms]
+        aff = sg.spai_affine_create(ctx, [sg.csr(w.n, *t) for t in terms])
         _, nnz, rp, ci = sg.spai_affine_pattern(aff)
         va = torch.empty(nnz, dtype=torch.float64, device="cuda")
-        sg.spai_assemble(ctx, aff, sg.affine_coefficients(w.params[0], 1.0), va)
+        sg.spai_assemble(ctx, aff, sg.affine_coefficients(w.params[0], sh), va)
         As.append(sg.csr(w.n, rp, ci, va, nnz))
-        keep.append((aff, va))
+        keep.append((aff, va, terms))
 
     def once():
+        if len(As) == 1:
+            sg.spai_pc_destroy(sg.spai_build(ctx, As[0], kinds[0])[0])
+            return
         for pc in sg.spai_build_batch(ctx, As, kinds)[0]:
             sg.spai_pc_destroy(pc)
     for _ in range(max(args.warmup, 1)):
@@ -241,10 +253,10 @@ def run_columns_case(args):
     wall = (time.perf_counter() - t0) / max(args.steps, 1)
     prof = [sg.spai_ctx_profile_entry(ctx, i) for i in range(sg.spai_ctx_profile_count(ctx))]
     sg.spai_ctx_profile(ctx, 0)
-    for aff, _ in keep:
+    for aff, _, _ in keep:
         sg.spai_affine_destroy(aff)
     sg.spai_ctx_destroy(ctx)
-    print(json.dumps({"kernel_case": "columns", "systems": len(ws), "columns": sum(w.n for w in ws),
+    print(json.dumps({"kernel_case": "columns", "workload": args.columns_workload, "systems": len(ws), "columns": sum(w.n for w in ws),
                       "steps": args.steps, "build_ms": 1e3 * wall,
                       "device_ms_per_build": {f["name"]: round(f["ms"] / max(args.steps, 1), 3) for f in prof}}),
           flush=True)
