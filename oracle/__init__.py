@@ -16,6 +16,11 @@ What it computes, with the passage of arXiv 1809.06574 it writes out:
 * ``spai_update`` -- min_Q ||A(1) - A(l) Q||_F (Table 1 first approach, Sec. 2.4),
   P_l = Q_l P_1 kept factored; ``spai_update_chained`` is Table 1's second approach;
   ``spai_update_diagonal`` takes Q_l diagonal (the same least squares on J_k = {k}).
+* ``spai_adaptive_pattern`` / ``spai_build_adaptive`` -- SPAI on a pattern grown column
+  by column (the adaptive pattern of the MSPAI code the paper runs, Sec. 3: tolerance
+  1e-4): least squares on J_k, residual, candidate columns that meet the residual's rows,
+  their one-dimensional improvement, the best below the mean added, until the residual
+  norm is below the tolerance or a step limit is reached.
 * ``block_gmres`` -- the right-preconditioned (Sec. 2.2 footnote) block Krylov solve
   of Sec. 2.1: block GMRES(m) over span{R0, AP R0, (AP)^2 R0, ...}.
 * ``lu_solve`` -- dense LU with partial pivoting for tiny reference solves.
@@ -238,6 +243,130 @@ def spai_build(A, n, kind=PATTERN_A, k0=0, k1=None, sets=None):
         Jptr, Jind, Iptr, Ilist = (_i32(a) for a in sets)
     val, status = _columns(A_csc, n, Jptr, Jind, Iptr, Ilist, 0, None, k0, k1)
     return Precond(n, Jptr, Jind, Iptr, Ilist, val, status, None, A_csc)
+
+
+# --------------------------------------------------------------------------------------
+# adaptive pattern (MSPAI, Sec. 3; the least squares of Sec. 2.2 on a growing J_k)
+# --------------------------------------------------------------------------------------
+
+ADAPTIVE_KEY_BITS = 30   # improvements compare at 2^-30 of ||r||^2 (ties: lower column index)
+ADAPTIVE_MAX_COLS = 32   # 1 + max_steps * max_new must not exceed this
+ADAPTIVE_MAX_ROWS = 128  # |I_k| above max_rows stops the growth of J_k
+
+
+def _adaptive_key(x, rr):
+    """Quantised improvement: floor(x / ||r||^2 * 2^30), clamped to [0, 2^30]."""
+    q = np.floor((x / rr) * float(1 << ADAPTIVE_KEY_BITS))
+    return int(min(max(q, 0.0), float(1 << ADAPTIVE_KEY_BITS)))
+
+
+def spai_adaptive_pattern(A, n, eps=1e-4, max_steps=5, max_new=5, max_rows=ADAPTIVE_MAX_ROWS, k0=0, k1=None,
+                          trace=None):
+    """Column patterns J_k of the adaptive SPAI, one column at a time (plain loops; small n).
+
+    For column k, starting from J_k = {k}:
+      1. I_k = {k} and the rows of the columns in J_k; m = argmin ||e_k - A(:, J_k) m||_2
+         (the column least squares of Sec. 2.2, solved here by numpy's Householder QR);
+      2. r = e_k - sum_c A(:, J_c) m_c (column by column); stop if ||r||_2 <= eps, after
+         max_steps additions, or if the least squares is rank deficient;
+      3. candidates: the columns j not in J_k with a nonzero in a row of I_k (the rows where
+         r can be nonzero); for each, the squared residual after the best one-column
+         correction, rho_j = ||r||^2 - (r . A(:,j))^2 / ||A(:,j)||^2;
+      4. add the at most max_new candidates of smallest rho_j among those with rho_j not
+         above the candidates' mean (compared as floor(rho / ||r||^2 * 2^30); ties by the
+         lower column index); the step is undone and the growth stops if |I_k| would
+         exceed max_rows.
+    Returns (Jptr, Jind) for columns k0 <= k < k1 (others J_k = {k}).  ``trace``, a list,
+    receives (k, step, J, I, rr, candidates, rho, chosen) per step for the tests."""
+    if 1 + max_steps * max_new > ADAPTIVE_MAX_COLS or max_rows > ADAPTIVE_MAX_ROWS:
+        raise ValueError("pattern limits exceed the supported sizes")
+    k1 = n if k1 is None else k1
+    rowptr, colind, val = _i32(A[0]), _i32(A[1]), _f64(A[2])
+    colptr, rowind, cval = csr_to_csc(A, n)
+    colnorm2 = np.zeros(n)
+    for j in range(n):
+        acc = 0.0
+        for q in range(colptr[j], colptr[j + 1]):
+            acc = acc + cval[q] * cval[q]
+        colnorm2[j] = acc
+    pats = []
+    for k in range(n):
+        if not (k0 <= k < k1):
+            pats.append([k])
+            continue
+        J = [k]
+
+        def rows_of(cols):
+            out = {k}
+            for j in cols:
+                out.update(int(x) for x in rowind[colptr[j]:colptr[j + 1]])
+            return sorted(out)
+
+        I = rows_of(J)
+        for step in range(max_steps + 1):
+            pos = {row: i for i, row in enumerate(I)}
+            Ah = np.zeros((len(I), len(J)))
+            for c, j in enumerate(J):
+                for q in range(colptr[j], colptr[j + 1]):
+                    Ah[pos[int(rowind[q])], c] = cval[q]
+            rhs = np.zeros(len(I))
+            rhs[pos[k]] = 1.0
+            if len(I) < len(J):
+                break
+            Q, R = np.linalg.qr(Ah)
+            d = np.abs(np.diag(R))
+            if d.max() == 0.0 or d.min() <= 1e-14 * d.max():
+                break
+            m = np.linalg.solve(R, Q.T @ rhs)
+            r = rhs.copy()
+            for c, j in enumerate(J):
+                for q in range(colptr[j], colptr[j + 1]):
+                    i = pos[int(rowind[q])]
+                    r[i] = r[i] - cval[q] * m[c]
+            rr = 0.0
+            for x in r:
+                rr = rr + x * x
+            if np.sqrt(rr) <= eps or step == max_steps:
+                break
+            inJ = set(J)
+            cand = sorted({int(j) for row in I for j in colind[rowptr[row]:rowptr[row + 1]]} - inJ)
+            if not cand:
+                break
+            rho = []
+            for j in cand:
+                dot = 0.0
+                for q in range(colptr[j], colptr[j + 1]):
+                    i = pos.get(int(rowind[q]))
+                    if i is not None:
+                        dot = dot + r[i] * cval[q]
+                rho.append(rr - dot * dot / colnorm2[j])
+            mean = 0.0
+            for x in rho:
+                mean = mean + x
+            mean = mean / len(rho)
+            kmean = _adaptive_key(mean, rr)
+            keyed = sorted((_adaptive_key(x, rr), j) for x, j in zip(rho, cand) if _adaptive_key(x, rr) <= kmean)
+            chosen = [j for _, j in keyed[:max_new]]
+            if trace is not None:
+                trace.append((k, step, list(J), list(I), rr, cand, rho, chosen))
+            newJ = sorted(J + chosen)
+            newI = rows_of(newJ)
+            if len(newI) > max_rows:
+                break
+            J, I = newJ, newI
+        pats.append(J)
+    Jptr = np.zeros(n + 1, np.int32)
+    Jptr[1:] = np.cumsum([len(x) for x in pats])
+    Jind = np.array([j for x in pats for j in x], np.int32)
+    return Jptr, Jind
+
+
+def spai_build_adaptive(A, n, eps=1e-4, max_steps=5, max_new=5, max_rows=ADAPTIVE_MAX_ROWS, k0=0, k1=None):
+    """Adaptive SPAI: the pattern of ``spai_adaptive_pattern``, then the column least
+    squares of ``spai_build`` on it (Householder QR, Sec. 2.2)."""
+    Jptr, Jind = spai_adaptive_pattern(A, n, eps, max_steps, max_new, max_rows, k0, k1)
+    Iptr, Ilist = index_sets(A, n, Jptr, Jind)
+    return spai_build(A, n, PATTERN_A, k0, k1, sets=(Jptr, Jind, Iptr, Ilist))
 
 
 def spai_update(base: Precond, A_new, n, k0=0, k1=None):
