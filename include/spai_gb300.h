@@ -236,6 +236,38 @@ SPAI_API spai_status spai_build_batch(spai_ctx ctx, int32_t nsys, const spai_csr
 SPAI_API spai_status spai_update(spai_ctx ctx, spai_pc base, const spai_csr *A_new, int32_t approach,
                         spai_pc *out);
 
+/* ----------------------------------------------------------------------------------
+ * Adaptive SPAI (the pattern growth of the MSPAI code the paper's experiments run, Sec. 3,
+ * "tolerance 1e-4", around the column least squares of Sec. 2.2).  For each column k,
+ * J_k starts as {k}; each step solves the column least squares on J_k (rows I_k = {k} and
+ * the rows of the columns in J_k), forms the residual r = e_k - A m_k, takes as
+ * candidates the columns j not in J_k with a nonzero in a row of I_k, scores each by the
+ * squared residual after the best one-column correction, rho_j = ||r||^2 - (r . A(:,j))^2
+ * / ||A(:,j)||^2, and adds the max_new best among those not above the candidates' mean
+ * (scores compared as floor(rho / ||r||^2 * 2^30), ties by the lower column index).  It
+ * stops when ||r||_2 <= eps, after max_steps steps, on a rank-deficient column problem,
+ * when no candidate is left, when a step meets more than 1024 candidate entries (counted
+ * with repeats over the rows of I_k), or when |I_k| would exceed max_rows (that step is
+ * undone).  The search runs in FP64; the factor on the final pattern is then computed by
+ * the column kernel of spai_build in the precision that `flags` selects.  The handle is an
+ * ordinary one: spai_update keeps its pattern (the update skips the search, Sec. 2.3-2.4),
+ * and apply, solve, export and destroy work as for spai_build.
+ * ---------------------------------------------------------------------------------- */
+typedef struct {
+    double eps;         /* target ||e_k - A m_k||_2 of every column (the paper's 1e-4) */
+    int32_t max_steps;  /* pattern-growth steps per column, >= 0 */
+    int32_t max_new;    /* columns added per step, >= 1; 1 + max_steps * max_new <= 32 */
+    int32_t max_rows;   /* largest |I_k|, 1 ... 128 */
+    int32_t reserved;   /* 0 */
+} spai_adaptive_opts;
+
+/* Build an adaptive SPAI of A (device CSR).  opts NULL: eps 1e-4, max_steps 5, max_new 5,
+ * max_rows 128.  flags: 0 (FP64 factor), SPAI_PREC_FP32 or SPAI_PREC_BF16.  Columns whose
+ * growth stopped at a size limit keep the pattern they had.  Synchronises a few times.
+ * Returns SPAI_ESINGULAR as spai_build does (handle still returned). */
+SPAI_API spai_status spai_build_adaptive(spai_ctx ctx, const spai_csr *A, const spai_adaptive_opts *opts,
+                                         int32_t flags, spai_pc *out);
+
 /* Kernel variants of the column least squares (process-wide; no device work).  A tile
  * shape is (low_precision: 0 FP64 / 1 FP32 working precision, max |I_k|, max |J_k|); its
  * variants are shared-memory tiles with teams of T = 1 ... 32 lanes per column (code T)

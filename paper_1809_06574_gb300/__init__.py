@@ -106,6 +106,11 @@ class spai_server_stats(C.Structure):
 
 ROUTE_BUILD, ROUTE_UPDATE, ROUTE_REUSE = 0, 1, 2
 
+
+class spai_adaptive_opts(C.Structure):
+    _fields_ = [("eps", C.c_double), ("max_steps", C.c_int32), ("max_new", C.c_int32),
+                ("max_rows", C.c_int32), ("reserved", C.c_int32)]
+
 _lib = None
 
 
@@ -162,6 +167,7 @@ def lib():
         "spai_server_stats_get": (i32, [vp, P(spai_server_stats)]),
         "spai_server_last_error": (C.c_char_p, [vp]),
         "spai_server_destroy": (i32, [vp]),
+        "spai_build_adaptive": (i32, [vp, P(spai_csr), P(spai_adaptive_opts), i32, P(vp)]),
         "spai_column_variants": (i32, [i32, i32, i32, P(i32), i32]),
         "spai_column_variant_get": (i32, [i32, i32, i32]),
         "spai_column_variant_set": (i32, [i32, i32, i32, i32]),
@@ -408,6 +414,21 @@ def block_solve(ctx, A, P, s, B, ldb, X, ldx, restart, tol, max_cycles, allow_no
         raise SpaiError(st, spai_last_error(ctx), result)
     _check(ctx, st, allow=(SPAI_ENOTCONV,))
     return result
+
+
+def spai_build_adaptive(ctx, A, eps=1e-4, max_steps=5, max_new=5, max_rows=128, flags=0, allow_singular=False):
+    """Adaptive SPAI (pattern grown per column, then the column least squares on it).
+    Returns (handle, status)."""
+    o = spai_adaptive_opts(float(eps), int(max_steps), int(max_new), int(max_rows), 0)
+    out = C.c_void_p()
+    st = lib().spai_build_adaptive(ctx, C.byref(A), C.byref(o), int(flags), C.byref(out))
+    if st == SPAI_ESINGULAR and not allow_singular:
+        msg = spai_last_error(ctx)
+        if out:
+            lib().spai_pc_destroy(out)
+        raise SpaiError(st, msg)
+    _check(ctx, st, allow=(SPAI_ESINGULAR,))
+    return out, st
 
 
 def spai_column_variants(low_precision, maxI, maxJ):

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libspai_gb300.so")
-SOURCES = ["k_sparse.cu", "k_spai.cu", "k_krylov.cu", "k_ozaki.cu", "spai_api.cu", "spai_serve.cu"]
+SOURCES = ["k_sparse.cu", "k_spai.cu", "k_krylov.cu", "k_ozaki.cu", "k_adaptive.cu", "spai_api.cu",
+           "spai_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", "-I", INCLUDE,
          "-I", CSRC]

@@ -1006,6 +1006,204 @@ extern "C" spai_status spai_build(spai_ctx ctx, const spai_csr *A, int32_t patte
     return st;
 }
 
+namespace {
+
+// Gives s (an analysis of pattern kind A) the column pattern (Jptr, Jind) instead, taking
+// ownership of both arrays on success: the row pattern of P and its position map
+// (transposition of J), I_k = union of rows(A(:,j)) over J_k, and the sizes.
+spai_status sym_set_pattern(spai_ctx ctx, Sym *s, int32_t *Jptr, int32_t *Jind, int32_t nnzP)
+{
+    cudaStream_t cs = ctx->stream;
+    const int32_t n = s->n;
+    spai_status st = SPAI_OK;
+    int32_t *p_rowptr = nullptr, *p_colind = nullptr, *p_map = nullptr, *perm = nullptr, *Iptr = nullptr,
+            *Ilist = nullptr, *counts = nullptr, *d_max = nullptr;
+    void *temp = nullptr;
+    auto done = [&](spai_status rc) {
+        dfree(ctx, perm);
+        dfree(ctx, temp);
+        dfree(ctx, counts);
+        dfree(ctx, d_max);
+        if (rc) {
+            dfree(ctx, p_rowptr);
+            dfree(ctx, p_colind);
+            dfree(ctx, p_map);
+            dfree(ctx, Iptr);
+            dfree(ctx, Ilist);
+        }
+        return rc;
+    };
+#define TRY(x)                                         \
+    do {                                               \
+        if ((st = (x)) != SPAI_OK) return done(st);    \
+    } while (0)
+#define TRYK(call, what)                                                                                     \
+    do {                                                                                                     \
+        if ((call) != 0)                                                                                     \
+            return done(fail(ctx, SPAI_ECUDA, "%s: kernel launch failed (%s)", what,                         \
+                             cudaGetErrorString(cudaGetLastError())));                                       \
+    } while (0)
+    const size_t tb = std::max(transpose_temp_bytes(n, std::max(nnzP, 1)), scan_temp_bytes(n));
+    TRY(dalloc(ctx, &temp, tb));
+    TRY(dalloc_n(ctx, &p_rowptr, (int64_t)n + 1));
+    TRY(dalloc_n(ctx, &p_colind, nnzP));
+    TRY(dalloc_n(ctx, &p_map, nnzP));
+    TRY(dalloc_n(ctx, &perm, nnzP));
+    TRY(dalloc_n(ctx, &counts, (int64_t)n + 1));
+    TRY(dalloc_n(ctx, &d_max, 2));
+    TRYK(launch_transpose(cs, n, nnzP, Jptr, Jind, p_rowptr, p_colind, perm, temp, ctx->d_err), "transpose pattern");
+    TRYK(launch_invert_perm(cs, nnzP, perm, p_map), "invert");
+    TRYK(launch_max_i32_diff(cs, n, Jptr, d_max), "max |J|");
+    int32_t maxJ = 0;
+    TRY(read_i32(ctx, d_max, &maxJ));
+    if (maxJ > colunion_max_lists())
+        return done(fail(ctx, SPAI_EINVAL, "a column pattern has %d entries; at most %d are supported", maxJ,
+                         colunion_max_lists()));
+    TRY(dalloc_n(ctx, &Iptr, (int64_t)n + 1));
+    TRYK(launch_colunion_count(cs, n, maxJ, Jptr, Jind, s->a_colptr, s->a_rowind, counts, ctx->d_err), "I count");
+    TRYK(launch_exclusive_scan(cs, counts, Iptr, n, temp, ctx->d_err), "scan");
+    int32_t nI = 0;
+    TRY(read_i32(ctx, Iptr + n, &nI));
+    TRY(dalloc_n(ctx, &Ilist, nI));
+    TRYK(launch_colunion_fill(cs, n, maxJ, Jptr, Jind, s->a_colptr, s->a_rowind, Iptr, Ilist, ctx->d_err), "I fill");
+    TRYK(launch_max_i32_diff(cs, n, Iptr, d_max + 1), "max |I|");
+    int32_t maxI = 0;
+    TRY(read_i32(ctx, d_max + 1, &maxI));
+    int herr = 0;
+    TRY(read_err(ctx, &herr));
+    if (herr) return done(fail(ctx, SPAI_EINVAL, "pattern analysis failed (device error 0x%x)", herr));
+    if (!spai_columns_fit(maxI, maxJ))
+        return done(fail(ctx, SPAI_EINVAL, "column problem of %d x %d exceeds the shared-memory tile", maxI, maxJ));
+#undef TRY
+#undef TRYK
+    // adopt the new pattern (pattern kind A aliases J and the row pattern to A's arrays)
+    if (!s->alias) {
+        dfree(ctx, s->Jptr);
+        dfree(ctx, s->Jind);
+        dfree(ctx, s->p_rowptr);
+        dfree(ctx, s->p_colind);
+        dfree(ctx, s->p_map);
+    }
+    dfree(ctx, s->Iptr);
+    dfree(ctx, s->Ilist);
+    s->alias = false;
+    s->Jptr = Jptr;
+    s->Jind = Jind;
+    s->nnzP = nnzP;
+    s->p_rowptr = p_rowptr;
+    s->p_colind = p_colind;
+    s->p_map = p_map;
+    s->Iptr = Iptr;
+    s->Ilist = Ilist;
+    s->nI = nI;
+    s->maxI = maxI;
+    s->maxJ = maxJ;
+    return done(SPAI_OK);
+}
+
+}  // namespace
+
+extern "C" spai_status spai_build_adaptive(spai_ctx ctx, const spai_csr *A, const spai_adaptive_opts *opts,
+                                           int32_t flags, spai_pc *out)
+{
+    if (!ctx || !out) return fail(ctx, SPAI_EINVAL, "NULL argument");
+    *out = nullptr;
+    spai_adaptive_opts o{1e-4, 5, 5, 128, 0};
+    if (opts) o = *opts;
+    const int prec = prec_of(flags);
+    if (prec < 0 || (flags & ~(SPAI_PREC_FP32 | SPAI_PREC_BF16)))
+        return fail(ctx, SPAI_EINVAL, "flags: SPAI_PREC_FP32 or SPAI_PREC_BF16 (exclusive) or 0");
+    if (!(o.eps >= 0.0) || o.max_steps < 0 || o.max_new < 1 || o.max_rows < 1 ||
+        o.max_rows > adaptive_max_rows() || 1 + (int64_t)o.max_steps * o.max_new > adaptive_max_cols())
+        return fail(ctx, SPAI_EINVAL, "adaptive options: eps >= 0, max_new >= 1, 1 <= max_rows <= %d, "
+                    "1 + max_steps * max_new <= %d", adaptive_max_rows(), adaptive_max_cols());
+    spai_status st = validate_device_csr(ctx, A, "A");
+    if (st) return st;
+    Sym *s = nullptr;
+    if ((st = sym_create(ctx, A, SPAI_PATTERN_A, &s))) return st;
+    const int32_t n = s->n;
+    double *cval = nullptr, *cn = nullptr;
+    int32_t *outJ = nullptr, *cnt = nullptr, *Jptr = nullptr, *Jind = nullptr;
+    void *temp = nullptr;
+    auto bail = [&](spai_status rc) {
+        dfree(ctx, cval);
+        dfree(ctx, cn);
+        dfree(ctx, outJ);
+        dfree(ctx, cnt);
+        dfree(ctx, temp);
+        dfree(ctx, Jptr);
+        dfree(ctx, Jind);
+        sym_release(s);
+        return rc;
+    };
+    if (n > 0) {
+        const int mc = adaptive_max_cols();
+        if ((st = dalloc_n(ctx, &cval, std::max(s->nnzA, 1))) || (st = dalloc_n(ctx, &cn, n)) ||
+            (st = dalloc_n(ctx, &outJ, (int64_t)n * mc)) || (st = dalloc_n(ctx, &cnt, (int64_t)n + 1)) ||
+            (st = dalloc(ctx, &temp, scan_temp_bytes(n))) || (st = dalloc_n(ctx, &Jptr, (int64_t)n + 1)))
+            return bail(st);
+        if (s->nnzA && launch_gather_f64(ctx->stream, s->nnzA, s->a_perm, A->val, cval))
+            return bail(fail(ctx, SPAI_ECUDA, "gather values: kernel launch failed"));
+        if (launch_colnorm2_csc(ctx->stream, n, s->a_colptr, cval, cn))
+            return bail(fail(ctx, SPAI_ECUDA, "column norms: kernel launch failed"));
+        AdaptiveProblem ap{};
+        ap.n = n;
+        ap.colptr = s->a_colptr;
+        ap.rowind = s->a_rowind;
+        ap.cval = cval;
+        ap.rowptr = s->a_rowptr;
+        ap.colind = s->a_colind;
+        ap.colnorm2 = cn;
+        ap.eps = o.eps;
+        ap.max_steps = o.max_steps;
+        ap.max_new = o.max_new;
+        ap.max_rows = o.max_rows;
+        ap.out_J = outJ;
+        ap.out_count = cnt;
+        ap.d_err = ctx->d_err;
+        {
+            ProfScope ps_(ctx, "adaptive_pattern", 0.0, 0.0);
+            if (launch_adaptive_pattern(ctx->stream, ap))
+                return bail(fail(ctx, SPAI_ECUDA, "adaptive pattern: kernel launch failed (%s)",
+                                 cudaGetErrorString(cudaGetLastError())));
+        }
+        if (launch_exclusive_scan(ctx->stream, cnt, Jptr, n, temp, ctx->d_err))
+            return bail(fail(ctx, SPAI_ECUDA, "scan: kernel launch failed"));
+        int32_t nnzP = 0;
+        if ((st = read_i32(ctx, Jptr + n, &nnzP))) return bail(st);
+        int herr = 0;
+        if ((st = read_err(ctx, &herr))) return bail(st);
+        // ERR_TOO_WIDE here only reports columns whose growth stopped at a size limit
+        if (herr & ~ERR_TOO_WIDE) return bail(fail(ctx, SPAI_EINVAL, "adaptive pattern failed (device error 0x%x)", herr));
+        if ((st = dalloc_n(ctx, &Jind, std::max(nnzP, 1)))) return bail(st);
+        if (launch_compact_lists(ctx->stream, n, outJ, mc, Jptr, Jind))
+            return bail(fail(ctx, SPAI_ECUDA, "compaction: kernel launch failed"));
+        if ((st = sym_set_pattern(ctx, s, Jptr, Jind, nnzP))) return bail(st);
+        Jptr = Jind = nullptr;  // owned by s now
+        dfree(ctx, cval);
+        dfree(ctx, cn);
+        dfree(ctx, outJ);
+        dfree(ctx, cnt);
+        dfree(ctx, temp);
+        cval = cn = nullptr;
+        outJ = cnt = nullptr;
+        temp = nullptr;
+    }
+    spai_pc pc = nullptr;
+    if ((st = pc_alloc(ctx, s, prec, &pc))) return bail(st);
+    pc->root = pc;
+    if (s->nnzA)
+        PKL("gather_csc", 0.0, 20.0 * s->nnzA, launch_gather_f64(ctx->stream, s->nnzA, s->a_perm, A->val, pc->a_cval),
+            "gather values");
+    st = run_columns(ctx, pc, 0, nullptr);
+    if (st && st != SPAI_ESINGULAR) {
+        spai_pc_destroy(pc);
+        return st;
+    }
+    *out = pc;
+    return st;
+}
+
 extern "C" spai_status spai_update(spai_ctx ctx, spai_pc base, const spai_csr *A_new, int32_t approach, spai_pc *out)
 {
     if (!ctx || !out || !base) return fail(ctx, SPAI_EINVAL, "NULL argument");

@@ -132,6 +132,26 @@ struct ColumnProblem {
     int32_t *col_status;             // 0 ok, 1 singular
     int *d_err;
 };
+// Adaptive SPAI pattern search (k_adaptive.cu): one warp per column grows J_k from {k};
+// the final lists go to out_J[k * adaptive_max_cols() ...], their sizes to out_count[k].
+struct AdaptiveProblem {
+    int32_t n;
+    const int32_t *colptr, *rowind;  // CSC of A
+    const double *cval;
+    const int32_t *rowptr, *colind;  // CSR pattern of A
+    const double *colnorm2;          // ||A(:,j)||^2
+    double eps;
+    int32_t max_steps, max_new, max_rows;
+    int32_t *out_J, *out_count;
+    int *d_err;
+};
+int adaptive_max_cols();
+int adaptive_max_rows();
+int launch_adaptive_pattern(cudaStream_t st, const AdaptiveProblem &ap);
+int launch_colnorm2_csc(cudaStream_t st, int32_t n, const int32_t *colptr, const double *cval, double *out);
+// out[ptr[k] + c] = lists[k * stride + c] for c < ptr[k + 1] - ptr[k]
+int launch_compact_lists(cudaStream_t st, int32_t n, const int32_t *lists, int32_t stride, const int32_t *ptr,
+                         int32_t *out);
 // Column problems of several systems: column g (0 <= g < total) is local column
 // g - start[i] of system i, start[i] <= g < start[i + 1]; tab[i] is its problem (device).
 struct ColumnBatch {
