@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--large-params", type=int, default=3)
     # batched workload: 256 independent 2D 5-point systems, sides 48-256
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-adaptive", action="store_true")
     ap.add_argument("--batched-only", action="store_true")
     ap.add_argument("--batched-systems", type=int, default=256)
     ap.add_argument("--batched-workers", type=int, default=8)
@@ -683,6 +684,69 @@ def run_update_order(sg, torch, ctx, w, nparams=4):
                     "over_s = one SPAI per parameter updated across s"}
 
 
+def run_adaptive(sg, torch, ctx, w, nparams=3):
+    """Adaptive SPAI (pattern grown per column to the paper's MSPAI tolerance 1e-4, at most
+    5 steps of 5 columns) on the sweep's matrices at the first shift: built at p_1, then
+    for the next `nparams` parameters an update from it (the base's pattern: no search,
+    Sec. 2.3-2.4) against a rebuild with its own search, each followed by the block GMRES
+    solve (8 RHS).  One stream, FP64; the paper's comparison (SPAI vs SPAI update, Sec. 3)."""
+    n, nr = w.n, int(w.B.shape[1])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d_terms = [tuple(torch.as_tensor(np.ascontiguousarray(a), device=dev) for a in t) for t in w.terms]
+    aff = sg.spai_affine_create(ctx, [sg.csr(n, *t) for t in d_terms])
+    _, nnz, rp, ci = sg.spai_affine_pattern(aff)
+    sh = w.shifts[0]
+    vals = [torch.empty(nnz, dtype=torch.float64, device=dev) for _ in range(nparams + 1)]
+    As = []
+    for i, v in enumerate(vals):
+        sg.spai_assemble(ctx, aff, sg.affine_coefficients(w.params[i], sh), v)
+        As.append(sg.csr(n, rp, ci, v, nnz))
+    B = torch.as_tensor(np.ascontiguousarray(w.B.T), device=dev)
+    X = torch.zeros((nr, n), dtype=torch.float64, device=dev)
+
+    def timed(f):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = f()
+        torch.cuda.synchronize()
+        return r, 1e3 * (time.perf_counter() - t0)
+
+    def solve(A, pc):
+        X.zero_()
+        info = sg.block_solve(ctx, A, pc, nr, B, n, X, n, w.restart, w.tol, 50)[1]
+        assert info["converged"], info
+        return info["iterations"]
+
+    sg.spai_pc_destroy(sg.spai_build_adaptive(ctx, As[0])[0])  # warm-up (kernel choices, pools)
+    base, t_base = timed(lambda: sg.spai_build_adaptive(ctx, As[0])[0])
+    nnz_p = sg.spai_pc_info(base)["nnz"]
+    rows = []
+    for i in range(1, nparams + 1):
+        q, t_upd = timed(lambda: sg.spai_update(ctx, base, As[i])[0])
+        it_upd, t_su = timed(lambda: solve(As[i], q))
+        sg.spai_pc_destroy(q)
+        pc, t_reb = timed(lambda: sg.spai_build_adaptive(ctx, As[i])[0])
+        it_reb, t_sr = timed(lambda: solve(As[i], pc))
+        sg.spai_pc_destroy(pc)
+        fixed = sg.spai_build(ctx, As[i], sg.PATTERN_A)[0]
+        it_fix = solve(As[i], fixed)
+        sg.spai_pc_destroy(fixed)
+        rows.append({"p": w.params[i], "update_ms": t_upd, "rebuild_ms": t_reb, "solve_after_update_ms": t_su,
+                     "solve_after_rebuild_ms": t_sr, "iterations_update": it_upd, "iterations_rebuild": it_reb,
+                     "iterations_fixed_pattern_A": it_fix})
+    sg.spai_pc_destroy(base)
+    sg.spai_affine_destroy(aff)
+    upd = float(np.mean([r["update_ms"] for r in rows]))
+    reb = float(np.mean([r["rebuild_ms"] for r in rows]))
+    tot_u = float(np.mean([r["update_ms"] + r["solve_after_update_ms"] for r in rows]))
+    tot_r = float(np.mean([r["rebuild_ms"] + r["solve_after_rebuild_ms"] for r in rows]))
+    return {"workload": f"3d-64^3-7pt at s={sh}: adaptive SPAI (eps 1e-4, 5 steps x 5 columns) at p_1, "
+                        f"update vs rebuild at {nparams} further p, block GMRES({w.restart}) 8 RHS, FP64",
+            "build_ms": t_base, "nnz_per_column": nnz_p / n, "update_ms": upd, "rebuild_ms": reb,
+            "update_saving": 1.0 - upd / reb, "update_plus_solve_ms": tot_u, "rebuild_plus_solve_ms": tot_r,
+            "update_plus_solve_saving": 1.0 - tot_u / tot_r, "per_parameter": rows}
+
+
 # ------------------------------------------------------------------------------- large
 def run_large(args, sg, torch):
     """3D side^3 27-point workload (side 128: n = 2,097,152, 27 nnz per column, 16 RHS):
@@ -1126,6 +1190,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_mixed:
         bvs = run_block_vs_single(sg, torch, ctx, w)
         order = run_update_order(sg, torch, ctx, w)
+    adaptive = None
+    if rank == 0 and world == 1 and not args.no_adaptive:
+        adaptive = run_adaptive(sg, torch, ctx, w)
     # many small systems: batched build and lockstep solves
     batched = None
     if rank == 0 and world == 1 and not args.no_batched:
@@ -1168,7 +1235,7 @@ def main():
                                             "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                                             "workers": args.workers},
             "roofline": roofline, "roofline_isolated": roofline_iso, "mixed_precision": mixed,
-            "warm_start": warm, "block_vs_single_rhs": bvs, "update_order": order,
+            "warm_start": warm, "block_vs_single_rhs": bvs, "update_order": order, "adaptive": adaptive,
             "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "large": large, "batched": batched, "gpu_launches": int(launches),
             "clocks": clk, "fp64_tflops_measured": fp64_tflops,
             "gmres_iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)),
