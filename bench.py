@@ -50,8 +50,9 @@ def parse():
     ap.add_argument("--workers", type=int, default=4)
     # single-kernel case (for profiler captures): H = V^T W or W -= V H at n = side^3, s = 8
     ap.add_argument("--kernel", default=None, choices=["dot", "update", "columns"])
-    ap.add_argument("--columns-workload", default="batched2d", choices=["batched2d", "sweep3d"],
-                    help="--kernel columns: the batched 2D systems (FP32) or one FP64 SPAI of the 3D sweep")
+    ap.add_argument("--columns-workload", default="batched2d", choices=["batched2d", "sweep3d", "adaptive3d"],
+                    help="--kernel columns: the batched 2D systems (FP32), one FP64 SPAI of the 3D sweep, "
+                         "or one adaptive SPAI of the 3D sweep's matrix (--side sets the grid)")
     ap.add_argument("--nblk", type=int, default=16)
     ap.add_argument("--orth", default="tensor", choices=["tensor", "fp64"])
     # serving: Poisson arrivals over a pool of 16 3D 7-point grids (sides 24-96)
@@ -217,7 +218,7 @@ def run_columns_case(args):
     import torch
     import synth
     import paper_1809_06574_gb300 as sg
-    if args.columns_workload == "sweep3d":  # one FP64 SPAI (pattern of A) of the sweep's first system
+    if args.columns_workload in ("sweep3d", "adaptive3d"):  # one SPAI of the sweep's first system
         ws = [synth.grid3d_7pt(side=args.side, nparams=args.nparams)]
         kinds = [sg.PATTERN_A]
         shifts = [ws[0].shifts[0]]
@@ -238,6 +239,9 @@ def run_columns_case(args):
         keep.append((aff, va, terms))
 
     def once():
+        if args.columns_workload == "adaptive3d":
+            sg.spai_pc_destroy(sg.spai_build_adaptive(ctx, As[0])[0])
+            return
         if len(As) == 1:
             sg.spai_pc_destroy(sg.spai_build(ctx, As[0], kinds[0])[0])
             return

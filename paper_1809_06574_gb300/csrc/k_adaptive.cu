@@ -7,8 +7,8 @@
 //      QR of the tile in shared memory (lanes own rows), back substitution;
 //   2. r = e_k - sum_c A(:, J_c) m_c (column by column) on I_k and ||r||^2; stop when
 //      ||r||_2 <= eps, after max_steps additions, or on a rank-deficient tile;
-//   3. candidates: columns j not in J_k with a nonzero in a row of I_k (CSR rows of A),
-//      gathered, sorted (bitonic) and de-duplicated in shared memory;
+//   3. candidates: columns j not in J_k with a nonzero in a row of I_k -- the sorted union
+//      of A's CSR rows of I_k (a warp-wide merge, 4 rows per lane), at most 1024;
 //      rho_j = ||r||^2 - (r . A(:,j))^2 / ||A(:,j)||^2 for each (A's column in CSC order);
 //   4. the <= max_new candidates of smallest rho_j among those not above the candidates'
 //      mean, both compared as floor(rho / ||r||^2 * 2^30) (ties: lower column index), join
@@ -27,7 +27,7 @@ namespace {
 
 constexpr int kAMJ = 32;     // columns of J_k
 constexpr int kAMI = 128;    // rows of I_k
-constexpr int kAMC = 1024;   // candidate entries (with repeats) of one step
+constexpr int kAMC = 1024;   // distinct candidates of one step
 constexpr int kKeyBits = 30;
 
 // per-warp shared memory
@@ -40,7 +40,7 @@ constexpr int kOffJ = kOffRd + kAMJ * 8;                   // kAMJ ints
 constexpr int kOffI = kOffJ + kAMJ * 4;                    // kAMI ints
 constexpr int kOffNJ = kOffI + kAMI * 4;                   // kAMJ ints (next J)
 constexpr int kOffC = kOffNJ + kAMJ * 4;                   // kAMC ints (candidates; next I)
-constexpr int kOffCnt = kOffC + kAMC * 4;                  // counters
+constexpr int kOffCnt = kOffC + kAMC * 4;                  // (spare)
 constexpr int kAdaptiveSmem = kOffCnt + 16;
 static_assert(kAMI * kAMJ * 8 >= kAMC * 8, "keys fit the tile");
 
@@ -123,7 +123,6 @@ __global__ void __launch_bounds__(32) k_adaptive_pattern(AdaptiveProblem ap)
     int32_t *Il = reinterpret_cast<int32_t *>(sm + kOffI);
     int32_t *nJl = reinterpret_cast<int32_t *>(sm + kOffNJ);
     int32_t *cand = reinterpret_cast<int32_t *>(sm + kOffC);
-    int *ccount = reinterpret_cast<int *>(sm + kOffCnt);
     const int lane = threadIdx.x;
     const int max_cols = 1 + ap.max_steps * ap.max_new;
 
@@ -212,61 +211,45 @@ __global__ void __launch_bounds__(32) k_adaptive_pattern(AdaptiveProblem ap)
             rr = warp_sum(rr);
             if (sqrt(rr) <= ap.eps || step == ap.max_steps || nj >= max_cols || !(rr > 0.0)) break;
 
-            // ---- candidates: columns of A's rows in I_k, not in J_k
-            if (lane == 0) *ccount = 0;
-            __syncwarp();
-            for (int i = lane; i < ni; i += 32) {
-                const int32_t l = Il[i];
-                const int32_t q1 = __ldg(ap.rowptr + l + 1);
-                for (int32_t q = __ldg(ap.rowptr + l); q < q1; ++q) {
-                    const int32_t j = __ldg(ap.colind + q);
-                    if (bsearch_list(Jl, nj, j) >= 0) continue;
-                    const int at = atomicAdd(ccount, 1);
-                    if (at < kAMC) cand[at] = j;
+            // ---- candidates: the sorted union of A's CSR rows of I_k without J_k (a warp-wide
+            // merge of the row lists, 4 rows per lane; each distinct column comes out once)
+            int32_t cpos[4], cend[4], chead[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = lane + 32 * u;
+                cpos[u] = cend[u] = 0;
+                chead[u] = INT_MAX;
+                if (i < ni) {
+                    const int32_t l = Il[i];
+                    cpos[u] = __ldg(ap.rowptr + l);
+                    cend[u] = __ldg(ap.rowptr + l + 1);
+                    if (cpos[u] < cend[u]) chead[u] = __ldg(ap.colind + cpos[u]);
+                }
+            }
+            int nc = 0;
+            while (true) {
+                int32_t lo = chead[0];
+#pragma unroll
+                for (int u = 1; u < 4; ++u) lo = min(lo, chead[u]);
+                const int32_t mcol = __reduce_min_sync(0xffffffffu, lo);
+                if (mcol == INT_MAX) break;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (chead[u] == mcol) {
+                        ++cpos[u];
+                        chead[u] = cpos[u] < cend[u] ? __ldg(ap.colind + cpos[u]) : INT_MAX;
+                    }
+                if (bsearch_list(Jl, nj, mcol) < 0) {
+                    if (lane == 0 && nc < kAMC) cand[nc] = mcol;
+                    ++nc;
                 }
             }
             __syncwarp();
-            const int raw = *ccount;
-            if (raw > kAMC) {  // more candidate entries than the buffer holds: stop growing
+            if (nc > kAMC) {  // more candidates than the buffer holds: stop growing
                 if (lane == 0) atomicOr(ap.d_err, ERR_TOO_WIDE);
                 break;
             }
-            if (raw == 0) break;
-            int P = 32;
-            while (P < raw) P <<= 1;
-            for (int i = raw + lane; i < P; i += 32) cand[i] = INT_MAX;
-            __syncwarp();
-            for (int kb = 2; kb <= P; kb <<= 1) {  // bitonic sort, ascending
-                for (int jb = kb >> 1; jb > 0; jb >>= 1) {
-                    for (int i = lane; i < P; i += 32) {
-                        const int p = i ^ jb;
-                        if (p > i) {
-                            const int32_t a = cand[i], b = cand[p];
-                            const bool up = (i & kb) == 0;
-                            if ((a > b) == up) {
-                                cand[i] = b;
-                                cand[p] = a;
-                            }
-                        }
-                    }
-                    __syncwarp();
-                }
-            }
-            int nc = 0;  // de-duplicate in place (writes never pass the reads of later chunks)
-            int32_t prev_last = INT_MIN;
-            for (int base = 0; base < raw; base += 32) {
-                const int i = base + lane;
-                const int32_t v = i < raw ? cand[i] : INT_MAX;
-                int32_t pv = __shfl_up_sync(0xffffffffu, v, 1);
-                if (lane == 0) pv = prev_last;
-                prev_last = __shfl_sync(0xffffffffu, v, 31);
-                const bool keep = i < raw && v != pv;
-                const unsigned bal = __ballot_sync(0xffffffffu, keep);
-                __syncwarp();
-                if (keep) cand[nc + __popc(bal & ((1u << lane) - 1u))] = v;
-                nc += __popc(bal);
-                __syncwarp();
-            }
+            if (nc == 0) break;
             // ---- improvements rho_j, their mean, and the keys (in the tile's space)
             double psum = 0.0;
             for (int e = lane; e < nc; e += 32) {
