@@ -2,9 +2,11 @@
 // Sec. 3, around the column least squares of Sec. 2.2).
 //
 // One warp per column k, persistent over the columns.  Starting from J_k = {k}:
-//   1. I_k = {k} and the rows of the columns in J_k (a warp-wide merge of the sorted
-//      column lists, one list per lane); m = argmin ||e_k - A(I_k, J_k) m||_2 by Householder
-//      QR of the tile in shared memory (lanes own rows), back substitution;
+//   1. I_k = {k} and the rows of the columns in J_k; m = argmin ||e_k - A(I_k, J_k) m||_2
+//      by Householder QR of the tile in shared memory (lanes own rows), back substitution.
+//      The QR is incremental: tile rows and columns are kept in the order they joined, the
+//      columns of earlier steps are zero in the rows added later, so their reflectors stay
+//      valid and a step only applies them to the new columns and factors those;
 //   2. r = e_k - sum_c A(:, J_c) m_c (column by column) on I_k and ||r||^2; stop when
 //      ||r||_2 <= eps, after max_steps additions, or on a rank-deficient tile;
 //   3. candidates: columns j not in J_k with a nonzero in a row of I_k -- the sorted union
@@ -30,19 +32,15 @@ constexpr int kAMI = 128;    // rows of I_k
 constexpr int kAMC = 1024;   // distinct candidates of one step
 constexpr int kKeyBits = 30;
 
-// per-warp shared memory
-constexpr int kOffAh = 0;                                  // kAMI x kAMJ doubles; reused for keys
-constexpr int kOffRhs = kOffAh + kAMI * kAMJ * 8;          // kAMI doubles
-constexpr int kOffR = kOffRhs + kAMI * 8;                  // kAMI doubles
-constexpr int kOffM = kOffR + kAMI * 8;                    // kAMJ doubles
-constexpr int kOffRd = kOffM + kAMJ * 8;                   // kAMJ doubles
-constexpr int kOffJ = kOffRd + kAMJ * 8;                   // kAMJ ints
-constexpr int kOffI = kOffJ + kAMJ * 4;                    // kAMI ints
-constexpr int kOffNJ = kOffI + kAMI * 4;                   // kAMJ ints (next J)
-constexpr int kOffC = kOffNJ + kAMJ * 4;                   // kAMC ints (candidates; next I)
-constexpr int kOffCnt = kOffC + kAMC * 4;                  // (spare)
-constexpr int kAdaptiveSmem = kOffCnt + 16;
-static_assert(kAMI * kAMJ * 8 >= kAMC * 8, "keys fit the tile");
+// per-warp shared memory, sized from the options: ld = max_rows, mc = 1 + max_steps * max_new
+//   Ah[ld * mc] tile (tile rows and columns in insertion order), rhs[ld] (Q^T e_k so far),
+//   r[ld], m[32], rd[32], invv[32], ck[kAMC] (candidates; then (key << 32) | column),
+//   Jl[32] (J sorted), Jt[32] (tile column -> column), nJl[32] (scratch),
+//   It[128] (tile row -> row), Is[128] (rows sorted), Ip[128] (sorted -> tile row), newR[128]
+__host__ __device__ constexpr int adaptive_smem(int ld, int mc)
+{
+    return 8 * (ld * mc + 2 * ld + 3 * kAMJ) + 8 * kAMC + 4 * (3 * kAMJ + 4 * kAMI);
+}
 
 __device__ __forceinline__ int bsearch_list(const int32_t *a, int len, int32_t key)
 {
@@ -110,75 +108,114 @@ __device__ int union_rows(const AdaptiveProblem &ap, const int32_t *J, int nj, i
     return cnt;
 }
 
+// tile row of row `row`, or -1
+__device__ __forceinline__ int tile_row(const int32_t *Is, const int32_t *Ip, int ni, int32_t row)
+{
+    const int i = bsearch_list(Is, ni, row);
+    return i < 0 ? -1 : Ip[i];
+}
+
+// Householder reflector of tile column c over tile rows c .. ni-1 (the QR is incremental:
+// columns factored in earlier steps keep their reflectors, stored below the diagonal with
+// v's first entry on it, 2 / v^T v in invv[c] and R's diagonal in rd[c]); false if the
+// column is zero there.  The caller applies it.
+__device__ __forceinline__ bool make_reflector(double *vc, int c, int ni, double *invv, double *rd, int lane)
+{
+    __syncwarp();  // the column's entries were last written by other lanes
+    double ss = 0.0;
+    for (int i = c + lane; i < ni; i += 32) ss = fma(vc[i], vc[i], ss);
+    ss = warp_sum(ss);
+    const double alpha = sqrt(ss);
+    if (!(alpha > 0.0)) return false;
+    const double xc = vc[c];
+    const double sgn = xc >= 0.0 ? 1.0 : -1.0;
+    __syncwarp();
+    if (lane == 0) {
+        vc[c] = xc + sgn * alpha;
+        rd[c] = -sgn * alpha;
+        invv[c] = 1.0 / (alpha * (alpha + fabs(xc)));
+    }
+    __syncwarp();
+    return true;
+}
+
+// col -= (2 v v^T / v^T v) col over tile rows c .. ni-1
+__device__ __forceinline__ void apply_reflector(const double *vc, double inv, int c, int ni, double *col, int lane)
+{
+    double d = 0.0;
+    for (int i = c + lane; i < ni; i += 32) d = fma(vc[i], col[i], d);
+    const double g = warp_sum(d) * inv;
+    for (int i = c + lane; i < ni; i += 32) col[i] = fma(-g, vc[i], col[i]);
+}
+
+// gathers column j of A into tile column `col` (rows already zero)
+__device__ __forceinline__ void gather_column(const AdaptiveProblem &ap, int32_t j, double *col, const int32_t *Is,
+                                              const int32_t *Ip, int ni, int lane)
+{
+    const int32_t q1 = __ldg(ap.colptr + j + 1);
+    for (int32_t q = __ldg(ap.colptr + j) + lane; q < q1; q += 32) {
+        const int t = tile_row(Is, Ip, ni, __ldg(ap.rowind + q));
+        if (t >= 0) col[t] = __ldg(ap.cval + q);
+    }
+}
+
 __global__ void __launch_bounds__(32) k_adaptive_pattern(AdaptiveProblem ap)
 {
     extern __shared__ __align__(16) char sm[];
-    double *Ah = reinterpret_cast<double *>(sm + kOffAh);
-    long long *keys = reinterpret_cast<long long *>(sm + kOffAh);
-    double *rhs = reinterpret_cast<double *>(sm + kOffRhs);
-    double *r = reinterpret_cast<double *>(sm + kOffR);
-    double *m = reinterpret_cast<double *>(sm + kOffM);
-    double *rd = reinterpret_cast<double *>(sm + kOffRd);
-    int32_t *Jl = reinterpret_cast<int32_t *>(sm + kOffJ);
-    int32_t *Il = reinterpret_cast<int32_t *>(sm + kOffI);
-    int32_t *nJl = reinterpret_cast<int32_t *>(sm + kOffNJ);
-    int32_t *cand = reinterpret_cast<int32_t *>(sm + kOffC);
+    const int ld = ap.max_rows, mc = 1 + ap.max_steps * ap.max_new;
+    double *Ah = reinterpret_cast<double *>(sm);
+    double *rhs = Ah + ld * mc;
+    double *r = rhs + ld;
+    double *m = r + ld;
+    double *rd = m + kAMJ;
+    double *invv = rd + kAMJ;
+    long long *ck = reinterpret_cast<long long *>(invv + kAMJ);
+    int32_t *Jl = reinterpret_cast<int32_t *>(ck + kAMC);
+    int32_t *Jt = Jl + kAMJ;
+    int32_t *nJl = Jt + kAMJ;
+    int32_t *It = nJl + kAMJ;
+    int32_t *Is = It + kAMI;
+    int32_t *Ip = Is + kAMI;
+    int32_t *newR = Ip + kAMI;
     const int lane = threadIdx.x;
-    const int max_cols = 1 + ap.max_steps * ap.max_new;
 
     for (int64_t kk = blockIdx.x; kk < ap.n; kk += gridDim.x) {
         const int32_t k = (int32_t)kk;
-        int nj = 1;
-        if (lane == 0) Jl[0] = k;
+        int nj = 1, ndone = 0;
+        if (lane == 0) Jl[0] = Jt[0] = k;
         __syncwarp();
-        int ni = union_rows(ap, Jl, nj, k, Il, kAMI, lane);
-        if (ni > ap.max_rows) {  // even {k} is too tall: keep it
+        int ni = union_rows(ap, Jl, 1, k, Is, kAMI, lane);
+        if (ni > ld) {  // even {k} is too tall: keep it
             if (lane == 0) atomicOr(ap.d_err, ERR_TOO_WIDE);
-        }
-        for (int step = 0; step <= ap.max_steps && ni <= ap.max_rows; ++step) {
-            // ---- tile A(I, J) and e_k
-            for (int e = lane; e < nj * kAMI; e += 32) Ah[e] = 0.0;
-            for (int i = lane; i < ni; i += 32) rhs[i] = (Il[i] == k) ? 1.0 : 0.0;
-            __syncwarp();
-            for (int c = 0; c < nj; ++c) {
-                const int32_t j = Jl[c];
-                const int32_t q1 = __ldg(ap.colptr + j + 1);
-                for (int32_t q = __ldg(ap.colptr + j) + lane; q < q1; q += 32) {
-                    const int i = bsearch_list(Il, ni, __ldg(ap.rowind + q));
-                    if (i >= 0) Ah[c * kAMI + i] = __ldg(ap.cval + q);
-                }
+        } else {
+            for (int i = lane; i < ni; i += 32) {
+                It[i] = Is[i];
+                Ip[i] = i;
+                Ah[i] = 0.0;
+                rhs[i] = Is[i] == k ? 1.0 : 0.0;
             }
             __syncwarp();
-            // ---- Householder QR (rows over lanes) applied to e_k as it goes
+            gather_column(ap, k, Ah, Is, Ip, ni, lane);
+            __syncwarp();
+        }
+        for (int step = 0; step <= ap.max_steps && ni <= ld; ++step) {
+            // ---- factor the columns added since the last step: earlier reflectors first
             bool singular = ni < nj;
-            for (int c = 0; c < nj && !singular; ++c) {
-                double *vc = Ah + c * kAMI;
-                double ss = 0.0;
-                for (int i = c + lane; i < ni; i += 32) ss = fma(vc[i], vc[i], ss);
-                ss = warp_sum(ss);
-                const double alpha = sqrt(ss);
-                if (!(alpha > 0.0)) {
+            for (int c = 0; c < ndone && !singular; ++c)
+                for (int t = ndone; t < nj; ++t) apply_reflector(Ah + c * ld, invv[c], c, ni, Ah + t * ld, lane);
+            __syncwarp();
+            for (int c = ndone; c < nj && !singular; ++c) {
+                double *vc = Ah + c * ld;
+                if (!make_reflector(vc, c, ni, invv, rd, lane)) {
                     singular = true;
                     break;
                 }
-                const double xc = vc[c];
-                const double sgn = xc >= 0.0 ? 1.0 : -1.0;
-                const double inv = 1.0 / (alpha * (alpha + fabs(xc)));
-                __syncwarp();
-                if (lane == 0) {
-                    vc[c] = xc + sgn * alpha;
-                    rd[c] = -sgn * alpha;
-                }
-                __syncwarp();
-                for (int t = c + 1; t <= nj; ++t) {
-                    double *col = t < nj ? Ah + t * kAMI : rhs;
-                    double d = 0.0;
-                    for (int i = c + lane; i < ni; i += 32) d = fma(vc[i], col[i], d);
-                    const double g = warp_sum(d) * inv;
-                    for (int i = c + lane; i < ni; i += 32) col[i] = fma(-g, vc[i], col[i]);
-                }
+                const double inv = invv[c];
+                for (int t = c + 1; t < nj; ++t) apply_reflector(vc, inv, c, ni, Ah + t * ld, lane);
+                apply_reflector(vc, inv, c, ni, rhs, lane);
                 __syncwarp();
             }
+            ndone = nj;
             if (!singular) {
                 double rmax = 0.0;
                 for (int c = 0; c < nj; ++c) rmax = fmax(rmax, fabs(rd[c]));
@@ -186,30 +223,30 @@ __global__ void __launch_bounds__(32) k_adaptive_pattern(AdaptiveProblem ap)
                     if (fabs(rd[c]) <= 1e-14 * rmax) singular = true;
             }
             if (singular) break;  // J_k stays as it is; the final build reports the column
-            for (int c = nj - 1; c >= 0; --c) {  // R m = (Q^T e_k)(0:nj)
+            for (int c = nj - 1; c >= 0; --c) {  // R m = (Q^T e_k)(0:nj), tile column order
                 double acc = 0.0;
-                for (int t = c + 1 + lane; t < nj; t += 32) acc = fma(Ah[t * kAMI + c], m[t], acc);
+                for (int t = c + 1 + lane; t < nj; t += 32) acc = fma(Ah[t * ld + c], m[t], acc);
                 acc = warp_sum(acc);
                 if (lane == 0) m[c] = (rhs[c] - acc) / rd[c];
                 __syncwarp();
             }
-            // ---- residual on I_k, column by column
-            for (int i = lane; i < ni; i += 32) r[i] = (Il[i] == k) ? 1.0 : 0.0;
+            // ---- residual on I_k (tile rows), column by column
+            for (int i = lane; i < ni; i += 32) r[i] = It[i] == k ? 1.0 : 0.0;
             __syncwarp();
             for (int c = 0; c < nj; ++c) {
-                const int32_t j = Jl[c];
-                const double mc = m[c];
+                const int32_t j = Jt[c];
+                const double mcv = m[c];
                 const int32_t q1 = __ldg(ap.colptr + j + 1);
                 for (int32_t q = __ldg(ap.colptr + j) + lane; q < q1; q += 32) {
-                    const int i = bsearch_list(Il, ni, __ldg(ap.rowind + q));
-                    if (i >= 0) r[i] = r[i] - __ldg(ap.cval + q) * mc;
+                    const int t = tile_row(Is, Ip, ni, __ldg(ap.rowind + q));
+                    if (t >= 0) r[t] = r[t] - __ldg(ap.cval + q) * mcv;
                 }
                 __syncwarp();
             }
             double rr = 0.0;
             for (int i = lane; i < ni; i += 32) rr = fma(r[i], r[i], rr);
             rr = warp_sum(rr);
-            if (sqrt(rr) <= ap.eps || step == ap.max_steps || nj >= max_cols || !(rr > 0.0)) break;
+            if (sqrt(rr) <= ap.eps || step == ap.max_steps || nj >= mc || !(rr > 0.0)) break;
 
             // ---- candidates: the sorted union of A's CSR rows of I_k without J_k (a warp-wide
             // merge of the row lists, 4 rows per lane; each distinct column comes out once)
@@ -220,7 +257,7 @@ __global__ void __launch_bounds__(32) k_adaptive_pattern(AdaptiveProblem ap)
                 cpos[u] = cend[u] = 0;
                 chead[u] = INT_MAX;
                 if (i < ni) {
-                    const int32_t l = Il[i];
+                    const int32_t l = It[i];
                     cpos[u] = __ldg(ap.rowptr + l);
                     cend[u] = __ldg(ap.rowptr + l + 1);
                     if (cpos[u] < cend[u]) chead[u] = __ldg(ap.colind + cpos[u]);
@@ -240,7 +277,7 @@ __global__ void __launch_bounds__(32) k_adaptive_pattern(AdaptiveProblem ap)
                         chead[u] = cpos[u] < cend[u] ? __ldg(ap.colind + cpos[u]) : INT_MAX;
                     }
                 if (bsearch_list(Jl, nj, mcol) < 0) {
-                    if (lane == 0 && nc < kAMC) cand[nc] = mcol;
+                    if (lane == 0 && nc < kAMC) ck[nc] = mcol;
                     ++nc;
                 }
             }
@@ -250,62 +287,120 @@ __global__ void __launch_bounds__(32) k_adaptive_pattern(AdaptiveProblem ap)
                 break;
             }
             if (nc == 0) break;
-            // ---- improvements rho_j, their mean, and the keys (in the tile's space)
+            // ---- improvements rho_j, their mean, and the keys (key << 32 | column)
             double psum = 0.0;
             for (int e = lane; e < nc; e += 32) {
-                const int32_t j = cand[e];
+                const int32_t j = (int32_t)ck[e];
                 double dot = 0.0;
                 const int32_t q1 = __ldg(ap.colptr + j + 1);
                 for (int32_t q = __ldg(ap.colptr + j); q < q1; ++q) {
-                    const int i = bsearch_list(Il, ni, __ldg(ap.rowind + q));
-                    if (i >= 0) dot = dot + r[i] * __ldg(ap.cval + q);
+                    const int t = tile_row(Is, Ip, ni, __ldg(ap.rowind + q));
+                    if (t >= 0) dot = dot + r[t] * __ldg(ap.cval + q);
                 }
                 const double cn = __ldg(ap.colnorm2 + j);
                 const double rho = cn == 0.0 ? rr : rr - dot * dot / cn;
-                keys[e] = adaptive_key(rho, rr);
+                ck[e] = (adaptive_key(rho, rr) << 32) | (long long)j;
                 psum += rho;
             }
             const double mean = warp_sum(psum) / (double)nc;
             const long long kmean = adaptive_key(mean, rr);
             __syncwarp();
             for (int e = lane; e < nc; e += 32)
-                keys[e] = keys[e] <= kmean ? ((keys[e] << 32) | (long long)cand[e]) : LLONG_MAX;
+                if ((ck[e] >> 32) > kmean) ck[e] = LLONG_MAX;
             __syncwarp();
             // ---- the max_new smallest (key, column)
             int nsel = 0;
-            for (int t = 0; t < ap.max_new && nj + nsel < max_cols; ++t) {
+            for (int t = 0; t < ap.max_new && nj + nsel < mc; ++t) {
                 long long best = LLONG_MAX;
-                for (int e = lane; e < nc; e += 32) best = keys[e] < best ? keys[e] : best;
+                for (int e = lane; e < nc; e += 32) best = ck[e] < best ? ck[e] : best;
                 best = warp_min_ll(best);
                 if (best == LLONG_MAX) break;
-                const int32_t j = (int32_t)(best & 0xffffffffll);
                 for (int e = lane; e < nc; e += 32)
-                    if (keys[e] == best) keys[e] = LLONG_MAX;
-                if (lane == 0) nJl[kAMJ - 1 - nsel] = j;  // chosen columns, kept at the end
+                    if (ck[e] == best) ck[e] = LLONG_MAX;
+                if (lane == 0) nJl[nsel] = (int32_t)(best & 0xffffffffll);
                 ++nsel;
                 __syncwarp();
             }
             if (nsel == 0) break;
-            if (lane == 0) {  // merge J and the chosen columns into nJl[0 .. nj + nsel)
-                int32_t ch[kAMJ];
-                for (int t = 0; t < nsel; ++t) ch[t] = nJl[kAMJ - 1 - t];
-                for (int a = 1; a < nsel; ++a)  // insertion sort of <= 5 values
-                    for (int b = a; b > 0 && ch[b - 1] > ch[b]; --b) {
-                        const int32_t x = ch[b];
-                        ch[b] = ch[b - 1];
-                        ch[b - 1] = x;
+            // chosen columns ascending (insertion sort of <= 31 values)
+            if (lane == 0)
+                for (int a = 1; a < nsel; ++a)
+                    for (int b = a; b > 0 && nJl[b - 1] > nJl[b]; --b) {
+                        const int32_t x = nJl[b];
+                        nJl[b] = nJl[b - 1];
+                        nJl[b - 1] = x;
                     }
-                int a = 0, b = 0, o = 0;
-                while (a < nj || b < nsel) nJl[o++] = (b >= nsel || (a < nj && Jl[a] < ch[b])) ? Jl[a++] : ch[b++];
+            __syncwarp();
+            // ---- rows the chosen columns add (sorted union of their lists, minus I_k)
+            int nnew = 0;
+            {
+                int32_t pos = 0, end = 0, head = INT_MAX;
+                if (lane < nsel) {
+                    const int32_t j = nJl[lane];
+                    pos = __ldg(ap.colptr + j);
+                    end = __ldg(ap.colptr + j + 1);
+                    if (pos < end) head = __ldg(ap.rowind + pos);
+                }
+                while (true) {
+                    const int32_t mrow = __reduce_min_sync(0xffffffffu, head);
+                    if (mrow == INT_MAX) break;
+                    if (head == mrow) {
+                        ++pos;
+                        head = pos < end ? __ldg(ap.rowind + pos) : INT_MAX;
+                    }
+                    if (bsearch_list(Is, ni, mrow) < 0) {
+                        if (lane == 0 && nnew < kAMI) newR[nnew] = mrow;
+                        ++nnew;
+                    }
+                }
+                __syncwarp();
+            }
+            if (ni + nnew > ld) break;  // the step is undone: J_k, I_k stay
+            // ---- commit: new rows (appended), new columns (appended), sorted views
+            const int nni = ni + nnew;
+            for (int i = lane; i < nnew; i += 32) {
+                It[ni + i] = newR[i];
+                rhs[ni + i] = 0.0;
+            }
+            for (int c = 0; c < nj; ++c)
+                for (int i = ni + lane; i < nni; i += 32) Ah[c * ld + i] = 0.0;
+            if (lane == 0) {
+                // merge the sorted rows with the sorted new rows, from the end (in place)
+                int a = ni - 1, b = nnew - 1, o = nni - 1;
+                while (b >= 0) {
+                    if (a >= 0 && Is[a] > newR[b]) {
+                        Is[o] = Is[a];
+                        Ip[o] = Ip[a];
+                        --a;
+                    } else {
+                        Is[o] = newR[b];
+                        Ip[o] = ni + b;
+                        --b;
+                    }
+                    --o;
+                }
+                // J sorted: merge with the chosen columns (from the end); tile columns appended
+                a = nj - 1;
+                b = nsel - 1;
+                o = nj + nsel - 1;
+                while (b >= 0) {
+                    if (a >= 0 && Jl[a] > nJl[b]) {
+                        Jl[o--] = Jl[a--];
+                    } else {
+                        Jl[o--] = nJl[b--];
+                    }
+                }
+                for (int t = 0; t < nsel; ++t) Jt[nj + t] = nJl[t];
             }
             __syncwarp();
-            const int nnj = nj + nsel;
-            const int nni = union_rows(ap, nJl, nnj, k, cand, kAMI, lane);
-            if (nni > ap.max_rows) break;  // the step is undone: J_k, I_k stay
-            for (int c = lane; c < nnj; c += 32) Jl[c] = nJl[c];
-            for (int i = lane; i < nni; i += 32) Il[i] = cand[i];
+            for (int t = 0; t < nsel; ++t) {
+                double *col = Ah + (nj + t) * ld;
+                for (int i = lane; i < nni; i += 32) col[i] = 0.0;
+                __syncwarp();
+                gather_column(ap, nJl[t], col, Is, Ip, nni, lane);
+            }
             __syncwarp();
-            nj = nnj;
+            nj += nsel;
             ni = nni;
         }
         for (int c = lane; c < nj; c += 32) ap.out_J[kk * kAMJ + c] = Jl[c];
@@ -341,17 +436,19 @@ int adaptive_max_rows() { return kAMI; }
 int launch_adaptive_pattern(cudaStream_t st, const AdaptiveProblem &ap)
 {
     if (ap.n <= 0) return 0;
-    if (cudaFuncSetAttribute(k_adaptive_pattern, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdaptiveSmem) !=
-        cudaSuccess)
+    const int mc = 1 + ap.max_steps * ap.max_new;
+    if (ap.max_rows < 1 || ap.max_rows > kAMI || mc > kAMJ || ap.max_new < 1 || ap.max_steps < 0) return -1;
+    const int smem = adaptive_smem(ap.max_rows, mc);
+    if (cudaFuncSetAttribute(k_adaptive_pattern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return -1;
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adaptive_pattern, 32, kAdaptiveSmem) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adaptive_pattern, 32, smem) != cudaSuccess)
         return -1;
     int64_t blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
     if (blocks > ap.n) blocks = ap.n;
-    k_adaptive_pattern<<<(unsigned)blocks, 32, kAdaptiveSmem, st>>>(ap);
+    k_adaptive_pattern<<<(unsigned)blocks, 32, smem, st>>>(ap);
     note_launches(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
