@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(32) k_adaptive_pattern(AdaptiveProblem ap)
                     if (cpos[u] < cend[u]) chead[u] = __ldg(ap.colind + cpos[u]);
                 }
             }
-            int nc = 0;
+            int nc = 0, jp = 0;  // jp walks the sorted J_k alongside the ascending output
             while (true) {
                 int32_t lo = chead[0];
 #pragma unroll
@@ -276,7 +276,8 @@ __global__ void __launch_bounds__(32) k_adaptive_pattern(AdaptiveProblem ap)
                         ++cpos[u];
                         chead[u] = cpos[u] < cend[u] ? __ldg(ap.colind + cpos[u]) : INT_MAX;
                     }
-                if (bsearch_list(Jl, nj, mcol) < 0) {
+                while (jp < nj && Jl[jp] < mcol) ++jp;
+                if (!(jp < nj && Jl[jp] == mcol)) {
                     if (lane == 0 && nc < kAMC) ck[nc] = mcol;
                     ++nc;
                 }
