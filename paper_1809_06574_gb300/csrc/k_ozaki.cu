@@ -175,7 +175,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
     return true;
 }
 
-// a warp's bounded wait on one mbarrier phase; the verdict is the same in every lane
+// a warp's bounded wait on one mbarrier phase; the outcome is the same in every lane
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity)
 {
     return __all_sync(0xffffffffu, mbar_wait_bounded(bar, parity)) != 0;
