@@ -116,3 +116,30 @@ def test_residual_never_grows_and_stops_for_a_reason():
         # always has candidates and stays far below the row cap here)
         if Jptr[k + 1] - Jptr[k] < full and not any(t[0] == k and t[1] == 3 for t in trace):
             assert col[k] <= eps * (1 + 1e-9), k
+
+
+def test_row_limit_undoes_the_step_that_would_exceed_it():
+    """With a tight row limit the growth stops at the last step that kept |I_k| within it:
+    every final pattern's row set fits, and adding the chosen columns of the next traced
+    step would not have (checked against the dense pattern)."""
+    w = synth.grid3d_7pt(side=6, nparams=2, seed=5)
+    n = w.n
+    A = oracle.assemble(w.terms, oracle.coefficients(0.5, 2.0), n)
+    D = _dense(A, n)
+    limit = 30
+    trace = []
+    Jptr, Jind = oracle.spai_adaptive_pattern(A, n, eps=1e-10, max_steps=6, max_new=5, max_rows=limit, trace=trace)
+    last = {}
+    for t in trace:
+        last[t[0]] = t
+    stopped = 0
+    for k in range(n):
+        J = Jind[Jptr[k]:Jptr[k + 1]].tolist()
+        rows = {k} | set(np.nonzero(D[:, J].any(axis=1))[0].tolist())
+        assert len(rows) <= limit
+        t = last.get(k)
+        if t is not None and t[2] == J and t[7]:  # the last traced step chose columns but J did not grow
+            grown = {k} | set(np.nonzero(D[:, sorted(J + t[7])].any(axis=1))[0].tolist())
+            assert len(grown) > limit
+            stopped += 1
+    assert stopped > 0  # the limit binds for some columns in this case
