@@ -96,3 +96,18 @@ def test_column_variant_table_is_host_logic(library):
         sg.spai_column_variant_set(1, 125, 27, code)  # a register tile cannot hold 125 x 27
     sg.spai_column_variant_set(1, 25, 13, 0)
     assert sg.spai_column_variant_get(1, 25, 13) == 0
+
+
+def test_adaptive_defaults_agree():
+    """The adaptive SPAI's documented defaults (tolerance 1e-4, 5 steps of 5 columns, 128
+    rows) are the same in the header, the binding and the oracle."""
+    import inspect
+
+    import oracle
+    import paper_1809_06574_gb300 as sg
+    text = open(HEADER).read()
+    assert "opts NULL: eps 1e-4, max_steps 5, max_new 5,\n * max_rows 128" in text
+    b = inspect.signature(sg.spai_build_adaptive).parameters
+    o = inspect.signature(oracle.spai_adaptive_pattern).parameters
+    for name, val in (("eps", 1e-4), ("max_steps", 5), ("max_new", 5), ("max_rows", 128)):
+        assert b[name].default == val and o[name].default == val, name
