@@ -111,3 +111,14 @@ def test_adaptive_defaults_agree():
     o = inspect.signature(oracle.spai_adaptive_pattern).parameters
     for name, val in (("eps", 1e-4), ("max_steps", 5), ("max_new", 5), ("max_rows", 128)):
         assert b[name].default == val and o[name].default == val, name
+
+
+def test_device_code_never_traps_or_batches_copies():
+    """Device-side failures are reported through the error word and bounded waits, never
+    by trapping; copies are issued one by one (no batched-copy runtime calls)."""
+    csrc = os.path.join(PKG, "csrc")
+    for name in os.listdir(csrc):
+        text = open(os.path.join(csrc, name)).read()
+        assert "__trap" not in text and "trap;" not in text, name
+        assert "assert(" not in text.replace("static_assert(", ""), name
+        assert "BatchAsync" not in text, name
