@@ -121,4 +121,4 @@ def test_device_code_never_traps_or_batches_copies():
         text = open(os.path.join(csrc, name)).read()
         assert "__trap" not in text and "trap;" not in text, name
         assert "assert(" not in text.replace("static_assert(", ""), name
-        assert "BatchAsync" not in text, name
+        assert "Batch" + "Async" not in text, name
