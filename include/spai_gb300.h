@@ -176,6 +176,10 @@ SPAI_API spai_status spai_assemble(spai_ctx ctx, spai_affine aff, const double *
 SPAI_API spai_status spai_affine_export(spai_ctx ctx, spai_affine aff, int32_t *rowptr,
                                         int32_t *colind);
 
+/* Releases the assembly handle and its device arrays (the pattern arrays returned by
+ * spai_affine_pattern become invalid).  The release is stream-ordered on the creating
+ * context's stream: work queued there before the call still sees the arrays; work on
+ * other streams that reads them must be complete first.  SPAI_EINVAL on NULL. */
 SPAI_API spai_status spai_affine_destroy(spai_affine aff);
 
 /* ----------------------------------------------------------------------------------
@@ -301,6 +305,11 @@ SPAI_API spai_status spai_pc_export(spai_ctx ctx, spai_pc pc, int32_t *Jptr, int
  * every update made from it and which is released with the last of them. */
 SPAI_API size_t spai_pc_mem_size(spai_pc pc, int32_t with_analysis);
 
+/* Releases the handle: its factor and matrix values, and its pattern analysis once the
+ * last handle sharing it is gone (for spai_build_batch, the batch's one allocation once
+ * all of its handles and their updates are gone).  Stream-ordered on the creating
+ * context's stream, as spai_affine_destroy.  An update must not be used after its base
+ * is destroyed.  SPAI_EINVAL on NULL. */
 SPAI_API spai_status spai_pc_destroy(spai_pc pc);
 
 /* ----------------------------------------------------------------------------------
