@@ -234,7 +234,7 @@ def run_columns_case(args):
         aff = sg.spai_affine_create(ctx, [sg.csr(w.n, *t) for t in terms])
         _, nnz, rp, ci = sg.spai_affine_pattern(aff)
         va = torch.empty(nnz, dtype=torch.float64, device="cuda")
-        sg.spai_assemble(ctx, aff, sg.affine_coefficients(w.params[0], sh), va)
+        sg.spai_assemble_shifted(ctx, aff, sh, w.params[0], w.alpha, w.beta, va)
         As.append(sg.csr(w.n, rp, ci, va, nnz))
         keep.append((aff, va, terms))
 
@@ -397,7 +397,7 @@ def serve_trace(sg, torch, systems, Bs, trace, **opts):
     is returned to host memory.  Returns the per-request results and the server stats."""
     srv = sg.spai_server_create(**opts)
     try:
-        ids = [sg.spai_server_add_system(srv, [sg.csr(w.n, *t) for t in w.terms]) for w in systems]
+        ids = [sg.spai_server_add_shifted_system(srv, [sg.csr(w.n, *t) for t in w.terms], w.alpha, w.beta) for w in systems]
         tickets = []
         done = []
         import queue as _q
@@ -421,7 +421,7 @@ def serve_trace(sg, torch, systems, Bs, trace, **opts):
                 time.sleep(delay)
             w = systems[sy]
             X = np.empty((w.n, nrhs), order="F")
-            tk = sg.spai_server_submit(srv, ids[sy], nrhs, p, s, sg.affine_coefficients(p, s), Bs[sy], X,
+            tk = sg.spai_server_submit(srv, ids[sy], nrhs, p, s, None, Bs[sy], X,
                                        t_arrival=t0 + ta)
             tickets.append(tk)
             pending.put((tk, X))
@@ -504,7 +504,7 @@ def run_batched(args, sg, torch):
         aff = sg.spai_affine_create(ctx, [sg.csr(w.n, *t) for t in w.terms])
         _, nnz, rp, ci = sg.spai_affine_pattern(aff)
         va = torch.empty(nnz, dtype=torch.float64, device=dev)
-        sg.spai_assemble(ctx, aff, sg.affine_coefficients(w.params[0], 1.0), va)
+        sg.spai_assemble_shifted(ctx, aff, 1.0, w.params[0], w.alpha, w.beta, va)
         B = torch.as_tensor(np.ascontiguousarray(w.B.T), device=dev)
         systems.append({"w": w, "aff": aff, "va": va, "A": sg.csr(w.n, rp, ci, va, nnz), "B": B})
     As = [y["A"] for y in systems]
@@ -594,7 +594,7 @@ def run_block_vs_single(sg, torch, ctx, w, nsys=5):
     vals = [torch.empty(nnz, dtype=torch.float64, device=dev) for _ in range(nsys)]
     As, pcs = [], []
     for i in range(nsys):
-        sg.spai_assemble(ctx, aff, sg.affine_coefficients(w.params[i], 1.0), vals[i])
+        sg.spai_assemble_shifted(ctx, aff, 1.0, w.params[i], w.alpha, w.beta, vals[i])
         As.append(sg.csr(n, rp, ci, vals[i], nnz))
         pcs.append(sg.spai_build(ctx, As[0])[0] if i == 0 else sg.spai_update(ctx, pcs[0], As[i])[0])
     B = torch.as_tensor(np.ascontiguousarray(w.B.T), device=dev)  # (8, n): column c at row c
@@ -650,7 +650,7 @@ def run_update_order(sg, torch, ctx, w, nparams=4):
     for p in ps:
         for sh in ss:
             v = torch.empty(nnz, dtype=torch.float64, device=dev)
-            sg.spai_assemble(ctx, aff, sg.affine_coefficients(p, sh), v)
+            sg.spai_assemble_shifted(ctx, aff, sh, p, w.alpha, w.beta, v)
             vals[(p, sh)] = sg.csr(n, rp, ci, v, nnz)
     B = torch.as_tensor(np.ascontiguousarray(w.B.T), device=dev)
     X = torch.zeros((nr, n), dtype=torch.float64, device=dev)
@@ -703,7 +703,7 @@ def run_adaptive(sg, torch, ctx, w, nparams=3):
     vals = [torch.empty(nnz, dtype=torch.float64, device=dev) for _ in range(nparams + 1)]
     As = []
     for i, v in enumerate(vals):
-        sg.spai_assemble(ctx, aff, sg.affine_coefficients(w.params[i], sh), v)
+        sg.spai_assemble_shifted(ctx, aff, sh, w.params[i], w.alpha, w.beta, v)
         As.append(sg.csr(n, rp, ci, v, nnz))
     B = torch.as_tensor(np.ascontiguousarray(w.B.T), device=dev)
     X = torch.zeros((nr, n), dtype=torch.float64, device=dev)
@@ -791,10 +791,10 @@ def run_large(args, sg, torch):
     sm_aff = sg.spai_affine_create(ctx, [sg.csr(ws.n, *t) for t in sm_terms])
     _, sm_nnz, sm_rp, sm_ci = sg.spai_affine_pattern(sm_aff)
     sm_va = torch.empty(sm_nnz, dtype=torch.float64, device=dev)
-    sg.spai_assemble(ctx, sm_aff, sg.affine_coefficients(ws.params[0], 1.0), sm_va)
+    sg.spai_assemble_shifted(ctx, sm_aff, 1.0, ws.params[0], ws.alpha, ws.beta, sm_va)
     sg.spai_pc_destroy(sg.spai_build(ctx, sg.csr(ws.n, sm_rp, sm_ci, sm_va, sm_nnz), sg.PATTERN_A)[0])
     sg.spai_affine_destroy(sm_aff)
-    sg.spai_assemble(ctx, aff, sg.affine_coefficients(w.params[0], 1.0), va[0])
+    sg.spai_assemble_shifted(ctx, aff, 1.0, w.params[0], w.alpha, w.beta, va[0])
     A1 = sg.csr(n, rp, ci, va[0], nnz)
     pc64, t_b64 = timed(lambda: sg.spai_build(ctx, A1, sg.PATTERN_A)[0])
     sg.spai_pc_destroy(pc64)
@@ -803,7 +803,7 @@ def run_large(args, sg, torch):
     solve(A1, base)  # warm-up of the solve path at this size
     rows = []
     for p in w.params[1:1 + args.large_params]:
-        sg.spai_assemble(ctx, aff, sg.affine_coefficients(p, 1.0), va[1])
+        sg.spai_assemble_shifted(ctx, aff, 1.0, p, w.alpha, w.beta, va[1])
         A = sg.csr(n, rp, ci, va[1], nnz)
         upd, t_u = timed(lambda: sg.spai_update(ctx, base, A, sg.UPDATE_FIRST | sg.PREC_BF16)[0])
         iu, t_su = timed(lambda: solve(A, upd))
@@ -929,7 +929,7 @@ class Sweep:
             if i == 0:
                 A, pc = A0s[si], base
             else:
-                sg.spai_assemble(wk.ctx, self.aff_now, sg.affine_coefficients(w.params[i], s), wk.va)
+                sg.spai_assemble_shifted(wk.ctx, self.aff_now, s, w.params[i], w.alpha, w.beta, wk.va)
                 A = sg.csr(n, rp, ci, wk.va, nnz)
                 pc, _ = sg.spai_update(wk.ctx, base, A, sg.UPDATE_FIRST | self.prec)
             if not (self.warm and si == prev_si):
@@ -966,7 +966,7 @@ class Sweep:
                     for k, wk in enumerate(self.workers)]
         try:
             for si, s in enumerate(w.shifts):
-                sg.spai_assemble(ctx, aff, sg.affine_coefficients(w.params[0], s), self.vb[si])
+                sg.spai_assemble_shifted(ctx, aff, s, w.params[0], w.alpha, w.beta, self.vb[si])
                 A0s[si] = sg.csr(n, rp, ci, self.vb[si], nnz)
                 # returns with the build complete: its handle is then read-only for the workers
                 bases[si] = sg.spai_build(ctx, A0s[si], sg.PATTERN_A | self.prec)[0]

@@ -171,6 +171,24 @@ SPAI_API spai_status spai_affine_pattern(spai_affine aff, int32_t *n, int32_t *n
  * nnz doubles.  Asynchronous. */
 SPAI_API spai_status spai_assemble(spai_ctx ctx, spai_affine aff, const double *coef, double *val_out);
 
+/* Coefficients of the shifted parametric second-order system, Sec. 1.1 Eqs. (3)-(9), with
+ * the Rayleigh damping of the experiments (Sec. 3: D = alpha M + beta K):
+ *   A(p, s) = s^2 M + s D(p) + K(p),  K(p) = K_0 + sum_i p_i K_i,  D(p) = alpha M + beta K(p)
+ * collected over the terms (M, K_0, K_1, ..., K_np):
+ *   coef[0] = s*s + alpha*s,  coef[1] = 1 + beta*s,  coef[1 + i] = (1 + beta*s) * p_i,
+ * each product and sum rounded separately (no fused multiply-add).  p: HOST array of np
+ * parameters (may be NULL when np = 0); coef: HOST array of np + 2 doubles.  0 <= np <= 14.
+ * Host arithmetic only (no context, no device work).  SPAI_EINVAL on bad sizes, NULL
+ * pointers or non-finite inputs. */
+SPAI_API spai_status spai_shifted_coefficients(int32_t np, const double *p, double s, double alpha, double beta,
+                                               double *coef);
+
+/* val_out = A(p, s) on the union pattern of `aff`, whose terms must be (M, K_0, ..., K_np)
+ * (nterms = np + 2, else SPAI_EINVAL): the coefficients of spai_shifted_coefficients, then
+ * spai_assemble.  p: HOST, np doubles.  val_out: device, nnz doubles.  Asynchronous. */
+SPAI_API spai_status spai_assemble_shifted(spai_ctx ctx, spai_affine aff, double s, int32_t np, const double *p,
+                                           double alpha, double beta, double *val_out);
+
 /* Copy the union pattern into caller memory (HOST or DEVICE): rowptr[n+1], colind[nnz].
  * Synchronises the stream. */
 SPAI_API spai_status spai_affine_export(spai_ctx ctx, spai_affine aff, int32_t *rowptr,
@@ -464,7 +482,8 @@ typedef struct {
     double p;              /* parameter value (routing distance) */
     double s;              /* shift (routing key: only builds at exactly this shift are reused) */
     const double *coef;    /* HOST, nterms doubles: A = sum_t coef[t] * term_t; copied at submit.
-                              Requests with equal (system, s, p) must pass equal coefficients */
+                              Requests with equal (system, s, p) must pass equal coefficients.
+                              NULL for a system from spai_server_add_shifted_system: A(p, s) */
     const double *B;       /* HOST or DEVICE, n x nrhs column-major, leading dimension n; read
                               while the request runs, so it must stay valid until it completes */
     double *X;             /* HOST or DEVICE, n x nrhs, leading dimension n: the solution, written
@@ -505,6 +524,14 @@ SPAI_API spai_status spai_server_create(const spai_server_opts *opts, spai_serve
  * beyond).  *id receives its id (0, 1, ...).  Counts
  * against the memory budget (SPAI_ENOMEM if it does not fit).  Synchronises. */
 SPAI_API spai_status spai_server_add_system(spai_server srv, int32_t nterms, const spai_csr *terms, int32_t *id);
+
+/* Register a shifted parametric second-order system (Sec. 1.1 Eqs. (3)-(9), Rayleigh damping
+ * D = alpha M + beta K(p) as in Sec. 3): terms = (M, K_0, K_1), so that a request's p and s
+ * define A(p, s) = (s^2 + alpha s) M + (1 + beta s) (K_0 + p K_1) (spai_shifted_coefficients).
+ * Requests to such a system may pass coef = NULL: the server forms these coefficients from
+ * the request's p and s.  Otherwise as spai_server_add_system. */
+SPAI_API spai_status spai_server_add_shifted_system(spai_server srv, const spai_csr *terms, double alpha, double beta,
+                                                    int32_t *id);
 
 /* Queue a request; *ticket identifies it for spai_server_wait.  Never blocks on the GPU. */
 SPAI_API spai_status spai_server_submit(spai_server srv, const spai_request *req, int64_t *ticket);

@@ -23,7 +23,7 @@ __all__ = [
     "spai_ctx_profile_entry", "spai_affine_create", "spai_affine_pattern",
     "spai_assemble", "spai_affine_export", "spai_affine_destroy", "spai_build", "spai_update", "spai_pc_info",
     "spai_pc_export", "spai_pc_destroy", "spai_build_batch", "block_solve_batch", "spai_spmm", "spai_pc_apply", "block_solve",
-    "affine_coefficients", "PATTERN_A", "PATTERN_A2", "UPDATE_FIRST", "UPDATE_CHAINED", "UPDATE_DIAGONAL", "PREC_FP32", "PREC_BF16",
+    "spai_shifted_coefficients", "spai_assemble_shifted", "spai_server_add_shifted_system", "PATTERN_A", "PATTERN_A2", "UPDATE_FIRST", "UPDATE_CHAINED", "UPDATE_DIAGONAL", "PREC_FP32", "PREC_BF16",
     "LIB_PATH", "spai_ctx_trim", "spai_solve_workspace_size", "spai_pc_mem_size",
     "spai_server_opts", "spai_request", "spai_result", "spai_server_stats", "spai_server_create",
     "spai_server_add_system", "spai_server_submit", "spai_server_wait", "spai_server_clock",
@@ -139,6 +139,8 @@ def lib():
         "spai_affine_create": (i32, [vp, i32, P(spai_csr), P(vp)]),
         "spai_affine_pattern": (i32, [vp, P(i32), P(i32), P(vp), P(vp)]),
         "spai_assemble": (i32, [vp, vp, P(dbl), vp]),
+        "spai_shifted_coefficients": (i32, [i32, P(dbl), dbl, dbl, dbl, P(dbl)]),
+        "spai_assemble_shifted": (i32, [vp, vp, dbl, i32, P(dbl), dbl, dbl, vp]),
         "spai_affine_export": (i32, [vp, vp, vp, vp]),
         "spai_affine_destroy": (i32, [vp]),
         "spai_build": (i32, [vp, P(spai_csr), i32, P(vp)]),
@@ -161,6 +163,7 @@ def lib():
         "spai_pc_mem_size": (sz, [vp, i32]),
         "spai_server_create": (i32, [P(spai_server_opts), P(vp)]),
         "spai_server_add_system": (i32, [vp, i32, P(spai_csr), P(i32)]),
+        "spai_server_add_shifted_system": (i32, [vp, P(spai_csr), dbl, dbl, P(i32)]),
         "spai_server_submit": (i32, [vp, P(spai_request), P(i64)]),
         "spai_server_wait": (i32, [vp, i64, P(spai_result)]),
         "spai_server_clock": (dbl, [vp]),
@@ -266,14 +269,27 @@ def spai_ctx_profile_entry(ctx, i):
 
 
 # ------------------------------------------------------------------ affine assembly
-def affine_coefficients(p: float, s: float):
-    """Coefficients of (M, K0, K1) in A(p, s) = s^2 M + s D(p) + K(p).
+def _params(p):
+    ps = [float(x) for x in p] if hasattr(p, "__len__") else [float(p)]
+    return len(ps), (C.c_double * max(len(ps), 1))(*ps)
 
-    With Rayleigh damping D = 0.05 M + 0.01 K(p) and K(p) = K0 + p K1:
-    A = (s^2 + 0.05 s) M + (1 + 0.01 s) K0 + (1 + 0.01 s) p K1.
-    """
-    c = 1.0 + 0.01 * s
-    return [s * s + 0.05 * s, c, c * p]
+
+def spai_shifted_coefficients(p, s, alpha, beta):
+    """Coefficients of (M, K_0, K_1, ...) in A(p, s) (computed by the library).  p: one
+    parameter or a sequence.  Returns a list of len(p) + 2 floats."""
+    k, pa = _params(p)
+    out = (C.c_double * (k + 2))()
+    st = lib().spai_shifted_coefficients(k, pa, float(s), float(alpha), float(beta), out)
+    if st != SPAI_OK:
+        raise SpaiError(st, "spai_shifted_coefficients: bad parameters")
+    return list(out)
+
+
+def spai_assemble_shifted(ctx, aff, s, p, alpha, beta, val_out):
+    """val_out = A(p, s) of the handle's terms (M, K_0, K_1, ...); p one value or a sequence."""
+    k, pa = _params(p)
+    return _check(ctx, lib().spai_assemble_shifted(ctx, aff, float(s), k, pa, float(alpha), float(beta),
+                                                   _ptr(val_out)))
 
 
 def spai_affine_create(ctx, terms):
@@ -485,12 +501,24 @@ def spai_server_add_system(srv, terms):
     return sid.value
 
 
+def spai_server_add_shifted_system(srv, terms, alpha, beta):
+    """terms: (M, K_0, K_1) as spai_csr; requests may then pass coef=None (A(p, s) formed by
+    the server with damping D = alpha M + beta K(p)).  Returns the system id."""
+    arr = (spai_csr * len(terms))(*terms)
+    if len(terms) != 3:
+        raise SpaiError(SPAI_EINVAL, "a shifted system has the three terms (M, K_0, K_1)")
+    sid = C.c_int32()
+    _server_check(srv, lib().spai_server_add_shifted_system(srv, arr, float(alpha), float(beta), C.byref(sid)))
+    return sid.value
+
+
 def spai_server_submit(srv, system, nrhs, p, s, coef, B, X=None, t_arrival=-1.0):
     """Queue one solve; B / X host or device, n x nrhs column-major (leading dimension n).
-    Returns the ticket.  B (and X) must stay alive until the request completes."""
-    cf = (C.c_double * len(coef))(*[float(c) for c in coef])
-    r = spai_request(int(system), int(nrhs), float(p), float(s), C.cast(cf, C.c_void_p), _ptr(B), _ptr(X),
-                     float(t_arrival))
+    coef=None for a shifted system (the server forms A(p, s)).  Returns the ticket.  B (and
+    X) must stay alive until the request completes."""
+    cf = None if coef is None else (C.c_double * len(coef))(*[float(c) for c in coef])
+    r = spai_request(int(system), int(nrhs), float(p), float(s), C.cast(cf, C.c_void_p) if cf is not None else None,
+                     _ptr(B), _ptr(X), float(t_arrival))
     t = C.c_int64()
     _server_check(srv, lib().spai_server_submit(srv, C.byref(r), C.byref(t)))
     return t.value

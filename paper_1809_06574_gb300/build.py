@@ -21,8 +21,10 @@ LIB = os.path.join(OUT_DIR, "libspai_gb300.so")
 SOURCES = ["k_sparse.cu", "k_spai.cu", "k_krylov.cu", "k_ozaki.cu", "k_adaptive.cu", "spai_api.cu",
            "spai_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", "-I", INCLUDE,
-         "-I", CSRC]
+# host code: no fused multiply-add contraction (gcc contracts by default on aarch64), so
+# host-side arithmetic rounds the same way on every host
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden,-ffp-contract=off", "-I",
+         INCLUDE, "-I", CSRC]
 
 
 def nvcc() -> str:

@@ -956,6 +956,36 @@ extern "C" spai_status spai_assemble(spai_ctx ctx, spai_affine aff, const double
     return SPAI_OK;
 }
 
+// Sec. 1.1 Eqs. (3)-(9) with Rayleigh damping (Sec. 3).  Host code is compiled with
+// -ffp-contract=off, so every product and sum below is rounded on its own on every host.
+extern "C" spai_status spai_shifted_coefficients(int32_t np, const double *p, double s, double alpha, double beta,
+                                                 double *coef)
+{
+    if (np < 0 || np > kMaxTerms - 2 || (np > 0 && !p) || !coef) return SPAI_EINVAL;
+    if (!std::isfinite(s) || !std::isfinite(alpha) || !std::isfinite(beta)) return SPAI_EINVAL;
+    for (int i = 0; i < np; ++i)
+        if (!std::isfinite(p[i])) return SPAI_EINVAL;
+    const double ss = s * s, as = alpha * s, bs = beta * s;
+    const double cK = 1.0 + bs;
+    coef[0] = ss + as;
+    coef[1] = cK;
+    for (int i = 0; i < np; ++i) coef[2 + i] = cK * p[i];
+    return SPAI_OK;
+}
+
+extern "C" spai_status spai_assemble_shifted(spai_ctx ctx, spai_affine aff, double s, int32_t np, const double *p,
+                                             double alpha, double beta, double *val_out)
+{
+    if (!ctx || !aff) return fail(ctx, SPAI_EINVAL, "NULL argument");
+    if (np + 2 != aff->T)
+        return fail(ctx, SPAI_EINVAL, "the affine handle has %d terms; (M, K_0, ..., K_np) needs np + 2 = %d", aff->T,
+                    np + 2);
+    double coef[kMaxTerms];
+    if (spai_shifted_coefficients(np, p, s, alpha, beta, coef))
+        return fail(ctx, SPAI_EINVAL, "shifted coefficients: bad parameters (NULL or non-finite)");
+    return spai_assemble(ctx, aff, coef, val_out);
+}
+
 extern "C" spai_status spai_affine_export(spai_ctx ctx, spai_affine aff, int32_t *rowptr, int32_t *colind)
 {
     if (!ctx || !aff) return fail(ctx, SPAI_EINVAL, "NULL argument");

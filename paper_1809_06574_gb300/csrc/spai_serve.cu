@@ -52,6 +52,8 @@ struct System {
     const int32_t *rowptr = nullptr, *colind = nullptr;
     size_t bytes = 0;        // device bytes of the affine handle
     size_t build_bytes = 0;  // measured bytes of one build with its analysis (0: none yet)
+    bool shifted = false;    // terms (M, K_0, K_1): requests may leave the coefficients to the server
+    double alpha = 0.0, beta = 0.0;  // its Rayleigh damping D = alpha M + beta K(p)
 };
 
 struct Entry {  // a cached SPAI build
@@ -503,10 +505,12 @@ extern "C" spai_status spai_server_create(const spai_server_opts *opts, spai_ser
     return SPAI_OK;
 }
 
-extern "C" spai_status spai_server_add_system(spai_server S, int32_t nterms, const spai_csr *terms, int32_t *id)
+namespace {
+
+spai_status add_system(spai_server S, int32_t nterms, const spai_csr *terms, int32_t *id, const System &proto)
 {
     if (!S || !terms || !id) return SPAI_EINVAL;
-    System y;
+    System y = proto;
     spai_status st = spai_affine_create(S->main_ctx, nterms, terms, &y.aff);
     if (st) {
         std::lock_guard<std::mutex> lk(S->mu);
@@ -544,6 +548,29 @@ extern "C" spai_status spai_server_add_system(spai_server S, int32_t nterms, con
     return SPAI_OK;
 }
 
+}  // namespace
+
+extern "C" spai_status spai_server_add_system(spai_server S, int32_t nterms, const spai_csr *terms, int32_t *id)
+{
+    return add_system(S, nterms, terms, id, System{});
+}
+
+extern "C" spai_status spai_server_add_shifted_system(spai_server S, const spai_csr *terms, double alpha, double beta,
+                                                      int32_t *id)
+{
+    if (!S) return SPAI_EINVAL;
+    if (!std::isfinite(alpha) || !std::isfinite(beta)) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        set_err(S, "add_shifted_system: damping coefficients must be finite");
+        return SPAI_EINVAL;
+    }
+    System proto;
+    proto.shifted = true;
+    proto.alpha = alpha;
+    proto.beta = beta;
+    return add_system(S, 3, terms, id, proto);
+}
+
 extern "C" spai_status spai_server_submit(spai_server S, const spai_request *req, int64_t *ticket)
 {
     if (!S || !req || !ticket) return SPAI_EINVAL;
@@ -553,9 +580,11 @@ extern "C" spai_status spai_server_submit(spai_server S, const spai_request *req
         return SPAI_EINVAL;
     }
     const int32_t s = req->nrhs;
-    if (!(s == 1 || s == 2 || s == 4 || s == 8 || s == 16) || !req->coef || !req->B || !std::isfinite(req->p) ||
-        !std::isfinite(req->s)) {
-        set_err(S, "submit: bad request (nrhs must be 1, 2, 4, 8 or 16; coef and B non-NULL; p, s finite)");
+    const System &ys = *S->systems[req->system];
+    if (!(s == 1 || s == 2 || s == 4 || s == 8 || s == 16) || (!req->coef && !ys.shifted) || !req->B ||
+        !std::isfinite(req->p) || !std::isfinite(req->s)) {
+        set_err(S, "submit: bad request (nrhs must be 1, 2, 4, 8 or 16; B non-NULL, and coef too unless the "
+                   "system is a shifted one; p, s finite)");
         return SPAI_EINVAL;
     }
     if (S->stop) {
@@ -564,8 +593,13 @@ extern "C" spai_status spai_server_submit(spai_server S, const spai_request *req
     }
     Req *q = new Req();
     q->r = *req;
-    const System &y = *S->systems[req->system];
-    q->coef.assign(req->coef, req->coef + y.nterms);
+    const System &y = ys;
+    if (req->coef) {
+        q->coef.assign(req->coef, req->coef + y.nterms);
+    } else {  // A(p, s) of the shifted second-order system
+        q->coef.assign(3, 0.0);
+        spai_shifted_coefficients(1, &req->p, req->s, y.alpha, y.beta, q->coef.data());
+    }
     q->r.coef = q->coef.data();
     q->ticket = S->next_ticket++;
     q->res.t_arrival = req->t_arrival >= 0.0 ? req->t_arrival : now_s(S);

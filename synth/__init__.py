@@ -139,6 +139,8 @@ class Workload:
     tol: float
     dims: tuple = ()
     extra: dict = field(default_factory=dict)
+    alpha: float = 0.05           # Rayleigh damping of the workload: D(p) = alpha M + beta K(p)
+    beta: float = 0.01
 
     @property
     def terms(self):

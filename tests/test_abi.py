@@ -68,11 +68,22 @@ def test_binding_fails_loudly_without_library(monkeypatch):
         sg.lib()
 
 
-def test_affine_coefficients_match_oracle():
+def test_shifted_coefficients_match_oracle(library):
+    """The library forms the coefficients of A(p, s) itself (host code, no GPU needed): they
+    equal the oracle's Rayleigh-damped coefficients (D = 0.05 M + 0.01 K(p)) bit for bit, and
+    the binding does no arithmetic of its own."""
     import oracle
     import paper_1809_06574_gb300 as sg
-    for p, s in ((0.1, 1.0), (0.7, 0.5), (1.0, 2.0)):
-        assert sg.affine_coefficients(p, s) == pytest.approx(oracle.coefficients(p, s), rel=1e-15)
+    import synth
+    w = synth.plain_2d_32()
+    for p, s in ((0.1, 1.0), (0.7, 0.5), (1.0, 2.0), (0.123456789, 1.7), (0.0, 0.0), (2.0, 1e-3)):
+        assert sg.spai_shifted_coefficients(p, s, w.alpha, w.beta) == oracle.coefficients(p, s), (p, s)
+    # several parameters: K(p) = K_0 + p_1 K_1 + p_2 K_2
+    c = sg.spai_shifted_coefficients([0.5, 0.25], 2.0, 0.1, 0.2)
+    assert c == [2.0 * 2.0 + 0.1 * 2.0, 1.0 + 0.2 * 2.0, (1.0 + 0.2 * 2.0) * 0.5, (1.0 + 0.2 * 2.0) * 0.25]
+    with pytest.raises(sg.SpaiError):
+        sg.spai_shifted_coefficients(float("nan"), 1.0, 0.05, 0.01)
+    assert not hasattr(sg, "affine_coefficients")
 
 
 def test_column_variant_table_is_host_logic(library):

@@ -30,8 +30,8 @@ def test_fullsize_sweep_pieces():
         assert nnz == 1810432
         v1 = torch.empty(nnz, dtype=torch.float64, device="cuda:0")
         v2 = torch.empty(nnz, dtype=torch.float64, device="cuda:0")
-        sg.spai_assemble(ctx, aff, sg.affine_coefficients(p1, s_shift), v1)
-        sg.spai_assemble(ctx, aff, sg.affine_coefficients(p2, s_shift), v2)
+        sg.spai_assemble_shifted(ctx, aff, s_shift, p1, w.alpha, w.beta, v1)
+        sg.spai_assemble_shifted(ctx, aff, s_shift, p2, w.alpha, w.beta, v2)
         A1d, A2d = sg.csr(n, rp, ci, v1, nnz), sg.csr(n, rp, ci, v2, nnz)
         pc1, _ = sg.spai_build(ctx, A1d, sg.PATTERN_A)
         pc2, _ = sg.spai_update(ctx, pc1, A2d, sg.UPDATE_FIRST)
@@ -87,8 +87,8 @@ def test_fullsize_27pt_128_bf16_build_update_solve():
         assert nnz == 55742968
         v1 = torch.empty(nnz, dtype=torch.float64, device="cuda:0")
         v2 = torch.empty(nnz, dtype=torch.float64, device="cuda:0")
-        sg.spai_assemble(ctx, aff, sg.affine_coefficients(p1, 1.0), v1)
-        sg.spai_assemble(ctx, aff, sg.affine_coefficients(p2, 1.0), v2)
+        sg.spai_assemble_shifted(ctx, aff, 1.0, p1, w.alpha, w.beta, v1)
+        sg.spai_assemble_shifted(ctx, aff, 1.0, p2, w.alpha, w.beta, v2)
         A1d, A2d = sg.csr(n, rp, ci, v1, nnz), sg.csr(n, rp, ci, v2, nnz)
         pc64, _ = sg.spai_build(ctx, A1d, sg.PATTERN_A)
         g64 = export(ctx, pc64)

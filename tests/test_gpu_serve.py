@@ -61,14 +61,14 @@ def _plain_route(sg, ctx, w, res, p, s, nrhs):
 def _serve(sg, systems, trace, **kw):
     srv = sg.spai_server_create(restart=RESTART, tol=TOL, **kw)
     try:
-        ids = [sg.spai_server_add_system(srv, [sg.csr(w.n, *t) for t in w.terms]) for w in systems]
+        ids = [sg.spai_server_add_shifted_system(srv, [sg.csr(w.n, *t) for t in w.terms], w.alpha, w.beta) for w in systems]
         Bs = [np.asfortranarray(w.B) for w in systems]
         Xs, tickets = [], []
         for sy, p, s, nrhs in trace:
             w = systems[sy]
             X = np.zeros((w.n, nrhs), order="F")
             Xs.append(X)
-            tickets.append(sg.spai_server_submit(srv, ids[sy], nrhs, p, s, sg.affine_coefficients(p, s),
+            tickets.append(sg.spai_server_submit(srv, ids[sy], nrhs, p, s, None,
                                                  Bs[sy], X))
         res = [sg.spai_server_wait(srv, t) for t in tickets]
         stats = sg.spai_server_stats_get(srv)
@@ -175,7 +175,7 @@ def test_fullsize_served_trace():
     srv = sg.spai_server_create(slots=4, reuse=True, radius=0.05, pattern_kind=sg.PREC_FP32, restart=30,
                                 max_cycles=100, tol=TOL, mem_budget=40 << 30)
     try:
-        ids = [sg.spai_server_add_system(srv, [sg.csr(w.n, *t) for t in w.terms]) for w in pool]
+        ids = [sg.spai_server_add_shifted_system(srv, [sg.csr(w.n, *t) for t in w.terms], w.alpha, w.beta) for w in pool]
         Bs = [np.asfortranarray(w.B) for w in pool]
         sampled, tickets, Xs = set(), [], {}
         for k, (_, sy, p, s, nrhs) in enumerate(trace):
@@ -184,7 +184,7 @@ def test_fullsize_served_trace():
                 sampled.add(sy)
                 X = np.zeros((pool[sy].n, nrhs), order="F")
                 Xs[k] = X
-            tickets.append(sg.spai_server_submit(srv, ids[sy], nrhs, p, s, sg.affine_coefficients(p, s), Bs[sy], X))
+            tickets.append(sg.spai_server_submit(srv, ids[sy], nrhs, p, s, None, Bs[sy], X))
         res = [sg.spai_server_wait(srv, t) for t in tickets]
         stats = sg.spai_server_stats_get(srv)
     finally:
@@ -210,9 +210,9 @@ def test_failed_requests_do_not_stop_the_server():
     trace = _trace(6, len(systems), seed=9)
     srv = sg.spai_server_create(slots=2, restart=1, max_cycles=1, tol=1e-12, reuse=True)
     try:
-        ids = [sg.spai_server_add_system(srv, [sg.csr(w.n, *t) for t in w.terms]) for w in systems]
+        ids = [sg.spai_server_add_shifted_system(srv, [sg.csr(w.n, *t) for t in w.terms], w.alpha, w.beta) for w in systems]
         Bs = [np.asfortranarray(w.B) for w in systems]  # read by the workers: kept alive here
-        tickets = [sg.spai_server_submit(srv, ids[sy], nrhs, p, s, sg.affine_coefficients(p, s), Bs[sy])
+        tickets = [sg.spai_server_submit(srv, ids[sy], nrhs, p, s, None, Bs[sy])
                    for sy, p, s, nrhs in trace]
         res = [sg.spai_server_wait(srv, t) for t in tickets]
         stats = sg.spai_server_stats_get(srv)

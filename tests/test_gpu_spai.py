@@ -76,6 +76,30 @@ def test_assembly_bit_exact(case, host_terms):
         _sg().spai_affine_destroy(aff)
 
 
+@pytest.mark.parametrize("case", ["2d-32", "3d-10-7pt", "3d-6-27pt"])
+def test_assemble_shifted_bit_exact(case):
+    """A(p, s) = s^2 M + s D(p) + K(p), D = alpha M + beta K(p) (Sec. 1.1, Sec. 3), formed
+    entirely by the library (coefficients and assembly), equals the oracle's assembly of
+    the same system bit for bit, for several shifts and parameters."""
+    import torch
+    sg = _sg()
+    w = {"2d-32": synth.plain_2d_32, "3d-10-7pt": lambda: synth.grid3d_7pt(side=10, nparams=2),
+         "3d-6-27pt": lambda: synth.grid3d_27pt(side=6, nparams=2)}[case]()
+    n = w.n
+    with context() as ctx:
+        aff = sg.spai_affine_create(ctx, [dev_csr(t, n) for t in w.terms])
+        _, nnz, _, _ = sg.spai_affine_pattern(aff)
+        for p, s in ((0.1, 1.0), (0.73, 0.5), (1.9, 2.0), (0.0, 0.0)):
+            v = torch.empty(max(nnz, 1), dtype=torch.float64, device="cuda:0")
+            sg.spai_assemble_shifted(ctx, aff, s, p, w.alpha, w.beta, v)
+            sg.spai_ctx_sync(ctx)
+            ref = oracle.assemble(w.terms, oracle.coefficients(p, s), n)
+            assert np.array_equal(v.cpu().numpy()[:nnz], ref[2]), (p, s)
+        with pytest.raises(sg.SpaiError):  # (M, K_0, K_1) needs exactly one parameter
+            sg.spai_assemble_shifted(ctx, aff, 1.0, [0.1, 0.2], w.alpha, w.beta, v)
+        sg.spai_affine_destroy(aff)
+
+
 # ----------------------------------------------------------------------------- build
 def _build_cases():
     cases = []
