@@ -268,8 +268,9 @@ SPAI_API spai_status spai_update(spai_ctx ctx, spai_pc base, const spai_csr *A_n
  * / ||A(:,j)||^2, and adds the max_new best among those not above the candidates' mean
  * (scores compared as floor(rho / ||r||^2 * 2^30), ties by the lower column index).  It
  * stops when ||r||_2 <= eps, after max_steps steps, on a rank-deficient column problem,
- * when no candidate is left, when a step has more than 1024 distinct candidates, or when
- * |I_k| would exceed max_rows (that step is undone).  The search runs in FP64; the factor on the final pattern is then computed by
+ * when no candidate is left, or when |I_k| would exceed max_rows (that step is undone).
+ * Every candidate of a step is scored, however many there are (the kernel scores them in
+ * windows of 1024).  The search runs in FP64; the factor on the final pattern is then computed by
  * the column kernel of spai_build in the precision that `flags` selects.  The handle is an
  * ordinary one: spai_update keeps its pattern (the update skips the search, Sec. 2.3-2.4),
  * and apply, solve, export and destroy work as for spai_build.

@@ -251,8 +251,7 @@ def spai_build(A, n, kind=PATTERN_A, k0=0, k1=None, sets=None):
 
 ADAPTIVE_KEY_BITS = 30   # improvements compare at 2^-30 of ||r||^2 (ties: lower column index)
 ADAPTIVE_MAX_COLS = 32   # 1 + max_steps * max_new must not exceed this
-ADAPTIVE_MAX_ROWS = 128  # |I_k| above max_rows stops the growth of J_k
-ADAPTIVE_MAX_CANDIDATES = 1024  # more distinct candidates in a step than this stop the growth
+ADAPTIVE_MAX_ROWS = 128  # largest accepted max_rows option (|I_k| above max_rows stops the growth)
 
 
 def _adaptive_key(x, rr):
@@ -276,9 +275,9 @@ def spai_adaptive_pattern(A, n, eps=1e-4, max_steps=5, max_new=5, max_rows=ADAPT
       4. add the at most max_new candidates of smallest rho_j among those with rho_j not
          above the candidates' mean (compared as floor(rho / ||r||^2 * 2^30); ties by the
          lower column index); the step is undone and the growth stops if |I_k| would
-         exceed max_rows.  Size limits (the device kernel's buffers, stated here so both
-         sides stop alike): |J_k| <= 32, |I_k| <= 128, at most 1024 distinct candidates in
-         a step; a zero column of A offers no improvement (rho_j = ||r||^2).
+         exceed max_rows.  The options bound the pattern: |J_k| <= 1 + max_steps * max_new
+         <= 32, |I_k| <= max_rows <= 128; every candidate of a step is scored, however many
+         there are.  A zero column of A offers no improvement (rho_j = ||r||^2).
     Returns (Jptr, Jind) for columns k0 <= k < k1 (others J_k = {k}).  ``trace``, a list,
     receives (k, step, J, I, rr, candidates, rho, chosen) per step for the tests."""
     if 1 + max_steps * max_new > ADAPTIVE_MAX_COLS or max_rows > ADAPTIVE_MAX_ROWS:
@@ -333,8 +332,8 @@ def spai_adaptive_pattern(A, n, eps=1e-4, max_steps=5, max_new=5, max_rows=ADAPT
                 break
             inJ = set(J)
             cand = sorted({int(j) for row in I for j in colind[rowptr[row]:rowptr[row + 1]]} - inJ)
-            if not cand or len(cand) > ADAPTIVE_MAX_CANDIDATES:
-                break  # no candidate, or more than 1024 distinct candidates
+            if not cand:
+                break
             rho = []
             for j in cand:
                 dot = 0.0

@@ -10,8 +10,9 @@
 //   2. r = e_k - sum_c A(:, J_c) m_c (column by column) on I_k and ||r||^2; stop when
 //      ||r||_2 <= eps, after max_steps additions, or on a rank-deficient tile;
 //   3. candidates: columns j not in J_k with a nonzero in a row of I_k -- the sorted union
-//      of A's CSR rows of I_k (a warp-wide merge, 4 rows per lane), at most 1024;
-//      rho_j = ||r||^2 - (r . A(:,j))^2 / ||A(:,j)||^2 for each (A's column in CSC order);
+//      of A's CSR rows of I_k (a warp-wide merge, 4 rows per lane), scored in windows of
+//      1024 however many there are; rho_j = ||r||^2 - (r . A(:,j))^2 / ||A(:,j)||^2 for
+//      each (A's column in CSC order);
 //   4. the <= max_new candidates of smallest rho_j among those not above the candidates'
 //      mean, both compared as floor(rho / ||r||^2 * 2^30) (ties: lower column index), join
 //      J_k; if |I_k| would then exceed max_rows the step is undone and the growth stops.
@@ -29,17 +30,18 @@ namespace {
 
 constexpr int kAMJ = 32;     // columns of J_k
 constexpr int kAMI = 128;    // rows of I_k
-constexpr int kAMC = 1024;   // distinct candidates of one step
+constexpr int kAMC = 1024;   // candidates per scoring window
 constexpr int kKeyBits = 30;
 
 // per-warp shared memory, sized from the options: ld = max_rows, mc = 1 + max_steps * max_new
 //   Ah[ld * mc] tile (tile rows and columns in insertion order), rhs[ld] (Q^T e_k so far),
-//   r[ld], m[32], rd[32], invv[32], ck[kAMC] (candidates; then (key << 32) | column),
+//   r[ld], m[32], rd[32], invv[32], ck[kAMC + 32] (a window of candidates, then (key << 32) |
+//   column, and room for the running list), sel[32] (the smallest (key, column) so far),
 //   Jl[32] (J sorted), Jt[32] (tile column -> column), nJl[32] (scratch),
 //   It[128] (tile row -> row), Is[128] (rows sorted), Ip[128] (sorted -> tile row), newR[128]
 __host__ __device__ constexpr int adaptive_smem(int ld, int mc)
 {
-    return 8 * (ld * mc + 2 * ld + 3 * kAMJ) + 8 * kAMC + 4 * (3 * kAMJ + 4 * kAMI);
+    return 8 * (ld * mc + 2 * ld + 3 * kAMJ) + 8 * (kAMC + 2 * kAMJ) + 4 * (3 * kAMJ + 4 * kAMI);
 }
 
 __device__ __forceinline__ int bsearch_list(const int32_t *a, int len, int32_t key)
@@ -170,7 +172,8 @@ __global__ void __launch_bounds__(32) k_adaptive_pattern(AdaptiveProblem ap)
     double *rd = m + kAMJ;
     double *invv = rd + kAMJ;
     long long *ck = reinterpret_cast<long long *>(invv + kAMJ);
-    int32_t *Jl = reinterpret_cast<int32_t *>(ck + kAMC);
+    long long *sel = ck + kAMC + kAMJ;
+    int32_t *Jl = reinterpret_cast<int32_t *>(sel + kAMJ);
     int32_t *Jt = Jl + kAMJ;
     int32_t *nJl = Jt + kAMJ;
     int32_t *It = nJl + kAMJ;
@@ -185,8 +188,8 @@ __global__ void __launch_bounds__(32) k_adaptive_pattern(AdaptiveProblem ap)
         if (lane == 0) Jl[0] = Jt[0] = k;
         __syncwarp();
         int ni = union_rows(ap, Jl, 1, k, Is, kAMI, lane);
-        if (ni > ld) {  // even {k} is too tall: keep it
-            if (lane == 0) atomicOr(ap.d_err, ERR_TOO_WIDE);
+        if (ni > ld) {
+            // even {k} is taller than max_rows: J_k = {k} (the row limit's rule, not an error)
         } else {
             for (int i = lane; i < ni; i += 32) {
                 It[i] = Is[i];
@@ -249,7 +252,12 @@ __global__ void __launch_bounds__(32) k_adaptive_pattern(AdaptiveProblem ap)
             if (sqrt(rr) <= ap.eps || step == ap.max_steps || nj >= mc || !(rr > 0.0)) break;
 
             // ---- candidates: the sorted union of A's CSR rows of I_k without J_k (a warp-wide
-            // merge of the row lists, 4 rows per lane; each distinct column comes out once)
+            // merge of the row lists, 4 rows per lane; each distinct column comes out once),
+            // taken in windows of kAMC.  Each window is scored -- its improvements rho_j summed
+            // for the mean, its (key << 32 | column) merged with the running list `sel` of the
+            // lim smallest so far.  Taking the lim smallest and then dropping those above the
+            // mean's key chooses what filtering by the mean first would: however many
+            // candidates there are, all of them are scored, with a buffer of kAMC.
             int32_t cpos[4], cend[4], chead[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -263,65 +271,79 @@ __global__ void __launch_bounds__(32) k_adaptive_pattern(AdaptiveProblem ap)
                     if (cpos[u] < cend[u]) chead[u] = __ldg(ap.colind + cpos[u]);
                 }
             }
-            int nc = 0, jp = 0;  // jp walks the sorted J_k alongside the ascending output
-            while (true) {
-                int32_t lo = chead[0];
-#pragma unroll
-                for (int u = 1; u < 4; ++u) lo = min(lo, chead[u]);
-                const int32_t mcol = __reduce_min_sync(0xffffffffu, lo);
-                if (mcol == INT_MAX) break;
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (chead[u] == mcol) {
-                        ++cpos[u];
-                        chead[u] = cpos[u] < cend[u] ? __ldg(ap.colind + cpos[u]) : INT_MAX;
-                    }
-                while (jp < nj && Jl[jp] < mcol) ++jp;
-                if (!(jp < nj && Jl[jp] == mcol)) {
-                    if (lane == 0 && nc < kAMC) ck[nc] = mcol;
-                    ++nc;
-                }
-            }
-            __syncwarp();
-            if (nc > kAMC) {  // more candidates than the buffer holds: stop growing
-                if (lane == 0) atomicOr(ap.d_err, ERR_TOO_WIDE);
-                break;
-            }
-            if (nc == 0) break;
-            // ---- improvements rho_j, their mean, and the keys (key << 32 | column)
+            const int lim = min(ap.max_new, mc - nj);
+            int jp = 0;       // jp walks the sorted J_k alongside the ascending output
+            int nbest = 0;    // sel[0 .. nbest): the smallest (key, column) so far, ascending
+            int64_t ncand = 0;
             double psum = 0.0;
-            for (int e = lane; e < nc; e += 32) {
-                const int32_t j = (int32_t)ck[e];
-                double dot = 0.0;
-                const int32_t q1 = __ldg(ap.colptr + j + 1);
-                for (int32_t q = __ldg(ap.colptr + j); q < q1; ++q) {
-                    const int t = tile_row(Is, Ip, ni, __ldg(ap.rowind + q));
-                    if (t >= 0) dot = dot + r[t] * __ldg(ap.cval + q);
+            bool more = true;
+            while (more) {
+                int nw = 0;
+                while (true) {
+                    int32_t lo = chead[0];
+#pragma unroll
+                    for (int u = 1; u < 4; ++u) lo = min(lo, chead[u]);
+                    const int32_t mcol = __reduce_min_sync(0xffffffffu, lo);
+                    if (mcol == INT_MAX) {
+                        more = false;
+                        break;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (chead[u] == mcol) {
+                            ++cpos[u];
+                            chead[u] = cpos[u] < cend[u] ? __ldg(ap.colind + cpos[u]) : INT_MAX;
+                        }
+                    while (jp < nj && Jl[jp] < mcol) ++jp;
+                    if (!(jp < nj && Jl[jp] == mcol)) {
+                        if (lane == 0) ck[nw] = mcol;
+                        if (++nw == kAMC) break;  // window full: score it, then merge on
+                    }
                 }
-                const double cn = __ldg(ap.colnorm2 + j);
-                const double rho = cn == 0.0 ? rr : rr - dot * dot / cn;
-                ck[e] = (adaptive_key(rho, rr) << 32) | (long long)j;
-                psum += rho;
-            }
-            const double mean = warp_sum(psum) / (double)nc;
-            const long long kmean = adaptive_key(mean, rr);
-            __syncwarp();
-            for (int e = lane; e < nc; e += 32)
-                if ((ck[e] >> 32) > kmean) ck[e] = LLONG_MAX;
-            __syncwarp();
-            // ---- the max_new smallest (key, column)
-            int nsel = 0;
-            for (int t = 0; t < ap.max_new && nj + nsel < mc; ++t) {
-                long long best = LLONG_MAX;
-                for (int e = lane; e < nc; e += 32) best = ck[e] < best ? ck[e] : best;
-                best = warp_min_ll(best);
-                if (best == LLONG_MAX) break;
-                for (int e = lane; e < nc; e += 32)
-                    if (ck[e] == best) ck[e] = LLONG_MAX;
-                if (lane == 0) nJl[nsel] = (int32_t)(best & 0xffffffffll);
-                ++nsel;
+                __syncwarp();
+                // ---- improvements rho_j of the window and their keys (key << 32 | column)
+                for (int e = lane; e < nw; e += 32) {
+                    const int32_t j = (int32_t)ck[e];
+                    double dot = 0.0;
+                    const int32_t q1 = __ldg(ap.colptr + j + 1);
+                    for (int32_t q = __ldg(ap.colptr + j); q < q1; ++q) {
+                        const int t = tile_row(Is, Ip, ni, __ldg(ap.rowind + q));
+                        if (t >= 0) dot = dot + r[t] * __ldg(ap.cval + q);
+                    }
+                    const double cn = __ldg(ap.colnorm2 + j);
+                    const double rho = cn == 0.0 ? rr : rr - dot * dot / cn;
+                    ck[e] = (adaptive_key(rho, rr) << 32) | (long long)j;
+                    psum += rho;
+                }
+                ncand += nw;
+                // ---- the lim smallest of the window and the running list
+                for (int e = lane; e < nbest; e += 32) ck[nw + e] = sel[e];
+                __syncwarp();
+                const int tot = nw + nbest;
+                int ns = 0;
+                for (int t = 0; t < lim; ++t) {
+                    long long best = LLONG_MAX;
+                    for (int e = lane; e < tot; e += 32) best = ck[e] < best ? ck[e] : best;
+                    best = warp_min_ll(best);
+                    if (best == LLONG_MAX) break;
+                    for (int e = lane; e < tot; e += 32)
+                        if (ck[e] == best) ck[e] = LLONG_MAX;
+                    if (lane == 0) sel[ns] = best;
+                    ++ns;
+                    __syncwarp();
+                }
+                nbest = ns;
                 __syncwarp();
             }
+            if (ncand == 0) break;
+            const double mean = warp_sum(psum) / (double)ncand;
+            const long long kmean = adaptive_key(mean, rr);
+            // ---- the chosen columns: the running list's entries whose key is not above the mean's
+            int nsel = 0;
+            while (nsel < nbest && (sel[nsel] >> 32) <= kmean) ++nsel;
+            if (lane == 0)
+                for (int t = 0; t < nsel; ++t) nJl[t] = (int32_t)(sel[t] & 0xffffffffll);
+            __syncwarp();
             if (nsel == 0) break;
             // chosen columns ascending (insertion sort of <= 31 values)
             if (lane == 0)

@@ -1203,8 +1203,7 @@ extern "C" spai_status spai_build_adaptive(spai_ctx ctx, const spai_csr *A, cons
         if ((st = read_i32(ctx, Jptr + n, &nnzP))) return bail(st);
         int herr = 0;
         if ((st = read_err(ctx, &herr))) return bail(st);
-        // ERR_TOO_WIDE here only reports columns whose growth stopped at a size limit
-        if (herr & ~ERR_TOO_WIDE) return bail(fail(ctx, SPAI_EINVAL, "adaptive pattern failed (device error 0x%x)", herr));
+        if (herr) return bail(fail(ctx, SPAI_EINVAL, "adaptive pattern failed (device error 0x%x)", herr));
         if ((st = dalloc_n(ctx, &Jind, std::max(nnzP, 1)))) return bail(st);
         if (launch_compact_lists(ctx->stream, n, outJ, mc, Jptr, Jind))
             return bail(fail(ctx, SPAI_ECUDA, "compaction: kernel launch failed"));

@@ -243,6 +243,21 @@ def random_sparse(n, density, seed, *, symmetric_pattern=False, diag_shift=None)
     return dense_to_csr(D, keep), D
 
 
+def bordered_sparse(n, density, seed, border_rows=1):
+    """``random_sparse`` with its first ``border_rows`` rows full (a bordered matrix, as a
+    constraint row or a global coupling gives): every column meets those rows, so a least-
+    squares problem whose row set contains one of them sees all n columns as neighbours.
+    The border entries are N(0,1) * 0.1; the diagonal stays dominant."""
+    rng = np.random.default_rng(np.random.SeedSequence(seed).spawn(1)[0])
+    (_, _, _), D = random_sparse(n, density, seed)
+    keep = D != 0
+    keep[:border_rows, :] = True
+    D[:border_rows, :] = np.where(D[:border_rows, :] != 0, D[:border_rows, :],
+                                  0.1 * rng.standard_normal((border_rows, n)))
+    D[np.arange(border_rows), np.arange(border_rows)] += 0.1 * n
+    return dense_to_csr(D, keep), D
+
+
 def rhs_block(n, s, seed):
     rng = np.random.default_rng(np.random.SeedSequence(seed).spawn(3)[1])
     return np.asfortranarray(rng.standard_normal((n, s)))

@@ -79,6 +79,35 @@ def test_adaptive_update_and_solve():
     print(f"adaptive 3d-9: {info['iterations']} iterations (oracle {io['iterations']})")
 
 
+def test_adaptive_more_candidates_than_one_window():
+    """A bordered matrix (row 0 full, n = 1,200): every column's row set holds row 0, so
+    each step of every column has ~1,199 candidates, more than the kernel's window of 1,024.
+    The kernel scores all of them in windows, so its patterns, row sets and entries equal
+    the oracle's (which has no cap) on sampled column ranges, and the build reports no
+    error."""
+    import paper_1809_06574_gb300 as sg
+    n = 1200
+    A, _ = synth.bordered_sparse(n, 0.002, seed=7)
+    opts = dict(eps=1e-10, max_steps=2, max_new=3)
+    with context() as ctx:
+        pc, st = sg.spai_build_adaptive(ctx, dev_csr(A, n), **opts)
+        g = export(ctx, pc)
+        sg.spai_pc_destroy(pc)
+    assert st == 0
+    for k0, k1 in ((0, 40), (600, 640), (n - 40, n)):
+        Jptr, Jind = oracle.spai_adaptive_pattern(A, n, k0=k0, k1=k1, **opts)
+        Iptr, Ilist = oracle.index_sets(A, n, Jptr, Jind)
+        ref = oracle.spai_build(A, n, oracle.PATTERN_A, k0=k0, k1=k1, sets=(Jptr, Jind, Iptr, Ilist))
+        for k in range(k0, k1):
+            a, b = g["Jptr"][k], g["Jptr"][k + 1]
+            assert b - a > 1, k  # the pattern grew despite the candidate count
+            assert np.array_equal(g["Jind"][a:b], Jind[Jptr[k]:Jptr[k + 1]]), k
+            ia, ib = g["Iptr"][k], g["Iptr"][k + 1]
+            assert np.array_equal(g["Ilist"][ia:ib], Ilist[Iptr[k]:Iptr[k + 1]]), k
+            got, want = g["val"][a:b], ref.val[Jptr[k]:Jptr[k + 1]]
+            assert np.max(np.abs(got - want)) <= 1e-10 * np.max(np.abs(want)), k
+
+
 def test_adaptive_options_are_checked():
     import paper_1809_06574_gb300 as sg
     w = synth.plain_2d_32()

@@ -143,3 +143,30 @@ def test_row_limit_undoes_the_step_that_would_exceed_it():
             assert len(grown) > limit
             stopped += 1
     assert stopped > 0  # the limit binds for some columns in this case
+
+
+def test_every_candidate_is_scored_however_many():
+    """A bordered matrix (row 0 full): column 0's first row set holds row 0, so every other
+    column (1,199 of them, more than any fixed buffer of 1,024) is a candidate.  The rule of
+    the adaptive pattern has no cap on candidates: all of them are scored, the choice is the
+    brute-force one over all of them, and the pattern grows."""
+    n = 1200
+    A, D = synth.bordered_sparse(n, 0.002, seed=7)
+    trace = []
+    Jptr, Jind = oracle.spai_adaptive_pattern(A, n, eps=1e-10, max_steps=2, max_new=3, k0=0, k1=1, trace=trace)
+    first = [t for t in trace if t[0] == 0 and t[1] == 0]
+    assert first
+    (k, step, J, I, rr, cand, rho, chosen) = first[0]
+    assert cand == [j for j in range(1, n)]  # all of them
+    e = np.zeros(n)
+    e[0] = 1.0
+    m = np.linalg.lstsq(D[:, J], e, rcond=None)[0]
+    r = e - D[:, J] @ m
+    assert abs(r @ r - rr) <= 1e-10 * rr
+    cn = np.sum(D * D, axis=0)
+    bf = r @ r - (r @ D) ** 2 / cn  # one-column improvement of every column at once
+    assert np.max(np.abs(np.array(rho) - bf[1:])) <= 1e-10 * rr
+    keys = [oracle._adaptive_key(x, rr) for x in rho]
+    kmean = oracle._adaptive_key(sum(rho) / len(rho), rr)
+    assert chosen == [j for _, j in sorted((q, j) for q, j in zip(keys, cand) if q <= kmean)][:3]
+    assert len(chosen) == 3 and Jptr[1] - Jptr[0] > 1
