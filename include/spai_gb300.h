@@ -117,6 +117,19 @@ SPAI_API const char *spai_last_error(spai_ctx ctx);
 /* Block the host until the context's stream has finished its work. */
 SPAI_API spai_status spai_ctx_sync(spai_ctx ctx);
 
+/* Time limit of the bounded device-side waits of this context's tensor-core products (the
+ * block Gram-Schmidt kernels of block_solve, spai_block_gram and spai_block_update), in
+ * seconds, 0 < seconds <= 10 (default 1).  A pipeline wait that runs out makes its kernel
+ * stop, wait for its own copies and tensor-core operations in flight (those waits keep a 1 s
+ * limit), free its tensor memory and return; the call then returns SPAI_ETIMEOUT (block_solve
+ * at the end of that Arnoldi step) and the context stays usable. */
+SPAI_API spai_status spai_ctx_set_wait_limit(spai_ctx ctx, double seconds);
+
+/* Test of the give-up path above: each of the next `count` tensor-core product launches on
+ * this context also waits, within the limit, on a barrier that nothing completes, so its
+ * wait runs out.  count 0 cancels.  No counterpart in the paper (failure detection). */
+SPAI_API spai_status spai_ctx_inject_stall(spai_ctx ctx, int32_t count);
+
 /* Device bytes currently held by the library for this context (handles + workspace). */
 SPAI_API size_t spai_ctx_mem_in_use(spai_ctx ctx);
 
@@ -351,11 +364,13 @@ SPAI_API spai_status spai_pc_apply(spai_ctx ctx, spai_pc pc, int32_t s, const do
  * already reserved by another allocator so that a new allocation would fail.
  * The staging blocks live in one fixed device array of 64 MiB built into the library,
  * which every device that loads the library holds until the process exits; n * s must
- * be <= 2,097,152, else SPAI_EINVAL.  X and Y must be DEVICE memory on the context's
- * device (current device).  The first call on each device looks up the array's address
- * and caches it, so make that call before any stream capture.  All calls share the
- * array: calls that overlap on the GPU (other streams, other host threads) race.
- * Asynchronous on the context's stream. */
+ * be <= 2,097,152, else SPAI_EINVAL.  X and Y must be DEVICE memory of the context's
+ * device, which must be the current device (else SPAI_EINVAL).  The first call on each
+ * device looks up the array's address and caches it for the rest of the process, so make
+ * that call before any stream capture; a device reset (cudaDeviceReset) while the library
+ * is loaded is not supported by this call.  All calls share the array: calls that overlap
+ * on the GPU (other streams, other host threads) race.  Asynchronous on the context's
+ * stream. */
 SPAI_API spai_status spai_pc_apply_noalloc(spai_ctx ctx, spai_pc pc, int32_t s, const double *X,
                                            int64_t ldx, double *Y, int64_t ldy);
 

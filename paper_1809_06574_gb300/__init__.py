@@ -19,7 +19,7 @@ import os
 __all__ = [
     "SpaiError", "spai_csr", "spai_solve_opts", "spai_solve_info", "csr", "lib",
     "spai_ctx_create", "spai_ctx_destroy", "spai_last_error", "spai_ctx_sync",
-    "spai_ctx_mem_in_use", "spai_launch_count", "spai_ctx_profile", "spai_ctx_profile_count", "spai_measure_fp64_rate",
+    "spai_ctx_mem_in_use", "spai_ctx_set_wait_limit", "spai_ctx_inject_stall", "spai_launch_count", "spai_ctx_profile", "spai_ctx_profile_count", "spai_measure_fp64_rate",
     "spai_ctx_profile_entry", "spai_affine_create", "spai_affine_pattern",
     "spai_assemble", "spai_affine_export", "spai_affine_destroy", "spai_build", "spai_update", "spai_pc_info",
     "spai_pc_export", "spai_pc_destroy", "spai_build_batch", "block_solve_batch", "spai_spmm", "spai_pc_apply", "block_solve",
@@ -131,6 +131,8 @@ def lib():
         "spai_last_error": (C.c_char_p, [vp]),
         "spai_ctx_sync": (i32, [vp]),
         "spai_ctx_mem_in_use": (sz, [vp]),
+        "spai_ctx_set_wait_limit": (i32, [vp, dbl]),
+        "spai_ctx_inject_stall": (i32, [vp, i32]),
         "spai_launch_count": (i64, []),
         "spai_measure_fp64_rate": (i32, [vp, P(dbl)]),
         "spai_ctx_profile": (i32, [vp, i32]),
@@ -234,6 +236,14 @@ def spai_last_error(ctx):
 
 def spai_ctx_sync(ctx):
     return _check(ctx, lib().spai_ctx_sync(ctx))
+
+
+def spai_ctx_set_wait_limit(ctx, seconds):
+    return _check(ctx, lib().spai_ctx_set_wait_limit(ctx, float(seconds)))
+
+
+def spai_ctx_inject_stall(ctx, count=1):
+    return _check(ctx, lib().spai_ctx_inject_stall(ctx, int(count)))
 
 
 def spai_ctx_mem_in_use(ctx):

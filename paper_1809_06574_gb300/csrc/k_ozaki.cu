@@ -58,7 +58,7 @@ constexpr int kCW = 8;             // converter warps
 constexpr int kCT = 32 * kCW;      // converter threads
 constexpr int kThreadsTC = 64 + 128 + kCT;  // copy warp, MMA warp, 4 drain warps, converters
 constexpr int kRawRow = kS * 8;    // 64 bytes: one row of an n x 8 block
-constexpr unsigned long long kWaitNs = 1000000000ull;  // a bounded wait gives up after 1 s
+constexpr unsigned long long kWaitNs = 1000000000ull;  // drain waits give up after 1 s
 constexpr unsigned kSuspendNs = 20000;                  // suspend hint of one try_wait
 static_assert(9 * 63 * 63 * kSegK < (1 << 24), "exact FP32 class sums");
 static_assert(kClsCols == 5 * 16, "drain_classes reads five 16-column groups");
@@ -79,7 +79,7 @@ constexpr int kDDigStage = 42 * 1024;   // cap of one digit stage
 constexpr int kDDigStages = 3;
 constexpr int kDSmem = 227 * 1024;
 constexpr int kDOffBar = kDSmem - 1024;
-constexpr int kDBars = 2 * (kDRawMax + kDDigStages + kBufs);
+constexpr int kDBars = 2 * (kDRawMax + kDDigStages + kBufs) + 1;  // + one that nothing completes (stall test)
 constexpr int kDOffFlag = kDOffBar + kDBars * 8;
 constexpr int kDOffTmem = kDOffFlag + 8;
 constexpr int kDOffExp = kDOffTmem + 8;
@@ -165,20 +165,22 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// wait for the phase of the given parity; false after kWaitNs without it
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+// wait for the phase of the given parity; false after `limit` ns without it.  The pipeline
+// waits take the caller's limit; the waits that drain a CTA's own copies and MMAs before
+// its shared and tensor memory are released always take kWaitNs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, unsigned long long limit = kWaitNs)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (global_ns() - t0 > limit) return false;
     return true;
 }
 
 // a warp's bounded wait on one mbarrier phase; the outcome is the same in every lane
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity)
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, unsigned long long limit)
 {
-    return __all_sync(0xffffffffu, mbar_wait_bounded(bar, parity)) != 0;
+    return __all_sync(0xffffffffu, mbar_wait_bounded(bar, parity, limit)) != 0;
 }
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
@@ -425,7 +427,8 @@ __global__ void __launch_bounds__(256) k_trsm_fixed(int32_t n, double *__restric
 // sums carry their own scale.
 __global__ void __launch_bounds__(kThreadsTC, 1)
     k_block_dot_tc(int32_t n, int32_t nblk, int32_t subs_per_chunk, const uint64_t *__restrict__ Vfs, int32_t ipad,
-                   const double *__restrict__ W, double *__restrict__ partial, int *err)
+                   const double *__restrict__ W, double *__restrict__ partial, int *err, unsigned long long wl,
+                   int stall)
 {
     extern __shared__ __align__(128) char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -449,6 +452,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     const uint32_t rfull0 = bar0, rempty0 = rfull0 + kDRawMax * 8;
     const uint32_t dfull0 = rempty0 + kDRawMax * 8, dempty0 = dfull0 + kDDigStages * 8;
     const uint32_t bfull0 = dempty0 + kDDigStages * 8, bfree0 = bfull0 + kBufs * 8;
+    const uint32_t never = bfree0 + kBufs * 8;  // initialised, never arrived at
     volatile int *flag = reinterpret_cast<volatile int *>(smem + kDOffFlag);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kDOffTmem);
     int32_t *wexp = reinterpret_cast<int32_t *>(smem + kDOffExp);
@@ -472,6 +476,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             mbar_init(bfull0 + 8 * b, 1);
             mbar_init(bfree0 + 8 * b, 128);
         }
+        mbar_init(never, 1);
         asm volatile("fence.mbarrier_init.release.cluster;");
         *flag = 0;
     }
@@ -495,7 +500,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             int issued = 0;
             for (int k = 0; k < nst; ++k) {
                 const int s = k % R;
-                if (k >= R && !mbar_wait_bounded(rempty0 + 8 * s, (uint32_t)(((k - R) / R) & 1))) {
+                if (k >= R && !mbar_wait_bounded(rempty0 + 8 * s, (uint32_t)(((k - R) / R) & 1), wl)) {
                     *flag = 1;
                     break;
                 }
@@ -519,16 +524,18 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         }
     } else if (warp == 1) {
         if (lane == 0 && work) {  // ---- MMA issuer
+            // test of the give-up path: a bounded wait on a barrier that nothing completes
+            if (stall && !mbar_wait_bounded(never, 0, wl)) *flag = 1;
             int done = 0;
             for (int k = 0; k < nst; ++k) {
                 const int d = k % kDDigStages, seg = k / sps, buf = seg % kBufs;
                 const bool first = k % sps == 0;
                 if (first && seg >= kBufs &&
-                    !mbar_wait_bounded(bfree0 + 8 * buf, (uint32_t)((seg / kBufs - 1) & 1))) {
+                    !mbar_wait_bounded(bfree0 + 8 * buf, (uint32_t)((seg / kBufs - 1) & 1), wl)) {
                     *flag = 1;
                     break;
                 }
-                if (!mbar_wait_bounded(dfull0 + 8 * d, (uint32_t)((k / kDDigStages) & 1)) || *flag) {
+                if (!mbar_wait_bounded(dfull0 + 8 * d, (uint32_t)((k / kDDigStages) & 1), wl) || *flag) {
                     *flag = 1;
                     break;
                 }
@@ -564,7 +571,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             bool ok = true;
             for (int seg = 0; seg < nseg; ++seg) {
                 const int buf = seg % kBufs;
-                if (!mbar_wait_bounded(bfull0 + 8 * buf, (uint32_t)((seg / kBufs) & 1)) || *flag) {
+                if (!mbar_wait_bounded(bfull0 + 8 * buf, (uint32_t)((seg / kBufs) & 1), wl) || *flag) {
                     *flag = 1;
                     ok = false;
                     break;
@@ -629,9 +636,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         bool bad = false;
         for (int k = 0; k < nst; ++k) {
             const int s = k % R, d = k % kDDigStages;
-            bool ok = warp_wait(rfull0 + 8 * s, (uint32_t)((k / R) & 1));
+            bool ok = warp_wait(rfull0 + 8 * s, (uint32_t)((k / R) & 1), wl);
             if (ok && k >= kDDigStages)
-                ok = warp_wait(dempty0 + 8 * d, (uint32_t)(((k - kDDigStages) / kDDigStages) & 1));
+                ok = warp_wait(dempty0 + 8 * d, (uint32_t)(((k - kDDigStages) / kDDigStages) & 1), wl);
             if (!ok || *flag) {
                 if (lane == 0) *flag = 1;
                 break;
@@ -761,7 +768,7 @@ constexpr int kUDigStages = 3;
 constexpr int kUSegSteps = kSegK / 16;        // K steps per segment
 constexpr int kUOffDig = kURawStages * kURawStage;
 constexpr int kUOffBar = kUOffDig + kUDigStages * kUDigStage;
-constexpr int kUBars = 2 * (kURawStages + kUDigStages + kBufs);
+constexpr int kUBars = 2 * (kURawStages + kUDigStages + kBufs) + 1;  // + one that nothing completes (stall test)
 constexpr int kUOffFlag = kUOffBar + kUBars * 8;
 constexpr int kUOffTmem = kUOffFlag + 8;
 constexpr int kUSmem = kUOffTmem + 16;
@@ -775,7 +782,8 @@ static_assert(kUOffDig % 16 == 0 && kUDigStage % 16 == 0 && kUOffBar % 8 == 0, "
 // the tile's rows.
 __global__ void __launch_bounds__(kThreadsTC, 1)
     k_block_update_tc(int32_t n, int32_t nblk, const uint64_t *__restrict__ Vf, const char *__restrict__ hdig,
-                      const int32_t *__restrict__ hexp, const double *base, double *out, double sign, int *err)
+                      const int32_t *__restrict__ hexp, const double *base, double *out, double sign, int *err,
+                      unsigned long long wl, int stall)
 {
     extern __shared__ __align__(128) char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -786,6 +794,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     const uint32_t rfull0 = bar0, rempty0 = rfull0 + kURawStages * 8;
     const uint32_t dfull0 = rempty0 + kURawStages * 8, dempty0 = dfull0 + kUDigStages * 8;
     const uint32_t bfull0 = dempty0 + kUDigStages * 8, bfree0 = bfull0 + kBufs * 8;
+    const uint32_t never = bfree0 + kBufs * 8;  // initialised, never arrived at
     volatile int *flag = reinterpret_cast<volatile int *>(smem + kUOffFlag);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kUOffTmem);
 
@@ -807,6 +816,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             mbar_init(bfull0 + 8 * b, 1);
             mbar_init(bfree0 + 8 * b, 128);
         }
+        mbar_init(never, 1);
         asm volatile("fence.mbarrier_init.release.cluster;");
         *flag = 0;
     }
@@ -829,7 +839,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 for (int kk = 0; kk < nk; ++kk, ++g) {
                     const int s = (int)(g % kURawStages);
                     if (g >= kURawStages &&
-                        !mbar_wait_bounded(rempty0 + 8 * s, (uint32_t)(((g - kURawStages) / kURawStages) & 1))) {
+                        !mbar_wait_bounded(rempty0 + 8 * s, (uint32_t)(((g - kURawStages) / kURawStages) & 1), wl)) {
                         *flag = 1;
                         break;
                     }
@@ -851,13 +861,15 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {  // ---- MMA thread
+            // test of the give-up path: a bounded wait on a barrier that nothing completes
+            if (stall && !mbar_wait_bounded(never, 0, wl)) *flag = 1;
             int64_t g = 0, gs = 0;
             int64_t last = -1;  // last digit stage consumed
             for (int64_t tile = blockIdx.x; tile < ntiles && !*flag; tile += gridDim.x) {
                 bool ok = true;
                 for (int sgm = 0; sgm < nsegt && ok; ++sgm, ++gs) {
                     const int buf = (int)(gs % kBufs);
-                    if (gs >= kBufs && !mbar_wait_bounded(bfree0 + 8 * buf, (uint32_t)((gs / kBufs - 1) & 1))) {
+                    if (gs >= kBufs && !mbar_wait_bounded(bfree0 + 8 * buf, (uint32_t)((gs / kBufs - 1) & 1), wl)) {
                         ok = false;
                         break;
                     }
@@ -865,7 +877,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     const int k0 = sgm * kUSegSteps, k1 = min(nk, k0 + kUSegSteps);
                     for (int kk = k0; kk < k1; ++kk, ++g) {
                         const int d = (int)(g % kUDigStages);
-                        if (!mbar_wait_bounded(dfull0 + 8 * d, (uint32_t)((g / kUDigStages) & 1))) {
+                        if (!mbar_wait_bounded(dfull0 + 8 * d, (uint32_t)((g / kUDigStages) & 1), wl)) {
                             ok = false;
                             break;
                         }
@@ -903,7 +915,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             for (int b = 0; b < kS; ++b) hi[b] = lo[b] = 0;
             for (int sgm = 0; sgm < nsegt; ++sgm, ++gs) {
                 const int buf = (int)(gs % kBufs);
-                if (!mbar_wait_bounded(bfull0 + 8 * buf, (uint32_t)((gs / kBufs) & 1)) || *flag) {
+                if (!mbar_wait_bounded(bfull0 + 8 * buf, (uint32_t)((gs / kBufs) & 1), wl) || *flag) {
                     *flag = 1;
                     ok = false;
                     break;
@@ -932,9 +944,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             const int rv = (int)min((int64_t)128, (int64_t)n - tile * 128);
             for (int kk = 0; kk < nk; ++kk, ++g) {
                 const int s = (int)(g % kURawStages), d = (int)(g % kUDigStages);
-                bool ok = warp_wait(rfull0 + 8 * s, (uint32_t)((g / kURawStages) & 1));
+                bool ok = warp_wait(rfull0 + 8 * s, (uint32_t)((g / kURawStages) & 1), wl);
                 if (ok && g >= kUDigStages)
-                    ok = warp_wait(dempty0 + 8 * d, (uint32_t)(((g - kUDigStages) / kUDigStages) & 1));
+                    ok = warp_wait(dempty0 + 8 * d, (uint32_t)(((g - kUDigStages) / kUDigStages) & 1), wl);
                 if (!ok || *flag) {
                     if (lane == 0) *flag = 1;
                     stop = true;
@@ -1024,7 +1036,7 @@ int launch_trsm_fixed(cudaStream_t st, int32_t n, double *Q, const double *R, co
 }
 
 int launch_block_update_tc(cudaStream_t st, int32_t n, int32_t nblk, const uint64_t *Vf, const double *H, void *hdig,
-                           int32_t *hexp, const double *base, double *out, double sign, int *d_err)
+                           int32_t *hexp, const double *base, double *out, double sign, int *d_err, TcWait wt)
 {
     if (n <= 0 || nblk <= 0 || nblk > block_update_tc_max_blocks()) return -1;
     k_h_digits<<<1, 256, 0, st>>>(nblk, H, (char *)hdig, hexp, d_err);
@@ -1037,13 +1049,13 @@ int launch_block_update_tc(cudaStream_t st, int32_t n, int32_t nblk, const uint6
     const int64_t tiles = ((int64_t)n + 127) / 128;
     const int grid = (int)(tiles < sms ? tiles : sms);
     k_block_update_tc<<<grid, kThreadsTC, kUSmem, st>>>(n, nblk, Vf, (const char *)hdig, hexp, base, out, sign,
-                                                         d_err);
+                                                         d_err, (unsigned long long)wt.ns, wt.stall);
     note_launches(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int launch_block_dot_tc(cudaStream_t st, int32_t n, int32_t nblk, const uint64_t *Vfs, int32_t ipad, const double *W,
-                        double *partial, double *out, int *d_err)
+                        double *partial, double *out, int *d_err, TcWait wt)
 {
     if (n <= 0 || nblk <= 0) return -1;
     if (cudaFuncSetAttribute(k_block_dot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kDSmem) != cudaSuccess)
@@ -1053,7 +1065,8 @@ int launch_block_dot_tc(cudaStream_t st, int32_t n, int32_t nblk, const uint64_t
     const int chunks = (int)((nt + spc - 1) / spc);
     const int mtiles = (nblk + kBlocksPerTile - 1) / kBlocksPerTile;
     dim3 grid(chunks, mtiles);
-    k_block_dot_tc<<<grid, kThreadsTC, kDSmem, st>>>(n, nblk, spc, Vfs, ipad, W, partial, d_err);
+    k_block_dot_tc<<<grid, kThreadsTC, kDSmem, st>>>(n, nblk, spc, Vfs, ipad, W, partial, d_err,
+                                                      (unsigned long long)wt.ns, wt.stall);
     note_launches(1);
     if (cudaGetLastError() != cudaSuccess) return -1;
     return launch_reduce_chunks(st, nblk * kS * kS, chunks, partial, out);

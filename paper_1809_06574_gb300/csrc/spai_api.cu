@@ -38,6 +38,8 @@ struct spai_ctx_s {
     void *ws = nullptr;        // grow-only solve workspace
     size_t ws_bytes = 0;
     double *h_pinned = nullptr;  // pinned host scratch for per-iteration read-backs
+    uint64_t wait_ns = 1000000000ull;  // limit of the tensor-core kernels' pipeline waits
+    int32_t stall_left = 0;            // tensor-core launches still to run the stall test
     // optional per-kernel-family timing with CUDA events on the context's stream
     struct ProfRec {
         int family;
@@ -744,6 +746,18 @@ spai_status apply_rm(spai_ctx ctx, spai_pc pc, int32_t s, const double *X, doubl
 
 bool valid_s(int32_t s) { return s == 1 || s == 2 || s == 4 || s == 8 || s == 16; }
 
+// wait settings of the next tensor-core launch on this context
+TcWait tc_wait(spai_ctx ctx)
+{
+    TcWait w;
+    w.ns = ctx->wait_ns;
+    if (ctx->stall_left > 0) {
+        --ctx->stall_left;
+        w.stall = 1;
+    }
+    return w;
+}
+
 }  // namespace
 
 // ===================================================================================
@@ -792,6 +806,24 @@ extern "C" spai_status spai_ctx_sync(spai_ctx ctx)
 {
     if (!ctx) return SPAI_EINVAL;
     CU(cudaStreamSynchronize(ctx->stream), "stream sync");
+    return SPAI_OK;
+}
+
+extern "C" spai_status spai_ctx_set_wait_limit(spai_ctx ctx, double seconds)
+{
+    if (!ctx) return SPAI_EINVAL;
+    if (!(seconds > 0.0 && seconds <= 10.0))
+        return fail(ctx, SPAI_EINVAL, "wait limit must be in (0, 10] seconds");
+    const double ns = seconds * 1e9;
+    ctx->wait_ns = ns < 1.0 ? 1ull : (uint64_t)ns;
+    return SPAI_OK;
+}
+
+extern "C" spai_status spai_ctx_inject_stall(spai_ctx ctx, int32_t count)
+{
+    if (!ctx) return SPAI_EINVAL;
+    if (count < 0) return fail(ctx, SPAI_EINVAL, "count must be >= 0");
+    ctx->stall_left = count;
     return SPAI_OK;
 }
 
@@ -2202,14 +2234,15 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
     auto gram_tc = [&](int nb, double *Wsrc, double *H) -> spai_status {
         const double f = 2.0 * n * s * s * nb, by = 8.0 * n * s * (nb + 1);
         if (!halves) {
-            PKL("block_dot_tc", f, by, launch_block_dot_tc(cs, n, nb, w.vfix_sub, ipad, Wsrc, w.partial, H, ctx->d_err),
+            PKL("block_dot_tc", f, by, launch_block_dot_tc(cs, n, nb, w.vfix_sub, ipad, Wsrc, w.partial, H, ctx->d_err, tc_wait(ctx)),
                 "block Gram product");
             return SPAI_OK;
         }
         ProfScope ps(ctx, "block_dot_tc", f, by);
         KL(launch_halves16(cs, n, Wsrc, w.Wh, false), "column halves");
-        KL(launch_block_dot_tc(cs, n, 2 * nb, w.vfix_sub, ipad, w.Wh, w.partial, w.HL, ctx->d_err), "block Gram product");
-        KL(launch_block_dot_tc(cs, n, 2 * nb, w.vfix_sub, ipad, w.Wh + half_elems, w.partial, w.HR, ctx->d_err),
+        KL(launch_block_dot_tc(cs, n, 2 * nb, w.vfix_sub, ipad, w.Wh, w.partial, w.HL, ctx->d_err, tc_wait(ctx)), "block Gram product");
+        KL(launch_block_dot_tc(cs, n, 2 * nb, w.vfix_sub, ipad, w.Wh + half_elems, w.partial, w.HR, ctx->d_err,
+                               tc_wait(ctx)),
            "block Gram product");
         KL(launch_pieces16(cs, nb, H, w.HL, w.HR, true), "merge pieces");
         return SPAI_OK;
@@ -2231,7 +2264,7 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
             (opts->orth == SPAI_ORTH_TENSOR || nb >= 2)) {
             if (!halves) {
                 PKL("block_update_tc", f, 8.0 * n * s * (nb + 2),
-                    launch_block_update_tc(cs, n, nb, w.vfix, H, w.hdig, w.hexp, basep, out, sign, ctx->d_err),
+                    launch_block_update_tc(cs, n, nb, w.vfix, H, w.hdig, w.hexp, basep, out, sign, ctx->d_err, tc_wait(ctx)),
                     "block update");
                 return SPAI_OK;
             }
@@ -2242,7 +2275,7 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
             for (int h = 0; h < 2; ++h) {
                 double *wh = w.Wh + h * half_elems;
                 KL(launch_block_update_tc(cs, n, 2 * nb, w.vfix, h ? w.HR : w.HL, w.hdig, w.hexp, basep ? wh : nullptr, wh,
-                                          sign, ctx->d_err),
+                                          sign, ctx->d_err, tc_wait(ctx)),
                    "block update");
             }
             KL(launch_halves16(cs, n, out, w.Wh, true), "merge halves");
@@ -2268,7 +2301,7 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
     }
     const size_t blk_elems = (size_t)n * s;
     const double nsd = (double)n * s;
-    double *h = ctx->h_pinned;  // [0,16) bnorm2, [16,32) rn2, [32,48) est, [48] flag
+    double *h = ctx->h_pinned;  // [0,16) bnorm2, [16,32) rn2, [32,48) est, [48] flag, [49] error word
     KL(launch_colnorm2(cs, s, n, w.Bw, w.partial, w.nrm2, chunks), "norm B");
     CU(cudaMemcpyAsync(h, w.nrm2, s * 8, cudaMemcpyDeviceToHost, cs), "read norms");
     CU(cudaStreamSynchronize(cs), "sync");
@@ -2338,9 +2371,16 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
                 launch_arnoldi_ls(cs, s, j, m, w.H1, w.H2, w.Rn, w.Qs, w.Rtri, w.G, w.thresh, w.est, w.flag), "least squares");
             CU(cudaMemcpyAsync(h + 32, w.est, s * 8, cudaMemcpyDeviceToHost, cs), "read estimates");
             CU(cudaMemcpyAsync(h + 48, w.flag, 4, cudaMemcpyDeviceToHost, cs), "read flag");
+            CU(cudaMemcpyAsync(h + 49, ctx->d_err, 4, cudaMemcpyDeviceToHost, cs), "read error word");
             CU(cudaStreamSynchronize(cs), "sync");
             ++iters;
             J = j + 1;
+            if (*(int32_t *)(h + 49) & ERR_TIMEOUT) {  // a bounded wait gave up: stop at once
+                int h_err = 0;
+                if ((st = read_err(ctx, &h_err))) return st;
+                return fail(ctx, SPAI_ETIMEOUT, "a bounded wait in a tensor-core product gave up (Arnoldi step %d)",
+                            iters);
+            }
             if (*(int32_t *)(h + 48)) break;
         }
         // X += P (V Y)
@@ -2754,7 +2794,7 @@ extern "C" spai_status spai_block_gram(spai_ctx ctx, int32_t s, int32_t n, int32
         PKL("to_fixed", 0.0, 16.0 * nsd * nblk,
             launch_to_fixed(ctx->stream, n, nblk, V, nullptr, vfix, nblk, 0, ctx->d_err), "fixed point");
         PKL("block_dot_tc", 2.0 * nsd * s * nblk, 8.0 * nsd * (nblk + 1),
-            launch_block_dot_tc(ctx->stream, n, nblk, vfix, nblk, W, partial, H, ctx->d_err), "tensor gram");
+            launch_block_dot_tc(ctx->stream, n, nblk, vfix, nblk, W, partial, H, ctx->d_err, tc_wait(ctx)), "tensor gram");
     }
     int h = 0;
     if ((st = read_err(ctx, &h))) return st;
@@ -2792,7 +2832,7 @@ extern "C" spai_status spai_block_update(spai_ctx ctx, int32_t s, int32_t n, int
         PKL("to_fixed", 0.0, 16.0 * nsd * nblk,
             launch_to_fixed(ctx->stream, n, nblk, V, vfix, nullptr, 0, 0, ctx->d_err), "fixed point");
         PKL("block_update_tc", 2.0 * nsd * s * nblk, 8.0 * nsd * (nblk + 2),
-            launch_block_update_tc(ctx->stream, n, nblk, vfix, H, hdig, hexp, W, W, sign, ctx->d_err),
+            launch_block_update_tc(ctx->stream, n, nblk, vfix, H, hdig, hexp, W, W, sign, ctx->d_err, tc_wait(ctx)),
             "tensor block update");
     }
     int h = 0;
@@ -2839,6 +2879,17 @@ extern "C" spai_status spai_pc_apply_noalloc(spai_ctx ctx, spai_pc pc, int32_t s
     if (n == 0) return SPAI_OK;
     if (ldx < n || ldy < n || !X || !Y) return fail(ctx, SPAI_EINVAL, "bad block arguments");
     if (!is_device_ptr(X) || !is_device_ptr(Y)) return fail(ctx, SPAI_EINVAL, "X and Y must be device memory");
+    {
+        // on the context's own device: a peer pointer would reach the kernels unchecked
+        cudaPointerAttributes ax, ay;
+        if (cudaPointerGetAttributes(&ax, X) != cudaSuccess || cudaPointerGetAttributes(&ay, Y) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, SPAI_EINVAL, "X, Y: pointer attributes unavailable");
+        }
+        if (ax.device != ctx->device || ay.device != ctx->device)
+            return fail(ctx, SPAI_EINVAL, "X and Y must be memory of the context's device %d (got %d, %d)", ctx->device,
+                        ax.device, ay.device);
+    }
     const size_t blk = (size_t)n * s;
     if (4 * blk > kNoAllocDoubles)
         return fail(ctx, SPAI_EINVAL, "n * s = %zu exceeds the no-allocation apply limit of %zu", blk,

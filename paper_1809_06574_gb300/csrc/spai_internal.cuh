@@ -303,6 +303,14 @@ int launch_gram_sym(cudaStream_t st, int32_t s, int32_t n, const double *W, doub
 int launch_reduce_chunks(cudaStream_t st, int32_t count, int chunks, const double *partial, double *out);
 
 // ---------------------------------------------------------------------- k_ozaki.cu
+// Bounded waits of the tensor-core kernels: pipeline waits give up after ns nanoseconds
+// (the drain of a CTA's own copies and MMAs keeps 1 s); stall != 0 adds, at the start of
+// the MMA issuer, a bounded wait on a barrier that nothing completes (a test of the
+// give-up path).
+struct TcWait {
+    uint64_t ns = 1000000000ull;
+    int stall = 0;
+};
 // FP64-accurate products on the tensor cores (s == 8): basis blocks as fixed point (Vf,
 // from launch_to_fixed, |v| < 2), W as FP64; BF16 digits are cut in shared memory.
 bool block_dot_tc_supported(int32_t s);
@@ -315,13 +323,13 @@ int launch_to_fixed(cudaStream_t st, int32_t n, int32_t nblocks, const double *X
 // H = V_{0..nblk-1}^T W (H[i][a][b]) from the sub-tile layout of ipad slots; partial needs
 // tc_partial_elems(n, nblk) doubles
 int launch_block_dot_tc(cudaStream_t st, int32_t n, int32_t nblk, const uint64_t *Vfs, int32_t ipad, const double *W,
-                        double *partial, double *out, int *d_err);
+                        double *partial, double *out, int *d_err, TcWait wt);
 // out = base + sign * V_{0..nblk-1} H (base may be null, may equal out): H is nblk*8 x 8
 // ([i][a][b]); hdig needs tc_hdig_bytes(nblk) bytes, hexp 8 ints
 int block_update_tc_max_blocks();
 size_t tc_hdig_bytes(int32_t nblk);
 int launch_block_update_tc(cudaStream_t st, int32_t n, int32_t nblk, const uint64_t *Vf, const double *H, void *hdig,
-                           int32_t *hexp, const double *base, double *out, double sign, int *d_err);
+                           int32_t *hexp, const double *base, double *out, double sign, int *d_err, TcWait wt);
 // Q := Q R^{-1} in place (s == 8, deflated columns -> 0) and the new basis block's fixed
 // point: row layout at F_row (n x 8), sub-tile layout at slot blk of ipad slots of F_sub
 int launch_trsm_fixed(cudaStream_t st, int32_t n, double *Q, const double *R, const int32_t *deflated, uint64_t *F_row,

@@ -134,3 +134,62 @@ def test_solve_with_tensor_orthogonalisation_matches_fp64(nrhs, restart, side):
     Xtc, itc = res[sg.ORTH_TENSOR]
     assert itc["iterations"] == i64["iterations"]
     assert np.linalg.norm(Xtc - X64) <= 1e-10 * np.linalg.norm(X64)
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """Failure detection of the tensor-core kernels without a fault: with a 2 ms wait limit,
+    an injected stall (a bounded wait on a barrier that nothing completes) makes the Gram
+    product and the block update give up -- each stops, drains its own copies and MMAs,
+    frees its tensor memory and returns -- and the call returns SPAI_ETIMEOUT.  The next
+    calls on the same context run normally and match the FP64 kernels; a block solve with a
+    stall stops with SPAI_ETIMEOUT and the next solve converges."""
+    import torch
+    import paper_1809_06574_gb300 as sg
+    n, nblk = 65536, 6
+    Q, W = _blocks(n, nblk, seed=3)
+    H = np.random.default_rng(5).standard_normal((nblk * 8, 8))
+    with context() as ctx:
+        sg.spai_ctx_set_wait_limit(ctx, 2e-3)
+        Vd = _to_dev_blocks(Q, n, nblk)
+        Wd = torch.as_tensor(np.ascontiguousarray(W), device="cuda:0")
+        Hd = torch.zeros((nblk, 8, 8), dtype=torch.float64, device="cuda:0")
+        for _ in range(2):  # twice in a row: each give-up leaves the context clean
+            sg.spai_ctx_inject_stall(ctx, 1)
+            with pytest.raises(sg.SpaiError) as ei:
+                sg.spai_block_gram(ctx, 8, n, nblk, Vd, Wd, Hd, sg.ORTH_TENSOR)
+            assert ei.value.status == sg.SPAI_ETIMEOUT
+        H64 = torch.zeros_like(Hd)
+        sg.spai_block_gram(ctx, 8, n, nblk, Vd, Wd, Hd, sg.ORTH_TENSOR)
+        sg.spai_block_gram(ctx, 8, n, nblk, Vd, Wd, H64, sg.ORTH_FP64)
+        wn = np.maximum(np.linalg.norm(W, axis=0), 1e-300)
+        assert np.max(np.abs((Hd - H64).cpu().numpy().reshape(-1, 8)) / wn) <= 2e-14
+        Hu = torch.as_tensor(np.ascontiguousarray(H), device="cuda:0")
+        Wt = Wd.clone()
+        sg.spai_ctx_inject_stall(ctx, 1)
+        with pytest.raises(sg.SpaiError) as ei:
+            sg.spai_block_update(ctx, 8, n, nblk, Vd, Hu, Wt, -1.0, sg.ORTH_TENSOR)
+        assert ei.value.status == sg.SPAI_ETIMEOUT
+        Wt, W64 = Wd.clone(), Wd.clone()
+        sg.spai_block_update(ctx, 8, n, nblk, Vd, Hu, Wt, -1.0, sg.ORTH_TENSOR)
+        sg.spai_block_update(ctx, 8, n, nblk, Vd, Hu, W64, -1.0, sg.ORTH_FP64)
+        assert torch.max(torch.abs(Wt - W64)).item() <= 2e-14 * torch.max(torch.abs(W64)).item()
+        # a block solve: the stalled product ends it with SPAI_ETIMEOUT; the next one converges
+        w = synth.grid3d_7pt(side=20, nparams=2, nrhs=8)
+        A = oracle.assemble(w.terms, oracle.coefficients(w.params[0], 1.0), w.n)
+        Ad = dev_csr(A, w.n)
+        pc, _ = sg.spai_build(ctx, Ad)
+        X = np.zeros((w.n, 8), order="F")
+        sg.spai_ctx_inject_stall(ctx, 1)
+        with pytest.raises(sg.SpaiError) as ei:
+            sg.block_solve(ctx, Ad, pc, 8, np.asfortranarray(w.B), w.n, X, w.n, 30, 1e-8, 20, orth=sg.ORTH_TENSOR)
+        assert ei.value.status == sg.SPAI_ETIMEOUT
+        sg.spai_ctx_set_wait_limit(ctx, 1.0)
+        X = np.zeros((w.n, 8), order="F")
+        st, info, rel = sg.block_solve(ctx, Ad, pc, 8, np.asfortranarray(w.B), w.n, X, w.n, 30, 1e-8, 20,
+                                       orth=sg.ORTH_TENSOR)
+        assert info["converged"] and max(rel) <= 1e-8
+        true_rel = np.linalg.norm(w.B - oracle.spmm(A, X, w.n), axis=0) / np.linalg.norm(w.B, axis=0)
+        assert np.all(true_rel <= 1e-8)
+        with pytest.raises(sg.SpaiError):
+            sg.spai_ctx_set_wait_limit(ctx, 0.0)
+        sg.spai_pc_destroy(pc)
