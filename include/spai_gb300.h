@@ -357,6 +357,15 @@ SPAI_API spai_status spai_spmm(spai_ctx ctx, const spai_csr *A, int32_t s, const
 SPAI_API spai_status spai_pc_apply(spai_ctx ctx, spai_pc pc, int32_t s, const double *X, int64_t ldx,
                           double *Y, int64_t ldy);
 
+/* The FP32 operator of SPAI_SOLVE_MIXED (see block_solve) on its own: Y = A X and Y = P X
+ * with the matrix's or factors' values and X rounded to FP32, products and sums in FP32 in
+ * each row's order (a factored chain keeps its intermediate blocks in FP32), Y written as
+ * FP64 (exact).  Arguments as spai_spmm / spai_pc_apply.  Asynchronous. */
+SPAI_API spai_status spai_spmm_fp32(spai_ctx ctx, const spai_csr *A, int32_t s, const double *X, int64_t ldx,
+                                    double *Y, int64_t ldy);
+SPAI_API spai_status spai_pc_apply_fp32(spai_ctx ctx, spai_pc pc, int32_t s, const double *X, int64_t ldx,
+                                        double *Y, int64_t ldy);
+
 /* Y = P X like spai_pc_apply, but without allocating any device memory.  The paper has
  * no counterpart: this entry point serves callers that cannot allocate at the point of
  * the apply -- an outside Krylov solver whose inner loop must not stall the device (a
@@ -385,12 +394,26 @@ SPAI_API spai_status spai_pc_apply_noalloc(spai_ctx ctx, spai_pc pc, int32_t s, 
 #define SPAI_ORTH_FP64 1    /* FP64 fused multiply-adds on the CUDA cores */
 #define SPAI_ORTH_TENSOR 2  /* tensor-core digits whenever s == 8 */
 
+/* Arithmetic of the solve's operator products (no counterpart in the paper: the mixed-
+ * precision form of its solve, with the accuracy won back by iterative refinement).
+ * SPAI_SOLVE_FP64: every product in FP64 (FP32 / BF16 factors converted exactly).
+ * SPAI_SOLVE_MIXED: inside each restart cycle the operator A P is applied in FP32 -- A's
+ * values (rounded once per solve), the factors' values and each input block rounded to
+ * FP32, products and sums in FP32 -- while the Krylov basis, the block Gram-Schmidt / QR,
+ * the projected least squares and the true residual b - A x stay FP64.  Every cycle starts
+ * from the FP64 true residual r (iterative refinement) and ends once each column's
+ * estimate is below max(tol ||b_i||, 2^-20 ||r_i||) or the restart length is reached; the
+ * solve stops when every column's FP64 true residual meets tol, as in SPAI_SOLVE_FP64.
+ * The workspace grows by 4 nnz(A) bytes. */
+#define SPAI_SOLVE_FP64 0
+#define SPAI_SOLVE_MIXED 1
+
 typedef struct {
     int32_t restart;     /* m: block Arnoldi steps per cycle, >= 1 */
     int32_t max_cycles;  /* restart cycles before SPAI_ENOTCONV, >= 1 */
     double tol;          /* stop when ||b_i - A x_i||_2 <= tol * ||b_i||_2 for every column */
     int32_t orth;        /* SPAI_ORTH_* */
-    int32_t reserved;
+    int32_t precision;   /* SPAI_SOLVE_FP64 (0) or SPAI_SOLVE_MIXED */
 } spai_solve_opts;
 
 /* Block Gram product H_i = V_i^T W, i < nblk, of the block orthogonalisation (Sec. 2.1).
@@ -490,6 +513,8 @@ typedef struct {
     size_t mem_budget;     /* device bytes for systems, cached builds and in-flight requests (0: no cap);
                               a request counts its slot's workspace and buffers, its factor and,
                               for a build, 16 nnz + 16 (n + 1) + 1 MiB of pattern-analysis buffers */
+    int32_t precision;     /* SPAI_SOLVE_FP64 or SPAI_SOLVE_MIXED: the solves' operator arithmetic */
+    int32_t reserved;      /* 0 */
 } spai_server_opts;
 
 typedef struct {

@@ -22,13 +22,13 @@ __all__ = [
     "spai_ctx_mem_in_use", "spai_ctx_set_wait_limit", "spai_ctx_inject_stall", "spai_launch_count", "spai_ctx_profile", "spai_ctx_profile_count", "spai_measure_fp64_rate",
     "spai_ctx_profile_entry", "spai_affine_create", "spai_affine_pattern",
     "spai_assemble", "spai_affine_export", "spai_affine_destroy", "spai_build", "spai_update", "spai_pc_info",
-    "spai_pc_export", "spai_pc_destroy", "spai_build_batch", "block_solve_batch", "spai_spmm", "spai_pc_apply", "block_solve",
+    "spai_pc_export", "spai_pc_destroy", "spai_build_batch", "block_solve_batch", "spai_spmm", "spai_pc_apply", "spai_spmm_fp32", "spai_pc_apply_fp32", "block_solve",
     "spai_shifted_coefficients", "spai_assemble_shifted", "spai_server_add_shifted_system", "PATTERN_A", "PATTERN_A2", "UPDATE_FIRST", "UPDATE_CHAINED", "UPDATE_DIAGONAL", "PREC_FP32", "PREC_BF16",
     "LIB_PATH", "spai_ctx_trim", "spai_solve_workspace_size", "spai_pc_mem_size",
     "spai_server_opts", "spai_request", "spai_result", "spai_server_stats", "spai_server_create",
     "spai_server_add_system", "spai_server_submit", "spai_server_wait", "spai_server_clock",
     "spai_server_stats_get", "spai_server_last_error", "spai_server_destroy",
-    "ROUTE_BUILD", "ROUTE_UPDATE", "ROUTE_REUSE",
+    "ROUTE_BUILD", "ROUTE_UPDATE", "ROUTE_REUSE", "SOLVE_FP64", "SOLVE_MIXED",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -59,10 +59,11 @@ class spai_csr(C.Structure):
 
 class spai_solve_opts(C.Structure):
     _fields_ = [("restart", C.c_int32), ("max_cycles", C.c_int32), ("tol", C.c_double),
-                ("orth", C.c_int32), ("reserved", C.c_int32)]
+                ("orth", C.c_int32), ("precision", C.c_int32)]
 
 
 ORTH_AUTO, ORTH_FP64, ORTH_TENSOR = 0, 1, 2
+SOLVE_FP64, SOLVE_MIXED = 0, 1  # operator products in FP64, or in FP32 with FP64 refinement
 
 
 class spai_solve_info(C.Structure):
@@ -76,7 +77,8 @@ class spai_solve_info(C.Structure):
 class spai_server_opts(C.Structure):
     _fields_ = [("slots", C.c_int32), ("pattern_kind", C.c_int32), ("reuse", C.c_int32),
                 ("restart", C.c_int32), ("max_cycles", C.c_int32), ("orth", C.c_int32),
-                ("radius", C.c_double), ("tol", C.c_double), ("mem_budget", C.c_size_t)]
+                ("radius", C.c_double), ("tol", C.c_double), ("mem_budget", C.c_size_t),
+                ("precision", C.c_int32), ("reserved", C.c_int32)]
 
 
 class spai_request(C.Structure):
@@ -153,6 +155,8 @@ def lib():
         "spai_spmm": (i32, [vp, P(spai_csr), i32, vp, i64, vp, i64]),
         "spai_pc_apply": (i32, [vp, vp, i32, vp, i64, vp, i64]),
         "spai_pc_apply_noalloc": (i32, [vp, vp, i32, vp, i64, vp, i64]),
+        "spai_spmm_fp32": (i32, [vp, P(spai_csr), i32, vp, i64, vp, i64]),
+        "spai_pc_apply_fp32": (i32, [vp, vp, i32, vp, i64, vp, i64]),
         "spai_block_gram": (i32, [vp, i32, i32, i32, vp, vp, vp, i32]),
         "spai_block_update": (i32, [vp, i32, i32, i32, vp, vp, vp, dbl, i32]),
         "block_solve": (i32, [vp, P(spai_csr), vp, i32, vp, i64, vp, i64, P(spai_solve_opts),
@@ -402,6 +406,16 @@ def spai_pc_apply(ctx, pc, s, X, ldx, Y, ldy):
     return _check(ctx, lib().spai_pc_apply(ctx, pc, int(s), _ptr(X), int(ldx), _ptr(Y), int(ldy)))
 
 
+def spai_spmm_fp32(ctx, A, s, X, ldx, Y, ldy):
+    """Y = A X with the FP32 operator of the mixed-precision solve (FP32 products and sums)."""
+    return _check(ctx, lib().spai_spmm_fp32(ctx, C.byref(A), int(s), _ptr(X), int(ldx), _ptr(Y), int(ldy)))
+
+
+def spai_pc_apply_fp32(ctx, pc, s, X, ldx, Y, ldy):
+    """Y = P X with the FP32 operator of the mixed-precision solve."""
+    return _check(ctx, lib().spai_pc_apply_fp32(ctx, pc, int(s), _ptr(X), int(ldx), _ptr(Y), int(ldy)))
+
+
 def spai_pc_apply_noalloc(ctx, pc, s, X, ldx, Y, ldy):
     """Y = P X without allocating device memory (fixed 64 MiB staging array in the library).
 
@@ -428,9 +442,9 @@ def spai_block_update(ctx, s, n, nblk, V, H, W, sign=-1.0, method=ORTH_FP64):
 
 
 def block_solve(ctx, A, P, s, B, ldb, X, ldx, restart, tol, max_cycles, allow_notconv=False,
-                orth=ORTH_AUTO):
+                orth=ORTH_AUTO, precision=SOLVE_FP64):
     """Solve A X = B (column-major n x s; host or device).  Returns (status, info, rel)."""
-    opts = spai_solve_opts(int(restart), int(max_cycles), float(tol), int(orth), 0)
+    opts = spai_solve_opts(int(restart), int(max_cycles), float(tol), int(orth), int(precision))
     info = spai_solve_info()
     rel = (C.c_double * int(s))()
     st = lib().block_solve(ctx, C.byref(A), P, int(s), _ptr(B), int(ldb), _ptr(X), int(ldx),
@@ -493,9 +507,9 @@ def _server_check(srv, st):
 
 
 def spai_server_create(slots=4, pattern_kind=PATTERN_A, reuse=True, restart=30, max_cycles=50,
-                       orth=ORTH_AUTO, radius=0.05, tol=1e-8, mem_budget=0):
+                       orth=ORTH_AUTO, radius=0.05, tol=1e-8, mem_budget=0, precision=SOLVE_FP64):
     o = spai_server_opts(int(slots), int(pattern_kind), int(bool(reuse)), int(restart), int(max_cycles),
-                         int(orth), float(radius), float(tol), int(mem_budget))
+                         int(orth), float(radius), float(tol), int(mem_budget), int(precision), 0)
     out = C.c_void_p()
     st = lib().spai_server_create(C.byref(o), C.byref(out))
     if st != SPAI_OK:

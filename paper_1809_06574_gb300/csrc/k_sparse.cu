@@ -550,6 +550,127 @@ __global__ void __launch_bounds__(kThreads) k_spmm(int32_t n, const int32_t *__r
     Y[row * S + c] = acc;
 }
 
+// ---------------------------------------------------------------------------------
+// FP32 CSR times row-major block: the operator of the mixed-precision solve.  The matrix
+// values (FP32, BF16 bits, or FP64 rounded once) and the X entries (FP64 rounded once, or
+// FP32) are multiplied and summed in FP32 in the row's order; Y is written as FP32 or as
+// FP64 (exact conversion).  T = S / C lanes per row, each owning C = min(S, 4) consecutive
+// columns (vector loads of X and Y); the nonzeros are taken four at a time, their index,
+// value and X loads issued together before the multiply-adds.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ float as_f32(float v) { return v; }
+__device__ __forceinline__ float as_f32(double v) { return (float)v; }
+__device__ __forceinline__ float as_f32(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
+
+template <int C>
+__device__ __forceinline__ void load_x(const float *p, float (&x)[C])
+{
+    if constexpr (C == 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    } else if constexpr (C == 2) {
+        const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+        x[0] = v.x; x[1] = v.y;
+    } else {
+        x[0] = __ldg(p);
+    }
+}
+
+template <int C>
+__device__ __forceinline__ void load_x(const double *p, float (&x)[C])
+{
+    if constexpr (C >= 2) {
+#pragma unroll
+        for (int h = 0; h < C / 2; ++h) {
+            const double2 v = __ldg(reinterpret_cast<const double2 *>(p) + h);
+            x[2 * h] = (float)v.x;
+            x[2 * h + 1] = (float)v.y;
+        }
+    } else {
+        x[0] = (float)__ldg(p);
+    }
+}
+
+template <int C>
+__device__ __forceinline__ void store_y(float *p, const float (&y)[C])
+{
+    if constexpr (C == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(y[0], y[1], y[2], y[3]);
+    } else if constexpr (C == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(y[0], y[1]);
+    } else {
+        p[0] = y[0];
+    }
+}
+
+template <int C>
+__device__ __forceinline__ void store_y(double *p, const float (&y)[C])
+{
+    if constexpr (C >= 2) {
+#pragma unroll
+        for (int h = 0; h < C / 2; ++h)
+            reinterpret_cast<double2 *>(p)[h] = make_double2((double)y[2 * h], (double)y[2 * h + 1]);
+    } else {
+        p[0] = (double)y[0];
+    }
+}
+
+template <int S, typename V, typename XT, typename YT>
+__global__ void __launch_bounds__(kThreads) k_spmm32(int32_t n, const int32_t *__restrict__ rowptr,
+                                                     const int32_t *__restrict__ colind, const V *__restrict__ val,
+                                                     const XT *__restrict__ X, YT *__restrict__ Y)
+{
+    constexpr int C = S < 4 ? S : 4, T = S / C;
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t row = g / T;
+    if (row >= n) return;
+    const int part = (int)(g % T);
+    const int32_t a = __ldg(rowptr + row), b = __ldg(rowptr + row + 1);
+    const XT *xb = X + part * C;
+    float acc[C];
+#pragma unroll
+    for (int k = 0; k < C; ++k) acc[k] = 0.0f;
+    int32_t q = a;
+    for (; q + 4 <= b; q += 4) {
+        int32_t c[4];
+        float v[4], x[4][C];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            c[u] = __ldg(colind + q + u);
+            v[u] = as_f32(__ldg(val + q + u));
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) load_x<C>(xb + (int64_t)c[u] * S, x[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int k = 0; k < C; ++k) acc[k] = fmaf(v[u], x[u][k], acc[k]);
+    }
+    for (; q < b; ++q) {
+        float x[C];
+        const float v = as_f32(__ldg(val + q));
+        load_x<C>(xb + (int64_t)__ldg(colind + q) * S, x);
+#pragma unroll
+        for (int k = 0; k < C; ++k) acc[k] = fmaf(v, x[k], acc[k]);
+    }
+    store_y<C>(Y + row * S + part * C, acc);
+}
+
+// Y[r][c] = q[r] X[r][c] in FP32 (a diagonal factor of the FP32 operator)
+template <int S, typename V, typename XT, typename YT>
+__global__ void k_scale_rows32(int32_t n, const V *__restrict__ q, const XT *__restrict__ X, YT *__restrict__ Y)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= (int64_t)n * S) return;
+    Y[g] = (YT)(as_f32(__ldg(q + g / S)) * as_f32(X[g]));
+}
+
+__global__ void k_round_f32(int64_t count, const double *__restrict__ src, float *__restrict__ dst)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+
 template <int S, typename V>
 __global__ void k_scale_rows(int32_t n, const V *__restrict__ q, const double *__restrict__ X,
                              double *__restrict__ Y)
@@ -881,6 +1002,109 @@ int launch_spmm_bf16v(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowp
                       const uint16_t *val, const double *X, double *Y)
 {
     return spmm_any<uint16_t>(st, s, n, rowptr, colind, val, X, Y);
+}
+
+namespace {
+
+template <typename V, typename XT, typename YT>
+int spmm32_any(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr, const int32_t *colind, const V *val,
+               const XT *X, YT *Y)
+{
+    if (n <= 0) return 0;
+    const int T = s < 4 ? 1 : s / 4;
+    const int g = grid_for((int64_t)n * T);
+    switch (s) {
+    case 1: k_spmm32<1, V, XT, YT><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, Y); break;
+    case 2: k_spmm32<2, V, XT, YT><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, Y); break;
+    case 4: k_spmm32<4, V, XT, YT><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, Y); break;
+    case 8: k_spmm32<8, V, XT, YT><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, Y); break;
+    case 16: k_spmm32<16, V, XT, YT><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, Y); break;
+    default: return -1;
+    }
+    return check_launch();
+}
+
+template <typename V, typename XT, typename YT>
+int scale_rows32_any(cudaStream_t st, int32_t s, int32_t n, const V *q, const XT *X, YT *Y)
+{
+    if (n <= 0) return 0;
+    const int g = grid_for((int64_t)n * s);
+    switch (s) {
+    case 1: k_scale_rows32<1, V, XT, YT><<<g, kThreads, 0, st>>>(n, q, X, Y); break;
+    case 2: k_scale_rows32<2, V, XT, YT><<<g, kThreads, 0, st>>>(n, q, X, Y); break;
+    case 4: k_scale_rows32<4, V, XT, YT><<<g, kThreads, 0, st>>>(n, q, X, Y); break;
+    case 8: k_scale_rows32<8, V, XT, YT><<<g, kThreads, 0, st>>>(n, q, X, Y); break;
+    case 16: k_scale_rows32<16, V, XT, YT><<<g, kThreads, 0, st>>>(n, q, X, Y); break;
+    default: return -1;
+    }
+    return check_launch();
+}
+
+template <typename XT, typename YT>
+int spmm32_vals(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr, const int32_t *colind, const F32Vals &v,
+                const XT *X, YT *Y)
+{
+    if (v.f32) return spmm32_any<float, XT, YT>(st, s, n, rowptr, colind, v.f32, X, Y);
+    if (v.bf16) return spmm32_any<uint16_t, XT, YT>(st, s, n, rowptr, colind, v.bf16, X, Y);
+    if (v.f64) return spmm32_any<double, XT, YT>(st, s, n, rowptr, colind, v.f64, X, Y);
+    return -1;
+}
+
+template <typename XT, typename YT>
+int scale32_vals(cudaStream_t st, int32_t s, int32_t n, const F32Vals &v, const XT *X, YT *Y)
+{
+    if (v.f32) return scale_rows32_any<float, XT, YT>(st, s, n, v.f32, X, Y);
+    if (v.bf16) return scale_rows32_any<uint16_t, XT, YT>(st, s, n, v.bf16, X, Y);
+    if (v.f64) return scale_rows32_any<double, XT, YT>(st, s, n, v.f64, X, Y);
+    return -1;
+}
+
+}  // namespace
+
+int launch_spmm32(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr, const int32_t *colind,
+                  const F32Vals &v, const double *X, float *Y)
+{
+    return spmm32_vals(st, s, n, rowptr, colind, v, X, Y);
+}
+int launch_spmm32(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr, const int32_t *colind,
+                  const F32Vals &v, const float *X, float *Y)
+{
+    return spmm32_vals(st, s, n, rowptr, colind, v, X, Y);
+}
+int launch_spmm32(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr, const int32_t *colind,
+                  const F32Vals &v, const double *X, double *Y)
+{
+    return spmm32_vals(st, s, n, rowptr, colind, v, X, Y);
+}
+int launch_spmm32(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr, const int32_t *colind,
+                  const F32Vals &v, const float *X, double *Y)
+{
+    return spmm32_vals(st, s, n, rowptr, colind, v, X, Y);
+}
+int launch_scale_rows32(cudaStream_t st, int32_t s, int32_t n, const F32Vals &q, const double *X, float *Y)
+{
+    return scale32_vals(st, s, n, q, X, Y);
+}
+int launch_scale_rows32(cudaStream_t st, int32_t s, int32_t n, const F32Vals &q, const float *X, float *Y)
+{
+    return scale32_vals(st, s, n, q, X, Y);
+}
+int launch_scale_rows32(cudaStream_t st, int32_t s, int32_t n, const F32Vals &q, const double *X, double *Y)
+{
+    return scale32_vals(st, s, n, q, X, Y);
+}
+int launch_scale_rows32(cudaStream_t st, int32_t s, int32_t n, const F32Vals &q, const float *X, double *Y)
+{
+    return scale32_vals(st, s, n, q, X, Y);
+}
+
+int launch_round_f32(cudaStream_t st, int64_t count, const double *src, float *dst)
+{
+    if (count <= 0) return 0;
+    int g = grid_for(count);
+    if (g > 8 * 152) g = 8 * 152;
+    k_round_f32<<<g, kThreads, 0, st>>>(count, src, dst);
+    return check_launch();
 }
 
 namespace {

@@ -744,7 +744,67 @@ spai_status apply_rm(spai_ctx ctx, spai_pc pc, int32_t s, const double *X, doubl
     return SPAI_OK;
 }
 
+// Y = P X with the FP32 operator of the mixed-precision solve: every factor's values and
+// its input rounded to FP32, products and sums in FP32; the intermediate blocks of a
+// factored chain are FP32 (t0 / t1), the last factor writes Y (FP32 or FP64).
+template <typename YT>
+spai_status apply32(spai_ctx ctx, spai_pc pc, int32_t s, const double *X, YT *Y, float *t0, float *t1)
+{
+    std::vector<spai_pc> chain;
+    for (spai_pc p = pc; p; p = p->parent) chain.push_back(p);
+    const void *cur = X;
+    bool cur_f64 = true;
+    float *bufs[2] = {t0, t1};
+    for (size_t i = chain.size(); i-- > 0;) {
+        spai_pc h = chain[i];
+        F32Vals v;
+        v.f32 = h->fval32;
+        v.bf16 = h->fval16;
+        v.f64 = (h->fval32 || h->fval16) ? nullptr : h->fval;
+        const int32_t n = h->sym->n;
+        const double nz = h->diag ? n : h->sym->nnzP, nn = n;
+        const double vb = h->fval16 ? 2.0 : h->fval32 ? 4.0 : 8.0;
+        const double xin = cur_f64 ? 8.0 : 4.0, yout = (i == 0) ? (double)sizeof(YT) : 4.0;
+        const double flops = (h->diag ? 1.0 : 2.0) * nz * s;
+        const double bytes = h->diag ? vb * nn + (xin + yout) * nn * s
+                                     : (vb + 4.0) * nz + 4.0 * (nn + 1) + (xin + yout) * nn * s;
+        int rc;
+        void *dst = (i == 0) ? (void *)Y : (void *)bufs[(chain.size() - 1 - i) & 1];
+        {
+            ProfScope ps(ctx, h->diag ? "scale_rows32" : "spmm32_P", flops, bytes);
+            if (i == 0) {
+                if (h->diag)
+                    rc = cur_f64 ? launch_scale_rows32(ctx->stream, s, n, v, (const double *)cur, (YT *)dst)
+                                 : launch_scale_rows32(ctx->stream, s, n, v, (const float *)cur, (YT *)dst);
+                else
+                    rc = cur_f64 ? launch_spmm32(ctx->stream, s, n, h->sym->p_rowptr, h->sym->p_colind, v,
+                                                 (const double *)cur, (YT *)dst)
+                                 : launch_spmm32(ctx->stream, s, n, h->sym->p_rowptr, h->sym->p_colind, v,
+                                                 (const float *)cur, (YT *)dst);
+            } else {
+                if (h->diag)
+                    rc = cur_f64 ? launch_scale_rows32(ctx->stream, s, n, v, (const double *)cur, (float *)dst)
+                                 : launch_scale_rows32(ctx->stream, s, n, v, (const float *)cur, (float *)dst);
+                else
+                    rc = cur_f64 ? launch_spmm32(ctx->stream, s, n, h->sym->p_rowptr, h->sym->p_colind, v,
+                                                 (const double *)cur, (float *)dst)
+                                 : launch_spmm32(ctx->stream, s, n, h->sym->p_rowptr, h->sym->p_colind, v,
+                                                 (const float *)cur, (float *)dst);
+            }
+        }
+        if (rc) return fail(ctx, SPAI_ECUDA, "FP32 preconditioner apply: kernel launch failed");
+        cur = dst;
+        cur_f64 = false;
+    }
+    return SPAI_OK;
+}
+
 bool valid_s(int32_t s) { return s == 1 || s == 2 || s == 4 || s == 8 || s == 16; }
+
+// Reduction of the residual one cycle of the mixed-precision solve aims for (2^-20, sixteen
+// FP32 unit roundoffs): below it the FP32 operator's rounding, not the Krylov space, limits
+// what the cycle can resolve.
+constexpr double kMixedCycleReduction = 0x1p-20;
 
 // wait settings of the next tensor-core launch on this context
 TcWait tc_wait(spai_ctx ctx)
@@ -2054,6 +2114,51 @@ extern "C" spai_status spai_pc_apply(spai_ctx ctx, spai_pc pc, int32_t s, const 
     return SPAI_OK;
 }
 
+extern "C" spai_status spai_spmm_fp32(spai_ctx ctx, const spai_csr *A, int32_t s, const double *X, int64_t ldx,
+                                      double *Y, int64_t ldy)
+{
+    if (!ctx) return SPAI_EINVAL;
+    spai_status st = check_csr_args(ctx, A, "A");
+    if (st) return st;
+    if (!valid_s(s)) return fail(ctx, SPAI_EINVAL, "s must be 1, 2, 4, 8 or 16");
+    const int32_t n = A->n;
+    if (n == 0) return SPAI_OK;
+    if (ldx < n || ldy < n || !X || !Y) return fail(ctx, SPAI_EINVAL, "bad block arguments");
+    void *w = nullptr;
+    const size_t blk = (size_t)n * s * 8, a32 = ((size_t)A->nnz * 4 + 255) / 256 * 256;
+    if ((st = temp_blocks(ctx, 2 * blk + a32, &w))) return st;
+    double *xr = (double *)w, *yr = (double *)((char *)w + blk);
+    float *av = (float *)((char *)w + 2 * blk);
+    F32Vals v;
+    v.f32 = av;
+    KL(launch_round_f32(ctx->stream, A->nnz, A->val, av), "A in FP32");
+    KL(launch_pack(ctx->stream, s, n, X, ldx, xr), "pack");
+    PKL("spmm32_A", 2.0 * A->nnz * s, 8.0 * A->nnz + 4.0 * (n + 1) + 16.0 * n * s,
+        launch_spmm32(ctx->stream, s, n, A->rowptr, A->colind, v, (const double *)xr, yr), "spmm fp32");
+    KL(launch_unpack(ctx->stream, s, n, yr, Y, ldy), "unpack");
+    return SPAI_OK;
+}
+
+extern "C" spai_status spai_pc_apply_fp32(spai_ctx ctx, spai_pc pc, int32_t s, const double *X, int64_t ldx,
+                                          double *Y, int64_t ldy)
+{
+    if (!ctx || !pc) return fail(ctx, SPAI_EINVAL, "NULL argument");
+    if (!valid_s(s)) return fail(ctx, SPAI_EINVAL, "s must be 1, 2, 4, 8 or 16");
+    const int32_t n = pc->sym->n;
+    if (n == 0) return SPAI_OK;
+    if (ldx < n || ldy < n || !X || !Y) return fail(ctx, SPAI_EINVAL, "bad block arguments");
+    void *w = nullptr;
+    const size_t blk = (size_t)n * s * 8;
+    spai_status st = temp_blocks(ctx, 4 * blk, &w);
+    if (st) return st;
+    double *xr = (double *)w, *yr = xr + (size_t)n * s;
+    float *t0 = (float *)(yr + (size_t)n * s), *t1 = t0 + (size_t)n * s;
+    KL(launch_pack(ctx->stream, s, n, X, ldx, xr), "pack");
+    if ((st = apply32<double>(ctx, pc, s, xr, yr, t0, t1))) return st;
+    KL(launch_unpack(ctx->stream, s, n, yr, Y, ldy), "unpack");
+    return SPAI_OK;
+}
+
 // ===================================================================================
 // block GMRES(m)
 // ===================================================================================
@@ -2215,12 +2320,17 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
         if (info) info->converged = 1;
         return SPAI_OK;
     }
+    if (opts->precision != SPAI_SOLVE_FP64 && opts->precision != SPAI_SOLVE_MIXED)
+        return fail(ctx, SPAI_EINVAL, "unknown solve precision %d", opts->precision);
+    const bool mixed = opts->precision == SPAI_SOLVE_MIXED;
     const int chunks = krylov_chunks(n);
     SolveWs w{};
     const size_t need = carve(w, nullptr, n, s, m, chunks);
+    const size_t need32 = mixed ? ((size_t)A->nnz * 4 + 255) / 256 * 256 : 0;  // A's values in FP32
     void *base = nullptr;
-    if ((st = temp_blocks(ctx, need, &base))) return st;
+    if ((st = temp_blocks(ctx, need + need32, &base))) return st;
     carve(w, base, n, s, m, chunks);
+    float *a32 = mixed ? (float *)((char *)base + need) : nullptr;
     cudaStream_t cs = ctx->stream;
     const bool b_dev = is_device_ptr(B), x_dev = is_device_ptr(X);
     if (opts->orth < SPAI_ORTH_AUTO || opts->orth > SPAI_ORTH_TENSOR)
@@ -2326,9 +2436,26 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
         return true;
     };
     if ((st = residual())) return st;
+    F32Vals a32v;
+    if (mixed) {
+        a32v.f32 = a32;
+        PKL("round_f32", 0.0, 12.0 * A->nnz, launch_round_f32(cs, A->nnz, A->val, a32), "A in FP32");
+    }
+    // the FP32 operator's (A P) W = A (P V_j), intermediates FP32 in the Z / T blocks
+    float *z32 = (float *)w.Z, *t032 = (float *)w.T0, *t132 = (float *)w.T1;
+    const double nnzA = A->nnz;
     int cycles = 0, iters = 0;
     while (!converged() && cycles < opts->max_cycles) {
         ++cycles;
+        if (mixed) {
+            // iterative refinement: this cycle solves the correction equation from the FP64 true
+            // residual r; its FP32 operator resolves r only to ~FP32 rounding, so the cycle stops
+            // once every column's estimate is below max(tol ||b_i||, eta ||r_i||), and the next
+            // cycle starts from the new FP64 true residual
+            double cthr[16];
+            for (int i = 0; i < s; ++i) cthr[i] = std::max(thresh[i], kMixedCycleReduction * sqrt(h[16 + i]));
+            CU(cudaMemcpyAsync(w.thresh, cthr, s * 8, cudaMemcpyHostToDevice, cs), "write thresholds");
+        }
         // V_0 S_0 = R (ref2 holds the residual norms^2)
         if ((st = cholqr2(ctx, w, n, s, w.W, w.V, w.Rn, w.ref2, (use_digits && !halves) ? 0 : -1, ipad))) return st;
         if ((st = fixed16(0))) return st;
@@ -2337,12 +2464,23 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
         for (int j = 0; j < m; ++j) {
             const double *Vj = w.V + (size_t)j * blk_elems;
             const double *Zj = Vj;
-            if (P) {
-                if ((st = apply_rm(ctx, P, s, Vj, w.Z, w.T0, w.T1))) return st;
-                Zj = w.Z;
+            if (mixed) {
+                if (P) {
+                    if ((st = apply32<float>(ctx, P, s, Vj, z32, t032, t132))) return st;
+                    PKL("spmm32_A", 2.0 * nnzA * s, 8.0 * nnzA + 4.0 * (n + 1) + 12.0 * nsd,
+                        launch_spmm32(cs, s, n, A->rowptr, A->colind, a32v, (const float *)z32, w.W), "A Z (FP32)");
+                } else {
+                    PKL("spmm32_A", 2.0 * nnzA * s, 8.0 * nnzA + 4.0 * (n + 1) + 16.0 * nsd,
+                        launch_spmm32(cs, s, n, A->rowptr, A->colind, a32v, Vj, w.W), "A V (FP32)");
+                }
+            } else {
+                if (P) {
+                    if ((st = apply_rm(ctx, P, s, Vj, w.Z, w.T0, w.T1))) return st;
+                    Zj = w.Z;
+                }
+                PKL("spmm_A", 2.0 * A->nnz * s, 12.0 * A->nnz + 4.0 * (n + 1) + 16.0 * nsd,
+                    launch_spmm(cs, s, n, A->rowptr, A->colind, A->val, Zj, w.W), "A Z");
             }
-            PKL("spmm_A", 2.0 * A->nnz * s, 12.0 * A->nnz + 4.0 * (n + 1) + 16.0 * nsd,
-                launch_spmm(cs, s, n, A->rowptr, A->colind, A->val, Zj, w.W), "A Z");
             PKL("colnorm2", 2.0 * nsd, 8.0 * nsd, launch_colnorm2(cs, s, n, w.W, w.partial, w.ref2, chunks), "norms");
             // two passes of block classical Gram-Schmidt against V_0..V_j
             const double nb = j + 1;
@@ -2388,7 +2526,10 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
             "back substitution");
         if ((st = vupdate(J, w.Y, nullptr, w.W, 1.0))) return st;
         const double *U = w.W;
-        if (P) {
+        if (P && mixed) {
+            if ((st = apply32<double>(ctx, P, s, w.W, w.Z, t032, t132))) return st;
+            U = w.Z;
+        } else if (P) {
             if ((st = apply_rm(ctx, P, s, w.W, w.Z, w.T0, w.T1))) return st;
             U = w.Z;
         }

@@ -108,6 +108,28 @@ int launch_iota_i32(cudaStream_t st, int64_t count, int32_t *dst);
 // same with FP32 values (products and sums in FP64)
 int launch_spmm_f32v(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr, const int32_t *colind,
                      const float *val, const double *X, double *Y);
+// ---- the FP32 operator of the mixed-precision solve: values (one of the three pointers)
+// and X rounded to FP32, products and sums in FP32 in each row's order; X and Y FP64 or FP32
+struct F32Vals {
+    const float *f32 = nullptr;
+    const uint16_t *bf16 = nullptr;
+    const double *f64 = nullptr;
+};
+int launch_spmm32(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr, const int32_t *colind,
+                  const F32Vals &v, const double *X, float *Y);
+int launch_spmm32(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr, const int32_t *colind,
+                  const F32Vals &v, const float *X, float *Y);
+int launch_spmm32(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr, const int32_t *colind,
+                  const F32Vals &v, const double *X, double *Y);
+int launch_spmm32(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr, const int32_t *colind,
+                  const F32Vals &v, const float *X, double *Y);
+// Y[r][c] = q[r] X[r][c] in FP32
+int launch_scale_rows32(cudaStream_t st, int32_t s, int32_t n, const F32Vals &q, const double *X, float *Y);
+int launch_scale_rows32(cudaStream_t st, int32_t s, int32_t n, const F32Vals &q, const float *X, float *Y);
+int launch_scale_rows32(cudaStream_t st, int32_t s, int32_t n, const F32Vals &q, const double *X, double *Y);
+int launch_scale_rows32(cudaStream_t st, int32_t s, int32_t n, const F32Vals &q, const float *X, double *Y);
+// dst[i] = src[i] rounded to FP32
+int launch_round_f32(cudaStream_t st, int64_t count, const double *src, float *dst);
 int launch_pack(cudaStream_t st, int32_t s, int32_t n, const double *src, int64_t ld, double *dst);
 // Y[r][c] = q[r] X[r][c] (a diagonal factor; q FP64, FP32 or BF16 bits, one of them given)
 int launch_scale_rows(cudaStream_t st, int32_t s, int32_t n, const double *q, const float *q32, const uint16_t *q16,

@@ -269,7 +269,9 @@ Take take(spai_server_s *S, int k, Job *job)
         } else {
             factor = build_estimate(S, y) + analysis_transient(y);
         }
-        const size_t ws = spai_solve_workspace_size(y.n, q->r.nrhs, S->o.restart);
+        // the mixed-precision solve adds A's values in FP32 to the workspace
+        const size_t ws = spai_solve_workspace_size(y.n, q->r.nrhs, S->o.restart) +
+                          (S->o.precision == SPAI_SOLVE_MIXED ? ((size_t)y.nnz * 4 + 255) / 256 * 256 : 0);
         const size_t a_need = round256((size_t)y.nnz * 8), x_need = round256((size_t)y.n * q->r.nrhs * 8);
         // a growing buffer is freed before it is allocated again: only the difference counts
         auto grow = [](size_t want, size_t cap) { return want > cap ? want - cap : 0; };
@@ -383,7 +385,7 @@ int run(spai_server_s *S, int k, const Job &job, spai_pc *built, std::string *ms
         *msg = cudaGetErrorString(ce);
         st = SPAI_ECUDA;
     }
-    spai_solve_opts so{S->o.restart, S->o.max_cycles, S->o.tol, S->o.orth, 0};
+    spai_solve_opts so{S->o.restart, S->o.max_cycles, S->o.tol, S->o.orth, S->o.precision};
     spai_solve_info info{};
     if (!st) {
         st = block_solve(ctx, &A, pc, s, q->r.B, n, sl.X, n, &so, &info, nullptr);
@@ -471,7 +473,8 @@ extern "C" spai_status spai_server_create(const spai_server_opts *opts, spai_ser
     if (opts->slots < 1 || opts->slots > 64 || opts->restart < 1 || opts->max_cycles < 1 || !(opts->tol >= 0.0) ||
         !(opts->radius >= 0.0) || (kind != SPAI_PATTERN_A && kind != SPAI_PATTERN_A2) ||
         (opts->pattern_kind & ~(kPrecBits | 1)) || (opts->pattern_kind & kPrecBits) == kPrecBits ||
-        opts->orth < SPAI_ORTH_AUTO || opts->orth > SPAI_ORTH_TENSOR)
+        opts->orth < SPAI_ORTH_AUTO || opts->orth > SPAI_ORTH_TENSOR ||
+        (opts->precision != SPAI_SOLVE_FP64 && opts->precision != SPAI_SOLVE_MIXED) || opts->reserved != 0)
         return SPAI_EINVAL;
     spai_server_s *S = new spai_server_s();
     S->o = *opts;

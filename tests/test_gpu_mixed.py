@@ -206,3 +206,142 @@ def test_fp32_and_bf16_flags_are_exclusive():
         with pytest.raises(sg.SpaiError) as e:
             sg.spai_build(ctx, dev_csr(A, w.n), sg.PATTERN_A | sg.PREC_FP32 | sg.PREC_BF16)
         assert e.value.status == sg.SPAI_EINVAL
+
+
+# ----------------------------------------------------------------------------- FP32 operator
+U32 = 2.0 ** -24
+
+
+def _abs_csr(A):
+    return (A[0], A[1], np.abs(A[2]))
+
+
+@pytest.mark.parametrize("case", ["3d-12-7pt", "3d-6-27pt", "random200"])
+@pytest.mark.parametrize("s", [1, 2, 4, 8, 16])
+def test_spmm_fp32_within_its_rounding_bound(case, s):
+    """Y = A X with A's values and X rounded to FP32 and k products summed in FP32 (k the
+    row's nonzeros): every entry is within (k + 2) u32 (|A| |X|) of the exact FP64 product
+    (two input roundings and k multiply-add roundings, u32 = 2^-24)."""
+    import torch
+    sg = _sg()
+    if case == "3d-12-7pt":
+        w = synth.grid3d_7pt(side=12, nparams=2)
+        A, n = oracle.assemble(w.terms, oracle.coefficients(0.5, 1.0), w.n), w.n
+    elif case == "3d-6-27pt":
+        w = synth.grid3d_27pt(side=6, nparams=2)
+        A, n = oracle.assemble(w.terms, oracle.coefficients(0.5, 1.0), w.n), w.n
+    else:
+        n = 200
+        A, _ = synth.random_sparse(n, 0.05, seed=3)
+    X = np.asfortranarray(np.random.default_rng(s).standard_normal((n, s)))
+    ref = oracle.spmm(A, X, n)
+    mag = oracle.spmm(_abs_csr(A), np.abs(X), n)
+    k = np.diff(A[0]).astype(np.float64)[:, None]
+    ld = n + 5
+    with context() as ctx:
+        Xd = torch.zeros((s, ld), dtype=torch.float64, device="cuda:0")
+        Xd[:, :n] = torch.as_tensor(X.T)
+        Yd = torch.full((s, ld), 3.0, dtype=torch.float64, device="cuda:0")
+        sg.spai_spmm_fp32(ctx, dev_csr(A, n), s, Xd, ld, Yd, ld)
+        sg.spai_ctx_sync(ctx)
+        Y = Yd.cpu().numpy()
+    got = Y[:, :n].T
+    assert np.all(Y[:, n:] == 3.0)
+    err = np.abs(got - ref)
+    bound = 1.001 * (k + 2) * U32 * mag
+    assert np.all(err <= bound), float(np.max(err / np.maximum(bound, 1e-300)))
+    # it is an FP32 computation: not all entries equal the FP64 product
+    assert np.max(err / np.maximum(mag, 1e-300)) > 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp64"])
+def test_pc_apply_fp32_chain_within_its_rounding_bound(prec):
+    """The FP32 apply of a factored update Q_2 (P_1 X) (values as stored, X and the FP32
+    intermediate rounded once each, FP32 sums): within (kP + kQ + 4) u32 |Q_2| (|P_1| |X|) of
+    the exact product of the stored factors, computed here from their exported values."""
+    import torch
+    sg = _sg()
+    w = synth.grid3d_7pt(side=11, nparams=3)
+    n = w.n
+    As = [oracle.assemble(w.terms, oracle.coefficients(p, 1.0), n) for p in (0.2, 0.7)]
+    flag = {"fp32": sg.PREC_FP32, "bf16": sg.PREC_BF16, "fp64": 0}[prec]
+    s = 8
+    X = np.asfortranarray(np.random.default_rng(9).standard_normal((n, s)))
+    with context() as ctx:
+        Ad = [dev_csr(A, n) for A in As]
+        p1, _ = sg.spai_build(ctx, Ad[0], sg.PATTERN_A | flag)
+        q2, _ = sg.spai_update(ctx, p1, Ad[1], sg.UPDATE_FIRST | flag)
+        g1, g2 = export(ctx, p1), export(ctx, q2)
+        Xd = torch.as_tensor(np.ascontiguousarray(X.T), device="cuda:0")
+        Yd = torch.zeros((s, n), dtype=torch.float64, device="cuda:0")
+        sg.spai_pc_apply_fp32(ctx, q2, s, Xd, n, Yd, n)
+        sg.spai_ctx_sync(ctx)
+        got = Yd.cpu().numpy().T
+        sg.spai_pc_destroy(q2)
+        sg.spai_pc_destroy(p1)
+
+    def csc_to_csr(g):  # exported column-order factor -> CSR triplet of the same matrix
+        cols = np.repeat(np.arange(n), np.diff(g["Jptr"]))
+        order = np.lexsort((cols, g["Jind"]))
+        rp = np.zeros(n + 1, np.int32)
+        np.add.at(rp, g["Jind"] + 1, 1)
+        return (np.cumsum(rp).astype(np.int32), cols[order].astype(np.int32), g["val"][order])
+
+    P1, Q2 = csc_to_csr(g1), csc_to_csr(g2)
+    ref = oracle.spmm(Q2, oracle.spmm(P1, X, n), n)
+    mag = oracle.spmm(_abs_csr(Q2), oracle.spmm(_abs_csr(P1), np.abs(X), n), n)
+    kk = float(np.diff(P1[0]).max() + np.diff(Q2[0]).max() + 4)
+    err = np.abs(got - ref)
+    assert np.all(err <= 1.001 * kk * U32 * mag), float(np.max(err / np.maximum(kk * U32 * mag, 1e-300)))
+
+
+def _mixed_cases():
+    return [("2d-32", 4, 0, 1), ("3d-16-7pt", 8, 1, 1), ("3d-16-7pt", 1, 1, 0), ("3d-14-7pt", 16, 2, 1),
+            ("3d-9-27pt", 8, 1, 1)]
+
+
+@pytest.mark.parametrize("name,s,factor,update", _mixed_cases(),
+                         ids=[f"{c[0]}-s{c[1]}-f{c[2]}-u{c[3]}" for c in _mixed_cases()])
+def test_mixed_solve_reaches_fp64_tolerance(name, s, factor, update):
+    """SPAI_SOLVE_MIXED: the operator A P in FP32 inside each cycle, FP64 basis, Gram-Schmidt,
+    least squares and true residual, FP64 refinement across cycles.  Every column's true
+    residual (recomputed here in FP64) meets tol 1e-8, and the solution is within 1e-6 of the
+    oracle's all-FP64 solve; factors FP64 (0), FP32 (1) or BF16 (2), built or updated."""
+    sg = _sg()
+    if name == "2d-32":
+        w = synth.plain_2d_32()
+    elif name == "3d-9-27pt":
+        w = synth.grid3d_27pt(side=9, nparams=3, nrhs=s)
+    else:
+        w = synth.grid3d_7pt(side=int(name.split("-")[1]), nparams=3, nrhs=max(s, 1), seed=5)
+    n = w.n
+    B = np.asfortranarray(w.B[:, :s])
+    As = [oracle.assemble(w.terms, oracle.coefficients(p, 1.0), n) for p in w.params[:2]]
+    Af = As[1] if update else As[0]
+    P1 = oracle.spai_build(As[0], n)
+    Pref = oracle.spai_update(P1, As[1], n) if update else P1
+    Xo, io = oracle.block_gmres(oracle.csr_apply(Af, n), Pref.apply, B, 30, 1e-8, 50)
+    flag = {0: 0, 1: sg.PREC_FP32, 2: sg.PREC_BF16}[factor]
+    with context() as ctx:
+        Ad = [dev_csr(A, n) for A in As]
+        pc1, _ = sg.spai_build(ctx, Ad[0], sg.PATTERN_A | flag)
+        pc = sg.spai_update(ctx, pc1, Ad[1], sg.UPDATE_FIRST | flag)[0] if update else pc1
+        res = {}
+        for precision in (sg.SOLVE_FP64, sg.SOLVE_MIXED):
+            X = np.zeros((n, s), order="F")
+            st, info, rel = sg.block_solve(ctx, Ad[1] if update else Ad[0], pc, s, B, n, X, n, 30, 1e-8, 50,
+                                           precision=precision)
+            res[precision] = (X, info)
+        if update:
+            sg.spai_pc_destroy(pc)
+        sg.spai_pc_destroy(pc1)
+    for precision, (X, info) in res.items():
+        assert info["converged"]
+        true_rel = np.linalg.norm(B - oracle.spmm(Af, X, n), axis=0) / np.linalg.norm(B, axis=0)
+        sol = np.linalg.norm(X - Xo) / np.linalg.norm(Xo)
+        print(f"{name} s={s} factor={factor} update={update} "
+              f"{'mixed' if precision else 'fp64'}: {info['iterations']} iterations in {info['cycles']} cycles "
+              f"(oracle {io['iterations']}), max true residual {true_rel.max():.2e}, "
+              f"solution error vs FP64 oracle {sol:.2e}")
+        assert np.all(true_rel <= 1e-8)
+        assert sol <= 1e-6
