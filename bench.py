@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-fifo-seconds", type=float, default=2.0)
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-rates", default="400,800", help="further offered rates of the serving workload")
+    ap.add_argument("--serve-rate-seconds", type=float, default=5.0)
+    ap.add_argument("--no-served-sweep", action="store_true")
     # large workload: 3D 128^3 27-point grid, 16 RHS, BF16-stored SPAI, update vs rebuild
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--large-only", action="store_true")
@@ -343,23 +346,81 @@ def oracle_sample(side, nparams, nsys, seed=0):
     return nsys / dt, dt, iters
 
 
-def cpu_baseline(side, nparams, nsys):
-    """Run the oracle sample in a fresh interpreter (all host cores for BLAS)."""
-    cores = os.cpu_count() or 1
-    env = dict(os.environ, OMP_NUM_THREADS=str(cores), OPENBLAS_NUM_THREADS=str(cores))
-    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
-            "v, dt, it = bench.oracle_sample(%d, %d, %d); print(json.dumps([v, dt, it]))"
-            % (ROOT, side, nparams, nsys))
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                       timeout=900)
-    if r.returncode != 0:
-        return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle",
-                "sample": f"failed: {r.stderr.strip()[-200:]}"}
-    v, dt, it = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {nsys} systems of the sweep (s=0.5: SPAI build + solve, then update + "
-                      f"solve), same n and RHS, {dt:.1f} s wall, {it} GMRES iterations; FP64 C "
-                      f"(SPAI, sparse products) + numpy/BLAS (block GMRES) with {cores} BLAS threads"}
+_ORACLE_W = {}
+
+
+def _oracle_system(job):
+    """One system of the sweep on the oracle, in a single-threaded worker process:
+    assemble A(p, s), SPAI build, right-preconditioned block GMRES to the tolerance.
+    Returns (seconds, iterations); the workload is generated once per process."""
+    import oracle
+    import synth
+    side, nparams, si, pi = job
+    key = (side, nparams)
+    if key not in _ORACLE_W:
+        _ORACLE_W[key] = synth.grid3d_7pt(side=side, nparams=nparams)
+    w = _ORACLE_W[key]
+    n = w.n
+    t0 = time.perf_counter()
+    A = oracle.assemble(w.terms, oracle.coefficients(w.params[pi], w.shifts[si]), n)
+    P = oracle.spai_build(A, n)
+    X, info = oracle.block_gmres(oracle.csr_apply(A, n), P.apply, w.B, w.restart, w.tol, 50)
+    assert info["converged"]
+    return time.perf_counter() - t0, info["iterations"]
+
+
+class OraclePool:
+    """One single-threaded oracle process per host core (spawned: no CUDA state is
+    inherited), each solving whole systems of the sweep; `cores` is the number of processes,
+    each with one BLAS / OpenMP thread."""
+
+    def __init__(self, side, nparams):
+        import multiprocessing as mp
+        self.cores = os.cpu_count() or 1
+        self.side, self.nparams = side, nparams
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.cores)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.round = 0
+
+    def run_round(self):
+        """Every process solves one system (shift k % 3, parameter (round + k) % nparams)."""
+        jobs = [(self.side, self.nparams, k % 3, (self.round + k) % self.nparams) for k in range(self.cores)]
+        self.round += 1
+        t0 = time.perf_counter()
+        out = self.pool.map(_oracle_system, jobs, chunksize=1)
+        return time.perf_counter() - t0, out
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline(side, nparams):
+    """The oracle on all host cores: one warm-up round (each process generates the workload),
+    then one timed round of one solve per process; solves / wall time of the round."""
+    try:
+        pool = OraclePool(side, nparams)
+        pool.run_round()
+        wall, out = pool.run_round()
+        pool.close()
+    except Exception as e:  # the baseline is reported, never required
+        return {"value": None, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+                "sample": f"failed: {str(e)[-200:]}"}
+    its = [o[1] for o in out]
+    return {"value": len(out) / wall, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+            "sample": f"{len(out)} systems of the sweep at once (shifts and parameters spread over the "
+                      f"processes), each assemble + SPAI build + block GMRES(50) to 1e-8 in its own "
+                      f"single-threaded process, one per host core; {wall:.1f} s wall; GMRES iterations "
+                      f"{min(its)}-{max(its)}; FP64 C (SPAI, sparse products) + numpy (block GMRES)"}
 
 
 def run_reference(args, rank, world):
@@ -367,24 +428,27 @@ def run_reference(args, rank, world):
         return
     import synth
     w = synth.grid3d_7pt(side=args.side, nparams=args.nparams)
-    cores = os.cpu_count() or 1
-    for _ in range(args.warmup):
-        oracle_sample(args.side, args.nparams, 1)
-    times = []
+    pool = OraclePool(args.side, args.nparams)
+    pool.run_round()  # generates the workload in every process
+    for _ in range(max(0, args.warmup - 1)):
+        pool.run_round()
+    total, solves = 0.0, 0
     for _ in range(args.steps):
-        _, dt, it = oracle_sample(args.side, args.nparams, 1)
-        times.append(dt)
-    total = sum(times)
-    value = args.steps / total
+        dt, out = pool.run_round()
+        total += dt
+        solves += len(out)
+    pool.close()
+    value = solves / total
     nnz = 7 * w.n - 6 * w.dims[0] ** 2
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": workload_config(w, nnz),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": "each step: system 1 of the sweep (s=0.5, first p): assemble, "
-                                   "SPAI build, block GMRES(50) to 1e-8, on the host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+                         "sample": f"each step: {pool.cores} systems of the sweep at once, one per "
+                                   f"single-threaded oracle process (one per host core): assemble, SPAI "
+                                   f"build, block GMRES(50) to 1e-8"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -460,7 +524,7 @@ def run_serving(args, sg, torch):
     trace = synth.serving_trace(args.serve_rate, args.serve_seconds, len(systems))
     common = dict(restart=30, max_cycles=100, tol=1e-8)
     served = dict(slots=args.serve_slots, reuse=True, radius=0.05, pattern_kind=sg.PREC_FP32,
-                  mem_budget=40 << 30, **common)
+                  mem_budget=40 << 30, precision=sg.SOLVE_MIXED, **common)
     # warm-up on a discarded server (module load, allocator pools); the timed server starts cold
     serve_trace(sg, torch, systems, Bs, [(0.0, i, 0.5, 1.0, 8) for i in range(len(systems))], **served)
     res, st = serve_trace(sg, torch, systems, Bs, trace, **served)
@@ -469,17 +533,75 @@ def run_serving(args, sg, torch):
     res_f, st_f = serve_trace(sg, torch, systems, Bs, fifo_trace, slots=1, reuse=False, mem_budget=40 << 30,
                               **common)
     fifo = serving_summary(res_f, st_f, None)
+    # offered rates above the first: where does the server stop keeping up?
+    rate_sweep = []
+    for rate in [float(x) for x in args.serve_rates.split(",") if x]:
+        tr = synth.serving_trace(rate, args.serve_rate_seconds, len(systems))
+        r_, s_ = serve_trace(sg, torch, systems, Bs, tr, **served)
+        sm = serving_summary(r_, s_, None)
+        rate_sweep.append({"offered": rate, "requests": sm["requests"], "served": round(sm["value"], 1),
+                           "p50_ms": sm["latency_ms"]["p50"], "p99_ms": sm["latency_ms"]["p99"],
+                           "routes": sm["routes"]})
     nbar = float(np.mean([systems[sy].n for _, sy, _, _, _ in trace]))
     return {
         "workload": f"Poisson {args.serve_rate:g} req/s for {args.serve_seconds:g} s over 16 3D 7-point grids "
                     f"(sides {synth.SERVE_SIDES[0]}-{synth.SERVE_SIDES[-1]}, mean n of the requests {nbar:.0f}); 70 % within "
                     f"0.05 of a served p; s in {{0.5,1,2}}; nrhs in {{1,4,8}}; block GMRES(30) to 1e-8; "
                     f"40 GB budget; solutions returned to host memory",
-        "served": {**out, "slots": args.serve_slots, "factors": "f32 (FP64 solve)", "reuse_radius": 0.05},
+        "served": {**out, "slots": args.serve_slots, "factors": "f32", "solve": "mixed (f32 operator, f64 refinement)",
+                   "reuse_radius": 0.05},
+        "rate_sweep": rate_sweep,
         "fifo_plain_fp64": {**fifo, "slots": 1, "factors": "f64", "reuse": False,
                             "trace": f"the first {args.serve_fifo_seconds:g} s of the same arrivals"},
         "served_over_fifo": out["value"] / fifo["value"] if fifo["value"] else None,
     }
+
+
+def run_served_sweep(args, sg, torch, w, steps, warmup=1):
+    """The headline sweep's systems (every p at every s, 8 right-hand sides) submitted to the
+    server all at once, a closed loop at saturation: served capacity = solves / makespan
+    (first submit to last completion, device-resident B and X).  The server runs the served
+    form -- FP32 factors, the FP32 operator with FP64 refinement, one build per shift cached
+    and every other parameter routed to an update from it (radius covering the sweep's p
+    range, as the plain sweep's one build per shift) -- on `slots` = bench workers."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = w.n
+    d_terms = [tuple(torch.as_tensor(np.ascontiguousarray(a), device=dev) for a in t) for t in w.terms]
+    B = torch.as_tensor(np.ascontiguousarray(w.B.T), device=dev)  # (8, n): column-major n x 8
+    reqs = [(p, s) for s in w.shifts for p in w.params]
+    Xs = [torch.empty((int(w.B.shape[1]), n), dtype=torch.float64, device=dev) for _ in reqs]
+    opts = dict(slots=args.workers, reuse=True, radius=1.0, pattern_kind=sg.PATTERN_A | sg.PREC_FP32,
+                restart=w.restart, max_cycles=50, tol=w.tol, precision=sg.SOLVE_MIXED)
+    spans, lats, iters, routes = [], [], [], {"build": 0, "update": 0, "reuse": 0}
+    for it in range(warmup + steps):
+        srv = sg.spai_server_create(**opts)
+        try:
+            sid = sg.spai_server_add_shifted_system(srv, [sg.csr(n, *t) for t in d_terms], w.alpha, w.beta)
+            torch.cuda.synchronize()
+            t0 = sg.spai_server_clock(srv)
+            tickets = [sg.spai_server_submit(srv, sid, int(w.B.shape[1]), p, s, None, B, X, t_arrival=t0)
+                       for (p, s), X in zip(reqs, Xs)]
+            res = [sg.spai_server_wait(srv, tk) for tk in tickets]
+        finally:
+            sg.spai_server_destroy(srv)
+        bad = [r for r in res if r["status"] != 0]
+        if bad:
+            raise RuntimeError(f"served sweep: {len(bad)} requests failed: {bad[0]}")
+        if it < warmup:
+            continue
+        spans.append(max(r["t_done"] for r in res) - t0)
+        lats.extend(r["t_done"] - r["t_arrival"] for r in res)
+        iters.extend(r["iterations"] for r in res)
+        for r in res:
+            routes[("build", "update", "reuse")[r["route"]]] += 1
+    lat = np.array(lats)
+    return {"value": len(reqs) * steps / sum(spans), "unit": UNIT, "steps": steps,
+            "ms_per_step": 1e3 * sum(spans) / steps,
+            "latency_ms": {"p50": round(1e3 * float(np.percentile(lat, 50)), 2),
+                           "p99": round(1e3 * float(np.percentile(lat, 99)), 2)},
+            "gmres_iterations_mean": float(np.mean(iters)), "routes": routes, "slots": args.workers,
+            "form": "server, FP32 factors, FP32 operator + FP64 refinement, one cached build per shift "
+                    "and updates from it, all 60 requests at once (closed loop)"}
 
 
 # ------------------------------------------------------------------------------- batched
@@ -860,9 +982,10 @@ class Sweep:
     `workers` host threads, each with its own stream and context, take them round-robin
     while the main context builds the bases."""
 
-    def __init__(self, sg, torch, ctx, w, host_inputs=False, workers=1, prec=0, warm=False):
+    def __init__(self, sg, torch, ctx, w, host_inputs=False, workers=1, prec=0, warm=False, solve_precision=0):
         self.sg, self.torch, self.ctx, self.w = sg, torch, ctx, w
         self.prec = prec  # 0: FP64 factors; sg.PREC_FP32: FP32 least squares and factors
+        self.solve_precision = solve_precision  # sg.SOLVE_MIXED: FP32 operator, FP64 refinement
         # warm: a worker starts each solve from its previous solution of the same shift (all
         # systems share B, and neighbouring parameters have close solutions)
         self.warm = warm
@@ -894,6 +1017,7 @@ class Sweep:
             self.pool = ThreadPoolExecutor(max_workers=workers)
         self.solves = 0
         self.iters = []
+        self.cycles = []
         self.errors = []
 
     def close(self):
@@ -937,12 +1061,13 @@ class Sweep:
                     wk.X.zero_()
             prev_si = si
             st, info, rel = sg.block_solve(wk.ctx, A, pc, self.s, self.B, n, wk.X, n,
-                                           w.restart, w.tol, 50)
+                                           w.restart, w.tol, 50, precision=self.solve_precision)
             if i > 0:
                 sg.spai_pc_destroy(pc)
             if not info["converged"]:
                 raise RuntimeError(f"solve did not converge: p={w.params[i]} s={s} {info}")
             out.append(info["iterations"])
+            self.cycles.append(info["cycles"])
         return out
 
     def step(self):
@@ -1030,7 +1155,7 @@ def main():
     # CPU baseline first, before any CUDA work in this process
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.side, args.nparams, 2)
+        cpu = cpu_baseline(args.side, args.nparams)
 
     import torch
     import paper_1809_06574_gb300 as sg
@@ -1096,20 +1221,19 @@ def main():
     t_max, total_solves = aggregate_replicas(dist, torch, "cuda", t_local, solves)
     value = total_solves / t_max
 
-    # the same sweep with FP32 SPAI factors (SPAI_PREC_FP32: FP32 least squares and factor
-    # storage, FP64 apply arithmetic, FP64 solve and true residuals to the same tolerance)
-    mixed = None
-    if not args.no_mixed:
-        ms_ = Sweep(sg, torch, ctx, w, workers=args.workers, prec=sg.PREC_FP32)
+    def timed_sweep(**kw):
+        """The sweep of the headline with other factor / solve precisions: warm-up, then the
+        same number of timed steps (device events, max over ranks)."""
+        sw = Sweep(sg, torch, ctx, w, workers=args.workers, **kw)
         for _ in range(max(1, args.warmup)):
-            ms_.step()
-        ms_.solves, ms_.iters = 0, []
+            sw.step()
+        sw.solves, sw.iters, sw.cycles = 0, [], []
         barrier()
         m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         m0.record(stream)
         for _ in range(args.steps):
-            ms_.step()
-        for wk in ms_.workers:
+            sw.step()
+        for wk in sw.workers:
             ev = torch.cuda.Event()
             ev.record(wk.stream)
             stream.wait_event(ev)
@@ -1120,41 +1244,35 @@ def main():
             t = torch.tensor([mt], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             mt = t.item()
-        mixed = {"value": ms_.solves * world / mt, "unit": UNIT, "ms_per_step": 1e3 * mt / args.steps,
-                 "dtype": "f64 solve (Gram-Schmidt f64-accurate on tensor cores), f32 SPAI factors",
-                 "gmres_iterations": {"mean": float(np.mean(ms_.iters)), "min": int(min(ms_.iters)),
-                                      "max": int(max(ms_.iters))},
-                 "note": "same sweep and true-residual tolerance; SPAI build/update solved and stored in "
-                         "FP32, applied with FP64 products and sums"}
-        ms_.close()
+        out = {"value": sw.solves * world / mt, "unit": UNIT, "ms_per_step": 1e3 * mt / args.steps,
+               "gmres_iterations": {"mean": float(np.mean(sw.iters)), "min": int(min(sw.iters)),
+                                    "max": int(max(sw.iters))},
+               "cycles": {"mean": float(np.mean(sw.cycles)), "max": int(max(sw.cycles))}}
+        sw.close()
+        return out
+
+    # the sweep in mixed precision (north star (1)): SPAI build / update in FP32 with FP32
+    # factors, the operator A P applied in FP32 inside each restart cycle, FP64 basis,
+    # Gram-Schmidt, projected least squares and true residual, FP64 refinement across cycles
+    mixed = None
+    fp32_factors = None
+    if not args.no_mixed:
+        mixed = timed_sweep(prec=sg.PREC_FP32, solve_precision=sg.SOLVE_MIXED)
+        mixed.update({"dtype": "f32 SPAI factors and f32 operator products, f64 basis/Gram-Schmidt/"
+                               "least squares/true residual (iterative refinement)",
+                      "vs_plain_fp64": None})
+        fp32_factors = timed_sweep(prec=sg.PREC_FP32)
+        fp32_factors["note"] = ("FP32 SPAI factors applied with FP64 products and sums, FP64 solve: the "
+                                "factor precision alone")
 
     # the same FP64 sweep with each solve started from the worker's previous solution of
     # the same shift (every system has the same B; neighbouring p have close solutions):
     # same true-residual tolerance, fewer iterations
     warm = None
     if not args.no_mixed:
-        ws_ = Sweep(sg, torch, ctx, w, workers=args.workers, warm=True)
-        for _ in range(max(1, args.warmup)):
-            ws_.step()
-        ws_.solves, ws_.iters = 0, []
-        barrier()
-        m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        m0.record(stream)
-        for _ in range(args.steps):
-            ws_.step()
-        for wk in ws_.workers:
-            ev = torch.cuda.Event()
-            ev.record(wk.stream)
-            stream.wait_event(ev)
-        m1.record(stream)
-        barrier()
-        mt = m0.elapsed_time(m1) / 1e3
-        warm = {"value": ws_.solves * world / mt, "unit": UNIT, "ms_per_step": 1e3 * mt / args.steps,
-                "gmres_iterations": {"mean": float(np.mean(ws_.iters)), "min": int(min(ws_.iters)),
-                                     "max": int(max(ws_.iters))},
-                "note": "FP64 as the headline; each solve's initial guess is the same worker's previous "
-                        "solution of the same shift (the workers take every 4th parameter), not zero"}
-        ws_.close()
+        warm = timed_sweep(warm=True)
+        warm["note"] = ("FP64 as the headline; each solve's initial guess is the same worker's previous "
+                        "solution of the same shift (the workers take every 4th parameter), not zero")
 
     # the dominant kernels once more with one solve at a time (no other stream sharing the
     # GPU): their own speed, beside the timed region's contended launch durations
@@ -1201,6 +1319,13 @@ def main():
     batched = None
     if rank == 0 and world == 1 and not args.no_batched:
         batched = run_batched(args, sg, torch)
+    # the headline's sweep through the server at saturation, beside the plain FP64 sweep
+    served_cap = None
+    if rank == 0 and world == 1 and not args.no_served_sweep:
+        served_cap = run_served_sweep(args, sg, torch, w, args.steps)
+        served_cap["vs_plain_fp64"] = served_cap["value"] / value
+    if mixed is not None:
+        mixed["vs_plain_fp64"] = mixed["value"] / value
     # served (continuous admission, update routing, FP32 factors) vs FIFO plain FP64
     serving = None
     if rank == 0 and world == 1 and not args.no_serve:
@@ -1231,6 +1356,8 @@ def main():
                 "tflops": round(f["flops"] / (f["ms"] * 1e-3) / 1e12, 4) if f["ms"] else 0,
                 "gbs": round(f["bytes"] / (f["ms"] * 1e-3) / 1e9, 1) if f["ms"] else 0,
                 "bound": r["bound"], "frac": None if r["frac"] is None else round(r["frac"], 4)}
+        # order: the contract's keys, then the detail, then (at the end of the line, where a
+        # truncated log still shows them) the comparisons the workload is about
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
@@ -1238,10 +1365,7 @@ def main():
             "data": "synthetic", "config": {**workload_config(w, nnz_expected),
                                             "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                                             "workers": args.workers},
-            "roofline": roofline, "roofline_isolated": roofline_iso, "mixed_precision": mixed,
-            "warm_start": warm, "block_vs_single_rhs": bvs, "update_order": order, "adaptive": adaptive,
-            "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "large": large, "batched": batched, "gpu_launches": int(launches),
-            "clocks": clk, "fp64_tflops_measured": fp64_tflops,
+            "gpu_launches": int(launches), "clocks": clk, "fp64_tflops_measured": fp64_tflops,
             "gmres_iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)),
                                  "max": int(max(iters))},
             "kernels": kernels,
@@ -1249,6 +1373,10 @@ def main():
             # by the kernel family that followed
             "idle_ms": {"total": round(sum(v for _, v in idle), 3),
                         **{k: round(v, 3) for k, v in idle[:8]}},
+            "large": large, "batched": batched, "adaptive": adaptive, "update_order": order,
+            "block_vs_single_rhs": bvs, "warm_start": warm, "fp32_factors": fp32_factors, "serving": serving,
+            "cpu_baseline": cpu, "e2e": e2e, "roofline": roofline, "roofline_isolated": roofline_iso,
+            "mixed_precision": mixed, "served_capacity": served_cap,
         }
         print(json.dumps(line), flush=True)
     sweep.close()
