@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(kThreads) k_trsm_rows(int32_t n, const double 
 //   k_gram_rows:  partial[chunk] of G = W^T W
 //   k_trsm_gram:  Q1 = W R^{-1} written, and partial[chunk] of G2 = Q1^T Q1, one pass
 // ---------------------------------------------------------------------------------
-template <int S, bool SOLVE>
+template <int S, bool SOLVE, bool STORE = SOLVE>
 __device__ __forceinline__ void gram_tiles(int64_t r0, int64_t r1, const double *__restrict__ W, const double *Rs,
                                            const double *rinv, double *__restrict__ Q1,
                                            double *__restrict__ partial_chunk)
@@ -303,7 +303,7 @@ __device__ __forceinline__ void gram_tiles(int64_t r0, int64_t r1, const double 
             row_load<S>(W, t0 + threadIdx.x, x);
             if constexpr (SOLVE) {
                 trsm_row<S>(x, Rs, rinv);
-                row_store<S>(Q1, t0 + threadIdx.x, x);
+                if constexpr (STORE) row_store<S>(Q1, t0 + threadIdx.x, x);
             }
 #pragma unroll
             for (int k = 0; k < S; ++k) tile[threadIdx.x * LD + k] = x[k];
@@ -353,6 +353,159 @@ __global__ void __launch_bounds__(kThreads) k_trsm_gram(int32_t n, const double 
     int64_t r0, r1;
     chunk_rows(n, blockIdx.x, gridDim.x, r0, r1);
     gram_tiles<S, true>(r0, r1, W, Rs, rinv, Q1, partial + (int64_t)blockIdx.x * S * S);
+}
+
+// out = R2 R1 of two upper triangular S x S factors (threads < S * S)
+template <int S>
+__device__ __forceinline__ void triu_mul_body(const double *__restrict__ R2, const double *__restrict__ R1,
+                                              double *__restrict__ out)
+{
+    const int a = threadIdx.x / S, b = threadIdx.x % S;
+    if (threadIdx.x >= S * S) return;
+    double acc = 0.0;
+    for (int c = a; c <= b; ++c) acc = fma(R2[a * S + c], R1[c * S + b], acc);
+    out[a * S + b] = acc;
+}
+
+// ---------------------------------------------------------------------------------
+// Cholesky-QR of an n x S block (S <= 8) in three launches, the small work of each pass
+// done by its last CTA: every CTA writes its chunk's partial sums, then takes a ticket;
+// the CTA with the last ticket adds all partials in chunk order (thread group q over the
+// fixed chunk range q, then the groups in order: the same sums whichever CTA is last),
+// does the pass's small dense step and resets the ticket for the next launch.
+//   k_cqr_gram:   G1 = W^T W; last CTA: R1 = chol(G1) with deflation against ref2
+//   k_cqr_gram2:  rows W R1^{-1} (in registers, not stored), G2 = their Gram; last CTA:
+//                 R2 = chol(G2), R = R2 R1
+//   k_cqr_apply:  Q = (W R1^{-1}) R2^{-1} (the same row operations as storing W R1^{-1}
+//                 first, so the same bits)
+//   k_colnorm2_t: column norms^2, the last CTA adds the partials
+// ---------------------------------------------------------------------------------
+template <int NE>
+__device__ bool last_cta_sum(const double *partial, unsigned *ticket, double *out)
+{
+    constexpr int NG = kThreads / NE;
+    static_assert(NG * NE == kThreads, "entries divide the block");
+    __shared__ unsigned s_last;
+    __shared__ double red[kThreads];
+    __syncthreads();  // this CTA's partial is written
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    const int chunks = gridDim.x;
+    const int e = threadIdx.x % NE, q = threadIdx.x / NE;
+    const int c0 = (int)((int64_t)chunks * q / NG), c1 = (int)((int64_t)chunks * (q + 1) / NG);
+    double acc = 0.0;
+    for (int c = c0; c < c1; ++c) acc += __ldcg(partial + (int64_t)c * NE + e);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < NE) {
+        double v = red[threadIdx.x];
+        for (int h = 1; h < NG; ++h) v += red[h * NE + threadIdx.x];
+        out[threadIdx.x] = v;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+    __syncthreads();
+    return true;
+}
+
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_cqr_gram(int32_t n, const double *__restrict__ W,
+                                                       const double *__restrict__ ref2, double tau2,
+                                                       double *__restrict__ partial, unsigned *__restrict__ ticket,
+                                                       double *__restrict__ R1, int32_t *__restrict__ defl1)
+{
+    __shared__ double G[S * S];
+    int64_t r0, r1;
+    chunk_rows(n, blockIdx.x, gridDim.x, r0, r1);
+    gram_tiles<S, false>(r0, r1, W, nullptr, nullptr, nullptr, partial + (int64_t)blockIdx.x * S * S);
+    if (!last_cta_sum<S * S>(partial, ticket, G)) return;
+    if (threadIdx.x < 32) chol_small_body<S>(G, ref2, tau2, R1, defl1);
+}
+
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_cqr_gram2(int32_t n, const double *__restrict__ W,
+                                                        const double *__restrict__ R1,
+                                                        const int32_t *__restrict__ defl1,
+                                                        double *__restrict__ partial, unsigned *__restrict__ ticket,
+                                                        double *__restrict__ R2, int32_t *__restrict__ defl2,
+                                                        double *__restrict__ Rout)
+{
+    __shared__ double Rs[S * S];
+    __shared__ double rinv[S];
+    __shared__ double G[S * S];
+    for (int e = threadIdx.x; e < S * S; e += blockDim.x) Rs[e] = R1[e];
+    if (threadIdx.x < S) rinv[threadIdx.x] = defl1[threadIdx.x] ? 0.0 : 1.0 / R1[threadIdx.x * S + threadIdx.x];
+    __syncthreads();
+    int64_t r0, r1;
+    chunk_rows(n, blockIdx.x, gridDim.x, r0, r1);
+    gram_tiles<S, true, false>(r0, r1, W, Rs, rinv, nullptr, partial + (int64_t)blockIdx.x * S * S);
+    if (!last_cta_sum<S * S>(partial, ticket, G)) return;
+    if (threadIdx.x < 32) chol_small_body<S>(G, nullptr, 0.0, R2, defl2);
+    __syncthreads();  // R2 (global) written by warp 0
+    triu_mul_body<S>(R2, R1, Rout);
+}
+
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_cqr_apply(int32_t n, const double *W, const double *__restrict__ R1,
+                                                        const int32_t *__restrict__ defl1,
+                                                        const double *__restrict__ R2,
+                                                        const int32_t *__restrict__ defl2, double *Q)
+{
+    __shared__ double Rs1[S * S], Rs2[S * S];
+    __shared__ double rinv1[S], rinv2[S];
+    for (int e = threadIdx.x; e < S * S; e += blockDim.x) {
+        Rs1[e] = R1[e];
+        Rs2[e] = R2[e];
+    }
+    if (threadIdx.x < S) {
+        rinv1[threadIdx.x] = defl1[threadIdx.x] ? 0.0 : 1.0 / R1[threadIdx.x * S + threadIdx.x];
+        rinv2[threadIdx.x] = defl2[threadIdx.x] ? 0.0 : 1.0 / R2[threadIdx.x * S + threadIdx.x];
+    }
+    __syncthreads();
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double x[S];
+    row_load<S>(W, r, x);
+    trsm_row<S>(x, Rs1, rinv1);
+    trsm_row<S>(x, Rs2, rinv2);
+    row_store<S>(Q, r, x);
+}
+
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_colnorm2_t(int32_t n, const double *__restrict__ W,
+                                                         double *__restrict__ partial, unsigned *__restrict__ ticket,
+                                                         double *__restrict__ out)
+{
+    constexpr int RG = kThreads / S;
+    __shared__ double red[kThreads];
+    __shared__ double sums[S];
+    const int c = threadIdx.x % S, g = threadIdx.x / S;
+    int64_t r0, r1;
+    chunk_rows(n, blockIdx.x, gridDim.x, r0, r1);
+    double acc0 = 0.0, acc1 = 0.0;
+    int64_t r = r0 + g;
+    for (; r + RG < r1; r += 2 * RG) {
+        const double w0 = __ldg(W + r * S + c), w1 = __ldg(W + (r + RG) * S + c);
+        acc0 = fma(w0, w0, acc0);
+        acc1 = fma(w1, w1, acc1);
+    }
+    if (r < r1) {
+        const double w0 = __ldg(W + r * S + c);
+        acc0 = fma(w0, w0, acc0);
+    }
+    red[threadIdx.x] = acc0 + acc1;
+    __syncthreads();
+    for (int h = RG / 2; h > 0; h >>= 1) {
+        if (g < h) red[threadIdx.x] += red[threadIdx.x + h * S];
+        __syncthreads();
+    }
+    if (g == 0) partial[(int64_t)blockIdx.x * S + c] = red[c];
+    if (!last_cta_sum<S>(partial, ticket, sums)) return;
+    if (threadIdx.x < S) out[threadIdx.x] = sums[threadIdx.x];
 }
 
 // ---------------------------------------------------------------------------------
@@ -532,17 +685,6 @@ __global__ void k_pieces16(int32_t nb, double *__restrict__ H, double *__restric
     double *piece = (b < 8 ? HL : HR) + ((2 * i + (a >> 3)) * 8 + (a & 7)) * 8 + (b & 7);
     if (merge) H[g] = *piece;
     else *piece = H[g];
-}
-
-template <int S>
-__device__ __forceinline__ void triu_mul_body(const double *__restrict__ R2, const double *__restrict__ R1,
-                                              double *__restrict__ out)
-{
-    const int a = threadIdx.x / S, b = threadIdx.x % S;
-    if (threadIdx.x >= S * S) return;
-    double acc = 0.0;
-    for (int c = a; c <= b; ++c) acc = fma(R2[a * S + c], R1[c * S + b], acc);
-    out[a * S + b] = acc;
 }
 
 template <int S>
@@ -934,6 +1076,50 @@ int launch_gram_rows(cudaStream_t st, int32_t s, int32_t n, const double *W, dou
     const int count = s * s;
     k_reduce_chunks<<<(unsigned)(((int64_t)count * 32 + 255) / 256), 256, 0, st>>>(count, chunks, partial, out);
     return check_launch(2);
+}
+
+// row chunks of the fused Cholesky-QR and norm kernels: 256-row tiles, at most four CTAs
+// per SM (608 partials for the last CTA to add)
+int cqr_chunks(int32_t n)
+{
+    int64_t c = ((int64_t)n + 255) / 256;
+    if (c > 608) c = 608;
+    if (c < 1) c = 1;
+    return (int)c;
+}
+
+bool cqr_supported(int32_t s) { return s == 1 || s == 2 || s == 4 || s == 8; }
+
+int launch_cqr_gram(cudaStream_t st, int32_t s, int32_t n, const double *W, const double *ref2, double tau2,
+                    double *partial, unsigned *ticket, double *R1, int32_t *defl1)
+{
+    const int chunks = cqr_chunks(n);
+    SPAI_DISPATCH_S8(s, (k_cqr_gram<S><<<chunks, kThreads, 0, st>>>(n, W, ref2, tau2, partial, ticket, R1, defl1)));
+    return check_launch();
+}
+
+int launch_cqr_gram2(cudaStream_t st, int32_t s, int32_t n, const double *W, const double *R1, const int32_t *defl1,
+                     double *partial, unsigned *ticket, double *R2, int32_t *defl2, double *Rout)
+{
+    const int chunks = cqr_chunks(n);
+    SPAI_DISPATCH_S8(s, (k_cqr_gram2<S><<<chunks, kThreads, 0, st>>>(n, W, R1, defl1, partial, ticket, R2, defl2,
+                                                                     Rout)));
+    return check_launch();
+}
+
+int launch_cqr_apply(cudaStream_t st, int32_t s, int32_t n, const double *W, const double *R1, const int32_t *defl1,
+                     const double *R2, const int32_t *defl2, double *Q)
+{
+    SPAI_DISPATCH_S8(s, (k_cqr_apply<S><<<grid_for(n), kThreads, 0, st>>>(n, W, R1, defl1, R2, defl2, Q)));
+    return check_launch();
+}
+
+int launch_colnorm2_t(cudaStream_t st, int32_t s, int32_t n, const double *W, double *partial, unsigned *ticket,
+                      double *out)
+{
+    const int chunks = cqr_chunks(n);
+    SPAI_DISPATCH_S8(s, (k_colnorm2_t<S><<<chunks, kThreads, 0, st>>>(n, W, partial, ticket, out)));
+    return check_launch();
 }
 
 int launch_trsm_gram(cudaStream_t st, int32_t s, int32_t n, const double *W, const double *R,

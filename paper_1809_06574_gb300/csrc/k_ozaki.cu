@@ -418,6 +418,54 @@ __global__ void __launch_bounds__(256) k_trsm_fixed(int32_t n, double *__restric
     if (bad) atomicOr(err, ERR_RANGE);
 }
 
+// Last pass of the fused Cholesky-QR for an 8-column basis block: Q = (W R1^{-1}) R2^{-1}
+// (the row solve every orthogonalisation kernel shares, twice) and the block's fixed point
+// as k_trsm_fixed writes it.
+__global__ void __launch_bounds__(256) k_cqr_apply_fixed(int32_t n, const double *__restrict__ W,
+                                                         const double *__restrict__ R1,
+                                                         const int32_t *__restrict__ defl1,
+                                                         const double *__restrict__ R2,
+                                                         const int32_t *__restrict__ defl2, double *__restrict__ Q,
+                                                         uint64_t *__restrict__ F_row, uint64_t *__restrict__ F_sub,
+                                                         int32_t ipad, int32_t blk, int *err)
+{
+    __shared__ double Rs1[kS * kS], Rs2[kS * kS];
+    __shared__ double rinv1[kS], rinv2[kS];
+    for (int e = threadIdx.x; e < kS * kS; e += blockDim.x) {
+        Rs1[e] = R1[e];
+        Rs2[e] = R2[e];
+    }
+    if (threadIdx.x < kS) {
+        rinv1[threadIdx.x] = defl1[threadIdx.x] ? 0.0 : 1.0 / R1[threadIdx.x * kS + threadIdx.x];
+        rinv2[threadIdx.x] = defl2[threadIdx.x] ? 0.0 : 1.0 / R2[threadIdx.x * kS + threadIdx.x];
+    }
+    __syncthreads();
+    const int64_t nt = ((int64_t)n + kKT - 1) / kKT * kKT;
+    bool bad = false;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nt; r += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t f[kS];
+#pragma unroll
+        for (int a = 0; a < kS; ++a) f[a] = 0;
+        if (r < n) {
+            double x[kS];
+            row_load<kS>(W, r, x);
+            trsm_row<kS>(x, Rs1, rinv1);
+            trsm_row<kS>(x, Rs2, rinv2);
+            row_store<kS>(Q, r, x);
+#pragma unroll
+            for (int a = 0; a < kS; ++a)
+                if (!to_fixed(x[a], 0, f[a])) bad = true;
+            ulonglong2 *fr = reinterpret_cast<ulonglong2 *>(F_row + r * kS);
+#pragma unroll
+            for (int k = 0; k < kS / 2; ++k) fr[k] = make_ulonglong2(f[2 * k], f[2 * k + 1]);
+        }
+        ulonglong2 *fs = reinterpret_cast<ulonglong2 *>(F_sub + (((r / kKT) * ipad + blk) * kKT + (r % kKT)) * kS);
+#pragma unroll
+        for (int k = 0; k < kS / 2; ++k) fs[k] = make_ulonglong2(f[2 * k], f[2 * k + 1]);
+    }
+    if (bad) atomicOr(err, ERR_RANGE);
+}
+
 // Gram product H_i = V_i^T W.  grid = (row chunks, M tiles of 16 blocks); a chunk is a
 // whole number of 16-row sub-tiles, at most 4096 rows.  A stage carries S sub-tiles (S
 // from the tile's block count, so that small products still fill the converters); a
@@ -1031,6 +1079,19 @@ int launch_trsm_fixed(cudaStream_t st, int32_t n, double *Q, const double *R, co
     int64_t g = (rows + 255) / 256;
     if (g > 8 * 152) g = 8 * 152;
     k_trsm_fixed<<<(unsigned)g, 256, 0, st>>>(n, Q, R, deflated, F_row, F_sub, ipad, blk, d_err);
+    note_launches(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_cqr_apply_fixed(cudaStream_t st, int32_t n, const double *W, const double *R1, const int32_t *defl1,
+                           const double *R2, const int32_t *defl2, double *Q, uint64_t *F_row, uint64_t *F_sub,
+                           int32_t ipad, int32_t blk, int *d_err)
+{
+    if (n <= 0) return 0;
+    const int64_t rows = ((int64_t)n + kKT - 1) / kKT * kKT;
+    int64_t g = (rows + 255) / 256;
+    if (g > 8 * 152) g = 8 * 152;
+    k_cqr_apply_fixed<<<(unsigned)g, 256, 0, st>>>(n, W, R1, defl1, R2, defl2, Q, F_row, F_sub, ipad, blk, d_err);
     note_launches(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

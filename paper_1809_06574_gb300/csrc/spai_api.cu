@@ -2168,6 +2168,7 @@ struct SolveWs {
     double *Bw, *Xw, *W, *Z, *T0, *T1, *V;
     double *partial, *H1, *H2, *G1, *R1, *R2, *Rn, *ref2, *nrm2, *thresh, *Qs, *Rtri, *G, *Y, *est;
     int32_t *defl1, *defl2, *flag;
+    unsigned *ticket;   // last-CTA tickets of the fused Cholesky-QR and norm kernels (zero between launches)
     uint64_t *vfix;     // fixed-point copies of the basis blocks, row layout (block update)
     uint64_t *vfix_sub; // the same, sub-tile layout across blocks (Gram product)
     void *hdig;     // digit pieces of H (tensor-core block update)
@@ -2226,6 +2227,7 @@ size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks
     w.defl1 = (int32_t *)take(s * 4);
     w.defl2 = (int32_t *)take(s * 4);
     w.flag = (int32_t *)take(64);
+    w.ticket = (unsigned *)take(64);
     w.vfix = (uint64_t *)take(digits ? blk * (m + 1) : 16);
     w.vfix_sub = (uint64_t *)take(digits ? tc_fixed_sub_bytes(n, nh) : 16);
     w.hdig = take(digits ? tc_hdig_bytes(nh) : 16);
@@ -2248,20 +2250,23 @@ spai_status cholqr2(spai_ctx ctx, SolveWs &w, int32_t n, int32_t s, const double
 {
     cudaStream_t st = ctx->stream;
     const double nsd = (double)n * s;
-    if (gram_rows_supported(s)) {
-        PKL("gram", nsd * (s + 1), 8.0 * nsd, launch_gram_rows(st, s, n, Win, w.partial, w.G1), "gram");
-        PKL("small_dense", 0.0, 0.0, launch_chol_small(st, s, w.G1, ref2, 1e-24, w.R1, w.defl1), "chol");
-        PKL("trsm_gram", nsd * s + nsd * (s + 1), 16.0 * nsd,
-            launch_trsm_gram(st, s, n, Win, w.R1, w.defl1, Qout, w.partial, w.G1), "trsm gram");
-        PKL("small_dense", 0.0, 0.0, launch_chol_small(st, s, w.G1, nullptr, 0.0, w.R2, w.defl2), "chol");
+    if (cqr_supported(s)) {
+        // three launches; each pass's last CTA does its Cholesky (and R = R2 R1)
+        PKL("cqr_gram", nsd * (s + 1), 8.0 * nsd,
+            launch_cqr_gram(st, s, n, Win, ref2, 1e-24, w.partial, w.ticket, w.R1, w.defl1), "Cholesky-QR pass 1");
+        PKL("cqr_gram2", nsd * s + nsd * (s + 1), 8.0 * nsd,
+            launch_cqr_gram2(st, s, n, Win, w.R1, w.defl1, w.partial, w.ticket, w.R2, w.defl2, Rout),
+            "Cholesky-QR pass 2");
         if (fix_blk >= 0) {
-            PKL("trsm_fixed", nsd * s, 32.0 * nsd,
-                launch_trsm_fixed(st, n, Qout, w.R2, w.defl2, w.vfix + (size_t)fix_blk * n * s, w.vfix_sub, ipad,
-                                  fix_blk, ctx->d_err),
-                "trsm fixed point");
+            PKL("cqr_apply_fixed", 2.0 * nsd * s, 32.0 * nsd,
+                launch_cqr_apply_fixed(st, n, Win, w.R1, w.defl1, w.R2, w.defl2, Qout,
+                                       w.vfix + (size_t)fix_blk * n * s, w.vfix_sub, ipad, fix_blk, ctx->d_err),
+                "Cholesky-QR pass 3 with fixed point");
         } else {
-            PKL("trsm_rows", nsd * s, 16.0 * nsd, launch_trsm_rows(st, s, n, Qout, w.R2, w.defl2, Qout), "trsm");
+            PKL("cqr_apply", 2.0 * nsd * s, 16.0 * nsd,
+                launch_cqr_apply(st, s, n, Win, w.R1, w.defl1, w.R2, w.defl2, Qout), "Cholesky-QR pass 3");
         }
+        return SPAI_OK;
     } else {
         PKL("gram", nsd * (s + 1), 8.0 * nsd, launch_gram_sym(st, s, n, Win, w.partial, w.G1), "gram");
         PKL("small_dense", 0.0, 0.0, launch_chol_small(st, s, w.G1, ref2, 1e-24, w.R1, w.defl1), "chol");
@@ -2411,6 +2416,16 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
     }
     const size_t blk_elems = (size_t)n * s;
     const double nsd = (double)n * s;
+    CU(cudaMemsetAsync(w.ticket, 0, 64, cs), "clear tickets");
+    // column norms^2 of a block (one launch with the last-CTA sum for s <= 8)
+    auto colnorms = [&](const double *Wb, double *out) -> spai_status {
+        if (cqr_supported(s)) {
+            PKL("colnorm2", 2.0 * nsd, 8.0 * nsd, launch_colnorm2_t(cs, s, n, Wb, w.partial, w.ticket, out), "norms");
+        } else {
+            PKL("colnorm2", 2.0 * nsd, 8.0 * nsd, launch_colnorm2(cs, s, n, Wb, w.partial, out, chunks), "norms");
+        }
+        return SPAI_OK;
+    };
     double *h = ctx->h_pinned;  // [0,16) bnorm2, [16,32) rn2, [32,48) est, [48] flag, [49] error word
     KL(launch_colnorm2(cs, s, n, w.Bw, w.partial, w.nrm2, chunks), "norm B");
     CU(cudaMemcpyAsync(h, w.nrm2, s * 8, cudaMemcpyDeviceToHost, cs), "read norms");
@@ -2425,7 +2440,7 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
     auto residual = [&]() -> spai_status {
         PKL("residual", 2.0 * A->nnz * s + nsd, 12.0 * A->nnz + 4.0 * (n + 1) + 24.0 * nsd,
             launch_residual(cs, s, n, A->rowptr, A->colind, A->val, w.Xw, w.Bw, w.W), "residual");
-        PKL("colnorm2", 2.0 * nsd, 8.0 * nsd, launch_colnorm2(cs, s, n, w.W, w.partial, w.ref2, chunks), "residual norms");
+        if ((st = colnorms(w.W, w.ref2))) return st;
         CU(cudaMemcpyAsync(h + 16, w.ref2, s * 8, cudaMemcpyDeviceToHost, cs), "read norms");
         CU(cudaStreamSynchronize(cs), "sync");
         return SPAI_OK;
@@ -2481,7 +2496,7 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
                 PKL("spmm_A", 2.0 * A->nnz * s, 12.0 * A->nnz + 4.0 * (n + 1) + 16.0 * nsd,
                     launch_spmm(cs, s, n, A->rowptr, A->colind, A->val, Zj, w.W), "A Z");
             }
-            PKL("colnorm2", 2.0 * nsd, 8.0 * nsd, launch_colnorm2(cs, s, n, w.W, w.partial, w.ref2, chunks), "norms");
+            if ((st = colnorms(w.W, w.ref2))) return st;
             // two passes of block classical Gram-Schmidt against V_0..V_j
             const double nb = j + 1;
             const bool tc = use_digits && (opts->orth == SPAI_ORTH_TENSOR || j + 1 >= 2);
