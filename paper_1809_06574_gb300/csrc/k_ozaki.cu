@@ -6,27 +6,29 @@
 // basis columns, N = s right-hand sides.  GB300's FP64 pipe gives ~1.2 TFLOP/s, so it is
 // done here with integer digits on the BF16 tensor cores and FP64 only for the final sum:
 //
-//  * every value is written in fixed point with 54 bits below 2^1 (V's columns are unit
+//  * every value is written in fixed point with resolution 2^-54 (V's columns are unit
 //    vectors, so |v| <= 1; W's columns are scaled by a power of two 2^-e_b so that
-//    |w| < 1) and rounded to nearest: x = sign * sum_p d_p 2^(6(8-p)-53), d_p in [0, 63];
+//    |w| < 1): m = round(x 2^54), and m in balanced base 128, m = sum_p d_p 128^(7-p) with
+//    eight digits d_p in [-64, 63] (p = 0 the most significant);
 //  * each digit is exact in BF16; the products of digits p and q are accumulated in FP32
 //    in tensor memory by weight class c = p + q (the MMA for digit p writes its products
-//    with W digit q into the columns of class p + q); a class collects at most 9 products
-//    of at most 63^2 per row, so sums over at most 464 rows stay below 2^24 and exact;
-//  * digit pairs with p + q <= 9 are kept (53 products); the dropped pairs weigh < 2^-58
-//    relative, below FP64 rounding of the same dot products;
-//  * every <= 464 rows (a segment) four drain warps read the exact class sums out of tensor
-//    memory into two exact 64-bit integers per output, hi = sum_{c<=4} S_c 2^(6(4-c)) and
-//    lo = sum_{c>=5} S_c 2^(6(9-c)), and at the end combine them in FP64 with the scale.
+//    with W digit q into the columns of class p + q); a class collects at most 8 products
+//    of at most 64^2 per row, so sums over at most 512 rows stay within 2^24 and exact;
+//  * digit pairs with p + q <= 8 are kept (43 products); the dropped pairs weigh < 2^-61
+//    relative to the largest entries per row, below FP64 rounding of the same dot products;
+//  * every <= 512 rows (a segment) four drain warps read the exact class sums out of tensor
+//    memory into two exact 64-bit integers per output, hi = sum_{c<=4} S_c 128^(4-c) and
+//    lo = sum_{5<=c<=8} S_c 128^(8-c), and at the end combine them in FP64 with the scale.
 //    Four accumulator buffers of 128 columns let the MMAs of the next segment run while a
 //    segment is drained.
 //
-// Every basis block is kept, besides its FP64 copy, as sign-magnitude 54-bit fixed point
-// (8 bytes per value, made once by k_to_fixed when the block is created); W is read as
-// FP64 and scaled per CTA.  Both kernels stream these 8-byte values and cut the digits in
-// shared memory: one thread issues cp.async.bulk copies of raw row tiles into a ring of
-// stages (completion counted on mbarriers), eight converter warps turn each raw stage into
-// nine BF16 digit planes laid out as the MMA's shared-memory operand (a second ring), one
+// Every basis block is kept, besides its FP64 copy, as its eight digit bytes (byte i holds
+// d + 64 of the digit of weight 128^i: 8 bytes per value, the same traffic as FP64, made
+// once by the kernel that creates the block); W is read as FP64 and scaled per CTA.  Both
+// kernels stream these 8-byte values and cut the digits in shared memory with byte
+// permutes: one thread issues cp.async.bulk copies of raw row tiles into a ring of stages
+// (completion counted on mbarriers), eight converter warps turn each raw stage into eight
+// BF16 digit planes laid out as the MMA's shared-memory operand (a second ring), one
 // thread issues the tcgen05.mma of every stage and frees the digit stage with
 // tcgen05.commit.  Every wait is bounded in time (1 s): on time-out the kernel raises an
 // error bit, waits (bounded) for its copies in flight, frees its tensor memory and returns.
@@ -44,15 +46,15 @@ constexpr int kS = 8;              // right-hand-side block width handled here
 constexpr int kBlocksPerTile = 16; // basis blocks per Gram CTA: MMA M = 128 columns
 constexpr int kM = kS * kBlocksPerTile;
 constexpr int kKT = 16;            // rows per sub-tile / digit piece (= MMA K)
-constexpr int kDig = 9;            // 6-bit digits per value
+constexpr int kDig = 8;            // balanced base-128 digits per value
 constexpr int kPiece = kS * kKT * 2;             // 256 bytes: 8 columns x 16 rows of BF16
 constexpr int kLBO = 128;                        // next core matrix along K
 constexpr int kSBO = kPiece;                     // next 8-row group (next block / digit)
 constexpr int kTmemCols = 512;
 constexpr int kBufCols = 128;      // one class accumulator: classes 0..10 x 8 columns
 constexpr int kBufs = kTmemCols / kBufCols;
-constexpr int kClsCols = 80;       // classes 0..9 are read; class 10 only collects padding
-constexpr int kSegK = 464;         // rows (Gram) / basis columns (update) per accumulation
+constexpr int kClsCols = 80;       // classes 0..9 are read (class 9 only collects padding products)
+constexpr int kSegK = 512;         // rows (Gram) / basis columns (update) per accumulation
 constexpr int kMaxRows = 4096;     // rows per Gram CTA: hi, lo stay below 2^53
 constexpr int kCW = 8;             // converter warps
 constexpr int kCT = 32 * kCW;      // converter threads
@@ -60,14 +62,23 @@ constexpr int kThreadsTC = 64 + 128 + kCT;  // copy warp, MMA warp, 4 drain warp
 constexpr int kRawRow = kS * 8;    // 64 bytes: one row of an n x 8 block
 constexpr unsigned long long kWaitNs = 1000000000ull;  // drain waits give up after 1 s
 constexpr unsigned kSuspendNs = 20000;                  // suspend hint of one try_wait
-static_assert(9 * 63 * 63 * kSegK < (1 << 24), "exact FP32 class sums");
+static_assert(8 * 64 * 64 * kSegK <= (1 << 24), "exact FP32 class sums");
 static_assert(kClsCols == 5 * 16, "drain_classes reads five 16-column groups");
 
-// number of W digits q used with V digit p (q <= min(8, 9 - p)), MMA N (padded to 16)
-__host__ __device__ constexpr int nq(int p) { return (9 - p < 8 ? 9 - p : 8) + 1; }
-__host__ __device__ constexpr int nmma(int p) { return ((8 * nq(p) + 15) / 16) * 16; }
-static_assert(8 * 8 + nmma(8) <= kBufCols && 8 * 7 + nmma(7) <= kBufCols, "class columns");
-static_assert(nmma(0) <= 8 * (kDig + 1), "B row groups");
+// number of W digits q used with V digit p (p + q <= 8, q <= 7), MMA N (padded to 16: the
+// padding products land in class 9, which is never read).  The MMA of digit 0 opens each
+// segment (accumulate off), so it spans all 80 class columns: the W digit planes are
+// followed by two zero groups, and its products with them clear classes 8 and 9.
+__host__ __device__ constexpr int nq(int p) { return 9 - p < 8 ? 9 - p : 8; }
+__host__ __device__ constexpr int nmma(int p) { return p == 0 ? kClsCols : ((8 * nq(p) + 15) / 16) * 16; }
+constexpr int kBGroups = kDig + 2;  // B operand row groups: the digit planes and two zero groups
+__host__ __device__ constexpr bool classes_fit()
+{
+    for (int p = 0; p < kDig; ++p)
+        if (8 * p + nmma(p) > kClsCols || nmma(p) > 8 * kBGroups) return false;
+    return true;
+}
+static_assert(classes_fit(), "class columns and B row groups");
 
 // ---- Gram kernel shared memory: raw ring | digit ring | slack | ... | barriers, flag, tmem, exps,
 // maxima at the end of the allocation.  The ring depths follow the tile's block count: a
@@ -87,8 +98,8 @@ constexpr int kDOffMax = kDOffExp + kS * 4;
 static_assert(kDOffMax + kCW * kS * 8 <= kDSmem, "Gram kernel shared memory");
 static_assert(2 * kDRawStage + kDDigStages * kDDigStage + 4096 <= kDOffBar, "two raw stages at least");
 
-// bytes of one sub-tile's digit pieces for nvb blocks: A planes + 9 W digits + a zero group
-__host__ __device__ constexpr int dsub_bytes(int nvb) { return kDig * nvb * kPiece + (kDig + 1) * kPiece; }
+// bytes of one sub-tile's digit pieces for nvb blocks: A planes + W digit planes + 2 zero groups
+__host__ __device__ constexpr int dsub_bytes(int nvb) { return kDig * nvb * kPiece + kBGroups * kPiece; }
 // sub-tiles per stage: the stage carries >= ~240 digit groups of 8 values when it can
 __host__ __device__ inline int dsubs_per_stage(int nvb)
 {
@@ -214,7 +225,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t v[16])
 }
 
 // Add the class sums of one accumulator buffer (this thread's tensor-memory row) into the
-// exact integers hi, lo of its 8 output columns.  |S_c| < 2^24: exact FP32 integers.
+// exact integers hi, lo of its 8 output columns.  |S_c| <= 2^24: exact FP32 integers.
 __device__ __forceinline__ void drain_classes(uint32_t tbuf, long long hi[kS], long long lo[kS])
 {
     uint32_t v[3][16];
@@ -227,8 +238,8 @@ __device__ __forceinline__ void drain_classes(uint32_t tbuf, long long hi[kS], l
         for (int c = 0; c < 16; ++c) {
             const int col = 16 * k + c, cls = col >> 3, b = col & 7;
             const long long d = (long long)__float2int_rz(__uint_as_float(v[k][c]));
-            if (cls <= 4) hi[b] += d << (6 * (4 - cls));
-            else lo[b] += d << (6 * (9 - cls));
+            if (cls <= 4) hi[b] += d << (7 * (4 - cls));
+            else lo[b] += d << (7 * (8 - cls));
         }
 #pragma unroll
     for (int k = 0; k < 2; ++k) tmem_ld16(tbuf + 48 + 16 * k, v[k]);
@@ -238,18 +249,20 @@ __device__ __forceinline__ void drain_classes(uint32_t tbuf, long long hi[kS], l
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
             const int col = 48 + 16 * k + c, cls = col >> 3, b = col & 7;
+            if (cls > 8) continue;  // class 9: padding products only
             const long long d = (long long)__float2int_rz(__uint_as_float(v[k][c]));
-            if (cls <= 4) hi[b] += d << (6 * (4 - cls));
-            else lo[b] += d << (6 * (9 - cls));
+            if (cls <= 4) hi[b] += d << (7 * (4 - cls));
+            else lo[b] += d << (7 * (8 - cls));
         }
 }
 
-// value of the digit products times 2^e: hi carries weights 2^-10..2^-34 (-> hi 2^-34),
-// lo 2^-40..2^-64 (-> lo 2^-64); |hi|, |lo| < 2^53 convert exactly, and 2^e is a normal
-// double for the exponents of finite nonzero columns (a zero column has e = 0)
+// value of the digit products times 2^e: a product of digits p, q weighs 2^(e - 10 - 7(p+q)),
+// so hi carries class 4's weight 2^(e-38) and lo class 8's 2^(e-66); |hi|, |lo| < 2^53
+// convert exactly, and 2^e is a normal double for the exponents of finite nonzero columns
+// (a zero column has e = 0)
 __device__ __forceinline__ double combine_hilo(long long hi, long long lo, int e)
 {
-    const double v = fma((double)hi, 0x1p-34, (double)lo * 0x1p-64);
+    const double v = fma((double)hi, 0x1p-38, (double)lo * 0x1p-66);
     return v * __longlong_as_double((long long)(1023 + e) << 52);
 }
 
@@ -261,8 +274,8 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_
         : "memory");
 }
 
-// fixed-point magnitude round(|x| * 2^(53 - e)) from the IEEE bits (integer ops only);
-// returns false if |x| * 2^-e >= 2
+// fixed-point magnitude round(|x| * 2^(54 - e)) (half away from zero) from the IEEE bits
+// (integer ops only); false if |x| * 2^-e >= 2
 __device__ __forceinline__ bool fixed_mag(double x, int e, uint64_t &mag, uint32_t &neg)
 {
     const uint64_t bits = (uint64_t)__double_as_longlong(x);
@@ -273,8 +286,8 @@ __device__ __forceinline__ bool fixed_mag(double x, int e, uint64_t &mag, uint32
         return true;
     }
     const uint64_t mant = (bits & ((1ull << 52) - 1)) | (1ull << 52);
-    const int shift = ex - 1022 - e;  // mag = mant * 2^shift
-    if (shift > 1) {
+    const int shift = ex - 1021 - e;  // mag = mant * 2^shift
+    if (shift > 2) {
         mag = 0;
         return false;
     }
@@ -289,76 +302,69 @@ __device__ __forceinline__ bool fixed_mag(double x, int e, uint64_t &mag, uint32
     return true;
 }
 
-// BF16 bits of the signed digit (sign, d in [0, 63])
-__device__ __forceinline__ uint32_t digit_bf16(uint32_t d, uint32_t neg)
-{
-    const float f = __uint_as_float(0x4B000000u | d) - 8388608.0f;  // exact
-    return (__float_as_uint(f) >> 16) | (neg << 15);
-}
+// sum over i < 8 of 64 * 128^i: m + kBdOffset has the base-128 digits d_i + 64 of the
+// balanced digits d_i of m
+constexpr uint64_t kBdOffset = 0x81020408102040ull;
+constexpr uint64_t kBdZero = 0x4040404040404040ull;  // the byte digits of 0
 
-// Sign-magnitude fixed point of x: bit 63 = sign, bits 0..53 = round(|x| 2^(53-e)).
-// False if |x| 2^-e >= 2 or x is not finite.
-__device__ __forceinline__ bool to_fixed(double x, int e, uint64_t &f)
+// Byte digits of x at scale 2^e: byte i = d_i + 64, m = round(x 2^(54-e)) = sum_i d_i 128^i,
+// d_i in [-64, 63].  False if |x| 2^-e >= 2, m is outside the eight digits' range, or x is
+// not finite.
+__device__ __forceinline__ bool to_bdigits(double x, int e, uint64_t &word)
 {
     uint64_t mag;
     uint32_t neg;
-    const bool ok = fixed_mag(x, e, mag, neg);
-    f = ((uint64_t)neg << 63) | mag;
+    bool ok = fixed_mag(x, e, mag, neg);
+    const long long m = neg ? -(long long)mag : (long long)mag;
+    const uint64_t u = (uint64_t)(m + (long long)kBdOffset);
+    if (u >> 56) {  // outside [-kBdOffset, 2^56 - kBdOffset)
+        ok = false;
+        word = kBdZero;
+    } else {
+        // the eight 7-bit fields of u, one per byte
+        word = (u & 0x7Full) | ((u << 1) & (0x7Full << 8)) | ((u << 2) & (0x7Full << 16)) |
+               ((u << 3) & (0x7Full << 24)) | ((u << 4) & (0x7Full << 32)) | ((u << 5) & (0x7Full << 40)) |
+               ((u << 6) & (0x7Full << 48)) | ((u << 7) & (0x7Full << 56));
+    }
     return ok;
 }
 
-// Nine BF16 digit planes of 8 fixed-point values (8 consecutive rows of one column), one
-// 16-byte chunk per plane at dst + p * pstride.  Two values at a time: their digits (6-bit
-// fields of the magnitudes) go into the two halves of one word OR-ed with the BF16 pattern
-// of 128, so each half is the BF16 number 128 + d, exactly; one BF16x2 fused multiply-add
-// (s (128 + d) - 128 s, s = +-1 the value's sign) leaves the signed digit s d in each half,
-// exactly (an integer below 64).
-__device__ __forceinline__ uint32_t digit_field(uint32_t lo, uint32_t hi, int sh)
+// Eight BF16 digit planes of 8 values in byte-digit form (8 consecutive rows of one
+// column), one 16-byte chunk per plane at dst + p * pstride, plane p = digit of weight
+// 128^(7-p).  For two rows and two digits one byte permute gathers the four digit bytes; a
+// second puts each beside the byte 0x43, so that each half is the BF16 number 128 + x
+// (x = d + 64 < 128, exact), and a BF16x2 add of -192 leaves d, exactly.
+__device__ __forceinline__ void bexpand8(const uint64_t f[8], char *dst, int pstride)
 {
-    if (sh >= 32) return hi >> (sh - 32);
-    if (sh > 26) return __funnelshift_r(lo, hi, sh);
-    return lo >> sh;
-}
-
-__device__ __forceinline__ void expand8(const uint64_t f[8], char *dst, int pstride)
-{
-    uint32_t hi[8], lo[8];
-    __nv_bfloat162 sgn[4], off[4];
+    const __nv_bfloat162 off = __floats2bfloat162_rn(-192.0f, -192.0f);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        lo[u] = (uint32_t)f[u];
-        hi[u] = (uint32_t)(f[u] >> 32);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const uint32_t n0 = hi[2 * q] >> 31, n1 = hi[2 * q + 1] >> 31;
-        // s = +-1 and -128 s for both halves (BF16 bit patterns)
-        const uint32_t sb = (0x3F80u | (n0 << 15)) | ((0x3F80u | (n1 << 15)) << 16);
-        const uint32_t cb = (0x4300u | ((n0 ^ 1u) << 15)) | ((0x4300u | ((n1 ^ 1u) << 15)) << 16);
-        sgn[q] = *reinterpret_cast<const __nv_bfloat162 *>(&sb);
-        off[q] = *reinterpret_cast<const __nv_bfloat162 *>(&cb);
-    }
-#pragma unroll
-    for (int p = 0; p < kDig; ++p) {
-        const int sh = 6 * (8 - p);
-        uint32_t w[4];
+    for (int pp = 0; pp < kDig; pp += 2) {
+        // planes pp, pp + 1: bytes 7 - pp and 6 - pp, in the high word for pp < 4
+        const int b0 = (7 - pp) & 3, b1 = (6 - pp) & 3;
+        const uint32_t sel = (uint32_t)(b0 | ((4 + b0) << 4) | (b1 << 8) | ((4 + b1) << 12));
+        uint32_t w0[4], w1[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const uint32_t a = digit_field(lo[2 * q], hi[2 * q], sh);
-            const uint32_t b = digit_field(lo[2 * q + 1], hi[2 * q + 1], sh);
-            const uint32_t t = (__byte_perm(a, b, 0x5410) & 0x003F003Fu) | 0x43004300u;
-            const __nv_bfloat162 r = __hfma2(*reinterpret_cast<const __nv_bfloat162 *>(&t), sgn[q], off[q]);
-            w[q] = *reinterpret_cast<const uint32_t *>(&r);
+            const uint32_t a = pp < 4 ? (uint32_t)(f[2 * q] >> 32) : (uint32_t)f[2 * q];
+            const uint32_t b = pp < 4 ? (uint32_t)(f[2 * q + 1] >> 32) : (uint32_t)f[2 * q + 1];
+            const uint32_t g = __byte_perm(a, b, sel);  // [x_pp(r0), x_pp(r1), x_pp+1(r0), x_pp+1(r1)]
+            uint32_t t0 = __byte_perm(g, 0x43434343u, 0x4140);
+            uint32_t t1 = __byte_perm(g, 0x43434343u, 0x4342);
+            const __nv_bfloat162 r0 = __hadd2(*reinterpret_cast<const __nv_bfloat162 *>(&t0), off);
+            const __nv_bfloat162 r1 = __hadd2(*reinterpret_cast<const __nv_bfloat162 *>(&t1), off);
+            w0[q] = *reinterpret_cast<const uint32_t *>(&r0);
+            w1[q] = *reinterpret_cast<const uint32_t *>(&r1);
         }
-        *reinterpret_cast<uint4 *>(dst + p * pstride) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4 *>(dst + pp * pstride) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+        *reinterpret_cast<uint4 *>(dst + (pp + 1) * pstride) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
     }
 }
 
-// Fixed-point copies of nblocks n x 8 row-major blocks X (|x| < 2, else ERR_RANGE), in
+// Byte-digit copies of nblocks n x 8 row-major blocks X (|x| < 2, else ERR_RANGE), in
 // one or both layouts: F_row like X (the update kernel's rows), F_sub sub-tile-major
 // across blocks -- block iblk0 + b, 16-row sub-tile t at ((t * ipad + iblk0 + b) * 16) * 8,
-// 1 KB per (sub-tile, block), rows past n zero -- so that the Gram kernel fetches a
-// sub-tile of all its blocks in one copy.
+// 1 KB per (sub-tile, block), rows past n the digits of 0 -- so that the Gram kernel
+// fetches a sub-tile of all its blocks in one copy.
 __global__ void k_to_fixed(int32_t n, int32_t nblocks, const double *__restrict__ X, uint64_t *__restrict__ F_row,
                            uint64_t *__restrict__ F_sub, int32_t ipad, int32_t iblk0, int *err)
 {
@@ -370,9 +376,9 @@ __global__ void k_to_fixed(int32_t n, int32_t nblocks, const double *__restrict_
         const int64_t b = g / per, e = g - b * per;
         const int64_t r = e / kS;
         const int a = (int)(e - r * kS);
-        uint64_t f = 0;
+        uint64_t f = kBdZero;
         if (r < n) {
-            if (!to_fixed(X[(b * n + r) * kS + a], 0, f)) bad = true;
+            if (!to_bdigits(X[(b * n + r) * kS + a], 0, f)) bad = true;
             if (F_row) F_row[(b * n + r) * kS + a] = f;
         }
         if (F_sub) F_sub[(((r / kKT) * ipad + iblk0 + b) * kKT + (r % kKT)) * kS + a] = f;
@@ -382,8 +388,8 @@ __global__ void k_to_fixed(int32_t n, int32_t nblocks, const double *__restrict_
 
 // Last step of Cholesky-QR for an 8-column basis block: Q := Q R^{-1} in place (the row
 // solve every orthogonalisation kernel shares; deflated columns -> 0), and the block's
-// fixed point written as k_to_fixed writes it (row layout; sub-tile layout at slot blk,
-// padding rows of the last sub-tile zero), saving a pass over the new block.
+// byte digits written as k_to_fixed writes them (row layout; sub-tile layout at slot blk,
+// padding rows of the last sub-tile the digits of 0), saving a pass over the new block.
 __global__ void __launch_bounds__(256) k_trsm_fixed(int32_t n, double *__restrict__ Q, const double *__restrict__ R,
                                                     const int32_t *__restrict__ deflated, uint64_t *__restrict__ F_row,
                                                     uint64_t *__restrict__ F_sub, int32_t ipad, int32_t blk, int *err)
@@ -398,7 +404,7 @@ __global__ void __launch_bounds__(256) k_trsm_fixed(int32_t n, double *__restric
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nt; r += (int64_t)gridDim.x * blockDim.x) {
         uint64_t f[kS];
 #pragma unroll
-        for (int a = 0; a < kS; ++a) f[a] = 0;
+        for (int a = 0; a < kS; ++a) f[a] = kBdZero;
         if (r < n) {
             double x[kS];
             row_load<kS>(Q, r, x);
@@ -406,7 +412,7 @@ __global__ void __launch_bounds__(256) k_trsm_fixed(int32_t n, double *__restric
             row_store<kS>(Q, r, x);
 #pragma unroll
             for (int a = 0; a < kS; ++a)
-                if (!to_fixed(x[a], 0, f[a])) bad = true;
+                if (!to_bdigits(x[a], 0, f[a])) bad = true;
             ulonglong2 *fr = reinterpret_cast<ulonglong2 *>(F_row + r * kS);
 #pragma unroll
             for (int k = 0; k < kS / 2; ++k) fr[k] = make_ulonglong2(f[2 * k], f[2 * k + 1]);
@@ -445,7 +451,7 @@ __global__ void __launch_bounds__(256) k_cqr_apply_fixed(int32_t n, const double
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nt; r += (int64_t)gridDim.x * blockDim.x) {
         uint64_t f[kS];
 #pragma unroll
-        for (int a = 0; a < kS; ++a) f[a] = 0;
+        for (int a = 0; a < kS; ++a) f[a] = kBdZero;
         if (r < n) {
             double x[kS];
             row_load<kS>(W, r, x);
@@ -454,7 +460,7 @@ __global__ void __launch_bounds__(256) k_cqr_apply_fixed(int32_t n, const double
             row_store<kS>(Q, r, x);
 #pragma unroll
             for (int a = 0; a < kS; ++a)
-                if (!to_fixed(x[a], 0, f[a])) bad = true;
+                if (!to_bdigits(x[a], 0, f[a])) bad = true;
             ulonglong2 *fr = reinterpret_cast<ulonglong2 *>(F_row + r * kS);
 #pragma unroll
             for (int k = 0; k < kS / 2; ++k) fr[k] = make_ulonglong2(f[2 * k], f[2 * k + 1]);
@@ -469,7 +475,7 @@ __global__ void __launch_bounds__(256) k_cqr_apply_fixed(int32_t n, const double
 // Gram product H_i = V_i^T W.  grid = (row chunks, M tiles of 16 blocks); a chunk is a
 // whole number of 16-row sub-tiles, at most 4096 rows.  A stage carries S sub-tiles (S
 // from the tile's block count, so that small products still fill the converters); a
-// segment of whole stages covers at most 464 rows and owns one accumulator buffer.
+// segment of whole stages covers at most 512 rows and owns one accumulator buffer.
 // Warp 0 copies, warp 1 issues MMAs, warps 2..5 drain, warps 6..13 convert.  W's columns
 // are scaled by powers of two from this chunk's own column maxima, so the chunk's partial
 // sums carry their own scale.
@@ -528,10 +534,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         asm volatile("fence.mbarrier_init.release.cluster;");
         *flag = 0;
     }
-    // zero row group 9 of every sub-tile's B operand (MMAs with N = 80 read it; the
-    // converters never write it)
-    for (int e = tid; e < kDDigStages * S * (kPiece / 16); e += kThreadsTC) {
-        const int o = e % (kPiece / 16), sd = e / (kPiece / 16);
+    // zero groups 8 and 9 of every sub-tile's B operand (the digit-0 MMA reads them; the
+    // converters never write them)
+    for (int e = tid; e < kDDigStages * S * 2 * (kPiece / 16); e += kThreadsTC) {
+        const int o = e % (2 * (kPiece / 16)), sd = e / (2 * (kPiece / 16));
         const int d = sd / S, sg = sd % S;
         *reinterpret_cast<uint4 *>(smem + dig_off + d * dsb + sg * sub_bytes + kDig * plane + kDig * kPiece +
                                    o * 16) = make_uint4(0, 0, 0, 0);
@@ -681,6 +687,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             asm volatile("bar.arrive 2, %0;" ::"r"(128 + kCT) : "memory");  // exps ready for the drain warps
         }
         const int gps = 16 * (nvb + 1);  // digit groups per sub-tile: (block slot, 8-row half, column)
+        // g / gps as ((g >> 4) * inv) >> 16: exact while g >> 4 < 2^16 / (nvb + 1)^2 (here < 204)
+        const uint32_t inv = (65536u + (uint32_t)nvb) / (uint32_t)(nvb + 1);
         bool bad = false;
         for (int k = 0; k < nst; ++k) {
             const int s = k % R, d = k % kDDigStages;
@@ -696,7 +704,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             char *dig = smem + dig_off + d * dsb;
             const int rot = (k * 32) & (kCT - 1);  // spreads the extra groups over the warps
             for (int g = (ct - rot) & (kCT - 1); g < ns * gps; g += kCT) {
-                const int sg = g / gps, r = g % gps;
+                const int sg = (int)(((uint32_t)(g >> 4) * inv) >> 16), r = g - sg * gps;
                 const int i = r >> 4, ko = (r >> 3) & 1, a = r & 7;
                 const int64_t t = t0 + (int64_t)k * S + sg;
                 const int rv = (int)min((int64_t)kKT, (int64_t)n - t * kKT);
@@ -708,14 +716,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     const int e = wexp[a];
 #pragma unroll
                     for (int v = 0; v < 8; ++v)
-                        if (!to_fixed((ko * 8 + v < rv) ? src[v * kS] : 0.0, e, f[v])) bad = true;
-                    expand8(f, db + kDig * plane + ko * kLBO + a * 16, kPiece);
+                        if (!to_bdigits((ko * 8 + v < rv) ? src[v * kS] : 0.0, e, f[v])) bad = true;
+                    bexpand8(f, db + kDig * plane + ko * kLBO + a * 16, kPiece);
                 } else {  // rows past n are zero in the sub-tile layout
                     const uint64_t *src =
                         reinterpret_cast<const uint64_t *>(raw + (sg * nvb + i) * (kKT * kRawRow)) + ko * 8 * kS + a;
 #pragma unroll
                     for (int v = 0; v < 8; ++v) f[v] = src[v * kS];
-                    expand8(f, db + i * kPiece + ko * kLBO + a * 16, plane);
+                    bexpand8(f, db + i * kPiece + ko * kLBO + a * 16, plane);
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -738,7 +746,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 }
 
 // Digits of H (nblk*8 basis columns x 8, H[c * 8 + b]) scaled per column b: piece (kappa, q)
-// at hdig + (kappa * 9 + q) * 256 holds columns 16 kappa .. 16 kappa + 15 (zero beyond
+// at hdig + (kappa * 8 + q) * 256 holds columns 16 kappa .. 16 kappa + 15 (zero beyond
 // nblk * 8); hexp[b] = column exponent.  One CTA.
 __global__ void k_h_digits(int32_t nblk, const double *__restrict__ H, char *__restrict__ hdig,
                            int32_t *__restrict__ hexp, int *err)
@@ -769,29 +777,16 @@ __global__ void k_h_digits(int32_t nblk, const double *__restrict__ H, char *__r
     const int nk = (nblk + 1) / 2;
     for (int item = threadIdx.x; item < nk * kS * 2; item += blockDim.x) {
         const int b = item % kS, ko = (item / kS) % 2, kappa = item / (2 * kS);
-        uint64_t mag[8];
-        uint32_t neg[8];
+        uint64_t f[8];
         bool bad = false;
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int c = kappa * 16 + ko * 8 + u;
             const double x = c < ncol ? H[c * kS + b] : 0.0;
-            if (!fixed_mag(x, ex_s[b], mag[u], neg[u])) bad = true;
+            if (!to_bdigits(x, ex_s[b], f[u])) bad = true;
         }
         if (bad) atomicOr(err, ERR_RANGE);
-#pragma unroll
-        for (int q = 0; q < kDig; ++q) {
-            const int sh = 6 * (8 - q);
-            uint32_t w[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const uint32_t lo = digit_bf16((uint32_t)(mag[2 * u] >> sh) & 63u, neg[2 * u]);
-                const uint32_t hi = digit_bf16((uint32_t)(mag[2 * u + 1] >> sh) & 63u, neg[2 * u + 1]);
-                w[u] = lo | (hi << 16);
-            }
-            *reinterpret_cast<uint4 *>(hdig + (kappa * kDig + q) * kPiece + ko * kLBO + b * 16) =
-                make_uint4(w[0], w[1], w[2], w[3]);
-        }
+        bexpand8(f, hdig + kappa * kDig * kPiece + ko * kLBO + b * 16, kPiece);
     }
 }
 
@@ -800,18 +795,18 @@ __global__ void k_h_digits(int32_t nblk, const double *__restrict__ H, char *__r
 // Block update out = base + sign * V_{0..nblk-1} H on the tensor cores (W -= V H of the
 // Gram-Schmidt passes, U = V Y of the solution update), same digit scheme.  The MMA's M
 // dimension is 128 rows of V, K runs over basis columns (16 = two blocks per MMA), N over
-// H's digit planes x 8 columns.  V's digits are cut per stage from its fixed-point rows
+// H's digit planes x 8 columns.  V's digits are cut per stage from its byte-digit rows
 // and laid out MN-major (8 basis columns x 8 contiguous rows per core matrix); H's digits
-// are built once per call by k_h_digits as K-major pieces, one 2304-byte group per 16
-// basis columns.  A segment of at most 29 K steps (464 basis columns) owns one accumulator
-// buffer; a 128-row tile has at most three segments.
+// are built once per call by k_h_digits as K-major pieces, one 2048-byte group per 16
+// basis columns.  A segment of at most 32 K steps (512 basis columns) owns one accumulator
+// buffer; a 128-row tile has at most two segments.
 // ---------------------------------------------------------------------------------
 constexpr int kURawBlk = 128 * kRawRow;       // 8 KB: 128 rows of one block
 constexpr int kURawStage = 2 * kURawBlk;      // two blocks = one K step
 constexpr int kURawStages = 6;
 constexpr int kUPlane = 2 * (8 * kPiece);     // one digit plane of a stage: 2 blocks x 2 KB
-constexpr int kUStageA = kDig * kUPlane;      // 36 KB
-constexpr int kUDigStage = kUStageA + (kDig + 1) * kPiece;  // + 9 H digit pieces + zero group
+constexpr int kUStageA = kDig * kUPlane;      // 32 KB
+constexpr int kUDigStage = kUStageA + kBGroups * kPiece;  // + the 8 H digit pieces and 2 zero groups
 constexpr int kUDigStages = 3;
 constexpr int kUSegSteps = kSegK / 16;        // K steps per segment
 constexpr int kUOffDig = kURawStages * kURawStage;
@@ -868,8 +863,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         asm volatile("fence.mbarrier_init.release.cluster;");
         *flag = 0;
     }
-    for (int e = tid; e < kUDigStages * (kPiece / 16); e += kThreadsTC) {
-        const int s = e / (kPiece / 16), o = e % (kPiece / 16);
+    // the two zero groups after each stage's H digit pieces (read by the digit-0 MMA)
+    for (int e = tid; e < kUDigStages * 2 * (kPiece / 16); e += kThreadsTC) {
+        const int s = e / (2 * (kPiece / 16)), o = e % (2 * (kPiece / 16));
         *reinterpret_cast<uint4 *>(smem + kUOffDig + s * kUDigStage + kUStageA + kDig * kPiece + o * 16) =
             make_uint4(0, 0, 0, 0);
     }
@@ -1006,8 +1002,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 char *dig = smem + kUOffDig + d * kUDigStage;
                 uint64_t f[8];
 #pragma unroll
-                for (int v = 0; v < 8; ++v) f[v] = (i < nbk && rloc + v < rv) ? src[v * kS] : 0ull;
-                expand8(f, dig + i * (8 * kPiece) + t8 * kPiece + ko * kLBO + a * 16, kUPlane);
+                for (int v = 0; v < 8; ++v) f[v] = (i < nbk && rloc + v < rv) ? src[v * kS] : kBdZero;
+                bexpand8(f, dig + i * (8 * kPiece) + t8 * kPiece + ko * kLBO + a * 16, kUPlane);
                 if (ct < kDig * kPiece / 16)  // H's digit pieces of this K step
                     reinterpret_cast<uint4 *>(dig + kUStageA)[ct] =
                         reinterpret_cast<const uint4 *>(hdig + (int64_t)kk * kDig * kPiece)[ct];
