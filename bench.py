@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--serve-rates", default="400,800", help="further offered rates of the serving workload")
     ap.add_argument("--serve-rate-seconds", type=float, default=5.0)
     ap.add_argument("--no-served-sweep", action="store_true")
+    ap.add_argument("--gcro-kmax", type=int, default=16, help="recycled columns per shift of the block GCRO leg")
     # large workload: 3D 128^3 27-point grid, 16 RHS, BF16-stored SPAI, update vs rebuild
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--large-only", action="store_true")
@@ -973,6 +974,7 @@ class Worker:
                 self.X = torch.zeros((s, n), dtype=torch.float64).pin_memory()
             else:
                 self.X = torch.zeros((s, n), dtype=torch.float64, device=dev)
+        self.rcs = {}  # block GCRO: a recycle space per shift
 
 
 class Sweep:
@@ -982,10 +984,14 @@ class Sweep:
     `workers` host threads, each with its own stream and context, take them round-robin
     while the main context builds the bases."""
 
-    def __init__(self, sg, torch, ctx, w, host_inputs=False, workers=1, prec=0, warm=False, solve_precision=0):
+    def __init__(self, sg, torch, ctx, w, host_inputs=False, workers=1, prec=0, warm=False, solve_precision=0,
+                 gcro_kmax=0):
         self.sg, self.torch, self.ctx, self.w = sg, torch, ctx, w
         self.prec = prec  # 0: FP64 factors; sg.PREC_FP32: FP32 least squares and factors
         self.solve_precision = solve_precision  # sg.SOLVE_MIXED: FP32 operator, FP64 refinement
+        # gcro_kmax > 0: block GCRO, each worker carrying a recycle space of that many columns
+        # per shift along its parameters (the span of its latest solutions of the shift)
+        self.gcro_kmax = gcro_kmax
         # warm: a worker starts each solve from its previous solution of the same shift (all
         # systems share B, and neighbouring parameters have close solutions)
         self.warm = warm
@@ -1024,6 +1030,8 @@ class Sweep:
         if self.pool is not None:
             self.pool.shutdown()
         for wk in self.workers:
+            for rc in wk.rcs.values():
+                self.sg.spai_recycle_destroy(rc)
             self.sg.spai_ctx_destroy(wk.ctx)
 
     def h2d_bytes(self):
@@ -1060,8 +1068,16 @@ class Sweep:
                 with torch.cuda.stream(wk.stream):
                     wk.X.zero_()
             prev_si = si
-            st, info, rel = sg.block_solve(wk.ctx, A, pc, self.s, self.B, n, wk.X, n,
-                                           w.restart, w.tol, 50, precision=self.solve_precision)
+            if self.gcro_kmax:
+                if si not in wk.rcs:
+                    wk.rcs[si] = sg.spai_recycle_create(wk.ctx, n, self.s, self.gcro_kmax)
+                with torch.cuda.stream(wk.stream):
+                    wk.X.zero_()
+                st, info, rel = sg.block_solve_gcro(wk.ctx, A, pc, self.s, self.B, n, wk.X, n, w.restart, w.tol, 50,
+                                                    wk.rcs[si], precision=self.solve_precision)
+            else:
+                st, info, rel = sg.block_solve(wk.ctx, A, pc, self.s, self.B, n, wk.X, n,
+                                               w.restart, w.tol, 50, precision=self.solve_precision)
             if i > 0:
                 sg.spai_pc_destroy(pc)
             if not info["converged"]:
@@ -1077,6 +1093,9 @@ class Sweep:
         before."""
         sg, torch, ctx, w, n = self.sg, self.torch, self.ctx, self.w, self.n
         aff = self.aff
+        for wk in self.workers:  # every step starts without recycled spaces
+            for rc in wk.rcs.values():
+                sg.spai_recycle_clear(rc)
         if self.host_inputs:
             aff = sg.spai_affine_create(ctx, [sg.csr(n, *t) for t in self.h_terms])
         self.aff_now = aff
@@ -1268,6 +1287,14 @@ def main():
     # the same FP64 sweep with each solve started from the worker's previous solution of
     # the same shift (every system has the same B; neighbouring p have close solutions):
     # same true-residual tolerance, fewer iterations
+    # block GCRO (the paper's solver) with each worker's recycled space along its parameters
+    gcro = None
+    if not args.no_mixed:
+        gcro = timed_sweep(gcro_kmax=args.gcro_kmax)
+        gcro["note"] = (f"FP64 as the headline; block GCRO, each worker carrying a recycled space of "
+                        f"{args.gcro_kmax} columns per shift (its latest solutions of the shift), cleared every step")
+        gcro_mixed = timed_sweep(gcro_kmax=args.gcro_kmax, prec=sg.PREC_FP32, solve_precision=sg.SOLVE_MIXED)
+        gcro["mixed_precision"] = {k: gcro_mixed[k] for k in ("value", "ms_per_step", "gmres_iterations", "cycles")}
     warm = None
     if not args.no_mixed:
         warm = timed_sweep(warm=True)
@@ -1374,7 +1401,8 @@ def main():
             "idle_ms": {"total": round(sum(v for _, v in idle), 3),
                         **{k: round(v, 3) for k, v in idle[:8]}},
             "large": large, "batched": batched, "adaptive": adaptive, "update_order": order,
-            "block_vs_single_rhs": bvs, "warm_start": warm, "fp32_factors": fp32_factors, "serving": serving,
+            "block_vs_single_rhs": bvs, "warm_start": warm, "gcro": gcro, "fp32_factors": fp32_factors,
+            "serving": serving,
             "cpu_baseline": cpu, "e2e": e2e, "roofline": roofline, "roofline_isolated": roofline_iso,
             "mixed_precision": mixed, "served_capacity": served_cap,
         }

@@ -478,6 +478,43 @@ SPAI_API spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, int
                         spai_solve_info *info, double *rel_residual);
 
 /* ----------------------------------------------------------------------------------
+ * Block GCRO, the solver of the paper's experiments (Sec. 3: GCRO and block GCRO), with its
+ * outer space carried along a sequence of systems A(p_1) X = B, A(p_2) X = B, ... (Sec. 1.3).
+ * A recycle space holds up to kmax columns U (in the preconditioned space of the right-
+ * preconditioned solve).  For each solve, with AP = A P:
+ *  - C T = AP U (block Gram-Schmidt and Cholesky-QR by s-column blocks; columns that AP U
+ *    leaves dependent are dropped as the Krylov blocks' are), U <- U T^{-1}, so AP U = C;
+ *  - every restart cycle starts from the residual projected off C (X~ += U C^T R,
+ *    R -= C C^T R), runs block Arnoldi on (I - C C^T) AP with two passes of block classical
+ *    Gram-Schmidt against [C, V], and minimises every column's residual over span([U, V]):
+ *    AP [U, V_j] = [C, V_{j+1}] [[I, C^T AP V_j], [0, Hbar_j]];
+ *  - the solve's iterate X~ (X = P X~) then joins U, the oldest s columns leaving a full
+ *    space: the span of the sequence's latest solutions is the next system's start.
+ * With an empty recycle space the solve is block_solve's block GMRES.
+ * ---------------------------------------------------------------------------------- */
+typedef struct spai_recycle_s *spai_recycle;
+
+/* Recycle space for n unknowns and s right-hand sides: kmax columns at most (a multiple of s,
+ * kmax / s <= 16), empty at first.  Device memory of the context (8 n kmax bytes). */
+SPAI_API spai_status spai_recycle_create(spai_ctx ctx, int32_t n, int32_t s, int32_t kmax, spai_recycle *out);
+/* Columns currently held (a multiple of s). */
+SPAI_API spai_status spai_recycle_info(spai_recycle r, int32_t *k);
+/* Copy the k columns to U (DEVICE, n x k column-major, leading dimension ldu >= n).  Asynchronous. */
+SPAI_API spai_status spai_recycle_export(spai_ctx ctx, spai_recycle r, double *U, int64_t ldu);
+/* Empty the space (the next solve starts without a recycled space). */
+SPAI_API spai_status spai_recycle_clear(spai_recycle r);
+SPAI_API spai_status spai_recycle_destroy(spai_recycle r);
+
+/* Solve A X = B by block GCRO with the recycle space rc (arguments as block_solve; X holds
+ * the initial guess on entry).  The workspace is that of block_solve with restart + kmax/s
+ * basis blocks.  On success the iterate joins rc; rc is left as it was on a failure except
+ * that its columns are rescaled (U <- U T^{-1}, the same span).  The recycle space may serve
+ * one solve at a time.  Synchronises; SPAI_ENOTCONV as block_solve. */
+SPAI_API spai_status block_solve_gcro(spai_ctx ctx, const spai_csr *A, spai_pc P, int32_t s, const double *B,
+                                      int64_t ldb, double *X, int64_t ldx, const spai_solve_opts *opts,
+                                      spai_recycle rc, spai_solve_info *info, double *rel_residual);
+
+/* ----------------------------------------------------------------------------------
  * Serving.  The paper's setting is a sequence of linear systems A(p_j) X_j = B_j that
  * differ only in the parameter (Sec. 1.3), whose SPAI preconditioner is updated cheaply
  * from an earlier build instead of being rebuilt (Sec. 2.3, Table 1; Sec. 2.4).  A server

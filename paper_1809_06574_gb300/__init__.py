@@ -22,7 +22,8 @@ __all__ = [
     "spai_ctx_mem_in_use", "spai_ctx_set_wait_limit", "spai_ctx_inject_stall", "spai_launch_count", "spai_ctx_profile", "spai_ctx_profile_count", "spai_measure_fp64_rate",
     "spai_ctx_profile_entry", "spai_affine_create", "spai_affine_pattern",
     "spai_assemble", "spai_affine_export", "spai_affine_destroy", "spai_build", "spai_update", "spai_pc_info",
-    "spai_pc_export", "spai_pc_destroy", "spai_build_batch", "block_solve_batch", "spai_spmm", "spai_pc_apply", "spai_spmm_fp32", "spai_pc_apply_fp32", "block_solve",
+    "spai_pc_export", "spai_pc_destroy", "spai_build_batch", "block_solve_batch", "spai_spmm", "spai_pc_apply", "spai_spmm_fp32", "spai_pc_apply_fp32", "block_solve", "block_solve_gcro",
+    "spai_recycle_create", "spai_recycle_info", "spai_recycle_export", "spai_recycle_clear", "spai_recycle_destroy",
     "spai_shifted_coefficients", "spai_assemble_shifted", "spai_server_add_shifted_system", "PATTERN_A", "PATTERN_A2", "UPDATE_FIRST", "UPDATE_CHAINED", "UPDATE_DIAGONAL", "PREC_FP32", "PREC_BF16",
     "LIB_PATH", "spai_ctx_trim", "spai_solve_workspace_size", "spai_pc_mem_size",
     "spai_server_opts", "spai_request", "spai_result", "spai_server_stats", "spai_server_create",
@@ -178,6 +179,13 @@ def lib():
         "spai_server_destroy": (i32, [vp]),
         "spai_build_adaptive": (i32, [vp, P(spai_csr), P(spai_adaptive_opts), i32, P(vp)]),
         "spai_column_variants": (i32, [i32, i32, i32, P(i32), i32]),
+        "spai_recycle_create": (i32, [vp, i32, i32, i32, P(vp)]),
+        "spai_recycle_info": (i32, [vp, P(i32)]),
+        "spai_recycle_export": (i32, [vp, vp, vp, i64]),
+        "spai_recycle_clear": (i32, [vp]),
+        "spai_recycle_destroy": (i32, [vp]),
+        "block_solve_gcro": (i32, [vp, P(spai_csr), vp, i32, vp, i64, vp, i64, P(spai_solve_opts), vp,
+                                   P(spai_solve_info), P(dbl)]),
         "spai_column_variant_get": (i32, [i32, i32, i32]),
         "spai_column_variant_set": (i32, [i32, i32, i32, i32]),
     }
@@ -449,6 +457,46 @@ def block_solve(ctx, A, P, s, B, ldb, X, ldx, restart, tol, max_cycles, allow_no
     rel = (C.c_double * int(s))()
     st = lib().block_solve(ctx, C.byref(A), P, int(s), _ptr(B), int(ldb), _ptr(X), int(ldx),
                            C.byref(opts), C.byref(info), rel)
+    result = (st, info.as_dict(), list(rel))
+    if st == SPAI_ENOTCONV and not allow_notconv:
+        raise SpaiError(st, spai_last_error(ctx), result)
+    _check(ctx, st, allow=(SPAI_ENOTCONV,))
+    return result
+
+
+def spai_recycle_create(ctx, n, s, kmax):
+    """Recycle space of block GCRO: up to kmax columns (a multiple of s) for n unknowns."""
+    out = C.c_void_p()
+    _check(ctx, lib().spai_recycle_create(ctx, int(n), int(s), int(kmax), C.byref(out)))
+    return out
+
+
+def spai_recycle_info(rc):
+    k = C.c_int32()
+    _check(None, lib().spai_recycle_info(rc, C.byref(k)))
+    return k.value
+
+
+def spai_recycle_export(ctx, rc, U, ldu):
+    return _check(ctx, lib().spai_recycle_export(ctx, rc, _ptr(U), int(ldu)))
+
+
+def spai_recycle_clear(rc):
+    return _check(None, lib().spai_recycle_clear(rc))
+
+
+def spai_recycle_destroy(rc):
+    return _check(None, lib().spai_recycle_destroy(rc))
+
+
+def block_solve_gcro(ctx, A, P, s, B, ldb, X, ldx, restart, tol, max_cycles, rc, allow_notconv=False,
+                     orth=ORTH_AUTO, precision=SOLVE_FP64):
+    """Block GCRO with the recycle space rc (see block_solve).  Returns (status, info, rel)."""
+    opts = spai_solve_opts(int(restart), int(max_cycles), float(tol), int(orth), int(precision))
+    info = spai_solve_info()
+    rel = (C.c_double * int(s))()
+    st = lib().block_solve_gcro(ctx, C.byref(A), P, int(s), _ptr(B), int(ldb), _ptr(X), int(ldx), C.byref(opts),
+                                rc, C.byref(info), rel)
     result = (st, info.as_dict(), list(rel))
     if st == SPAI_ENOTCONV and not allow_notconv:
         raise SpaiError(st, spai_last_error(ctx), result)

@@ -897,6 +897,32 @@ __global__ void k_set_rhs(int32_t m, const double *__restrict__ S0, double *__re
         G[e] = (e < S * S) ? S0[e] : 0.0;
 }
 
+// Least-squares state of a cycle whose first kb block columns are the recycled space's
+// identity columns (block GCRO: AP U = C): G = 0 with S0 at block kb; the reflectors of
+// steps 0 .. kb-1 the identity (2S x 2S) and block columns 0 .. kb-1 of R the identity.
+// kb = 0 is k_set_rhs.
+template <int S>
+__global__ void k_ls_prefix(int32_t kb, int32_t m, const double *__restrict__ S0, double *__restrict__ Qs,
+                            double *__restrict__ Rtri, double *__restrict__ G)
+{
+    constexpr int S2 = 2 * S;
+    const int64_t ld = (int64_t)(m + 1) * S;
+    const int64_t ng = (int64_t)(m + 1) * S * S, nq = (int64_t)kb * S2 * S2, nr = (int64_t)kb * S * ld;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ng + nq + nr;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        if (e < ng) {
+            const int64_t lo = (int64_t)kb * S * S;
+            G[e] = (e >= lo && e < lo + S * S) ? S0[e - lo] : 0.0;
+        } else if (e < ng + nq) {
+            const int64_t q = e - ng, r = (q % (S2 * S2)) / S2, c = q % S2;
+            Qs[q] = (r == c) ? 1.0 : 0.0;
+        } else {
+            const int64_t q = e - ng - nq, col = q / ld, row = q % ld;
+            Rtri[q] = (row == col) ? 1.0 : 0.0;
+        }
+    }
+}
+
 template <int S>
 __global__ void k_set_rhs_b(int32_t m, const double *__restrict__ S0, double *__restrict__ G)
 {
@@ -1300,6 +1326,17 @@ int launch_set_rhs(cudaStream_t st, int32_t s, int32_t m, const double *S0, doub
     SPAI_DISPATCH_S(s, (k_set_rhs<S><<<cap_grid((count + 255) / 256), 256, 0, st>>>(m, S0, G)));
     return check_launch();
 }
+int launch_ls_prefix(cudaStream_t st, int32_t s, int32_t kb, int32_t m, const double *S0, double *Qs, double *Rtri,
+                     double *G)
+{
+    const int64_t ld = (int64_t)(m + 1) * s;
+    const int64_t count = (int64_t)(m + 1) * s * s + (int64_t)kb * 4 * s * s + (int64_t)kb * s * ld;
+    int g = grid_for(count);
+    if (g > 1024) g = 1024;
+    SPAI_DISPATCH_S(s, (k_ls_prefix<S><<<g, kThreads, 0, st>>>(kb, m, S0, Qs, Rtri, G)));
+    return check_launch();
+}
+
 
 int launch_backsolve(cudaStream_t st, int32_t s, int32_t J, int32_t ldr, const double *Rtri,
                      const double *G, double *Y)

@@ -104,6 +104,13 @@ struct spai_pc_s {
     Arena *arena = nullptr;    // non-null: fval*, a_cval and status live in this arena
 };
 
+// recycled outer space of block GCRO: k of kmax columns as k / s row-major n x s blocks
+struct spai_recycle_s {
+    spai_ctx ctx = nullptr;
+    int32_t n = 0, s = 0, kmax = 0, k = 0;
+    double *U = nullptr;
+};
+
 struct spai_affine_s {
     spai_ctx ctx = nullptr;
     int32_t n = 0, T = 0;
@@ -805,6 +812,9 @@ bool valid_s(int32_t s) { return s == 1 || s == 2 || s == 4 || s == 8 || s == 16
 // FP32 unit roundoffs): below it the FP32 operator's rounding, not the Krylov space, limits
 // what the cycle can resolve.
 constexpr double kMixedCycleReduction = 0x1p-20;
+
+// largest recycled space of block GCRO, in blocks of s columns
+constexpr int kMaxRecycleBlocks = 16;
 
 // wait settings of the next tensor-core launch on this context
 TcWait tc_wait(spai_ctx ctx)
@@ -2166,6 +2176,7 @@ namespace {
 
 struct SolveWs {
     double *Bw, *Xw, *W, *Z, *T0, *T1, *V;
+    double *Xh, *D;     // block GCRO: the preconditioned-space iterate and a correction block
     double *partial, *H1, *H2, *G1, *R1, *R2, *Rn, *ref2, *nrm2, *thresh, *Qs, *Rtri, *G, *Y, *est;
     int32_t *defl1, *defl2, *flag;
     unsigned *ticket;   // last-CTA tickets of the fused Cholesky-QR and norm kernels (zero between launches)
@@ -2202,6 +2213,8 @@ size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks
     w.T0 = (double *)take(blk);
     w.T1 = (double *)take(blk);
     w.V = (double *)take(blk * (m + 1));
+    w.Xh = (double *)take(blk);
+    w.D = (double *)take(blk);
     const bool digits = digits_for(s, m);
     const int32_t nh = (s == 16 ? 2 : 1) * (m + 1);  // basis (half-)blocks of the digit kernels
     {
@@ -2304,9 +2317,16 @@ extern "C" spai_status spai_ctx_trim(spai_ctx ctx)
     return SPAI_OK;
 }
 
-extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, int32_t s, const double *B,
-                                   int64_t ldb, double *X, int64_t ldx, const spai_solve_opts *opts,
-                                   spai_solve_info *info, double *rel_residual)
+namespace {
+
+// Right-preconditioned block GMRES(m) (rc == nullptr) and block GCRO with a recycled outer
+// space rc (its columns U, with C = AP U orthonormal, come first in the basis: every cycle
+// starts from the residual projected off C, orthogonalises against [C, V], and minimises
+// over span([U, V]); the solve's iterate joins rc for the next system).  With rc empty the
+// two are the same computation.
+spai_status solve_impl(spai_ctx ctx, const spai_csr *A, spai_pc P, int32_t s, const double *B, int64_t ldb,
+                       double *X, int64_t ldx, const spai_solve_opts *opts, spai_solve_info *info,
+                       double *rel_residual, spai_recycle rc)
 {
     if (!ctx) return SPAI_EINVAL;
     spai_status st = check_csr_args(ctx, A, "A");
@@ -2327,22 +2347,27 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
     }
     if (opts->precision != SPAI_SOLVE_FP64 && opts->precision != SPAI_SOLVE_MIXED)
         return fail(ctx, SPAI_EINVAL, "unknown solve precision %d", opts->precision);
+    if (rc && (rc->n != n || rc->s != s))
+        return fail(ctx, SPAI_EINVAL, "recycle space made for n=%d, s=%d; the solve has n=%d, s=%d", rc->n, rc->s, n, s);
     const bool mixed = opts->precision == SPAI_SOLVE_MIXED;
+    const int32_t kbmax = rc ? rc->kmax / s : 0;  // recycled blocks: basis slots 0 .. kb-1 hold C
+    int32_t kb = rc ? rc->k / s : 0;
+    const int32_t mt = m + kbmax;                 // the workspace's restart length
     const int chunks = krylov_chunks(n);
     SolveWs w{};
-    const size_t need = carve(w, nullptr, n, s, m, chunks);
+    const size_t need = carve(w, nullptr, n, s, mt, chunks);
     const size_t need32 = mixed ? ((size_t)A->nnz * 4 + 255) / 256 * 256 : 0;  // A's values in FP32
     void *base = nullptr;
     if ((st = temp_blocks(ctx, need + need32, &base))) return st;
-    carve(w, base, n, s, m, chunks);
+    carve(w, base, n, s, mt, chunks);
     float *a32 = mixed ? (float *)((char *)base + need) : nullptr;
     cudaStream_t cs = ctx->stream;
     const bool b_dev = is_device_ptr(B), x_dev = is_device_ptr(X);
     if (opts->orth < SPAI_ORTH_AUTO || opts->orth > SPAI_ORTH_TENSOR)
         return fail(ctx, SPAI_EINVAL, "unknown orthogonalisation method %d", opts->orth);
-    const bool use_digits = digits_for(s, m) && opts->orth != SPAI_ORTH_FP64;
+    const bool use_digits = digits_for(s, mt) && opts->orth != SPAI_ORTH_FP64;
     const bool halves = use_digits && s == 16;  // 16 columns as two 8-column halves
-    const int32_t ipad = (halves ? 2 : 1) * (m + 1);
+    const int32_t ipad = (halves ? 2 : 1) * (mt + 1);
     const size_t half_elems = (size_t)n * 8;
     // H = V_{0..nb-1}^T Wsrc on the tensor cores: a 16-column block as two halves against
     // all 2 nb half-blocks of the basis, the two 8-column results merged into 16 x 16 blocks
@@ -2372,14 +2397,16 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
            "fixed point");
         return SPAI_OK;
     };
-    // out = base + sign * V_{0..nb-1} H: tensor-core digits when available, else FP64
-    auto vupdate = [&](int nb, const double *H, const double *basep, double *out, double sign) -> spai_status {
+    // out = base + sign * V_{first..first+nb-1} H: tensor-core digits when available, else FP64
+    auto vupdate_at = [&](int first, int nb, const double *H, const double *basep, double *out,
+                          double sign) -> spai_status {
         const double f = 2.0 * n * s * s * nb;
+        const uint64_t *vf = w.vfix + (size_t)first * n * s;  // 8-column blocks or pairs of half-blocks
         if (use_digits && (halves ? 2 : 1) * nb <= block_update_tc_max_blocks() &&
             (opts->orth == SPAI_ORTH_TENSOR || nb >= 2)) {
             if (!halves) {
                 PKL("block_update_tc", f, 8.0 * n * s * (nb + 2),
-                    launch_block_update_tc(cs, n, nb, w.vfix, H, w.hdig, w.hexp, basep, out, sign, ctx->d_err, tc_wait(ctx)),
+                    launch_block_update_tc(cs, n, nb, vf, H, w.hdig, w.hexp, basep, out, sign, ctx->d_err, tc_wait(ctx)),
                     "block update");
                 return SPAI_OK;
             }
@@ -2389,16 +2416,19 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
             if (basep) KL(launch_halves16(cs, n, const_cast<double *>(basep), w.Wh, false), "column halves");
             for (int h = 0; h < 2; ++h) {
                 double *wh = w.Wh + h * half_elems;
-                KL(launch_block_update_tc(cs, n, 2 * nb, w.vfix, h ? w.HR : w.HL, w.hdig, w.hexp, basep ? wh : nullptr, wh,
+                KL(launch_block_update_tc(cs, n, 2 * nb, vf, h ? w.HR : w.HL, w.hdig, w.hexp, basep ? wh : nullptr, wh,
                                           sign, ctx->d_err, tc_wait(ctx)),
                    "block update");
             }
             KL(launch_halves16(cs, n, out, w.Wh, true), "merge halves");
         } else {
             PKL("block_update", f, 8.0 * n * s * (nb + 2),
-                launch_block_update(cs, s, n, nb, w.V, H, basep, out, sign), "block update");
+                launch_block_update(cs, s, n, nb, w.V + (size_t)first * n * s, H, basep, out, sign), "block update");
         }
         return SPAI_OK;
+    };
+    auto vupdate = [&](int nb, const double *H, const double *basep, double *out, double sign) -> spai_status {
+        return vupdate_at(0, nb, H, basep, out, sign);
     };
 
     // inputs -> row-major device blocks (T0 stages host data column-major)
@@ -2450,7 +2480,6 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
             if (!(sqrt(h[16 + i]) <= thresh[i])) return false;
         return true;
     };
-    if ((st = residual())) return st;
     F32Vals a32v;
     if (mixed) {
         a32v.f32 = a32;
@@ -2459,9 +2488,89 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
     // the FP32 operator's (A P) W = A (P V_j), intermediates FP32 in the Z / T blocks
     float *z32 = (float *)w.Z, *t032 = (float *)w.T0, *t132 = (float *)w.T1;
     const double nnzA = A->nnz;
+    // Wout = A P Vin (FP64 products, or the FP32 operator of the mixed solve)
+    auto apply_op = [&](const double *Vin, double *Wout) -> spai_status {
+        if (mixed) {
+            if (P) {
+                if ((st = apply32<float>(ctx, P, s, Vin, z32, t032, t132))) return st;
+                PKL("spmm32_A", 2.0 * nnzA * s, 8.0 * nnzA + 4.0 * (n + 1) + 12.0 * nsd,
+                    launch_spmm32(cs, s, n, A->rowptr, A->colind, a32v, (const float *)z32, Wout), "A Z (FP32)");
+            } else {
+                PKL("spmm32_A", 2.0 * nnzA * s, 8.0 * nnzA + 4.0 * (n + 1) + 16.0 * nsd,
+                    launch_spmm32(cs, s, n, A->rowptr, A->colind, a32v, Vin, Wout), "A V (FP32)");
+            }
+        } else {
+            const double *Zj = Vin;
+            if (P) {
+                if ((st = apply_rm(ctx, P, s, Vin, w.Z, w.T0, w.T1))) return st;
+                Zj = w.Z;
+            }
+            PKL("spmm_A", 2.0 * A->nnz * s, 12.0 * A->nnz + 4.0 * (n + 1) + 16.0 * nsd,
+                launch_spmm(cs, s, n, A->rowptr, A->colind, A->val, Zj, Wout), "A Z");
+        }
+        return SPAI_OK;
+    };
+    // Out += P Din (the preconditioner in the solve's arithmetic); Din is left as it is
+    auto add_precond = [&](const double *Din, double *Out) -> spai_status {
+        const double *U = Din;
+        if (P && mixed) {
+            if ((st = apply32<double>(ctx, P, s, Din, w.Z, t032, t132))) return st;
+            U = w.Z;
+        } else if (P) {
+            if ((st = apply_rm(ctx, P, s, Din, w.Z, w.T0, w.T1))) return st;
+            U = w.Z;
+        }
+        PKL("axpy", 2.0 * nsd, 24.0 * nsd, launch_axpy(cs, (int64_t)blk_elems, 1.0, U, Out), "X update");
+        return SPAI_OK;
+    };
+    // H = V_{0..nb-1}^T Wsrc over the first nb basis slots
+    auto gram_any = [&](int nb, double *Wsrc, double *H) -> spai_status {
+        if (use_digits && (opts->orth == SPAI_ORTH_TENSOR || nb >= 2)) return gram_tc(nb, Wsrc, H);
+        PKL("block_dot", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
+            launch_block_dot(cs, s, n, nb, w.V, Wsrc, w.partial, H, chunks), "block Gram product");
+        return SPAI_OK;
+    };
+    if (rc) KL(launch_zero(cs, (int64_t)blk_elems, w.Xh), "zero the GCRO iterate");
+    // the recycled space's image: C T = A P U block by block (two passes of block CGS against
+    // the C blocks before it, Cholesky-QR), C_i in basis slot i, U <- U T^{-1} in place
+    for (int i = 0; i < kb; ++i) {
+        double *Ui = rc->U + (size_t)i * blk_elems;
+        if ((st = apply_op(Ui, w.W))) return st;
+        if ((st = colnorms(w.W, w.ref2))) return st;
+        if (i > 0) {
+            if ((st = gram_any(i, w.W, w.H1))) return st;
+            if ((st = vupdate(i, w.H1, w.W, w.W, -1.0))) return st;
+            if ((st = gram_any(i, w.W, w.H2))) return st;
+            if ((st = vupdate(i, w.H2, w.W, w.W, -1.0))) return st;
+            KL(launch_axpy(cs, (int64_t)i * s * s, 1.0, w.H2, w.H1), "T column");
+        }
+        if ((st = cholqr2(ctx, w, n, s, w.W, w.V + (size_t)i * blk_elems, w.Rn, w.ref2,
+                          (use_digits && !halves) ? i : -1, ipad)))
+            return st;
+        if ((st = fixed16(i))) return st;
+        // U_i <- (U_i - U_{<i} T_{<i,i}) T_ii^{-1}; columns deflated in the Cholesky-QR -> 0
+        if (i > 0) KL(launch_block_update(cs, s, n, i, rc->U, w.H1, Ui, w.D, -1.0), "recycled space");
+        KL(launch_trsm_rows(cs, s, n, i > 0 ? w.D : Ui, w.Rn, w.defl2, Ui), "recycled space");
+    }
+    if ((st = residual())) return st;
     int cycles = 0, iters = 0;
     while (!converged() && cycles < opts->max_cycles) {
         ++cycles;
+        if (kb > 0) {
+            // start from the residual projected off C: X~ += U C^T R, R -= C C^T R
+            if ((st = gram_any(kb, w.W, w.H1))) return st;
+            KL(launch_block_update(cs, s, n, kb, rc->U, w.H1, nullptr, w.D, 1.0), "U C^T R");
+            if ((st = vupdate(kb, w.H1, w.W, w.W, -1.0))) return st;
+            KL(launch_axpy(cs, (int64_t)blk_elems, 1.0, w.D, w.Xh), "GCRO iterate");
+            if ((st = add_precond(w.D, w.Xw))) return st;
+            if ((st = colnorms(w.W, w.ref2))) return st;
+            CU(cudaMemcpyAsync(h + 16, w.ref2, s * 8, cudaMemcpyDeviceToHost, cs), "read norms");
+            CU(cudaStreamSynchronize(cs), "sync");
+            if (converged()) {  // the recycled space held the solution: confirm with the true residual
+                if ((st = residual())) return st;
+                continue;
+            }
+        }
         if (mixed) {
             // iterative refinement: this cycle solves the correction equation from the FP64 true
             // residual r; its FP32 operator resolves r only to ~FP32 rounding, so the cycle stops
@@ -2471,57 +2580,32 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
             for (int i = 0; i < s; ++i) cthr[i] = std::max(thresh[i], kMixedCycleReduction * sqrt(h[16 + i]));
             CU(cudaMemcpyAsync(w.thresh, cthr, s * 8, cudaMemcpyHostToDevice, cs), "write thresholds");
         }
-        // V_0 S_0 = R (ref2 holds the residual norms^2)
-        if ((st = cholqr2(ctx, w, n, s, w.W, w.V, w.Rn, w.ref2, (use_digits && !halves) ? 0 : -1, ipad))) return st;
-        if ((st = fixed16(0))) return st;
-        PKL("small_dense", 0.0, 0.0, launch_set_rhs(cs, s, m, w.Rn, w.G), "rhs");
+        // V_0 S_0 = R (ref2 holds the residual norms^2), in basis slot kb
+        if ((st = cholqr2(ctx, w, n, s, w.W, w.V + (size_t)kb * blk_elems, w.Rn, w.ref2,
+                          (use_digits && !halves) ? kb : -1, ipad)))
+            return st;
+        if ((st = fixed16(kb))) return st;
+        PKL("small_dense", 0.0, 0.0, launch_ls_prefix(cs, s, kb, mt, w.Rn, w.Qs, w.Rtri, w.G), "rhs");
         int J = 0;
         for (int j = 0; j < m; ++j) {
-            const double *Vj = w.V + (size_t)j * blk_elems;
-            const double *Zj = Vj;
-            if (mixed) {
-                if (P) {
-                    if ((st = apply32<float>(ctx, P, s, Vj, z32, t032, t132))) return st;
-                    PKL("spmm32_A", 2.0 * nnzA * s, 8.0 * nnzA + 4.0 * (n + 1) + 12.0 * nsd,
-                        launch_spmm32(cs, s, n, A->rowptr, A->colind, a32v, (const float *)z32, w.W), "A Z (FP32)");
-                } else {
-                    PKL("spmm32_A", 2.0 * nnzA * s, 8.0 * nnzA + 4.0 * (n + 1) + 16.0 * nsd,
-                        launch_spmm32(cs, s, n, A->rowptr, A->colind, a32v, Vj, w.W), "A V (FP32)");
-                }
-            } else {
-                if (P) {
-                    if ((st = apply_rm(ctx, P, s, Vj, w.Z, w.T0, w.T1))) return st;
-                    Zj = w.Z;
-                }
-                PKL("spmm_A", 2.0 * A->nnz * s, 12.0 * A->nnz + 4.0 * (n + 1) + 16.0 * nsd,
-                    launch_spmm(cs, s, n, A->rowptr, A->colind, A->val, Zj, w.W), "A Z");
-            }
+            const double *Vj = w.V + (size_t)(kb + j) * blk_elems;
+            if ((st = apply_op(Vj, w.W))) return st;
             if ((st = colnorms(w.W, w.ref2))) return st;
-            // two passes of block classical Gram-Schmidt against V_0..V_j
-            const double nb = j + 1;
-            const bool tc = use_digits && (opts->orth == SPAI_ORTH_TENSOR || j + 1 >= 2);
-            if (tc) {
-                if ((st = gram_tc(j + 1, w.W, w.H1))) return st;
-            } else {
-                PKL("block_dot", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
-                    launch_block_dot(cs, s, n, j + 1, w.V, w.W, w.partial, w.H1, chunks), "H1");
-            }
-            if ((st = vupdate(j + 1, w.H1, w.W, w.W, -1.0))) return st;
-            if (tc) {
-                if ((st = gram_tc(j + 1, w.W, w.H2))) return st;
-            } else {
-                PKL("block_dot", 2.0 * nsd * s * nb, 8.0 * nsd * (nb + 1),
-                    launch_block_dot(cs, s, n, j + 1, w.V, w.W, w.partial, w.H2, chunks), "H2");
-            }
-            if ((st = vupdate(j + 1, w.H2, w.W, w.W, -1.0))) return st;
-            double *Vn = w.V + (size_t)(j + 1) * blk_elems;
+            // two passes of block classical Gram-Schmidt against C_0..C_{kb-1}, V_0..V_j
+            const int nb = kb + j + 1;
+            if ((st = gram_any(nb, w.W, w.H1))) return st;
+            if ((st = vupdate(nb, w.H1, w.W, w.W, -1.0))) return st;
+            if ((st = gram_any(nb, w.W, w.H2))) return st;
+            if ((st = vupdate(nb, w.H2, w.W, w.W, -1.0))) return st;
+            double *Vn = w.V + (size_t)(kb + j + 1) * blk_elems;
             // the new block's fixed point (for the products of the next steps) comes with it
-            if ((st = cholqr2(ctx, w, n, s, w.W, Vn, w.Rn, w.ref2, (use_digits && !halves && j + 1 < m) ? j + 1 : -1,
-                              ipad)))
+            if ((st = cholqr2(ctx, w, n, s, w.W, Vn, w.Rn, w.ref2,
+                              (use_digits && !halves && j + 1 < m) ? kb + j + 1 : -1, ipad)))
                 return st;
-            if (j + 1 < m && (st = fixed16(j + 1))) return st;
-            PKL("arnoldi_ls", 16.0 * s * s * s * (j + 1), 0.0,
-                launch_arnoldi_ls(cs, s, j, m, w.H1, w.H2, w.Rn, w.Qs, w.Rtri, w.G, w.thresh, w.est, w.flag), "least squares");
+            if (j + 1 < m && (st = fixed16(kb + j + 1))) return st;
+            PKL("arnoldi_ls", 16.0 * s * s * s * (nb), 0.0,
+                launch_arnoldi_ls(cs, s, kb + j, mt, w.H1, w.H2, w.Rn, w.Qs, w.Rtri, w.G, w.thresh, w.est, w.flag),
+                "least squares");
             CU(cudaMemcpyAsync(h + 32, w.est, s * 8, cudaMemcpyDeviceToHost, cs), "read estimates");
             CU(cudaMemcpyAsync(h + 48, w.flag, 4, cudaMemcpyDeviceToHost, cs), "read flag");
             CU(cudaMemcpyAsync(h + 49, ctx->d_err, 4, cudaMemcpyDeviceToHost, cs), "read error word");
@@ -2536,19 +2620,17 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
             }
             if (*(int32_t *)(h + 48)) break;
         }
-        // X += P (V Y)
-        PKL("backsolve", (double)J * s * J * s * s, 0.0, launch_backsolve(cs, s, J, (m + 1) * s, w.Rtri, w.G, w.Y),
-            "back substitution");
-        if ((st = vupdate(J, w.Y, nullptr, w.W, 1.0))) return st;
-        const double *U = w.W;
-        if (P && mixed) {
-            if ((st = apply32<double>(ctx, P, s, w.W, w.Z, t032, t132))) return st;
-            U = w.Z;
-        } else if (P) {
-            if ((st = apply_rm(ctx, P, s, w.W, w.Z, w.T0, w.T1))) return st;
-            U = w.Z;
+        // X += P ([U, V] Y)
+        PKL("backsolve", (double)(kb + J) * s * (kb + J) * s * s, 0.0,
+            launch_backsolve(cs, s, kb + J, (mt + 1) * s, w.Rtri, w.G, w.Y), "back substitution");
+        if (kb > 0) {
+            KL(launch_block_update(cs, s, n, kb, rc->U, w.Y, nullptr, w.D, 1.0), "U Y_U");
+            if ((st = vupdate_at(kb, J, w.Y + (size_t)kb * s * s, w.D, w.W, 1.0))) return st;
+        } else {
+            if ((st = vupdate(J, w.Y, nullptr, w.W, 1.0))) return st;
         }
-        PKL("axpy", 2.0 * nsd, 24.0 * nsd, launch_axpy(cs, (int64_t)blk_elems, 1.0, U, w.Xw), "X update");
+        if (rc) KL(launch_axpy(cs, (int64_t)blk_elems, 1.0, w.W, w.Xh), "GCRO iterate");
+        if ((st = add_precond(w.W, w.Xw))) return st;
         if ((st = residual())) return st;
     }
     // solution out
@@ -2584,6 +2666,94 @@ extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, i
     }
     if (!conv) return fail(ctx, SPAI_ENOTCONV, "not converged after %d cycles: column %d relative residual %.3e",
                            cycles, worst, worst_rel);
+    if (rc && kbmax > 0) {
+        // the solve's iterate joins the recycled space (the oldest block leaves a full one)
+        if (kb == kbmax) {
+            for (int i = 0; i + 1 < kbmax; ++i)
+                CU(cudaMemcpyAsync(rc->U + (size_t)i * blk_elems, rc->U + (size_t)(i + 1) * blk_elems, blk_elems * 8,
+                                   cudaMemcpyDeviceToDevice, cs),
+                   "recycled space");
+            kb = kbmax - 1;
+        }
+        CU(cudaMemcpyAsync(rc->U + (size_t)kb * blk_elems, w.Xh, blk_elems * 8, cudaMemcpyDeviceToDevice, cs),
+           "recycled space");
+        rc->k = (kb + 1) * s;
+        CU(cudaStreamSynchronize(cs), "sync");
+    }
+    return SPAI_OK;
+}
+
+}  // namespace
+
+extern "C" spai_status block_solve(spai_ctx ctx, const spai_csr *A, spai_pc P, int32_t s, const double *B,
+                                   int64_t ldb, double *X, int64_t ldx, const spai_solve_opts *opts,
+                                   spai_solve_info *info, double *rel_residual)
+{
+    return solve_impl(ctx, A, P, s, B, ldb, X, ldx, opts, info, rel_residual, nullptr);
+}
+
+extern "C" spai_status block_solve_gcro(spai_ctx ctx, const spai_csr *A, spai_pc P, int32_t s, const double *B,
+                                        int64_t ldb, double *X, int64_t ldx, const spai_solve_opts *opts,
+                                        spai_recycle rc, spai_solve_info *info, double *rel_residual)
+{
+    if (!ctx) return SPAI_EINVAL;
+    if (!rc) return fail(ctx, SPAI_EINVAL, "NULL recycle space");
+    return solve_impl(ctx, A, P, s, B, ldb, X, ldx, opts, info, rel_residual, rc);
+}
+
+extern "C" spai_status spai_recycle_create(spai_ctx ctx, int32_t n, int32_t s, int32_t kmax, spai_recycle *out)
+{
+    if (!ctx || !out) return fail(ctx, SPAI_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (n < 1 || !valid_s(s) || kmax < 0 || kmax % s != 0 || kmax / s > kMaxRecycleBlocks)
+        return fail(ctx, SPAI_EINVAL, "recycle space: n >= 1, s in {1,2,4,8,16}, kmax a multiple of s, kmax / s <= %d",
+                    kMaxRecycleBlocks);
+    spai_recycle r = new spai_recycle_s();
+    r->ctx = ctx;
+    r->n = n;
+    r->s = s;
+    r->kmax = kmax;
+    if (kmax > 0) {
+        spai_status st = dalloc_n(ctx, &r->U, (int64_t)n * kmax);
+        if (st) {
+            delete r;
+            return st;
+        }
+    }
+    *out = r;
+    return SPAI_OK;
+}
+
+extern "C" spai_status spai_recycle_info(spai_recycle r, int32_t *k)
+{
+    if (!r) return SPAI_EINVAL;
+    if (k) *k = r->k;
+    return SPAI_OK;
+}
+
+extern "C" spai_status spai_recycle_export(spai_ctx ctx, spai_recycle r, double *U, int64_t ldu)
+{
+    if (!ctx || !r) return fail(ctx, SPAI_EINVAL, "NULL argument");
+    if (r->k == 0) return SPAI_OK;
+    if (!U || ldu < r->n) return fail(ctx, SPAI_EINVAL, "bad export arguments");
+    const int32_t s = r->s, n = r->n;
+    for (int i = 0; i < r->k / s; ++i)
+        KL(launch_unpack(ctx->stream, s, n, r->U + (size_t)i * n * s, U + (size_t)i * s * ldu, ldu), "unpack");
+    return SPAI_OK;
+}
+
+extern "C" spai_status spai_recycle_clear(spai_recycle r)
+{
+    if (!r) return SPAI_EINVAL;
+    r->k = 0;
+    return SPAI_OK;
+}
+
+extern "C" spai_status spai_recycle_destroy(spai_recycle r)
+{
+    if (!r) return SPAI_EINVAL;
+    dfree(r->ctx, r->U);
+    delete r;
     return SPAI_OK;
 }
 

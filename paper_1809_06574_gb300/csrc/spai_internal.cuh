@@ -326,6 +326,9 @@ int launch_arnoldi_ls(cudaStream_t st, int32_t s, int32_t j, int32_t m, const do
                       const double *Rsub, double *Qs, double *Rtri, double *G, const double *thresh, double *est,
                       int32_t *flag);
 int launch_set_rhs(cudaStream_t st, int32_t s, int32_t m, const double *S0, double *G);
+// least-squares state with kb identity block columns first (recycled space), S0 at block kb
+int launch_ls_prefix(cudaStream_t st, int32_t s, int32_t kb, int32_t m, const double *S0, double *Qs, double *Rtri,
+                     double *G);
 int launch_backsolve(cudaStream_t st, int32_t s, int32_t J, int32_t ldr, const double *Rtri,
                      const double *G, double *Y);
 int launch_axpy(cudaStream_t st, int64_t count, double alpha, const double *x, double *y);
