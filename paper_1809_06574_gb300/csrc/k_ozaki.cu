@@ -61,7 +61,10 @@ constexpr int kCT = 32 * kCW;      // converter threads
 constexpr int kThreadsTC = 64 + 128 + kCT;  // copy warp, MMA warp, 4 drain warps, converters
 constexpr int kRawRow = kS * 8;    // 64 bytes: one row of an n x 8 block
 constexpr unsigned long long kWaitNs = 1000000000ull;  // drain waits give up after 1 s
-constexpr unsigned kSuspendNs = 20000;                  // suspend hint of one try_wait
+#ifndef SPAI_TC_SUSPEND_NS
+#define SPAI_TC_SUSPEND_NS 20000
+#endif
+constexpr unsigned kSuspendNs = SPAI_TC_SUSPEND_NS;     // suspend hint of one try_wait
 static_assert(8 * 64 * 64 * kSegK <= (1 << 24), "exact FP32 class sums");
 static_assert(kClsCols == 5 * 16, "drain_classes reads five 16-column groups");
 
