@@ -62,8 +62,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-fifo-seconds", type=float, default=2.0)
     ap.add_argument("--serve-slots", type=int, default=4)
-    ap.add_argument("--serve-rates", default="400,800", help="further offered rates of the serving workload")
-    ap.add_argument("--serve-rate-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-rates", default="300,400", help="further offered rates of the serving workload")
+    ap.add_argument("--serve-rate-seconds", type=float, default=4.0)
     ap.add_argument("--no-served-sweep", action="store_true")
     ap.add_argument("--gcro-kmax", type=int, default=16, help="recycled columns per shift of the block GCRO leg")
     # large workload: 3D 128^3 27-point grid, 16 RHS, BF16-stored SPAI, update vs rebuild
@@ -1349,7 +1349,7 @@ def main():
     # the headline's sweep through the server at saturation, beside the plain FP64 sweep
     served_cap = None
     if rank == 0 and world == 1 and not args.no_served_sweep:
-        served_cap = run_served_sweep(args, sg, torch, w, args.steps)
+        served_cap = run_served_sweep(args, sg, torch, w, min(args.steps, 5))
         served_cap["vs_plain_fp64"] = served_cap["value"] / value
     if mixed is not None:
         mixed["vs_plain_fp64"] = mixed["value"] / value
