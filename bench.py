@@ -49,7 +49,7 @@ def parse():
     # host threads (each with its own stream and context) sharing a shift's independent solves
     ap.add_argument("--workers", type=int, default=4)
     # single-kernel case (for profiler captures): H = V^T W or W -= V H at n = side^3, s = 8
-    ap.add_argument("--kernel", default=None, choices=["dot", "update", "columns"])
+    ap.add_argument("--kernel", default=None, choices=["dot", "update", "columns", "spmm32", "spmm"])
     ap.add_argument("--columns-workload", default="batched2d", choices=["batched2d", "sweep3d", "adaptive3d"],
                     help="--kernel columns: the batched 2D systems (FP32), one FP64 SPAI of the 3D sweep, "
                          "or one adaptive SPAI of the 3D sweep's matrix (--side sets the grid)")
@@ -157,13 +157,15 @@ def _peaks():
 
 # FP64 ALU peak from unit counts and clock: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2.07 GHz
 FP64_NOMINAL_TFLOPS = 152 * 4 * 2070e6 / 1e12
-# one FP64-accurate product of the digit kernels costs 53 BF16 digit-pair products
-DIGIT_PRODUCTS = 53
+# FP32 ALU peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
+# one FP64-accurate product of the digit kernels costs 43 BF16 digit-pair products
+DIGIT_PRODUCTS = 43
 # how each kernel family computes: FP64 ALUs, tensor cores (digit products), or neither
 FAMILY_UNIT = {
     "block_dot_tc": "tensor", "block_update_tc": "tensor", "to_fixed": "none",
     "axpy": "none", "gather_csc": "none", "small_dense": "latency", "arnoldi_ls": "latency",
-    "backsolve": "latency",
+    "backsolve": "latency", "spmm32_A": "fp32", "spmm32_P": "fp32", "scale_rows32": "fp32", "round_f32": "none",
 }
 # DRAM bytes per launch, (a * blocks + b) * n * s, where blocks = algorithmic bytes per launch
 # / (8 n s) (the Gram product: basis blocks + W; the update: basis blocks + W read and
@@ -171,8 +173,8 @@ FAMILY_UNIT = {
 # s = 8, 16 basis blocks (read + write bytes; summarised under profiles/).  A family is
 # left out (traffic null) while its kernel has changed since its capture.
 NCU_TRAFFIC = {
-    "block_dot_tc": (8.0, (296.057e6 + 3.242e6) / 2097152 - 8.0 * 17),
-    "block_update_tc": (8.0, (285.324e6 + 11.673e6) / 2097152 - 8.0 * 18),
+    "block_dot_tc": (8.0, (296.019e6 + 3.201e6) / 2097152 - 8.0 * 17),
+    "block_update_tc": (8.0, (285.285e6 + 11.929e6) / 2097152 - 8.0 * 18),
 }
 
 
@@ -193,7 +195,8 @@ def roofline_entry(f, n, s, fp64_probe=None):
         out.update({"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
                     "traffic": None})
         return out
-    cpeak = FP64_NOMINAL_TFLOPS if unit == "fp64" else (bf16_sus / DIGIT_PRODUCTS if unit == "tensor" else 0.0)
+    cpeak = {"fp64": FP64_NOMINAL_TFLOPS, "fp32": FP32_NOMINAL_TFLOPS,
+             "tensor": bf16_sus / DIGIT_PRODUCTS}.get(unit, 0.0)
     t_hbm = f["bytes"] / (hbm * 1e9)
     t_alu = f["flops"] / (cpeak * 1e12) if cpeak > 0 else 0.0
     if t_hbm >= t_alu:
@@ -203,8 +206,10 @@ def roofline_entry(f, n, s, fp64_probe=None):
     else:
         ach = f["flops"] / sec / 1e12
         out.update({"bound": "alu", "achieved": ach, "peak": cpeak, "unit": "TFLOP/s", "frac": ach / cpeak,
-                    "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz"
-                    + (f"; FMA probe measured {fp64_probe:.3f} TFLOP/s in this run" if fp64_probe else "")})
+                    "peak_source": ("derived: 152 SM x 256 FP32 flop/clk x 2.07 GHz" if unit == "fp32" else
+                                    "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz"
+                                    + (f"; FMA probe measured {fp64_probe:.3f} TFLOP/s in this run"
+                                       if fp64_probe else ""))})
     out["traffic"] = None
     if f["name"] in NCU_TRAFFIC and f["bytes"] > 0:
         a, b = NCU_TRAFFIC[f["name"]]
@@ -271,12 +276,50 @@ def run_columns_case(args):
           flush=True)
 
 
+def run_spmm_case(args):
+    """Y = A X on its own at the sweep's size: A(p_1, s_1) of the 3D side^3 7-point workload,
+    X n x 8; `spmm32` the FP32 operator of the mixed solve, `spmm` the FP64 product."""
+    import torch
+    import paper_1809_06574_gb300 as sg
+    import synth
+    w = synth.grid3d_7pt(side=args.side, nparams=2)
+    n, s = w.n, 8
+    stream = torch.cuda.current_stream()
+    ctx = sg.spai_ctx_create(stream.cuda_stream, 0)
+    d_terms = [tuple(torch.as_tensor(np.ascontiguousarray(a), device="cuda") for a in tr) for tr in w.terms]
+    aff = sg.spai_affine_create(ctx, [sg.csr(n, *tr) for tr in d_terms])
+    _, nnz, rp, ci = sg.spai_affine_pattern(aff)
+    va = torch.empty(nnz, dtype=torch.float64, device="cuda")
+    sg.spai_assemble_shifted(ctx, aff, w.shifts[0], w.params[0], w.alpha, w.beta, va)
+    A = sg.csr(n, rp, ci, va, nnz)
+    g = torch.Generator(device="cpu").manual_seed(0)
+    X = torch.randn(s, n, dtype=torch.float64, generator=g).cuda()
+    Y = torch.empty_like(X)
+    f = sg.spai_spmm_fp32 if args.kernel == "spmm32" else sg.spai_spmm
+    for _ in range(max(args.warmup, 1)):
+        f(ctx, A, s, X, n, Y, n)
+    sg.spai_ctx_profile(ctx, 1)
+    for _ in range(args.steps):
+        f(ctx, A, s, X, n, Y, n)
+    torch.cuda.synchronize()
+    prof = [sg.spai_ctx_profile_entry(ctx, i) for i in range(sg.spai_ctx_profile_count(ctx))]
+    prof = [p for p in prof if not p["name"].startswith("idle:")]
+    sg.spai_affine_destroy(aff)
+    sg.spai_ctx_destroy(ctx)
+    fams = {p["name"]: roofline_entry(p, n=n, s=s) for p in prof}
+    print(json.dumps({"kernel_case": args.kernel, "n": n, "nnz": nnz, "s": s, "steps": args.steps,
+                      "families": fams}), flush=True)
+
+
 def run_kernel_case(args):
     """One kernel on its own at the sweep's size: H = V^T W (dot) or W -= V H (update)."""
     import torch
     import paper_1809_06574_gb300 as sg
     if args.kernel == "columns":
         run_columns_case(args)
+        return
+    if args.kernel in ("spmm32", "spmm"):
+        run_spmm_case(args)
         return
     n, s, nb = args.side ** 3, 8, args.nblk
     g = torch.Generator(device="cpu").manual_seed(0)

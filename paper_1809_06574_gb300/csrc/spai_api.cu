@@ -2100,7 +2100,8 @@ extern "C" spai_status spai_spmm(spai_ctx ctx, const spai_csr *A, int32_t s, con
     if ((st = temp_blocks(ctx, 2 * blk, &w))) return st;
     double *xr = (double *)w, *yr = (double *)((char *)w + blk);
     KL(launch_pack(ctx->stream, s, n, X, ldx, xr), "pack");
-    KL(launch_spmm(ctx->stream, s, n, A->rowptr, A->colind, A->val, xr, yr), "spmm");
+    PKL("spmm_A", 2.0 * A->nnz * s, 12.0 * A->nnz + 4.0 * (n + 1) + 16.0 * n * s,
+        launch_spmm(ctx->stream, s, n, A->rowptr, A->colind, A->val, xr, yr), "spmm");
     KL(launch_unpack(ctx->stream, s, n, yr, Y, ldy), "unpack");
     return SPAI_OK;
 }
