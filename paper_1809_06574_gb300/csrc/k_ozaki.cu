@@ -277,59 +277,38 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_
         : "memory");
 }
 
-// fixed-point magnitude round(|x| * 2^(54 - e)) (half away from zero) from the IEEE bits
-// (integer ops only); false if |x| * 2^-e >= 2
-__device__ __forceinline__ bool fixed_mag(double x, int e, uint64_t &mag, uint32_t &neg)
-{
-    const uint64_t bits = (uint64_t)__double_as_longlong(x);
-    neg = (uint32_t)(bits >> 63);
-    const int ex = (int)((bits >> 52) & 0x7FF);
-    if (ex == 0) {  // zero or subnormal: below the fixed-point resolution
-        mag = 0;
-        return true;
-    }
-    const uint64_t mant = (bits & ((1ull << 52) - 1)) | (1ull << 52);
-    const int shift = ex - 1021 - e;  // mag = mant * 2^shift
-    if (shift > 2) {
-        mag = 0;
-        return false;
-    }
-    if (shift >= 0) {
-        mag = mant << shift;
-    } else if (shift > -64) {
-        const int rs = -shift;
-        mag = (mant >> rs) + ((mant >> (rs - 1)) & 1ull);
-    } else {
-        mag = 0;
-    }
-    return true;
-}
-
 // sum over i < 8 of 64 * 128^i: m + kBdOffset has the base-128 digits d_i + 64 of the
 // balanced digits d_i of m
 constexpr uint64_t kBdOffset = 0x81020408102040ull;
 constexpr uint64_t kBdZero = 0x4040404040404040ull;  // the byte digits of 0
 
+// the eight 7-bit fields of a 28-bit value, one per byte of a 32-bit word
+__device__ __forceinline__ uint32_t spread28(uint32_t x)
+{
+    return (x & 0x7Fu) | ((x << 1) & 0x7F00u) | ((x << 2) & 0x7F0000u) | ((x << 3) & 0x7F000000u);
+}
+
 // Byte digits of x at scale 2^e: byte i = d_i + 64, m = round(x 2^(54-e)) = sum_i d_i 128^i,
-// d_i in [-64, 63].  False if |x| 2^-e >= 2, m is outside the eight digits' range, or x is
-// not finite.
+// d_i in [-64, 63].  The scaling by a power of two is exact and m is rounded to nearest
+// (ties to even) by the conversion to a 64-bit integer; the bytes are the base-128 digits
+// of m + kBdOffset.  False if |x| 2^-e >= 2, m is outside the eight digits' range, or x is
+// not finite (the conversion of a NaN or an infinity lands outside that range too).
 __device__ __forceinline__ bool to_bdigits(double x, int e, uint64_t &word)
 {
-    uint64_t mag;
-    uint32_t neg;
-    bool ok = fixed_mag(x, e, mag, neg);
-    const long long m = neg ? -(long long)mag : (long long)mag;
+    // x 2^(54 - e) in two exact power-of-two factors, each a normal double (the scale of a
+    // column of tiny values can exceed 2^1023)
+    const int k = 54 - e, k1 = k > 1023 ? 1023 : (k < -1022 ? -1022 : k), k2 = k - k1;
+    double scaled = x * __longlong_as_double((long long)(1023 + k1) << 52);
+    if (k2 != 0) scaled *= __longlong_as_double((long long)(1023 + (k2 > 1023 ? 1023 : (k2 < -1022 ? -1022 : k2))) << 52);
+    const bool in_range = fabs(scaled) < 0x1p55;  // |x| 2^-e < 2 (false for NaN)
+    const long long m = in_range ? __double2ll_rn(scaled) : 0;
     const uint64_t u = (uint64_t)(m + (long long)kBdOffset);
-    if (u >> 56) {  // outside [-kBdOffset, 2^56 - kBdOffset)
-        ok = false;
+    if (!in_range || (u >> 56)) {  // outside [-kBdOffset, 2^56 - kBdOffset) or |x| 2^-e >= 2
         word = kBdZero;
-    } else {
-        // the eight 7-bit fields of u, one per byte
-        word = (u & 0x7Full) | ((u << 1) & (0x7Full << 8)) | ((u << 2) & (0x7Full << 16)) |
-               ((u << 3) & (0x7Full << 24)) | ((u << 4) & (0x7Full << 32)) | ((u << 5) & (0x7Full << 40)) |
-               ((u << 6) & (0x7Full << 48)) | ((u << 7) & (0x7Full << 56));
+        return false;
     }
-    return ok;
+    word = (uint64_t)spread28((uint32_t)u & 0x0FFFFFFFu) | ((uint64_t)spread28((uint32_t)(u >> 28)) << 32);
+    return true;
 }
 
 // Eight BF16 digit planes of 8 values in byte-digit form (8 consecutive rows of one
