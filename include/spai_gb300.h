@@ -358,9 +358,10 @@ SPAI_API spai_status spai_pc_apply(spai_ctx ctx, spai_pc pc, int32_t s, const do
                           double *Y, int64_t ldy);
 
 /* The FP32 operator of SPAI_SOLVE_MIXED (see block_solve) on its own: Y = A X and Y = P X
- * with the matrix's or factors' values and X rounded to FP32, products and sums in FP32 in
- * each row's order (a factored chain keeps its intermediate blocks in FP32), Y written as
- * FP64 (exact).  Arguments as spai_spmm / spai_pc_apply.  Asynchronous. */
+ * with the matrix's or factors' values and X rounded to FP32 (X once, before the product,
+ * as the solve keeps its newest basis block in FP32), products and sums in FP32 in each
+ * row's order (a factored chain keeps its intermediate blocks in FP32), Y written as FP64
+ * (exact).  Arguments as spai_spmm / spai_pc_apply.  Asynchronous. */
 SPAI_API spai_status spai_spmm_fp32(spai_ctx ctx, const spai_csr *A, int32_t s, const double *X, int64_t ldx,
                                     double *Y, int64_t ldy);
 SPAI_API spai_status spai_pc_apply_fp32(spai_ctx ctx, spai_pc pc, int32_t s, const double *X, int64_t ldx,

@@ -453,7 +453,8 @@ template <int S>
 __global__ void __launch_bounds__(kThreads) k_cqr_apply(int32_t n, const double *W, const double *__restrict__ R1,
                                                         const int32_t *__restrict__ defl1,
                                                         const double *__restrict__ R2,
-                                                        const int32_t *__restrict__ defl2, double *Q)
+                                                        const int32_t *__restrict__ defl2, double *Q,
+                                                        float *__restrict__ Q32)
 {
     __shared__ double Rs1[S * S], Rs2[S * S];
     __shared__ double rinv1[S], rinv2[S];
@@ -473,6 +474,10 @@ __global__ void __launch_bounds__(kThreads) k_cqr_apply(int32_t n, const double 
     trsm_row<S>(x, Rs1, rinv1);
     trsm_row<S>(x, Rs2, rinv2);
     row_store<S>(Q, r, x);
+    if (Q32) {
+#pragma unroll
+        for (int a = 0; a < S; ++a) Q32[r * S + a] = (float)x[a];
+    }
 }
 
 template <int S>
@@ -1134,9 +1139,9 @@ int launch_cqr_gram2(cudaStream_t st, int32_t s, int32_t n, const double *W, con
 }
 
 int launch_cqr_apply(cudaStream_t st, int32_t s, int32_t n, const double *W, const double *R1, const int32_t *defl1,
-                     const double *R2, const int32_t *defl2, double *Q)
+                     const double *R2, const int32_t *defl2, double *Q, float *Q32)
 {
-    SPAI_DISPATCH_S8(s, (k_cqr_apply<S><<<grid_for(n), kThreads, 0, st>>>(n, W, R1, defl1, R2, defl2, Q)));
+    SPAI_DISPATCH_S8(s, (k_cqr_apply<S><<<grid_for(n), kThreads, 0, st>>>(n, W, R1, defl1, R2, defl2, Q, Q32)));
     return check_launch();
 }
 

@@ -288,22 +288,46 @@ __device__ __forceinline__ uint32_t spread28(uint32_t x)
     return (x & 0x7Fu) | ((x << 1) & 0x7F00u) | ((x << 2) & 0x7F0000u) | ((x << 3) & 0x7F000000u);
 }
 
+// fixed-point magnitude round(|x| * 2^(54 - e)) (half away from zero) from the IEEE bits
+// (integer operations only: the FP64 conversions are slow on this GPU); false if
+// |x| * 2^-e >= 2 or x is not finite
+__device__ __forceinline__ bool fixed_mag(double x, int e, uint64_t &mag, uint32_t &neg)
+{
+    const uint64_t bits = (uint64_t)__double_as_longlong(x);
+    neg = (uint32_t)(bits >> 63);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    if (ex == 0) {  // zero or subnormal: below the fixed-point resolution
+        mag = 0;
+        return true;
+    }
+    const uint64_t mant = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+    const int shift = ex - 1021 - e;  // mag = mant * 2^shift
+    if (shift > 2) {
+        mag = 0;
+        return false;
+    }
+    if (shift >= 0) {
+        mag = mant << shift;
+    } else if (shift > -64) {
+        const int rs = -shift;
+        mag = (mant >> rs) + ((mant >> (rs - 1)) & 1ull);
+    } else {
+        mag = 0;
+    }
+    return true;
+}
+
 // Byte digits of x at scale 2^e: byte i = d_i + 64, m = round(x 2^(54-e)) = sum_i d_i 128^i,
-// d_i in [-64, 63].  The scaling by a power of two is exact and m is rounded to nearest
-// (ties to even) by the conversion to a 64-bit integer; the bytes are the base-128 digits
-// of m + kBdOffset.  False if |x| 2^-e >= 2, m is outside the eight digits' range, or x is
-// not finite (the conversion of a NaN or an infinity lands outside that range too).
+// d_i in [-64, 63]: the bytes are the base-128 digits of m + kBdOffset.  False if
+// |x| 2^-e >= 2, m is outside the eight digits' range, or x is not finite.
 __device__ __forceinline__ bool to_bdigits(double x, int e, uint64_t &word)
 {
-    // x 2^(54 - e) in two exact power-of-two factors, each a normal double (the scale of a
-    // column of tiny values can exceed 2^1023)
-    const int k = 54 - e, k1 = k > 1023 ? 1023 : (k < -1022 ? -1022 : k), k2 = k - k1;
-    double scaled = x * __longlong_as_double((long long)(1023 + k1) << 52);
-    if (k2 != 0) scaled *= __longlong_as_double((long long)(1023 + (k2 > 1023 ? 1023 : (k2 < -1022 ? -1022 : k2))) << 52);
-    const bool in_range = fabs(scaled) < 0x1p55;  // |x| 2^-e < 2 (false for NaN)
-    const long long m = in_range ? __double2ll_rn(scaled) : 0;
+    uint64_t mag;
+    uint32_t neg;
+    const bool ok = fixed_mag(x, e, mag, neg);
+    const long long m = neg ? -(long long)mag : (long long)mag;
     const uint64_t u = (uint64_t)(m + (long long)kBdOffset);
-    if (!in_range || (u >> 56)) {  // outside [-kBdOffset, 2^56 - kBdOffset) or |x| 2^-e >= 2
+    if (!ok || (u >> 56)) {  // outside [-kBdOffset, 2^56 - kBdOffset)
         word = kBdZero;
         return false;
     }
@@ -415,7 +439,7 @@ __global__ void __launch_bounds__(256) k_cqr_apply_fixed(int32_t n, const double
                                                          const double *__restrict__ R2,
                                                          const int32_t *__restrict__ defl2, double *__restrict__ Q,
                                                          uint64_t *__restrict__ F_row, uint64_t *__restrict__ F_sub,
-                                                         int32_t ipad, int32_t blk, int *err)
+                                                         int32_t ipad, int32_t blk, int *err, float *__restrict__ Q32)
 {
     __shared__ double Rs1[kS * kS], Rs2[kS * kS];
     __shared__ double rinv1[kS], rinv2[kS];
@@ -440,6 +464,11 @@ __global__ void __launch_bounds__(256) k_cqr_apply_fixed(int32_t n, const double
             trsm_row<kS>(x, Rs1, rinv1);
             trsm_row<kS>(x, Rs2, rinv2);
             row_store<kS>(Q, r, x);
+            if (Q32) {  // the block in FP32: the input of the mixed solve's FP32 operator
+                float4 *q = reinterpret_cast<float4 *>(Q32 + r * kS);
+                q[0] = make_float4((float)x[0], (float)x[1], (float)x[2], (float)x[3]);
+                q[1] = make_float4((float)x[4], (float)x[5], (float)x[6], (float)x[7]);
+            }
 #pragma unroll
             for (int a = 0; a < kS; ++a)
                 if (!to_bdigits(x[a], 0, f[a])) bad = true;
@@ -1063,13 +1092,14 @@ int launch_trsm_fixed(cudaStream_t st, int32_t n, double *Q, const double *R, co
 
 int launch_cqr_apply_fixed(cudaStream_t st, int32_t n, const double *W, const double *R1, const int32_t *defl1,
                            const double *R2, const int32_t *defl2, double *Q, uint64_t *F_row, uint64_t *F_sub,
-                           int32_t ipad, int32_t blk, int *d_err)
+                           int32_t ipad, int32_t blk, int *d_err, float *Q32)
 {
     if (n <= 0) return 0;
     const int64_t rows = ((int64_t)n + kKT - 1) / kKT * kKT;
     int64_t g = (rows + 255) / 256;
     if (g > 8 * 152) g = 8 * 152;
-    k_cqr_apply_fixed<<<(unsigned)g, 256, 0, st>>>(n, W, R1, defl1, R2, defl2, Q, F_row, F_sub, ipad, blk, d_err);
+    k_cqr_apply_fixed<<<(unsigned)g, 256, 0, st>>>(n, W, R1, defl1, R2, defl2, Q, F_row, F_sub, ipad, blk, d_err,
+                                                   Q32);
     note_launches(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

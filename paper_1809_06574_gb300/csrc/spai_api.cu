@@ -754,13 +754,13 @@ spai_status apply_rm(spai_ctx ctx, spai_pc pc, int32_t s, const double *X, doubl
 // Y = P X with the FP32 operator of the mixed-precision solve: every factor's values and
 // its input rounded to FP32, products and sums in FP32; the intermediate blocks of a
 // factored chain are FP32 (t0 / t1), the last factor writes Y (FP32 or FP64).
-template <typename YT>
-spai_status apply32(spai_ctx ctx, spai_pc pc, int32_t s, const double *X, YT *Y, float *t0, float *t1)
+template <typename YT, typename XT>
+spai_status apply32(spai_ctx ctx, spai_pc pc, int32_t s, const XT *X, YT *Y, float *t0, float *t1)
 {
     std::vector<spai_pc> chain;
     for (spai_pc p = pc; p; p = p->parent) chain.push_back(p);
     const void *cur = X;
-    bool cur_f64 = true;
+    bool cur_f64 = sizeof(XT) == 8;
     float *bufs[2] = {t0, t1};
     for (size_t i = chain.size(); i-- > 0;) {
         spai_pc h = chain[i];
@@ -2137,15 +2137,17 @@ extern "C" spai_status spai_spmm_fp32(spai_ctx ctx, const spai_csr *A, int32_t s
     if (ldx < n || ldy < n || !X || !Y) return fail(ctx, SPAI_EINVAL, "bad block arguments");
     void *w = nullptr;
     const size_t blk = (size_t)n * s * 8, a32 = ((size_t)A->nnz * 4 + 255) / 256 * 256;
-    if ((st = temp_blocks(ctx, 2 * blk + a32, &w))) return st;
+    if ((st = temp_blocks(ctx, 2 * blk + a32 + blk / 2, &w))) return st;
     double *xr = (double *)w, *yr = (double *)((char *)w + blk);
     float *av = (float *)((char *)w + 2 * blk);
+    float *x32 = (float *)((char *)w + 2 * blk + a32);
     F32Vals v;
     v.f32 = av;
     KL(launch_round_f32(ctx->stream, A->nnz, A->val, av), "A in FP32");
     KL(launch_pack(ctx->stream, s, n, X, ldx, xr), "pack");
-    PKL("spmm32_A", 2.0 * A->nnz * s, 8.0 * A->nnz + 4.0 * (n + 1) + 16.0 * n * s,
-        launch_spmm32(ctx->stream, s, n, A->rowptr, A->colind, v, (const double *)xr, yr), "spmm fp32");
+    KL(launch_round_f32(ctx->stream, (int64_t)n * s, xr, x32), "X in FP32");  // once, as the solve's basis
+    PKL("spmm32_A", 2.0 * A->nnz * s, 8.0 * A->nnz + 4.0 * (n + 1) + 12.0 * n * s,
+        launch_spmm32(ctx->stream, s, n, A->rowptr, A->colind, v, (const float *)x32, yr), "spmm fp32");
     KL(launch_unpack(ctx->stream, s, n, yr, Y, ldy), "unpack");
     return SPAI_OK;
 }
@@ -2178,6 +2180,7 @@ namespace {
 struct SolveWs {
     double *Bw, *Xw, *W, *Z, *T0, *T1, *V;
     double *Xh, *D;     // block GCRO: the preconditioned-space iterate and a correction block
+    float *V32;         // mixed precision: the newest basis block in FP32 (the FP32 operator's input)
     double *partial, *H1, *H2, *G1, *R1, *R2, *Rn, *ref2, *nrm2, *thresh, *Qs, *Rtri, *G, *Y, *est;
     int32_t *defl1, *defl2, *flag;
     unsigned *ticket;   // last-CTA tickets of the fused Cholesky-QR and norm kernels (zero between launches)
@@ -2216,6 +2219,7 @@ size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks
     w.V = (double *)take(blk * (m + 1));
     w.Xh = (double *)take(blk);
     w.D = (double *)take(blk);
+    w.V32 = (float *)take(blk / 2);
     const bool digits = digits_for(s, m);
     const int32_t nh = (s == 16 ? 2 : 1) * (m + 1);  // basis (half-)blocks of the digit kernels
     {
@@ -2260,7 +2264,7 @@ size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks
 // fix_blk >= 0 (s == 8) the last pass also writes Q's fixed-point copies (basis slot fix_blk
 // of ipad) for the tensor-core products.
 spai_status cholqr2(spai_ctx ctx, SolveWs &w, int32_t n, int32_t s, const double *Win, double *Qout, double *Rout,
-                    const double *ref2, int fix_blk, int32_t ipad)
+                    const double *ref2, int fix_blk, int32_t ipad, float *Q32 = nullptr)
 {
     cudaStream_t st = ctx->stream;
     const double nsd = (double)n * s;
@@ -2274,11 +2278,11 @@ spai_status cholqr2(spai_ctx ctx, SolveWs &w, int32_t n, int32_t s, const double
         if (fix_blk >= 0) {
             PKL("cqr_apply_fixed", 2.0 * nsd * s, 32.0 * nsd,
                 launch_cqr_apply_fixed(st, n, Win, w.R1, w.defl1, w.R2, w.defl2, Qout,
-                                       w.vfix + (size_t)fix_blk * n * s, w.vfix_sub, ipad, fix_blk, ctx->d_err),
+                                       w.vfix + (size_t)fix_blk * n * s, w.vfix_sub, ipad, fix_blk, ctx->d_err, Q32),
                 "Cholesky-QR pass 3 with fixed point");
         } else {
             PKL("cqr_apply", 2.0 * nsd * s, 16.0 * nsd,
-                launch_cqr_apply(st, s, n, Win, w.R1, w.defl1, w.R2, w.defl2, Qout), "Cholesky-QR pass 3");
+                launch_cqr_apply(st, s, n, Win, w.R1, w.defl1, w.R2, w.defl2, Qout, Q32), "Cholesky-QR pass 3");
         }
         return SPAI_OK;
     } else {
@@ -2295,6 +2299,7 @@ spai_status cholqr2(spai_ctx ctx, SolveWs &w, int32_t n, int32_t s, const double
                 "fixed point");
     }
     PKL("small_dense", 0.0, 0.0, launch_triu_mul(st, s, w.R2, w.R1, Rout), "triu");
+    if (Q32) KL(launch_round_f32(st, (int64_t)n * s, Qout, Q32), "basis block in FP32");
     return SPAI_OK;
 }
 
@@ -2489,9 +2494,19 @@ spai_status solve_impl(spai_ctx ctx, const spai_csr *A, spai_pc P, int32_t s, co
     // the FP32 operator's (A P) W = A (P V_j), intermediates FP32 in the Z / T blocks
     float *z32 = (float *)w.Z, *t032 = (float *)w.T0, *t132 = (float *)w.T1;
     const double nnzA = A->nnz;
-    // Wout = A P Vin (FP64 products, or the FP32 operator of the mixed solve)
-    auto apply_op = [&](const double *Vin, double *Wout) -> spai_status {
-        if (mixed) {
+    // Wout = A P Vin (FP64 products, or the FP32 operator of the mixed solve; Vin32, when
+    // given, is Vin in FP32 and the FP32 operator reads it instead)
+    auto apply_op = [&](const double *Vin, double *Wout, const float *Vin32 = nullptr) -> spai_status {
+        if (mixed && Vin32) {
+            if (P) {
+                if ((st = apply32<float>(ctx, P, s, Vin32, z32, t032, t132))) return st;
+                PKL("spmm32_A", 2.0 * nnzA * s, 8.0 * nnzA + 4.0 * (n + 1) + 12.0 * nsd,
+                    launch_spmm32(cs, s, n, A->rowptr, A->colind, a32v, (const float *)z32, Wout), "A Z (FP32)");
+            } else {
+                PKL("spmm32_A", 2.0 * nnzA * s, 8.0 * nnzA + 4.0 * (n + 1) + 12.0 * nsd,
+                    launch_spmm32(cs, s, n, A->rowptr, A->colind, a32v, Vin32, Wout), "A V (FP32)");
+            }
+        } else if (mixed) {
             if (P) {
                 if ((st = apply32<float>(ctx, P, s, Vin, z32, t032, t132))) return st;
                 PKL("spmm32_A", 2.0 * nnzA * s, 8.0 * nnzA + 4.0 * (n + 1) + 12.0 * nsd,
@@ -2581,16 +2596,18 @@ spai_status solve_impl(spai_ctx ctx, const spai_csr *A, spai_pc P, int32_t s, co
             for (int i = 0; i < s; ++i) cthr[i] = std::max(thresh[i], kMixedCycleReduction * sqrt(h[16 + i]));
             CU(cudaMemcpyAsync(w.thresh, cthr, s * 8, cudaMemcpyHostToDevice, cs), "write thresholds");
         }
-        // V_0 S_0 = R (ref2 holds the residual norms^2), in basis slot kb
+        // V_0 S_0 = R (ref2 holds the residual norms^2), in basis slot kb (and in FP32 for the
+        // mixed solve's operator)
+        float *v32 = mixed ? w.V32 : nullptr;
         if ((st = cholqr2(ctx, w, n, s, w.W, w.V + (size_t)kb * blk_elems, w.Rn, w.ref2,
-                          (use_digits && !halves) ? kb : -1, ipad)))
+                          (use_digits && !halves) ? kb : -1, ipad, v32)))
             return st;
         if ((st = fixed16(kb))) return st;
         PKL("small_dense", 0.0, 0.0, launch_ls_prefix(cs, s, kb, mt, w.Rn, w.Qs, w.Rtri, w.G), "rhs");
         int J = 0;
         for (int j = 0; j < m; ++j) {
             const double *Vj = w.V + (size_t)(kb + j) * blk_elems;
-            if ((st = apply_op(Vj, w.W))) return st;
+            if ((st = apply_op(Vj, w.W, v32))) return st;
             if ((st = colnorms(w.W, w.ref2))) return st;
             // two passes of block classical Gram-Schmidt against C_0..C_{kb-1}, V_0..V_j
             const int nb = kb + j + 1;
@@ -2601,7 +2618,7 @@ spai_status solve_impl(spai_ctx ctx, const spai_csr *A, spai_pc P, int32_t s, co
             double *Vn = w.V + (size_t)(kb + j + 1) * blk_elems;
             // the new block's fixed point (for the products of the next steps) comes with it
             if ((st = cholqr2(ctx, w, n, s, w.W, Vn, w.Rn, w.ref2,
-                              (use_digits && !halves && j + 1 < m) ? kb + j + 1 : -1, ipad)))
+                              (use_digits && !halves && j + 1 < m) ? kb + j + 1 : -1, ipad, j + 1 < m ? v32 : nullptr)))
                 return st;
             if (j + 1 < m && (st = fixed16(kb + j + 1))) return st;
             PKL("arnoldi_ls", 16.0 * s * s * s * (nb), 0.0,

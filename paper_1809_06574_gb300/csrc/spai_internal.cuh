@@ -317,8 +317,9 @@ int launch_cqr_gram(cudaStream_t st, int32_t s, int32_t n, const double *W, cons
                     double *partial, unsigned *ticket, double *R1, int32_t *defl1);
 int launch_cqr_gram2(cudaStream_t st, int32_t s, int32_t n, const double *W, const double *R1, const int32_t *defl1,
                      double *partial, unsigned *ticket, double *R2, int32_t *defl2, double *Rout);
+// (Q32: non-null for an FP32 copy of Q as well)
 int launch_cqr_apply(cudaStream_t st, int32_t s, int32_t n, const double *W, const double *R1, const int32_t *defl1,
-                     const double *R2, const int32_t *defl2, double *Q);
+                     const double *R2, const int32_t *defl2, double *Q, float *Q32);
 int launch_colnorm2_t(cudaStream_t st, int32_t s, int32_t n, const double *W, double *partial, unsigned *ticket,
                       double *out);
 // projected least squares of block column j (Hessenberg column = H1 + H2 over Rsub)
@@ -373,7 +374,7 @@ int launch_block_update_tc(cudaStream_t st, int32_t n, int32_t nblk, const uint6
 // Cholesky-QR) with the new basis block's fixed point, laid out as launch_trsm_fixed does
 int launch_cqr_apply_fixed(cudaStream_t st, int32_t n, const double *W, const double *R1, const int32_t *defl1,
                            const double *R2, const int32_t *defl2, double *Q, uint64_t *F_row, uint64_t *F_sub,
-                           int32_t ipad, int32_t blk, int *d_err);
+                           int32_t ipad, int32_t blk, int *d_err, float *Q32);
 // Q := Q R^{-1} in place (s == 8, deflated columns -> 0) and the new basis block's fixed
 // point: row layout at F_row (n x 8), sub-tile layout at slot blk of ipad slots of F_sub
 int launch_trsm_fixed(cudaStream_t st, int32_t n, double *Q, const double *R, const int32_t *deflated, uint64_t *F_row,
