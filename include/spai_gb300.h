@@ -454,14 +454,16 @@ SPAI_API size_t spai_solve_workspace_size(int32_t n, int32_t s, int32_t restart)
  * Gram-Schmidt products, Cholesky-QR and projected least squares per system (segmented
  * reductions, one CTA per system for the small blocks), and one read-back per Arnoldi step
  * covers every system's convergence test -- so the launches and synchronisations of a
- * step do not grow with nsys.  A system whose columns have converged keeps iterating with
- * the others (each step can only lower its residual) until all have, or max_cycles runs
- * out.  A[i]: DEVICE CSR (n_i >= 1, sum of n_i and of nnz below 2^31); P: NULL (no
+ * step do not grow with nsys.  A system leaves the lockstep when its residual estimate
+ * meets tol: its steps of the cycle are over (the per-step kernels run on the row chunks of
+ * the systems still stepping), its X is updated at the cycle's end from its own steps, and
+ * it takes part in later cycles only while its true residual is above tol -- so each
+ * system takes the steps block_solve would take on it alone.  A[i]: DEVICE CSR (n_i >= 1, sum of n_i and of nnz below 2^31); P: NULL (no
  * preconditioner) or nsys handles whose chains have the same depth, each level of the
  * same kind (full or diagonal) and precision in every system; B[i], X[i]: DEVICE arrays
  * (host array of device pointers), n_i x s column-major, leading dimension n_i; X[i]
- * holds the initial guess on entry.  info: nsys entries (iterations = Arnoldi steps until
- * the system's own estimate met tol; cycles = the cycle after which its true residual did).
+ * holds the initial guess on entry.  info: nsys entries (iterations = the Arnoldi steps the
+ * system took over all cycles; cycles = the cycle after which its true residual met tol).
  * Orthogonalisation in FP64 (opts->orth ignored).  1 <= nsys <= 65536.  Synchronises.
  * Returns SPAI_ENOTCONV if some system did not converge. */
 SPAI_API spai_status block_solve_batch(spai_ctx ctx, int32_t nsys, const spai_csr *A, const spai_pc *P, int32_t s,

@@ -594,10 +594,12 @@ template <int S>
 __global__ void __launch_bounds__(kThreads) k_block_update_seg(int64_t ntot, int nblk, const double *__restrict__ V,
                                                                const double *__restrict__ H, int64_t hstride,
                                                                const double *base, double *out, double sign,
-                                                               SegChunks sc)
+                                                               SegChunks sc, const int32_t *__restrict__ jlim)
 {
     const int64_t r0 = sc.r0[blockIdx.x], r1 = sc.r1[blockIdx.x];
-    const double *Hs = H + (int64_t)sc.sys[blockIdx.x] * hstride;
+    const int32_t sys = sc.sys[blockIdx.x];
+    const double *Hs = H + (int64_t)sys * hstride;
+    if (jlim) nblk = min(nblk, jlim[sys]);
     for (int64_t g = threadIdx.x; g < (r1 - r0) * S; g += blockDim.x) {
         const int64_t r = r0 + g / S;
         const int b = (int)(g % S);
@@ -883,9 +885,10 @@ __global__ void __launch_bounds__(LsCfg<S>::NT)
     k_arnoldi_ls_b(int32_t j, int32_t m, const double *__restrict__ H1, const double *__restrict__ H2,
                    const double *__restrict__ Rsub, double *__restrict__ Qs, double *__restrict__ Rtri,
                    double *__restrict__ G, const double *__restrict__ thresh, double *__restrict__ est,
-                   int32_t *__restrict__ flag)
+                   int32_t *__restrict__ flag, const int32_t *__restrict__ jlim)
 {
     const int64_t b = blockIdx.x;
+    if (jlim && j >= jlim[b]) return;  // a system whose steps are over keeps its state
     const int64_t hs = (int64_t)(m + 1) * S * S;
     const int64_t qs = (int64_t)m * 4 * S * S;
     const int64_t rs = (int64_t)(m + 1) * S * m * S;
@@ -970,15 +973,18 @@ __global__ void k_backsolve(int32_t J, int32_t ldr, const double *__restrict__ R
     backsolve_body<S>(J, ldr, Rtri, G, Y);
 }
 
-// one CTA per system (m: restart length, for the per-system strides)
+// one CTA per system (m: restart length, for the per-system strides); system b solves for
+// its first min(J, jlim[b]) block rows and zeroes the rest of its J block rows
 template <int S>
 __global__ void k_backsolve_b(int32_t J, int32_t m, const double *__restrict__ Rtri, const double *__restrict__ G,
-                              double *__restrict__ Y)
+                              double *__restrict__ Y, const int32_t *__restrict__ jlim)
 {
     const int64_t b = blockIdx.x;
     const int ldr = (m + 1) * S;
-    backsolve_body<S>(J, ldr, Rtri + b * (int64_t)(m + 1) * S * m * S, G + b * (int64_t)(m + 1) * S * S,
-                      Y + b * (int64_t)m * S * S);
+    const int32_t Jb = jlim ? min(J, jlim[b]) : J;
+    double *Yb = Y + b * (int64_t)m * S * S;
+    for (int e = Jb * S * S + threadIdx.x; e < J * S * S; e += blockDim.x) Yb[e] = 0.0;
+    backsolve_body<S>(Jb, ldr, Rtri + b * (int64_t)(m + 1) * S * m * S, G + b * (int64_t)(m + 1) * S * S, Yb);
 }
 
 __global__ void k_axpy(int64_t count, double alpha, const double *__restrict__ x,
@@ -1176,6 +1182,7 @@ int reduce_seg(cudaStream_t st, int32_t count, const SegChunks &sc, const double
 
 int launch_colnorm2_seg(cudaStream_t st, int32_t s, const double *W, const SegChunks &sc, double *partial, double *out)
 {
+    if (sc.nchunks <= 0) return -1;
     SPAI_DISPATCH_S(s, (k_colnorm2_seg<S><<<sc.nchunks, kThreads, 0, st>>>(W, sc, partial)));
     reduce_seg(st, s, sc, partial, out, s);
     return check_launch(2);
@@ -1184,6 +1191,7 @@ int launch_colnorm2_seg(cudaStream_t st, int32_t s, const double *W, const SegCh
 int launch_block_dot_seg(cudaStream_t st, int32_t s, int64_t ntot, int32_t nblk, const double *V, const double *W,
                          const SegChunks &sc, double *partial, double *out, int64_t ostride)
 {
+    if (sc.nchunks <= 0) return -1;
     dim3 grid(sc.nchunks, nblk);
     SPAI_DISPATCH_S(s, (k_block_dot_seg<S><<<grid, kThreads, 0, st>>>(ntot, V, W, sc, partial, nblk)));
     reduce_seg(st, nblk * s * s, sc, partial, out, ostride);
@@ -1191,15 +1199,18 @@ int launch_block_dot_seg(cudaStream_t st, int32_t s, int64_t ntot, int32_t nblk,
 }
 
 int launch_block_update_seg(cudaStream_t st, int32_t s, int64_t ntot, int32_t nblk, const double *V, const double *H,
-                            int64_t hstride, const double *base, double *out, double sign, const SegChunks &sc)
+                            int64_t hstride, const double *base, double *out, double sign, const SegChunks &sc,
+                            const int32_t *jlim)
 {
+    if (sc.nchunks <= 0) return 0;
     SPAI_DISPATCH_S(s, (k_block_update_seg<S><<<sc.nchunks, kThreads, 0, st>>>(ntot, nblk, V, H, hstride, base, out,
-                                                                               sign, sc)));
+                                                                               sign, sc, jlim)));
     return check_launch();
 }
 
 int launch_gram_seg(cudaStream_t st, int32_t s, const double *W, const SegChunks &sc, double *partial, double *G)
 {
+    if (sc.nchunks <= 0) return -1;
     SPAI_DISPATCH_S(s, (k_gram_seg<S><<<sc.nchunks, kThreads, 0, st>>>(W, sc, partial)));
     reduce_seg(st, s * s, sc, partial, G, (int64_t)s * s);
     return check_launch(2);
@@ -1208,6 +1219,7 @@ int launch_gram_seg(cudaStream_t st, int32_t s, const double *W, const SegChunks
 int launch_trsm_gram_seg(cudaStream_t st, int32_t s, const double *W, const double *R, const int32_t *deflated,
                          double *Q1, const SegChunks &sc, double *partial, double *G2)
 {
+    if (sc.nchunks <= 0) return -1;
     SPAI_DISPATCH_S(s, (k_trsm_gram_seg<S><<<sc.nchunks, kThreads, 0, st>>>(W, R, deflated, Q1, sc, partial)));
     reduce_seg(st, s * s, sc, partial, G2, (int64_t)s * s);
     return check_launch(2);
@@ -1216,6 +1228,7 @@ int launch_trsm_gram_seg(cudaStream_t st, int32_t s, const double *W, const doub
 int launch_trsm_rows_seg(cudaStream_t st, int32_t s, const double *W, const double *R, const int32_t *deflated,
                          double *out, const SegChunks &sc)
 {
+    if (sc.nchunks <= 0) return -1;
     SPAI_DISPATCH_S(s, (k_trsm_rows_seg<S><<<sc.nchunks, kThreads, 0, st>>>(W, R, deflated, out, sc)));
     return check_launch();
 }
@@ -1235,10 +1248,10 @@ int launch_triu_mul_b(cudaStream_t st, int32_t s, int32_t nsys, const double *R2
 
 int launch_arnoldi_ls_b(cudaStream_t st, int32_t s, int32_t nsys, int32_t j, int32_t m, const double *H1,
                         const double *H2, const double *Rsub, double *Qs, double *Rtri, double *G, const double *thresh,
-                        double *est, int32_t *flag)
+                        double *est, int32_t *flag, const int32_t *jlim)
 {
     SPAI_DISPATCH_S(s, (k_arnoldi_ls_b<S><<<nsys, LsCfg<S>::NT, 0, st>>>(j, m, H1, H2, Rsub, Qs, Rtri, G, thresh, est,
-                                                                         flag)));
+                                                                         flag, jlim)));
     return check_launch();
 }
 
@@ -1249,9 +1262,9 @@ int launch_set_rhs_b(cudaStream_t st, int32_t s, int32_t nsys, int32_t m, const 
 }
 
 int launch_backsolve_b(cudaStream_t st, int32_t s, int32_t nsys, int32_t J, int32_t m, const double *Rtri,
-                       const double *G, double *Y)
+                       const double *G, double *Y, const int32_t *jlim)
 {
-    SPAI_DISPATCH_S(s, (k_backsolve_b<S><<<nsys, 512, 0, st>>>(J, m, Rtri, G, Y)));
+    SPAI_DISPATCH_S(s, (k_backsolve_b<S><<<nsys, 512, 0, st>>>(J, m, Rtri, G, Y, jlim)));
     return check_launch();
 }
 

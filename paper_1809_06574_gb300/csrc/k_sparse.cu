@@ -550,6 +550,39 @@ __global__ void __launch_bounds__(kThreads) k_spmm(int32_t n, const int32_t *__r
     Y[row * S + c] = acc;
 }
 
+// The same product restricted to a list of row chunks: chunk c (grid column blockIdx.x)
+// covers rows [r0[c], r1[c]), at most kThreads / S * gridDim.y of them.  Rows outside the
+// listed chunks are neither read as outputs nor written.
+template <int S, typename V>
+__global__ void __launch_bounds__(kThreads) k_spmm_seg(const int64_t *__restrict__ r0s,
+                                                       const int64_t *__restrict__ r1s,
+                                                       const int32_t *__restrict__ rowptr,
+                                                       const int32_t *__restrict__ colind,
+                                                       const V *__restrict__ val,
+                                                       const double *__restrict__ X, double *__restrict__ Y)
+{
+    const int64_t g = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t row = __ldg(r0s + blockIdx.x) + g / S;
+    const int c = (int)(g % S);
+    if (row >= __ldg(r1s + blockIdx.x)) return;
+    const int32_t a = __ldg(rowptr + row), b = __ldg(rowptr + row + 1);
+    double acc = 0.0;
+    for (int32_t q = a; q < b; ++q)
+        acc = fma(as_f64(__ldg(val + q)), __ldg(X + (int64_t)__ldg(colind + q) * S + c), acc);
+    Y[row * S + c] = acc;
+}
+
+template <int S, typename V>
+__global__ void k_scale_rows_seg(const int64_t *__restrict__ r0s, const int64_t *__restrict__ r1s,
+                                 const V *__restrict__ q, const double *__restrict__ X, double *__restrict__ Y)
+{
+    const int64_t g = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t row = __ldg(r0s + blockIdx.x) + g / S;
+    if (row >= __ldg(r1s + blockIdx.x)) return;
+    const int64_t e = row * S + g % S;
+    Y[e] = as_f64(__ldg(q + row)) * X[e];
+}
+
 // ---------------------------------------------------------------------------------
 // FP32 CSR times row-major block: the operator of the mixed-precision solve.  The matrix
 // values (FP32, BF16 bits, or FP64 rounded once) and the X entries (FP64 rounded once, or
@@ -1131,6 +1164,66 @@ int launch_scale_rows(cudaStream_t st, int32_t s, int32_t n, const double *q, co
     if (q16) return scale_rows_any<uint16_t>(st, s, n, q16, X, Y);
     if (q32) return scale_rows_any<float>(st, s, n, q32, X, Y);
     return scale_rows_any<double>(st, s, n, q, X, Y);
+}
+
+namespace {
+
+template <typename V>
+int spmm_seg_any(cudaStream_t st, int32_t s, int32_t nchunks, int64_t max_rows, const int64_t *r0, const int64_t *r1,
+                 const int32_t *rowptr, const int32_t *colind, const V *val, const double *X, double *Y)
+{
+    if (nchunks <= 0) return 0;
+    const int64_t sub = (max_rows * s + kThreads - 1) / kThreads;
+    if (sub < 1 || sub > 65535) return -1;
+    const dim3 grid((unsigned)nchunks, (unsigned)sub);
+    switch (s) {
+    case 1: k_spmm_seg<1, V><<<grid, kThreads, 0, st>>>(r0, r1, rowptr, colind, val, X, Y); break;
+    case 2: k_spmm_seg<2, V><<<grid, kThreads, 0, st>>>(r0, r1, rowptr, colind, val, X, Y); break;
+    case 4: k_spmm_seg<4, V><<<grid, kThreads, 0, st>>>(r0, r1, rowptr, colind, val, X, Y); break;
+    case 8: k_spmm_seg<8, V><<<grid, kThreads, 0, st>>>(r0, r1, rowptr, colind, val, X, Y); break;
+    case 16: k_spmm_seg<16, V><<<grid, kThreads, 0, st>>>(r0, r1, rowptr, colind, val, X, Y); break;
+    default: return -1;
+    }
+    return check_launch();
+}
+
+template <typename V>
+int scale_rows_seg_any(cudaStream_t st, int32_t s, int32_t nchunks, int64_t max_rows, const int64_t *r0,
+                       const int64_t *r1, const V *q, const double *X, double *Y)
+{
+    if (nchunks <= 0) return 0;
+    const int64_t sub = (max_rows * s + kThreads - 1) / kThreads;
+    if (sub < 1 || sub > 65535) return -1;
+    const dim3 grid((unsigned)nchunks, (unsigned)sub);
+    switch (s) {
+    case 1: k_scale_rows_seg<1, V><<<grid, kThreads, 0, st>>>(r0, r1, q, X, Y); break;
+    case 2: k_scale_rows_seg<2, V><<<grid, kThreads, 0, st>>>(r0, r1, q, X, Y); break;
+    case 4: k_scale_rows_seg<4, V><<<grid, kThreads, 0, st>>>(r0, r1, q, X, Y); break;
+    case 8: k_scale_rows_seg<8, V><<<grid, kThreads, 0, st>>>(r0, r1, q, X, Y); break;
+    case 16: k_scale_rows_seg<16, V><<<grid, kThreads, 0, st>>>(r0, r1, q, X, Y); break;
+    default: return -1;
+    }
+    return check_launch();
+}
+
+}  // namespace
+
+int launch_spmm_seg(cudaStream_t st, int32_t s, int32_t nchunks, int64_t max_rows, const int64_t *r0,
+                    const int64_t *r1, const int32_t *rowptr, const int32_t *colind, const double *val,
+                    const float *val32, const uint16_t *val16, const double *X, double *Y)
+{
+    if (val16) return spmm_seg_any<uint16_t>(st, s, nchunks, max_rows, r0, r1, rowptr, colind, val16, X, Y);
+    if (val32) return spmm_seg_any<float>(st, s, nchunks, max_rows, r0, r1, rowptr, colind, val32, X, Y);
+    return spmm_seg_any<double>(st, s, nchunks, max_rows, r0, r1, rowptr, colind, val, X, Y);
+}
+
+int launch_scale_rows_seg(cudaStream_t st, int32_t s, int32_t nchunks, int64_t max_rows, const int64_t *r0,
+                          const int64_t *r1, const double *q, const float *q32, const uint16_t *q16, const double *X,
+                          double *Y)
+{
+    if (q16) return scale_rows_seg_any<uint16_t>(st, s, nchunks, max_rows, r0, r1, q16, X, Y);
+    if (q32) return scale_rows_seg_any<float>(st, s, nchunks, max_rows, r0, r1, q32, X, Y);
+    return scale_rows_seg_any<double>(st, s, nchunks, max_rows, r0, r1, q, X, Y);
 }
 
 int launch_pack(cudaStream_t st, int32_t s, int32_t n, const double *src, int64_t ld, double *dst)

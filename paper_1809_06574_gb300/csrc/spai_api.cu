@@ -2923,6 +2923,50 @@ extern "C" spai_status block_solve_batch(spai_ctx ctx, int32_t nsys, const spai_
     CU(cudaMemcpyAsync(d_r0, cr0.data(), (size_t)nch * 8, cudaMemcpyHostToDevice, cs), "chunks");
     CU(cudaMemcpyAsync(d_r1, cr1.data(), (size_t)nch * 8, cudaMemcpyHostToDevice, cs), "chunks");
     const SegChunks sc{d_csys, d_r0, d_r1, d_c0, nch, nsys};
+    // Systems leave the lockstep as they finish: jlim[b] is system b's step limit in the
+    // current cycle (m while it takes Arnoldi steps, the steps it took once its residual
+    // estimate met tol, 0 once its true residual did), and sca lists the row chunks of the
+    // systems still stepping (a compacted copy of sc, rebuilt when one stops), so that the
+    // per-step kernels run over those rows only.
+    int32_t *d_csys_a = nullptr, *d_c0_a = nullptr, *d_jlim = nullptr;
+    int64_t *d_r0_a = nullptr, *d_r1_a = nullptr;
+    if ((st = al.get(&d_csys_a, nch)) || (st = al.get(&d_c0_a, (int64_t)nsys + 1)) || (st = al.get(&d_r0_a, nch)) ||
+        (st = al.get(&d_r1_a, nch)) || (st = al.get(&d_jlim, nsys)))
+        return st;
+    SegChunks sca{d_csys_a, d_r0_a, d_r1_a, d_c0_a, 0, nsys};
+    std::vector<int32_t> jlim((size_t)nsys, m), csys_a, c0_a((size_t)nsys + 1, 0);
+    std::vector<int64_t> r0_a, r1_a;
+    csys_a.reserve((size_t)nch);
+    r0_a.reserve((size_t)nch);
+    r1_a.reserve((size_t)nch);
+    double rows_a = 0.0, nnz_a = 0.0;  // rows and nonzeros of A in the listed chunks
+    auto set_active = [&]() -> spai_status {
+        csys_a.clear();
+        r0_a.clear();
+        r1_a.clear();
+        rows_a = nnz_a = 0.0;
+        for (int i = 0; i < nsys; ++i) {
+            c0_a[i] = (int32_t)csys_a.size();
+            if (jlim[i] != m) continue;
+            rows_a += (double)A[i].n;
+            nnz_a += (double)A[i].nnz;
+            for (int32_t c = c0[i]; c < c0[i + 1]; ++c) {
+                csys_a.push_back(i);
+                r0_a.push_back(cr0[c]);
+                r1_a.push_back(cr1[c]);
+            }
+        }
+        c0_a[nsys] = (int32_t)csys_a.size();
+        sca.nchunks = c0_a[nsys];
+        if (sca.nchunks) {
+            CU(cudaMemcpyAsync(d_csys_a, csys_a.data(), (size_t)sca.nchunks * 4, cudaMemcpyHostToDevice, cs), "chunks");
+            CU(cudaMemcpyAsync(d_r0_a, r0_a.data(), (size_t)sca.nchunks * 8, cudaMemcpyHostToDevice, cs), "chunks");
+            CU(cudaMemcpyAsync(d_r1_a, r1_a.data(), (size_t)sca.nchunks * 8, cudaMemcpyHostToDevice, cs), "chunks");
+        }
+        CU(cudaMemcpyAsync(d_c0_a, c0_a.data(), ((size_t)nsys + 1) * 4, cudaMemcpyHostToDevice, cs), "chunks");
+        CU(cudaMemcpyAsync(d_jlim, jlim.data(), (size_t)nsys * 4, cudaMemcpyHostToDevice, cs), "step limits");
+        return SPAI_OK;
+    };
 
     // ---- workspace: n_tot x s blocks, the basis, and every system's small blocks
     const int64_t blk = (int64_t)ntot * s, ss = (int64_t)s * s;
@@ -2942,12 +2986,34 @@ extern "C" spai_status block_solve_batch(spai_ctx ctx, int32_t nsys, const spai_
         (st = al.get(&flag, nsys)))
         return st;
 
-    // Y = P X through the stacked chain (T0 / T1 between levels)
-    auto apply_P = [&](const double *Xin, double *Yout) -> spai_status {
+    // Y = P X through the stacked chain (T0 / T1 between levels); on the rows of the systems
+    // still stepping when `active` (the factors' nonzeros counted in proportion to the rows)
+    auto apply_P = [&](const double *Xin, double *Yout, bool active) -> spai_status {
         const double *cur = Xin;
         for (size_t l = 0; l < levels.size(); ++l) {
             const StackedFactor &f = levels[l];
             double *dst = (l + 1 == levels.size()) ? Yout : ((l & 1) ? T1 : T0);
+            if (active) {
+                const double share = rows_a / (double)ntot, fnz = (double)f.nnz * share, ab = rows_a * s;
+                if (f.diag) {
+                    PKL("scale_rows", ab, 8.0 * rows_a + 16.0 * ab,
+                        launch_scale_rows_seg(cs, s, sca.nchunks, kChunkRows, d_r0_a, d_r1_a,
+                                              f.prec == 0 ? (const double *)f.val : nullptr,
+                                              f.prec == 1 ? (const float *)f.val : nullptr,
+                                              f.prec == 2 ? (const uint16_t *)f.val : nullptr, cur, dst),
+                        "diagonal factor apply");
+                } else {
+                    const double vb = f.prec == 2 ? 6.0 : f.prec == 1 ? 8.0 : 12.0;
+                    PKL("spmm_P", 2.0 * fnz * s, vb * fnz + 4.0 * rows_a + 16.0 * ab,
+                        launch_spmm_seg(cs, s, sca.nchunks, kChunkRows, d_r0_a, d_r1_a, f.rowptr, f.colind,
+                                        f.prec == 0 ? (const double *)f.val : nullptr,
+                                        f.prec == 1 ? (const float *)f.val : nullptr,
+                                        f.prec == 2 ? (const uint16_t *)f.val : nullptr, cur, dst),
+                        "apply");
+                }
+                cur = dst;
+                continue;
+            }
             const double fl = 2.0 * (double)f.nnz * s;
             if (f.diag) {
                 PKL("scale_rows", (double)ntot * s, 8.0 * ntot + 16.0 * blk,
@@ -2969,15 +3035,16 @@ extern "C" spai_status block_solve_batch(spai_ctx ctx, int32_t nsys, const spai_
         }
         return SPAI_OK;
     };
-    // W = Q R per system, two passes of Cholesky QR (the block_solve sequence, per system)
+    // W = Q R per system still stepping, two passes of Cholesky QR (the block_solve sequence,
+    // per system)
     auto cholqr2_b = [&](const double *Win, double *Qout) -> spai_status {
-        const double nsd = (double)blk;
-        PKL("gram", nsd * (s + 1), 8.0 * nsd, launch_gram_seg(cs, s, Win, sc, partial, G1), "gram");
+        const double nsd = rows_a * s;
+        PKL("gram", nsd * (s + 1), 8.0 * nsd, launch_gram_seg(cs, s, Win, sca, partial, G1), "gram");
         PKL("small_dense", 0.0, 0.0, launch_chol_small_b(cs, s, nsys, G1, ref2, 1e-24, R1, defl1), "chol");
         PKL("trsm_gram", nsd * s + nsd * (s + 1), 16.0 * nsd,
-            launch_trsm_gram_seg(cs, s, Win, R1, defl1, Qout, sc, partial, G1), "trsm gram");
+            launch_trsm_gram_seg(cs, s, Win, R1, defl1, Qout, sca, partial, G1), "trsm gram");
         PKL("small_dense", 0.0, 0.0, launch_chol_small_b(cs, s, nsys, G1, nullptr, 0.0, R2, defl2), "chol");
-        PKL("trsm_rows", nsd * s, 16.0 * nsd, launch_trsm_rows_seg(cs, s, Qout, R2, defl2, Qout, sc), "trsm");
+        PKL("trsm_rows", nsd * s, 16.0 * nsd, launch_trsm_rows_seg(cs, s, Qout, R2, defl2, Qout, sca), "trsm");
         PKL("small_dense", 0.0, 0.0, launch_triu_mul_b(cs, s, nsys, R2, R1, Rn), "triu");
         return SPAI_OK;
     };
@@ -3018,68 +3085,77 @@ extern "C" spai_status block_solve_batch(spai_ctx ctx, int32_t nsys, const spai_
     };
     if ((st = residual())) return st;
     // per system: the cycle after which its true residual met tol (0: at the start), and
-    // the Arnoldi steps up to the step whose estimate met tol in that cycle
-    std::vector<int> conv_cycle((size_t)nsys, -1), done_it((size_t)nsys, -1);
-    int cycles = 0, iters = 0;
+    // the Arnoldi steps it took (it takes none once its steps of a cycle are over)
+    std::vector<int> conv_cycle((size_t)nsys, -1), own_it((size_t)nsys, 0);
+    int cycles = 0;
     for (int i = 0; i < nsys; ++i)
-        if (sys_converged(i)) conv_cycle[i] = 0, done_it[i] = 0;
+        if (sys_converged(i)) conv_cycle[i] = 0;
     while (!all_converged() && cycles < opts->max_cycles) {
         ++cycles;
+        int nact = 0;
+        for (int i = 0; i < nsys; ++i) {
+            jlim[i] = conv_cycle[i] >= 0 ? 0 : m;
+            nact += jlim[i] == m;
+        }
+        if ((st = set_active())) return st;
         if ((st = cholqr2_b(W, V))) return st;
         PKL("small_dense", 0.0, 0.0, launch_set_rhs_b(cs, s, nsys, m, Rn, Gv), "rhs");
         int J = 0;
-        for (int j = 0; j < m; ++j) {
+        for (int j = 0; j < m && nact > 0; ++j) {
             const double *Vj = V + (int64_t)j * blk;
             const double *Zj = Vj;
             if (!levels.empty()) {
-                if ((st = apply_P(Vj, Z))) return st;
+                if ((st = apply_P(Vj, Z, true))) return st;
                 Zj = Z;
             }
-            PKL("spmm_A", 2.0 * nnz * s, 12.0 * nnz + 4.0 * (ntot + 1) + 16.0 * blk,
-                launch_spmm(cs, s, ntot, rp, ci, va, Zj, W), "A Z");
-            PKL("colnorm2", 2.0 * blk, 8.0 * blk, launch_colnorm2_seg(cs, s, W, sc, partial, ref2), "norms");
-            const double nb = j + 1, f = 2.0 * blk * s * nb, by = 8.0 * blk * (nb + 1);
+            const double ab = rows_a * s;
+            PKL("spmm_A", 2.0 * nnz_a * s, 12.0 * nnz_a + 4.0 * rows_a + 16.0 * ab,
+                launch_spmm_seg(cs, s, sca.nchunks, kChunkRows, d_r0_a, d_r1_a, rp, ci, va, nullptr, nullptr, Zj, W),
+                "A Z");
+            PKL("colnorm2", 2.0 * ab, 8.0 * ab, launch_colnorm2_seg(cs, s, W, sca, partial, ref2), "norms");
+            const double nb = j + 1, f = 2.0 * ab * s * nb, by = 8.0 * ab * (nb + 1);
             const int64_t hs = (int64_t)(m + 1) * ss;
-            PKL("block_dot", f, by, launch_block_dot_seg(cs, s, ntot, j + 1, V, W, sc, partial, H1, hs), "H1");
-            PKL("block_update", f, 8.0 * blk * (nb + 2),
-                launch_block_update_seg(cs, s, ntot, j + 1, V, H1, hs, W, W, -1.0, sc), "update");
-            PKL("block_dot", f, by, launch_block_dot_seg(cs, s, ntot, j + 1, V, W, sc, partial, H2, hs), "H2");
-            PKL("block_update", f, 8.0 * blk * (nb + 2),
-                launch_block_update_seg(cs, s, ntot, j + 1, V, H2, hs, W, W, -1.0, sc), "update");
+            PKL("block_dot", f, by, launch_block_dot_seg(cs, s, ntot, j + 1, V, W, sca, partial, H1, hs), "H1");
+            PKL("block_update", f, 8.0 * ab * (nb + 2),
+                launch_block_update_seg(cs, s, ntot, j + 1, V, H1, hs, W, W, -1.0, sca), "update");
+            PKL("block_dot", f, by, launch_block_dot_seg(cs, s, ntot, j + 1, V, W, sca, partial, H2, hs), "H2");
+            PKL("block_update", f, 8.0 * ab * (nb + 2),
+                launch_block_update_seg(cs, s, ntot, j + 1, V, H2, hs, W, W, -1.0, sca), "update");
             if ((st = cholqr2_b(W, V + (int64_t)(j + 1) * blk))) return st;
-            PKL("arnoldi_ls", 16.0 * ss * s * (j + 1) * nsys, 0.0,
-                launch_arnoldi_ls_b(cs, s, nsys, j, m, H1, H2, Rn, Qs, Rtri, Gv, thresh, est, flag), "least squares");
+            PKL("arnoldi_ls", 16.0 * ss * s * (j + 1) * nact, 0.0,
+                launch_arnoldi_ls_b(cs, s, nsys, j, m, H1, H2, Rn, Qs, Rtri, Gv, thresh, est, flag, d_jlim),
+                "least squares");
             CU(cudaMemcpyAsync(hflag.data(), flag, (size_t)nsys * 4, cudaMemcpyDeviceToHost, cs), "read flags");
             CU(cudaStreamSynchronize(cs), "sync");
-            ++iters;
             J = j + 1;
-            bool all = true;
+            int stopped = 0;
             for (int i = 0; i < nsys; ++i) {
-                if (hflag[i] && conv_cycle[i] < 0 && done_it[i] < 0) done_it[i] = iters;
-                all = all && hflag[i];
+                if (jlim[i] != m) continue;
+                ++own_it[i];
+                if (!hflag[i]) continue;
+                jlim[i] = j + 1;  // its estimate met tol: its steps of this cycle are over
+                ++stopped;
             }
-            if (all) break;
+            nact -= stopped;
+            if (stopped && nact > 0 && (st = set_active())) return st;
         }
-        // X += P (V Y), every system with its own Y
-        PKL("backsolve", (double)J * s * J * s * s * nsys, 0.0, launch_backsolve_b(cs, s, nsys, J, m, Rtri, Gv, Y),
-            "back substitution");
+        // X += P (V Y), every system with its own Y over its own steps (none for a system
+        // that had converged before the cycle, whose X is left as it was)
+        CU(cudaMemcpyAsync(d_jlim, jlim.data(), (size_t)nsys * 4, cudaMemcpyHostToDevice, cs), "step limits");
+        PKL("backsolve", (double)J * s * J * s * s * nsys, 0.0,
+            launch_backsolve_b(cs, s, nsys, J, m, Rtri, Gv, Y, d_jlim), "back substitution");
         PKL("block_update", 2.0 * blk * s * J, 8.0 * blk * (J + 2),
-            launch_block_update_seg(cs, s, ntot, J, V, Y, (int64_t)m * ss, nullptr, W, 1.0, sc), "V Y");
+            launch_block_update_seg(cs, s, ntot, J, V, Y, (int64_t)m * ss, nullptr, W, 1.0, sc, d_jlim), "V Y");
         const double *U = W;
         if (!levels.empty()) {
-            if ((st = apply_P(W, Z))) return st;
+            if ((st = apply_P(W, Z, false))) return st;
             U = Z;
         }
         PKL("axpy", 2.0 * blk, 24.0 * blk, launch_axpy(cs, blk, 1.0, U, Xw), "X update");
         if ((st = residual())) return st;
         for (int i = 0; i < nsys; ++i) {
             if (conv_cycle[i] >= 0) continue;
-            if (sys_converged(i)) {
-                conv_cycle[i] = cycles;
-                if (done_it[i] < 0) done_it[i] = iters;
-            } else {
-                done_it[i] = -1;  // not there yet: its step is counted again in the next cycle
-            }
+            if (sys_converged(i)) conv_cycle[i] = cycles;
         }
     }
     for (int i = 0; i < nsys; ++i) KL(launch_unpack(cs, s, A[i].n, Xw + off[i] * s, X[i], A[i].n), "unpack X");
@@ -3098,7 +3174,7 @@ extern "C" spai_status block_solve_batch(spai_ctx ctx, int32_t nsys, const spai_
             if (rel > wr) { wr = rel; worst = c; }
             if (!(rn <= th[k])) conv = false;
         }
-        info[i].iterations = done_it[i] >= 0 ? done_it[i] : iters;
+        info[i].iterations = own_it[i];
         info[i].cycles = conv_cycle[i] >= 0 ? conv_cycle[i] : cycles;
         info[i].converged = conv ? 1 : 0;
         info[i].worst_column = worst;

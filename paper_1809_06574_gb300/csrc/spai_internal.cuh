@@ -132,6 +132,14 @@ int launch_scale_rows32(cudaStream_t st, int32_t s, int32_t n, const F32Vals &q,
 int launch_round_f32(cudaStream_t st, int64_t count, const double *src, float *dst);
 int launch_pack(cudaStream_t st, int32_t s, int32_t n, const double *src, int64_t ld, double *dst);
 // Y[r][c] = q[r] X[r][c] (a diagonal factor; q FP64, FP32 or BF16 bits, one of them given)
+// Y = A X and Y = diag(q) X on the rows of a list of nchunks row chunks [r0[c], r1[c]) of at
+// most max_rows rows each (one value array given: FP64, FP32 or BF16 bits; FP64 arithmetic)
+int launch_spmm_seg(cudaStream_t st, int32_t s, int32_t nchunks, int64_t max_rows, const int64_t *r0,
+                    const int64_t *r1, const int32_t *rowptr, const int32_t *colind, const double *val,
+                    const float *val32, const uint16_t *val16, const double *X, double *Y);
+int launch_scale_rows_seg(cudaStream_t st, int32_t s, int32_t nchunks, int64_t max_rows, const int64_t *r0,
+                          const int64_t *r1, const double *q, const float *q32, const uint16_t *q16, const double *X,
+                          double *Y);
 int launch_scale_rows(cudaStream_t st, int32_t s, int32_t n, const double *q, const float *q32, const uint16_t *q16,
                       const double *X, double *Y);
 int launch_unpack(cudaStream_t st, int32_t s, int32_t n, const double *src, double *dst,
@@ -267,8 +275,10 @@ int launch_colnorm2_seg(cudaStream_t st, int32_t s, const double *W, const SegCh
 // partial: nchunks * nblk * s * s doubles
 int launch_block_dot_seg(cudaStream_t st, int32_t s, int64_t ntot, int32_t nblk, const double *V, const double *W,
                          const SegChunks &sc, double *partial, double *out, int64_t ostride);
+// jlim (may be NULL): system b uses its first min(nblk, jlim[b]) blocks only
 int launch_block_update_seg(cudaStream_t st, int32_t s, int64_t ntot, int32_t nblk, const double *V, const double *H,
-                            int64_t hstride, const double *base, double *out, double sign, const SegChunks &sc);
+                            int64_t hstride, const double *base, double *out, double sign, const SegChunks &sc,
+                            const int32_t *jlim = nullptr);
 int launch_gram_seg(cudaStream_t st, int32_t s, const double *W, const SegChunks &sc, double *partial, double *G);
 int launch_trsm_gram_seg(cudaStream_t st, int32_t s, const double *W, const double *R, const int32_t *deflated,
                          double *Q1, const SegChunks &sc, double *partial, double *G2);
@@ -277,12 +287,14 @@ int launch_trsm_rows_seg(cudaStream_t st, int32_t s, const double *W, const doub
 int launch_chol_small_b(cudaStream_t st, int32_t s, int32_t nsys, const double *G, const double *ref2, double tau2,
                         double *R, int32_t *deflated);
 int launch_triu_mul_b(cudaStream_t st, int32_t s, int32_t nsys, const double *R2, const double *R1, double *out);
+// jlim (may be NULL): system b takes step j only when j < jlim[b] (its state is kept otherwise)
 int launch_arnoldi_ls_b(cudaStream_t st, int32_t s, int32_t nsys, int32_t j, int32_t m, const double *H1,
                         const double *H2, const double *Rsub, double *Qs, double *Rtri, double *G, const double *thresh,
-                        double *est, int32_t *flag);
+                        double *est, int32_t *flag, const int32_t *jlim = nullptr);
 int launch_set_rhs_b(cudaStream_t st, int32_t s, int32_t nsys, int32_t m, const double *S0, double *G);
+// jlim (may be NULL): system b solves for its first min(J, jlim[b]) block rows, the rest of Y zero
 int launch_backsolve_b(cudaStream_t st, int32_t s, int32_t nsys, int32_t J, int32_t m, const double *Rtri,
-                       const double *G, double *Y);
+                       const double *G, double *Y, const int32_t *jlim = nullptr);
 int krylov_chunks(int32_t n);
 // doubles needed for the partial sums of launch_block_dot with up to nblk_max blocks
 size_t dot_partial_elems(int32_t s, int32_t nblk_max);

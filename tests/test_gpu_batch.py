@@ -125,7 +125,10 @@ def test_batch_reports_singular_system():
 
 def test_batched_solve_matches_oracle_and_single_solves():
     """block_solve_batch: every system against the oracle's block GMRES (solution bar 1e-6),
-    its own true residual recomputed on the host, and the single-system block_solve."""
+    its own true residual recomputed on the host, and the single-system block_solve.  A
+    system leaves the lockstep once its residual estimate meets tol, so it takes the steps
+    the single solve takes (one step apart at most where rounding moves the estimate across
+    tol) and, with the same steps, reaches the single solve's iterate to rounding."""
     import torch
     sg = _sg()
     ws = [synth.grid_workload((d, d), "5pt", seed=20 + d, nrhs=4, params=[0.3, 0.45]) for d in (17, 30, 23, 41)]
@@ -146,16 +149,22 @@ def test_batched_solve_matches_oracle_and_single_solves():
         Xd = [torch.zeros((s, w.n), dtype=torch.float64, device="cuda:0") for w in ws]
         st, infos = sg.block_solve_batch(ctx, d2, upd, s, Bd, Xd, 30, 1e-8, 50)
         Xb = [x.cpu().numpy().T.copy() for x in Xd]
-        single = []
+        single, single_info = [], []
         for w, d, q in zip(ws, d2, upd):
             X = np.zeros((w.n, s), order="F")
-            sg.block_solve(ctx, d, q, s, np.asfortranarray(w.B), w.n, X, w.n, 30, 1e-8, 50)
+            _, sinf, _ = sg.block_solve(ctx, d, q, s, np.asfortranarray(w.B), w.n, X, w.n, 30, 1e-8, 50)
             single.append(X)
+            single_info.append(sinf)
         for q in upd + base:
             sg.spai_pc_destroy(q)
     assert st == 0
-    for i, (w, a1, a2, k, X, Xs, inf) in enumerate(zip(ws, A1, A2, kinds, Xb, single, infos)):
+    its = [inf["iterations"] for inf in infos]
+    assert len(set(its)) > 1  # the systems stop after different numbers of steps
+    for i, (w, a1, a2, k, X, Xs, inf, sinf) in enumerate(zip(ws, A1, A2, kinds, Xb, single, infos, single_info)):
         assert inf["converged"] and inf["max_rel_residual"] <= 1e-8, (i, inf)
+        assert abs(inf["iterations"] - sinf["iterations"]) <= 1 and inf["cycles"] == sinf["cycles"], (i, inf, sinf)
+        if inf["iterations"] == sinf["iterations"]:
+            assert np.linalg.norm(X - Xs) <= 1e-8 * np.linalg.norm(Xs), i
         bn = np.linalg.norm(w.B, axis=0)
         rel = np.linalg.norm(w.B - oracle.spmm(a2, X, w.n), axis=0) / np.where(bn > 0, bn, 1.0)
         assert np.all(rel <= 1e-8), (i, rel)
