@@ -53,6 +53,12 @@ def parse():
     ap.add_argument("--columns-workload", default="batched2d", choices=["batched2d", "sweep3d", "adaptive3d"],
                     help="--kernel columns: the batched 2D systems (FP32), one FP64 SPAI of the 3D sweep, "
                          "or one adaptive SPAI of the 3D sweep's matrix (--side sets the grid)")
+    ap.add_argument("--columns-prec", default="fp64", choices=["fp64", "fp32"],
+                    help="factor precision of the sweep3d column case")
+    ap.add_argument("--columns-normal", action="store_true",
+                    help="column case: solve the column problems by their normal equations (SPAI_LS_NORMAL)")
+    ap.add_argument("--columns-variant", type=int, default=0,
+                    help="pin this column-kernel variant code for the 25 x 7 tiles of the sweep3d column case")
     ap.add_argument("--nblk", type=int, default=16)
     ap.add_argument("--orth", default="tensor", choices=["tensor", "fp64"])
     # serving: Poisson arrivals over a pool of 16 3D 7-point grids (sides 24-96)
@@ -229,14 +235,20 @@ def run_columns_case(args):
     import paper_1809_06574_gb300 as sg
     if args.columns_workload in ("sweep3d", "adaptive3d"):  # one SPAI of the sweep's first system
         ws = [synth.grid3d_7pt(side=args.side, nparams=args.nparams)]
-        kinds = [sg.PATTERN_A]
+        kinds = [sg.PATTERN_A | (sg.PREC_FP32 if args.columns_prec == "fp32" else 0)]
+        if args.columns_normal:
+            kinds = [k | sg.LS_NORMAL for k in kinds]
         shifts = [ws[0].shifts[0]]
     else:
         ws = synth.batched_2d(args.batched_systems)
         kinds = [(sg.PATTERN_A if w.extra["pattern"] == "A" else sg.PATTERN_A2) | sg.PREC_FP32 for w in ws]
+        if args.columns_normal:
+            kinds = [k | sg.LS_NORMAL for k in kinds]
         shifts = [1.0] * len(ws)
     stream = torch.cuda.current_stream()
     ctx = sg.spai_ctx_create(stream.cuda_stream, 0)
+    if args.columns_variant and args.columns_workload == "sweep3d":
+        sg.spai_column_variant_set(args.columns_prec == "fp32", 25, 7, args.columns_variant)
     As, keep = [], []
     for w, sh in zip(ws, shifts):
         terms = [tuple(torch.as_tensor(np.ascontiguousarray(a), device="cuda") for a in t) for t in w.terms]
@@ -270,7 +282,10 @@ def run_columns_case(args):
     for aff, _, _ in keep:
         sg.spai_affine_destroy(aff)
     sg.spai_ctx_destroy(ctx)
-    print(json.dumps({"kernel_case": "columns", "workload": args.columns_workload, "systems": len(ws), "columns": sum(w.n for w in ws),
+    print(json.dumps({"kernel_case": "columns", "workload": args.columns_workload, "precision": args.columns_prec,
+                      "variant": args.columns_variant or "tuned",
+                      "least_squares": "normal equations" if args.columns_normal else "Householder QR",
+                      "systems": len(ws), "columns": sum(w.n for w in ws),
                       "steps": args.steps, "build_ms": 1e3 * wall,
                       "device_ms_per_build": {f["name"]: round(f["ms"] / max(args.steps, 1), 3) for f in prof}}),
           flush=True)

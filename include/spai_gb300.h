@@ -79,6 +79,18 @@ typedef struct spai_pc_s *spai_pc;
  * apply converts exactly to FP64 and forms products and sums in FP64.  Exclusive with
  * SPAI_PREC_FP32 (SPAI_EINVAL if both are set). */
 #define SPAI_PREC_BF16 0x200
+/* SPAI_LS_NORMAL, OR-ed into spai_build's pattern_kind, spai_update's approach or
+ * spai_build_batch's kinds: each column least-squares problem (Sec. 2.2; the update's,
+ * Sec. 2.4) is solved by its normal equations instead of Householder QR -- G = Ahat^T Ahat
+ * and h = Ahat^T rhs summed over the nonzero entries of Ahat's columns, G = R^T R by
+ * Cholesky, two triangular solves, one GPU lane per column.  The same minimiser in exact
+ * arithmetic, at a fraction of the work for sparse tiles, with a rounding error that grows
+ * with cond(Ahat)^2 instead of cond(Ahat); a column is rank deficient (status 1, entries 0)
+ * when a Cholesky pivot R_cc^2 is at most rel^2 times the largest diagonal entry of G, rel
+ * = 1e-7 in FP64 and 1e-3 in FP32 (QR's test is |R_cc| <= 1e-14 / 1e-5 times max |R_tt|).
+ * Tiles larger than 32 rows x 8 columns are solved by QR as without the flag.  Not the
+ * paper's solver for these problems: an opt-in for well-conditioned sparse tiles. */
+#define SPAI_LS_NORMAL 0x400
 
 /* Update approaches of Table 1 (Sec. 2.3). */
 #define SPAI_UPDATE_FIRST 1    /* min ||A(1) - A(l) Q||_F, P_l = Q_l P_1 (proposed, Sec. 2.4) */

@@ -43,6 +43,7 @@ UPDATE_FIRST, UPDATE_CHAINED = 1, 2
 UPDATE_DIAGONAL = 4  # OR into an approach: diagonal Q_l
 PREC_FP32 = 0x100  # OR into a pattern kind or an update approach: FP32 least squares and factor
 PREC_BF16 = 0x200  # the same least squares, factor stored in BF16
+LS_NORMAL = 0x400  # OR into a pattern kind or an update approach: column problems by their normal equations
 
 
 class SpaiError(RuntimeError):
@@ -521,9 +522,9 @@ def spai_build_adaptive(ctx, A, eps=1e-4, max_steps=5, max_new=5, max_rows=128, 
 
 def spai_column_variants(low_precision, maxI, maxJ):
     """Codes of the column-kernel variants that fit the tile shape (default first)."""
-    buf = (C.c_int32 * 16)()
-    k = lib().spai_column_variants(int(bool(low_precision)), int(maxI), int(maxJ), buf, 16)
-    return [int(buf[i]) for i in range(min(k, 16))]
+    buf = (C.c_int32 * 32)()
+    k = lib().spai_column_variants(int(bool(low_precision)), int(maxI), int(maxJ), buf, 32)
+    return [int(buf[i]) for i in range(min(k, 32))]
 
 
 def spai_column_variant_get(low_precision, maxI, maxJ):

@@ -54,6 +54,26 @@ template <> __device__ __forceinline__ float singular_rel<float>() { return 1e-5
 
 constexpr int kBlock = 128;
 
+// A's value q (or the right-hand side's) in the working precision: an FP32 solve reads the
+// values rounded to FP32 beforehand when they are given (the same rounding, no FP64
+// conversion per lane), else it rounds the FP64 value itself
+template <typename R, typename P>
+__device__ __forceinline__ R a_value(const P &cp, int32_t q)
+{
+    if constexpr (sizeof(R) == 4) {
+        if (cp.cval32) return __ldg(cp.cval32 + q);
+    }
+    return (R)__ldg(cp.cval + q);
+}
+template <typename R, typename P>
+__device__ __forceinline__ R r_value(const P &cp, int32_t q)
+{
+    if constexpr (sizeof(R) == 4) {
+        if (cp.r_val32) return __ldg(cp.r_val32 + q);
+    }
+    return (R)__ldg(cp.r_val + q);
+}
+
 // per-column shared-memory region: Ahat (maxJ x ld, column-major) | rhs (ld) | rdiag (maxJ)
 // R: working precision (double, or float for SPAI_PREC_FP32 / SPAI_PREC_BF16); A's values
 // are read in FP64 and rounded once to R; the result is written to out_val (R = double),
@@ -84,7 +104,7 @@ __device__ __forceinline__ void column_ls(const P &cp, int64_t k, R *Ah, int ld,
         const int32_t a = __ldg(cp.colptr + j), b = __ldg(cp.colptr + j + 1);
         for (int32_t q = a + tl; q < b; q += T) {
             const int pos = bsearch_i32(Ik, ni, __ldg(cp.rowind + q));
-            if (pos >= 0) Ah[c * ld + pos] = (R)__ldg(cp.cval + q);
+            if (pos >= 0) Ah[c * ld + pos] = a_value<R>(cp, q);
         }
     }
     if (cp.mode == 0) {
@@ -96,7 +116,7 @@ __device__ __forceinline__ void column_ls(const P &cp, int64_t k, R *Ah, int ld,
         const int32_t a = __ldg(cp.r_colptr + k), b = __ldg(cp.r_colptr + k + 1);
         for (int32_t q = a + tl; q < b; q += T) {
             const int pos = bsearch_i32(Ik, ni, __ldg(cp.r_rowind + q));
-            if (pos >= 0) rhs[pos] = (R)__ldg(cp.r_val + q);
+            if (pos >= 0) rhs[pos] = r_value<R>(cp, q);
         }
     }
     __syncwarp(mask);
@@ -225,7 +245,7 @@ __device__ __forceinline__ void column_ls_reg(const P &cp, int64_t k, int tl, un
             const int32_t q1 = __ldg(cp.colptr + j + 1);
             for (int32_t q = __ldg(cp.colptr + j); q < q1; ++q) {
                 const int32_t r = __ldg(cp.rowind + q);
-                const R v = (R)__ldg(cp.cval + q);
+                const R v = a_value<R>(cp, q);
 #pragma unroll
                 for (int i = 0; i < RPL; ++i)
                     if (row[i] == r) a[c][i] = v;
@@ -238,7 +258,7 @@ __device__ __forceinline__ void column_ls_reg(const P &cp, int64_t k, int tl, un
         const int32_t q1 = __ldg(cp.r_colptr + k + 1);
         for (int32_t q = __ldg(cp.r_colptr + k); q < q1; ++q) {
             const int32_t r = __ldg(cp.r_rowind + q);
-            const R v = (R)__ldg(cp.r_val + q);
+            const R v = r_value<R>(cp, q);
 #pragma unroll
             for (int i = 0; i < RPL; ++i)
                 if (row[i] == r) b[i] = v;
@@ -361,12 +381,459 @@ __global__ void __launch_bounds__(kBlock) k_spai_columns_reg(ColumnProblem cp0, 
     }
 }
 
+// ---- one lane per column problem for small tiles.  The lane stages its own problem in
+// its own shared-memory region -- the row list I_k padded with INT_MAX to MI entries, Ahat
+// column-major with leading dimension ld, the right-hand side -- placing every entry of
+// A(:, J_k) by a fixed-step binary search over the staged rows, then runs the Householder
+// sweep of column_ls with T = 1: the reflector of column c and the column it is applied
+// to sit in registers (each tile entry is loaded and stored once per reflector, nothing is
+// reduced across lanes), R stays in the tile (its diagonal in registers) for the back
+// substitution.  MI (a power of two >= ld) and MJ (>= |J_k|) are compile-time bounds:
+// every row loop is unrolled over MI, rows past |I_k| skipped by predicates, rows above
+// the reflector's row skipped at compile time.  Same arithmetic as column_ls, the dot
+// products summed in four interleaved partial sums.
+constexpr int kLaneBlock = 32;
+
+// index of the first staged row >= r (rows sorted, INT_MAX beyond |I_k|, MI a power of two)
+template <int MI>
+__device__ __forceinline__ int lane_pos(const int32_t *rows, int32_t r)
+{
+    int p = 0;
+#pragma unroll
+    for (int s = MI / 2; s > 0; s >>= 1)
+        if (rows[p + s - 1] < r) p += s;
+    return p;
+}
+
+// stage the lane's problem: rows of I_k, Ahat = A(I_k, J_k) and the right-hand side;
+// false (status 1, ERR_TOO_WIDE) when the tile exceeds the lane's region
+// With rhs NULL (a build by the normal equations) the right-hand side e_k is not staged: *pk
+// is the position of row k in I_k (or -1).
+template <int MI, int MJ, typename R, typename P>
+__device__ __forceinline__ bool gather_lane(const P &cp, int64_t k, int32_t *rows, R *Ah, R *rhs, int ld, int mj,
+                                            int32_t ni, int32_t ja, int32_t nj, int32_t ia, int *pk = nullptr)
+{
+    if (ni > ld || nj > mj || ni > MI || nj > MJ) {
+        atomicOr(cp.d_err, ERR_TOO_WIDE);
+        cp.col_status[k] = 1;
+        return false;
+    }
+    // the column pointers of all of J_k first (two rounds of independent loads), then each
+    // column's entries four at a time with their four searches interleaved
+    int32_t q0[MJ], q1[MJ];
+#pragma unroll
+    for (int c = 0; c < MJ; ++c) q0[c] = (c < nj) ? __ldg(cp.Jind + ja + c) : 0;
+#pragma unroll
+    for (int c = 0; c < MJ; ++c) {
+        const int32_t j = q0[c];
+        q0[c] = (c < nj) ? __ldg(cp.colptr + j) : 0;
+        q1[c] = (c < nj) ? __ldg(cp.colptr + j + 1) : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < MI; ++i) rows[i] = (i < ni) ? __ldg(cp.Ilist + ia + i) : INT_MAX;
+    for (int e = 0; e < nj * ld; ++e) Ah[e] = R(0);
+    if (rhs)
+        for (int i = 0; i < ni; ++i) rhs[i] = R(0);
+#pragma unroll
+    for (int c = 0; c < MJ; ++c) {
+#pragma unroll 2
+        for (int32_t q = q0[c]; q < q1[c]; q += 4) {
+            int32_t r[4];
+            R v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool in = q + u < q1[c];
+                r[u] = in ? __ldg(cp.rowind + q + u) : INT_MAX;
+                v[u] = in ? a_value<R>(cp, q + u) : R(0);
+            }
+            int p[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int s = MI / 2; s > 0; s >>= 1)
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (rows[p[u] + s - 1] < r[u]) p[u] += s;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (r[u] != INT_MAX && rows[p[u]] == r[u]) Ah[c * ld + p[u]] = v[u];
+        }
+    }
+    if (!rhs) {
+        const int p = lane_pos<MI>(rows, (int32_t)k);
+        *pk = (rows[p] == (int32_t)k) ? p : -1;
+    } else if (cp.mode == 0) {
+        const int p = lane_pos<MI>(rows, (int32_t)k);
+        if (rows[p] == (int32_t)k) rhs[p] = R(1);
+    } else {
+        const int32_t a = __ldg(cp.r_colptr + k), b = __ldg(cp.r_colptr + k + 1);
+        for (int32_t q = a; q < b; ++q) {
+            const int32_t r = __ldg(cp.r_rowind + q);
+            const int p = lane_pos<MI>(rows, r);
+            if (rows[p] == r) rhs[p] = r_value<R>(cp, q);
+        }
+    }
+    return true;
+}
+
+// the solution m (or zeros for a rank-deficient column) to the factor, and the status;
+// om: the output positions out_map[ja + c], loaded early by the caller
+template <int MJ, typename R, typename P>
+__device__ __forceinline__ void store_lane(const P &cp, int64_t k, int32_t nj, const int32_t (&om)[MJ],
+                                           const R (&m)[MJ], bool singular)
+{
+#pragma unroll
+    for (int c = 0; c < MJ; ++c) {
+        if (c < nj) {
+            const R v = singular ? R(0) : m[c];
+            if (cp.out_val16) cp.out_val16[om[c]] = __bfloat16_as_ushort(__float2bfloat16_rn((float)v));
+            else if (cp.out_val32) cp.out_val32[om[c]] = (float)v;
+            else cp.out_val[om[c]] = (double)v;
+        }
+    }
+    cp.col_status[k] = singular ? 1 : 0;
+}
+
+template <int MJ, typename P>
+__device__ __forceinline__ void load_out_map(const P &cp, int32_t ja, int32_t nj, int32_t (&om)[MJ])
+{
+#pragma unroll
+    for (int c = 0; c < MJ; ++c) om[c] = (c < nj) ? __ldg(cp.out_map + ja + c) : 0;
+}
+
+template <int MI, int MJ, typename R, typename P>
+__device__ __forceinline__ void column_ls_lane(const P &cp, int64_t k, int32_t *rows, R *Ah, int ld, int mj)
+{
+    R *rhs = Ah + (size_t)mj * ld;
+    const int32_t ia = __ldg(cp.Iptr + k), ni = __ldg(cp.Iptr + k + 1) - ia;
+    const int32_t ja = __ldg(cp.Jptr + k), nj = __ldg(cp.Jptr + k + 1) - ja;
+    if (!gather_lane<MI, MJ, R>(cp, k, rows, Ah, rhs, ld, mj, ni, ja, nj, ia)) return;
+    int32_t om[MJ];
+    load_out_map<MJ>(cp, ja, nj, om);
+
+    // ---- Householder QR; R above the diagonal stays in the tile, its diagonal in rd
+    bool singular = ni < nj;
+    R rd[MJ];
+#pragma unroll
+    for (int c = 0; c < MJ; ++c) {
+        rd[c] = R(1);
+        if (c < nj && !singular) {
+            R v[MI];
+            R s4[4] = {R(0), R(0), R(0), R(0)};
+#pragma unroll
+            for (int i = c; i < MI; ++i) {
+                v[i] = (i < ni) ? Ah[c * ld + i] : R(0);
+                s4[i & 3] = fma(v[i], v[i], s4[i & 3]);
+            }
+            const R alpha = sqrt((s4[0] + s4[1]) + (s4[2] + s4[3]));
+            if (!(alpha > R(0))) {
+                singular = true;
+            } else {
+                const R xc = v[c];
+                const R sgn = (xc >= R(0)) ? R(1) : R(-1);
+                const R inv = R(1) / (alpha * (alpha + fabs(xc)));  // 2 / v^T v
+                v[c] = xc + sgn * alpha;
+                rd[c] = -sgn * alpha;
+                for (int t = c + 1; t <= nj; ++t) {  // t == nj is the right-hand side
+                    R *col = (t < nj) ? (Ah + t * ld) : rhs;
+                    R x[MI];
+                    R d4[4] = {R(0), R(0), R(0), R(0)};
+#pragma unroll
+                    for (int i = c; i < MI; ++i) {
+                        if (i < ni) {
+                            x[i] = col[i];
+                            d4[i & 3] = fma(v[i], x[i], d4[i & 3]);
+                        }
+                    }
+                    const R g = ((d4[0] + d4[1]) + (d4[2] + d4[3])) * inv;
+#pragma unroll
+                    for (int i = c; i < MI; ++i)
+                        if (i < ni) col[i] = fma(-g, v[i], x[i]);
+                }
+            }
+        }
+    }
+    if (!singular) {
+        R rmax = R(0);
+#pragma unroll
+        for (int c = 0; c < MJ; ++c)
+            if (c < nj) rmax = fmax(rmax, fabs(rd[c]));
+#pragma unroll
+        for (int c = 0; c < MJ; ++c)
+            if (c < nj && fabs(rd[c]) <= singular_rel<R>() * rmax) singular = true;
+    }
+    // ---- back substitution R m = (Q^T rhs)(0:nj)
+    R m[MJ];
+#pragma unroll
+    for (int c = MJ - 1; c >= 0; --c) {
+        m[c] = R(0);
+        if (c < nj && !singular) {
+            R acc = R(0);
+#pragma unroll
+            for (int t = c + 1; t < MJ; ++t)
+                if (t < nj) acc = fma(Ah[t * ld + c], m[t], acc);
+            m[c] = (rhs[c] - acc) / rd[c];
+        }
+    }
+    store_lane<MJ, R>(cp, k, nj, om, m, singular);
+}
+
+// rank-deficiency threshold of the normal equations: a Cholesky pivot (R_cc^2) at most
+// rel^2 times the largest diagonal entry of G; the normal equations resolve R's diagonal
+// only to about the square root of the working precision
+template <typename R> __device__ __forceinline__ R singular_rel_ne();
+template <> __device__ __forceinline__ double singular_rel_ne<double>() { return 1e-7; }
+template <> __device__ __forceinline__ float singular_rel_ne<float>() { return 1e-3f; }
+
+// The same column problem by its normal equations (SPAI_LS_NORMAL): G = Ahat^T Ahat and
+// h = Ahat^T rhs (in FP64 summed over the nonzero entries of each column of Ahat only --
+// a column of A has few, so the work is the nonzeros' products, not the dense tile's; in
+// FP32 row by row over the dense tile), then G = R^T R by Cholesky and R^T R m = h by two
+// triangular solves, all in registers.  Exact arithmetic gives the least-squares
+// solution of column_ls; in floating point the error grows with cond(Ahat)^2 instead of
+// cond(Ahat).
+template <int MI, int MJ, typename R, typename P>
+__device__ __forceinline__ void column_ne_lane(const P &cp, int64_t k, int32_t *rows, R *Ah, int ld, int mj,
+                                               bool with_rhs)
+{
+    // a build (rhs e_k) stages no right-hand side: h_c = Ahat(k, c)
+    R *rhs = with_rhs ? Ah + (size_t)mj * ld : nullptr;
+    const int32_t ia = __ldg(cp.Iptr + k), ni = __ldg(cp.Iptr + k + 1) - ia;
+    const int32_t ja = __ldg(cp.Jptr + k), nj = __ldg(cp.Jptr + k + 1) - ja;
+    int pk = -1;
+    if (!gather_lane<MI, MJ, R>(cp, k, rows, Ah, rhs, ld, mj, ni, ja, nj, ia, &pk)) return;
+    int32_t om[MJ];
+    load_out_map<MJ>(cp, ja, nj, om);
+
+    // ---- G (upper triangle) and h
+    R G[MJ][MJ], h[MJ];
+#pragma unroll
+    for (int c = 0; c < MJ; ++c) {
+        h[c] = R(0);
+#pragma unroll
+        for (int t = c; t < MJ; ++t) G[c][t] = R(0);
+    }
+    if constexpr (sizeof(R) == 4) {
+        // FP32: row by row over the dense tile, every product of a row at once (no branches;
+        // the FP32 pipe has the throughput to spare)
+        for (int i = 0; i < ni; ++i) {
+            R a[MJ];
+#pragma unroll
+            for (int c = 0; c < MJ; ++c) a[c] = (c < nj) ? Ah[c * ld + i] : R(0);
+#pragma unroll
+            for (int c = 0; c < MJ; ++c)
+#pragma unroll
+                for (int t = c; t < MJ; ++t) G[c][t] = fma(a[c], a[t], G[c][t]);
+            if (rhs) {
+                const R b = rhs[i];
+#pragma unroll
+                for (int c = 0; c < MJ; ++c) h[c] = fma(a[c], b, h[c]);
+            }
+        }
+    } else {
+        // FP64: the products of each column's nonzero entries only (the FP64 pipe is the
+        // bound: a column of A has few nonzeros in its tile column)
+#pragma unroll
+        for (int c = 0; c < MJ; ++c) {
+            if (c < nj) {
+                for (int i = 0; i < ni; ++i) {
+                    const R a = Ah[c * ld + i];
+                    if (a != R(0)) {
+#pragma unroll
+                        for (int t = c; t < MJ; ++t)
+                            if (t < nj) G[c][t] = fma(a, Ah[t * ld + i], G[c][t]);
+                        if (rhs) h[c] = fma(a, rhs[i], h[c]);
+                    }
+                }
+            }
+        }
+    }
+    if (!rhs) {
+#pragma unroll
+        for (int c = 0; c < MJ; ++c) h[c] = (c < nj && pk >= 0) ? Ah[c * ld + pk] : R(0);
+    }
+    // ---- G = R^T R (R upper, over G's upper triangle), R^T y = h, R m = y
+    bool singular = ni < nj;
+    R gmax = R(0);
+#pragma unroll
+    for (int c = 0; c < MJ; ++c)
+        if (c < nj) gmax = fmax(gmax, G[c][c]);
+    const R rel = singular_rel_ne<R>();
+    const R tiny = rel * rel * gmax;
+    R rinv[MJ];
+#pragma unroll
+    for (int c = 0; c < MJ; ++c) {
+        rinv[c] = R(0);
+        if (c < nj && !singular) {
+            R d = G[c][c];
+#pragma unroll
+            for (int p = 0; p < c; ++p) d = fma(-G[p][c], G[p][c], d);
+            if (!(d > tiny)) {
+                singular = true;
+            } else {
+                const R rcc = sqrt(d);
+                rinv[c] = R(1) / rcc;
+                G[c][c] = rcc;
+#pragma unroll
+                for (int t = c + 1; t < MJ; ++t) {
+                    if (t < nj) {
+                        R e = G[c][t];
+#pragma unroll
+                        for (int p = 0; p < c; ++p) e = fma(-G[p][c], G[p][t], e);
+                        G[c][t] = e * rinv[c];
+                    }
+                }
+            }
+        }
+    }
+    R m[MJ];
+#pragma unroll
+    for (int c = 0; c < MJ; ++c) {  // R^T y = h
+        m[c] = R(0);
+        if (c < nj && !singular) {
+            R e = h[c];
+#pragma unroll
+            for (int p = 0; p < c; ++p) e = fma(-G[p][c], m[p], e);
+            m[c] = e * rinv[c];
+        }
+    }
+#pragma unroll
+    for (int c = MJ - 1; c >= 0; --c) {  // R m = y
+        if (c < nj && !singular) {
+            R e = m[c];
+#pragma unroll
+            for (int t = c + 1; t < MJ; ++t)
+                if (t < nj) e = fma(-G[c][t], m[t], e);
+            m[c] = e * rinv[c];
+        }
+    }
+    store_lane<MJ, R>(cp, k, nj, om, m, singular);
+}
+
+// words of one lane's region: MI row slots, then (mj + 1) x ld values of R; odd in units of
+// R, so that the lanes of a warp reading the same offset of their regions hit distinct banks
+__host__ __device__ inline int lane_words(int mi, int ld, int mj, bool low, bool with_rhs = true)
+{
+    const int vals = (mj + (with_rhs ? 1 : 0)) * ld;
+    return low ? ((mi + vals) | 1) : 2 * ((mi / 2 + vals) | 1);
+}
+template <int MI, typename R>
+__host__ __device__ inline int lane_stride_words(int ld, int mj, bool with_rhs)
+{
+    return lane_words(MI, ld, mj, sizeof(R) == 4, with_rhs);
+}
+
+template <int MI, int MJ, typename R, bool NE>
+__global__ void __launch_bounds__(kLaneBlock) k_spai_columns_lane(ColumnProblem cp0, ColumnBatch bt, int ld, int mj,
+                                                                  bool with_rhs)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *base =
+        reinterpret_cast<uint32_t *>(smem_raw) + (size_t)threadIdx.x * lane_stride_words<MI, R>(ld, mj, with_rhs);
+    int32_t *rows = reinterpret_cast<int32_t *>(base);
+    R *Ah = reinterpret_cast<R *>(base + MI);
+    const int64_t total = bt.tab ? bt.total : (int64_t)cp0.n;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        if (bt.tab) {
+            int lo = 0, hi = bt.nsys - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(bt.start + mid) <= g) lo = mid; else hi = mid - 1;
+            }
+            if constexpr (NE) column_ne_lane<MI, MJ, R>(bt.tab[lo], g - __ldg(bt.start + lo), rows, Ah, ld, mj, with_rhs);
+            else column_ls_lane<MI, MJ, R>(bt.tab[lo], g - __ldg(bt.start + lo), rows, Ah, ld, mj);
+        } else {
+            if constexpr (NE) column_ne_lane<MI, MJ, R>(cp0, g, rows, Ah, ld, mj, with_rhs);
+            else column_ls_lane<MI, MJ, R>(cp0, g, rows, Ah, ld, mj);
+        }
+    }
+}
+
+// the one-lane shapes: rows MI (a power of two), columns MJ
+struct LaneShape {
+    int MI, MJ;
+};
+constexpr LaneShape kLaneShapes[] = {{16, 5}, {32, 7}, {32, 8}, {32, 13}};
+constexpr int kNumLaneShapes = 4;
+constexpr int kLaneTeamBase = 96;  // team codes kLaneTeamBase + i select kLaneShapes[i]
+
+bool lane_fits(int i, int32_t maxI, int32_t maxJ, bool low)
+{
+    if (maxI > kLaneShapes[i].MI || maxJ > kLaneShapes[i].MJ) return false;
+    const int ld = maxI < 1 ? 1 : maxI, mj = maxJ < 1 ? 1 : maxJ;
+    return (size_t)kLaneBlock * lane_words(kLaneShapes[i].MI, ld, mj, low) * 4 <= 200 * 1024;
+}
+
+template <int MI, int MJ, typename R, bool NE = false>
+int launch_lane(cudaStream_t st, const ColumnProblem &cp, const ColumnBatch &bt, int32_t maxI, int32_t maxJ)
+{
+    const int ld = maxI < 1 ? 1 : maxI, mj = maxJ < 1 ? 1 : maxJ;
+    if (ld > MI || mj > MJ) return -1;
+    // the normal equations of a build stage no right-hand side (batches are builds)
+    const bool with_rhs = !(NE && (bt.tab || cp.mode == 0));
+    const size_t smem = (size_t)kLaneBlock * lane_stride_words<MI, R>(ld, mj, with_rhs) * 4;
+    if (smem > 227 * 1024) return -1;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_spai_columns_lane<MI, MJ, R, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return -1;
+    const int64_t total = bt.tab ? bt.total : (int64_t)cp.n;
+    int64_t blocks = (total + kLaneBlock - 1) / kLaneBlock;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spai_columns_lane<MI, MJ, R, NE>, kLaneBlock, smem) !=
+            cudaSuccess)
+        return -1;
+    const int64_t resident = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    if (blocks > resident) blocks = resident;
+    if (blocks < 1) blocks = 1;
+    k_spai_columns_lane<MI, MJ, R, NE><<<(unsigned)blocks, kLaneBlock, smem, st>>>(cp, bt, ld, mj, with_rhs);
+    note_launches(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// normal-equations shapes (SPAI_LS_NORMAL): G's upper triangle stays in registers, so MJ <= 8
+constexpr LaneShape kNeShapes[] = {{16, 5}, {32, 7}, {32, 8}};
+constexpr int kNumNeShapes = 3;
+constexpr int kNeTeamBase = 112;  // team codes kNeTeamBase + i select kNeShapes[i]
+
+bool ne_fits(int i, int32_t maxI, int32_t maxJ, bool low)
+{
+    if (maxI > kNeShapes[i].MI || maxJ > kNeShapes[i].MJ) return false;
+    const int ld = maxI < 1 ? 1 : maxI, mj = maxJ < 1 ? 1 : maxJ;
+    return (size_t)kLaneBlock * lane_words(kNeShapes[i].MI, ld, mj, low) * 4 <= 200 * 1024;
+}
+
+template <typename R>
+int launch_ne_shape(cudaStream_t st, const ColumnProblem &cp, const ColumnBatch &bt, int i, int32_t maxI,
+                    int32_t maxJ)
+{
+    switch (i) {
+    case 0: return launch_lane<16, 5, R, true>(st, cp, bt, maxI, maxJ);
+    case 1: return launch_lane<32, 7, R, true>(st, cp, bt, maxI, maxJ);
+    case 2: return launch_lane<32, 8, R, true>(st, cp, bt, maxI, maxJ);
+    default: return -1;
+    }
+}
+
+template <typename R>
+int launch_lane_shape(cudaStream_t st, const ColumnProblem &cp, const ColumnBatch &bt, int i, int32_t maxI,
+                      int32_t maxJ)
+{
+    switch (i) {
+    case 0: return launch_lane<16, 5, R>(st, cp, bt, maxI, maxJ);
+    case 1: return launch_lane<32, 7, R>(st, cp, bt, maxI, maxJ);
+    case 2: return launch_lane<32, 8, R>(st, cp, bt, maxI, maxJ);
+    case 3: return launch_lane<32, 13, R>(st, cp, bt, maxI, maxJ);
+    default: return -1;
+    }
+}
+
 // the register-tiled shapes: team T, rows per lane RPL (tile rows <= T * RPL), columns MJ
 struct RegShape {
     int T, RPL, MJ;
 };
-constexpr RegShape kRegShapes[] = {{4, 4, 5}, {8, 4, 8}, {4, 8, 8}, {8, 4, 13}};
-constexpr int kNumRegShapes = 4;
+constexpr RegShape kRegShapes[] = {{4, 4, 5}, {8, 4, 8}, {4, 8, 8}, {8, 4, 13}, {4, 8, 7}};
+constexpr int kNumRegShapes = 5;
 constexpr int kRegTeamBase = 64;  // team codes kRegTeamBase + i select kRegShapes[i]
 
 template <int T, int RPL, int MJ, typename R>
@@ -402,6 +869,7 @@ int launch_reg_shape(cudaStream_t st, const ColumnProblem &cp, const ColumnBatch
     case 1: return launch_reg<8, 4, 8, R>(st, cp, bt);
     case 2: return launch_reg<4, 8, 8, R>(st, cp, bt);
     case 3: return launch_reg<8, 4, 13, R>(st, cp, bt);
+    case 4: return launch_reg<4, 8, 7, R>(st, cp, bt);  // the 3D 7-point tiles (25 x 7): no padded column
     default: return -1;
     }
 }
@@ -510,6 +978,16 @@ template <typename R>
 int launch_columns(cudaStream_t st, const ColumnProblem &cp, const ColumnBatch &bt, int32_t maxI, int32_t maxJ,
                    int T)
 {
+    if (T >= kNeTeamBase) {
+        const int i = T - kNeTeamBase;
+        if (i >= kNumNeShapes || !ne_fits(i, maxI, maxJ, sizeof(R) == 4)) return -1;
+        return launch_ne_shape<R>(st, cp, bt, i, maxI, maxJ);
+    }
+    if (T >= kLaneTeamBase) {
+        const int i = T - kLaneTeamBase;
+        if (i >= kNumLaneShapes || !lane_fits(i, maxI, maxJ, sizeof(R) == 4)) return -1;
+        return launch_lane_shape<R>(st, cp, bt, i, maxI, maxJ);
+    }
     if (T >= kRegTeamBase) {
         const int i = T - kRegTeamBase;
         if (i >= kNumRegShapes || !reg_fits(i, maxI, maxJ)) return -1;
@@ -562,6 +1040,16 @@ int spai_columns_teams(int32_t maxI, int32_t maxJ, bool low_precision, int *team
         if (T != def && threads_for(T, per)) teams[k++] = T;
     for (int i = 0; i < kNumRegShapes; ++i)
         if (reg_fits(i, maxI, maxJ)) teams[k++] = kRegTeamBase + i;
+    for (int i = 0; i < kNumLaneShapes; ++i)
+        if (lane_fits(i, maxI, maxJ, low_precision)) teams[k++] = kLaneTeamBase + i;
+    return k;
+}
+
+int spai_columns_ne_teams(int32_t maxI, int32_t maxJ, bool low_precision, int *teams)
+{
+    int k = 0;
+    for (int i = 0; i < kNumNeShapes; ++i)
+        if (ne_fits(i, maxI, maxJ, low_precision)) teams[k++] = kNeTeamBase + i;
     return k;
 }
 

@@ -455,6 +455,21 @@ __global__ void k_gather_seg(int32_t nseg, const int64_t *__restrict__ start, co
     }
 }
 
+// dst[start[g] + j] = (float)src_g[j]: segments rounded to FP32 into one stacked array
+__global__ void k_round_seg(int32_t nseg, const int64_t *__restrict__ start, const double *const *__restrict__ src,
+                            float *__restrict__ dst)
+{
+    const int64_t total = start[nseg];
+    for (int64_t t0 = (int64_t)blockIdx.x * kSegTile; t0 < total; t0 += (int64_t)gridDim.x * kSegTile) {
+        int g = seg_of(start, nseg, t0);
+        const int64_t t1 = min(t0 + (int64_t)kSegTile, total);
+        for (int64_t e = t0 + threadIdx.x; e < t1; e += blockDim.x) {
+            while (e >= __ldg(start + g + 1)) ++g;
+            dst[e] = (float)src[g][e - start[g]];
+        }
+    }
+}
+
 // out[g] = smallest j with a_g[j] != 0 (INT_MAX if none; out filled with INT_MAX first)
 __global__ void k_first_nonzero_seg(int32_t nseg, const int64_t *__restrict__ start, const int32_t *const *__restrict__ a,
                                     int32_t *__restrict__ out)
@@ -921,6 +936,14 @@ int launch_gather_seg(cudaStream_t st, int32_t nseg, int64_t total, const int64_
     if (total <= 0) return 0;
     k_gather_seg<<<grid_cap((total + kSegTile - 1) / kSegTile * kThreads), kThreads, 0, st>>>(nseg, start, val, perm,
                                                                                                dst);
+    return check_launch();
+}
+
+int launch_round_seg(cudaStream_t st, int32_t nseg, int64_t total, const int64_t *start, const double *const *src,
+                     float *dst)
+{
+    if (total <= 0) return 0;
+    k_round_seg<<<grid_cap((total + kSegTile - 1) / kSegTile * kThreads), kThreads, 0, st>>>(nseg, start, src, dst);
     return check_launch();
 }
 

@@ -101,6 +101,7 @@ struct spai_pc_s {
     double *a_cval = nullptr;  // this matrix's values in CSC order
     int32_t *status = nullptr;
     bool diag = false;         // diagonal factor (n values, SPAI_UPDATE_DIAGONAL)
+    bool normal = false;       // column problems by their normal equations (SPAI_LS_NORMAL)
     Arena *arena = nullptr;    // non-null: fval*, a_cval and status live in this arena
 };
 
@@ -571,10 +572,11 @@ std::map<std::tuple<int, int, int>, int> g_tune;
 constexpr int64_t kTuneColumns = 262144;
 
 spai_status tuned_team(spai_ctx ctx, bool low, int32_t maxI, int32_t maxJ, int64_t total,
-                       const std::function<int(int, int64_t)> &launch, int *team, bool *done)
+                       const std::function<int(int, int64_t)> &launch, int *team, bool *done, bool normal = false)
 {
     const int64_t sample = std::min(total, kTuneColumns);
-    const auto key = std::make_tuple(low ? 1 : 0, (maxI + 7) / 8 * 8, maxJ);
+    // normal-equations shapes are tuned apart (keys 2, 3): they are another arithmetic
+    const auto key = std::make_tuple((low ? 1 : 0) + (normal ? 2 : 0), (maxI + 7) / 8 * 8, maxJ);
     auto lookup = [&]() {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
@@ -584,8 +586,8 @@ spai_status tuned_team(spai_ctx ctx, bool low, int32_t maxI, int32_t maxJ, int64
     if ((*team = lookup())) return SPAI_OK;
     std::lock_guard<std::mutex> run(g_tune_run_mu);
     if ((*team = lookup())) return SPAI_OK;  // tuned by another thread meanwhile
-    int cand[16];
-    const int nc = spai_columns_teams(maxI, maxJ, low, cand);
+    int cand[32];
+    const int nc = normal ? spai_columns_ne_teams(maxI, maxJ, low, cand) : spai_columns_teams(maxI, maxJ, low, cand);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CU(cudaEventCreate(&e0), "event");
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -628,6 +630,13 @@ spai_status tuned_team(spai_ctx ctx, bool low, int32_t maxI, int32_t maxJ, int64
     return SPAI_OK;
 }
 
+// device scratch released (stream-ordered) when the scope ends
+struct DevScratch {
+    spai_ctx ctx;
+    void *p = nullptr;
+    ~DevScratch() { dfree(ctx, p); }
+};
+
 spai_status run_columns(spai_ctx ctx, spai_pc pc, int mode, const double *rhs_cval)
 {
     Sym *s = pc->sym;
@@ -653,17 +662,37 @@ spai_status run_columns(spai_ctx ctx, spai_pc pc, int mode, const double *rhs_cv
     if (s->n == 0) return SPAI_OK;
     {
         const double aI = (double)s->nI / s->n, aJ = (double)s->nnzP / s->n;
-        const double fl = (double)s->n * (2 * aJ * aJ * (aI - aJ / 3) + 4 * aI * aJ + aJ * aJ);
+        double fl = (double)s->n * (2 * aJ * aJ * (aI - aJ / 3) + 4 * aI * aJ + aJ * aJ);
         const double by = 12.0 * s->nnzA * (mode ? 2 : 1) + 8.0 * (s->n + 1) + 4.0 * s->nI + 16.0 * s->nnzP;
         const bool low = cp.out_val32 || cp.out_val16;
+        // an FP32 solve reads A's values (and the right-hand side's) rounded to FP32 once here
+        DevScratch scratch{ctx};
+        float *v32 = nullptr;
+        if (low && s->nnzA > 0) {
+            spai_status st = dalloc_n(ctx, &v32, (int64_t)s->nnzA * (mode ? 2 : 1));
+            if (st) return st;
+            scratch.p = v32;
+            KL(launch_round_f32(ctx->stream, s->nnzA, cp.cval, v32), "values in FP32");
+            cp.cval32 = v32;
+            if (mode) {
+                KL(launch_round_f32(ctx->stream, s->nnzA, cp.r_val, v32 + s->nnzA), "values in FP32");
+                cp.r_val32 = v32 + s->nnzA;
+            }
+        }
         auto launch = [&](int t, int64_t limit) {
             ColumnProblem part = cp;
             part.n = (int32_t)std::min<int64_t>(cp.n, limit);
             return launch_spai_columns_team(ctx->stream, part, low, s->maxI, s->maxJ, t);
         };
-        int team = 0;
+        int team = 0, ne[32];
         bool done = false;
-        spai_status st = tuned_team(ctx, low, s->maxI, s->maxJ, cp.n, launch, &team, &done);
+        // SPAI_LS_NORMAL: the normal-equations kernels where the tile fits them, else QR
+        const bool normal = pc->normal && spai_columns_ne_teams(s->maxI, s->maxJ, low, ne) > 0;
+        if (normal) {  // G from the nonzeros (nnz(A) / n per column), Cholesky, two solves
+            const double az = (double)s->nnzA / s->n;
+            fl = (double)s->n * (az * aJ * (aJ + 1) + (mode ? 2 * az * aJ : 0) + aJ * aJ * aJ / 3 + 2 * aJ * aJ);
+        }
+        spai_status st = tuned_team(ctx, low, s->maxI, s->maxJ, cp.n, launch, &team, &done, normal);
         if (st) return st;
         if (!done) PKL("spai_columns", fl, by, launch(team, cp.n), "column least squares");
     }
@@ -1119,7 +1148,8 @@ extern "C" spai_status spai_build(spai_ctx ctx, const spai_csr *A, int32_t patte
     *out = nullptr;
     const int prec = prec_of(pattern_kind);
     if (prec < 0) return fail(ctx, SPAI_EINVAL, "SPAI_PREC_FP32 and SPAI_PREC_BF16 are exclusive");
-    pattern_kind &= ~(SPAI_PREC_FP32 | SPAI_PREC_BF16);
+    const bool normal = (pattern_kind & SPAI_LS_NORMAL) != 0;
+    pattern_kind &= ~(SPAI_PREC_FP32 | SPAI_PREC_BF16 | SPAI_LS_NORMAL);
     if (pattern_kind != SPAI_PATTERN_A && pattern_kind != SPAI_PATTERN_A2)
         return fail(ctx, SPAI_EINVAL, "unknown pattern kind %d", pattern_kind);
     spai_status st = validate_device_csr(ctx, A, "A");
@@ -1129,6 +1159,7 @@ extern "C" spai_status spai_build(spai_ctx ctx, const spai_csr *A, int32_t patte
     spai_pc pc = nullptr;
     if ((st = pc_alloc(ctx, s, prec, &pc))) { sym_release(s); return st; }
     pc->root = pc;
+    pc->normal = normal;
     if (s->nnzA)
         PKL("gather_csc", 0.0, 20.0 * s->nnzA, launch_gather_f64(ctx->stream, s->nnzA, s->a_perm, A->val, pc->a_cval),
             "gather values");
@@ -1342,7 +1373,8 @@ extern "C" spai_status spai_update(spai_ctx ctx, spai_pc base, const spai_csr *A
     const int prec = prec_of(approach);
     if (prec < 0) return fail(ctx, SPAI_EINVAL, "SPAI_PREC_FP32 and SPAI_PREC_BF16 are exclusive");
     const bool diag = (approach & SPAI_UPDATE_DIAGONAL) != 0;
-    approach &= ~(SPAI_PREC_FP32 | SPAI_PREC_BF16 | SPAI_UPDATE_DIAGONAL);
+    const bool normal = (approach & SPAI_LS_NORMAL) != 0;
+    approach &= ~(SPAI_PREC_FP32 | SPAI_PREC_BF16 | SPAI_UPDATE_DIAGONAL | SPAI_LS_NORMAL);
     if (approach != SPAI_UPDATE_FIRST && approach != SPAI_UPDATE_CHAINED)
         return fail(ctx, SPAI_EINVAL, "unknown update approach %d", approach);
     spai_status st = check_csr_args(ctx, A_new, "A_new");
@@ -1362,6 +1394,7 @@ extern "C" spai_status spai_update(spai_ctx ctx, spai_pc base, const spai_csr *A
     }
     spai_pc pc = nullptr;
     if ((st = pc_alloc(ctx, s, prec, &pc, diag))) return st;
+    pc->normal = normal;
     s->refs++;
     spai_pc from = (approach == SPAI_UPDATE_FIRST) ? base->root : base;
     pc->parent = from;
@@ -1400,16 +1433,19 @@ namespace {
 
 spai_status run_columns_batch(spai_ctx ctx, int32_t nsys, spai_pc *pcs)
 {
-    // buckets of systems whose problems share a tile: (low precision, max |J|, max |I| rounded up to 8)
+    // buckets of systems whose problems share a tile: (low precision + 2 for the normal
+    // equations, max |J|, max |I| rounded up to 8)
     std::map<std::tuple<int, int, int>, std::vector<int>> buckets;
     for (int i = 0; i < nsys; ++i) {
         const Sym *s = pcs[i]->sym;
         if (s->n == 0) continue;
-        buckets[std::make_tuple(pcs[i]->fval ? 0 : 1, s->maxJ, (s->maxI + 7) / 8 * 8)].push_back(i);
+        buckets[std::make_tuple((pcs[i]->fval ? 0 : 1) + (pcs[i]->normal ? 2 : 0), s->maxJ, (s->maxI + 7) / 8 * 8)]
+            .push_back(i);
     }
     spai_status st = SPAI_OK;
     for (auto &b : buckets) {
-        const int low = std::get<0>(b.first), maxJ = std::get<1>(b.first);
+        const int low = std::get<0>(b.first) & 1, maxJ = std::get<1>(b.first);
+        const bool want_normal = std::get<0>(b.first) >= 2;
         const std::vector<int> &mem = b.second;
         const int m = (int)mem.size();
         int maxI = 0;  // tile rows: the bucket's largest |I_k| (its class, a multiple of 8, keys the tuning)
@@ -1444,6 +1480,29 @@ spai_status run_columns_batch(spai_ctx ctx, int32_t nsys, spai_pc *pcs)
             fl += (double)s->n * (2 * aJ * aJ * (aI - aJ / 3) + 4 * aI * aJ + aJ * aJ);
             by += 12.0 * s->nnzA + 8.0 * (s->n + 1) + 4.0 * s->nI + 16.0 * s->nnzP;
         }
+        // FP32 solves read A's values rounded to FP32 once here (all systems of the bucket)
+        DevScratch scratch{ctx};
+        if (low) {
+            std::vector<int64_t> vstart((size_t)m + 1, 0);
+            std::vector<const double *> vsrc((size_t)m);
+            for (int t = 0; t < m; ++t) {
+                vstart[t + 1] = vstart[t] + pcs[mem[t]]->sym->nnzA;
+                vsrc[t] = tab[t].cval;
+            }
+            const int64_t tot = vstart[m];
+            const size_t o_start = ((size_t)tot * 4 + 255) / 256 * 256, o_src = o_start + ((size_t)m + 1) * 8;
+            char *sc = nullptr;
+            if ((st = dalloc(ctx, (void **)&sc, o_src + (size_t)m * 8))) return st;
+            scratch.p = sc;
+            float *v32 = (float *)sc;
+            CU(cudaMemcpyAsync(sc + o_start, vstart.data(), ((size_t)m + 1) * 8, cudaMemcpyHostToDevice, ctx->stream),
+               "segments");
+            CU(cudaMemcpyAsync(sc + o_src, vsrc.data(), (size_t)m * 8, cudaMemcpyHostToDevice, ctx->stream), "segments");
+            KL(launch_round_seg(ctx->stream, m, tot, (const int64_t *)(sc + o_start), (const double *const *)(sc + o_src),
+                                v32),
+               "values in FP32");
+            for (int t = 0; t < m; ++t) tab[t].cval32 = v32 + vstart[t];
+        }
         ColumnProblem *d_tab = nullptr;
         int64_t *d_start = nullptr;
         if ((st = dalloc_n(ctx, &d_tab, m)) || (st = dalloc_n(ctx, &d_start, (int64_t)m + 1))) {
@@ -1459,9 +1518,10 @@ spai_status run_columns_batch(spai_ctx ctx, int32_t nsys, spai_pc *pcs)
             part.total = std::min(bt.total, limit);
             return launch_spai_columns_batch(ctx->stream, part, low != 0, maxI, maxJ, t);
         };
-        int team = 0;
+        int team = 0, ne[32];
         bool done = false;
-        if ((st = tuned_team(ctx, low != 0, maxI, maxJ, bt.total, launch, &team, &done))) {
+        const bool normal = want_normal && spai_columns_ne_teams(maxI, maxJ, low != 0, ne) > 0;
+        if ((st = tuned_team(ctx, low != 0, maxI, maxJ, bt.total, launch, &team, &done, normal))) {
             dfree(ctx, d_tab);
             dfree(ctx, d_start);
             return st;
@@ -1883,7 +1943,7 @@ extern "C" spai_status spai_build_batch(spai_ctx ctx, int32_t nsys, const spai_c
     for (int i = 0; i < nsys; ++i) {
         precs[i] = prec_of(pattern_kind[i]);
         if (precs[i] < 0) return fail(ctx, SPAI_EINVAL, "system %d: SPAI_PREC_FP32 and SPAI_PREC_BF16 are exclusive", i);
-        kinds[i] = pattern_kind[i] & ~(SPAI_PREC_FP32 | SPAI_PREC_BF16);
+        kinds[i] = pattern_kind[i] & ~(SPAI_PREC_FP32 | SPAI_PREC_BF16 | SPAI_LS_NORMAL);
         if (kinds[i] != SPAI_PATTERN_A && kinds[i] != SPAI_PATTERN_A2)
             return fail(ctx, SPAI_EINVAL, "system %d: unknown pattern kind %d", i, kinds[i]);
         if ((st = check_csr_args(ctx, &A[i], "A"))) return st;
@@ -1905,6 +1965,7 @@ extern "C" spai_status spai_build_batch(spai_ctx ctx, int32_t nsys, const spai_c
     if (stacked) {
         std::vector<spai_pc> pcs;
         if ((st = build_batch_stacked(ctx, nsys, A, kinds.data(), precs.data(), pcs))) return st;
+        for (int i = 0; i < nsys; ++i) pcs[i]->normal = (pattern_kind[i] & SPAI_LS_NORMAL) != 0;
         st = run_columns_batch(ctx, nsys, pcs.data());
         if (st && st != SPAI_ESINGULAR) {
             for (spai_pc pc : pcs) spai_pc_destroy(pc);
@@ -1931,6 +1992,7 @@ extern "C" spai_status spai_build_batch(spai_ctx ctx, int32_t nsys, const spai_c
             return st;
         }
         pcs[i]->root = pcs[i];
+        pcs[i]->normal = (pattern_kind[i] & SPAI_LS_NORMAL) != 0;
         if (syms[i]->nnzA)
             PKL("gather_csc", 0.0, 20.0 * syms[i]->nnzA,
                 launch_gather_f64(ctx->stream, syms[i]->nnzA, syms[i]->a_perm, A[i].val, pcs[i]->a_cval),
@@ -1948,7 +2010,7 @@ extern "C" spai_status spai_build_batch(spai_ctx ctx, int32_t nsys, const spai_c
 extern "C" int32_t spai_column_variants(int32_t low_precision, int32_t maxI, int32_t maxJ, int32_t *codes, int32_t cap)
 {
     if (maxI < 1 || maxJ < 1 || !spai_columns_fit(maxI, maxJ)) return 0;
-    int cand[16];
+    int cand[32];
     const int nc = spai_columns_teams(maxI, maxJ, low_precision != 0, cand);
     for (int i = 0; i < nc && i < cap && codes; ++i) codes[i] = cand[i];
     return nc;
@@ -1971,7 +2033,7 @@ extern "C" spai_status spai_column_variant_set(int32_t low_precision, int32_t ma
         return SPAI_OK;
     }
     // the code must fit every shape of the class: the largest max |I_k| it holds
-    int cand[16];
+    int cand[32];
     const int nc = spai_columns_fit(std::get<1>(key), maxJ)
                        ? spai_columns_teams(std::get<1>(key), maxJ, low_precision != 0, cand)
                        : 0;

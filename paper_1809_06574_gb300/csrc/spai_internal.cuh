@@ -130,6 +130,10 @@ int launch_scale_rows32(cudaStream_t st, int32_t s, int32_t n, const F32Vals &q,
 int launch_scale_rows32(cudaStream_t st, int32_t s, int32_t n, const F32Vals &q, const float *X, double *Y);
 // dst[i] = src[i] rounded to FP32
 int launch_round_f32(cudaStream_t st, int64_t count, const double *src, float *dst);
+// dst[start[g] + j] = (float)src[g][j] for the nseg segments laid end to end (total = start[nseg];
+// start and src device arrays)
+int launch_round_seg(cudaStream_t st, int32_t nseg, int64_t total, const int64_t *start, const double *const *src,
+                     float *dst);
 int launch_pack(cudaStream_t st, int32_t s, int32_t n, const double *src, int64_t ld, double *dst);
 // Y[r][c] = q[r] X[r][c] (a diagonal factor; q FP64, FP32 or BF16 bits, one of them given)
 // Y = A X and Y = diag(q) X on the rows of a list of nchunks row chunks [r0[c], r1[c]) of at
@@ -155,6 +159,7 @@ struct ColumnProblem {
     int32_t mode;                    // 0 build (rhs e_k), 1 update (rhs column k of R)
     const int32_t *r_colptr, *r_rowind;
     const double *r_val;             // rhs matrix (CSC values) in update mode
+    const float *cval32, *r_val32;   // non-null: the same values rounded to FP32 once (FP32 solves read these)
     const int32_t *out_map;          // J position -> position in the output array
     double *out_val;
     float *out_val32;                // non-null: solve in FP32 and write here instead
@@ -202,8 +207,12 @@ int launch_spai_columns(cudaStream_t st, const ColumnProblem &cp, int32_t maxI, 
 int launch_spai_columns_team(cudaStream_t st, const ColumnProblem &cp, bool low_precision, int32_t maxI,
                              int32_t maxJ, int team);
 // Team sizes that fit a maxI x maxJ problem (the default choice first), then the codes
-// (64 + i) of the register-tiled shapes that fit; returns how many (at most 12).
+// (64 + i) of the register-tiled shapes and (96 + i) of the one-lane shapes that fit;
+// returns how many (at most 15; teams needs room for 32).
 int spai_columns_teams(int32_t maxI, int32_t maxJ, bool low_precision, int *teams);
+// Codes (112 + i) of the normal-equations shapes (SPAI_LS_NORMAL) that fit; 0 when the tile
+// is too large for them (such problems are solved by Householder QR).
+int spai_columns_ne_teams(int32_t maxI, int32_t maxJ, bool low_precision, int *teams);
 // All columns of a batch in one persistent launch with team size `team` (FP32 working
 // precision if low_precision); every problem must fit maxI x maxJ.
 int launch_spai_columns_batch(cudaStream_t st, const ColumnBatch &bt, bool low_precision, int32_t maxI,
