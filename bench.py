@@ -582,7 +582,7 @@ def run_serving(args, sg, torch):
     Bs = [torch.from_numpy(np.asfortranarray(w.B).T.copy()).pin_memory() for w in systems]  # (8, n): column-major n x 8
     trace = synth.serving_trace(args.serve_rate, args.serve_seconds, len(systems))
     common = dict(restart=30, max_cycles=100, tol=1e-8)
-    served = dict(slots=args.serve_slots, reuse=True, radius=0.05, pattern_kind=sg.PREC_FP32,
+    served = dict(slots=args.serve_slots, reuse=True, radius=0.05, pattern_kind=sg.PREC_FP32 | sg.LS_NORMAL,
                   mem_budget=40 << 30, precision=sg.SOLVE_MIXED, **common)
     # warm-up on a discarded server (module load, allocator pools); the timed server starts cold
     serve_trace(sg, torch, systems, Bs, [(0.0, i, 0.5, 1.0, 8) for i in range(len(systems))], **served)
@@ -629,7 +629,7 @@ def run_served_sweep(args, sg, torch, w, steps, warmup=1):
     B = torch.as_tensor(np.ascontiguousarray(w.B.T), device=dev)  # (8, n): column-major n x 8
     reqs = [(p, s) for s in w.shifts for p in w.params]
     Xs = [torch.empty((int(w.B.shape[1]), n), dtype=torch.float64, device=dev) for _ in reqs]
-    opts = dict(slots=args.workers, reuse=True, radius=1.0, pattern_kind=sg.PATTERN_A | sg.PREC_FP32,
+    opts = dict(slots=args.workers, reuse=True, radius=1.0, pattern_kind=sg.PATTERN_A | sg.PREC_FP32 | sg.LS_NORMAL,
                 restart=w.restart, max_cycles=50, tol=w.tol, precision=sg.SOLVE_MIXED)
     spans, lats, iters, routes = [], [], [], {"build": 0, "update": 0, "reuse": 0}
     for it in range(warmup + steps):
@@ -659,7 +659,7 @@ def run_served_sweep(args, sg, torch, w, steps, warmup=1):
             "latency_ms": {"p50": round(1e3 * float(np.percentile(lat, 50)), 2),
                            "p99": round(1e3 * float(np.percentile(lat, 99)), 2)},
             "gmres_iterations_mean": float(np.mean(iters)), "routes": routes, "slots": args.workers,
-            "form": "server, FP32 factors, FP32 operator + FP64 refinement, one cached build per shift "
+            "form": "server, FP32 factors (normal equations), FP32 operator + FP64 refinement, one cached build per shift "
                     "and updates from it, all 60 requests at once (closed loop)"}
 
 
@@ -1342,9 +1342,9 @@ def main():
     mixed = None
     fp32_factors = None
     if not args.no_mixed:
-        mixed = timed_sweep(prec=sg.PREC_FP32, solve_precision=sg.SOLVE_MIXED)
-        mixed.update({"dtype": "f32 SPAI factors and f32 operator products, f64 basis/Gram-Schmidt/"
-                               "least squares/true residual (iterative refinement)",
+        mixed = timed_sweep(prec=sg.PREC_FP32 | sg.LS_NORMAL, solve_precision=sg.SOLVE_MIXED)
+        mixed.update({"dtype": "f32 SPAI factors (column problems by their normal equations) and f32 operator "
+                               "products, f64 basis/Gram-Schmidt/least squares/true residual (iterative refinement)",
                       "vs_plain_fp64": None})
         fp32_factors = timed_sweep(prec=sg.PREC_FP32)
         fp32_factors["note"] = ("FP32 SPAI factors applied with FP64 products and sums, FP64 solve: the "
@@ -1359,7 +1359,8 @@ def main():
         gcro = timed_sweep(gcro_kmax=args.gcro_kmax)
         gcro["note"] = (f"FP64 as the headline; block GCRO, each worker carrying a recycled space of "
                         f"{args.gcro_kmax} columns per shift (its latest solutions of the shift), cleared every step")
-        gcro_mixed = timed_sweep(gcro_kmax=args.gcro_kmax, prec=sg.PREC_FP32, solve_precision=sg.SOLVE_MIXED)
+        gcro_mixed = timed_sweep(gcro_kmax=args.gcro_kmax, prec=sg.PREC_FP32 | sg.LS_NORMAL,
+                                 solve_precision=sg.SOLVE_MIXED)
         gcro["mixed_precision"] = {k: gcro_mixed[k] for k in ("value", "ms_per_step", "gmres_iterations", "cycles")}
     warm = None
     if not args.no_mixed:

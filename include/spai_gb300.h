@@ -555,7 +555,8 @@ typedef struct spai_server_s *spai_server;
 
 typedef struct {
     int32_t slots;         /* requests on the GPU at once, 1..64 */
-    int32_t pattern_kind;  /* SPAI_PATTERN_A or SPAI_PATTERN_A2, optionally | SPAI_PREC_FP32 or SPAI_PREC_BF16 */
+    int32_t pattern_kind;  /* SPAI_PATTERN_A or SPAI_PATTERN_A2, optionally | SPAI_PREC_FP32 or SPAI_PREC_BF16,
+                              | SPAI_LS_NORMAL (builds and updates alike) */
     int32_t reuse;         /* 1: cache builds and route nearby requests to spai_update; 0: build per request */
     int32_t restart;       /* block GMRES(m) restart length m */
     int32_t max_cycles;    /* restart cycles before a request fails with SPAI_ENOTCONV */

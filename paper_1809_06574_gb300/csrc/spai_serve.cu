@@ -45,6 +45,7 @@ size_t round256(size_t b) { return ((b ? b : 16) + 255) / 256 * 256; }
 constexpr size_t kMaxSystems = 1024;
 
 constexpr int32_t kPrecBits = SPAI_PREC_FP32 | SPAI_PREC_BF16;
+constexpr int32_t kKindFlags = kPrecBits | SPAI_LS_NORMAL;  // bits of pattern_kind beside the pattern
 
 struct System {
     spai_affine aff = nullptr;
@@ -156,7 +157,7 @@ size_t build_estimate(const spai_server_s *S, const System &y)
 {
     if (y.build_bytes) return y.build_bytes;
     const size_t n1 = (size_t)y.n + 1, nz = (size_t)y.nnz, mr = (size_t)(y.max_row > 0 ? y.max_row : 1);
-    const bool a2 = (S->o.pattern_kind & ~kPrecBits) == SPAI_PATTERN_A2;
+    const bool a2 = (S->o.pattern_kind & ~kKindFlags) == SPAI_PATTERN_A2;
     const size_t nzP = a2 ? nz * mr : nz;
     size_t b = 3 * round256(n1 * 4) + 3 * round256(nz * 4) + round256(nzP * mr * 4);
     if (a2) b += 2 * round256(n1 * 4) + 3 * round256(nzP * 4);
@@ -169,7 +170,7 @@ size_t analysis_transient(const System &y) { return 16 * (size_t)y.nnz + 16 * ((
 
 size_t update_estimate(const spai_server_s *S, const System &y)
 {
-    const bool a2 = (S->o.pattern_kind & ~kPrecBits) == SPAI_PATTERN_A2;
+    const bool a2 = (S->o.pattern_kind & ~kKindFlags) == SPAI_PATTERN_A2;
     const int32_t prec = S->o.pattern_kind & kPrecBits;
     const size_t nzP = a2 ? (size_t)y.nnz * (size_t)(y.max_row > 0 ? y.max_row : 1) : (size_t)y.nnz;
     const size_t vb = prec == SPAI_PREC_BF16 ? 2 : prec == SPAI_PREC_FP32 ? 4 : 8;
@@ -369,7 +370,7 @@ int run(spai_server_s *S, int k, const Job &job, spai_pc *built, std::string *ms
         pc = own;
         *built = own;  // the caller caches or destroys it, whatever happens to the solve
     } else if (job.route == SPAI_ROUTE_UPDATE) {
-        st = spai_update(ctx, job.e->pc, &A, SPAI_UPDATE_FIRST | prec, &own);
+        st = spai_update(ctx, job.e->pc, &A, SPAI_UPDATE_FIRST | prec | (S->o.pattern_kind & SPAI_LS_NORMAL), &own);
         if (st) {
             *msg = spai_last_error(ctx);
             if (own) spai_pc_destroy(own);
@@ -469,10 +470,10 @@ extern "C" spai_status spai_server_create(const spai_server_opts *opts, spai_ser
 {
     if (!opts || !out) return SPAI_EINVAL;
     *out = nullptr;
-    const int32_t kind = opts->pattern_kind & ~kPrecBits;
+    const int32_t kind = opts->pattern_kind & ~kKindFlags;
     if (opts->slots < 1 || opts->slots > 64 || opts->restart < 1 || opts->max_cycles < 1 || !(opts->tol >= 0.0) ||
         !(opts->radius >= 0.0) || (kind != SPAI_PATTERN_A && kind != SPAI_PATTERN_A2) ||
-        (opts->pattern_kind & ~(kPrecBits | 1)) || (opts->pattern_kind & kPrecBits) == kPrecBits ||
+        (opts->pattern_kind & ~(kKindFlags | 1)) || (opts->pattern_kind & kPrecBits) == kPrecBits ||
         opts->orth < SPAI_ORTH_AUTO || opts->orth > SPAI_ORTH_TENSOR ||
         (opts->precision != SPAI_SOLVE_FP64 && opts->precision != SPAI_SOLVE_MIXED) || opts->reserved != 0)
         return SPAI_EINVAL;

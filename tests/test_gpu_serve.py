@@ -122,14 +122,18 @@ def test_plain_mode_builds_every_request_and_fp32_factors_converge():
     # FIFO on one slot: requests start in arrival order
     starts = [r["t_start"] for r in res]
     assert starts == sorted(starts)
-    res32, Xs32, _ = _serve(sg, systems, trace, slots=2, reuse=True, pattern_kind=sg.PREC_FP32)
-    for (sy, p, s, nrhs), r, X, X64 in zip(trace, res32, Xs32, Xs):
-        assert r["status"] == 0 and r["max_rel_residual"] <= TOL
-        w = systems[sy]
-        A = oracle.assemble(w.terms, oracle.coefficients(p, s), w.n)
-        rel = np.linalg.norm(w.B[:, :nrhs] - oracle.spmm(A, X, w.n), axis=0) / np.linalg.norm(w.B[:, :nrhs], axis=0)
-        assert np.all(rel <= TOL)
-        assert np.linalg.norm(X - X64) <= 1e-6 * np.linalg.norm(X64)
+    # FP32 factors, by QR and by the normal equations (SPAI_LS_NORMAL), each with the
+    # mixed-precision solve too: every solution meets tol and the FP64 solution's bar
+    for kind, prec in ((sg.PREC_FP32, sg.SOLVE_FP64), (sg.PREC_FP32 | sg.LS_NORMAL, sg.SOLVE_FP64),
+                       (sg.PREC_FP32 | sg.LS_NORMAL, sg.SOLVE_MIXED)):
+        res32, Xs32, _ = _serve(sg, systems, trace, slots=2, reuse=True, pattern_kind=kind, precision=prec)
+        for (sy, p, s, nrhs), r, X, X64 in zip(trace, res32, Xs32, Xs):
+            assert r["status"] == 0 and r["max_rel_residual"] <= TOL
+            w = systems[sy]
+            A = oracle.assemble(w.terms, oracle.coefficients(p, s), w.n)
+            rel = np.linalg.norm(w.B[:, :nrhs] - oracle.spmm(A, X, w.n), axis=0) / np.linalg.norm(w.B[:, :nrhs], axis=0)
+            assert np.all(rel <= TOL)
+            assert np.linalg.norm(X - X64) <= 1e-6 * np.linalg.norm(X64)
 
 
 def test_memory_budget_evicts_and_refuses():
