@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(kThreads) k_cqr_apply(int32_t n, const double 
     row_store<S>(Q, r, x);
     if (Q32) {
 #pragma unroll
-        for (int a = 0; a < S; ++a) Q32[r * S + a] = (float)x[a];
+        for (int a = 0; a < S; ++a) Q32[r * S + a] = f64_to_f32(x[a]);
     }
 }
 

@@ -466,8 +466,8 @@ __global__ void __launch_bounds__(256) k_cqr_apply_fixed(int32_t n, const double
             row_store<kS>(Q, r, x);
             if (Q32) {  // the block in FP32: the input of the mixed solve's FP32 operator
                 float4 *q = reinterpret_cast<float4 *>(Q32 + r * kS);
-                q[0] = make_float4((float)x[0], (float)x[1], (float)x[2], (float)x[3]);
-                q[1] = make_float4((float)x[4], (float)x[5], (float)x[6], (float)x[7]);
+                q[0] = make_float4(f64_to_f32(x[0]), f64_to_f32(x[1]), f64_to_f32(x[2]), f64_to_f32(x[3]));
+                q[1] = make_float4(f64_to_f32(x[4]), f64_to_f32(x[5]), f64_to_f32(x[6]), f64_to_f32(x[7]));
             }
 #pragma unroll
             for (int a = 0; a < kS; ++a)

@@ -607,7 +607,7 @@ __global__ void k_scale_rows_seg(const int64_t *__restrict__ r0s, const int64_t 
 // value and X loads issued together before the multiply-adds.
 // ---------------------------------------------------------------------------------
 __device__ __forceinline__ float as_f32(float v) { return v; }
-__device__ __forceinline__ float as_f32(double v) { return (float)v; }
+__device__ __forceinline__ float as_f32(double v) { return f64_to_f32(v); }
 __device__ __forceinline__ float as_f32(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
 
 template <int C>
@@ -631,11 +631,11 @@ __device__ __forceinline__ void load_x(const double *p, float (&x)[C])
 #pragma unroll
         for (int h = 0; h < C / 2; ++h) {
             const double2 v = __ldg(reinterpret_cast<const double2 *>(p) + h);
-            x[2 * h] = (float)v.x;
-            x[2 * h + 1] = (float)v.y;
+            x[2 * h] = f64_to_f32(v.x);
+            x[2 * h + 1] = f64_to_f32(v.y);
         }
     } else {
-        x[0] = (float)__ldg(p);
+        x[0] = f64_to_f32(__ldg(p));
     }
 }
 
@@ -657,9 +657,9 @@ __device__ __forceinline__ void store_y(double *p, const float (&y)[C])
     if constexpr (C >= 2) {
 #pragma unroll
         for (int h = 0; h < C / 2; ++h)
-            reinterpret_cast<double2 *>(p)[h] = make_double2((double)y[2 * h], (double)y[2 * h + 1]);
+            reinterpret_cast<double2 *>(p)[h] = make_double2(f32_to_f64(y[2 * h]), f32_to_f64(y[2 * h + 1]));
     } else {
-        p[0] = (double)y[0];
+        p[0] = f32_to_f64(y[0]);
     }
 }
 
@@ -710,13 +710,15 @@ __global__ void k_scale_rows32(int32_t n, const V *__restrict__ q, const XT *__r
 {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= (int64_t)n * S) return;
-    Y[g] = (YT)(as_f32(__ldg(q + g / S)) * as_f32(X[g]));
+    const float y = as_f32(__ldg(q + g / S)) * as_f32(X[g]);
+    if constexpr (sizeof(YT) == 8) Y[g] = f32_to_f64(y);
+    else Y[g] = y;
 }
 
 __global__ void k_round_f32(int64_t count, const double *__restrict__ src, float *__restrict__ dst)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = (float)src[i];
+        dst[i] = f64_to_f32(src[i]);
 }
 
 template <int S, typename V>

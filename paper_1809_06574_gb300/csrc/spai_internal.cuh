@@ -220,6 +220,41 @@ int launch_spai_columns_batch(cudaStream_t st, const ColumnBatch &bt, bool low_p
 
 // ---------------------------------------------------------------------- shared device code
 #ifdef __CUDACC__
+// Conversions between FP32 and FP64 written from the IEEE 754 binary32 / binary64 layouts
+// with integer operations: GB300 runs the conversion instructions on its FP64 pipe, whose
+// throughput is a small fraction of the integer pipes', and the mixed-precision operator
+// converts every entry it reads or writes.  Numbers whose result is normal take the integer
+// path; zeros, subnormals, infinities and NaN (rare here) take the conversion instruction.
+//
+// binary32 -> binary64 (exact): the sign moves from bit 31 to bit 63, the biased exponent
+// gains 1023 - 127 = 896, the 23 fraction bits gain 29 low zero bits.
+__device__ __forceinline__ double f32_to_f64(float x)
+{
+    const uint32_t u = __float_as_uint(x), e = (u >> 23) & 0xFFu;
+    if (e - 1u < 254u)  // normal
+        return __hiloint2double((int)((u & 0x80000000u) | (((u >> 3) & 0x0FFFFFFFu) + (896u << 20))),
+                                (int)(u << 29));
+    if ((u << 1) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);  // +-0
+    return (double)x;
+}
+
+// binary64 -> binary32, rounded to nearest, ties to even: the biased exponent loses 896 and
+// the fraction its 29 low bits, rounded up when they exceed half a unit of the last kept
+// place or equal it with an odd last kept bit (a carry out of the fraction moves to the next
+// binade, and past the largest finite value to infinity, as the rounding rule asks).
+__device__ __forceinline__ float f64_to_f32(double x)
+{
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t e = (hi >> 20) & 0x7FFu;
+    if (e - 897u < 254u) {  // the result's biased exponent e - 896 is in 1 .. 254: normal
+        uint32_t f = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+        const uint32_t rem = lo & 0x1FFFFFFFu;
+        f += (rem > 0x10000000u || (rem == 0x10000000u && (f & 1u))) ? 1u : 0u;
+        return __uint_as_float(f);
+    }
+    return (float)x;
+}
+
 // x := x R^{-1} for one row (R upper triangular S x S, row-major; rinv[b] = 1 / R_bb, or 0
 // for a deflated column).  Every row-wise triangular solve of the block orthogonalisation
 // uses this one sequence, so a row solved in different kernels gets the same bits.

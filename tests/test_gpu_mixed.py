@@ -254,6 +254,38 @@ def test_spmm_fp32_within_its_rounding_bound(case, s):
     assert np.max(err / np.maximum(mag, 1e-300)) > 1e-10
 
 
+def test_fp32_operator_conversions_are_ieee_exact():
+    """The FP32 operator converts its FP64 input to FP32 and its FP32 result to FP64 with
+    integer operations on the IEEE 754 layouts: with A = I (one product by 1.0 per row) Y is
+    X rounded to FP32 and widened back (plus +0, the sum's start), which must equal numpy's
+    IEEE conversions bit for bit -- ties to even, the overflow threshold, the subnormal range
+    and zeros included."""
+    import torch
+    sg = _sg()
+    f32 = np.float32
+    tiny, big = float(np.finfo(f32).tiny), float(np.finfo(f32).max)
+    ulp1 = 2.0 ** -23
+    special = [0.0, -0.0, 1.0, -1.0, 1.0 + ulp1 / 2, 1.0 + 1.5 * ulp1, -(1.0 + ulp1 / 2), 3.0 + 2 * ulp1,
+               1.0 + ulp1 / 2 + 2.0 ** -40, 1.0 + ulp1 / 2 - 2.0 ** -40, tiny, tiny / 2, tiny / 3, -tiny * 0.75,
+               1e-42, 1e-46, big, -big, big * (1 + 2.0 ** -25), big * (1 + 2.0 ** -23), 1e39, -1e300,
+               float(np.nextafter(f32(1.0), f32(2.0))), 0.1, -0.1, 2.0 ** -126, 2.0 ** 127, 7e-39]
+    rng = np.random.default_rng(17)
+    body = np.concatenate([rng.standard_normal(3000) * 10.0 ** rng.integers(-40, 40, 3000),
+                           (rng.integers(1, 2 ** 24, 2000) + 0.5) * 2.0 ** rng.integers(-60, 60, 2000)])
+    x = np.concatenate([np.array(special), body])
+    n = len(x)
+    A = (np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.ones(n))
+    with np.errstate(over="ignore"):
+        want = x.astype(f32).astype(np.float64) + 0.0  # the row sum starts from +0: -0 + +0 = +0
+    with context() as ctx:
+        Xd = torch.as_tensor(x.reshape(1, n).copy(), device="cuda:0")
+        Yd = torch.zeros((1, n), dtype=torch.float64, device="cuda:0")
+        sg.spai_spmm_fp32(ctx, dev_csr(A, n), 1, Xd, n, Yd, n)
+        sg.spai_ctx_sync(ctx)
+        got = Yd.cpu().numpy()[0]
+    assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "fp64"])
 def test_pc_apply_fp32_chain_within_its_rounding_bound(prec):
     """The FP32 apply of a factored update Q_2 (P_1 X) (values as stored, X and the FP32
