@@ -58,6 +58,8 @@ constexpr int kSegK = 512;         // rows (Gram) / basis columns (update) per a
 constexpr int kMaxRows = 4096;     // rows per Gram CTA: hi, lo stay below 2^53
 constexpr int kCW = 8;             // converter warps
 constexpr int kCT = 32 * kCW;      // converter threads
+constexpr int kCG = 2;             // Gram kernel: converter groups taking alternate stages
+constexpr int kCTG = kCT / kCG;    // threads of one converter group
 constexpr int kThreadsTC = 64 + 128 + kCT;  // copy warp, MMA warp, 4 drain warps, converters
 constexpr int kRawRow = kS * 8;    // 64 bytes: one row of an n x 8 block
 constexpr unsigned long long kWaitNs = 1000000000ull;  // drain waits give up after 1 s
@@ -253,6 +255,29 @@ __device__ __forceinline__ void drain_classes(uint32_t tbuf, long long hi[kS], l
         for (int c = 0; c < 16; ++c) {
             const int col = 48 + 16 * k + c, cls = col >> 3, b = col & 7;
             if (cls > 8) continue;  // class 9: padding products only
+            const long long d = (long long)__float2int_rz(__uint_as_float(v[k][c]));
+            if (cls <= 4) hi[b] += d << (7 * (4 - cls));
+            else lo[b] += d << (7 * (8 - cls));
+        }
+}
+
+// The same sums for one V digit p when the digit planes are stacked in M (the Gram kernel
+// with at most two blocks, one MMA per sub-tile): this thread's tensor-memory row is (p,
+// block, column) and its 64 columns are (W digit q, output column b); the products of
+// class c = p + q <= 8 are added with the weights of drain_classes, higher classes dropped.
+// Every cell sums at most 512 products of at most 64^2: exact FP32 integers.
+__device__ __forceinline__ void drain_stacked(uint32_t tbuf, int p, long long hi[kS], long long lo[kS])
+{
+    uint32_t v[4][16];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) tmem_ld16(tbuf + 16 * k, v[k]);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const int col = 16 * k + c, q = col >> 3, b = col & 7, cls = p + q;
+            if (cls > 8) continue;
             const long long d = (long long)__float2int_rz(__uint_as_float(v[k][c]));
             if (cls <= 4) hi[b] += d << (7 * (4 - cls));
             else lo[b] += d << (7 * (8 - cls));
@@ -531,10 +556,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     if (tid == 0) {
         for (int s = 0; s < R; ++s) {
             mbar_init(rfull0 + 8 * s, 1);
-            mbar_init(rempty0 + 8 * s, kCW);
+            mbar_init(rempty0 + 8 * s, kCW / kCG);
         }
         for (int s = 0; s < kDDigStages; ++s) {
-            mbar_init(dfull0 + 8 * s, kCW);
+            mbar_init(dfull0 + 8 * s, kCW / kCG);
             mbar_init(dempty0 + 8 * s, 1);
         }
         for (int b = 0; b < kBufs; ++b) {
@@ -559,6 +584,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
     const bool work = nvb > 0 && nsub > 0;
+    // at most two blocks: the eight V digit planes stacked in M (rows (p, block, column),
+    // 64 nvb of the MMA's 128) against the eight W digit planes in N, one MMA per sub-tile;
+    // classes are formed when the sums are drained
+    const bool stacked = nvb <= 2;
 
     if (warp == 0) {
         if (lane == 0 && work) {  // ---- copies of stage k into raw stage k % R
@@ -610,6 +639,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 for (int sg = 0; sg < ns; ++sg) {
                     const char *sb = st + sg * sub_bytes;
                     const uint64_t db = make_desc(smem_u32(sb + kDig * plane));
+                    if (stacked) {
+                        mma_bf16(tmem + buf * kBufCols, make_desc(smem_u32(sb)), db, make_idesc(kM, 8 * kDig),
+                                 (first && sg == 0) ? 0u : 1u);
+                        continue;
+                    }
 #pragma unroll
                     for (int p = 0; p < kDig; ++p) {
                         const uint64_t da = make_desc(smem_u32(sb + p * plane));
@@ -630,6 +664,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     } else if (warp < 6) {  // ---- drain warps: tensor-memory lanes 32 (warp % 4) .. + 31 = basis columns
         if (work) {
             const int quarter = warp & 3;
+            const int m = quarter * 32 + lane;
+            const int pd = m / (8 * nvb);  // stacked: this row's V digit
             long long hi[kS], lo[kS];
 #pragma unroll
             for (int b = 0; b < kS; ++b) hi[b] = lo[b] = 0;
@@ -642,13 +678,38 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                drain_classes(tmem + ((uint32_t)(quarter * 32) << 16) + buf * kBufCols, hi, lo);
+                const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + buf * kBufCols;
+                if (stacked) drain_stacked(tb, pd < kDig ? pd : kDig, hi, lo);  // rows past 64 nvb: unused
+                else drain_classes(tb, hi, lo);
                 asm volatile("tcgen05.fence::before_thread_sync;");
                 mbar_arrive(bfree0 + 8 * buf);
             }
             // the chunk's W scale is known once the converters have started (named barrier 1)
             asm volatile("bar.sync 2, %0;" ::"r"(128 + kCT) : "memory");
-            const int m = quarter * 32 + lane;
+            if (stacked) {
+                // sum the eight digit rows of every (block, column): through the raw ring, idle
+                // once the last accumulator is drained (all copies landed, all converted)
+                long long *stg = reinterpret_cast<long long *>(smem);
+                if (ok && m < 64 * nvb)
+#pragma unroll
+                    for (int b = 0; b < kS; ++b) {
+                        stg[(2 * m) * kS + b] = hi[b];
+                        stg[(2 * m + 1) * kS + b] = lo[b];
+                    }
+                asm volatile("bar.sync 3, 128;" ::: "memory");
+                if (ok && m < 8 * nvb) {
+#pragma unroll
+                    for (int b = 0; b < kS; ++b) {
+                        long long h = 0, l = 0;
+                        for (int p = 0; p < kDig; ++p) {
+                            h += stg[(2 * (p * 8 * nvb + m)) * kS + b];
+                            l += stg[(2 * (p * 8 * nvb + m) + 1) * kS + b];
+                        }
+                        hi[b] = h;
+                        lo[b] = l;
+                    }
+                }
+            }
             if (ok && m < nvb * kS) {
                 const int gm = blk0 * kS + m;
                 double *dst = partial + ((int64_t)chunk * nblk + (gm >> 3)) * (kS * kS) + (gm & 7) * kS;
@@ -700,8 +761,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         const int gps = 16 * (nvb + 1);  // digit groups per sub-tile: (block slot, 8-row half, column)
         // g / gps as ((g >> 4) * inv) >> 16: exact while g >> 4 < 2^16 / (nvb + 1)^2 (here < 204)
         const uint32_t inv = (65536u + (uint32_t)nvb) / (uint32_t)(nvb + 1);
+        // two groups of four warps take alternate stages, so that two stages are converted at
+        // once (a stage's conversion is a chain of dependent shared-memory steps)
+        const int cg = cw / (kCW / kCG), ctg = ct % kCTG;
         bool bad = false;
-        for (int k = 0; k < nst; ++k) {
+        for (int k = cg; k < nst; k += kCG) {
             const int s = k % R, d = k % kDDigStages;
             bool ok = warp_wait(rfull0 + 8 * s, (uint32_t)((k / R) & 1), wl);
             if (ok && k >= kDDigStages)
@@ -713,8 +777,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             const int ns = min(S, nsub - k * S);
             const char *raw = smem + s * rsb;
             char *dig = smem + dig_off + d * dsb;
-            const int rot = (k * 32) & (kCT - 1);  // spreads the extra groups over the warps
-            for (int g = (ct - rot) & (kCT - 1); g < ns * gps; g += kCT) {
+            const int rot = ((k / kCG) * 32) & (kCTG - 1);  // spreads the extra groups over the warps
+            for (int g = (ctg - rot) & (kCTG - 1); g < ns * gps; g += kCTG) {
                 const int sg = (int)(((uint32_t)(g >> 4) * inv) >> 16), r = g - sg * gps;
                 const int i = r >> 4, ko = (r >> 3) & 1, a = r & 7;
                 const int64_t t = t0 + (int64_t)k * S + sg;

@@ -35,8 +35,10 @@ def _ref(Q, W):
     return (Q.astype(np.longdouble).T @ W.astype(np.longdouble)).astype(np.float64)
 
 
-@pytest.mark.parametrize("n,nblk", [(1000, 1), (4999, 4), (20000, 17), (70001, 51)])
+@pytest.mark.parametrize("n,nblk", [(1000, 1), (30000, 2), (4999, 4), (20000, 17), (12345, 18), (70001, 51)])
 def test_tensor_gram_as_accurate_as_fp64(n, nblk):
+    """Tiles of one or two blocks (nblk 1, 2 and the last tile of 17 or 18) take the
+    stacked-digit MMA, the others one MMA per digit; both are exact digit sums."""
     import torch
     import paper_1809_06574_gb300 as sg
     Q, W = _blocks(n, nblk, seed=n + nblk)
