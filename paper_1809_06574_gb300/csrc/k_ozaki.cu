@@ -147,6 +147,20 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t 
 }
 
 
+// The same MMA (and the commit below) issued by one lane of a converged warp: the whole warp
+// runs the issuing loop, so the descriptors and addresses it computes are warp-uniform, and
+// an elect.sync predicate lets exactly one lane issue.
+__device__ __forceinline__ void mma_bf16_warp(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                              uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p, e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+}
+
 __host__ __device__ constexpr uint32_t make_idesc_amn(int M, int N) { return make_idesc(M, N) | (1u << 15); }
 
 // MN-major descriptor of the update kernel's A operand (basis rows): next 8 basis columns
@@ -218,6 +232,15 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
+}
+
+__device__ __forceinline__ void mma_commit_warp(uint32_t bar)
+{
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}\n" ::"r"(bar)
+        : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t v[16])
@@ -617,20 +640,18 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 if (!mbar_wait_bounded(rfull0 + 8 * (k % R), (uint32_t)((k / R) & 1))) *flag = 1;
         }
     } else if (warp == 1) {
-        if (lane == 0 && work) {  // ---- MMA issuer
+        if (work) {  // ---- MMA issuer: the whole warp runs the loop, one elected lane issues
             // test of the give-up path: a bounded wait on a barrier that nothing completes
-            if (stall && !mbar_wait_bounded(never, 0, wl)) *flag = 1;
+            if (stall && !warp_wait(never, 0, wl) && lane == 0) *flag = 1;
             int done = 0;
             for (int k = 0; k < nst; ++k) {
                 const int d = k % kDDigStages, seg = k / sps, buf = seg % kBufs;
                 const bool first = k % sps == 0;
-                if (first && seg >= kBufs &&
-                    !mbar_wait_bounded(bfree0 + 8 * buf, (uint32_t)((seg / kBufs - 1) & 1), wl)) {
-                    *flag = 1;
-                    break;
-                }
-                if (!mbar_wait_bounded(dfull0 + 8 * d, (uint32_t)((k / kDDigStages) & 1), wl) || *flag) {
-                    *flag = 1;
+                bool ok = !(first && seg >= kBufs) ||
+                          warp_wait(bfree0 + 8 * buf, (uint32_t)((seg / kBufs - 1) & 1), wl);
+                if (ok) ok = warp_wait(dfull0 + 8 * d, (uint32_t)((k / kDDigStages) & 1), wl);
+                if (!ok || __any_sync(0xffffffffu, *flag != 0)) {
+                    if (lane == 0) *flag = 1;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
@@ -640,25 +661,27 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     const char *sb = st + sg * sub_bytes;
                     const uint64_t db = make_desc(smem_u32(sb + kDig * plane));
                     if (stacked) {
-                        mma_bf16(tmem + buf * kBufCols, make_desc(smem_u32(sb)), db, make_idesc(kM, 8 * kDig),
-                                 (first && sg == 0) ? 0u : 1u);
+                        mma_bf16_warp(tmem + buf * kBufCols, make_desc(smem_u32(sb)), db, make_idesc(kM, 8 * kDig),
+                                      (first && sg == 0) ? 0u : 1u);
                         continue;
                     }
 #pragma unroll
                     for (int p = 0; p < kDig; ++p) {
                         const uint64_t da = make_desc(smem_u32(sb + p * plane));
-                        mma_bf16(tmem + buf * kBufCols + 8 * p, da, db, make_idesc(kM, nmma(p)),
-                                 (first && sg == 0 && p == 0) ? 0u : 1u);
+                        mma_bf16_warp(tmem + buf * kBufCols + 8 * p, da, db, make_idesc(kM, nmma(p)),
+                                      (first && sg == 0 && p == 0) ? 0u : 1u);
                     }
                 }
-                mma_commit(dempty0 + 8 * d);
-                if (k % sps == sps - 1 || k == nst - 1) mma_commit(bfull0 + 8 * buf);
+                mma_commit_warp(dempty0 + 8 * d);
+                if (k % sps == sps - 1 || k == nst - 1) mma_commit_warp(bfull0 + 8 * buf);
                 done = k + 1;
             }
             // the last commit: all MMAs done before shared memory is released
             if (done > 0) {
                 const int k = done - 1;
-                if (!mbar_wait_bounded(dempty0 + 8 * (k % kDDigStages), (uint32_t)((k / kDDigStages) & 1))) *flag = 1;
+                if (!warp_wait(dempty0 + 8 * (k % kDDigStages), (uint32_t)((k / kDDigStages) & 1), kWaitNs) &&
+                    lane == 0)
+                    *flag = 1;
             }
         }
     } else if (warp < 6) {  // ---- drain warps: tensor-memory lanes 32 (warp % 4) .. + 31 = basis columns
