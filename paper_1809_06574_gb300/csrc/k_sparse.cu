@@ -603,7 +603,7 @@ __global__ void k_scale_rows_seg(const int64_t *__restrict__ r0s, const int64_t 
 // values (FP32, BF16 bits, or FP64 rounded once) and the X entries (FP64 rounded once, or
 // FP32) are multiplied and summed in FP32 in the row's order; Y is written as FP32 or as
 // FP64 (exact conversion).  T = S / C lanes per row, each owning C = min(S, 4) consecutive
-// columns (vector loads of X and Y); the nonzeros are taken four at a time, their index,
+// columns (vector loads of X and Y); the nonzeros are taken eight at a time, their index,
 // value and X loads issued together before the multiply-adds.
 // ---------------------------------------------------------------------------------
 __device__ __forceinline__ float as_f32(float v) { return v; }
@@ -668,40 +668,39 @@ __global__ void __launch_bounds__(kThreads) k_spmm32(int32_t n, const int32_t *_
                                                      const int32_t *__restrict__ colind, const V *__restrict__ val,
                                                      const XT *__restrict__ X, YT *__restrict__ Y)
 {
-    constexpr int C = S < 4 ? S : 4, T = S / C;
-    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t row = g / T;
-    if (row >= n) return;
-    const int part = (int)(g % T);
-    const int32_t a = __ldg(rowptr + row), b = __ldg(rowptr + row + 1);
-    const XT *xb = X + part * C;
-    float acc[C];
+    constexpr int C = S < 4 ? S : 4, T = S / C, U = 8;
+    const int64_t lanes = (int64_t)n * T;
+    // one wave of blocks walks all (row, part) lanes; a lane's nonzeros go eight at a time,
+    // every index, value and X load of the eight issued before the multiply-adds (a row of
+    // a 7- or 27-point stencil takes one or four such rounds); the sums stay in row order
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < lanes; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = g / T;
+        const int part = (int)(g % T);
+        const int32_t a = __ldg(rowptr + row), b = __ldg(rowptr + row + 1);
+        const XT *xb = X + part * C;
+        float acc[C];
 #pragma unroll
-    for (int k = 0; k < C; ++k) acc[k] = 0.0f;
-    int32_t q = a;
-    for (; q + 4 <= b; q += 4) {
-        int32_t c[4];
-        float v[4], x[4][C];
+        for (int k = 0; k < C; ++k) acc[k] = 0.0f;
+        for (int32_t q = a; q < b; q += U) {
+            int32_t c[U];
+            float v[U], x[U][C];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            c[u] = __ldg(colind + q + u);
-            v[u] = as_f32(__ldg(val + q + u));
+            for (int u = 0; u < U; ++u) {
+                const bool in = q + u < b;
+                c[u] = in ? __ldg(colind + q + u) : -1;
+                v[u] = in ? as_f32(__ldg(val + q + u)) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (c[u] >= 0) load_x<C>(xb + (int64_t)c[u] * S, x[u]);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (c[u] >= 0)
+#pragma unroll
+                    for (int k = 0; k < C; ++k) acc[k] = fmaf(v[u], x[u][k], acc[k]);
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) load_x<C>(xb + (int64_t)c[u] * S, x[u]);
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int k = 0; k < C; ++k) acc[k] = fmaf(v[u], x[u][k], acc[k]);
+        store_y<C>(Y + row * S + part * C, acc);
     }
-    for (; q < b; ++q) {
-        float x[C];
-        const float v = as_f32(__ldg(val + q));
-        load_x<C>(xb + (int64_t)__ldg(colind + q) * S, x);
-#pragma unroll
-        for (int k = 0; k < C; ++k) acc[k] = fmaf(v, x[k], acc[k]);
-    }
-    store_y<C>(Y + row * S + part * C, acc);
 }
 
 // Y[r][c] = q[r] X[r][c] in FP32 (a diagonal factor of the FP32 operator)
@@ -1070,7 +1069,23 @@ int spmm32_any(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr, con
 {
     if (n <= 0) return 0;
     const int T = s < 4 ? 1 : s / 4;
-    const int g = grid_for((int64_t)n * T);
+    // one wave: every SM's resident blocks, fewer for small n
+    int dev = 0, sms = 152, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return -1;
+    cudaError_t oe = cudaErrorInvalidValue;
+    switch (s) {
+    case 1: oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm32<1, V, XT, YT>, kThreads, 0); break;
+    case 2: oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm32<2, V, XT, YT>, kThreads, 0); break;
+    case 4: oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm32<4, V, XT, YT>, kThreads, 0); break;
+    case 8: oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm32<8, V, XT, YT>, kThreads, 0); break;
+    case 16: oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm32<16, V, XT, YT>, kThreads, 0); break;
+    default: return -1;
+    }
+    if (oe != cudaSuccess) return -1;
+    const int64_t want = ((int64_t)n * T + kThreads - 1) / kThreads, wave = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    const int g = (int)(want < wave ? want : wave);
     switch (s) {
     case 1: k_spmm32<1, V, XT, YT><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, Y); break;
     case 2: k_spmm32<2, V, XT, YT><<<g, kThreads, 0, st>>>(n, rowptr, colind, val, X, Y); break;
