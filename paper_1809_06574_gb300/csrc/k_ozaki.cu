@@ -781,9 +781,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             asm volatile("bar.sync 1, %0;" ::"r"(kCT) : "memory");
             asm volatile("bar.arrive 2, %0;" ::"r"(128 + kCT) : "memory");  // exps ready for the drain warps
         }
-        const int gps = 16 * (nvb + 1);  // digit groups per sub-tile: (block slot, 8-row half, column)
-        // g / gps as ((g >> 4) * inv) >> 16: exact while g >> 4 < 2^16 / (nvb + 1)^2 (here < 204)
-        const uint32_t inv = (65536u + (uint32_t)nvb) / (uint32_t)(nvb + 1);
         // two groups of four warps take alternate stages, so that two stages are converted at
         // once (a stage's conversion is a chain of dependent shared-memory steps)
         const int cg = cw / (kCW / kCG), ctg = ct % kCTG;
@@ -800,30 +797,44 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             const int ns = min(S, nsub - k * S);
             const char *raw = smem + s * rsb;
             char *dig = smem + dig_off + d * dsb;
-            const int rot = ((k / kCG) * 32) & (kCTG - 1);  // spreads the extra groups over the warps
-            for (int g = (ctg - rot) & (kCTG - 1); g < ns * gps; g += kCTG) {
-                const int sg = (int)(((uint32_t)(g >> 4) * inv) >> 16), r = g - sg * gps;
-                const int i = r >> 4, ko = (r >> 3) & 1, a = r & 7;
-                const int64_t t = t0 + (int64_t)k * S + sg;
-                const int rv = (int)min((int64_t)kKT, (int64_t)n - t * kKT);
-                char *db = dig + sg * sub_bytes;
+            // W groups (FP64 -> digits, about four times a V group's work) on threads 0, 1, ...;
+            // V groups first to the threads without a W group, four each, then to all in turn,
+            // so that the stage's slowest warp carries about the mean work
+            const int nwg = 16 * ns, nvg = 16 * nvb * ns;
+            // the roles rotate by a warp from stage to stage: a warp does not wait for the
+            // others between its stages, so each carries the mean over stages
+            const int cr = (ctg + (k / kCG) * 32) & (kCTG - 1);
+            for (int w = cr; w < nwg; w += kCTG) {
+                const int sg = w >> 4, ko = (w >> 3) & 1, a = w & 7;
+                const int64_t tt = t0 + (int64_t)k * S + sg;
+                const int rv = (int)min((int64_t)kKT, (int64_t)n - tt * kKT);
+                const double *src =
+                    reinterpret_cast<const double *>(raw + (S * nvb + sg) * (kKT * kRawRow)) + ko * 8 * kS + a;
+                const int e = wexp[a];
                 uint64_t f[8];
-                if (i == nvb) {  // W: FP64 -> fixed point with this chunk's column scale
-                    const double *src =
-                        reinterpret_cast<const double *>(raw + (S * nvb + sg) * (kKT * kRawRow)) + ko * 8 * kS + a;
-                    const int e = wexp[a];
 #pragma unroll
-                    for (int v = 0; v < 8; ++v)
-                        if (!to_bdigits((ko * 8 + v < rv) ? src[v * kS] : 0.0, e, f[v])) bad = true;
-                    bexpand8(f, db + kDig * plane + ko * kLBO + a * 16, kPiece);
-                } else {  // rows past n are zero in the sub-tile layout
-                    const uint64_t *src =
-                        reinterpret_cast<const uint64_t *>(raw + (sg * nvb + i) * (kKT * kRawRow)) + ko * 8 * kS + a;
-#pragma unroll
-                    for (int v = 0; v < 8; ++v) f[v] = src[v * kS];
-                    bexpand8(f, db + i * kPiece + ko * kLBO + a * 16, plane);
-                }
+                for (int v = 0; v < 8; ++v)
+                    if (!to_bdigits((ko * 8 + v < rv) ? src[v * kS] : 0.0, e, f[v])) bad = true;
+                bexpand8(f, dig + sg * sub_bytes + kDig * plane + ko * kLBO + a * 16, kPiece);
             }
+            auto v_group = [&](int j) {  // V group j of the stage: (sub-tile, block, 8-row half, column)
+                const int sg = j / (16 * nvb), r = j - sg * 16 * nvb;
+                const int i = r >> 4, ko = (r >> 3) & 1, a = r & 7;
+                const uint64_t *src =
+                    reinterpret_cast<const uint64_t *>(raw + (sg * nvb + i) * (kKT * kRawRow)) + ko * 8 * kS + a;
+                uint64_t f[8];
+#pragma unroll
+                for (int v = 0; v < 8; ++v) f[v] = src[v * kS];  // rows past n are zero in the sub-tile layout
+                bexpand8(f, dig + sg * sub_bytes + i * kPiece + ko * kLBO + a * 16, plane);
+            };
+            // (a warp pays for every path its lanes take, so the first deal goes to whole warps
+            // without a W group)
+            const int ww = (nwg + 31) & ~31;             // threads of the warps with W groups
+            const int tf = ww < kCTG ? kCTG - ww : 0;    // threads of the other warps
+            const int first = min(4 * tf, nvg);          // V groups dealt to those threads alone
+            if (cr >= ww)
+                for (int j = cr - ww; j < first; j += tf) v_group(j);
+            for (int j = first + cr; j < nvg; j += kCTG) v_group(j);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) {
