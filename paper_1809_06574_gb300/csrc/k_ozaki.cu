@@ -1066,6 +1066,18 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             long long hi[kS], lo[kS];
 #pragma unroll
             for (int b = 0; b < kS; ++b) hi[b] = lo[b] = 0;
+            // this row of the base, loaded before the tile's sums are waited for
+            const int64_t r = tile * 128 + quarter * 32 + lane;
+            double bv[kS];
+#pragma unroll
+            for (int b = 0; b < kS; ++b) bv[b] = 0.0;
+            if (base && r < n)
+#pragma unroll
+                for (int h = 0; h < kS / 2; ++h) {
+                    const double2 x = reinterpret_cast<const double2 *>(base + r * kS)[h];
+                    bv[2 * h] = x.x;
+                    bv[2 * h + 1] = x.y;
+                }
             for (int sgm = 0; sgm < nsegt; ++sgm, ++gs) {
                 const int buf = (int)(gs % kBufs);
                 if (!mbar_wait_bounded(bfull0 + 8 * buf, (uint32_t)((gs / kBufs) & 1), wl) || *flag) {
@@ -1078,12 +1090,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 asm volatile("tcgen05.fence::before_thread_sync;");
                 mbar_arrive(bfree0 + 8 * buf);
             }
-            const int64_t r = tile * 128 + quarter * 32 + lane;
             if (ok && r < n) {
 #pragma unroll
                 for (int b = 0; b < kS; ++b) {
                     const double vh = combine_hilo(hi[b], lo[b], hexp[b]);
-                    out[r * kS + b] = base ? fma(sign, vh, base[r * kS + b]) : sign * vh;
+                    out[r * kS + b] = base ? fma(sign, vh, bv[b]) : sign * vh;
                 }
             }
         }
