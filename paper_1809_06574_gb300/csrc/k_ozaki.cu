@@ -1093,7 +1093,15 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             if (ok && r < n) {
 #pragma unroll
                 for (int b = 0; b < kS; ++b) {
-                    const double vh = combine_hilo(hi[b], lo[b], hexp[b]);
+                    // hi 2^28 + lo in one exact 64-bit integer when hi is small (it is unless the
+                    // basis entries reach 2^-8): one conversion and one scaling instead of
+                    // combine_hilo's two and three, the same single rounding of the same exact sum
+                    double vh;
+                    const long long ah = hi[b] < 0 ? -hi[b] : hi[b];
+                    if (ah < (1ll << 34) && hexp[b] > -900)
+                        vh = (double)((hi[b] << 28) + lo[b]) * __longlong_as_double((long long)(1023 + hexp[b] - 66) << 52);
+                    else
+                        vh = combine_hilo(hi[b], lo[b], hexp[b]);
                     out[r * kS + b] = base ? fma(sign, vh, bv[b]) : sign * vh;
                 }
             }
