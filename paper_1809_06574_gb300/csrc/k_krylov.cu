@@ -275,7 +275,9 @@ __global__ void __launch_bounds__(kThreads) k_trsm_rows(int32_t n, const double 
 // Cholesky-QR kernels for S <= 8.  A block of 256 threads walks its row chunk (one tile
 // where n allows) in tiles of 256 rows: each thread loads one row with 16-byte loads (k_trsm_gram also solves it
 // against R and stores it as Q1) into a shared-memory tile; then thread (pair p = (a, b),
-// a <= b; row group g) adds x_a x_b over rows g, g + RG, ... of the tile.  The FP64
+// a <= b; row group g) adds x_a x_b over rows g, g + RG, ... of the tile, while the
+// thread's row of the next tile is already being loaded (the FP64 pipe, not the loads,
+// bounds these kernels on GB300, so it should not wait for them).  The FP64
 // reduction at the end is one sum over the RG groups per pair (FP64 adds are as dear as
 // FMAs on this GPU, so no per-thread butterflies).
 //   k_gram_rows:  partial[chunk] of G = W^T W
@@ -296,11 +298,11 @@ __device__ __forceinline__ void gram_tiles(int64_t r0, int64_t r1, const double 
     while (rem >= S - a) { rem -= S - a; ++a; }
     const int b = a + rem;
     double acc0 = 0.0, acc1 = 0.0;
+    double x[S];
+    if (r0 + threadIdx.x < r1) row_load<S>(W, r0 + threadIdx.x, x);
     for (int64_t t0 = r0; t0 < r1; t0 += kThreads) {
         const int rows = (int)((r1 - t0) < kThreads ? (r1 - t0) : kThreads);
         if (threadIdx.x < rows) {
-            double x[S];
-            row_load<S>(W, t0 + threadIdx.x, x);
             if constexpr (SOLVE) {
                 trsm_row<S>(x, Rs, rinv);
                 if constexpr (STORE) row_store<S>(Q1, t0 + threadIdx.x, x);
@@ -309,6 +311,8 @@ __device__ __forceinline__ void gram_tiles(int64_t r0, int64_t r1, const double 
             for (int k = 0; k < S; ++k) tile[threadIdx.x * LD + k] = x[k];
         }
         __syncthreads();
+        // the next tile's row is in flight while this tile's products run
+        if (t0 + kThreads + threadIdx.x < r1) row_load<S>(W, t0 + kThreads + threadIdx.x, x);
         if (g < RG) {
             int r = g;
             for (; r + RG < rows; r += 2 * RG) {
@@ -399,7 +403,15 @@ __device__ bool last_cta_sum(const double *partial, unsigned *ticket, double *ou
     const int e = threadIdx.x % NE, q = threadIdx.x / NE;
     const int c0 = (int)((int64_t)chunks * q / NG), c1 = (int)((int64_t)chunks * (q + 1) / NG);
     double acc = 0.0;
-    for (int c = c0; c < c1; ++c) acc += __ldcg(partial + (int64_t)c * NE + e);
+    int c = c0;
+    for (; c + 8 <= c1; c += 8) {  // eight loads in flight, added in chunk order
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldcg(partial + (int64_t)(c + u) * NE + e);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += v[u];
+    }
+    for (; c < c1; ++c) acc += __ldcg(partial + (int64_t)c * NE + e);
     red[threadIdx.x] = acc;
     __syncthreads();
     if (threadIdx.x < NE) {
