@@ -212,11 +212,19 @@ __device__ __forceinline__ void chol_small_body(const double *__restrict__ G, co
             A[i][lane] = G[i * S + lane];
             Rs[i][lane] = 0.0;
         }
+    // the thresholds before the first pivot: a load per pivot would wait out a memory
+    // round trip between every two __syncwarp
+    double gkk[S], thr[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        gkk[k] = G[k * S + k];
+        thr[k] = ref2 ? tau2 * ref2[k] : 0.0;
+    }
     __syncwarp();
+#pragma unroll
     for (int k = 0; k < S; ++k) {
         const double d = A[k][k];
-        const double gkk = G[k * S + k];
-        bool defl = !(d > 0.0) || d <= 1e-15 * gkk || (ref2 && d <= tau2 * ref2[k]);
+        bool defl = !(d > 0.0) || d <= 1e-15 * gkk[k] || (ref2 && d <= thr[k]);
         if (!defl) {
             const double rkk = sqrt(d);
             if (lane >= k && lane < S) Rs[k][lane] = (lane == k) ? rkk : A[k][lane] / rkk;
@@ -384,13 +392,10 @@ __device__ __forceinline__ void triu_mul_body(const double *__restrict__ R2, con
 //                 first, so the same bits)
 //   k_colnorm2_t: column norms^2, the last CTA adds the partials
 // ---------------------------------------------------------------------------------
-template <int NE>
-__device__ bool last_cta_sum(const double *partial, unsigned *ticket, double *out)
+// true in the CTA that takes the last ticket: every CTA's partial is then visible to it
+__device__ __forceinline__ bool take_last_ticket(unsigned *ticket)
 {
-    constexpr int NG = kThreads / NE;
-    static_assert(NG * NE == kThreads, "entries divide the block");
     __shared__ unsigned s_last;
-    __shared__ double red[kThreads];
     __syncthreads();  // this CTA's partial is written
     if (threadIdx.x == 0) {
         __threadfence();
@@ -399,25 +404,73 @@ __device__ bool last_cta_sum(const double *partial, unsigned *ticket, double *ou
     __syncthreads();
     if (!s_last) return false;
     __threadfence();
+    return true;
+}
+
+// p[c * stride] added over chunks c0 <= c < c1 in chunk order, sixteen loads in flight (the
+// partials sit in L2, a long round trip away on this two-die GPU)
+__device__ __forceinline__ double sum_chunks(const double *p, int stride, int c0, int c1)
+{
+    double acc = 0.0;
+    int c = c0;
+    for (; c + 16 <= c1; c += 16) {
+        double v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) v[u] = __ldcg(p + (int64_t)(c + u) * stride);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) acc += v[u];
+    }
+    for (; c < c1; ++c) acc += __ldcg(p + (int64_t)c * stride);
+    return acc;
+}
+
+template <int NE>
+__device__ bool last_cta_sum(const double *partial, unsigned *ticket, double *out)
+{
+    constexpr int NG = kThreads / NE;
+    static_assert(NG * NE == kThreads, "entries divide the block");
+    __shared__ double red[kThreads];
+    if (!take_last_ticket(ticket)) return false;
     const int chunks = gridDim.x;
     const int e = threadIdx.x % NE, q = threadIdx.x / NE;
     const int c0 = (int)((int64_t)chunks * q / NG), c1 = (int)((int64_t)chunks * (q + 1) / NG);
-    double acc = 0.0;
-    int c = c0;
-    for (; c + 8 <= c1; c += 8) {  // eight loads in flight, added in chunk order
-        double v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = __ldcg(partial + (int64_t)(c + u) * NE + e);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) acc += v[u];
-    }
-    for (; c < c1; ++c) acc += __ldcg(partial + (int64_t)c * NE + e);
-    red[threadIdx.x] = acc;
+    red[threadIdx.x] = sum_chunks(partial + e, NE, c0, c1);
     __syncthreads();
     if (threadIdx.x < NE) {
         double v = red[threadIdx.x];
         for (int h = 1; h < NG; ++h) v += red[h * NE + threadIdx.x];
         out[threadIdx.x] = v;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+    __syncthreads();
+    return true;
+}
+
+// The same for the chunks' S x S Gram partials (symmetric): only the S (S + 1) / 2 pairs
+// a <= b are added, thread (pair p, group q) over the fixed chunk range q, and out gets
+// both triangles.
+template <int S>
+__device__ bool last_cta_gram(const double *partial, unsigned *ticket, double *out)
+{
+    constexpr int NP = S * (S + 1) / 2;
+    constexpr int NG = kThreads / NP;
+    __shared__ double red[kThreads];
+    if (!take_last_ticket(ticket)) return false;
+    const int chunks = gridDim.x;
+    const int p = threadIdx.x % NP, q = threadIdx.x / NP;
+    int a = 0, rem = p;
+    while (rem >= S - a) { rem -= S - a; ++a; }
+    const int b = a + rem;
+    if (q < NG) {
+        const int c0 = (int)((int64_t)chunks * q / NG), c1 = (int)((int64_t)chunks * (q + 1) / NG);
+        red[threadIdx.x] = sum_chunks(partial + a * S + b, S * S, c0, c1);
+    }
+    __syncthreads();
+    if (threadIdx.x < NP) {
+        double v = red[threadIdx.x];
+        for (int h = 1; h < NG; ++h) v += red[h * NP + threadIdx.x];
+        out[a * S + b] = v;
+        out[b * S + a] = v;
     }
     if (threadIdx.x == 0) *ticket = 0u;
     __syncthreads();
@@ -434,7 +487,7 @@ __global__ void __launch_bounds__(kThreads) k_cqr_gram(int32_t n, const double *
     int64_t r0, r1;
     chunk_rows(n, blockIdx.x, gridDim.x, r0, r1);
     gram_tiles<S, false>(r0, r1, W, nullptr, nullptr, nullptr, partial + (int64_t)blockIdx.x * S * S);
-    if (!last_cta_sum<S * S>(partial, ticket, G)) return;
+    if (!last_cta_gram<S>(partial, ticket, G)) return;
     if (threadIdx.x < 32) chol_small_body<S>(G, ref2, tau2, R1, defl1);
 }
 
@@ -455,7 +508,7 @@ __global__ void __launch_bounds__(kThreads) k_cqr_gram2(int32_t n, const double 
     int64_t r0, r1;
     chunk_rows(n, blockIdx.x, gridDim.x, r0, r1);
     gram_tiles<S, true, false>(r0, r1, W, Rs, rinv, nullptr, partial + (int64_t)blockIdx.x * S * S);
-    if (!last_cta_sum<S * S>(partial, ticket, G)) return;
+    if (!last_cta_gram<S>(partial, ticket, G)) return;
     if (threadIdx.x < 32) chol_small_body<S>(G, nullptr, 0.0, R2, defl2);
     __syncthreads();  // R2 (global) written by warp 0
     triu_mul_body<S>(R2, R1, Rout);
@@ -1127,12 +1180,13 @@ int launch_gram_rows(cudaStream_t st, int32_t s, int32_t n, const double *W, dou
     return check_launch(2);
 }
 
-// row chunks of the fused Cholesky-QR and norm kernels: 256-row tiles, at most four CTAs
-// per SM (608 partials for the last CTA to add)
+// row chunks of the fused Cholesky-QR and norm kernels: 256-row tiles, at most two CTAs
+// per SM (304 partials for the last CTA to add: the row passes run as fast as with four
+// CTAs per SM, and the last CTA's sum, a chain of L2 round trips, takes half as long)
 int cqr_chunks(int32_t n)
 {
     int64_t c = ((int64_t)n + 255) / 256;
-    if (c > 608) c = 608;
+    if (c > 304) c = 304;
     if (c < 1) c = 1;
     return (int)c;
 }
