@@ -386,10 +386,10 @@ __device__ __forceinline__ void triu_mul_body(const double *__restrict__ R2, con
 // fixed chunk range q, then the groups in order: the same sums whichever CTA is last),
 // does the pass's small dense step and resets the ticket for the next launch.
 //   k_cqr_gram:   G1 = W^T W; last CTA: R1 = chol(G1) with deflation against ref2
-//   k_cqr_gram2:  rows W R1^{-1} (in registers, not stored), G2 = their Gram; last CTA:
+//   k_cqr_gram2:  rows Q1 = W R1^{-1}, stored in Q, and G2 = their Gram; last CTA:
 //                 R2 = chol(G2), R = R2 R1
-//   k_cqr_apply:  Q = (W R1^{-1}) R2^{-1} (the same row operations as storing W R1^{-1}
-//                 first, so the same bits)
+//   k_cqr_apply:  Q := Q1 R2^{-1} in place (one row solve on the FP64 pipe instead of
+//                 redoing W R1^{-1}: the stored rows are the same bits)
 //   k_colnorm2_t: column norms^2, the last CTA adds the partials
 // ---------------------------------------------------------------------------------
 // true in the CTA that takes the last ticket: every CTA's partial is then visible to it
@@ -495,9 +495,9 @@ template <int S>
 __global__ void __launch_bounds__(kThreads) k_cqr_gram2(int32_t n, const double *__restrict__ W,
                                                         const double *__restrict__ R1,
                                                         const int32_t *__restrict__ defl1,
-                                                        double *__restrict__ partial, unsigned *__restrict__ ticket,
-                                                        double *__restrict__ R2, int32_t *__restrict__ defl2,
-                                                        double *__restrict__ Rout)
+                                                        double *__restrict__ Q1, double *__restrict__ partial,
+                                                        unsigned *__restrict__ ticket, double *__restrict__ R2,
+                                                        int32_t *__restrict__ defl2, double *__restrict__ Rout)
 {
     __shared__ double Rs[S * S];
     __shared__ double rinv[S];
@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(kThreads) k_cqr_gram2(int32_t n, const double 
     __syncthreads();
     int64_t r0, r1;
     chunk_rows(n, blockIdx.x, gridDim.x, r0, r1);
-    gram_tiles<S, true, false>(r0, r1, W, Rs, rinv, nullptr, partial + (int64_t)blockIdx.x * S * S);
+    gram_tiles<S, true>(r0, r1, W, Rs, rinv, Q1, partial + (int64_t)blockIdx.x * S * S);
     if (!last_cta_gram<S>(partial, ticket, G)) return;
     if (threadIdx.x < 32) chol_small_body<S>(G, nullptr, 0.0, R2, defl2);
     __syncthreads();  // R2 (global) written by warp 0
@@ -515,28 +515,18 @@ __global__ void __launch_bounds__(kThreads) k_cqr_gram2(int32_t n, const double 
 }
 
 template <int S>
-__global__ void __launch_bounds__(kThreads) k_cqr_apply(int32_t n, const double *W, const double *__restrict__ R1,
-                                                        const int32_t *__restrict__ defl1,
-                                                        const double *__restrict__ R2,
-                                                        const int32_t *__restrict__ defl2, double *Q,
-                                                        float *__restrict__ Q32)
+__global__ void __launch_bounds__(kThreads) k_cqr_apply(int32_t n, double *Q, const double *__restrict__ R2,
+                                                        const int32_t *__restrict__ defl2, float *__restrict__ Q32)
 {
-    __shared__ double Rs1[S * S], Rs2[S * S];
-    __shared__ double rinv1[S], rinv2[S];
-    for (int e = threadIdx.x; e < S * S; e += blockDim.x) {
-        Rs1[e] = R1[e];
-        Rs2[e] = R2[e];
-    }
-    if (threadIdx.x < S) {
-        rinv1[threadIdx.x] = defl1[threadIdx.x] ? 0.0 : 1.0 / R1[threadIdx.x * S + threadIdx.x];
-        rinv2[threadIdx.x] = defl2[threadIdx.x] ? 0.0 : 1.0 / R2[threadIdx.x * S + threadIdx.x];
-    }
+    __shared__ double Rs2[S * S];
+    __shared__ double rinv2[S];
+    for (int e = threadIdx.x; e < S * S; e += blockDim.x) Rs2[e] = R2[e];
+    if (threadIdx.x < S) rinv2[threadIdx.x] = defl2[threadIdx.x] ? 0.0 : 1.0 / R2[threadIdx.x * S + threadIdx.x];
     __syncthreads();
     const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n) return;
     double x[S];
-    row_load<S>(W, r, x);
-    trsm_row<S>(x, Rs1, rinv1);
+    row_load<S>(Q, r, x);
     trsm_row<S>(x, Rs2, rinv2);
     row_store<S>(Q, r, x);
     if (Q32) {
@@ -1202,18 +1192,18 @@ int launch_cqr_gram(cudaStream_t st, int32_t s, int32_t n, const double *W, cons
 }
 
 int launch_cqr_gram2(cudaStream_t st, int32_t s, int32_t n, const double *W, const double *R1, const int32_t *defl1,
-                     double *partial, unsigned *ticket, double *R2, int32_t *defl2, double *Rout)
+                     double *Q1, double *partial, unsigned *ticket, double *R2, int32_t *defl2, double *Rout)
 {
     const int chunks = cqr_chunks(n);
-    SPAI_DISPATCH_S8(s, (k_cqr_gram2<S><<<chunks, kThreads, 0, st>>>(n, W, R1, defl1, partial, ticket, R2, defl2,
-                                                                     Rout)));
+    SPAI_DISPATCH_S8(s, (k_cqr_gram2<S><<<chunks, kThreads, 0, st>>>(n, W, R1, defl1, Q1, partial, ticket, R2,
+                                                                     defl2, Rout)));
     return check_launch();
 }
 
-int launch_cqr_apply(cudaStream_t st, int32_t s, int32_t n, const double *W, const double *R1, const int32_t *defl1,
-                     const double *R2, const int32_t *defl2, double *Q, float *Q32)
+int launch_cqr_apply(cudaStream_t st, int32_t s, int32_t n, double *Q, const double *R2, const int32_t *defl2,
+                     float *Q32)
 {
-    SPAI_DISPATCH_S8(s, (k_cqr_apply<S><<<grid_for(n), kThreads, 0, st>>>(n, W, R1, defl1, R2, defl2, Q, Q32)));
+    SPAI_DISPATCH_S8(s, (k_cqr_apply<S><<<grid_for(n), kThreads, 0, st>>>(n, Q, R2, defl2, Q32)));
     return check_launch();
 }
 

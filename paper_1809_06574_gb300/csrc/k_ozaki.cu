@@ -478,37 +478,28 @@ __global__ void __launch_bounds__(256) k_trsm_fixed(int32_t n, double *__restric
     if (bad) atomicOr(err, ERR_RANGE);
 }
 
-// Last pass of the fused Cholesky-QR for an 8-column basis block: Q = (W R1^{-1}) R2^{-1}
-// (the row solve every orthogonalisation kernel shares, twice) and the block's fixed point
-// as k_trsm_fixed writes it.  Four CTAs per SM, each thread over rows r, r + grid, ...
-// with its next row loaded before the current one is solved (the two row solves keep the
-// FP64 pipe busy meanwhile); the register cap keeps the factors in shared memory rather
-// than in 144 registers, which would leave one CTA per SM.
-__global__ void __launch_bounds__(256, 4) k_cqr_apply_fixed(int32_t n, const double *__restrict__ W,
-                                                            const double *__restrict__ R1,
-                                                            const int32_t *__restrict__ defl1,
-                                                            const double *__restrict__ R2,
-                                                            const int32_t *__restrict__ defl2, double *__restrict__ Q,
+// Last pass of the fused Cholesky-QR for an 8-column basis block: Q := Q1 R2^{-1} in place,
+// Q holding Q1 = W R1^{-1} from the second pass (the row solve every orthogonalisation
+// kernel shares), and the block's fixed point as k_trsm_fixed writes it.  Four CTAs per
+// SM, each thread over rows r, r + grid, ... with its next row loaded before the current
+// one is solved (the row solve keeps the FP64 pipe busy meanwhile); the register cap keeps
+// the factor in shared memory rather than in registers.
+__global__ void __launch_bounds__(256, 4) k_cqr_apply_fixed(int32_t n, double *Q, const double *__restrict__ R2,
+                                                            const int32_t *__restrict__ defl2,
                                                             uint64_t *__restrict__ F_row, uint64_t *__restrict__ F_sub,
                                                             int32_t ipad, int32_t blk, int *err, float *__restrict__ Q32)
 {
-    __shared__ double Rs1[kS * kS], Rs2[kS * kS];
-    __shared__ double rinv1[kS], rinv2[kS];
-    for (int e = threadIdx.x; e < kS * kS; e += blockDim.x) {
-        Rs1[e] = R1[e];
-        Rs2[e] = R2[e];
-    }
-    if (threadIdx.x < kS) {
-        rinv1[threadIdx.x] = defl1[threadIdx.x] ? 0.0 : 1.0 / R1[threadIdx.x * kS + threadIdx.x];
-        rinv2[threadIdx.x] = defl2[threadIdx.x] ? 0.0 : 1.0 / R2[threadIdx.x * kS + threadIdx.x];
-    }
+    __shared__ double Rs2[kS * kS];
+    __shared__ double rinv2[kS];
+    for (int e = threadIdx.x; e < kS * kS; e += blockDim.x) Rs2[e] = R2[e];
+    if (threadIdx.x < kS) rinv2[threadIdx.x] = defl2[threadIdx.x] ? 0.0 : 1.0 / R2[threadIdx.x * kS + threadIdx.x];
     __syncthreads();
     const int64_t nt = ((int64_t)n + kKT - 1) / kKT * kKT;
     const int64_t step = (int64_t)gridDim.x * blockDim.x;
     bool bad = false;
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double xn[kS];
-    if (r < n) row_load<kS>(W, r, xn);
+    if (r < n) row_load<kS>(Q, r, xn);
     for (; r < nt; r += step) {
         asm volatile("" ::: "memory");  // the factors are read from shared memory in every row
         uint64_t f[kS];
@@ -518,8 +509,7 @@ __global__ void __launch_bounds__(256, 4) k_cqr_apply_fixed(int32_t n, const dou
             double x[kS];
 #pragma unroll
             for (int a = 0; a < kS; ++a) x[a] = xn[a];
-            if (r + step < n) row_load<kS>(W, r + step, xn);
-            trsm_row<kS>(x, Rs1, rinv1);
+            if (r + step < n) row_load<kS>(Q, r + step, xn);
             trsm_row<kS>(x, Rs2, rinv2);
             row_store<kS>(Q, r, x);
             if (Q32) {  // the block in FP32: the input of the mixed solve's FP32 operator
@@ -1217,16 +1207,14 @@ int launch_trsm_fixed(cudaStream_t st, int32_t n, double *Q, const double *R, co
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_cqr_apply_fixed(cudaStream_t st, int32_t n, const double *W, const double *R1, const int32_t *defl1,
-                           const double *R2, const int32_t *defl2, double *Q, uint64_t *F_row, uint64_t *F_sub,
-                           int32_t ipad, int32_t blk, int *d_err, float *Q32)
+int launch_cqr_apply_fixed(cudaStream_t st, int32_t n, double *Q, const double *R2, const int32_t *defl2,
+                           uint64_t *F_row, uint64_t *F_sub, int32_t ipad, int32_t blk, int *d_err, float *Q32)
 {
     if (n <= 0) return 0;
     const int64_t rows = ((int64_t)n + kKT - 1) / kKT * kKT;
     int64_t g = (rows + 255) / 256;
     if (g > 4 * 152) g = 4 * 152;
-    k_cqr_apply_fixed<<<(unsigned)g, 256, 0, st>>>(n, W, R1, defl1, R2, defl2, Q, F_row, F_sub, ipad, blk, d_err,
-                                                   Q32);
+    k_cqr_apply_fixed<<<(unsigned)g, 256, 0, st>>>(n, Q, R2, defl2, F_row, F_sub, ipad, blk, d_err, Q32);
     note_launches(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

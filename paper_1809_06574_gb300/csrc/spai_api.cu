@@ -2322,9 +2322,9 @@ size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks
 // W = Q R with Q orthonormal (deflated columns zero), two passes of Cholesky QR:
 //   G1 = W^T W, R1 = chol(G1); Q1 = W R1^{-1}; G2 = Q1^T Q1, R2 = chol(G2); Q = Q1 R2^{-1};
 //   R = R2 R1.
-// For s <= 8 the rows stay in registers: Q1 and G2 come from one pass over W, and with
-// fix_blk >= 0 (s == 8) the last pass also writes Q's fixed-point copies (basis slot fix_blk
-// of ipad) for the tensor-core products.
+// For s <= 8, Q1 (written to Qout) and G2 come from one pass over W, the last pass solves
+// Qout in place, and with fix_blk >= 0 (s == 8) it also writes Q's fixed-point copies
+// (basis slot fix_blk of ipad) for the tensor-core products.  Qout must not overlap Win.
 spai_status cholqr2(spai_ctx ctx, SolveWs &w, int32_t n, int32_t s, const double *Win, double *Qout, double *Rout,
                     const double *ref2, int fix_blk, int32_t ipad, float *Q32 = nullptr)
 {
@@ -2334,17 +2334,17 @@ spai_status cholqr2(spai_ctx ctx, SolveWs &w, int32_t n, int32_t s, const double
         // three launches; each pass's last CTA does its Cholesky (and R = R2 R1)
         PKL("cqr_gram", nsd * (s + 1), 8.0 * nsd,
             launch_cqr_gram(st, s, n, Win, ref2, 1e-24, w.partial, w.ticket, w.R1, w.defl1), "Cholesky-QR pass 1");
-        PKL("cqr_gram2", nsd * s + nsd * (s + 1), 8.0 * nsd,
-            launch_cqr_gram2(st, s, n, Win, w.R1, w.defl1, w.partial, w.ticket, w.R2, w.defl2, Rout),
+        PKL("cqr_gram2", nsd * s + nsd * (s + 1), 16.0 * nsd,
+            launch_cqr_gram2(st, s, n, Win, w.R1, w.defl1, Qout, w.partial, w.ticket, w.R2, w.defl2, Rout),
             "Cholesky-QR pass 2");
         if (fix_blk >= 0) {
-            PKL("cqr_apply_fixed", 2.0 * nsd * s, 32.0 * nsd,
-                launch_cqr_apply_fixed(st, n, Win, w.R1, w.defl1, w.R2, w.defl2, Qout,
-                                       w.vfix + (size_t)fix_blk * n * s, w.vfix_sub, ipad, fix_blk, ctx->d_err, Q32),
+            PKL("cqr_apply_fixed", nsd * s, 32.0 * nsd,
+                launch_cqr_apply_fixed(st, n, Qout, w.R2, w.defl2, w.vfix + (size_t)fix_blk * n * s, w.vfix_sub, ipad,
+                                       fix_blk, ctx->d_err, Q32),
                 "Cholesky-QR pass 3 with fixed point");
         } else {
-            PKL("cqr_apply", 2.0 * nsd * s, 16.0 * nsd,
-                launch_cqr_apply(st, s, n, Win, w.R1, w.defl1, w.R2, w.defl2, Qout, Q32), "Cholesky-QR pass 3");
+            PKL("cqr_apply", nsd * s, 16.0 * nsd, launch_cqr_apply(st, s, n, Qout, w.R2, w.defl2, Q32),
+                "Cholesky-QR pass 3");
         }
         return SPAI_OK;
     } else {

@@ -365,17 +365,18 @@ int launch_trsm_gram(cudaStream_t st, int32_t s, int32_t n, const double *W, con
 int launch_triu_mul(cudaStream_t st, int32_t s, const double *R2, const double *R1, double *out);
 // Cholesky-QR W = Q R (s <= 8) in three launches whose last CTA (ticket, zero before the
 // first launch and left zero) finishes each pass: R1 = chol(W^T W) with deflation against
-// ref2 (tau2); R2 = chol of the Gram of W R1^{-1}, Rout = R2 R1; Q = (W R1^{-1}) R2^{-1}.
-// partial: cqr_chunks(n) * s * s doubles.  Column norms^2 the same way (out: s doubles).
+// ref2 (tau2); Q1 = W R1^{-1} stored in Q (Q must not overlap W), R2 = chol of its Gram,
+// Rout = R2 R1; Q := Q1 R2^{-1} in place.  partial: cqr_chunks(n) * s * s doubles.  Column
+// norms^2 the same way (out: s doubles).
 bool cqr_supported(int32_t s);
 int cqr_chunks(int32_t n);
 int launch_cqr_gram(cudaStream_t st, int32_t s, int32_t n, const double *W, const double *ref2, double tau2,
                     double *partial, unsigned *ticket, double *R1, int32_t *defl1);
 int launch_cqr_gram2(cudaStream_t st, int32_t s, int32_t n, const double *W, const double *R1, const int32_t *defl1,
-                     double *partial, unsigned *ticket, double *R2, int32_t *defl2, double *Rout);
+                     double *Q1, double *partial, unsigned *ticket, double *R2, int32_t *defl2, double *Rout);
 // (Q32: non-null for an FP32 copy of Q as well)
-int launch_cqr_apply(cudaStream_t st, int32_t s, int32_t n, const double *W, const double *R1, const int32_t *defl1,
-                     const double *R2, const int32_t *defl2, double *Q, float *Q32);
+int launch_cqr_apply(cudaStream_t st, int32_t s, int32_t n, double *Q, const double *R2, const int32_t *defl2,
+                     float *Q32);
 int launch_colnorm2_t(cudaStream_t st, int32_t s, int32_t n, const double *W, double *partial, unsigned *ticket,
                       double *out);
 // projected least squares of block column j (Hessenberg column = H1 + H2 over Rsub)
@@ -426,11 +427,11 @@ int block_update_tc_max_blocks();
 size_t tc_hdig_bytes(int32_t nblk);
 int launch_block_update_tc(cudaStream_t st, int32_t n, int32_t nblk, const uint64_t *Vf, const double *H, void *hdig,
                            int32_t *hexp, const double *base, double *out, double sign, int *d_err, TcWait wt);
-// Q = (W R1^{-1}) R2^{-1} (s == 8, deflated columns -> 0, the last pass of the fused
-// Cholesky-QR) with the new basis block's fixed point, laid out as launch_trsm_fixed does
-int launch_cqr_apply_fixed(cudaStream_t st, int32_t n, const double *W, const double *R1, const int32_t *defl1,
-                           const double *R2, const int32_t *defl2, double *Q, uint64_t *F_row, uint64_t *F_sub,
-                           int32_t ipad, int32_t blk, int *d_err, float *Q32);
+// Q := Q1 R2^{-1} in place, Q holding Q1 = W R1^{-1} from launch_cqr_gram2 (s == 8,
+// deflated columns -> 0, the last pass of the fused Cholesky-QR) with the new basis block's
+// fixed point, laid out as launch_trsm_fixed does
+int launch_cqr_apply_fixed(cudaStream_t st, int32_t n, double *Q, const double *R2, const int32_t *defl2,
+                           uint64_t *F_row, uint64_t *F_sub, int32_t ipad, int32_t blk, int *d_err, float *Q32);
 // Q := Q R^{-1} in place (s == 8, deflated columns -> 0) and the new basis block's fixed
 // point: row layout at F_row (n x 8), sub-tile layout at slot blk of ipad slots of F_sub
 int launch_trsm_fixed(cudaStream_t st, int32_t n, double *Q, const double *R, const int32_t *deflated, uint64_t *F_row,
