@@ -184,14 +184,17 @@ NCU_TRAFFIC = {
 }
 
 
-def roofline_entry(f, n, s, fp64_probe=None):
+def roofline_entry(f, n, s, fp64_probe=None, fp32_probe=None, unit=None):
     """Binding roof of one kernel family: max(bytes / HBM, flops / compute peak).
 
     Bytes and flops are the algorithmic figures of the method (FP64 operands), credited per
     launch by the library's profiler.  Compute peak: the FP64 ALUs for FP64 kernels, the
-    BF16 tensor peak / 53 for the digit-product kernels (FP64-equivalent flops)."""
+    FP32 ALUs for FP32 kernels (`unit` overrides the family's default, e.g. the column
+    problems of an FP32 build), the BF16 tensor peak / 43 for the digit-product kernels
+    (FP64-equivalent flops).  The FMA probes' measured rates are quoted beside the derived
+    peaks."""
     hbm, bf16, bf16_sus, src = _peaks()
-    unit = FAMILY_UNIT.get(f["name"], "fp64")
+    unit = unit or FAMILY_UNIT.get(f["name"], "fp64")
     launches = max(f["launches"], 1)
     sec = f["ms"] * 1e-3
     out = {"kernel": f["name"], "launches": f["launches"], "avg_launch_ms": f["ms"] / launches,
@@ -212,7 +215,9 @@ def roofline_entry(f, n, s, fp64_probe=None):
     else:
         ach = f["flops"] / sec / 1e12
         out.update({"bound": "alu", "achieved": ach, "peak": cpeak, "unit": "TFLOP/s", "frac": ach / cpeak,
-                    "peak_source": ("derived: 152 SM x 256 FP32 flop/clk x 2.07 GHz" if unit == "fp32" else
+                    "peak_source": ("derived: 152 SM x 256 FP32 flop/clk x 2.07 GHz"
+                                    + (f"; FP32 FMA probe measured {fp32_probe:.1f} TFLOP/s in this run"
+                                       if fp32_probe else "") if unit == "fp32" else
                                     "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz"
                                     + (f"; FMA probe measured {fp64_probe:.3f} TFLOP/s in this run"
                                        if fp64_probe else ""))})
@@ -279,10 +284,18 @@ def run_columns_case(args):
     wall = (time.perf_counter() - t0) / max(args.steps, 1)
     prof = [sg.spai_ctx_profile_entry(ctx, i) for i in range(sg.spai_ctx_profile_count(ctx))]
     sg.spai_ctx_profile(ctx, 0)
+    fp32_rate = max(sg.spai_measure_fp32_rate(ctx) for _ in range(3))
     for aff, _, _ in keep:
         sg.spai_affine_destroy(aff)
     sg.spai_ctx_destroy(ctx)
+    col_unit = "fp32" if args.columns_prec == "fp32" else "fp64"
+    roofs = {}
+    for f in prof:
+        if f["name"] == "spai_columns":
+            r = roofline_entry(f, n=sum(w.n for w in ws), s=1, fp32_probe=fp32_rate, unit=col_unit)
+            roofs[f["name"]] = {k: r[k] for k in ("bound", "achieved", "peak", "unit", "frac", "peak_source")}
     print(json.dumps({"kernel_case": "columns", "workload": args.columns_workload, "precision": args.columns_prec,
+                      "fp32_tflops_measured": fp32_rate, "roofline": roofs,
                       "variant": args.columns_variant or "tuned",
                       "least_squares": "normal equations" if args.columns_normal else "Householder QR",
                       "systems": len(ws), "columns": sum(w.n for w in ws),
@@ -770,6 +783,7 @@ def run_block_vs_single(sg, torch, ctx, w, nsys=5):
     solves of the same systems (Sec. 2.1: block methods share one Krylov space), on the
     first `nsys` parameters of the shift s = 1 (SPAI build at the first, updates after),
     one stream, FP64 throughout."""
+    nsys = min(nsys, len(w.params))  # a sweep reduced by --nparams has fewer parameters
     n, nr = w.n, int(w.B.shape[1])
     dev = torch.device("cuda", torch.cuda.current_device())
     d_terms = [tuple(torch.as_tensor(np.ascontiguousarray(a), device=dev) for a in t) for t in w.terms]
@@ -1264,6 +1278,7 @@ def main():
         return
     ctx = sg.spai_ctx_create(stream.cuda_stream, 0)
     fp64_tflops = max(sg.spai_measure_fp64_rate(ctx) for _ in range(3))
+    fp32_tflops = max(sg.spai_measure_fp32_rate(ctx) for _ in range(3))
 
     sweep = Sweep(sg, torch, ctx, w, workers=args.workers)
     sweep.profile(1)  # the warm-up also fills the profiler's pools of CUDA events
@@ -1306,13 +1321,19 @@ def main():
     t_max, total_solves = aggregate_replicas(dist, torch, "cuda", t_local, solves)
     value = total_solves / t_max
 
-    def timed_sweep(**kw):
+    def timed_sweep(fp32_roofs=False, **kw):
         """The sweep of the headline with other factor / solve precisions: warm-up, then the
-        same number of timed steps (device events, max over ranks)."""
+        same number of timed steps (device events, max over ranks).  fp32_roofs: the FP32
+        kernel families of the timed steps (the column problems of FP32 builds, the FP32
+        operator products) against the FP32 ALU roof."""
         sw = Sweep(sg, torch, ctx, w, workers=args.workers, **kw)
+        if fp32_roofs:
+            sw.profile(1)  # the warm-up fills the profiler's pools of CUDA events
         for _ in range(max(1, args.warmup)):
             sw.step()
         sw.solves, sw.iters, sw.cycles = 0, [], []
+        if fp32_roofs:
+            sw.profile(1)  # clears the warm-up's totals
         barrier()
         m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         m0.record(stream)
@@ -1333,6 +1354,19 @@ def main():
                "gmres_iterations": {"mean": float(np.mean(sw.iters)), "min": int(min(sw.iters)),
                                     "max": int(max(sw.iters))},
                "cycles": {"mean": float(np.mean(sw.cycles)), "max": int(max(sw.cycles))}}
+        if fp32_roofs:
+            fams = [f for f in sw.profile_entries() if not f["name"].startswith("idle:")]
+            sw.profile(0)
+            tot = sum(f["ms"] for f in fams) or 1.0
+            roofs = {}
+            for f in fams:
+                if f["name"] in ("spai_columns", "spmm32_A", "spmm32_P") and f["ms"] > 0:
+                    r = roofline_entry(f, n=w.n, s=int(w.B.shape[1]), fp32_probe=fp32_tflops, unit="fp32")
+                    roofs[f["name"]] = {"launches": f["launches"], "ms": round(f["ms"], 3),
+                                        "share": round(f["ms"] / tot, 4), "bound": r["bound"],
+                                        "achieved": round(r["achieved"], 3), "unit": r["unit"],
+                                        "frac": round(r["frac"], 4)}
+            out["kernels_fp32"] = roofs
         sw.close()
         return out
 
@@ -1342,7 +1376,7 @@ def main():
     mixed = None
     fp32_factors = None
     if not args.no_mixed:
-        mixed = timed_sweep(prec=sg.PREC_FP32 | sg.LS_NORMAL, solve_precision=sg.SOLVE_MIXED)
+        mixed = timed_sweep(fp32_roofs=True, prec=sg.PREC_FP32 | sg.LS_NORMAL, solve_precision=sg.SOLVE_MIXED)
         mixed.update({"dtype": "f32 SPAI factors (column problems by their normal equations) and f32 operator "
                                "products, f64 basis/Gram-Schmidt/least squares/true residual (iterative refinement)",
                       "vs_plain_fp64": None})
@@ -1460,6 +1494,7 @@ def main():
                                             "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                                             "workers": args.workers},
             "gpu_launches": int(launches), "clocks": clk, "fp64_tflops_measured": fp64_tflops,
+            "fp32_tflops_measured": fp32_tflops,
             "gmres_iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)),
                                  "max": int(max(iters))},
             "kernels": kernels,

@@ -158,6 +158,12 @@ SPAI_API int64_t spai_launch_count(void);
  * this library's FP64 kernels are bound by this rate rather than by HBM bandwidth. */
 SPAI_API spai_status spai_measure_fp64_rate(spai_ctx ctx, double *tflops);
 
+/* Diagnostics: measured FP32 (non-tensor) fused-multiply-add throughput of the current
+ * device in TFLOP/s, measured the same way (synchronises).  It is what the FP32 kernels
+ * could reach: the FP32 column problems of FP32 builds, and the FP32 operator products of
+ * the mixed-precision solve.  Like the FP64 probe, it has no counterpart in the paper. */
+SPAI_API spai_status spai_measure_fp32_rate(spai_ctx ctx, double *tflops);
+
 /* Optional timing of the library's kernels by family ("spmm_A", "block_dot", ...): while
  * enabled, each launch is bracketed by CUDA events recorded on the context's stream and
  * credited with the algorithmic flops and bytes of that launch.  spai_ctx_profile

@@ -20,6 +20,7 @@ __all__ = [
     "SpaiError", "spai_csr", "spai_solve_opts", "spai_solve_info", "csr", "lib",
     "spai_ctx_create", "spai_ctx_destroy", "spai_last_error", "spai_ctx_sync",
     "spai_ctx_mem_in_use", "spai_ctx_set_wait_limit", "spai_ctx_inject_stall", "spai_launch_count", "spai_ctx_profile", "spai_ctx_profile_count", "spai_measure_fp64_rate",
+    "spai_measure_fp32_rate",
     "spai_ctx_profile_entry", "spai_affine_create", "spai_affine_pattern",
     "spai_assemble", "spai_affine_export", "spai_affine_destroy", "spai_build", "spai_update", "spai_pc_info",
     "spai_pc_export", "spai_pc_destroy", "spai_build_batch", "block_solve_batch", "spai_spmm", "spai_pc_apply", "spai_spmm_fp32", "spai_pc_apply_fp32", "block_solve", "block_solve_gcro",
@@ -139,6 +140,7 @@ def lib():
         "spai_ctx_inject_stall": (i32, [vp, i32]),
         "spai_launch_count": (i64, []),
         "spai_measure_fp64_rate": (i32, [vp, P(dbl)]),
+        "spai_measure_fp32_rate": (i32, [vp, P(dbl)]),
         "spai_ctx_profile": (i32, [vp, i32]),
         "spai_ctx_profile_count": (i32, [vp]),
         "spai_ctx_profile_entry": (i32, [vp, i32, P(C.c_char_p), P(i64), P(dbl), P(dbl), P(dbl)]),
@@ -270,6 +272,12 @@ def spai_launch_count():
 def spai_measure_fp64_rate(ctx):
     r = C.c_double()
     _check(ctx, lib().spai_measure_fp64_rate(ctx, C.byref(r)))
+    return r.value
+
+
+def spai_measure_fp32_rate(ctx):
+    r = C.c_double()
+    _check(ctx, lib().spai_measure_fp32_rate(ctx, C.byref(r)))
     return r.value
 
 

@@ -1446,7 +1446,7 @@ int launch_residual(cudaStream_t st, int32_t s, int32_t n, const int32_t *rowptr
 }  // namespace spai
 
 // ---------------------------------------------------------------------------------
-// FP64 FMA throughput probe: 8 independent dependency chains per thread.
+// FP64 and FP32 FMA throughput probes: 8 independent dependency chains per thread.
 // ---------------------------------------------------------------------------------
 namespace spai {
 namespace {
@@ -1470,6 +1470,32 @@ __global__ void k_fp64_fma_probe(int iters, double seed, double *sink)
 int launch_fp64_probe(cudaStream_t st, int blocks, int threads, int iters, double *sink)
 {
     k_fp64_fma_probe<<<blocks, threads, 0, st>>>(iters, 1.0, sink);
+    return check_launch();
+}
+
+namespace {
+// FP32 FMA throughput probe: 8 independent dependency chains per thread, as above
+__global__ void k_fp32_fma_probe(int iters, float seed, float *sink)
+{
+    float a[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a[c] = seed + threadIdx.x * 1e-6f + c * 1e-4f;
+    const float b = 0.9999999f, d = 1e-7f;
+#pragma unroll 8  // the loop's own instructions share the issue slots with the FMAs
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a[c] = fmaf(a[c], b, d);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += a[c];
+    if (s == 12345.678f) sink[0] = s;  // never true; keeps the chains alive
+}
+}  // namespace
+
+int launch_fp32_probe(cudaStream_t st, int blocks, int threads, int iters, float *sink)
+{
+    k_fp32_fma_probe<<<blocks, threads, 0, st>>>(iters, 1.0f, sink);
     return check_launch();
 }
 }  // namespace spai

@@ -935,27 +935,51 @@ extern "C" size_t spai_ctx_mem_in_use(spai_ctx ctx)
 
 extern "C" int64_t spai_launch_count(void) { return spai::launches_total(); }
 
+namespace {
+// FMA throughput of one probe kernel in TFLOP/s: a warm-up launch, then one timed launch of
+// 8 blocks per SM x 256 threads x 8 chains x iters FMAs on the context's stream
+template <class Launch>
+spai_status measure_fma_rate(spai_ctx ctx, int iters, Launch launch, double *tflops)
+{
+    int sms = 0;
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "attribute");
+    const int blocks = sms * 8, threads = 256;
+    cudaEvent_t a = nullptr, b = nullptr;
+    CU(cudaEventCreate(&a), "event");
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return fail(ctx, SPAI_ECUDA, "event");
+    }
+    spai_status st = SPAI_OK;
+    if (launch(blocks, threads, iters / 16) != 0 || cudaEventRecord(a, ctx->stream) != cudaSuccess ||
+        launch(blocks, threads, iters) != 0 || cudaEventRecord(b, ctx->stream) != cudaSuccess ||
+        cudaEventSynchronize(b) != cudaSuccess)
+        st = fail(ctx, SPAI_ECUDA, "FMA probe: %s", cudaGetErrorString(cudaGetLastError()));
+    float ms = 0.f;
+    if (st == SPAI_OK && cudaEventElapsedTime(&ms, a, b) != cudaSuccess) st = fail(ctx, SPAI_ECUDA, "event time");
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st == SPAI_OK) *tflops = 2.0 * 8.0 * (double)blocks * threads * iters / (ms * 1e-3) / 1e12;
+    return st;
+}
+}  // namespace
+
 extern "C" spai_status spai_measure_fp64_rate(spai_ctx ctx, double *tflops)
 {
     if (!ctx || !tflops) return fail(ctx, SPAI_EINVAL, "NULL argument");
-    int sms = 0;
-    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "attribute");
-    const int blocks = sms * 8, threads = 256, iters = 4096;
-    cudaEvent_t a = nullptr, b = nullptr;
-    CU(cudaEventCreate(&a), "event");
-    CU(cudaEventCreate(&b), "event");
     double *sink = (double *)ctx->d_scalar + 8;
-    KL(launch_fp64_probe(ctx->stream, blocks, threads, 256, sink), "warm-up");
-    CU(cudaEventRecord(a, ctx->stream), "event");
-    KL(launch_fp64_probe(ctx->stream, blocks, threads, iters, sink), "probe");
-    CU(cudaEventRecord(b, ctx->stream), "event");
-    CU(cudaEventSynchronize(b), "event sync");
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, a, b);
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    *tflops = 2.0 * 8.0 * (double)blocks * threads * iters / (ms * 1e-3) / 1e12;
-    return SPAI_OK;
+    return measure_fma_rate(
+        ctx, 4096, [&](int blocks, int threads, int it) { return launch_fp64_probe(ctx->stream, blocks, threads, it, sink); },
+        tflops);
+}
+
+extern "C" spai_status spai_measure_fp32_rate(spai_ctx ctx, double *tflops)
+{
+    if (!ctx || !tflops) return fail(ctx, SPAI_EINVAL, "NULL argument");
+    float *sink = (float *)((double *)ctx->d_scalar + 8);
+    return measure_fma_rate(
+        ctx, 65536, [&](int blocks, int threads, int it) { return launch_fp32_probe(ctx->stream, blocks, threads, it, sink); },
+        tflops);
 }
 
 extern "C" spai_status spai_ctx_profile(spai_ctx ctx, int32_t enable)

@@ -438,5 +438,7 @@ int launch_trsm_fixed(cudaStream_t st, int32_t n, double *Q, const double *R, co
                       uint64_t *F_sub, int32_t ipad, int32_t blk, int *d_err);
 // FP64 FMA throughput probe: blocks x threads x 8 chains x iters FMAs
 int launch_fp64_probe(cudaStream_t st, int blocks, int threads, int iters, double *sink);
+// FP32 FMA throughput probe: blocks x threads x 8 chains x iters FMAs
+int launch_fp32_probe(cudaStream_t st, int blocks, int threads, int iters, float *sink);
 
 }  // namespace spai
