@@ -221,6 +221,9 @@ def roofline_entry(f, n, s, fp64_probe=None, fp32_probe=None, unit=None):
                                     "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz"
                                     + (f"; FMA probe measured {fp64_probe:.3f} TFLOP/s in this run"
                                        if fp64_probe else ""))})
+    # the compute side's fraction as well, whichever roof binds (an FP32 kernel near the
+    # ridge can be HBM-bound by its algorithmic bytes and still far from the FP32 ALU peak)
+    out["alu_frac"] = f["flops"] / sec / 1e12 / cpeak if cpeak > 0 else None
     out["traffic"] = None
     if f["name"] in NCU_TRAFFIC and f["bytes"] > 0:
         a, b = NCU_TRAFFIC[f["name"]]
@@ -293,7 +296,8 @@ def run_columns_case(args):
     for f in prof:
         if f["name"] == "spai_columns":
             r = roofline_entry(f, n=sum(w.n for w in ws), s=1, fp32_probe=fp32_rate, unit=col_unit)
-            roofs[f["name"]] = {k: r[k] for k in ("bound", "achieved", "peak", "unit", "frac", "peak_source")}
+            roofs[f["name"]] = {k: r[k] for k in ("bound", "achieved", "peak", "unit", "frac", "alu_frac",
+                                                  "peak_source")}
     print(json.dumps({"kernel_case": "columns", "workload": args.columns_workload, "precision": args.columns_prec,
                       "fp32_tflops_measured": fp32_rate, "roofline": roofs,
                       "variant": args.columns_variant or "tuned",
@@ -1365,7 +1369,7 @@ def main():
                     roofs[f["name"]] = {"launches": f["launches"], "ms": round(f["ms"], 3),
                                         "share": round(f["ms"] / tot, 4), "bound": r["bound"],
                                         "achieved": round(r["achieved"], 3), "unit": r["unit"],
-                                        "frac": round(r["frac"], 4)}
+                                        "frac": round(r["frac"], 4), "alu_frac": round(r["alu_frac"], 4)}
             out["kernels_fp32"] = roofs
         sw.close()
         return out
