@@ -179,8 +179,8 @@ FAMILY_UNIT = {
 # s = 8, 16 basis blocks (read + write bytes; summarised under profiles/).  A family is
 # left out (traffic null) while its kernel has changed since its capture.
 NCU_TRAFFIC = {
-    "block_dot_tc": (8.0, (296.019e6 + 3.201e6) / 2097152 - 8.0 * 17),
-    "block_update_tc": (8.0, (285.285e6 + 11.929e6) / 2097152 - 8.0 * 18),
+    "block_dot_tc": (8.0, (296.053e6 + 3.258e6) / 2097152 - 8.0 * 17),
+    "block_update_tc": (8.0, (285.268e6 + 11.305e6) / 2097152 - 8.0 * 18),
 }
 
 
