@@ -480,15 +480,43 @@ __device__ bool last_cta_gram(const double *partial, unsigned *ticket, double *o
 template <int S>
 __global__ void __launch_bounds__(kThreads) k_cqr_gram(int32_t n, const double *__restrict__ W,
                                                        const double *__restrict__ ref2, double tau2,
-                                                       double *__restrict__ partial, unsigned *__restrict__ ticket,
-                                                       double *__restrict__ R1, int32_t *__restrict__ defl1)
+                                                       const double *__restrict__ H1, const double *__restrict__ H2,
+                                                       int32_t hrows, double *__restrict__ partial,
+                                                       unsigned *__restrict__ ticket, double *__restrict__ R1,
+                                                       int32_t *__restrict__ defl1)
 {
     __shared__ double G[S * S];
+    __shared__ double hred[kThreads];
+    __shared__ double r2[S];
     int64_t r0, r1;
     chunk_rows(n, blockIdx.x, gridDim.x, r0, r1);
     gram_tiles<S, false>(r0, r1, W, nullptr, nullptr, nullptr, partial + (int64_t)blockIdx.x * S * S);
     if (!last_cta_gram<S>(partial, ticket, G)) return;
-    if (threadIdx.x < 32) chol_small_body<S>(G, ref2, tau2, R1, defl1);
+    const double *ref = ref2;
+    if (H1) {
+        // W is what two block CGS passes left of W0 against an orthonormal (or zero-column)
+        // basis V, with coefficients H1 + H2 (hrows x S): W0 = V (H1 + H2) + W, W orthogonal
+        // to V, so ||W0(:, c)||^2 = ||(H1 + H2)(:, c)||^2 + G_cc, the deflation scale, without
+        // another pass over W0.  Thread (column c, group g) over rows g, g + NG, ...; the
+        // groups are added in order.
+        constexpr int NG = kThreads / S;
+        const int c = threadIdx.x % S, g = threadIdx.x / S;
+        double acc = 0.0;
+        for (int r = g; r < hrows; r += NG) {
+            const double h = H1[r * S + c] + H2[r * S + c];
+            acc = fma(h, h, acc);
+        }
+        hred[threadIdx.x] = acc;
+        __syncthreads();
+        if (threadIdx.x < S) {
+            double v = G[c * S + c];
+            for (int q = 0; q < NG; ++q) v += hred[q * S + c];
+            r2[c] = v;
+        }
+        __syncthreads();
+        ref = r2;
+    }
+    if (threadIdx.x < 32) chol_small_body<S>(G, ref, tau2, R1, defl1);
 }
 
 template <int S>
@@ -1184,10 +1212,12 @@ int cqr_chunks(int32_t n)
 bool cqr_supported(int32_t s) { return s == 1 || s == 2 || s == 4 || s == 8; }
 
 int launch_cqr_gram(cudaStream_t st, int32_t s, int32_t n, const double *W, const double *ref2, double tau2,
-                    double *partial, unsigned *ticket, double *R1, int32_t *defl1)
+                    const double *H1, const double *H2, int32_t hrows, double *partial, unsigned *ticket,
+                    double *R1, int32_t *defl1)
 {
     const int chunks = cqr_chunks(n);
-    SPAI_DISPATCH_S8(s, (k_cqr_gram<S><<<chunks, kThreads, 0, st>>>(n, W, ref2, tau2, partial, ticket, R1, defl1)));
+    SPAI_DISPATCH_S8(s, (k_cqr_gram<S><<<chunks, kThreads, 0, st>>>(n, W, ref2, tau2, H1, H2, hrows, partial,
+                                                                    ticket, R1, defl1)));
     return check_launch();
 }
 

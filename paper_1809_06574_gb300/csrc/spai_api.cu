@@ -2349,15 +2349,20 @@ size_t carve(SolveWs &w, void *base, int32_t n, int32_t s, int32_t m, int chunks
 // For s <= 8, Q1 (written to Qout) and G2 come from one pass over W, the last pass solves
 // Qout in place, and with fix_blk >= 0 (s == 8) it also writes Q's fixed-point copies
 // (basis slot fix_blk of ipad) for the tensor-core products.  Qout must not overlap Win.
+// Deflation is judged against ref2 (squared column norms before orthogonalisation), or for
+// s <= 8 with H1 non-null against the norms the first pass forms from the block CGS
+// coefficients H1, H2 (hrows rows).
 spai_status cholqr2(spai_ctx ctx, SolveWs &w, int32_t n, int32_t s, const double *Win, double *Qout, double *Rout,
-                    const double *ref2, int fix_blk, int32_t ipad, float *Q32 = nullptr)
+                    const double *ref2, int fix_blk, int32_t ipad, float *Q32 = nullptr, const double *H1 = nullptr,
+                    const double *H2 = nullptr, int32_t hrows = 0)
 {
     cudaStream_t st = ctx->stream;
     const double nsd = (double)n * s;
     if (cqr_supported(s)) {
         // three launches; each pass's last CTA does its Cholesky (and R = R2 R1)
         PKL("cqr_gram", nsd * (s + 1), 8.0 * nsd,
-            launch_cqr_gram(st, s, n, Win, ref2, 1e-24, w.partial, w.ticket, w.R1, w.defl1), "Cholesky-QR pass 1");
+            launch_cqr_gram(st, s, n, Win, ref2, 1e-24, H1, H2, hrows, w.partial, w.ticket, w.R1, w.defl1),
+            "Cholesky-QR pass 1");
         PKL("cqr_gram2", nsd * s + nsd * (s + 1), 16.0 * nsd,
             launch_cqr_gram2(st, s, n, Win, w.R1, w.defl1, Qout, w.partial, w.ticket, w.R2, w.defl2, Rout),
             "Cholesky-QR pass 2");
@@ -2694,7 +2699,9 @@ spai_status solve_impl(spai_ctx ctx, const spai_csr *A, spai_pc P, int32_t s, co
         for (int j = 0; j < m; ++j) {
             const double *Vj = w.V + (size_t)(kb + j) * blk_elems;
             if ((st = apply_op(Vj, w.W, v32))) return st;
-            if ((st = colnorms(w.W, w.ref2))) return st;
+            // the deflation scale, W's column norms before the projections: for s <= 8 the
+            // first Cholesky-QR pass forms them from the projections' coefficients
+            if (!cqr_supported(s) && (st = colnorms(w.W, w.ref2))) return st;
             // two passes of block classical Gram-Schmidt against C_0..C_{kb-1}, V_0..V_j
             const int nb = kb + j + 1;
             if ((st = gram_any(nb, w.W, w.H1))) return st;
@@ -2704,7 +2711,8 @@ spai_status solve_impl(spai_ctx ctx, const spai_csr *A, spai_pc P, int32_t s, co
             double *Vn = w.V + (size_t)(kb + j + 1) * blk_elems;
             // the new block's fixed point (for the products of the next steps) comes with it
             if ((st = cholqr2(ctx, w, n, s, w.W, Vn, w.Rn, w.ref2,
-                              (use_digits && !halves && j + 1 < m) ? kb + j + 1 : -1, ipad, j + 1 < m ? v32 : nullptr)))
+                              (use_digits && !halves && j + 1 < m) ? kb + j + 1 : -1, ipad, j + 1 < m ? v32 : nullptr,
+                              w.H1, w.H2, nb * s)))
                 return st;
             if (j + 1 < m && (st = fixed16(kb + j + 1))) return st;
             PKL("arnoldi_ls", 16.0 * s * s * s * (nb), 0.0,

@@ -367,11 +367,15 @@ int launch_triu_mul(cudaStream_t st, int32_t s, const double *R2, const double *
 // first launch and left zero) finishes each pass: R1 = chol(W^T W) with deflation against
 // ref2 (tau2); Q1 = W R1^{-1} stored in Q (Q must not overlap W), R2 = chol of its Gram,
 // Rout = R2 R1; Q := Q1 R2^{-1} in place.  partial: cqr_chunks(n) * s * s doubles.  Column
-// norms^2 the same way (out: s doubles).
+// norms^2 the same way (out: s doubles).  With H1 non-null, W is what two block CGS passes
+// with coefficients H1, H2 (hrows x s each, against an orthonormal basis) left of a block
+// W0, and the deflation scale is W0's column norms^2, ||(H1 + H2)(:, c)||^2 + (W^T W)_cc;
+// ref2 is then not read.
 bool cqr_supported(int32_t s);
 int cqr_chunks(int32_t n);
 int launch_cqr_gram(cudaStream_t st, int32_t s, int32_t n, const double *W, const double *ref2, double tau2,
-                    double *partial, unsigned *ticket, double *R1, int32_t *defl1);
+                    const double *H1, const double *H2, int32_t hrows, double *partial, unsigned *ticket,
+                    double *R1, int32_t *defl1);
 int launch_cqr_gram2(cudaStream_t st, int32_t s, int32_t n, const double *W, const double *R1, const int32_t *defl1,
                      double *Q1, double *partial, unsigned *ticket, double *R2, int32_t *defl2, double *Rout);
 // (Q32: non-null for an FP32 copy of Q as well)
