@@ -281,13 +281,13 @@ __global__ void __launch_bounds__(kThreads) k_trsm_rows(int32_t n, const double 
 
 // ---------------------------------------------------------------------------------
 // Cholesky-QR kernels for S <= 8.  A block of 256 threads walks its row chunk (one tile
-// where n allows) in tiles of 256 rows: each thread loads one row with 16-byte loads (k_trsm_gram also solves it
-// against R and stores it as Q1) into a shared-memory tile; then thread (pair p = (a, b),
-// a <= b; row group g) adds x_a x_b over rows g, g + RG, ... of the tile, while the
-// thread's row of the next tile is already being loaded (the FP64 pipe, not the loads,
-// bounds these kernels on GB300, so it should not wait for them).  The FP64
-// reduction at the end is one sum over the RG groups per pair (FP64 adds are as dear as
-// FMAs on this GPU, so no per-thread butterflies).
+// where n allows) in tiles of 256 rows: each thread loads one row with 16-byte loads
+// (k_trsm_gram and k_cqr_gram2 also solve it against R and store it as Q1) into a
+// shared-memory tile; then thread (pair p = (a, b), a <= b; row group g) adds x_a x_b
+// over rows g, g + RG, ... of the tile, while the thread's row of the next tile is already
+// being loaded (the FP64 pipe, not the loads, bounds these kernels on GB300, so it should
+// not wait for them).  The FP64 reduction at the end is one sum over the RG groups per
+// pair (FP64 adds are as dear as FMAs on this GPU, so no per-thread butterflies).
 //   k_gram_rows:  partial[chunk] of G = W^T W
 //   k_trsm_gram:  Q1 = W R^{-1} written, and partial[chunk] of G2 = Q1^T Q1, one pass
 // ---------------------------------------------------------------------------------
