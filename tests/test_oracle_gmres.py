@@ -138,3 +138,31 @@ def test_paper_quoted_savings_from_printed_tables():
     assert abs(block - g["quoted_block_saving"]) < 0.01
     assert abs(upd - g["quoted_update_saving"]) < 0.02
     assert abs(both - g["quoted_block_plus_update_saving"]) < 0.02
+
+
+@pytest.mark.parametrize("scale", [1.0, 1e-6, 1e-11, 1e-13])
+def test_cgs2_coefficients_give_the_deflation_scale(scale):
+    """The deflation scale of the new block's QR is each column's norm before the two block
+    CGS passes (``wn`` in the oracle's Arnoldi step).  Against a basis whose columns are
+    orthonormal or zero (deflated), W0 = V (H1 + H2) + W2 with W2 orthogonal to V, so
+    ||W0(:, c)||^2 = ||(H1 + H2)(:, c)||^2 + ||W2(:, c)||^2: the GPU's first Cholesky-QR pass
+    forms the scale this way from quantities it already has.  Checked on blocks from fully
+    independent down to numerically dependent (scale = the size of the part outside V),
+    and the deflation decision of ``_block_qr``'s threshold is the same with either scale."""
+    rng = np.random.default_rng(7)
+    n, s, nb = 500, 8, 6
+    V, _ = np.linalg.qr(rng.standard_normal((n, nb * s)))
+    V[:, [5, 19, 40]] = 0.0  # deflated basis columns
+    W0 = V @ rng.standard_normal((nb * s, s)) + scale * rng.standard_normal((n, s))
+    W0[:, 2] *= 1e3  # columns of different sizes
+    wn2 = np.sum(W0 * W0, axis=0)
+    H1 = V.T @ W0
+    W1 = W0 - V @ H1
+    H2 = V.T @ W1
+    W2 = W1 - V @ H2
+    est = np.sum((H1 + H2) ** 2, axis=0) + np.sum(W2 * W2, axis=0)
+    assert np.max(np.abs(est - wn2) / wn2) <= 1e-13
+    # the deflation threshold (|R_kk| <= 1e-12 * scale) decides the same with either scale
+    _, R = np.linalg.qr(W2)
+    d = np.abs(np.diag(R))
+    assert np.array_equal(d <= oracle.DEFLATE_REL * np.sqrt(wn2), d <= oracle.DEFLATE_REL * np.sqrt(est))
